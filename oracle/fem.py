@@ -1,0 +1,168 @@
+"""P1 finite elements on the uniform triangulation of D = (0,1)^2 (Sec. 2.3).
+
+Test infrastructure only (see ``oracle/__init__.py``).
+
+Mesh reading (the paper only says "uniform triangular meshes"): the unit
+square is cut into n x n squares of side h = 1/n and each square is split by
+its south-west to north-east diagonal.  Cell (i, j) = [ih,(i+1)h] x [jh,(j+1)h]
+holds the lower triangle {(i,j), (i+1,j), (i+1,j+1)} and the upper triangle
+{(i,j), (i+1,j+1), (i,j+1)}.  Homogeneous Dirichlet conditions: only the
+(n-1)^2 interior nodes are unknowns, numbered row by row,
+k = (j-1)(n-1) + (i-1).
+
+The coefficient is constant on each triangle, equal to a at the centroid
+(one-point rule); the mass matrix is the exact consistent P1 mass (c = 1).
+Matrices are assembled by an explicit loop over elements from the vertex
+coordinates: nothing here assumes the stencil that results.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+
+def mesh(n: int):
+    """Return (coords [(n+1)^2, 2], triangles [2n^2, 3] vertex ids, interior map).
+
+    Node id = j*(n+1) + i.  Triangle t = p*n*n + j*n + i with p = 0 for the lower and
+    p = 1 for the upper triangle of cell (i, j).  ``interior[id]`` is the unknown
+    number of a node, or -1 on the boundary.
+    """
+    h = 1.0 / n
+    idx = np.arange(n + 1)
+    I, J = np.meshgrid(idx, idx, indexing="xy")  # I[j, i] = i
+    coords = np.stack([I.ravel() * h, J.ravel() * h], axis=1)
+
+    def nid(i, j):
+        return j * (n + 1) + i
+
+    tris = np.zeros((2, n, n, 3), dtype=np.int64)
+    for j in range(n):
+        for i in range(n):
+            tris[0, j, i] = (nid(i, j), nid(i + 1, j), nid(i + 1, j + 1))
+            tris[1, j, i] = (nid(i, j), nid(i + 1, j + 1), nid(i, j + 1))
+    tris = tris.reshape(-1, 3)
+
+    interior = -np.ones((n + 1) * (n + 1), dtype=np.int64)
+    for j in range(1, n):
+        for i in range(1, n):
+            interior[nid(i, j)] = (j - 1) * (n - 1) + (i - 1)
+    return coords, tris, interior
+
+
+def centroids(n: int) -> np.ndarray:
+    """Centroids of all 2 n^2 triangles, as the mean of the three vertices."""
+    coords, tris, _ = mesh(n)
+    return coords[tris].mean(axis=1)
+
+
+def psi_pairs(s: int):
+    """Frequency pairs (k1, k2) of the first s terms of the synthetic coefficient family.
+
+    All pairs with k1, k2 >= 1 ordered by k1^2 + k2^2, ties broken by smaller k1.
+    """
+    K = int(np.ceil(2.0 * np.sqrt(max(s, 1)))) + 2
+    pairs = [(k1, k2) for k1 in range(1, K + 1) for k2 in range(1, K + 1)]
+    pairs.sort(key=lambda p: (p[0] ** 2 + p[1] ** 2, p[0]))
+    return pairs[:s]
+
+
+def psi_matrix(n: int, s: int, decay: float = 2.0) -> np.ndarray:
+    """Psi[t, j-1] = psi_j(c_t) = j^-decay sin(pi k1_j x1) sin(pi k2_j x2) at triangle centroids."""
+    c = centroids(n)
+    out = np.zeros((c.shape[0], s))
+    for j, (k1, k2) in enumerate(psi_pairs(s), start=1):
+        out[:, j - 1] = j ** (-decay) * np.sin(np.pi * k1 * c[:, 0]) * np.sin(np.pi * k2 * c[:, 1])
+    return out
+
+
+def coefficient(n: int, y: np.ndarray, a0: float = 1.0, decay: float = 2.0) -> np.ndarray:
+    """a(c_t, y) = a0 + sum_{j<=s} y_j psi_j(c_t) for every triangle t (eq. coeff, eq. coeff_s).
+
+    The truncation dimension is len(y): terms beyond it are zero.
+    """
+    y = np.asarray(y, dtype=np.float64)
+    if y.size == 0:
+        return np.full(2 * n * n, float(a0))
+    return a0 + psi_matrix(n, y.size, decay) @ y
+
+
+def element_matrices(coords: np.ndarray, tri: np.ndarray):
+    """Local P1 stiffness (for a = 1) and consistent mass of one triangle."""
+    p = coords[tri]  # 3 x 2
+    B = np.array([[p[1, 0] - p[0, 0], p[2, 0] - p[0, 0]],
+                  [p[1, 1] - p[0, 1], p[2, 1] - p[0, 1]]])
+    area = 0.5 * abs(np.linalg.det(B))
+    ref_grad = np.array([[-1.0, -1.0], [1.0, 0.0], [0.0, 1.0]])  # gradients on the reference triangle
+    G = ref_grad @ np.linalg.inv(B)  # rows: physical gradients of the three hat functions
+    K = area * (G @ G.T)
+    Mloc = (area / 12.0) * (np.ones((3, 3)) + np.eye(3))
+    return K, Mloc
+
+
+_ELEMENT_CACHE: dict = {}
+
+
+def _element_entries(n: int, with_boundary: bool):
+    """Element loop over all triangles: for every local (a, b) pair whose two nodes are
+    unknowns, record (row, col, triangle, K_ab for a = 1, M_ab).  The geometric part does
+    not depend on the coefficient, so it is cached per mesh."""
+    key = (n, with_boundary)
+    if key in _ELEMENT_CACHE:
+        return _ELEMENT_CACHE[key]
+    coords, tris, interior = mesh(n)
+    rows, cols, tt, kv, mv = [], [], [], [], []
+    for t in range(tris.shape[0]):
+        K, Mloc = element_matrices(coords, tris[t])
+        for a in range(3):
+            ga = tris[t, a]
+            ra = ga if with_boundary else interior[ga]
+            if ra < 0:
+                continue
+            for b in range(3):
+                gb = tris[t, b]
+                cb = gb if with_boundary else interior[gb]
+                if cb < 0:
+                    continue
+                rows.append(ra)
+                cols.append(cb)
+                tt.append(t)
+                kv.append(K[a, b])
+                mv.append(Mloc[a, b])
+    ent = tuple(np.asarray(v) for v in (rows, cols, tt, kv, mv))
+    _ELEMENT_CACHE[key] = ent
+    return ent
+
+
+def assemble(n: int, a_t: np.ndarray | None = None, with_boundary: bool = False):
+    """Stiffness A = sum_T a_T K_T and mass M = sum_T M_T over the elements (Sec. 2.3).
+
+    Returns sparse CSR matrices over the interior unknowns, or over all (n+1)^2
+    nodes when ``with_boundary`` is set (used by exactness tests).
+    """
+    nt = 2 * n * n
+    if a_t is None:
+        a_t = np.ones(nt)
+    a_t = np.asarray(a_t, dtype=np.float64).ravel()
+    assert a_t.size == nt
+    rows, cols, tt, kv, mv = _element_entries(n, with_boundary)
+    size = (n + 1) ** 2 if with_boundary else (n - 1) ** 2
+    A = sp.coo_matrix((a_t[tt] * kv, (rows, cols)), shape=(size, size)).tocsr()
+    M = sp.coo_matrix((mv, (rows, cols)), shape=(size, size)).tocsr()
+    A.sum_duplicates()
+    M.sum_duplicates()
+    return A, M
+
+
+_MASS_CACHE: dict = {}
+
+
+def mass(n: int):
+    """The y-independent mass matrix (built once per mesh, Sec. 4.2)."""
+    if n not in _MASS_CACHE:
+        _MASS_CACHE[n] = assemble(n, np.ones(2 * n * n))[1]
+    return _MASS_CACHE[n]
+
+
+def stiffness(n: int, a_t: np.ndarray):
+    return assemble(n, a_t)[0]

@@ -1,0 +1,81 @@
+"""Per-sample level differences and the two-grid MLQMC estimator (Sec. 4.3).
+
+Test infrastructure only (see ``oracle/__init__.py``).
+
+Algorithm 2, for level l with fine mesh h_l, truncation s_l, coarse mesh H_l
+and coarse truncation S_l, shift Delta^(r) and lattice point k:
+
+* y = {k z_l / N_l + Delta^(r)} - 1/2 (eq. t_kl, eq. rqmc), k = 0..N_l-1.
+* the coarse pair (lambda_H, u_H) on (H_l, S_l) (step 6);
+* lambda^l by the two-grid update on (h_l, s_l) (eq. 2grid_src_ell,
+  eq. 2grid_update_ell);
+* for l > 0, lambda^{l-1} by the two-grid update on (h_{l-1}, s_{l-1}) from the
+  SAME coarse pair (steps 10-14); lambda^{-1} = 0;
+* Q^(r)_l = (1/N_l) sum_k (lambda^l - lambda^{l-1}) (steps 15-16),
+  Qhat_l = mean over r, Qhat^ML = sum_l Qhat_l (eq. tg-mlqmc), and the
+  sample-variance error estimate of eq. sample_var per level, added over
+  the independent levels (eq. ml-var).
+
+A level whose coarse mesh and truncation equal its fine ones (H_l = h_l,
+S_l = s_l) is a direct eigensolve: lambda^l = lambda_{h_l, s_l}.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import lattice, twogrid
+
+
+def sample_level(level, prev, y, a0: float = 1.0, decay: float = 2.0):
+    """(lambda_H, lambda^l, lambda^{l-1}, difference) for one parameter vector y (len >= s_l).
+
+    ``level`` and ``prev`` carry n_fine, n_coarse, s, S (``prev`` is None on level 0).
+    """
+    lam_H, u_H = twogrid.coarse_pair(level.n_coarse, y[: level.S], a0, decay)
+    if level.n_fine == level.n_coarse and level.s == level.S:
+        lam_l = lam_H
+    else:
+        lam_l = twogrid.twogrid_update(level.n_fine, y[: level.s], lam_H, u_H, level.n_coarse, a0, decay)
+    if prev is None:
+        return lam_H, lam_l, 0.0, lam_l
+    if prev.n_fine == level.n_coarse and prev.s == level.S:
+        lam_p = lam_H
+    else:
+        lam_p = twogrid.twogrid_update(prev.n_fine, y[: prev.s], lam_H, u_H, level.n_coarse, a0, decay)
+    return lam_H, lam_l, lam_p, lam_l - lam_p
+
+
+def level_samples(level, prev, z, delta, ks, a0: float = 1.0, decay: float = 2.0) -> np.ndarray:
+    """Per-sample results [R, len(ks), 4] = (lambda_H, lambda^l, lambda^{l-1}, diff) at lattice
+    indices ks for every shift row of ``delta`` [R, s_l]."""
+    delta = np.atleast_2d(delta)
+    out = np.zeros((delta.shape[0], len(ks), 4))
+    for r in range(delta.shape[0]):
+        Y = lattice.points(z, level.N, delta[r], ks)
+        for i in range(len(ks)):
+            out[r, i] = sample_level(level, prev, Y[i], a0, decay)
+    return out
+
+
+def shift_means(diffs: np.ndarray, N: int) -> np.ndarray:
+    """Q^(r)_l = (1/N_l) sum_k diff[r, k] for each shift r (Algorithm 2, steps 15-16)."""
+    return np.asarray(diffs).sum(axis=1) / N
+
+
+def estimate(level_shift_means):
+    """Shift-averaged MLQMC estimate and its standard error.
+
+    ``level_shift_means[l]`` holds Q^(r)_l for r = 1..R.  Returns (Qhat^ML, SE, Qhat_l[], Vhat_l[])
+    with Vhat_l = sum_r (Qhat_l - Q^(r)_l)^2 / (R (R - 1)) (eq. sample_var) and
+    SE = sqrt(sum_l Vhat_l) (eq. ml-var).
+    """
+    qhat, vhat = [], []
+    for q in level_shift_means:
+        q = np.asarray(q, dtype=np.float64)
+        R = q.size
+        if R < 2:
+            raise ValueError("the sample-variance estimate needs R >= 2 shifts")
+        m = q.sum() / R
+        qhat.append(m)
+        vhat.append(((m - q) ** 2).sum() / (R * (R - 1)))
+    return float(sum(qhat)), float(np.sqrt(sum(vhat))), qhat, vhat

@@ -1,0 +1,124 @@
+"""Seeded synthetic inputs shared by the oracle, the tests and the benchmark.
+
+This module holds no arithmetic of the method: only the workload table (mesh
+widths, truncation dimensions, point counts, shift counts, seeds) and seeded
+random draws.  Everything the method computes from these inputs (lattice
+generating vectors, lattice points, coefficients, eigenpairs) is implemented
+separately on each side.
+
+Random shifts (Sec. 2.5, randomly shifted rank-1 lattice rules): the paper does
+not name a generator.  The shifts are drawn with
+``numpy.random.default_rng(seed).random((R, s_l))``, level by level for
+l = 0..L in order, and passed to both sides as inputs.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import List
+
+import numpy as np
+
+
+@dataclass(frozen=True)
+class Level:
+    """One MLQMC level: fine mesh 1/n_fine, coarse mesh 1/n_coarse, truncations s and S,
+    N lattice points and R shifts.  n_coarse == n_fine with S == s marks a direct
+    (non-two-grid) eigensolve on that level."""
+
+    n_fine: int
+    n_coarse: int
+    s: int
+    S: int
+    N: int
+    R: int
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    levels: List[Level]
+    seed: int
+    precision: str  # "fp64" or "mixed"
+    tol: float  # relative tolerance on each per-sample eigenvalue versus the oracle
+    a0: float = 1.0
+    decay: float = 2.0
+    notes: str = ""
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def samples(self) -> int:
+        return sum(lv.N * lv.R for lv in self.levels)
+
+
+def _ceil_sqrt(s: int) -> int:
+    r = int(np.floor(np.sqrt(s)))
+    while r * r < s:
+        r += 1
+    return r
+
+
+# The five workloads of the build.  Coarse truncation S = ceil(sqrt(s)) (Sec. 4.3);
+# coarse meshes as read for each workload.
+WORKLOADS = {
+    # single level, FP64: h = 1/16 (225 dofs), H = 1/8, s = 16, S = 4, N = 256, R = 8, seed 0
+    "qmc_h16_s16": Workload(
+        "qmc_h16_s16",
+        [Level(16, 8, 16, 4, 256, 8)],
+        seed=0, precision="fp64", tol=1e-10,
+    ),
+    # 4-level MLQMC, FP64: h = 1/16..1/128, H = 1/8,1/8,1/16,1/16, s = 16..128
+    "mlqmc4_h16_128": Workload(
+        "mlqmc4_h16_128",
+        [
+            Level(16, 8, 16, _ceil_sqrt(16), 4096, 16),
+            Level(32, 8, 32, _ceil_sqrt(32), 2048, 16),
+            Level(64, 16, 64, _ceil_sqrt(64), 1024, 16),
+            Level(128, 16, 128, _ceil_sqrt(128), 512, 16),
+        ],
+        seed=1, precision="fp64", tol=1e-10,
+    ),
+    # single level h = 1/512, H = 1/32, s = 256, S = 16, 64 points x 16 shifts
+    "single_h512_s256": Workload(
+        "single_h512_s256",
+        [Level(512, 32, 256, 16, 64, 16)],
+        seed=2, precision="mixed", tol=1e-10,
+    ),
+    # 6-level MLQMC h = 1/32..1/1024, level 0 direct (H = h0 = 1/32, S = s0)
+    "mlqmc6_h32_1024": Workload(
+        "mlqmc6_h32_1024",
+        [Level(32, 32, 32, 32, 16384, 16)]
+        + [Level(32 << l, 32, 32 << l, _ceil_sqrt(32 << l), 16384 >> l, 16) for l in range(1, 6)],
+        seed=3, precision="mixed", tol=1e-7,
+    ),
+    # h = 1/1024 (1,046,529 dofs), H = 1/64, s = 1024, S = 32, 32 points x 16 shifts
+    "stress_h1024_s1024": Workload(
+        "stress_h1024_s1024",
+        [Level(1024, 64, 1024, 32, 32, 16)],
+        seed=4, precision="mixed", tol=1e-7,
+    ),
+}
+
+
+def shifts(seed: int, levels: List[Level]) -> List[np.ndarray]:
+    """Random shifts Delta_l in [0,1)^{R x s_l}, drawn level by level from one generator."""
+    rng = np.random.default_rng(seed)
+    return [rng.random((lv.R, lv.s)) for lv in levels]
+
+
+def random_points(seed: int, count: int, s: int) -> np.ndarray:
+    """Uniform parameter vectors y in [-1/2, 1/2)^s for single-point tests."""
+    rng = np.random.default_rng(seed)
+    return rng.random((count, s)) - 0.5
+
+
+def random_vectors(seed: int, count: int, n: int) -> np.ndarray:
+    """Standard normal test vectors (operator-apply tests)."""
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((count, n))
+
+
+def random_cell_coefficients(seed: int, count: int, n: int, lo: float = 0.2, hi: float = 1.8) -> np.ndarray:
+    """Per-triangle coefficients in [lo, hi): layout [count][2][n][n] (lower / upper triangle
+    of cell (i, j) at [.][0][j][i] / [.][1][j][i])."""
+    rng = np.random.default_rng(seed)
+    return lo + (hi - lo) * rng.random((count, 2, n, n))

@@ -1,0 +1,112 @@
+"""Pins for the oracle's lattice rules, CBC construction (Sec. 2.5) and estimator
+(Algorithm 2, eq. sample_var, eq. tg-mlqmc)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import lattice, mlqmc
+from synthetic_inputs import Level
+
+
+@pytest.mark.parametrize("N", [8, 64, 256, 1024])
+def test_first_component_is_one(N):
+    assert lattice.cbc(N, 3)[0] == 1
+
+
+@pytest.mark.parametrize("N", [4, 16, 128])
+def test_one_dimensional_error_closed_form(N):
+    # sum_k B2(k/N) = 1/(6N), so e^2 = gamma_1/(6 N^2) for z = 1
+    assert lattice.cbc_error2([1], N, [1.0]) == pytest.approx(1.0 / (6 * N * N), rel=1e-12)
+    assert lattice.cbc_error2([1], N, [0.25]) == pytest.approx(0.25 / (6 * N * N), rel=1e-12)
+
+
+@pytest.mark.parametrize("N,s", [(16, 4), (32, 3), (64, 4)])
+def test_cbc_is_componentwise_argmin(N, s):
+    gamma = [(j + 1) ** -2.0 for j in range(s)]
+    z = lattice.cbc(N, s)
+    for j in range(1, s):
+        cands = [c for c in range(1, N // 2 + 1) if math.gcd(c, N) == 1]
+        errs = [lattice.cbc_error2(list(z[:j]) + [c], N, gamma[: j + 1]) for c in cands]
+        best = min(errs)
+        assert lattice.cbc_error2(list(z[: j + 1]), N, gamma[: j + 1]) <= best * (1 + 1e-10)
+        # tie rule: no smaller candidate reaches the minimum
+        first = next(c for c, e in zip(cands, errs) if e <= best * (1 + 1e-10))
+        assert z[j] == first
+
+
+def test_lattice_dual_exactness():
+    # (1/N) sum_k exp(2 pi i m.(t_k + Delta)) = exp(2 pi i m.Delta) if m.z = 0 mod N, else 0
+    N, s = 64, 3
+    z = lattice.cbc(N, s)
+    rng = np.random.default_rng(5)
+    delta = rng.random(s)
+    Y = lattice.points(z, N, delta, np.arange(N)) + 0.5
+    for m in [(1, 0, 0), (0, 1, 1), (2, -1, 3), (int(z[1]), -1, 0), (5, 7, -2), (N, 0, 0)]:
+        m = np.array(m)
+        val = np.exp(2j * np.pi * (Y @ m)).mean()
+        if int(m @ z) % N == 0:
+            assert abs(val - np.exp(2j * np.pi * (m @ delta))) < 1e-12
+        else:
+            assert abs(val) < 1e-12
+
+
+def test_lattice_integrates_low_order_trig_product_exactly():
+    # prod_j (1 + alpha_j cos(2 pi m_j x_j)) has integral 1; exact when no nonzero m with
+    # |m_j| <= 1 lies in the dual lattice
+    N, s = 128, 3
+    z = lattice.cbc(N, s)
+    import itertools
+    dual_free = all(int(np.dot(m, z)) % N != 0
+                    for m in itertools.product((-1, 0, 1), repeat=s) if any(m))
+    assert dual_free
+    Y = lattice.points(z, N, np.array([0.1, 0.7, 0.33]), np.arange(N)) + 0.5
+    f = np.prod(1 + np.array([0.5, 0.3, 0.2]) * np.cos(2 * np.pi * Y), axis=1)
+    assert abs(f.mean() - 1.0) < 1e-13
+    # and a rule that is not dual-free misses: z = (1, 1, 1) has m = (1, -1, 0) in its dual
+    Y = lattice.points(np.array([1, 1, 1]), N, np.array([0.1, 0.7, 0.33]), np.arange(N)) + 0.5
+    f = np.prod(1 + np.array([0.5, 0.3, 0.2]) * np.cos(2 * np.pi * Y), axis=1)
+    assert abs(f.mean() - 1.0) > 1e-3
+
+
+def test_points_range_and_origin():
+    z = np.array([1, 3, 5])
+    Y = lattice.points(z, 16, np.zeros(3), np.arange(16))
+    assert np.all(Y >= -0.5) and np.all(Y < 0.5)
+    assert np.all(Y[0] == -0.5)
+    Y = lattice.points(z, 16, np.array([0.99, 0.5, 0.0]), [3])
+    assert np.allclose(Y[0], [np.mod(3 / 16 + 0.99, 1) - 0.5, np.mod(9 / 16 + 0.5, 1) - 0.5, 15 / 16 - 0.5])
+
+
+def test_estimator_worked_example():
+    # two levels, two shifts: Q^(r)_0 = (1, 3), Q^(r)_1 = (0.5, 0.25)
+    est, se, qhat, vhat = mlqmc.estimate([[1.0, 3.0], [0.5, 0.25]])
+    assert qhat == [2.0, 0.375]
+    assert vhat == [1.0, 0.015625]
+    assert est == 2.375
+    assert se == pytest.approx(np.sqrt(1.015625))
+
+
+def test_estimator_needs_two_shifts():
+    with pytest.raises(ValueError):
+        mlqmc.estimate([[1.0]])
+
+
+def test_shift_means():
+    d = np.array([[1.0, 2.0, 3.0, 4.0], [0.0, 0.0, 0.0, 8.0]])
+    assert np.allclose(mlqmc.shift_means(d, 4), [2.5, 2.0])
+
+
+def test_sample_level_difference_uses_one_coarse_pair():
+    from oracle import twogrid
+    lv = Level(32, 8, 8, 3, 16, 2)
+    pv = Level(16, 8, 4, 2, 16, 2)
+    y = np.array([0.2, -0.1, 0.3, 0.05, -0.4, 0.1, 0.2, -0.2])
+    lam_H, lam_l, lam_p, d = mlqmc.sample_level(lv, pv, y)
+    lH, uH = twogrid.coarse_pair(8, y[:3])
+    assert lam_H == lH
+    assert lam_l == twogrid.twogrid_update(32, y[:8], lH, uH, 8)
+    assert lam_p == twogrid.twogrid_update(16, y[:4], lH, uH, 8)
+    assert d == lam_l - lam_p
+    # level 0: lambda^{-1} = 0
+    assert mlqmc.sample_level(pv, None, y)[3] == mlqmc.sample_level(pv, None, y)[1]
