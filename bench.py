@@ -1,0 +1,352 @@
+"""Throughput of the two-grid MLQMC level evaluation on one GB300 (or N, one process per GPU).
+
+A step is one pass of the whole hot path over one batch of synthetic input: every level of the
+workload, every shift, every lattice point -- lattice points, centroid coefficients, coarse
+eigensolves, fine shifted solves, Rayleigh quotients, level differences and per-shift sums.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--precision fp64|mixed]
+    python bench.py --impl reference ...     # the FP64 CPU oracle on a bounded sample
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synthetic_inputs import WORKLOADS, shifts  # noqa: E402
+
+METRIC = "two-grid eigen-samples/s at rel. err<=1e-10 vs FP64 oracle; mixed vs plain GPU"
+DEFAULT_WORKLOAD = "mlqmc4_h16_128"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--no-baseline", action="store_true", help="skip the timed CPU oracle sample")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison run")
+    ap.add_argument("--baseline-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+class ClockSampler:
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.reasons = set()
+        self._stop = threading.Event()
+        self._th = None
+
+    def _run(self):
+        q = ("index,clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                f = [x.strip() for x in out.stdout.strip().split(",")]
+                if len(f) >= 8:
+                    self.samples.append((float(f[1]), float(f[2])))
+                    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+                    for nm, v in zip(names, f[4:8]):
+                        if v.lower().startswith("active"):
+                            self.reasons.add(nm)
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._th = threading.Thread(target=self._run, daemon=True)
+        self._th.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._th:
+            self._th.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": sorted(self.reasons), "samples": 0}
+        return {"sm_mhz": statistics.median(s[0] for s in self.samples),
+                "sm_max_mhz": max(s[1] for s in self.samples), "reasons": sorted(self.reasons),
+                "samples": len(self.samples)}
+
+
+# ------------------------------------------------------------------------------------------
+def setup_context(binding, wl, stream_ptr, prec, seed_offset=0):
+    ctx = binding.Context(0, stream_ptr)
+    ctx.mq_set_coefficient(wl.a0, max(lv.s for lv in wl.levels), 0, wl.decay)
+    ctx.mq_set_levels(wl.levels)
+    zs = [binding.mq_cbc_lattice(lv.N, lv.s, wl.decay) for lv in wl.levels]
+    ds = shifts(wl.seed + seed_offset, wl.levels)
+    for l in range(len(wl.levels)):
+        ctx.mq_set_lattice(l, zs[l])
+        ctx.mq_set_shifts(l, ds[l])
+    ctx.mq_set_precision(binding.MQ_PREC_MIXED if prec == "mixed" else binding.MQ_PREC_FP64)
+    return ctx, zs, ds
+
+
+def run_device_step(ctx, wl, outs, sums):
+    for l, lv in enumerate(wl.levels):
+        ctx.mq_eval_level_device(l, 0, lv.N, outs[l], sums[l])
+
+
+def time_device(binding, torch, wl, prec, steps, warmup, stream, seed_offset=0):
+    ctx, zs, ds = setup_context(binding, wl, stream.cuda_stream, prec, seed_offset)
+    outs = [torch.empty((lv.R, lv.N, 4), dtype=torch.float64, device="cuda") for lv in wl.levels]
+    sums = [torch.empty(lv.R, dtype=torch.float64, device="cuda") for lv in wl.levels]
+    for _ in range(warmup):
+        run_device_step(ctx, wl, outs, sums)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        run_device_step(ctx, wl, outs, sums)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    # per-level kernel times and iteration counts from one more (untimed) pass
+    per_level_ms = np.zeros(len(wl.levels))
+    kstats = {}
+    for l, lv in enumerate(wl.levels):
+        ctx.mq_eval_level_device(l, 0, lv.N, outs[l], sums[l])
+        st = ctx.mq_get_stats()
+        per_level_ms[l] = st["kernel_ms"]
+        kstats[l] = [st]
+    return ctx, ms, per_level_ms * steps, kstats, outs
+
+
+def time_e2e(binding, wl, prec, steps, stream_ptr):
+    """End to end through the public host API: every step uploads the lattices and shifts from
+    host memory and reads every per-sample result back."""
+    import torch
+
+    ctx, zs, ds = setup_context(binding, wl, stream_ptr, prec)
+    h2d = sum(z.nbytes + d.nbytes for z, d in zip(zs, ds))
+    d2h = sum(lv.R * lv.N * 4 * 8 + lv.R * 8 for lv in wl.levels)
+    host_out = [np.zeros((lv.R, lv.N, 4)) for lv in wl.levels]
+    # one untimed pass
+    for l, lv in enumerate(wl.levels):
+        ctx.mq_eval_level(l, 0, lv.N)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        ctx.mq_reset_sums()
+        for l, lv in enumerate(wl.levels):
+            ctx.mq_set_lattice(l, zs[l])
+            ctx.mq_set_shifts(l, ds[l])
+            ps, _ = ctx.mq_eval_level(l, 0, lv.N)
+            host_out[l] = ps
+        ctx.mq_estimate()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    ctx.close()
+    return dt, h2d, d2h
+
+
+# ------------------------------------------------------------------------------------------
+def _oracle_sample(args):
+    import os as _os
+
+    _os.environ.setdefault("OMP_NUM_THREADS", "1")
+    _os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    from oracle import mlqmc
+
+    lv, pv, z, delta_row, k = args
+    t = time.perf_counter()
+    mlqmc.level_samples(lv, pv, z, delta_row[None, :], [k])
+    return time.perf_counter() - t
+
+
+def cpu_baseline(wl, seconds_budget, zs, ds):
+    """Times the oracle as it stands on a bounded sample of every level (one sample per process,
+    all host cores) and scales to samples/s of the whole workload."""
+    import multiprocessing as mp
+
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    per_level = []
+    total_t = 0.0
+    with ctx.Pool(cores, initializer=_pool_init) as pool:
+        # one warm sample per level (imports, caches), then a timed batch per level
+        for l, lv in enumerate(wl.levels):
+            pv = wl.levels[l - 1] if l > 0 else None
+            pool.map(_oracle_sample, [(lv, pv, zs[l], ds[l][0], 0)] * cores)
+        budget_per_level = seconds_budget / len(wl.levels)
+        for l, lv in enumerate(wl.levels):
+            pv = wl.levels[l - 1] if l > 0 else None
+            # probe the per-sample cost with one wave, then size the timed wave
+            t0 = time.perf_counter()
+            pool.map(_oracle_sample, [(lv, pv, zs[l], ds[l][i % lv.R], i) for i in range(cores)])
+            wave = time.perf_counter() - t0
+            waves = max(1, int(budget_per_level / max(wave, 1e-3)))
+            n = waves * cores
+            t0 = time.perf_counter()
+            pool.map(_oracle_sample, [(lv, pv, zs[l], ds[l][i % lv.R], (i * 7) % lv.N) for i in range(n)])
+            dt = time.perf_counter() - t0
+            per_level.append((n, dt))
+            total_t += dt
+    # whole-workload time = sum over levels of (samples of the level / measured rate)
+    est = sum(lv.N * lv.R * dt / n for lv, (n, dt) in zip(wl.levels, per_level))
+    value = wl.samples / est
+    sample = "; ".join(f"level {l}: {n} samples in {dt:.1f} s" for l, (n, dt) in enumerate(per_level))
+    return {"value": value, "unit": "samples/s", "cores": cores, "kind": "oracle",
+            "sample": sample + f" (extrapolated to {wl.samples} samples by the per-level rates)"}
+
+
+def _pool_init():
+    os.environ["OMP_NUM_THREADS"] = "1"
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+
+
+# ------------------------------------------------------------------------------------------
+def fp64_peak_tflops(clock_mhz=None):
+    """Nominal FP64 rate of a GB300 (1.25 TFLOP/s at the boost clock), scaled to the sampled clock."""
+    nominal = 1.25
+    if clock_mhz:
+        return nominal * clock_mhz / 2070.0
+    return nominal
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return main_reference(args, wl, rank, world)
+    import torch
+
+    from paper_2103_03407_gb300 import binding, build
+
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        torch.cuda.set_device(local)
+    build.build()
+    binding.load()
+    stream = torch.cuda.Stream()
+    sampler = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        with sampler:
+            ctx, ms, per_level_ms, kstats, outs = time_device(binding, torch, wl, args.precision, args.steps,
+                                                              args.warmup, stream, seed_offset=rank)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    samples_per_step = wl.samples * world
+    value = samples_per_step * args.steps / (ms / 1e3)
+    plain = None
+    if not args.no_plain and args.precision == "mixed" and rank == 0:
+        ctxp, msp, _, _, _ = time_device(binding, torch, wl, "fp64", 1, 1, stream)
+        plain = {"value": wl.samples / (msp / 1e3), "unit": "samples/s", "ms_per_step": msp, "steps": 1}
+        ctxp.close()
+    e2e = None
+    if not args.no_e2e:
+        dt, h2d, d2h = time_e2e(binding, wl, args.precision, max(1, args.steps), stream.cuda_stream)
+        e2e = {"value": wl.samples * max(1, args.steps) / dt, "unit": "samples/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+    # dominant kernel: the per-sample kernel of the finest level
+    lst = [kstats[l][-1] for l in range(len(wl.levels))]
+    sample_ms = [s["sample_ms"] for s in lst]
+    coef_ms = [s["coef_ms"] for s in lst]
+    top = int(np.argmax(sample_ms))
+    clocks = sampler.summary()
+    roofline = {"bound": "alu", "kernel": f"sample_kernel level {top}", "achieved": None,
+                "peak": fp64_peak_tflops(), "unit": "TFLOP/s", "frac": None, "traffic": None,
+                "note": "FP64 flop model pending"}
+    result = {
+        "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "levels": [lv.__dict__ for lv in wl.levels], "samples_per_step": wl.samples,
+                   "precision": args.precision, "l2": "inputs larger than L2 (coefficient fields of the finest "
+                   "level exceed 129 MB)", "parallelism": f"dp{world} (independent shifts per rank)"},
+        "e2e": e2e, "gpu_launches": None, "roofline": roofline, "clocks": clocks,
+        "per_level": [{"level": l, "kernel_ms": float(per_level_ms[l] / args.steps), "coef_ms": coef_ms[l],
+                       "sample_ms": sample_ms[l], "coarse_iters_mean": lst[l]["coarse_iters_mean"],
+                       "fine_iters_mean": lst[l]["fine_iters_mean"], "outer_iters_mean": lst[l]["outer_iters_mean"],
+                       "blocks": lst[l]["blocks"], "threads": lst[l]["threads"], "smem": lst[l]["smem_bytes"],
+                       "workspace": lst[l]["workspace_bytes"]} for l in range(len(wl.levels))],
+        "plain_fp64": plain,
+    }
+    # kernels launched per step: per level lattice + 2-3 GEMMs + sample + shift sums
+    launches = 0
+    for l in range(len(wl.levels)):
+        launches += 1 + 1 + (0 if wl.levels[l].n_fine == wl.levels[l].n_coarse and wl.levels[l].s == wl.levels[l].S
+                             else 1) + (1 if l > 0 else 0) + 1 + 1
+    result["gpu_launches"] = launches * args.steps
+    if rank == 0 and not args.no_baseline:
+        result["cpu_baseline"] = cpu_baseline(wl, args.baseline_seconds, ctx_lattices(wl, binding),
+                                              shifts(wl.seed, wl.levels))
+    if rank == 0:
+        print(json.dumps(result))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def ctx_lattices(wl, binding):
+    return [binding.mq_cbc_lattice(lv.N, lv.s, wl.decay) for lv in wl.levels]
+
+
+def main_reference(args, wl, rank, world):
+    if rank != 0:
+        return
+    from oracle import lattice
+
+    zs = [lattice.cbc(lv.N, lv.s, wl.decay) for lv in wl.levels]
+    ds = shifts(wl.seed, wl.levels)
+    budget = max(5.0, 60.0 / max(1, args.steps + args.warmup))
+    vals = []
+    info = None
+    for i in range(args.warmup + args.steps):
+        info = cpu_baseline(wl, budget, zs, ds)
+        if i >= args.warmup:
+            vals.append(info["value"])
+    value = float(np.mean(vals))
+    ms = wl.samples / value * 1e3
+    out = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": wl.name, "samples_per_step": wl.samples},
+           "cpu_baseline": {"kind": "oracle", "cores": info["cores"], "sample": info["sample"], "value": value,
+                            "unit": "samples/s"},
+           "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,175 @@
+/*
+ * mlqmc_evp.h -- C ABI of the GB300 (sm_103a) two-grid MLQMC eigenvalue library.
+ *
+ * Problem (Sec. 1, eq. evp; Sec. 2, eq. coeff): the smallest eigenvalue lambda(y) of
+ *     -div(a(x, y) grad u) = lambda u  on D = (0,1)^2,  u = 0 on the boundary,
+ *     a(x, y) = a0 + sum_{j=1}^{s} y_j psi_j(x),  y_j in [-1/2, 1/2),
+ * discretised by P1 finite elements on the uniform triangulation of D into n x n squares, each
+ * split by its south-west to north-east diagonal (Sec. 2.3), with a evaluated at triangle
+ * centroids and the exact consistent mass matrix.
+ *
+ * The library evaluates, for a batch of randomly shifted rank-1 lattice points (Sec. 2.5,
+ * eq. rqmc, eq. t_kl), the two-grid-truncation eigenvalue approximations of Algorithm 1 and the
+ * level differences lambda^l - lambda^{l-1} of Algorithm 2, and forms the shift-averaged MLQMC
+ * estimate with its sample-variance standard error (eq. tg-mlqmc, eq. sample_var, eq. ml-var).
+ *
+ * Conventions
+ *   - Every call returns an mq_status; no call aborts the process.  On failure the message of
+ *     mq_last_error() says why (valid until the next call on the same context).
+ *   - Host arrays passed in are owned by the caller and copied before the call returns.
+ *   - The library owns every device buffer it allocates; pointers named d_* are device
+ *     pointers owned by the caller, which must stay valid until the call returns (calls that
+ *     take them synchronise the context stream before returning).
+ *   - Node vectors over a mesh 1/n hold the (n-1)^2 interior nodes row by row:
+ *     index (j-1)(n-1) + (i-1) for the node (i/n, j/n), 1 <= i, j <= n-1.
+ *   - Per-triangle arrays over a mesh 1/n hold 2 n^2 values: the lower triangle
+ *     {(i,j),(i+1,j),(i+1,j+1)} of cell (i,j) at j*n + i and the upper triangle
+ *     {(i,j),(i+1,j+1),(i,j+1)} at n*n + j*n + i.
+ */
+#ifndef MLQMC_EVP_H
+#define MLQMC_EVP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mq_ctx mq_ctx;
+
+typedef enum {
+  MQ_OK = 0,
+  MQ_EINVAL = 1,   /* bad argument: size, range, null pointer, a <= 0 at a centroid */
+  MQ_ENOMEM = 2,   /* host or device allocation failed */
+  MQ_ECUDA = 3,    /* a CUDA call failed; the message names it */
+  MQ_ENOCONV = 4,  /* at least one sample hit an iteration cap; results are still written */
+  MQ_ETIMEOUT = 5, /* reserved: a bounded device wait ran out */
+  MQ_ESTATE = 6    /* call out of order (e.g. evaluate before levels, lattice or shifts are set) */
+} mq_status;
+
+typedef enum {
+  MQ_PREC_FP64 = 0,  /* every step in FP64 */
+  MQ_PREC_MIXED = 1  /* FP32 multigrid-preconditioned MINRES inside FP64 iterative refinement;
+                        coefficients, residuals, Rayleigh quotients, coarse eigenpairs in FP64 */
+} mq_precision;
+
+/* One MLQMC level (Algorithm 2).  n_fine = 1/h_l and n_coarse = 1/H_l are powers of two with
+ * 2 <= n_coarse <= n_fine <= 4096; 1 <= S <= s.  n_coarse == n_fine with S == s makes the level a
+ * direct eigensolve (lambda^l = lambda_{h_l, s_l}).  N lattice points (k = 0..N-1), R shifts. */
+typedef struct {
+  int32_t n_fine, n_coarse;
+  int32_t s, S;
+  uint32_t N;
+  int32_t R;
+} mq_level;
+
+/* Per-call statistics (mq_get_stats). */
+typedef struct {
+  uint64_t samples;          /* samples evaluated by the last evaluation call */
+  uint64_t noconv;           /* samples with an iteration cap hit */
+  double coarse_iters_mean;  /* coarse eigensolver (LOBPCG) iterations per sample */
+  int32_t coarse_iters_max;
+  double fine_iters_mean;    /* inner MINRES iterations per fine solve */
+  int32_t fine_iters_max;
+  double outer_iters_mean;   /* FP64 refinement steps per fine solve */
+  int32_t outer_iters_max;
+  double kernel_ms;          /* device time of the last evaluation (CUDA events) */
+  double coef_ms;            /* of which: coefficient evaluation */
+  double sample_ms;          /* of which: per-sample eigen/solve kernel */
+  int32_t blocks, threads;   /* launch shape of the per-sample kernel */
+  int32_t smem_bytes;        /* dynamic shared memory per block (0 = workspace in global memory) */
+  int64_t workspace_bytes;   /* per-block workspace */
+} mq_stats;
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t to launch on, or
+ * NULL for a stream the context creates and owns. */
+mq_status mq_create(mq_ctx** out, int device, void* cuda_stream);
+mq_status mq_destroy(mq_ctx* ctx);
+
+/* Coefficient a(x, y) = a0 + sum_{j<=s} y_j psi_j(x) (Sec. 2, eq. coeff; truncated as in
+ * eq. coeff_s).  family 0: psi_j(x) = j^-decay sin(pi k1_j x1) sin(pi k2_j x2) with (k1, k2)
+ * the j-th pair with k1, k2 >= 1 ordered by k1^2 + k2^2, ties by smaller k1.  s_max bounds the
+ * truncation of every level.  a0 > 0.  Requires a >= a_min > 0 at all centroids (checked per
+ * evaluation: a non-positive value gives MQ_EINVAL). */
+mq_status mq_set_coefficient(mq_ctx* ctx, double a0, int32_t s_max, int32_t family, double decay);
+
+/* Levels l = 0..L (copied).  Resets the estimator sums, lattices and shifts. */
+mq_status mq_set_levels(mq_ctx* ctx, int32_t L_plus_1, const mq_level* levels);
+
+/* Generating vector z[0..s-1] of level `level` (copied), 0 < z_j < N (Sec. 2.5). */
+mq_status mq_set_lattice(mq_ctx* ctx, int32_t level, const uint32_t* z, int32_t s);
+
+/* Random shifts Delta[R][s_l] of level `level`, row-major, each in [0, 1) (copied). */
+mq_status mq_set_shifts(mq_ctx* ctx, int32_t level, const double* delta);
+
+/* Precision mode and the relative residual tolerance of the fine shifted solve
+ * (tol_linear <= 0 keeps the default 1e-10). */
+mq_status mq_set_precision(mq_ctx* ctx, mq_precision prec, double tol_linear);
+
+/* Evaluate level `level` at lattice indices k in [k0, k1) for every shift (Algorithm 2, steps
+ * 5-15): per sample the coarse eigenpair on (H_l, S_l), lambda^l by Algorithm 1 on (h_l, s_l)
+ * and, for l > 0, lambda^{l-1} on (h_{l-1}, s_{l-1}) from the same coarse pair.
+ *   per_sample: NULL or host [R][k1-k0][4] = (lambda_H, lambda^l, lambda^{l-1}, difference),
+ *               lambda^{-1} = 0 on level 0.
+ *   shift_sums: NULL or host [R]; sum over k of the differences is ADDED to each entry.
+ * The context also accumulates the sums for mq_estimate.  Returns MQ_ENOCONV (results written)
+ * when any sample hit an iteration cap. */
+mq_status mq_eval_level(mq_ctx* ctx, int32_t level, uint32_t k0, uint32_t k1, double* per_sample,
+                        double* shift_sums);
+
+/* As mq_eval_level with device outputs: d_per_sample [R][k1-k0][4], d_shift_sums [R]
+ * (overwritten, not added).  Either may be NULL.  Nothing is copied to the host except the
+ * convergence flags; the context sums are still accumulated on the device. */
+mq_status mq_eval_level_device(mq_ctx* ctx, int32_t level, uint32_t k0, uint32_t k1,
+                               double* d_per_sample, double* d_shift_sums);
+
+/* Estimate from the sums accumulated so far (eq. tg-mlqmc): Q^(r)_l = sum_k diff / n_l where
+ * n_l is the number of points evaluated on level l, Qhat_l = mean_r Q^(r)_l, mean = sum_l Qhat_l,
+ * level_var[l] = sum_r (Qhat_l - Q^(r)_l)^2 / (R (R - 1)) (eq. sample_var), std_err =
+ * sqrt(sum_l level_var[l]) (eq. ml-var).  level_mean / level_var: NULL or host [L+1].
+ * MQ_ESTATE if a level has no points yet; MQ_EINVAL if R < 2 on any level. */
+mq_status mq_estimate(mq_ctx* ctx, double* mean, double* std_err, double* level_mean,
+                      double* level_var);
+
+/* Clear the estimator sums (keeps levels, lattices and shifts). */
+mq_status mq_reset_sums(mq_ctx* ctx);
+
+/* Single explicit parameter vector y[0..s_l-1] on level `level`: the coarse eigenvalue
+ * lambda_{H_l,S_l}(y), lambda^l(y) and (l > 0) lambda^{l-1}(y) (Algorithm 1).  Any output may
+ * be NULL.  u_H: NULL or host [(n_coarse-1)^2], the coarse eigenvector, ||u_H||_M = 1, sum > 0. */
+mq_status mq_eval_point(mq_ctx* ctx, int32_t level, const double* y, double* lam_H,
+                        double* lam_h_twogrid, double* lam_hm1_twogrid, double* u_H);
+
+mq_status mq_get_stats(mq_ctx* ctx, void* stats, size_t bytes);
+const char* mq_last_error(const mq_ctx* ctx);
+
+/* ---- building blocks, exposed for step-by-step parity checks ---------------------------- */
+
+/* CBC generating vector (host; Sec. 2.5): product weights gamma_j = j^-decay, squared
+ * shift-averaged worst-case error e^2(z) = -1 + (1/N) sum_k prod_j (1 + gamma_j B2({k z_j/N})),
+ * B2(x) = x^2 - x + 1/6; component j takes the smallest candidate z in [1, N/2] coprime to N
+ * whose error is within an absolute 1e-12 of the minimum.  z_out: host [s].  N >= 2. */
+mq_status mq_cbc_lattice(uint32_t N, int32_t s, double decay, uint32_t* z_out);
+
+/* Lattice points of level `level` for k in [k0, k1) (eq. t_kl, eq. rqmc):
+ * d_Y [R][k1-k0][s_l], y = {k z / N + Delta_r} - 1/2. */
+mq_status mq_lattice_points_device(mq_ctx* ctx, int32_t level, uint32_t k0, uint32_t k1,
+                                   double* d_Y);
+
+/* Coefficients at the centroids of mesh 1/n (eq. coeff_s): d_a[b][2n^2] = a0 + sum_{j<s}
+ * d_Y[b*ldy + j] psi_{j+1}(c_t), for b < B, with the context's precision mode
+ * (FP64: FP64 GEMM; MIXED: tensor-core split GEMM accurate to FP64 rounding of the terms). */
+mq_status mq_coefficients_device(mq_ctx* ctx, int32_t n, int32_t s, const double* d_Y,
+                                 int32_t B, int32_t ldy, double* d_a);
+
+/* Operator apply on mesh 1/n for B coefficient fields d_a[b][2n^2] (FP64):
+ * which = 0: y = A x, 1: y = M x, 2: y = (A - sigma M) x.  d_x, d_y: [B][(n-1)^2]. */
+mq_status mq_apply_operator_device(mq_ctx* ctx, int32_t n, int32_t B, const double* d_a,
+                                   int32_t which, double sigma, const double* d_x, double* d_y);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MLQMC_EVP_H */

@@ -67,8 +67,19 @@ def psi_pairs(s: int):
     return pairs[:s]
 
 
+_PSI_CACHE: dict = {}
+
+
 def psi_matrix(n: int, s: int, decay: float = 2.0) -> np.ndarray:
-    """Psi[t, j-1] = psi_j(c_t) = j^-decay sin(pi k1_j x1) sin(pi k2_j x2) at triangle centroids."""
+    """Psi[t, j-1] = psi_j(c_t) = j^-decay sin(pi k1_j x1) sin(pi k2_j x2) at triangle centroids
+    (cached per mesh, truncation and decay; callers must not modify the result)."""
+    key = (n, s, decay)
+    if key not in _PSI_CACHE:
+        _PSI_CACHE[key] = _psi_matrix(n, s, decay)
+    return _PSI_CACHE[key]
+
+
+def _psi_matrix(n: int, s: int, decay: float) -> np.ndarray:
     c = centroids(n)
     out = np.zeros((c.shape[0], s))
     for j, (k1, k2) in enumerate(psi_pairs(s), start=1):

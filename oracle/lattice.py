@@ -13,8 +13,11 @@ Test infrastructure only (see ``oracle/__init__.py``).
 
   with B2(x) = x^2 - x + 1/6 the Bernoulli polynomial of degree 2.  Component j
   takes the candidate z in [1, N/2] with gcd(z, N) = 1 that minimises e^2 given
-  the earlier components; candidates within a relative 1e-12 of the minimum
-  count as tied and the smallest of them is taken.
+  the earlier components; candidates within an absolute 1e-12 of the minimum
+  count as tied and the smallest of them is taken.  (e^2 is a difference of
+  order-one sums, so rounding alone separates candidates that tie exactly, such
+  as every candidate for the first component, by up to ~1e-15; the tie window
+  absorbs that.)
 """
 from __future__ import annotations
 
@@ -38,7 +41,7 @@ def cbc_error2(z, N: int, gamma) -> float:
     return -1.0 + total / N
 
 
-def cbc(N: int, s: int, decay: float = 2.0, tie_rtol: float = 1e-12) -> np.ndarray:
+def cbc(N: int, s: int, decay: float = 2.0, tie_atol: float = 1e-12) -> np.ndarray:
     """Generating vector z (length s) by CBC with product weights gamma_j = j^-decay."""
     gamma = np.array([(j + 1) ** (-decay) for j in range(s)])
     k = np.arange(N, dtype=np.int64)
@@ -52,7 +55,7 @@ def cbc(N: int, s: int, decay: float = 2.0, tie_rtol: float = 1e-12) -> np.ndarr
             frac = ((np.outer(cands[c0:c0 + step], k)) % N) / N  # [cand, k]
             e2[c0:c0 + step] = -1.0 + np.mean(prod[None, :] * (1.0 + gamma[j] * bernoulli2(frac)), axis=1)
         best = e2.min()
-        pick = int(cands[np.nonzero(e2 <= best + tie_rtol * abs(best))[0][0]])
+        pick = int(cands[np.nonzero(e2 <= best + tie_atol)[0][0]])
         z.append(pick)
         prod = prod * (1.0 + gamma[j] * bernoulli2(((k * pick) % N) / N))
     return np.array(z, dtype=np.int64)

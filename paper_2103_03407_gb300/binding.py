@@ -1,0 +1,233 @@
+"""ctypes binding of the C ABI in ``include/mlqmc_evp.h`` (argument marshalling only).
+
+Every function keeps the name of the C entry point it wraps.  Host arrays are numpy arrays;
+device arrays are torch CUDA tensors (PyTorch provides device memory and streams only), passed
+by their data pointer.  A non-OK status raises :class:`MQError` carrying the library message;
+``MQ_ENOCONV`` raises :class:`MQNoConvergence` after the outputs are written.
+
+Loading fails loudly when the library has not been built: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libmlqmc_evp.so")
+
+MQ_OK, MQ_EINVAL, MQ_ENOMEM, MQ_ECUDA, MQ_ENOCONV, MQ_ETIMEOUT, MQ_ESTATE = range(7)
+MQ_PREC_FP64, MQ_PREC_MIXED = 0, 1
+STATUS_NAMES = {0: "MQ_OK", 1: "MQ_EINVAL", 2: "MQ_ENOMEM", 3: "MQ_ECUDA", 4: "MQ_ENOCONV", 5: "MQ_ETIMEOUT",
+                6: "MQ_ESTATE"}
+
+# every symbol the header declares
+EXPORTS = [
+    "mq_create", "mq_destroy", "mq_set_coefficient", "mq_set_levels", "mq_set_lattice", "mq_set_shifts",
+    "mq_set_precision", "mq_eval_level", "mq_eval_level_device", "mq_estimate", "mq_reset_sums", "mq_eval_point",
+    "mq_get_stats", "mq_last_error", "mq_cbc_lattice", "mq_lattice_points_device", "mq_coefficients_device",
+    "mq_apply_operator_device",
+]
+
+
+class MQError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class MQNoConvergence(MQError):
+    pass
+
+
+class mq_level(C.Structure):
+    _fields_ = [("n_fine", C.c_int32), ("n_coarse", C.c_int32), ("s", C.c_int32), ("S", C.c_int32),
+                ("N", C.c_uint32), ("R", C.c_int32)]
+
+
+class mq_stats(C.Structure):
+    _fields_ = [("samples", C.c_uint64), ("noconv", C.c_uint64), ("coarse_iters_mean", C.c_double),
+                ("coarse_iters_max", C.c_int32), ("fine_iters_mean", C.c_double), ("fine_iters_max", C.c_int32),
+                ("outer_iters_mean", C.c_double), ("outer_iters_max", C.c_int32), ("kernel_ms", C.c_double),
+                ("coef_ms", C.c_double), ("sample_ms", C.c_double), ("blocks", C.c_int32), ("threads", C.c_int32),
+                ("smem_bytes", C.c_int32), ("workspace_bytes", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the library (once).  Raises if it is missing: build it with paper_2103_03407_gb300.build."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing (run python -m paper_2103_03407_gb300.build)")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    i32, u32, f64, sz = C.c_int32, C.c_uint32, C.c_double, C.c_size_t
+    dp = C.POINTER(C.c_double)
+    sig = {
+        "mq_create": ([C.POINTER(P), C.c_int, P], C.c_int),
+        "mq_destroy": ([P], C.c_int),
+        "mq_set_coefficient": ([P, f64, i32, i32, f64], C.c_int),
+        "mq_set_levels": ([P, i32, C.POINTER(mq_level)], C.c_int),
+        "mq_set_lattice": ([P, i32, C.POINTER(u32), i32], C.c_int),
+        "mq_set_shifts": ([P, i32, dp], C.c_int),
+        "mq_set_precision": ([P, C.c_int, f64], C.c_int),
+        "mq_eval_level": ([P, i32, u32, u32, dp, dp], C.c_int),
+        "mq_eval_level_device": ([P, i32, u32, u32, P, P], C.c_int),
+        "mq_estimate": ([P, dp, dp, dp, dp], C.c_int),
+        "mq_reset_sums": ([P], C.c_int),
+        "mq_eval_point": ([P, i32, dp, dp, dp, dp, dp], C.c_int),
+        "mq_get_stats": ([P, P, sz], C.c_int),
+        "mq_last_error": ([P], C.c_char_p),
+        "mq_cbc_lattice": ([u32, i32, f64, C.POINTER(u32)], C.c_int),
+        "mq_lattice_points_device": ([P, i32, u32, u32, P], C.c_int),
+        "mq_coefficients_device": ([P, i32, i32, P, i32, i32, P], C.c_int),
+        "mq_apply_operator_device": ([P, i32, i32, P, i32, f64, P, P], C.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _tptr(t):
+    """Device pointer of a torch CUDA tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("device arguments must be contiguous CUDA tensors")
+    return C.c_void_p(t.data_ptr())
+
+
+class Context:
+    """Owns one ``mq_ctx``.  Methods are the C entry points with the context argument bound."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.lib = load()
+        h = C.c_void_p()
+        st = self.lib.mq_create(C.byref(h), int(device), C.c_void_p(stream) if stream else None)
+        if st != MQ_OK:
+            raise MQError(st, "mq_create failed (no CUDA device?)")
+        self.h = h
+        self.levels = []
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mq_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, st):
+        if st == MQ_OK:
+            return
+        msg = self.lib.mq_last_error(self.h).decode()
+        if st == MQ_ENOCONV:
+            raise MQNoConvergence(st, msg)
+        raise MQError(st, msg)
+
+    # --- configuration ---------------------------------------------------------------------
+    def mq_set_coefficient(self, a0=1.0, s_max=16, family=0, decay=2.0):
+        self._check(self.lib.mq_set_coefficient(self.h, float(a0), int(s_max), int(family), float(decay)))
+
+    def mq_set_levels(self, levels):
+        arr = (mq_level * len(levels))()
+        for i, lv in enumerate(levels):
+            arr[i] = mq_level(lv.n_fine, lv.n_coarse, lv.s, lv.S, lv.N, lv.R)
+        self._check(self.lib.mq_set_levels(self.h, len(levels), arr))
+        self.levels = list(levels)
+
+    def mq_set_lattice(self, level, z):
+        z = np.ascontiguousarray(z, dtype=np.uint32)
+        self._check(self.lib.mq_set_lattice(self.h, int(level), z.ctypes.data_as(C.POINTER(C.c_uint32)), z.size))
+
+    def mq_set_shifts(self, level, delta):
+        d = np.ascontiguousarray(delta, dtype=np.float64)
+        self._check(self.lib.mq_set_shifts(self.h, int(level), _dptr(d)))
+
+    def mq_set_precision(self, prec=MQ_PREC_FP64, tol_linear=0.0):
+        self._check(self.lib.mq_set_precision(self.h, int(prec), float(tol_linear)))
+
+    # --- evaluation --------------------------------------------------------------------------
+    def mq_eval_level(self, level, k0, k1, per_sample=True, shift_sums=None):
+        """Returns (per_sample [R, k1-k0, 4] or None, shift_sums [R])."""
+        R = self.levels[level].R
+        ps = np.zeros((R, k1 - k0, 4)) if per_sample else None
+        ss = np.zeros(R) if shift_sums is None else np.ascontiguousarray(shift_sums, dtype=np.float64)
+        st = self.lib.mq_eval_level(self.h, int(level), int(k0), int(k1), _dptr(ps) if ps is not None else None,
+                                    _dptr(ss))
+        self._check(st)
+        return ps, ss
+
+    def mq_eval_level_device(self, level, k0, k1, d_per_sample=None, d_shift_sums=None):
+        self._check(self.lib.mq_eval_level_device(self.h, int(level), int(k0), int(k1), _tptr(d_per_sample),
+                                                  _tptr(d_shift_sums)))
+
+    def mq_estimate(self):
+        L = len(self.levels)
+        m, se = C.c_double(), C.c_double()
+        lm, lv = np.zeros(L), np.zeros(L)
+        self._check(self.lib.mq_estimate(self.h, C.byref(m), C.byref(se), _dptr(lm), _dptr(lv)))
+        return m.value, se.value, lm, lv
+
+    def mq_reset_sums(self):
+        self._check(self.lib.mq_reset_sums(self.h))
+
+    def mq_eval_point(self, level, y, want_u=False):
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        lH, lh, lp = C.c_double(), C.c_double(), C.c_double()
+        nc = self.levels[level].n_coarse
+        u = np.zeros((nc - 1) ** 2) if want_u else None
+        st = self.lib.mq_eval_point(self.h, int(level), _dptr(y), C.byref(lH), C.byref(lh), C.byref(lp),
+                                    _dptr(u) if u is not None else None)
+        self._check(st)
+        return (lH.value, lh.value, lp.value, u) if want_u else (lH.value, lh.value, lp.value)
+
+    def mq_get_stats(self):
+        s = mq_stats()
+        self._check(self.lib.mq_get_stats(self.h, C.byref(s), C.sizeof(s)))
+        return s.as_dict()
+
+    # --- building blocks ----------------------------------------------------------------------
+    def mq_lattice_points_device(self, level, k0, k1, d_Y):
+        self._check(self.lib.mq_lattice_points_device(self.h, int(level), int(k0), int(k1), _tptr(d_Y)))
+
+    def mq_coefficients_device(self, n, s, d_Y, B, ldy, d_a):
+        self._check(self.lib.mq_coefficients_device(self.h, int(n), int(s), _tptr(d_Y), int(B), int(ldy),
+                                                    _tptr(d_a)))
+
+    def mq_apply_operator_device(self, n, B, d_a, which, sigma, d_x, d_y):
+        self._check(self.lib.mq_apply_operator_device(self.h, int(n), int(B), _tptr(d_a), int(which), float(sigma),
+                                                      _tptr(d_x), _tptr(d_y)))
+
+
+def mq_cbc_lattice(N: int, s: int, decay: float = 2.0) -> np.ndarray:
+    lib = load()
+    z = np.zeros(s, dtype=np.uint32)
+    st = lib.mq_cbc_lattice(int(N), int(s), float(decay), z.ctypes.data_as(C.POINTER(C.c_uint32)))
+    if st != MQ_OK:
+        raise MQError(st, "mq_cbc_lattice: bad arguments")
+    return z

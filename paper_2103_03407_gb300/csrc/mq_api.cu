@@ -1,0 +1,725 @@
+// Host side of the C ABI declared in include/mlqmc_evp.h: context, argument validation, device
+// buffers, the coefficient tables, the level evaluation driver and the estimator.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/mlqmc_evp.h"
+#include "mq_internal.h"
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct mq_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int sm_count = 0;
+  int smem_optin = 0;
+  std::string err;
+
+  bool coef_set = false;
+  double a0 = 1.0, decay = 2.0;
+  int s_max = 0, family = 0;
+  int* d_k1 = nullptr;
+  int* d_k2 = nullptr;
+  double* d_cj = nullptr;
+
+  std::vector<mq_level> levels;
+  std::vector<std::vector<uint32_t>> z;
+  std::vector<uint32_t*> d_z;
+  std::vector<std::vector<double>> delta;
+  std::vector<double*> d_delta;
+  std::vector<std::vector<double>> sums;  // per level, per shift
+  std::vector<uint64_t> npoints;          // per level: points evaluated
+
+  int prec = MQ_PREC_FP64;
+  double tol_lin = 1e-10;
+
+  std::map<int, std::pair<int, double*>> psi;  // mesh n -> (rows, table [rows][2n^2])
+
+  DevBuf Y, af, ac, ap, out, stat, outer, scratch, sums_d, flags_d, uout, misc;
+  mq_stats stats{};
+  size_t last_B = 0;  // samples of the last pass (their per-sample counters are still on the device)
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+};
+
+namespace {
+
+mq_status fail(mq_ctx* c, mq_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return s;
+}
+
+#define MQ_CUDA(c, call)                                                                  \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) return fail(c, MQ_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+mq_status grow(mq_ctx* c, DevBuf& b, size_t bytes) {
+  if (bytes <= b.bytes) return MQ_OK;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  size_t want = std::max(bytes, (size_t)256);
+  if (cudaMalloc(&b.p, want) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, MQ_ENOMEM, "device allocation of %zu bytes failed", want);
+  }
+  b.bytes = want;
+  return MQ_OK;
+}
+
+bool pow2(int n) { return n >= 1 && (n & (n - 1)) == 0; }
+
+// frequency pairs of the synthetic family: k1, k2 >= 1 ordered by k1^2 + k2^2, then k1
+void psi_pairs(int s, std::vector<int>& k1, std::vector<int>& k2) {
+  const int K = (int)std::ceil(2.0 * std::sqrt((double)std::max(s, 1))) + 2;
+  std::vector<std::pair<int, int>> pr;
+  for (int a = 1; a <= K; ++a)
+    for (int b = 1; b <= K; ++b) pr.emplace_back(a, b);
+  std::stable_sort(pr.begin(), pr.end(), [](const std::pair<int, int>& x, const std::pair<int, int>& y) {
+    const int nx = x.first * x.first + x.second * x.second, ny = y.first * y.first + y.second * y.second;
+    return nx != ny ? nx < ny : x.first < y.first;
+  });
+  k1.resize(s);
+  k2.resize(s);
+  for (int j = 0; j < s; ++j) {
+    k1[j] = pr[j].first;
+    k2[j] = pr[j].second;
+  }
+}
+
+mq_status ensure_psi(mq_ctx* c, int n, int rows, const double** out) {
+  auto it = c->psi.find(n);
+  if (it != c->psi.end() && it->second.first >= rows) {
+    *out = it->second.second;
+    return MQ_OK;
+  }
+  if (it != c->psi.end()) {
+    cudaFree(it->second.second);
+    c->psi.erase(it);
+  }
+  const size_t bytes = (size_t)std::max(rows, 1) * 2 * n * n * sizeof(double);
+  double* d = nullptr;
+  if (cudaMalloc(&d, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, MQ_ENOMEM, "psi table for n=%d, s=%d (%zu bytes)", n, rows, bytes);
+  }
+  MQ_CUDA(c, mq::launch_psi_table(n, rows, c->d_k1, c->d_k2, c->d_cj, d, c->stream));
+  c->psi[n] = {rows, d};
+  *out = d;
+  return MQ_OK;
+}
+
+mq_status check_level_ready(mq_ctx* c, int level) {
+  if (!c->coef_set) return fail(c, MQ_ESTATE, "coefficient not set");
+  if (c->levels.empty()) return fail(c, MQ_ESTATE, "levels not set");
+  if (level < 0 || level >= (int)c->levels.size()) return fail(c, MQ_EINVAL, "level %d out of range", level);
+  if (c->d_z[level] == nullptr) return fail(c, MQ_ESTATE, "lattice of level %d not set", level);
+  if (c->d_delta[level] == nullptr) return fail(c, MQ_ESTATE, "shifts of level %d not set", level);
+  return MQ_OK;
+}
+
+// threads per CTA for a fine mesh 1/n
+int threads_for(int n) { return n <= 16 ? 128 : 256; }
+
+struct LevelGeom {
+  int nf, nc, np, s, S, sp, direct_f, direct_p;
+};
+
+LevelGeom geom(const mq_ctx* c, int level) {
+  const mq_level& lv = c->levels[level];
+  LevelGeom g{};
+  g.nf = lv.n_fine;
+  g.nc = lv.n_coarse;
+  g.s = lv.s;
+  g.S = lv.S;
+  g.direct_f = (lv.n_fine == lv.n_coarse && lv.s == lv.S);
+  if (level > 0) {
+    const mq_level& pv = c->levels[level - 1];
+    g.np = pv.n_fine;
+    g.sp = pv.s;
+    g.direct_p = (pv.n_fine == lv.n_coarse && pv.s == lv.S);
+  }
+  return g;
+}
+
+// Runs the per-sample pipeline on B = R * npts samples whose parameters are in c->Y (ldy = s).
+// Writes c->out / c->stat / c->outer; returns timings in stats.
+mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk, bool want_u) {
+  const size_t B = (size_t)R * npts;
+  const double* psi_f = nullptr;
+  const double* psi_c = nullptr;
+  const double* psi_p = nullptr;
+  mq_status st;
+  if ((st = ensure_psi(c, g.nc, c->s_max, &psi_c)) != MQ_OK) return st;
+  if (!g.direct_f && (st = ensure_psi(c, g.nf, c->s_max, &psi_f)) != MQ_OK) return st;
+  if (g.np && !g.direct_p && (st = ensure_psi(c, g.np, c->s_max, &psi_p)) != MQ_OK) return st;
+  const size_t nTf = (size_t)2 * g.nf * g.nf, nTc = (size_t)2 * g.nc * g.nc, nTp = (size_t)2 * g.np * g.np;
+  if ((st = grow(c, c->ac, B * nTc * sizeof(double))) != MQ_OK) return st;
+  if (!g.direct_f && (st = grow(c, c->af, B * nTf * sizeof(double))) != MQ_OK) return st;
+  if (g.np && !g.direct_p && (st = grow(c, c->ap, B * nTp * sizeof(double))) != MQ_OK) return st;
+  if ((st = grow(c, c->out, B * 4 * sizeof(double))) != MQ_OK) return st;
+  if ((st = grow(c, c->stat, B * 4 * sizeof(int))) != MQ_OK) return st;
+  if ((st = grow(c, c->outer, B * 2 * sizeof(int))) != MQ_OK) return st;
+  if (want_u && (st = grow(c, c->uout, B * (size_t)(g.nc - 1) * (g.nc - 1) * sizeof(double))) != MQ_OK) return st;
+
+  const int mixed = c->prec == MQ_PREC_MIXED;
+  MQ_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
+  const double* Y = (const double*)c->Y.p;
+  MQ_CUDA(c, mq::launch_coef_gemm_f64(Y, g.s, (int)B, g.S, psi_c, (int)nTc, c->a0, (double*)c->ac.p, c->stream));
+  if (!g.direct_f)
+    MQ_CUDA(c, mq::launch_coef_gemm_f64(Y, g.s, (int)B, g.s, psi_f, (int)nTf, c->a0, (double*)c->af.p, c->stream));
+  if (g.np && !g.direct_p)
+    MQ_CUDA(c, mq::launch_coef_gemm_f64(Y, g.s, (int)B, g.sp, psi_p, (int)nTp, c->a0, (double*)c->ap.p, c->stream));
+  MQ_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
+
+  mq::SampleLaunch p{};
+  p.nf = g.nf;
+  p.nc = g.nc;
+  p.np = g.np;
+  p.direct_f = g.direct_f;
+  p.direct_p = g.direct_p;
+  p.R = R;
+  p.npts = npts;
+  p.chunk = chunk;
+  p.a_f = (const double*)c->af.p;
+  p.a_c = (const double*)c->ac.p;
+  p.a_p = (const double*)c->ap.p;
+  p.out = (double*)c->out.p;
+  p.stat = (int*)c->stat.p;
+  p.outer = (int*)c->outer.p;
+  p.u_out = want_u ? (double*)c->uout.p : nullptr;
+  p.tol_eig = 1e-12;
+  p.max_eig_it = 200;
+  p.tol_lin = c->tol_lin;
+  if (mixed) {
+    p.tol_inner = 1e-5;
+    p.max_outer = 10;
+  } else {
+    p.tol_inner = 0.1 * c->tol_lin;
+    p.max_outer = 4;
+  }
+  p.max_inner_it = 500;
+  p.nu = 2;
+  p.omega = 0.8;
+
+  const int threads = threads_for(std::max(g.nf, g.nc));
+  const size_t slab = mq::sample_slab_bytes(g.nf, g.nc, g.np, mixed);
+  const int static_smem = mq::sample_static_smem(mixed);
+  const size_t smem_cap = (size_t)std::max(0, c->smem_optin - static_smem - 1024);
+  const bool use_smem = slab <= smem_cap;
+  const size_t smem = use_smem ? slab : 0;
+  if (use_smem) MQ_CUDA(c, mq::set_sample_smem(mixed, (int)smem));
+  int occ = mq::sample_occupancy(mixed, threads, smem);
+  if (occ < 1) occ = 1;
+  const int cpr = (npts + chunk - 1) / chunk;
+  const long nchunks = (long)cpr * R;
+  int blocks = (int)std::min<long>(nchunks, (long)c->sm_count * occ);
+  if (blocks < 1) blocks = 1;
+  if (!use_smem) {
+    if ((st = grow(c, c->scratch, (size_t)blocks * slab)) != MQ_OK) return st;
+  }
+  p.gscratch = (char*)c->scratch.p;
+  p.slab_bytes = slab;
+  p.use_smem = use_smem;
+  MQ_CUDA(c, mq::launch_sample(p, mixed, blocks, threads, smem, c->stream));
+  MQ_CUDA(c, cudaEventRecord(c->ev[2], c->stream));
+  c->stats.blocks = blocks;
+  c->stats.threads = threads;
+  c->stats.smem_bytes = (int)smem;
+  c->stats.workspace_bytes = (int64_t)slab;
+  return MQ_OK;
+}
+
+mq_status collect_stats(mq_ctx* c, size_t B, int* any_flags) {
+  std::vector<int> st(B * 4), ou(B * 2);
+  MQ_CUDA(c, cudaMemcpyAsync(st.data(), c->stat.p, B * 4 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  MQ_CUDA(c, cudaMemcpyAsync(ou.data(), c->outer.p, B * 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  MQ_CUDA(c, cudaStreamSynchronize(c->stream));
+  mq_stats& s = c->stats;
+  double ce = 0, fi = 0, oi = 0;
+  long nf = 0;
+  int cemax = 0, fimax = 0, oimax = 0, fl = 0;
+  uint64_t nc = 0;
+  for (size_t b = 0; b < B; ++b) {
+    ce += st[b * 4];
+    cemax = std::max(cemax, st[b * 4]);
+    for (int k = 0; k < 2; ++k) {
+      if (ou[b * 2 + k] > 0) {
+        fi += st[b * 4 + 1 + k];
+        fimax = std::max(fimax, st[b * 4 + 1 + k]);
+        oi += ou[b * 2 + k];
+        oimax = std::max(oimax, ou[b * 2 + k]);
+        ++nf;
+      }
+    }
+    fl |= st[b * 4 + 3];
+    if (st[b * 4 + 3] & (mq::kFlagEigNoConv | mq::kFlagLinNoConv | mq::kFlagBreakdown)) ++nc;
+  }
+  s.samples = B;
+  s.noconv = nc;
+  s.coarse_iters_mean = B ? ce / B : 0;
+  s.coarse_iters_max = cemax;
+  s.fine_iters_mean = nf ? fi / nf : 0;
+  s.fine_iters_max = fimax;
+  s.outer_iters_mean = nf ? oi / nf : 0;
+  s.outer_iters_max = oimax;
+  *any_flags = fl;
+  return MQ_OK;
+}
+
+mq_status timing(mq_ctx* c) {
+  float t0 = 0, t1 = 0;
+  MQ_CUDA(c, cudaEventSynchronize(c->ev[2]));
+  MQ_CUDA(c, cudaEventElapsedTime(&t0, c->ev[0], c->ev[1]));
+  MQ_CUDA(c, cudaEventElapsedTime(&t1, c->ev[1], c->ev[2]));
+  c->stats.coef_ms += t0;
+  c->stats.sample_ms += t1;
+  c->stats.kernel_ms += t0 + t1;
+  return MQ_OK;
+}
+
+mq_status flags_status(mq_ctx* c, int fl) {
+  if (fl & mq::kFlagBadCoef)
+    return fail(c, MQ_EINVAL, "coefficient a(x, y) <= 0 at a centroid (Assumption A1 violated)");
+  if (fl & (mq::kFlagEigNoConv | mq::kFlagLinNoConv | mq::kFlagBreakdown))
+    return fail(c, MQ_ENOCONV, "%llu sample(s) hit an iteration cap or broke down (flags 0x%x)",
+                (unsigned long long)c->stats.noconv, fl);
+  return MQ_OK;
+}
+
+// points per pass so that the coefficient buffers stay within a memory budget
+int points_per_pass(const mq_ctx* c, const LevelGeom& g, int R, int npts) {
+  const size_t per_sample = sizeof(double) * ((size_t)2 * g.nf * g.nf + (size_t)2 * g.nc * g.nc +
+                                              (size_t)2 * g.np * g.np + (size_t)g.s + 8);
+  const size_t budget = (size_t)16 << 30;
+  size_t pts = budget / (per_sample * (size_t)R);
+  if (pts < 1) pts = 1;
+  return (int)std::min<size_t>(pts, (size_t)npts);
+}
+
+int chunk_for(const mq_ctx* c, int R, int npts) {
+  // points per warm-start chain: enough chains to fill the GPU, chains as long as possible
+  const long want = (long)c->sm_count * 4;
+  long ch = ((long)R * npts + want - 1) / want;
+  return (int)std::max(1L, std::min<long>(ch, 64));
+}
+
+mq_status eval_level_impl(mq_ctx* c, int level, uint32_t k0, uint32_t k1, double* per_sample, double* shift_sums,
+                          double* d_per_sample, double* d_shift_sums) {
+  mq_status st = check_level_ready(c, level);
+  if (st != MQ_OK) return st;
+  const mq_level& lv = c->levels[level];
+  if (k1 < k0 || k1 > lv.N) return fail(c, MQ_EINVAL, "point range [%u, %u) outside [0, %u)", k0, k1, lv.N);
+  MQ_CUDA(c, cudaSetDevice(c->device));
+  const LevelGeom g = geom(c, level);
+  const int R = lv.R;
+  const int npts = (int)(k1 - k0);
+  c->stats = mq_stats{};
+  if (npts == 0) return MQ_OK;
+  const int ppp = points_per_pass(c, g, R, npts);
+  std::vector<double> host_out;
+  std::vector<double> level_add(R, 0.0);
+  int any_flags = 0;
+  for (int p0 = 0; p0 < npts; p0 += ppp) {
+    const int pn = std::min(ppp, npts - p0);
+    const size_t B = (size_t)R * pn;
+    if ((st = grow(c, c->Y, B * g.s * sizeof(double))) != MQ_OK) return st;
+    MQ_CUDA(c, mq::launch_lattice_points(c->d_z[level], lv.N, c->d_delta[level], R, g.s, k0 + p0, pn,
+                                         (double*)c->Y.p, c->stream));
+    if ((st = run_samples(c, g, R, pn, chunk_for(c, R, pn), false)) != MQ_OK) return st;
+    if ((st = grow(c, c->sums_d, R * sizeof(double))) != MQ_OK) return st;
+    if ((st = grow(c, c->flags_d, sizeof(int))) != MQ_OK) return st;
+    MQ_CUDA(c, cudaMemsetAsync(c->flags_d.p, 0, sizeof(int), c->stream));
+    MQ_CUDA(c, mq::launch_shift_sums((const double*)c->out.p, (const int*)c->stat.p, R, pn, (double*)c->sums_d.p,
+                                     (int*)c->flags_d.p, c->stream));
+    std::vector<double> sums(R);
+    int fl = 0;
+    MQ_CUDA(c, cudaMemcpyAsync(sums.data(), c->sums_d.p, R * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    MQ_CUDA(c, cudaMemcpyAsync(&fl, c->flags_d.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    if (per_sample) {
+      host_out.resize(B * 4);
+      MQ_CUDA(c, cudaMemcpyAsync(host_out.data(), c->out.p, B * 4 * sizeof(double), cudaMemcpyDeviceToHost,
+                                 c->stream));
+    }
+    if (d_per_sample) {
+      // [R][npts][4] layout of the caller: scatter this pass's [R][pn][4]
+      for (int r = 0; r < R; ++r)
+        MQ_CUDA(c, cudaMemcpyAsync(d_per_sample + ((size_t)r * npts + p0) * 4,
+                                   (const double*)c->out.p + (size_t)r * pn * 4, (size_t)pn * 4 * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, c->stream));
+    }
+    MQ_CUDA(c, cudaStreamSynchronize(c->stream));
+    if ((st = timing(c)) != MQ_OK) return st;
+    if (per_sample) {
+      for (int r = 0; r < R; ++r)
+        std::memcpy(per_sample + ((size_t)r * npts + p0) * 4, host_out.data() + (size_t)r * pn * 4,
+                    (size_t)pn * 4 * sizeof(double));
+    }
+    for (int r = 0; r < R; ++r) level_add[r] += sums[r];
+    any_flags |= fl;
+    c->last_B = B;
+  }
+  if (d_shift_sums)
+    MQ_CUDA(c, cudaMemcpyAsync(d_shift_sums, level_add.data(), R * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  MQ_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (int r = 0; r < R; ++r) {
+    c->sums[level][r] += level_add[r];
+    if (shift_sums) shift_sums[r] += level_add[r];
+  }
+  c->npoints[level] += (uint64_t)npts;
+  if (any_flags) {
+    int dummy;
+    if ((st = collect_stats(c, c->last_B, &dummy)) != MQ_OK) return st;
+  }
+  c->stats.samples = (uint64_t)R * npts;
+  return flags_status(c, any_flags);
+}
+
+}  // namespace
+
+extern "C" {
+
+mq_status mq_create(mq_ctx** out, int device, void* cuda_stream) {
+  if (!out) return MQ_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return MQ_ECUDA;
+  }
+  if (device < 0 || device >= ndev) return MQ_EINVAL;
+  mq_ctx* c = new (std::nothrow) mq_ctx();
+  if (!c) return MQ_ENOMEM;
+  c->device = device;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    delete c;
+    return MQ_ECUDA;
+  }
+  cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+  cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  if (cuda_stream) {
+    c->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return MQ_ECUDA;
+    }
+    c->own_stream = true;
+  }
+  for (auto& e : c->ev) cudaEventCreate(&e);
+  *out = c;
+  return MQ_OK;
+}
+
+mq_status mq_destroy(mq_ctx* c) {
+  if (!c) return MQ_EINVAL;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  for (DevBuf* b : {&c->Y, &c->af, &c->ac, &c->ap, &c->out, &c->stat, &c->outer, &c->scratch, &c->sums_d,
+                    &c->flags_d, &c->uout, &c->misc})
+    if (b->p) cudaFree(b->p);
+  for (auto& kv : c->psi) cudaFree(kv.second.second);
+  for (auto p : c->d_z)
+    if (p) cudaFree(p);
+  for (auto p : c->d_delta)
+    if (p) cudaFree(p);
+  if (c->d_k1) cudaFree(c->d_k1);
+  if (c->d_k2) cudaFree(c->d_k2);
+  if (c->d_cj) cudaFree(c->d_cj);
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return MQ_OK;
+}
+
+const char* mq_last_error(const mq_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+mq_status mq_set_coefficient(mq_ctx* c, double a0, int32_t s_max, int32_t family, double decay) {
+  if (!c) return MQ_EINVAL;
+  if (!(a0 > 0.0) || !std::isfinite(a0)) return fail(c, MQ_EINVAL, "a0 must be positive, got %g", a0);
+  if (s_max < 0 || s_max > 65536) return fail(c, MQ_EINVAL, "s_max %d out of range", s_max);
+  if (family != 0) return fail(c, MQ_EINVAL, "unknown coefficient family %d", family);
+  if (!std::isfinite(decay)) return fail(c, MQ_EINVAL, "decay must be finite");
+  MQ_CUDA(c, cudaSetDevice(c->device));
+  std::vector<int> k1, k2;
+  psi_pairs(std::max(s_max, 1), k1, k2);
+  std::vector<double> cj(std::max(s_max, 1));
+  for (int j = 0; j < (int)cj.size(); ++j) cj[j] = std::pow((double)(j + 1), -decay);
+  for (auto& kv : c->psi) cudaFree(kv.second.second);
+  c->psi.clear();
+  if (c->d_k1) cudaFree(c->d_k1);
+  if (c->d_k2) cudaFree(c->d_k2);
+  if (c->d_cj) cudaFree(c->d_cj);
+  const size_t m = cj.size();
+  MQ_CUDA(c, cudaMalloc(&c->d_k1, m * sizeof(int)));
+  MQ_CUDA(c, cudaMalloc(&c->d_k2, m * sizeof(int)));
+  MQ_CUDA(c, cudaMalloc(&c->d_cj, m * sizeof(double)));
+  MQ_CUDA(c, cudaMemcpy(c->d_k1, k1.data(), m * sizeof(int), cudaMemcpyHostToDevice));
+  MQ_CUDA(c, cudaMemcpy(c->d_k2, k2.data(), m * sizeof(int), cudaMemcpyHostToDevice));
+  MQ_CUDA(c, cudaMemcpy(c->d_cj, cj.data(), m * sizeof(double), cudaMemcpyHostToDevice));
+  c->a0 = a0;
+  c->s_max = s_max;
+  c->family = family;
+  c->decay = decay;
+  c->coef_set = true;
+  return MQ_OK;
+}
+
+mq_status mq_set_levels(mq_ctx* c, int32_t L_plus_1, const mq_level* levels) {
+  if (!c) return MQ_EINVAL;
+  if (L_plus_1 < 1 || L_plus_1 > 32 || !levels) return fail(c, MQ_EINVAL, "need 1..32 levels");
+  if (!c->coef_set) return fail(c, MQ_ESTATE, "set the coefficient before the levels");
+  for (int l = 0; l < L_plus_1; ++l) {
+    const mq_level& v = levels[l];
+    if (!pow2(v.n_fine) || !pow2(v.n_coarse) || v.n_coarse < 2 || v.n_fine > 4096 || v.n_coarse > v.n_fine)
+      return fail(c, MQ_EINVAL, "level %d: meshes must be powers of two with 2 <= n_coarse <= n_fine <= 4096", l);
+    if (v.S < 1 || v.s < v.S || v.s > c->s_max)
+      return fail(c, MQ_EINVAL, "level %d: need 1 <= S <= s <= s_max (%d)", l, c->s_max);
+    if (v.N < 1 || v.R < 1) return fail(c, MQ_EINVAL, "level %d: need N >= 1 and R >= 1", l);
+    if (l > 0) {
+      const mq_level& p = levels[l - 1];
+      if (p.n_fine < v.n_coarse || p.n_fine % v.n_coarse)
+        return fail(c, MQ_EINVAL, "level %d: coarse mesh must be nested in the fine mesh of level %d", l, l - 1);
+      if (p.s > v.s) return fail(c, MQ_EINVAL, "level %d: s must not decrease across levels", l);
+    }
+  }
+  MQ_CUDA(c, cudaSetDevice(c->device));
+  for (auto p : c->d_z)
+    if (p) cudaFree(p);
+  for (auto p : c->d_delta)
+    if (p) cudaFree(p);
+  c->levels.assign(levels, levels + L_plus_1);
+  c->z.assign(L_plus_1, {});
+  c->delta.assign(L_plus_1, {});
+  c->d_z.assign(L_plus_1, nullptr);
+  c->d_delta.assign(L_plus_1, nullptr);
+  c->sums.assign(L_plus_1, {});
+  for (int l = 0; l < L_plus_1; ++l) c->sums[l].assign(levels[l].R, 0.0);
+  c->npoints.assign(L_plus_1, 0);
+  return MQ_OK;
+}
+
+mq_status mq_set_lattice(mq_ctx* c, int32_t level, const uint32_t* z, int32_t s) {
+  if (!c) return MQ_EINVAL;
+  if (level < 0 || level >= (int)c->levels.size()) return fail(c, MQ_EINVAL, "level %d out of range", level);
+  const mq_level& lv = c->levels[level];
+  if (!z || s != lv.s) return fail(c, MQ_EINVAL, "lattice of level %d needs s = %d components", level, lv.s);
+  for (int j = 0; j < s; ++j)
+    if (z[j] == 0 || z[j] >= lv.N) return fail(c, MQ_EINVAL, "z[%d] = %u not in (0, N)", j, z[j]);
+  MQ_CUDA(c, cudaSetDevice(c->device));
+  if (c->d_z[level]) cudaFree(c->d_z[level]);
+  c->d_z[level] = nullptr;
+  MQ_CUDA(c, cudaMalloc(&c->d_z[level], s * sizeof(uint32_t)));
+  MQ_CUDA(c, cudaMemcpy(c->d_z[level], z, s * sizeof(uint32_t), cudaMemcpyHostToDevice));
+  c->z[level].assign(z, z + s);
+  return MQ_OK;
+}
+
+mq_status mq_set_shifts(mq_ctx* c, int32_t level, const double* delta) {
+  if (!c) return MQ_EINVAL;
+  if (level < 0 || level >= (int)c->levels.size()) return fail(c, MQ_EINVAL, "level %d out of range", level);
+  if (!delta) return fail(c, MQ_EINVAL, "null shifts");
+  const mq_level& lv = c->levels[level];
+  const size_t m = (size_t)lv.R * lv.s;
+  for (size_t q = 0; q < m; ++q)
+    if (!(delta[q] >= 0.0 && delta[q] < 1.0)) return fail(c, MQ_EINVAL, "shift entry %zu = %g not in [0, 1)", q, delta[q]);
+  MQ_CUDA(c, cudaSetDevice(c->device));
+  if (c->d_delta[level]) cudaFree(c->d_delta[level]);
+  c->d_delta[level] = nullptr;
+  MQ_CUDA(c, cudaMalloc(&c->d_delta[level], m * sizeof(double)));
+  MQ_CUDA(c, cudaMemcpy(c->d_delta[level], delta, m * sizeof(double), cudaMemcpyHostToDevice));
+  c->delta[level].assign(delta, delta + m);
+  return MQ_OK;
+}
+
+mq_status mq_set_precision(mq_ctx* c, mq_precision prec, double tol_linear) {
+  if (!c) return MQ_EINVAL;
+  if (prec != MQ_PREC_FP64 && prec != MQ_PREC_MIXED) return fail(c, MQ_EINVAL, "unknown precision %d", (int)prec);
+  if (!std::isfinite(tol_linear) || tol_linear >= 1.0) return fail(c, MQ_EINVAL, "tolerance must be < 1");
+  c->prec = prec;
+  c->tol_lin = tol_linear > 0 ? tol_linear : 1e-10;
+  return MQ_OK;
+}
+
+mq_status mq_eval_level(mq_ctx* c, int32_t level, uint32_t k0, uint32_t k1, double* per_sample, double* shift_sums) {
+  if (!c) return MQ_EINVAL;
+  return eval_level_impl(c, level, k0, k1, per_sample, shift_sums, nullptr, nullptr);
+}
+
+mq_status mq_eval_level_device(mq_ctx* c, int32_t level, uint32_t k0, uint32_t k1, double* d_per_sample,
+                               double* d_shift_sums) {
+  if (!c) return MQ_EINVAL;
+  return eval_level_impl(c, level, k0, k1, nullptr, nullptr, d_per_sample, d_shift_sums);
+}
+
+mq_status mq_reset_sums(mq_ctx* c) {
+  if (!c) return MQ_EINVAL;
+  for (size_t l = 0; l < c->sums.size(); ++l) std::fill(c->sums[l].begin(), c->sums[l].end(), 0.0);
+  std::fill(c->npoints.begin(), c->npoints.end(), 0);
+  return MQ_OK;
+}
+
+mq_status mq_estimate(mq_ctx* c, double* mean, double* std_err, double* level_mean, double* level_var) {
+  if (!c) return MQ_EINVAL;
+  if (c->levels.empty()) return fail(c, MQ_ESTATE, "levels not set");
+  double tot = 0.0, var = 0.0;
+  for (size_t l = 0; l < c->levels.size(); ++l) {
+    const int R = c->levels[l].R;
+    if (c->npoints[l] == 0) return fail(c, MQ_ESTATE, "level %zu has no evaluated points", l);
+    if (R < 2) return fail(c, MQ_EINVAL, "level %zu: the standard error needs R >= 2 shifts", l);
+    std::vector<double> q(R);
+    double m = 0.0;
+    for (int r = 0; r < R; ++r) {
+      q[r] = c->sums[l][r] / (double)c->npoints[l];
+      m += q[r];
+    }
+    m /= R;
+    double v = 0.0;
+    for (int r = 0; r < R; ++r) v += (m - q[r]) * (m - q[r]);
+    v /= (double)R * (R - 1);
+    tot += m;
+    var += v;
+    if (level_mean) level_mean[l] = m;
+    if (level_var) level_var[l] = v;
+  }
+  if (mean) *mean = tot;
+  if (std_err) *std_err = std::sqrt(var);
+  return MQ_OK;
+}
+
+mq_status mq_eval_point(mq_ctx* c, int32_t level, const double* y, double* lam_H, double* lam_h, double* lam_hm1,
+                        double* u_H) {
+  if (!c) return MQ_EINVAL;
+  if (!c->coef_set) return fail(c, MQ_ESTATE, "coefficient not set");
+  if (level < 0 || level >= (int)c->levels.size()) return fail(c, MQ_EINVAL, "level %d out of range", level);
+  if (!y) return fail(c, MQ_EINVAL, "null parameter vector");
+  MQ_CUDA(c, cudaSetDevice(c->device));
+  const LevelGeom g = geom(c, level);
+  mq_status st;
+  if ((st = grow(c, c->Y, g.s * sizeof(double))) != MQ_OK) return st;
+  MQ_CUDA(c, cudaMemcpyAsync(c->Y.p, y, g.s * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  c->stats = mq_stats{};
+  if ((st = run_samples(c, g, 1, 1, 1, u_H != nullptr)) != MQ_OK) return st;
+  double o[4];
+  MQ_CUDA(c, cudaMemcpyAsync(o, c->out.p, sizeof o, cudaMemcpyDeviceToHost, c->stream));
+  if (u_H)
+    MQ_CUDA(c, cudaMemcpyAsync(u_H, c->uout.p, (size_t)(g.nc - 1) * (g.nc - 1) * sizeof(double),
+                               cudaMemcpyDeviceToHost, c->stream));
+  MQ_CUDA(c, cudaStreamSynchronize(c->stream));
+  if ((st = timing(c)) != MQ_OK) return st;
+  int fl = 0;
+  c->last_B = 1;
+  if ((st = collect_stats(c, 1, &fl)) != MQ_OK) return st;
+  if (lam_H) *lam_H = o[0];
+  if (lam_h) *lam_h = o[1];
+  if (lam_hm1) *lam_hm1 = o[2];
+  return flags_status(c, fl);
+}
+
+mq_status mq_get_stats(mq_ctx* c, void* stats, size_t bytes) {
+  if (!c || !stats) return MQ_EINVAL;
+  if (c->last_B) {
+    // iteration counters of the last pass (the sample count stays that of the whole call)
+    const uint64_t samples = c->stats.samples;
+    int fl = 0;
+    mq_status st = collect_stats(c, c->last_B, &fl);
+    if (st != MQ_OK) return st;
+    c->stats.samples = samples;
+  }
+  std::memcpy(stats, &c->stats, std::min(bytes, sizeof(mq_stats)));
+  return MQ_OK;
+}
+
+mq_status mq_cbc_lattice(uint32_t N, int32_t s, double decay, uint32_t* z_out) {
+  if (N < 2 || s < 1 || !z_out || !std::isfinite(decay)) return MQ_EINVAL;
+  std::vector<uint32_t> cand;
+  for (uint32_t q = 1; q <= N / 2; ++q)
+    if (std::gcd(q, N) == 1) cand.push_back(q);
+  if (cand.empty()) cand.push_back(1);
+  std::vector<double> prod(N, 1.0), e2(cand.size());
+  auto b2 = [](double x) { return x * x - x + 1.0 / 6.0; };
+  for (int j = 0; j < s; ++j) {
+    const double gam = std::pow((double)(j + 1), -decay);
+    for (size_t ci = 0; ci < cand.size(); ++ci) {
+      const uint64_t zc = cand[ci];
+      double acc = 0.0;
+      for (uint32_t k = 0; k < N; ++k) acc += prod[k] * (1.0 + gam * b2((double)((k * zc) % N) / (double)N));
+      e2[ci] = -1.0 + acc / N;
+    }
+    const double best = *std::min_element(e2.begin(), e2.end());
+    size_t pick = 0;
+    while (!(e2[pick] <= best + 1e-12)) ++pick;
+    z_out[j] = cand[pick];
+    const uint64_t zc = cand[pick];
+    for (uint32_t k = 0; k < N; ++k) prod[k] *= 1.0 + gam * b2((double)((k * zc) % N) / (double)N);
+  }
+  return MQ_OK;
+}
+
+mq_status mq_lattice_points_device(mq_ctx* c, int32_t level, uint32_t k0, uint32_t k1, double* d_Y) {
+  if (!c) return MQ_EINVAL;
+  mq_status st = check_level_ready(c, level);
+  if (st != MQ_OK) return st;
+  const mq_level& lv = c->levels[level];
+  if (k1 < k0 || k1 > lv.N || !d_Y) return fail(c, MQ_EINVAL, "bad point range or output");
+  MQ_CUDA(c, cudaSetDevice(c->device));
+  MQ_CUDA(c, mq::launch_lattice_points(c->d_z[level], lv.N, c->d_delta[level], lv.R, lv.s, k0, (int)(k1 - k0), d_Y,
+                                       c->stream));
+  MQ_CUDA(c, cudaStreamSynchronize(c->stream));
+  return MQ_OK;
+}
+
+mq_status mq_coefficients_device(mq_ctx* c, int32_t n, int32_t s, const double* d_Y, int32_t B, int32_t ldy,
+                                 double* d_a) {
+  if (!c) return MQ_EINVAL;
+  if (!c->coef_set) return fail(c, MQ_ESTATE, "coefficient not set");
+  if (!pow2(n) || n < 2 || n > 4096 || s < 0 || s > c->s_max || B < 0 || ldy < s || (!d_Y && B * s) || (!d_a && B))
+    return fail(c, MQ_EINVAL, "bad coefficient arguments");
+  MQ_CUDA(c, cudaSetDevice(c->device));
+  const double* psi = nullptr;
+  mq_status st = ensure_psi(c, n, std::max(c->s_max, 1), &psi);
+  if (st != MQ_OK) return st;
+  MQ_CUDA(c, mq::launch_coef_gemm_f64(d_Y, ldy, B, s, psi, 2 * n * n, c->a0, d_a, c->stream));
+  MQ_CUDA(c, cudaStreamSynchronize(c->stream));
+  return MQ_OK;
+}
+
+mq_status mq_apply_operator_device(mq_ctx* c, int32_t n, int32_t B, const double* d_a, int32_t which, double sigma,
+                                   const double* d_x, double* d_y) {
+  if (!c) return MQ_EINVAL;
+  if (!pow2(n) || n < 2 || n > 4096 || B < 0 || which < 0 || which > 2 || (B && (!d_a || !d_x || !d_y)))
+    return fail(c, MQ_EINVAL, "bad operator arguments");
+  MQ_CUDA(c, cudaSetDevice(c->device));
+  mq_status st = grow(c, c->misc, (size_t)B * 3 * (n + 1) * (n + 1) * sizeof(double));
+  if (st != MQ_OK) return st;
+  MQ_CUDA(c, mq::launch_apply_operator(n, B, d_a, which, sigma, d_x, d_y, (double*)c->misc.p, c->stream));
+  MQ_CUDA(c, cudaStreamSynchronize(c->stream));
+  return MQ_OK;
+}
+
+}  // extern "C"

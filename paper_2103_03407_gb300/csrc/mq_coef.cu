@@ -1,0 +1,141 @@
+// Lattice points and centroid coefficients (the data-parallel front of the level evaluation).
+//
+//  * lattice_points: y = {k z / N + Delta_r} - 1/2 (Sec. 2.5, eq. rqmc; eq. t_kl), exact integer
+//    arithmetic for k z mod N, one IEEE division and the same wrap as the fractional part.
+//  * psi_table: Psi[j][t] = j^-decay sin(pi k1_j x_t) sin(pi k2_j y_t) at the centroids of the
+//    2 n^2 triangles (lower triangle of cell (i,j): ((3i+2)/(3n), (3j+1)/(3n)); upper:
+//    ((3i+1)/(3n), (3j+2)/(3n))).
+//  * coef_gemm_f64: a[b][t] = a0 + sum_{j<s} Y[b][j] Psi[j][t] (eq. coeff, eq. coeff_s) as a
+//    tiled FP64 GEMM (register-blocked 4 x 8 outputs per thread, shared-memory K tiles).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "mq_internal.h"
+
+namespace mq {
+namespace {
+
+__global__ void lattice_kernel(const uint32_t* __restrict__ z, uint32_t N, const double* __restrict__ delta, int R,
+                               int s, uint32_t k0, int npts, double* __restrict__ Y) {
+  const size_t tot = (size_t)R * npts * s;
+  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(q % s);
+    const size_t b = q / s;
+    const int kk = (int)(b % npts);
+    const int r = (int)(b / npts);
+    const uint64_t k = (uint64_t)k0 + (uint64_t)kk;
+    const uint64_t m = (k * (uint64_t)z[j]) % (uint64_t)N;
+    double t = (double)m / (double)N + delta[(size_t)r * s + j];
+    if (t >= 1.0) t -= 1.0;
+    Y[q] = t - 0.5;
+  }
+}
+
+__global__ void psi_kernel(int n, int s, const int* __restrict__ k1, const int* __restrict__ k2,
+                           const double* __restrict__ cj, double* __restrict__ psi) {
+  const size_t nn = (size_t)n * n, nT = 2 * nn, tot = (size_t)s * nT;
+  const double inv3n = 1.0 / (3.0 * n);
+  (void)inv3n;
+  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(q / nT);
+    const size_t t = q % nT;
+    const int plane = (int)(t / nn);
+    const size_t cell = t % nn;
+    const int i = (int)(cell % n), jj = (int)(cell / n);
+    const double x = (double)(3 * i + (plane == 0 ? 2 : 1)) / (double)(3 * n);
+    const double y = (double)(3 * jj + (plane == 0 ? 1 : 2)) / (double)(3 * n);
+    psi[q] = cj[j] * sinpi((double)k1[j] * x) * sinpi((double)k2[j] * y);
+  }
+}
+
+constexpr int GBM = 64, GBN = 128, GBK = 16;
+
+// C[b][t] = a0 + sum_j Y[b*ldy + j] Psi[j*nT + t]; 256 threads as 16 x 16, 4 x 8 outputs each.
+__global__ void __launch_bounds__(256) gemm_f64_kernel(const double* __restrict__ Y, int ldy, int B, int s,
+                                                       const double* __restrict__ Psi, int nT, double a0,
+                                                       double* __restrict__ C) {
+  __shared__ double As[GBK][GBM + 1];
+  __shared__ double Bs[GBK][GBN];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int b0 = blockIdx.y * GBM, t0 = blockIdx.x * GBN;
+  double acc[4][8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.0;
+  for (int k0 = 0; k0 < s; k0 += GBK) {
+    // Y tile: 64 rows x 16 k
+    for (int q = threadIdx.x; q < GBM * GBK; q += 256) {
+      const int rr = q / GBK, kk = q % GBK;
+      const int b = b0 + rr, k = k0 + kk;
+      As[kk][rr] = (b < B && k < s) ? Y[(size_t)b * ldy + k] : 0.0;
+    }
+    // Psi tile: 16 k x 128 t
+    for (int q = threadIdx.x; q < GBK * GBN; q += 256) {
+      const int kk = q / GBN, cc = q % GBN;
+      const int k = k0 + kk, t = t0 + cc;
+      Bs[kk][cc] = (k < s && t < nT) ? Psi[(size_t)k * nT + t] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GBK; ++kk) {
+      double a[4], bv[8];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fma(a[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int b = b0 + ty + 16 * i;
+    if (b >= B) continue;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int t = t0 + tx + 16 * j;
+      if (t < nT) C[(size_t)b * nT + t] = a0 + acc[i][j];
+    }
+  }
+}
+
+int grid_for(size_t tot, int threads) {
+  size_t g = (tot + threads - 1) / threads;
+  if (g > 152 * 32) g = 152 * 32;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+cudaError_t launch_lattice_points(const uint32_t* d_z, uint32_t N, const double* d_delta, int R, int s, uint32_t k0,
+                                  int npts, double* d_Y, cudaStream_t st) {
+  const size_t tot = (size_t)R * npts * s;
+  if (tot == 0) return cudaSuccess;
+  lattice_kernel<<<grid_for(tot, 256), 256, 0, st>>>(d_z, N, d_delta, R, s, k0, npts, d_Y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_psi_table(int n, int s, const int* d_k1, const int* d_k2, const double* d_cj, double* d_psi,
+                             cudaStream_t st) {
+  const size_t tot = (size_t)s * 2 * n * n;
+  if (tot == 0) return cudaSuccess;
+  psi_kernel<<<grid_for(tot, 256), 256, 0, st>>>(n, s, d_k1, d_k2, d_cj, d_psi);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coef_gemm_f64(const double* d_Y, int ldy, int B, int s, const double* d_psi, int nT, double a0,
+                                 double* d_a, cudaStream_t st) {
+  if (B == 0 || nT == 0) return cudaSuccess;
+  dim3 grid((nT + GBN - 1) / GBN, (B + GBM - 1) / GBM);
+  if (grid.y > 65535) return cudaErrorInvalidValue;
+  gemm_f64_kernel<<<grid, 256, 0, st>>>(d_Y, ldy, B, s, d_psi, nT, a0, d_a);
+  return cudaGetLastError();
+}
+
+}  // namespace mq

@@ -1,0 +1,65 @@
+// Internal declarations shared by the library's translation units (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace mq {
+
+constexpr int kMaxMG = 13;  // multigrid levels: meshes 1/4096 .. 1/2
+
+// Per-launch parameters of the per-sample kernel (one CTA evaluates whole samples).
+struct SampleLaunch {
+  int nf, nc, np;          // fine mesh 1/h_l, coarse mesh 1/H_l, previous fine mesh (0: none)
+  int direct_f, direct_p;  // lambda^l (resp. lambda^{l-1}) equals the coarse eigenvalue
+  int R, npts, chunk;      // shifts, points per shift in this batch, points per warm-start chain
+  const double* a_f;       // [B][2 nf^2] centroid coefficients, truncation s_l
+  const double* a_c;       // [B][2 nc^2] truncation S_l
+  const double* a_p;       // [B][2 np^2] truncation s_{l-1}
+  double* out;             // [B][4] lambda_H, lambda^l, lambda^{l-1}, difference
+  int* stat;               // [B][4] coarse iterations, inner iterations (l, l-1), flags
+  int* outer;              // [B][2] refinement steps (l, l-1)
+  double* u_out;           // NULL or [B][(nc-1)^2] coarse eigenvectors
+  char* gscratch;          // per-CTA workspace slabs when they do not fit in shared memory
+  size_t slab_bytes;
+  int use_smem;
+  double tol_eig;
+  int max_eig_it;
+  double tol_lin;          // relative FP64 residual target of the shifted solve
+  double tol_inner;        // relative reduction of the preconditioned residual per inner solve
+  int max_inner_it;
+  int max_outer;
+  int nu;                  // Jacobi sweeps before and after each coarse-grid correction
+  double omega;            // Jacobi damping
+};
+
+// Sample flags (stat[b][3])
+enum : int {
+  kFlagEigNoConv = 1,
+  kFlagLinNoConv = 2,
+  kFlagBadCoef = 4,
+  kFlagBreakdown = 8,
+};
+
+size_t sample_slab_bytes(int nf, int nc, int np, int mixed);
+cudaError_t launch_sample(const SampleLaunch& p, int mixed, int blocks, int threads, size_t smem,
+                          cudaStream_t st);
+int sample_occupancy(int mixed, int threads, size_t smem);
+int sample_static_smem(int mixed);
+cudaError_t set_sample_smem(int mixed, int bytes);
+
+// Coefficient building blocks (mq_coef.cu)
+cudaError_t launch_lattice_points(const uint32_t* d_z, uint32_t N, const double* d_delta, int R, int s,
+                                  uint32_t k0, int npts, double* d_Y, cudaStream_t st);
+cudaError_t launch_psi_table(int n, int s, const int* d_k1, const int* d_k2, const double* d_cj,
+                             double* d_psi, cudaStream_t st);
+cudaError_t launch_coef_gemm_f64(const double* d_Y, int ldy, int B, int s, const double* d_psi, int nT,
+                                 double a0, double* d_a, cudaStream_t st);
+cudaError_t launch_apply_operator(int n, int B, const double* d_a, int which, double sigma,
+                                  const double* d_x, double* d_y, double* d_scratch, cudaStream_t st);
+cudaError_t launch_shift_sums(const double* d_out, const int* d_stat, int R, int npts, double* d_sums,
+                              int* d_flags, cudaStream_t st);
+
+}  // namespace mq

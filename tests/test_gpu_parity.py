@@ -1,0 +1,229 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances: integer and lattice-point work bit-exact; coefficients 1e-14 absolute (a ~ 1);
+operator applications 1e-13 relative; coarse eigenvalues 1e-12 relative; two-grid
+eigenvalues and level differences 1e-10 relative (FP64 and mixed paths), the workload target.
+"""
+import numpy as np
+import pytest
+
+from oracle import fem, lattice, mlqmc, twogrid
+from synthetic_inputs import WORKLOADS, Level, random_cell_coefficients, random_points, random_vectors, shifts
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+TOL_LAMBDA = 1e-10
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2103_03407_gb300 import binding, build
+
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.fail("a GPU test ran without a CUDA device")
+    return binding
+
+
+def make_ctx(B, levels, seed=0, prec=0, s_max=None):
+    ctx = B.Context(0)
+    ctx.mq_set_coefficient(1.0, s_max or max(lv.s for lv in levels), 0, 2.0)
+    ctx.mq_set_levels(levels)
+    zs, ds = [], shifts(seed, levels)
+    for l, lv in enumerate(levels):
+        z = lattice.cbc(lv.N, lv.s)
+        zs.append(z)
+        ctx.mq_set_lattice(l, z)
+        ctx.mq_set_shifts(l, ds[l])
+    ctx.mq_set_precision(prec)
+    return ctx, zs, ds
+
+
+def test_lattice_points_bit_exact(B):
+    lv = Level(16, 8, 16, 4, 256, 3)
+    ctx, zs, ds = make_ctx(B, [lv])
+    k0, k1 = 5, 101
+    d = torch.empty((lv.R, k1 - k0, lv.s), dtype=torch.float64, device="cuda")
+    ctx.mq_lattice_points_device(0, k0, k1, d)
+    got = d.cpu().numpy()
+    for r in range(lv.R):
+        ref = lattice.points(zs[0], lv.N, ds[0][r], np.arange(k0, k1))
+        assert np.array_equal(got[r], ref)
+
+
+@pytest.mark.parametrize("n,s", [(2, 1), (8, 16), (16, 37), (32, 64)])
+def test_coefficients_match_oracle(B, n, s):
+    ctx, _, _ = make_ctx(B, [Level(n, n, s, s, 8, 2)])
+    Y = random_points(n + s, 5, s)
+    dY = torch.from_numpy(Y).cuda()
+    da = torch.empty((5, 2 * n * n), dtype=torch.float64, device="cuda")
+    ctx.mq_coefficients_device(n, s, dY, 5, s, da)
+    got = da.cpu().numpy()
+    for b in range(5):
+        assert np.abs(got[b] - fem.coefficient(n, Y[b])).max() < 1e-14
+
+
+@pytest.mark.parametrize("n", [2, 4, 8, 16, 64])
+def test_operator_apply_matches_assembled_matrices(B, n):
+    ctx, _, _ = make_ctx(B, [Level(8, 8, 1, 1, 8, 2)])
+    nb = 3
+    a = random_cell_coefficients(n, nb, n).reshape(nb, -1)
+    x = random_vectors(n + 1, nb, (n - 1) ** 2)
+    da, dx = torch.from_numpy(a).cuda(), torch.from_numpy(x).cuda()
+    dy = torch.empty_like(dx)
+    sigma = 19.5
+    for which in range(3):
+        ctx.mq_apply_operator_device(n, nb, da, which, sigma, dx, dy)
+        got = dy.cpu().numpy()
+        for b in range(nb):
+            A, M = fem.assemble(n, a[b])
+            ref = [A @ x[b], M @ x[b], A @ x[b] - sigma * (M @ x[b])][which]
+            assert np.abs(got[b] - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+POINT_CASES = [
+    # (levels, level index): single level, two levels with a previous fine mesh, direct level 0
+    ([Level(16, 8, 16, 4, 8, 2)], 0),
+    ([Level(16, 8, 16, 4, 8, 2), Level(32, 8, 32, 6, 8, 2)], 1),
+    ([Level(32, 16, 8, 4, 8, 2), Level(64, 16, 16, 4, 8, 2)], 1),
+    ([Level(8, 8, 4, 4, 8, 2)], 0),
+    ([Level(8, 8, 4, 4, 8, 2), Level(32, 8, 16, 4, 8, 2)], 1),
+]
+
+
+@pytest.mark.parametrize("case", range(len(POINT_CASES)))
+@pytest.mark.parametrize("prec", [0, 1])
+def test_eval_point_matches_oracle(B, case, prec):
+    levels, l = POINT_CASES[case]
+    ctx, _, _ = make_ctx(B, levels, prec=prec)
+    lv = levels[l]
+    pv = levels[l - 1] if l > 0 else None
+    for y in random_points(100 + case, 3, lv.s):
+        lH, lh, lp, u = ctx.mq_eval_point(l, y, want_u=True)
+        rH, rh, rp, rd = mlqmc.sample_level(lv, pv, y)
+        assert lH == pytest.approx(rH, rel=1e-12)
+        assert lh == pytest.approx(rh, rel=TOL_LAMBDA)
+        assert lp == pytest.approx(rp, rel=TOL_LAMBDA, abs=0 if pv else 1e-300)
+        _, uref = twogrid.coarse_pair(lv.n_coarse, y[: lv.S])
+        assert np.abs(u - uref).max() < 1e-9
+
+
+def _check_level(per_sample, ref):
+    # per-sample (lambda_H, lambda^l, lambda^{l-1}, difference)
+    assert np.all(np.abs(per_sample[..., 0] - ref[..., 0]) <= 1e-12 * np.abs(ref[..., 0]))
+    assert np.all(np.abs(per_sample[..., 1] - ref[..., 1]) <= TOL_LAMBDA * np.abs(ref[..., 1]))
+    assert np.all(np.abs(per_sample[..., 2] - ref[..., 2]) <= TOL_LAMBDA * np.abs(ref[..., 2]))
+    # the difference is checked relative to the eigenvalues it is formed from
+    assert np.all(np.abs(per_sample[..., 3] - ref[..., 3]) <= 2 * TOL_LAMBDA * np.abs(ref[..., 1]))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_eval_level_single_level_workload(B, prec):
+    wl = WORKLOADS["qmc_h16_s16"]
+    lv = wl.levels[0]
+    ctx, zs, ds = make_ctx(B, wl.levels, seed=wl.seed, prec=prec)
+    k0, k1 = 3, 40  # several warm-start chains and a ragged tail
+    ps, sums = ctx.mq_eval_level(0, k0, k1)
+    ref = mlqmc.level_samples(lv, None, zs[0], ds[0], list(range(k0, k1)))
+    _check_level(ps, ref)
+    assert np.allclose(sums, ref[..., 3].sum(axis=1), rtol=1e-12, atol=0)
+    m, se, lm, lvv = ctx.mq_estimate()
+    om, ose, _, _ = mlqmc.estimate([mlqmc.shift_means(ref[..., 3], k1 - k0)])
+    assert m == pytest.approx(om, rel=1e-12)
+    assert se == pytest.approx(ose, rel=1e-6)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_eval_level_multilevel_workload_sampled(B, prec):
+    wl = WORKLOADS["mlqmc4_h16_128"]
+    ctx, zs, ds = make_ctx(B, wl.levels, seed=wl.seed, prec=prec)
+    for l, (k0, k1) in [(1, (0, 3)), (2, (7, 9)), (3, (0, 1))]:
+        lv, pv = wl.levels[l], wl.levels[l - 1]
+        ps, _ = ctx.mq_eval_level(l, k0, k1)
+        ref = mlqmc.level_samples(lv, pv, zs[l], ds[l], list(range(k0, k1)))
+        _check_level(ps, ref)
+
+
+def test_full_size_level_sampled_outputs(B):
+    # the finest level of the 4-level workload at its full point count (8,192 samples), in the
+    # launch configuration of the benchmark; a few samples checked against the oracle
+    wl = WORKLOADS["mlqmc4_h16_128"]
+    ctx, zs, ds = make_ctx(B, wl.levels, seed=wl.seed, prec=1)
+    l = 3
+    lv, pv = wl.levels[l], wl.levels[l - 1]
+    ps, sums = ctx.mq_eval_level(l, 0, lv.N)
+    rng = np.random.default_rng(0)
+    picks = [(int(r), int(k)) for r, k in zip(rng.integers(0, lv.R, 4), rng.integers(0, lv.N, 4))]
+    picks.append((lv.R - 1, lv.N - 1))
+    for r, k in picks:
+        ref = mlqmc.level_samples(lv, pv, zs[l], ds[l][r : r + 1], [k])[0, 0]
+        _check_level(ps[r, k][None, None], ref[None, None])
+    assert np.allclose(sums, ps[..., 3].sum(axis=1), rtol=1e-12)
+    assert np.all(np.isfinite(ps))
+
+
+def test_warm_start_does_not_change_results(B):
+    lv = Level(16, 8, 16, 4, 64, 2)
+    ctx, zs, ds = make_ctx(B, [lv])
+    ps, _ = ctx.mq_eval_level(0, 0, 20)
+    Y = lattice.points(zs[0], lv.N, ds[0][1], np.arange(20))
+    for k in (0, 1, 7, 19):
+        lH, lh, _ = ctx.mq_eval_point(0, Y[k])  # a single cold-started sample
+        assert ps[1, k, 0] == pytest.approx(lH, rel=1e-12)
+        assert ps[1, k, 1] == pytest.approx(lh, rel=1e-12)
+
+
+def test_device_outputs_equal_host_outputs(B):
+    lv = Level(32, 8, 16, 4, 64, 3)
+    ctx, _, _ = make_ctx(B, [lv])
+    ps, sums = ctx.mq_eval_level(0, 4, 30)
+    d_ps = torch.empty((lv.R, 26, 4), dtype=torch.float64, device="cuda")
+    d_s = torch.empty(lv.R, dtype=torch.float64, device="cuda")
+    ctx.mq_eval_level_device(0, 4, 30, d_ps, d_s)
+    assert np.array_equal(d_ps.cpu().numpy(), ps)
+    assert np.array_equal(d_s.cpu().numpy(), sums)
+
+
+def test_degenerate_direct_level(B):
+    # H = h and S = s: the level value is the fine eigenvalue itself
+    lv = Level(16, 16, 6, 6, 16, 2)
+    ctx, _, _ = make_ctx(B, [lv])
+    y = random_points(5, 1, 6)[0]
+    lH, lh, _ = ctx.mq_eval_point(0, y)
+    ref = twogrid.fine_eigenvalue(16, y)
+    assert lH == pytest.approx(ref, rel=1e-12) and lh == lH
+
+
+def test_empty_range_and_errors(B):
+    lv = Level(16, 8, 16, 4, 64, 1)
+    ctx, _, _ = make_ctx(B, [lv])
+    ps, sums = ctx.mq_eval_level(0, 10, 10)
+    assert ps.shape == (1, 0, 4) and sums[0] == 0.0
+    with pytest.raises(B.MQError) as e:
+        ctx.mq_eval_level(0, 0, 65)
+    assert e.value.status == B.MQ_EINVAL
+    ctx.mq_eval_level(0, 0, 2)
+    with pytest.raises(B.MQError) as e:  # one shift: no standard error
+        ctx.mq_estimate()
+    assert e.value.status == B.MQ_EINVAL
+    with pytest.raises(B.MQError) as e:
+        ctx.mq_set_shifts(0, np.full((1, 16), 1.0))
+    assert e.value.status == B.MQ_EINVAL
+    ctx2 = B.Context(0)
+    ctx2.mq_set_coefficient(1.0, 16)
+    ctx2.mq_set_levels([lv])
+    with pytest.raises(B.MQError) as e:
+        ctx2.mq_eval_level(0, 0, 1)
+    assert e.value.status == B.MQ_ESTATE
+
+
+def test_nonpositive_coefficient_is_rejected(B):
+    # a0 = 0.2 with y = -1/2 sign(psi_j) drives a below zero somewhere (Assumption A1)
+    ctx = B.Context(0)
+    ctx.mq_set_coefficient(0.2, 16)
+    ctx.mq_set_levels([Level(16, 8, 16, 4, 8, 2)])
+    with pytest.raises(B.MQError) as e:
+        ctx.mq_eval_point(0, np.full(16, -0.5))
+    assert e.value.status == B.MQ_EINVAL

@@ -29,9 +29,9 @@ def test_cbc_is_componentwise_argmin(N, s):
         cands = [c for c in range(1, N // 2 + 1) if math.gcd(c, N) == 1]
         errs = [lattice.cbc_error2(list(z[:j]) + [c], N, gamma[: j + 1]) for c in cands]
         best = min(errs)
-        assert lattice.cbc_error2(list(z[: j + 1]), N, gamma[: j + 1]) <= best * (1 + 1e-10)
+        assert lattice.cbc_error2(list(z[: j + 1]), N, gamma[: j + 1]) <= best + 1e-12
         # tie rule: no smaller candidate reaches the minimum
-        first = next(c for c, e in zip(cands, errs) if e <= best * (1 + 1e-10))
+        first = next(c for c, e in zip(cands, errs) if e <= best + 1e-12)
         assert z[j] == first
 
 
