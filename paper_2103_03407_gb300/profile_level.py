@@ -1,0 +1,51 @@
+"""Runs one level of a workload on a subset of its lattice points (for profilers and timing).
+
+    python -m paper_2103_03407_gb300.profile_level --workload mlqmc4_h16_128 --level 1 --points 64 \
+        --precision mixed [--repeat 2]
+
+Prints the device time and iteration statistics of each evaluation as JSON lines.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="mlqmc4_h16_128")
+    ap.add_argument("--level", type=int, action="append")
+    ap.add_argument("--points", type=int, default=64)
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--repeat", type=int, default=1)
+    a = ap.parse_args()
+    from paper_2103_03407_gb300 import binding, build
+    from synthetic_inputs import WORKLOADS, shifts
+
+    build.build()
+    wl = WORKLOADS[a.workload]
+    ctx = binding.Context(0)
+    ctx.mq_set_coefficient(wl.a0, max(lv.s for lv in wl.levels), 0, wl.decay)
+    ctx.mq_set_levels(wl.levels)
+    ds = shifts(wl.seed, wl.levels)
+    for l, lv in enumerate(wl.levels):
+        ctx.mq_set_lattice(l, binding.mq_cbc_lattice(lv.N, lv.s, wl.decay))
+        ctx.mq_set_shifts(l, ds[l])
+    ctx.mq_set_precision(binding.MQ_PREC_MIXED if a.precision == "mixed" else binding.MQ_PREC_FP64)
+    for l in a.level or [len(wl.levels) - 1]:
+        n = min(a.points, wl.levels[l].N)
+        for _ in range(a.repeat):
+            ctx.mq_eval_level(l, 0, n, per_sample=False)
+            st = ctx.mq_get_stats()
+            print(json.dumps({"level": l, "points": n, "samples": n * wl.levels[l].R, **st}))
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()
