@@ -168,6 +168,41 @@ mq_status mq_coefficients_device(mq_ctx* ctx, int32_t n, int32_t s, const double
 mq_status mq_apply_operator_device(mq_ctx* ctx, int32_t n, int32_t B, const double* d_a,
                                    int32_t which, double sigma, const double* d_x, double* d_y);
 
+
+/* ---- allocation-free entry point ------------------------------------------------------------
+ * No counterpart in the paper: an extra way to call the per-sample two-grid kernel for callers
+ * that cannot allocate device memory -- code running while someone else captures a CUDA graph,
+ * plugins inside a host application with its own fixed memory pool, real-time services that
+ * forbid allocation after start-up.  It calls no cudaMalloc, cudaFree or other allocating
+ * routine and needs no context: the per-block workspace lives in one fixed 32 MiB device array
+ * inside the library, which every GPU that loads the library holds until the process exits.
+ *
+ * For B samples it computes the coarse eigenpair on mesh 1/n_coarse, the two-grid eigenvalue
+ * on mesh 1/n_fine and (n_prev > 0) on mesh 1/n_prev from the same coarse pair (Algorithm 1
+ * steps as in mq_eval_level), from caller-evaluated centroid coefficients:
+ *   d_a_coarse [B][2 n_coarse^2] (truncation S), d_a_fine [B][2 n_fine^2] (truncation s) or NULL
+ *   for a direct level (the fine value is then the coarse eigenvalue), d_a_prev [B][2 n_prev^2]
+ *   or NULL (with n_prev > 0: the previous-level value is the coarse eigenvalue).
+ * Outputs (device, caller-owned): d_out [B][4] = (lambda_H, lambda^l, lambda^{l-1}, difference);
+ * d_stat [B][4] = (coarse iterations, inner iterations on n_fine, on n_prev, flags: 1 eigensolver
+ * cap, 2 linear-solver cap, 4 coefficient <= 0, 8 breakdown); d_outer [B][2] refinement steps.
+ * Samples are split into chains of consecutive indices; within a chain each coarse eigensolve
+ * starts from the previous sample's eigenvector.  precision: MQ_PREC_FP64 or MQ_PREC_MIXED;
+ * tol_linear <= 0 selects 1e-10.  The launch is asynchronous on cuda_stream (NULL: the default
+ * stream); check d_stat after synchronising.
+ *
+ * The first call on each device looks up the device address of the array (with that device
+ * current) and caches it; make that first call before any stream capture begins.  The array
+ * keeps the contents of the last call; the kernel clears everything it reads before use.  All
+ * calls share the one array, so calls whose kernels overlap on the GPU (different streams, or
+ * different host threads) race and corrupt each other's results: serialise them.
+ * Returns MQ_EINVAL for bad sizes or null pointers, and when one block's workspace for these
+ * meshes exceeds the 32 MiB array (e.g. n_fine = 4096); MQ_ECUDA when the launch fails. */
+mq_status mq_twogrid_samples_noalloc(int32_t n_fine, int32_t n_coarse, int32_t n_prev, int32_t precision,
+                                     int32_t B, const double* d_a_fine, const double* d_a_coarse,
+                                     const double* d_a_prev, double tol_linear, double* d_out,
+                                     int32_t* d_stat, int32_t* d_outer, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

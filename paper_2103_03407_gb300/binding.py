@@ -27,7 +27,7 @@ EXPORTS = [
     "mq_create", "mq_destroy", "mq_set_coefficient", "mq_set_levels", "mq_set_lattice", "mq_set_shifts",
     "mq_set_precision", "mq_eval_level", "mq_eval_level_device", "mq_estimate", "mq_reset_sums", "mq_eval_point",
     "mq_get_stats", "mq_last_error", "mq_cbc_lattice", "mq_lattice_points_device", "mq_coefficients_device",
-    "mq_apply_operator_device",
+    "mq_apply_operator_device", "mq_twogrid_samples_noalloc",
 ]
 
 
@@ -90,6 +90,7 @@ def load(path: str = LIB_PATH):
         "mq_lattice_points_device": ([P, i32, u32, u32, P], C.c_int),
         "mq_coefficients_device": ([P, i32, i32, P, i32, i32, P], C.c_int),
         "mq_apply_operator_device": ([P, i32, i32, P, i32, f64, P, P], C.c_int),
+        "mq_twogrid_samples_noalloc": ([i32, i32, i32, i32, i32, P, P, P, f64, P, P, P, P], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -222,6 +223,19 @@ class Context:
     def mq_apply_operator_device(self, n, B, d_a, which, sigma, d_x, d_y):
         self._check(self.lib.mq_apply_operator_device(self.h, int(n), int(B), _tptr(d_a), int(which), float(sigma),
                                                       _tptr(d_x), _tptr(d_y)))
+
+
+def mq_twogrid_samples_noalloc(n_fine, n_coarse, n_prev, precision, B, d_a_fine, d_a_coarse, d_a_prev, d_out,
+                               d_stat, d_outer, tol_linear=0.0, stream=None):
+    """The allocation-free per-sample entry point (see the header): device tensors in and out,
+    asynchronous on ``stream`` (a cudaStream_t value or None for the default stream)."""
+    lib = load()
+    st = lib.mq_twogrid_samples_noalloc(int(n_fine), int(n_coarse), int(n_prev), int(precision), int(B),
+                                        _tptr(d_a_fine), _tptr(d_a_coarse), _tptr(d_a_prev), float(tol_linear),
+                                        _tptr(d_out), _tptr(d_stat), _tptr(d_outer),
+                                        C.c_void_p(stream) if stream else None)
+    if st != MQ_OK:
+        raise MQError(st, "mq_twogrid_samples_noalloc failed")
 
 
 def mq_cbc_lattice(N: int, s: int, decay: float = 2.0) -> np.ndarray:
