@@ -37,13 +37,13 @@ namespace mq {
 namespace {
 
 // ---------------------------------------------------------------------------------------------
-// workspace carving
+// workspace carving (16-byte aligned arrays)
 struct Carver {
   uintptr_t base, cur;
   __host__ __device__ explicit Carver(void* b) : base((uintptr_t)b), cur((uintptr_t)b) {}
   template <typename T>
   __host__ __device__ T* take(size_t count) {
-    cur = (cur + 255) & ~(uintptr_t)255;
+    cur = (cur + 15) & ~(uintptr_t)15;
     T* p = (T*)cur;
     cur += count * sizeof(T);
     return p;
@@ -52,38 +52,40 @@ struct Carver {
 };
 
 __host__ __device__ inline int ilog2(int n) {
+#ifdef __CUDA_ARCH__
+  return __ffs(n) - 1;  // n is a power of two
+#else
   int l = 0;
   while ((1 << l) < n) ++l;
   return l;
+#endif
 }
 __host__ __device__ inline size_t gsz(int n) { return (size_t)(n + 1) * (size_t)(n + 1); }
 
+// Multigrid hierarchy for the stiffness A on meshes n, n/2, ..., 2 (level 0 = finest).
 template <typename T>
 struct MGDesc {
   int L;
   int n[kMaxMG];
-  T* wx[kMaxMG];
-  T* wy[kMaxMG];
-  T* x[kMaxMG];  // level solution (level 0: supplied by the caller)
-  T* t[kMaxMG];  // Jacobi ping-pong partner / residual
-  T* b[kMaxMG];  // level right-hand side (level 0: supplied by the caller)
-  T* cell[2];    // ping-pong per-triangle coefficients while building
+  T* wx[kMaxMG];  // weight of edge (i,j)-(i+1,j) at padded node (i,j)
+  T* wy[kMaxMG];  // weight of edge (i,j)-(i,j+1)
+  T* dinv[kMaxMG];  // 1 / diag(A)
+  T* x[kMaxMG];   // level solution (level 0: supplied by the caller)
+  T* t[kMaxMG];   // Jacobi partner
+  T* b[kMaxMG];   // level right-hand side (level 0: supplied by the caller)
+  T* cell[2];     // ping-pong per-triangle coefficients while building
 };
 
 template <typename T>
-__host__ __device__ void carve_mg(Carver& c, int n, MGDesc<T>& d, T* wx0, T* wy0) {
-  d.L = ilog2(n);  // meshes n, n/2, ..., 2
+__host__ __device__ void carve_mg(Carver& c, int n, MGDesc<T>& d) {
+  d.L = ilog2(n);
   for (int l = 0; l < d.L; ++l) {
     const int nl = n >> l;
     d.n[l] = nl;
     const size_t V = gsz(nl);
-    if (l == 0 && wx0) {
-      d.wx[0] = wx0;
-      d.wy[0] = wy0;
-    } else {
-      d.wx[l] = c.take<T>(V);
-      d.wy[l] = c.take<T>(V);
-    }
+    d.wx[l] = c.take<T>(V);
+    d.wy[l] = c.take<T>(V);
+    d.dinv[l] = c.take<T>(V);
     d.t[l] = c.take<T>(V);
     d.x[l] = l ? c.take<T>(V) : nullptr;
     d.b[l] = l ? c.take<T>(V) : nullptr;
@@ -93,13 +95,18 @@ __host__ __device__ void carve_mg(Carver& c, int n, MGDesc<T>& d, T* wx0, T* wy0
   d.cell[1] = c.take<T>(cells);
 }
 
+// Coarse eigensolve workspace: FP64 LOBPCG basis, FP64 operator weights, FP32 preconditioner.
 struct CoarseWS {
-  MGDesc<double> mg;
-  double *x, *Ax, *Mx, *w, *Aw, *Mw, *p, *Ap, *Mp, *r, *uprev;
+  MGDesc<float> mg;
+  double *wx, *wy;
+  double *x, *Ax, *Mx, *w, *Aw, *Mw, *p, *Ap, *Mp, *uprev;
+  float *r32, *w32;
 };
 
 __host__ __device__ void carve_coarse(Carver& c, int nc, CoarseWS& ws) {
   const size_t V = gsz(nc);
+  ws.wx = c.take<double>(V);
+  ws.wy = c.take<double>(V);
   ws.x = c.take<double>(V);
   ws.Ax = c.take<double>(V);
   ws.Mx = c.take<double>(V);
@@ -109,25 +116,24 @@ __host__ __device__ void carve_coarse(Carver& c, int nc, CoarseWS& ws) {
   ws.p = c.take<double>(V);
   ws.Ap = c.take<double>(V);
   ws.Mp = c.take<double>(V);
-  ws.r = c.take<double>(V);
   ws.uprev = c.take<double>(V);
-  carve_mg<double>(c, nc, ws.mg, nullptr, nullptr);
+  ws.r32 = c.take<float>(V);
+  ws.w32 = c.take<float>(V);
+  carve_mg<float>(c, nc, ws.mg);
 }
 
+// Fine shifted-solve workspace: FP64 solution and right-hand side, inner vectors in T.
 template <typename T>
 struct FineWS {
   MGDesc<T> mg;
-  double *wx64, *wy64, *x64, *r64, *b64;
+  double *x64, *b64;
   T *vo, *v, *z, *zn, *wo, *w, *q, *xi;
 };
 
 template <typename T>
 __host__ __device__ void carve_fine(Carver& c, int n, FineWS<T>& ws) {
   const size_t V = gsz(n);
-  ws.wx64 = c.take<double>(V);
-  ws.wy64 = c.take<double>(V);
   ws.x64 = c.take<double>(V);
-  ws.r64 = c.take<double>(V);
   ws.b64 = c.take<double>(V);
   ws.vo = c.take<T>(V);
   ws.v = c.take<T>(V);
@@ -137,8 +143,7 @@ __host__ __device__ void carve_fine(Carver& c, int n, FineWS<T>& ws) {
   ws.w = c.take<T>(V);
   ws.q = c.take<T>(V);
   ws.xi = c.take<T>(V);
-  const bool same = sizeof(T) == sizeof(double);
-  carve_mg<T>(c, n, ws.mg, same ? (T*)ws.wx64 : nullptr, same ? (T*)ws.wy64 : nullptr);
+  carve_mg<T>(c, n, ws.mg);
 }
 
 template <typename T>
@@ -146,11 +151,11 @@ __host__ __device__ size_t slab_size(int nf, int nc, int np) {
   Carver c(nullptr);
   CoarseWS cw;
   carve_coarse(c, nc, cw);
-  const size_t coarse = (c.used() + 255) & ~(size_t)255;
+  const size_t coarse = (c.used() + 15) & ~(size_t)15;
   Carver f(nullptr);
   FineWS<T> fw;
   carve_fine<T>(f, nf > np ? nf : np, fw);
-  return coarse + ((f.used() + 255) & ~(size_t)255);
+  return coarse + ((f.used() + 15) & ~(size_t)15);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -173,9 +178,15 @@ __device__ __forceinline__ void for_all(size_t count, F f) {
   for (size_t q = threadIdx.x; q < count; q += blockDim.x) f(q);
 }
 
-// Sum NV values over the block; every thread receives the totals.  Fixed order: deterministic.
-template <int NV, typename A>
-__device__ __forceinline__ void block_sum(A (&v)[NV], double (&out)[NV], double* red) {
+struct NoEp {
+  __device__ void operator()(const double*) const {}
+};
+
+// Sum NV values over the block (fixed order: deterministic).  Thread 0 runs ep(totals) before the
+// closing barrier, so scalars it derives are visible to every thread after the call; every thread
+// also receives the totals in out.
+template <int NV, typename A, class Ep = NoEp>
+__device__ __forceinline__ void block_sum(A (&v)[NV], double (&out)[NV], double* red, Ep ep = Ep()) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
@@ -186,13 +197,16 @@ __device__ __forceinline__ void block_sum(A (&v)[NV], double (&out)[NV], double*
   }
   __syncthreads();
   if (wid == 0) {
+    double tot[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
       double s = lane < nw ? red[lane * NV + i] : 0.0;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      tot[i] = s;
       if (lane == 0) red[32 * NV + i] = s;
     }
+    if (lane == 0) ep(tot);
   }
   __syncthreads();
 #pragma unroll
@@ -200,14 +214,12 @@ __device__ __forceinline__ void block_sum(A (&v)[NV], double (&out)[NV], double*
   __syncthreads();
 }
 
-// stiffness (weighted five-point edge form) at padded node p; also returns the diagonal
-template <typename T>
-__device__ __forceinline__ T stiff(const T* __restrict__ wx, const T* __restrict__ wy, const T* x, int p, int ld,
-                                   T& diag) {
-  const T we = wx[p], ww = wx[p - 1], wn = wy[p], ws = wy[p - ld];
-  const T xp = x[p];
-  diag = we + ww + wn + ws;
-  return we * (xp - x[p + 1]) + ww * (xp - x[p - 1]) + wn * (xp - x[p + ld]) + ws * (xp - x[p - ld]);
+// stiffness (weighted five-point edge form) at padded node p
+template <typename T, typename X>
+__device__ __forceinline__ T stiff(const T* __restrict__ wx, const T* __restrict__ wy, const X* x, int p, int ld) {
+  const T xp = (T)x[p];
+  return wx[p] * (xp - (T)x[p + 1]) + wx[p - 1] * (xp - (T)x[p - 1]) + wy[p] * (xp - (T)x[p + ld]) +
+         wy[p - ld] * (xp - (T)x[p - ld]);
 }
 
 // mass seven-point sum without the h^2/12 factor
@@ -216,8 +228,23 @@ __device__ __forceinline__ T mass7(const T* x, int p, int ld) {
   return T(6) * x[p] + (x[p + 1] + x[p - 1]) + (x[p + ld] + x[p - ld]) + (x[p + ld + 1] + x[p - ld - 1]);
 }
 
+// FP64 stiffness at interior node (i, j) of mesh n with the edge weights formed from the
+// centroid coefficients a (lower triangles first, then upper).
+__device__ __forceinline__ double stiff_cells(const double* __restrict__ a, int n, const double* x, int p, int ld,
+                                              int i, int j) {
+  const double* lo = a;
+  const double* up = a + (size_t)n * n;
+  const int c = j * n + i;
+  const double lij = lo[c], li1j = lo[c - 1], li1j1 = lo[c - n - 1];
+  const double uij = up[c], uij1 = up[c - n], ui1j1 = up[c - n - 1];
+  const double we = 0.5 * (lij + uij1), ww = 0.5 * (li1j + ui1j1);
+  const double wn = 0.5 * (uij + li1j), ws = 0.5 * (uij1 + li1j1);
+  const double xp = x[p];
+  return we * (xp - x[p + 1]) + ww * (xp - x[p - 1]) + wn * (xp - x[p + ld]) + ws * (xp - x[p - ld]);
+}
+
 // ---------------------------------------------------------------------------------------------
-// operator setup: edge weights of every multigrid level from the fine centroid coefficients
+// operator setup
 template <typename T, typename S>
 __device__ void weights_from_cells(int n, const S* low, const S* up, T* wx, T* wy) {
   const int ld = n + 1;
@@ -231,7 +258,6 @@ __device__ void weights_from_cells(int n, const S* low, const S* up, T* wx, T* w
   });
 }
 
-// per-triangle coefficients of the mesh n/2 as means over the four fine triangles they contain
 template <typename T, typename S>
 __device__ void coarsen_cells(int n, const S* low, const S* up, T* out) {
   const int m = n / 2;
@@ -247,7 +273,14 @@ __device__ void coarsen_cells(int n, const S* low, const S* up, T* out) {
   });
 }
 
-// builds all levels; returns true when every fine coefficient is positive (Assumption A1)
+template <typename T>
+__device__ void inverse_diagonal(int n, const T* wx, const T* wy, T* dinv) {
+  const int ld = n + 1;
+  for_interior(n, [&](int p, int, int) { dinv[p] = T(1) / (wx[p] + wx[p - 1] + wy[p] + wy[p - ld]); });
+}
+
+// Builds every level (weights, inverse diagonals) from the fine centroid coefficients a.
+// Returns true when every coefficient is positive (Assumption A1).
 template <typename T>
 __device__ bool build_mg(MGDesc<T>& d, const double* __restrict__ a, int n, double* red) {
   int bad = 0;
@@ -260,15 +293,18 @@ __device__ bool build_mg(MGDesc<T>& d, const double* __restrict__ a, int n, doub
     const T* src = d.cell[(l - 1) & 1];
     weights_from_cells<T, T>(nl, src, src + (size_t)nl * nl, d.wx[l], d.wy[l]);
     if (l + 1 < d.L) coarsen_cells<T, T>(nl, src, src + (size_t)nl * nl, d.cell[l & 1]);
+    inverse_diagonal<T>(d.n[l - 1], d.wx[l - 1], d.wy[l - 1], d.dinv[l - 1]);
     __syncthreads();
   }
+  inverse_diagonal<T>(d.n[d.L - 1], d.wx[d.L - 1], d.wy[d.L - 1], d.dinv[d.L - 1]);
   double v[1] = {(double)bad}, o[1];
   block_sum<1, double>(v, o, red);
   return o[0] == 0.0;
 }
 
-// symmetric V-cycle for A (damped Jacobi, nu sweeps before and after, Galerkin coarse levels,
-// exact solve on the one-unknown mesh 1/2): x0 = B^{-1} b0
+// Symmetric V-cycle for A: damped Jacobi (nu sweeps before and after the coarse correction),
+// Galerkin coarse levels, exact solve on the one-unknown mesh 1/2.  x0 = B^{-1} b0.
+// The residual is restricted with P^T in the same sweep that forms it.
 template <typename T>
 __device__ void vcycle(const MGDesc<T>& d, const T* b0, T* x0, int nu, T omega) {
   const int L = d.L;
@@ -276,56 +312,43 @@ __device__ void vcycle(const MGDesc<T>& d, const T* b0, T* x0, int nu, T omega) 
     const int n = d.n[l], ld = n + 1;
     const T* b = l ? d.b[l] : b0;
     T* xa = l ? d.x[l] : x0;
-    const T* wx = d.wx[l];
-    const T* wy = d.wy[l];
+    const T* __restrict__ wx = d.wx[l];
+    const T* __restrict__ wy = d.wy[l];
+    const T* __restrict__ di = d.dinv[l];
     T* cur = d.t[l];
     T* oth = xa;
-    for_interior(n, [&](int p, int, int) {
-      const T dg = wx[p] + wx[p - 1] + wy[p] + wy[p - ld];
-      cur[p] = omega * b[p] / dg;
-    });
+    for_interior(n, [&](int p, int, int) { cur[p] = omega * di[p] * b[p]; });
     __syncthreads();
     for (int k = 1; k < nu; ++k) {
-      for_interior(n, [&](int p, int, int) {
-        T dg;
-        const T ax = stiff(wx, wy, cur, p, ld, dg);
-        oth[p] = cur[p] + omega * (b[p] - ax) / dg;
-      });
+      for_interior(n, [&](int p, int, int) { oth[p] = cur[p] + omega * di[p] * (b[p] - stiff<T, T>(wx, wy, cur, p, ld)); });
       __syncthreads();
       T* tt = cur;
       cur = oth;
       oth = tt;
     }
-    for_interior(n, [&](int p, int, int) {
-      T dg;
-      oth[p] = b[p] - stiff(wx, wy, cur, p, ld, dg);
-    });
-    __syncthreads();
     T* bc = d.b[l + 1];
+    const T* cx = cur;
     for_interior(n >> 1, [&](int P, int I, int J) {
       const int p = (2 * J) * ld + 2 * I;
-      bc[P] = oth[p] + T(0.5) * ((oth[p + 1] + oth[p - 1]) + (oth[p + ld] + oth[p - ld]) +
-                                 (oth[p + ld + 1] + oth[p - ld - 1]));
+      auto res = [&](int q) { return b[q] - stiff<T, T>(wx, wy, cx, q, ld); };
+      bc[P] = res(p) + T(0.5) * ((res(p + 1) + res(p - 1)) + (res(p + ld) + res(p - ld)) +
+                                 (res(p + ld + 1) + res(p - ld - 1)));
     });
     __syncthreads();
   }
   {
-    // mesh 1/2: one unknown at padded index 4
     const T* b = (L - 1) ? d.b[L - 1] : b0;
     T* x = (L - 1) ? d.x[L - 1] : x0;
-    if (threadIdx.x == 0) {
-      const T* wx = d.wx[L - 1];
-      const T* wy = d.wy[L - 1];
-      x[4] = b[4] / (wx[4] + wx[3] + wy[4] + wy[1]);
-    }
+    if (threadIdx.x == 0) x[4] = b[4] * d.dinv[L - 1][4];  // mesh 1/2: one unknown at padded index 4
     __syncthreads();
   }
   for (int l = L - 2; l >= 0; --l) {
     const int n = d.n[l], ld = n + 1;
     const T* b = l ? d.b[l] : b0;
     T* xa = l ? d.x[l] : x0;
-    const T* wx = d.wx[l];
-    const T* wy = d.wy[l];
+    const T* __restrict__ wx = d.wx[l];
+    const T* __restrict__ wy = d.wy[l];
+    const T* __restrict__ di = d.dinv[l];
     T* cur = ((nu - 1) & 1) ? xa : d.t[l];
     T* oth = ((nu - 1) & 1) ? d.t[l] : xa;
     const T* xc = d.x[l + 1];
@@ -342,11 +365,7 @@ __device__ void vcycle(const MGDesc<T>& d, const T* b0, T* x0, int nu, T omega) 
     });
     __syncthreads();
     for (int k = 0; k < nu; ++k) {
-      for_interior(n, [&](int p, int, int) {
-        T dg;
-        const T ax = stiff(wx, wy, cur, p, ld, dg);
-        oth[p] = cur[p] + omega * (b[p] - ax) / dg;
-      });
+      for_interior(n, [&](int p, int, int) { oth[p] = cur[p] + omega * di[p] * (b[p] - stiff<T, T>(wx, wy, cur, p, ld)); });
       __syncthreads();
       T* tt = cur;
       cur = oth;
@@ -360,82 +379,97 @@ __device__ void zero_vec(T* v, int n) {
   for_all(gsz(n), [&](size_t q) { v[q] = T(0); });
 }
 
+template <typename T>
+__device__ void zero_mg(const MGDesc<T>& d) {
+  for (int l = 0; l < d.L; ++l) {
+    zero_vec(d.t[l], d.n[l]);
+    zero_vec(d.dinv[l], d.n[l]);
+    if (l) {
+      zero_vec(d.x[l], d.n[l]);
+      zero_vec(d.b[l], d.n[l]);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------------------------
-// small dense Rayleigh-Ritz for LOBPCG (one thread).  Basis [x, w, p] (k = 2 or 3); returns the
-// number of basis vectors kept (0: failure) and c with c^T GM c = 1 for the smallest Ritz value.
-__device__ int rayleigh_ritz(const double GA[3][3], const double GM[3][3], int k, double c[3], double& theta) {
+// Small dense Rayleigh-Ritz for LOBPCG, run by one thread.  The pencil is shifted by the current
+// Ritz value in FP64 before it is rounded to FP32: the shifted Gram matrix GA - theta GM has
+// entries of the size of the correction, so FP32 resolves the correction to FP32 relative
+// accuracy (GB300 executes FP64 at a small fraction of the FP32 rate, and a single thread's FP64
+// instruction costs a full warp's issue slot).  Basis [x, w, p] (k = 2 or 3).  Returns the number
+// of basis vectors kept (0: failure), the coefficients c of the smallest Ritz vector and mu, the
+// smallest eigenvalue of the shifted pencil (theta_new - theta).
+__device__ int rayleigh_ritz_shifted(const float GAs[3][3], const float GM[3][3], int k, float c[3], float& mu) {
   for (; k >= 2; --k) {
-    double dsc[3], A[3][3], B[3][3], Lm[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    float dsc[3], A[3][3], B[3][3], Lm[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
     bool ok = true;
     for (int i = 0; i < k; ++i) {
-      if (!(GM[i][i] > 0.0)) ok = false;
-      dsc[i] = ok ? 1.0 / sqrt(GM[i][i]) : 0.0;
+      if (!(GM[i][i] > 0.0f)) ok = false;
+      dsc[i] = ok ? rsqrtf(GM[i][i]) : 0.0f;
     }
     if (!ok) continue;
     for (int i = 0; i < k; ++i)
       for (int j = 0; j < k; ++j) {
-        A[i][j] = dsc[i] * GA[i][j] * dsc[j];
+        A[i][j] = dsc[i] * GAs[i][j] * dsc[j];
         B[i][j] = dsc[i] * GM[i][j] * dsc[j];
       }
     for (int i = 0; i < k && ok; ++i)
       for (int j = 0; j <= i; ++j) {
-        double s = B[i][j];
+        float s = B[i][j];
         for (int m = 0; m < j; ++m) s -= Lm[i][m] * Lm[j][m];
         if (i == j) {
-          if (!(s > 1e-12)) {
+          if (!(s > 1e-5f)) {
             ok = false;
             break;
           }
-          Lm[i][i] = sqrt(s);
+          Lm[i][i] = sqrtf(s);
         } else {
           Lm[i][j] = s / Lm[j][j];
         }
       }
     if (!ok) continue;
-    // C = L^{-1} A L^{-T}
-    double Y[3][3], C[3][3];
+    float Y[3][3], C[3][3];
     for (int j = 0; j < k; ++j)
       for (int i = 0; i < k; ++i) {
-        double s = A[i][j];
+        float s = A[i][j];
         for (int m = 0; m < i; ++m) s -= Lm[i][m] * Y[m][j];
         Y[i][j] = s / Lm[i][i];
       }
     for (int i = 0; i < k; ++i)
       for (int j = 0; j < k; ++j) {
-        double s = Y[i][j];
+        float s = Y[i][j];
         for (int m = 0; m < j; ++m) s -= Lm[j][m] * C[i][m];
         C[i][j] = s / Lm[j][j];
       }
     for (int i = 0; i < k; ++i)
-      for (int j = 0; j < i; ++j) C[i][j] = C[j][i] = 0.5 * (C[i][j] + C[j][i]);
-    // cyclic Jacobi eigen-decomposition of the k x k symmetric C
-    double V[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
-    for (int sweep = 0; sweep < 30; ++sweep) {
-      double off = 0.0, dia = 0.0;
+      for (int j = 0; j < i; ++j) C[i][j] = C[j][i] = 0.5f * (C[i][j] + C[j][i]);
+    float V[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    for (int sweep = 0; sweep < 12; ++sweep) {
+      float off = 0.0f, dia = 0.0f;
       for (int i = 0; i < k; ++i) {
         dia += C[i][i] * C[i][i];
         for (int j = i + 1; j < k; ++j) off += C[i][j] * C[i][j];
       }
-      if (off <= 1e-32 * dia) break;
+      if (off <= 1e-14f * dia || off == 0.0f) break;
       for (int pI = 0; pI < k - 1; ++pI)
         for (int qI = pI + 1; qI < k; ++qI) {
-          const double apq = C[pI][qI];
-          if (apq == 0.0) continue;
-          const double tau = (C[qI][qI] - C[pI][pI]) / (2.0 * apq);
-          const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-          const double cs = 1.0 / sqrt(1.0 + t * t), sn = t * cs;
+          const float apq = C[pI][qI];
+          if (apq == 0.0f) continue;
+          const float tau = (C[qI][qI] - C[pI][pI]) / (2.0f * apq);
+          const float t = (tau >= 0 ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
+          const float cs = rsqrtf(1.0f + t * t), sn = t * cs;
           for (int m = 0; m < k; ++m) {
-            const double cmp = C[m][pI], cmq = C[m][qI];
+            const float cmp = C[m][pI], cmq = C[m][qI];
             C[m][pI] = cs * cmp - sn * cmq;
             C[m][qI] = sn * cmp + cs * cmq;
           }
           for (int m = 0; m < k; ++m) {
-            const double cpm = C[pI][m], cqm = C[qI][m];
+            const float cpm = C[pI][m], cqm = C[qI][m];
             C[pI][m] = cs * cpm - sn * cqm;
             C[qI][m] = sn * cpm + cs * cqm;
           }
           for (int m = 0; m < k; ++m) {
-            const double vmp = V[m][pI], vmq = V[m][qI];
+            const float vmp = V[m][pI], vmq = V[m][qI];
             V[m][pI] = cs * vmp - sn * vmq;
             V[m][qI] = sn * vmp + cs * vmq;
           }
@@ -444,16 +478,15 @@ __device__ int rayleigh_ritz(const double GA[3][3], const double GM[3][3], int k
     int mi = 0;
     for (int i = 1; i < k; ++i)
       if (C[i][i] < C[mi][mi]) mi = i;
-    theta = C[mi][mi];
-    // c = D L^{-T} y
-    double y[3] = {V[0][mi], V[1][mi], k > 2 ? V[2][mi] : 0.0};
-    double cc[3] = {0, 0, 0};
+    mu = C[mi][mi];
+    float y[3] = {V[0][mi], V[1][mi], k > 2 ? V[2][mi] : 0.0f};
+    float cc[3] = {0, 0, 0};
     for (int i = k - 1; i >= 0; --i) {
-      double s = y[i];
+      float s = y[i];
       for (int m = i + 1; m < k; ++m) s -= Lm[m][i] * cc[m];
       cc[i] = s / Lm[i][i];
     }
-    for (int i = 0; i < 3; ++i) c[i] = i < k ? cc[i] * dsc[i] : 0.0;
+    for (int i = 0; i < 3; ++i) c[i] = i < k ? cc[i] * dsc[i] : 0.0f;
     return k;
   }
   return 0;
@@ -463,38 +496,39 @@ struct EigShared {
   double c[3];   // x_new = c0 x + c1 w + c2 p
   double pc[2];  // p_new = pc0 w + pc1 p
   double theta;
+  double scale;  // normalisation factor
   int k;
+  int conv;
 };
 
-// LOBPCG for the smallest eigenpair of (A_H, M_H); x holds the start vector (not normalised).
-// Returns iterations used, or -1 when the tolerance was not reached.  On return x is the
-// M-normalised eigenvector with a positive sum and lam its Rayleigh quotient.
-__device__ int lobpcg(CoarseWS& ws, int n, double tol, int maxit, int nu, double omega, double* red,
-                      EigShared* sh, double& lam) {
+// LOBPCG for the smallest eigenpair of (A_H, M_H), preconditioned by one FP32 V-cycle on A_H.
+// x holds the start vector.  Returns the iterations used, or -1 when the tolerance was not
+// reached.  On return x is the M-normalised eigenvector with a positive sum and lam its
+// Rayleigh quotient.
+__device__ int lobpcg(CoarseWS& ws, int n, double tol, int maxit, int nu, float omega, double* red, EigShared* sh,
+                      double& lam) {
   const int ld = n + 1;
   const double hm = 1.0 / (12.0 * n * n);
-  const MGDesc<double>& mg = ws.mg;
-  const double* wx = mg.wx[0];
-  const double* wy = mg.wy[0];
+  const double* __restrict__ wx = ws.wx;
+  const double* __restrict__ wy = ws.wy;
   auto applyAM = [&](const double* u, double* Au, double* Mu, double& uAu, double& uMu) {
     double acc[2] = {0.0, 0.0}, o[2];
     for_interior(n, [&](int p, int, int) {
-      double dg;
-      const double au = stiff(wx, wy, u, p, ld, dg);
+      const double au = stiff<double, double>(wx, wy, u, p, ld);
       const double mu = hm * mass7(u, p, ld);
       Au[p] = au;
       Mu[p] = mu;
       acc[0] += u[p] * au;
       acc[1] += u[p] * mu;
     });
-    block_sum<2, double>(acc, o, red);
+    block_sum<2, double>(acc, o, red, [&](const double* t) { sh->scale = (double)rsqrtf((float)t[1]); sh->theta = t[0] / t[1]; });
     uAu = o[0];
     uMu = o[1];
   };
   double xAx, xMx;
   applyAM(ws.x, ws.Ax, ws.Mx, xAx, xMx);
   {
-    const double s = 1.0 / sqrt(xMx);
+    const double s = sh->scale;
     for_interior(n, [&](int p, int, int) {
       ws.x[p] *= s;
       ws.Ax[p] *= s;
@@ -502,7 +536,7 @@ __device__ int lobpcg(CoarseWS& ws, int n, double tol, int maxit, int nu, double
     });
     __syncthreads();
   }
-  double theta = xAx / xMx;
+  double theta = sh->theta;
   bool have_p = false;
   int it = 0, conv = 0;
   for (; it < maxit; ++it) {
@@ -510,24 +544,25 @@ __device__ int lobpcg(CoarseWS& ws, int n, double tol, int maxit, int nu, double
       double acc[2] = {0.0, 0.0}, o[2];
       for_interior(n, [&](int p, int, int) {
         const double rv = ws.Ax[p] - theta * ws.Mx[p];
-        ws.r[p] = rv;
+        ws.r32[p] = (float)rv;
         acc[0] += rv * rv;
         acc[1] += ws.Mx[p] * ws.Mx[p];
       });
-      block_sum<2, double>(acc, o, red);
-      if (sqrt(o[0]) <= tol * fabs(theta) * sqrt(o[1])) {
+      block_sum<2, double>(acc, o, red, [&](const double* t) { sh->conv = t[0] <= tol * tol * theta * theta * t[1]; });
+      if (sh->conv) {
         conv = 1;
         break;
       }
     }
-    vcycle<double>(mg, ws.r, ws.w, nu, omega);
+    vcycle<float>(ws.mg, ws.r32, ws.w32, nu, omega);
+    for_interior(n, [&](int p, int, int) { ws.w[p] = (double)ws.w32[p]; });
+    __syncthreads();
     double g[12];
     {
       double acc[12];
       for (int i = 0; i < 12; ++i) acc[i] = 0.0;
       for_interior(n, [&](int p, int, int) {
-        double dg;
-        const double aw = stiff(wx, wy, ws.w, p, ld, dg);
+        const double aw = stiff<double, double>(wx, wy, ws.w, p, ld);
         const double mw = hm * mass7(ws.w, p, ld);
         ws.Aw[p] = aw;
         ws.Mw[p] = mw;
@@ -548,43 +583,62 @@ __device__ int lobpcg(CoarseWS& ws, int n, double tol, int maxit, int nu, double
           acc[11] += pv * ws.Mp[p];
         }
       });
-      block_sum<12, double>(acc, g, red);
-    }
-    if (threadIdx.x == 0) {
-      double GA[3][3], GM[3][3];
-      GA[0][0] = g[4];
-      GM[0][0] = g[5];
-      GA[1][1] = g[0];
-      GM[1][1] = g[1];
-      GA[0][1] = GA[1][0] = g[2];
-      GM[0][1] = GM[1][0] = g[3];
-      GA[2][2] = g[10];
-      GM[2][2] = g[11];
-      GA[1][2] = GA[2][1] = g[6];
-      GM[1][2] = GM[2][1] = g[7];
-      GA[0][2] = GA[2][0] = g[8];
-      GM[0][2] = GM[2][0] = g[9];
-      double c[3], th;
-      const int k = rayleigh_ritz(GA, GM, have_p ? 3 : 2, c, th);
-      if (k > 0) {
-        if (c[0] < 0) {
-          c[0] = -c[0];
-          c[1] = -c[1];
-          c[2] = -c[2];
+      const bool hp = have_p;
+      block_sum<12, double>(acc, g, red, [&](const double* gg) {
+        // Gram matrices of the basis [x, w, p]
+        double GA[3][3], GM[3][3];
+        GA[0][0] = gg[4];
+        GM[0][0] = gg[5];
+        GA[1][1] = gg[0];
+        GM[1][1] = gg[1];
+        GA[0][1] = GA[1][0] = gg[2];
+        GM[0][1] = GM[1][0] = gg[3];
+        GA[2][2] = gg[10];
+        GM[2][2] = gg[11];
+        GA[1][2] = GA[2][1] = gg[6];
+        GM[1][2] = GM[2][1] = gg[7];
+        GA[0][2] = GA[2][0] = gg[8];
+        GM[0][2] = GM[2][0] = gg[9];
+        const int kk = hp ? 3 : 2;
+        const double th0 = GA[0][0] / GM[0][0];  // Rayleigh quotient of the current x
+        float As[3][3], Mf[3][3];
+        for (int i = 0; i < kk; ++i)
+          for (int j = 0; j < kk; ++j) {
+            As[i][j] = (float)(GA[i][j] - th0 * GM[i][j]);
+            Mf[i][j] = (float)GM[i][j];
+          }
+        float cf[3], mu;
+        const int k = rayleigh_ritz_shifted(As, Mf, kk, cf, mu);
+        if (k > 0) {
+          if (cf[0] < 0) {
+            cf[0] = -cf[0];
+            cf[1] = -cf[1];
+            cf[2] = -cf[2];
+          }
+          // Rayleigh quotient of the new iterate from the FP64 Gram matrices; approximate
+          // normalisations (the Gram matrices are recomputed every iteration)
+          const double c0 = cf[0], c1 = cf[1], c2 = k > 2 ? cf[2] : 0.0;
+          double ca = 0.0, cm = 0.0;
+          const double cv[3] = {c0, c1, c2};
+          for (int i = 0; i < k; ++i)
+            for (int j = 0; j < k; ++j) {
+              ca += cv[i] * GA[i][j] * cv[j];
+              cm += cv[i] * GM[i][j] * cv[j];
+            }
+          const float xs = rsqrtf((float)cm);
+          const float pp = cf[1] * cf[1] * Mf[1][1] + 2 * cf[1] * (k > 2 ? cf[2] : 0.0f) * Mf[1][2] +
+                           (k > 2 ? cf[2] * cf[2] * Mf[2][2] : 0.0f);
+          const float ps = pp > 0 ? rsqrtf(pp) : 0.0f;
+          sh->pc[0] = cf[1] * ps;
+          sh->pc[1] = (k > 2 ? cf[2] : 0.0f) * ps;
+          sh->c[0] = c0 * xs;
+          sh->c[1] = c1 * xs;
+          sh->c[2] = c2 * xs;
+          sh->theta = ca / cm;
         }
-        // p_new = c1 w + c2 p, M-normalised
-        const double pp = c[1] * c[1] * GM[1][1] + 2 * c[1] * c[2] * GM[1][2] + c[2] * c[2] * GM[2][2];
-        const double ps = pp > 0 ? 1.0 / sqrt(pp) : 0.0;
-        sh->pc[0] = c[1] * ps;
-        sh->pc[1] = (k > 2 ? c[2] : 0.0) * ps;
-        sh->c[0] = c[0];
-        sh->c[1] = c[1];
-        sh->c[2] = k > 2 ? c[2] : 0.0;
-        sh->theta = th;
-      }
-      sh->k = k;
+        sh->k = k;
+      });
     }
-    __syncthreads();
     const int k = sh->k;
     if (k == 0) break;
     const double c0 = sh->c[0], c1 = sh->c[1], c2 = sh->c[2], q0 = sh->pc[0], q1 = sh->pc[1];
@@ -609,13 +663,30 @@ __device__ int lobpcg(CoarseWS& ws, int n, double tol, int maxit, int nu, double
   applyAM(ws.x, ws.Ax, ws.Mx, xA, xM);
   double sacc[1] = {0.0}, so[1];
   for_interior(n, [&](int p, int, int) { sacc[0] += ws.x[p]; });
-  block_sum<1, double>(sacc, so, red);
-  const double sc = (so[0] < 0 ? -1.0 : 1.0) / sqrt(xM);
+  block_sum<1, double>(sacc, so, red, [&](const double* t) {
+    sh->scale = (t[0] < 0 ? -1.0 : 1.0) / sqrt(xM);
+    sh->theta = xA / xM;
+  });
+  const double sc = sh->scale;
   for_interior(n, [&](int p, int, int) { ws.x[p] *= sc; });
   __syncthreads();
-  lam = xA / xM;
+  lam = sh->theta;
   return conv ? it : -1;
 }
+
+// MINRES scalars, owned by thread 0 and read by all threads after each reduction.  The
+// recurrences run in the inner precision T (FP32 on the mixed path), the refinement norms in FP64.
+template <typename T>
+struct MinresShared {
+  T gam, gam_old, eta, eta0, c, c_old, s, s_old;
+  T ig;           // 1 / gamma_j
+  T c1, c2;       // v_new = q - c1 v - c2 v_old
+  T cx, ia1, a2, a3;  // pending w / x update
+  T delta;
+  T rs;           // 1 / ||r|| of the refinement residual
+  double rnorm, bnorm;
+  int done, breakdown;
+};
 
 // ---------------------------------------------------------------------------------------------
 // two-grid update on the fine mesh n: returns the Rayleigh quotient of the solution of
@@ -624,7 +695,7 @@ __device__ int lobpcg(CoarseWS& ws, int n, double tol, int maxit, int nu, double
 template <typename T>
 __device__ double twogrid_fine(FineWS<T>& ws, char* fine_base, int n, const double* __restrict__ a,
                                const double* uH, int nc, double sigma, const SampleLaunch& P, double* red,
-                               int& iters, int& outer, int& flags) {
+                               MinresShared<T>* ms, int& iters, int& outer, int& flags) {
   const int ld = n + 1;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -633,9 +704,7 @@ __device__ double twogrid_fine(FineWS<T>& ws, char* fine_base, int n, const doub
   }
   __syncthreads();
   const double hm = 1.0 / (12.0 * n * n);
-  // zero every vector of the region (boundary rings must be zero)
   zero_vec(ws.x64, n);
-  zero_vec(ws.r64, n);
   zero_vec(ws.b64, n);
   zero_vec(ws.vo, n);
   zero_vec(ws.v, n);
@@ -645,23 +714,18 @@ __device__ double twogrid_fine(FineWS<T>& ws, char* fine_base, int n, const doub
   zero_vec(ws.w, n);
   zero_vec(ws.q, n);
   zero_vec(ws.xi, n);
-  for (int l = 0; l < ws.mg.L; ++l) {
-    zero_vec(ws.mg.t[l], ws.mg.n[l]);
-    if (l) {
-      zero_vec(ws.mg.x[l], ws.mg.n[l]);
-      zero_vec(ws.mg.b[l], ws.mg.n[l]);
-    }
-  }
+  zero_mg(ws.mg);
   __syncthreads();
-  const bool ok = build_mg<T>(ws.mg, a, n, red);
-  if (!ok) flags |= kFlagBadCoef;
-  if (sizeof(T) != sizeof(double)) {
-    weights_from_cells<double, double>(n, a, a + (size_t)n * n, ws.wx64, ws.wy64);
-    __syncthreads();
-  }
-  const double* wx = ws.wx64;
-  const double* wy = ws.wy64;
-  // b = M P u_H  (P: P1 interpolation from the nested coarse mesh)
+  if (!build_mg<T>(ws.mg, a, n, red)) flags |= kFlagBadCoef;
+  // FP64 operator for the residual and the Rayleigh quotient: the FP64 weights of level 0 when the
+  // inner precision is FP64, otherwise weights formed on the fly from the centroid coefficients
+  const bool w64 = sizeof(T) == sizeof(double);
+  const double* wx64 = (const double*)ws.mg.wx[0];
+  const double* wy64 = (const double*)ws.mg.wy[0];
+  auto K64 = [&](const double* x, int p, int i, int j) {
+    return w64 ? stiff<double, double>(wx64, wy64, x, p, ld) : stiff_cells(a, n, x, p, ld, i, j);
+  };
+  // b = M P u_H  (P: P1 interpolation from the nested coarse mesh); x64 holds P u_H for a moment
   {
     const int lr = ilog2(n / nc);
     const int rm = (1 << lr) - 1;
@@ -676,184 +740,196 @@ __device__ double twogrid_fine(FineWS<T>& ws, char* fine_base, int n, const doub
         v = (1.0 - xi_) * uH[c0] + (xi_ - et) * uH[c0 + 1] + et * uH[c0 + ldc + 1];
       else
         v = (1.0 - et) * uH[c0] + (et - xi_) * uH[c0 + ldc] + xi_ * uH[c0 + ldc + 1];
-      ws.r64[p] = v;
+      ws.x64[p] = v;
     });
     __syncthreads();
     double acc[1] = {0.0}, o[1];
     for_interior(n, [&](int p, int, int) {
-      const double bv = hm * mass7(ws.r64, p, ld);
+      const double bv = hm * mass7(ws.x64, p, ld);
       ws.b64[p] = bv;
+      ws.v[p] = T(bv);
       acc[0] += bv * bv;
     });
-    block_sum<1, double>(acc, o, red);
-    for_interior(n, [&](int p, int, int) { ws.r64[p] = ws.b64[p]; });
+    block_sum<1, double>(acc, o, red, [&](const double* t) {
+      ms->bnorm = ms->rnorm = sqrt(t[0]);
+      ms->rs = T(1.0 / ms->rnorm);
+    });
+    for_interior(n, [&](int p, int, int) { ws.x64[p] = 0.0; });
     __syncthreads();
-    outer = 0;
-    iters = 0;
-    double bnorm = sqrt(o[0]);
-    double rnorm = bnorm;
-    const T sigm = T(sigma * hm);
-    const T om = T(P.omega);
-    const T* twx = ws.mg.wx[0];
-    const T* twy = ws.mg.wy[0];
-    for (; outer < P.max_outer; ++outer) {
-      if (!(rnorm > P.tol_lin * bnorm)) break;
-      // inner: MINRES on (A - sigma M) xi = r / ||r|| in precision T, preconditioned by the V-cycle
-      const double rs = 1.0 / rnorm;
-      for_interior(n, [&](int p, int, int) {
-        ws.v[p] = T(ws.r64[p] * rs);
-        ws.vo[p] = T(0);
-        ws.w[p] = T(0);
-        ws.wo[p] = T(0);
-        ws.xi[p] = T(0);
+  }
+  outer = 0;
+  iters = 0;
+  const T sigm = T(sigma * hm);
+  const T om = T(P.omega);
+  const T* twx = ws.mg.wx[0];
+  const T* twy = ws.mg.wy[0];
+  for (; outer < P.max_outer; ++outer) {
+    if (!(ms->rnorm > P.tol_lin * ms->bnorm)) break;
+    // inner: MINRES on (A - sigma M) xi = r / ||r|| in precision T, preconditioned by the V-cycle;
+    // v holds r (unscaled)
+    const T rs = ms->rs;
+    for_interior(n, [&](int p, int, int) {
+      ws.v[p] *= rs;
+      ws.vo[p] = T(0);
+      ws.w[p] = T(0);
+      ws.wo[p] = T(0);
+      ws.xi[p] = T(0);
+    });
+    __syncthreads();
+    T* vo = ws.vo;
+    T* v = ws.v;
+    T* z = ws.z;
+    T* zn = ws.zn;
+    T* wo = ws.wo;
+    T* w = ws.w;
+    vcycle<T>(ws.mg, v, z, P.nu, om);
+    {
+      T acc1[1] = {T(0)};
+      double o1[1];
+      for_interior(n, [&](int p, int, int) { acc1[0] += v[p] * z[p]; });
+      block_sum<1, T>(acc1, o1, red, [&](const double* t) {
+        const T t0 = T(t[0]);
+        ms->breakdown = !(t0 > T(0));
+        const T g = ms->breakdown ? T(1) : sqrt(t0);
+        ms->gam = g;
+        ms->eta = ms->eta0 = g;
+        ms->gam_old = T(1);
+        ms->c = ms->c_old = T(1);
+        ms->s = ms->s_old = T(0);
+        ms->ig = T(1) / g;
+        ms->done = ms->breakdown;
       });
-      __syncthreads();
-      T* vo = ws.vo;
-      T* v = ws.v;
-      T* z = ws.z;
-      T* zn = ws.zn;
-      T* wo = ws.wo;
-      T* w = ws.w;
-      vcycle<T>(ws.mg, v, z, P.nu, om);
-      double gam;
+    }
+    if (ms->breakdown) {
+      flags |= kFlagBreakdown;
+      break;
+    }
+    int j = 0;
+    bool pending = false;
+    for (; j < P.max_inner_it && !ms->done; ++j) {
+      // [pending w/x update of the previous iteration] + q = K z / gamma, delta
       {
         T acc1[1] = {T(0)};
         double o1[1];
-        for_interior(n, [&](int p, int, int) { acc1[0] += v[p] * z[p]; });
-        block_sum<1, T>(acc1, o1, red);
-        gam = o1[0];
-      }
-      if (!(gam > 0.0)) {
-        flags |= kFlagBreakdown;
-        break;
-      }
-      gam = sqrt(gam);
-      double eta = gam, eta0 = gam, gam_old = 1.0;
-      double s_old = 0.0, s = 0.0, c_old = 1.0, c = 1.0;
-      int j = 0;
-      bool done = false;
-      double cx = 0.0, a1 = 1.0, a2 = 0.0, a3 = 0.0;  // pending w/x update
-      bool pending = false;
-      for (; j < P.max_inner_it && !done; ++j) {
-        // [pending update of w, x from the previous iteration] + q = K z / gam, delta
-        const T ig = T(1.0 / gam);
-        double delta;
-        {
-          T acc1[1] = {T(0)};
-          double o1[1];
-          const T ta1 = T(1.0 / a1), ta2 = T(a2), ta3 = T(a3), tcx = T(cx);
-          T* zp = zn;  // z of the previous iteration (normalised) is in zn when pending
-          for_interior(n, [&](int p, int, int) {
-            if (pending) {
-              const T wnew = (zp[p] - ta3 * wo[p] - ta2 * w[p]) * ta1;
-              wo[p] = wnew;  // becomes w after the pointer swap below
-              ws.xi[p] += tcx * wnew;
-            }
-            T dg;
-            const T kz = (stiff(twx, twy, z, p, ld, dg) - sigm * mass7(z, p, ld)) * ig;
-            ws.q[p] = kz;
-            acc1[0] += kz * z[p];
-          });
-          block_sum<1, T>(acc1, o1, red);
-          delta = o1[0] / gam;
-          if (pending) {
-            T* tt = wo;
-            wo = w;
-            w = tt;
-          }
-          pending = false;
-        }
-        // v_new = q - (delta/gam) v - (gam/gam_old) v_old ; z normalised in place
-        {
-          const T c1 = T(delta / gam), c2 = T(gam / gam_old);
-          for_interior(n, [&](int p, int, int) {
-            vo[p] = ws.q[p] - c1 * v[p] - c2 * vo[p];
-            z[p] *= ig;
-          });
-          __syncthreads();
-          T* tt = vo;
-          vo = v;
-          v = tt;  // v = v_new, vo = v_j
-        }
-        // zn = B^{-1} v_new, gamma_new
-        vcycle<T>(ws.mg, v, zn, P.nu, om);
-        double gnew;
-        {
-          T acc1[1] = {T(0)};
-          double o1[1];
-          for_interior(n, [&](int p, int, int) { acc1[0] += v[p] * zn[p]; });
-          block_sum<1, T>(acc1, o1, red);
-          gnew = o1[0];
-        }
-        if (!(gnew >= 0.0)) {
-          flags |= kFlagBreakdown;
-          gnew = 0.0;
-        }
-        gnew = sqrt(gnew);
-        const double al0 = c * delta - c_old * s * gam;
-        const double al1 = sqrt(al0 * al0 + gnew * gnew);
-        const double al2 = s * delta + c_old * c * gam;
-        const double al3 = s_old * gam;
-        const double cn = al0 / al1, sn = gnew / al1;
-        // w_new = (z_j - al3 w_old - al2 w)/al1 ; x += cn eta w_new   (applied lazily)
-        // z_j is the normalised z (in buffer z); move it to zn's slot after swapping
-        {
-          T* tt = z;
-          z = zn;
-          zn = tt;  // z = z_{j+1} (unnormalised), zn = z_j (normalised)
-        }
-        cx = cn * eta;
-        a1 = al1;
-        a2 = al2;
-        a3 = al3;
-        pending = true;
-        eta = -sn * eta;
-        s_old = s;
-        s = sn;
-        c_old = c;
-        c = cn;
-        gam_old = gam;
-        gam = gnew;
-        if (fabs(eta) <= P.tol_inner * eta0 || gnew == 0.0) done = true;
-      }
-      if (pending) {
-        const T ta1 = T(1.0 / a1), ta2 = T(a2), ta3 = T(a3), tcx = T(cx);
+        const T ig = ms->ig;
+        const T ta1 = ms->ia1, ta2 = ms->a2, ta3 = ms->a3, tcx = ms->cx;
+        const bool pend = pending;
+        const T* zp = zn;
         for_interior(n, [&](int p, int, int) {
-          const T wnew = (zn[p] - ta3 * wo[p] - ta2 * w[p]) * ta1;
-          ws.xi[p] += tcx * wnew;
+          if (pend) {
+            const T wnew = (zp[p] - ta3 * wo[p] - ta2 * w[p]) * ta1;
+            wo[p] = wnew;
+            ws.xi[p] += tcx * wnew;
+          }
+          const T kz = (stiff<T, T>(twx, twy, z, p, ld) - sigm * mass7(z, p, ld)) * ig;
+          ws.q[p] = kz;
+          acc1[0] += kz * z[p];
+        });
+        block_sum<1, T>(acc1, o1, red, [&](const double* t) {
+          const T delta = T(t[0]) * ms->ig;
+          ms->c1 = delta * ms->ig;
+          ms->c2 = ms->gam / ms->gam_old;
+          ms->delta = delta;
+        });
+        if (pend) {
+          T* tt = wo;
+          wo = w;
+          w = tt;
+        }
+      }
+      // v_new = q - (delta/gam) v - (gam/gam_old) v_old ; z normalised in place
+      {
+        const T c1 = ms->c1, c2 = ms->c2, ig = ms->ig;
+        for_interior(n, [&](int p, int, int) {
+          vo[p] = ws.q[p] - c1 * v[p] - c2 * vo[p];
+          z[p] *= ig;
         });
         __syncthreads();
+        T* tt = vo;
+        vo = v;
+        v = tt;
       }
-      iters += j;
-      if (!done) flags |= kFlagLinNoConv;
-      // x64 += ||r|| xi ; r64 = b - (A - sigma M) x64 in FP64
-      for_interior(n, [&](int p, int, int) { ws.x64[p] += rnorm * (double)ws.xi[p]; });
-      __syncthreads();
-      double acc2[1] = {0.0}, o2[1];
-      for_interior(n, [&](int p, int, int) {
-        double dg;
-        const double kx = stiff(wx, wy, ws.x64, p, ld, dg) - sigma * hm * mass7(ws.x64, p, ld);
-        const double rv = ws.b64[p] - kx;
-        ws.r64[p] = rv;
-        acc2[0] += rv * rv;
-      });
-      block_sum<1, double>(acc2, o2, red);
-      const double rnew = sqrt(o2[0]);
-      const bool stalled = !(rnew < 0.5 * rnorm);
-      rnorm = rnew;
-      if (stalled) {
-        ++outer;
-        break;
+      vcycle<T>(ws.mg, v, zn, P.nu, om);
+      {
+        T acc1[1] = {T(0)};
+        double o1[1];
+        for_interior(n, [&](int p, int, int) { acc1[0] += v[p] * zn[p]; });
+        const T tol = T(P.tol_inner);
+        block_sum<1, T>(acc1, o1, red, [&](const double* t) {
+          T gnew = T(t[0]);
+          if (!(gnew >= T(0))) {
+            ms->breakdown = 1;
+            gnew = T(0);
+          }
+          gnew = sqrt(gnew);
+          const T delta = ms->delta, gam = ms->gam;
+          const T al0 = ms->c * delta - ms->c_old * ms->s * gam;
+          const T al1 = sqrt(al0 * al0 + gnew * gnew);
+          const T al2 = ms->s * delta + ms->c_old * ms->c * gam;
+          const T al3 = ms->s_old * gam;
+          const T ia1 = T(1) / al1;
+          const T cn = al0 * ia1, sn = gnew * ia1;
+          ms->cx = cn * ms->eta;
+          ms->ia1 = ia1;
+          ms->a2 = al2;
+          ms->a3 = al3;
+          ms->eta = -sn * ms->eta;
+          ms->s_old = ms->s;
+          ms->s = sn;
+          ms->c_old = ms->c;
+          ms->c = cn;
+          ms->gam_old = gam;
+          ms->gam = gnew;
+          ms->ig = gnew > T(0) ? T(1) / gnew : T(0);
+          ms->done = fabs(ms->eta) <= tol * ms->eta0 || gnew == T(0) || ms->breakdown;
+        });
+        T* tt = z;
+        z = zn;
+        zn = tt;  // z = z_{j+1} (unnormalised), zn = z_j (normalised)
+        pending = true;
       }
     }
-    if (!(rnorm <= P.tol_lin * bnorm) && !(rnorm < 1e-6 * bnorm)) flags |= kFlagLinNoConv;
+    if (pending) {
+      const T ta1 = ms->ia1, ta2 = ms->a2, ta3 = ms->a3, tcx = ms->cx;
+      for_interior(n, [&](int p, int, int) {
+        const T wnew = (zn[p] - ta3 * wo[p] - ta2 * w[p]) * ta1;
+        ws.xi[p] += tcx * wnew;
+      });
+      __syncthreads();
+    }
+    iters += j;
+    if (ms->breakdown) flags |= kFlagBreakdown;
+    if (!ms->done) flags |= kFlagLinNoConv;
+    // x64 += ||r|| xi ; r = b - (A - sigma M) x64 in FP64, stored (unscaled) in v
+    const double rn = ms->rnorm;
+    for_interior(n, [&](int p, int, int) { ws.x64[p] += rn * (double)ws.xi[p]; });
+    __syncthreads();
+    double acc2[1] = {0.0}, o2[1];
+    for_interior(n, [&](int p, int i, int j) {
+      const double kx = K64(ws.x64, p, i, j) - sigma * hm * mass7(ws.x64, p, ld);
+      const double rv = ws.b64[p] - kx;
+      ws.v[p] = T(rv);
+      acc2[0] += rv * rv;
+    });
+    int stalled = 0;
+    block_sum<1, double>(acc2, o2, red, [&](const double* t) {
+      const double rnew = sqrt(t[0]);
+      ms->done = !(rnew < 0.5 * ms->rnorm);  // no progress: stop refining
+      ms->rnorm = rnew;
+      ms->rs = T(1.0 / rnew);
+    });
+    stalled = ms->done;
+    if (stalled) {
+      ++outer;
+      break;
+    }
   }
+  if (!(ms->rnorm <= P.tol_lin * ms->bnorm) && !(ms->rnorm < 1e-6 * ms->bnorm)) flags |= kFlagLinNoConv;
   // Rayleigh quotient in FP64
   double acc[2] = {0.0, 0.0}, o[2];
-  for_interior(n, [&](int p, int, int) {
-    double dg;
+  for_interior(n, [&](int p, int i, int j) {
     const double x = ws.x64[p];
-    acc[0] += x * stiff(wx, wy, ws.x64, p, ld, dg);
+    acc[0] += x * K64(ws.x64, p, i, j);
     acc[1] += x * hm * mass7(ws.x64, p, ld);
   });
   block_sum<2, double>(acc, o, red);
@@ -862,17 +938,20 @@ __device__ double twogrid_fine(FineWS<T>& ws, char* fine_base, int n, const doub
 
 template <typename T>
 __global__ void __launch_bounds__(512) sample_kernel(SampleLaunch P) {
-  extern __shared__ __align__(256) char smem_dyn[];
+  extern __shared__ __align__(16) char smem_dyn[];
   __shared__ double red[32 * 12 + 12];
   __shared__ EigShared esh;
+  __shared__ MinresShared<T> msh;
   __shared__ CoarseWS cws;
   __shared__ FineWS<T> fws;
   char* base = P.use_smem ? smem_dyn : P.gscratch + (size_t)blockIdx.x * P.slab_bytes;
   size_t coarse_bytes;
   {
     Carver c(base);
-    carve_coarse(c, P.nc, cws);  // every thread writes the same values
-    coarse_bytes = (c.used() + 255) & ~(size_t)255;
+    CoarseWS tmp;
+    carve_coarse(c, P.nc, tmp);
+    coarse_bytes = (c.used() + 15) & ~(size_t)15;
+    if (threadIdx.x == 0) cws = tmp;
   }
   char* fine_base = base + coarse_bytes;
   __syncthreads();
@@ -883,17 +962,14 @@ __global__ void __launch_bounds__(512) sample_kernel(SampleLaunch P) {
   // coarse vectors: zero once (rings stay zero; interiors are always written before use)
   {
     CoarseWS& w = cws;
-    double* vs[11] = {w.x, w.Ax, w.Mx, w.w, w.Aw, w.Mw, w.p, w.Ap, w.Mp, w.r, w.uprev};
-    for (int i = 0; i < 11; ++i) zero_vec(vs[i], nc);
-    for (int l = 0; l < w.mg.L; ++l) {
-      zero_vec(w.mg.t[l], w.mg.n[l]);
-      if (l) {
-        zero_vec(w.mg.x[l], w.mg.n[l]);
-        zero_vec(w.mg.b[l], w.mg.n[l]);
-      }
-    }
+    double* vs[12] = {w.wx, w.wy, w.x, w.Ax, w.Mx, w.w, w.Aw, w.Mw, w.p, w.Ap, w.Mp, w.uprev};
+    for (int i = 0; i < 12; ++i) zero_vec(vs[i], nc);
+    zero_vec(w.r32, nc);
+    zero_vec(w.w32, nc);
+    zero_mg(w.mg);
     __syncthreads();
   }
+  const float omega = (float)P.omega;
   for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     const int r = ch / cpr;
     const int k0 = (ch % cpr) * P.chunk;
@@ -903,28 +979,35 @@ __global__ void __launch_bounds__(512) sample_kernel(SampleLaunch P) {
       int flags = 0;
       // ---- coarse eigenpair (Algorithm 1 step 1; Algorithm 2 steps 6-7)
       CoarseWS& cw = cws;
-      if (!build_mg<double>(cw.mg, P.a_c + b * ncT, nc, red)) flags |= kFlagBadCoef;
+      const double* ac = P.a_c + b * ncT;
+      if (!build_mg<float>(cw.mg, ac, nc, red)) flags |= kFlagBadCoef;
+      weights_from_cells<double, double>(nc, ac, ac + (size_t)nc * nc, cw.wx, cw.wy);
       if (kk == k0) {
-        for_interior(nc, [&](int p, int i, int j) { cw.x[p] = sinpi((double)i / nc) * sinpi((double)j / nc); });
+        const float inc = 1.0f / (float)nc;
+        for_interior(nc, [&](int p, int i, int j) { cw.x[p] = (double)(sinpif(i * inc) * sinpif(j * inc)); });
       } else {
         for_interior(nc, [&](int p, int, int) { cw.x[p] = cw.uprev[p]; });
       }
       __syncthreads();
       double lamH;
-      const int eit = lobpcg(cw, nc, P.tol_eig, P.max_eig_it, P.nu, P.omega, red, &esh, lamH);
+      const int eit = lobpcg(cw, nc, P.tol_eig, P.max_eig_it, P.nu, omega, red, &esh, lamH);
       if (eit < 0) flags |= kFlagEigNoConv;
       for_interior(nc, [&](int p, int, int) { cw.uprev[p] = cw.x[p]; });
       if (P.u_out) {
-        for_interior(nc, [&](int p, int i, int j) { P.u_out[b * (size_t)(nc - 1) * (nc - 1) + (j - 1) * (nc - 1) + (i - 1)] = cw.x[p]; });
+        for_interior(nc, [&](int p, int i, int j) {
+          P.u_out[b * (size_t)(nc - 1) * (nc - 1) + (j - 1) * (nc - 1) + (i - 1)] = cw.x[p];
+        });
       }
       __syncthreads();
       // ---- fine two-grid updates (Algorithm 1 steps 2-4; Algorithm 2 steps 9-14)
       double lf = lamH, lp = 0.0;
       int itf = 0, itp = 0, of = 0, op = 0;
-      if (!P.direct_f) lf = twogrid_fine<T>(fws, fine_base, P.nf, P.a_f + b * nfT, cw.x, nc, lamH, P, red, itf, of, flags);
+      if (!P.direct_f)
+        lf = twogrid_fine<T>(fws, fine_base, P.nf, P.a_f + b * nfT, cw.x, nc, lamH, P, red, &msh, itf, of, flags);
       if (P.np > 0) {
         lp = lamH;
-        if (!P.direct_p) lp = twogrid_fine<T>(fws, fine_base, P.np, P.a_p + b * npT, cw.x, nc, lamH, P, red, itp, op, flags);
+        if (!P.direct_p)
+          lp = twogrid_fine<T>(fws, fine_base, P.np, P.a_p + b * npT, cw.x, nc, lamH, P, red, &msh, itp, op, flags);
       }
       if (threadIdx.x == 0) {
         P.out[b * 4 + 0] = lamH;
@@ -962,8 +1045,7 @@ __global__ void apply_kernel(int n, const double* __restrict__ a, int which, dou
   const int ld = n + 1;
   const double hm = 1.0 / (12.0 * n * n);
   for_interior(n, [&](int p, int i, int j) {
-    double dg;
-    const double ax = stiff(wx, wy, xp, p, ld, dg);
+    const double ax = stiff<double, double>(wx, wy, xp, p, ld);
     const double mx = hm * mass7(xp, p, ld);
     y[b * nI + (size_t)(j - 1) * (n - 1) + (i - 1)] = which == 0 ? ax : which == 1 ? mx : ax - sigma * mx;
   });
