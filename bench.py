@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--no-baseline", action="store_true", help="skip the timed CPU oracle sample")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison run")
-    ap.add_argument("--baseline-seconds", type=float, default=15.0)
+    ap.add_argument("--baseline-seconds", type=float, default=20.0)
     return ap.parse_args()
 
 
@@ -128,21 +128,21 @@ def time_device(binding, torch, wl, prec, steps, warmup, stream, seed_offset=0):
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    ctx.mq_reset_sums()  # also clears the per-level device timers
     ev0.record(stream)
     for _ in range(steps):
         run_device_step(ctx, wl, outs, sums)
     ev1.record(stream)
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
-    # per-level kernel times and iteration counts from one more (untimed) pass
-    per_level_ms = np.zeros(len(wl.levels))
+    # per-level device time of the timed region (CUDA events on the launching stream)
+    timing = [ctx.mq_get_level_timing(l) for l in range(len(wl.levels))]
+    # iteration counts from one more (untimed, identical) pass
     kstats = {}
     for l, lv in enumerate(wl.levels):
         ctx.mq_eval_level_device(l, 0, lv.N, outs[l], sums[l])
-        st = ctx.mq_get_stats()
-        per_level_ms[l] = st["kernel_ms"]
-        kstats[l] = [st]
-    return ctx, ms, per_level_ms * steps, kstats, outs
+        kstats[l] = [ctx.mq_get_stats()]
+    return ctx, ms, timing, kstats, outs
 
 
 def time_e2e(binding, wl, prec, steps, stream_ptr):
@@ -229,6 +229,67 @@ def _pool_init():
 
 
 # ------------------------------------------------------------------------------------------
+# Bytes the per-sample kernel moves per unknown if every array access of every sweep goes to
+# memory once (the design's algorithmic traffic; derivation in the design doc section 6):
+#   fine solve, per inner MINRES + V-cycle iteration: 55 words of the inner precision;
+#   per FP64 refinement step: 52 inner words + 48 bytes; per solve (setup, RHS, Rayleigh
+#   quotient, clearing): 18 inner words + 88 bytes;
+#   coarse LOBPCG, per iteration: 390 bytes per coarse unknown.
+def sample_kernel_bytes(wl, level, st, prec):
+    e = 4 if prec == "mixed" else 8
+    lv = wl.levels[level]
+    fine = []
+    if not (lv.n_fine == lv.n_coarse and lv.s == lv.S):
+        fine.append((lv.n_fine - 1) ** 2)
+    if level > 0:
+        pv = wl.levels[level - 1]
+        if not (pv.n_fine == lv.n_coarse and pv.s == lv.S):
+            fine.append((pv.n_fine - 1) ** 2)
+    I, O = st["fine_iters_mean"], st["outer_iters_mean"]
+    per_solve = lambda n: n * (55 * e * I + (52 * e + 48) * O + 18 * e + 88)
+    coarse = (lv.n_coarse - 1) ** 2 * 390 * st["coarse_iters_mean"]
+    return lv.N * lv.R * (sum(per_solve(n) for n in fine) + coarse)
+
+
+# ncu DRAM traffic of the per-sample kernel, valid only for the source it was measured on
+# (profiles/sample_kernel_mlqmc4_h16_128.md); scaled per sample from a smaller capture
+SAMPLE_KERNEL_TRAFFIC = {"source_sha256": "18dde7f9e22ceb93a4d3dd9acfbb27fb013fd4ba22a94cb5482b15c6b21ad8a4",
+                         "level": 3, "bytes_per_sample": 61.458284e9 / 1024}
+
+
+def _sample_source_hash():
+    import hashlib
+
+    path = os.path.join(ROOT, "paper_2103_03407_gb300", "csrc", "mq_sample.cu")
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+            if k in d:
+                return float(d[k]), "measured"
+    except Exception:
+        pass
+    return 6800.0, "fallback"
+
+
+def sample_kernel_roofline(wl, level, st, prec, ms_per_launch):
+    nbytes = sample_kernel_bytes(wl, level, st, prec)
+    achieved = nbytes / (ms_per_launch * 1e-3) / 1e9
+    peak, kind = hbm_peak()
+    lv = wl.levels[level]
+    traffic = None
+    t = SAMPLE_KERNEL_TRAFFIC
+    if t["source_sha256"] and t["source_sha256"] == _sample_source_hash() and t["level"] == level:
+        traffic = t["bytes_per_sample"] * lv.N * lv.R
+    return {"bound": "hbm", "kernel": f"sample_kernel (level {level}, {lv.N * lv.R} samples per launch)",
+            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+            "algorithmic_bytes": nbytes, "peak_kind": kind}
+
+
 def fp64_peak_tflops(clock_mhz=None):
     """Nominal FP64 rate of a GB300 (1.25 TFLOP/s at the boost clock), scaled to the sampled clock."""
     nominal = 1.25
@@ -261,8 +322,8 @@ def main():
     torch.cuda.synchronize()
     with torch.cuda.stream(stream):
         with sampler:
-            ctx, ms, per_level_ms, kstats, outs = time_device(binding, torch, wl, args.precision, args.steps,
-                                                              args.warmup, stream, seed_offset=rank)
+            ctx, ms, timing, kstats, outs = time_device(binding, torch, wl, args.precision, args.steps,
+                                                        args.warmup, stream, seed_offset=rank)
     if world > 1:
         t = torch.tensor([ms], dtype=torch.float64, device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -279,15 +340,13 @@ def main():
         dt, h2d, d2h = time_e2e(binding, wl, args.precision, max(1, args.steps), stream.cuda_stream)
         e2e = {"value": wl.samples * max(1, args.steps) / dt, "unit": "samples/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
-    # dominant kernel: the per-sample kernel of the finest level
+    # dominant kernel: the per-sample kernel of the level with the largest device time
     lst = [kstats[l][-1] for l in range(len(wl.levels))]
-    sample_ms = [s["sample_ms"] for s in lst]
-    coef_ms = [s["coef_ms"] for s in lst]
+    sample_ms = [timing[l][1] / max(1, timing[l][2]) for l in range(len(wl.levels))]  # per launch
+    coef_ms = [timing[l][0] / max(1, timing[l][2]) for l in range(len(wl.levels))]
     top = int(np.argmax(sample_ms))
     clocks = sampler.summary()
-    roofline = {"bound": "alu", "kernel": f"sample_kernel level {top}", "achieved": None,
-                "peak": fp64_peak_tflops(), "unit": "TFLOP/s", "frac": None, "traffic": None,
-                "note": "FP64 flop model pending"}
+    roofline = sample_kernel_roofline(wl, top, lst[top], args.precision, sample_ms[top])
     result = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -296,7 +355,7 @@ def main():
                    "precision": args.precision, "l2": "inputs larger than L2 (coefficient fields of the finest "
                    "level exceed 129 MB)", "parallelism": f"dp{world} (independent shifts per rank)"},
         "e2e": e2e, "gpu_launches": None, "roofline": roofline, "clocks": clocks,
-        "per_level": [{"level": l, "kernel_ms": float(per_level_ms[l] / args.steps), "coef_ms": coef_ms[l],
+        "per_level": [{"level": l, "kernel_ms": coef_ms[l] + sample_ms[l], "coef_ms": coef_ms[l],
                        "sample_ms": sample_ms[l], "coarse_iters_mean": lst[l]["coarse_iters_mean"],
                        "fine_iters_mean": lst[l]["fine_iters_mean"], "outer_iters_mean": lst[l]["outer_iters_mean"],
                        "blocks": lst[l]["blocks"], "threads": lst[l]["threads"], "smem": lst[l]["smem_bytes"],

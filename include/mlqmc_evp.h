@@ -132,8 +132,14 @@ mq_status mq_eval_level_device(mq_ctx* ctx, int32_t level, uint32_t k0, uint32_t
 mq_status mq_estimate(mq_ctx* ctx, double* mean, double* std_err, double* level_mean,
                       double* level_var);
 
-/* Clear the estimator sums (keeps levels, lattices and shifts). */
+/* Clear the estimator sums and the per-level timers (keeps levels, lattices and shifts). */
 mq_status mq_reset_sums(mq_ctx* ctx);
+
+/* Device time accumulated on level `level` since mq_set_levels or mq_reset_sums, measured with
+ * CUDA events on the context stream: coefficient evaluation (coef_ms), the per-sample kernel
+ * (sample_ms) and the number of per-sample kernel launches.  Any output may be NULL. */
+mq_status mq_get_level_timing(mq_ctx* ctx, int32_t level, double* coef_ms, double* sample_ms,
+                              uint64_t* launches);
 
 /* Single explicit parameter vector y[0..s_l-1] on level `level`: the coarse eigenvalue
  * lambda_{H_l,S_l}(y), lambda^l(y) and (l > 0) lambda^{l-1}(y) (Algorithm 1).  Any output may

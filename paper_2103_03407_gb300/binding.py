@@ -25,7 +25,8 @@ STATUS_NAMES = {0: "MQ_OK", 1: "MQ_EINVAL", 2: "MQ_ENOMEM", 3: "MQ_ECUDA", 4: "M
 # every symbol the header declares
 EXPORTS = [
     "mq_create", "mq_destroy", "mq_set_coefficient", "mq_set_levels", "mq_set_lattice", "mq_set_shifts",
-    "mq_set_precision", "mq_eval_level", "mq_eval_level_device", "mq_estimate", "mq_reset_sums", "mq_eval_point",
+    "mq_set_precision", "mq_eval_level", "mq_eval_level_device", "mq_estimate", "mq_reset_sums",
+    "mq_get_level_timing", "mq_eval_point",
     "mq_get_stats", "mq_last_error", "mq_cbc_lattice", "mq_lattice_points_device", "mq_coefficients_device",
     "mq_apply_operator_device", "mq_twogrid_samples_noalloc",
 ]
@@ -83,6 +84,7 @@ def load(path: str = LIB_PATH):
         "mq_eval_level_device": ([P, i32, u32, u32, P, P], C.c_int),
         "mq_estimate": ([P, dp, dp, dp, dp], C.c_int),
         "mq_reset_sums": ([P], C.c_int),
+        "mq_get_level_timing": ([P, i32, dp, dp, C.POINTER(C.c_uint64)], C.c_int),
         "mq_eval_point": ([P, i32, dp, dp, dp, dp, dp], C.c_int),
         "mq_get_stats": ([P, P, sz], C.c_int),
         "mq_last_error": ([P], C.c_char_p),
@@ -196,6 +198,12 @@ class Context:
 
     def mq_reset_sums(self):
         self._check(self.lib.mq_reset_sums(self.h))
+
+    def mq_get_level_timing(self, level):
+        """(coef_ms, sample_ms, launches) accumulated on a level since the last reset."""
+        a, b, n = C.c_double(), C.c_double(), C.c_uint64()
+        self._check(self.lib.mq_get_level_timing(self.h, int(level), C.byref(a), C.byref(b), C.byref(n)))
+        return a.value, b.value, n.value
 
     def mq_eval_point(self, level, y, want_u=False):
         y = np.ascontiguousarray(y, dtype=np.float64)

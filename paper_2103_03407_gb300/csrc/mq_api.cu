@@ -47,6 +47,8 @@ struct mq_ctx {
   std::vector<double*> d_delta;
   std::vector<std::vector<double>> sums;  // per level, per shift
   std::vector<uint64_t> npoints;          // per level: points evaluated
+  std::vector<double> lvl_coef_ms, lvl_sample_ms;  // per level: accumulated device time
+  std::vector<uint64_t> lvl_launches;              // per level: per-sample kernel launches
 
   int prec = MQ_PREC_FP64;
   double tol_lin = 1e-10;
@@ -291,7 +293,7 @@ mq_status collect_stats(mq_ctx* c, size_t B, int* any_flags) {
   return MQ_OK;
 }
 
-mq_status timing(mq_ctx* c) {
+mq_status timing(mq_ctx* c, int level) {
   float t0 = 0, t1 = 0;
   MQ_CUDA(c, cudaEventSynchronize(c->ev[2]));
   MQ_CUDA(c, cudaEventElapsedTime(&t0, c->ev[0], c->ev[1]));
@@ -299,6 +301,11 @@ mq_status timing(mq_ctx* c) {
   c->stats.coef_ms += t0;
   c->stats.sample_ms += t1;
   c->stats.kernel_ms += t0 + t1;
+  if (level >= 0 && level < (int)c->lvl_coef_ms.size()) {
+    c->lvl_coef_ms[level] += t0;
+    c->lvl_sample_ms[level] += t1;
+    c->lvl_launches[level] += 1;
+  }
   return MQ_OK;
 }
 
@@ -373,7 +380,7 @@ mq_status eval_level_impl(mq_ctx* c, int level, uint32_t k0, uint32_t k1, double
                                    cudaMemcpyDeviceToDevice, c->stream));
     }
     MQ_CUDA(c, cudaStreamSynchronize(c->stream));
-    if ((st = timing(c)) != MQ_OK) return st;
+    if ((st = timing(c, level)) != MQ_OK) return st;
     if (per_sample) {
       for (int r = 0; r < R; ++r)
         std::memcpy(per_sample + ((size_t)r * npts + p0) * 4, host_out.data() + (size_t)r * pn * 4,
@@ -521,6 +528,9 @@ mq_status mq_set_levels(mq_ctx* c, int32_t L_plus_1, const mq_level* levels) {
   c->sums.assign(L_plus_1, {});
   for (int l = 0; l < L_plus_1; ++l) c->sums[l].assign(levels[l].R, 0.0);
   c->npoints.assign(L_plus_1, 0);
+  c->lvl_coef_ms.assign(L_plus_1, 0.0);
+  c->lvl_sample_ms.assign(L_plus_1, 0.0);
+  c->lvl_launches.assign(L_plus_1, 0);
   return MQ_OK;
 }
 
@@ -581,6 +591,18 @@ mq_status mq_reset_sums(mq_ctx* c) {
   if (!c) return MQ_EINVAL;
   for (size_t l = 0; l < c->sums.size(); ++l) std::fill(c->sums[l].begin(), c->sums[l].end(), 0.0);
   std::fill(c->npoints.begin(), c->npoints.end(), 0);
+  std::fill(c->lvl_coef_ms.begin(), c->lvl_coef_ms.end(), 0.0);
+  std::fill(c->lvl_sample_ms.begin(), c->lvl_sample_ms.end(), 0.0);
+  std::fill(c->lvl_launches.begin(), c->lvl_launches.end(), 0);
+  return MQ_OK;
+}
+
+mq_status mq_get_level_timing(mq_ctx* c, int32_t level, double* coef_ms, double* sample_ms, uint64_t* launches) {
+  if (!c) return MQ_EINVAL;
+  if (level < 0 || level >= (int)c->lvl_coef_ms.size()) return fail(c, MQ_EINVAL, "level %d out of range", level);
+  if (coef_ms) *coef_ms = c->lvl_coef_ms[level];
+  if (sample_ms) *sample_ms = c->lvl_sample_ms[level];
+  if (launches) *launches = c->lvl_launches[level];
   return MQ_OK;
 }
 
@@ -631,7 +653,7 @@ mq_status mq_eval_point(mq_ctx* c, int32_t level, const double* y, double* lam_H
     MQ_CUDA(c, cudaMemcpyAsync(u_H, c->uout.p, (size_t)(g.nc - 1) * (g.nc - 1) * sizeof(double),
                                cudaMemcpyDeviceToHost, c->stream));
   MQ_CUDA(c, cudaStreamSynchronize(c->stream));
-  if ((st = timing(c)) != MQ_OK) return st;
+  if ((st = timing(c, -1)) != MQ_OK) return st;
   int fl = 0;
   c->last_B = 1;
   if ((st = collect_stats(c, 1, &fl)) != MQ_OK) return st;
