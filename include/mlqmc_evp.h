@@ -103,9 +103,24 @@ mq_status mq_set_lattice(mq_ctx* ctx, int32_t level, const uint32_t* z, int32_t 
 /* Random shifts Delta[R][s_l] of level `level`, row-major, each in [0, 1) (copied). */
 mq_status mq_set_shifts(mq_ctx* ctx, int32_t level, const double* delta);
 
-/* Precision mode and the relative residual tolerance of the fine shifted solve
- * (tol_linear <= 0 keeps the default 1e-10). */
+/* Precision mode and the relative residual target ||b - (A - lambda_H M) w|| / ||b|| of the fine
+ * shifted solve (tol_linear <= 0: default 1e-7 for MQ_PREC_MIXED, 1e-8 for MQ_PREC_FP64; the
+ * Rayleigh quotient is second-order accurate in the solve error, so these keep lambda^h within
+ * ~1e-13 of the exact two-grid value). */
 mq_status mq_set_precision(mq_ctx* ctx, mq_precision prec, double tol_linear);
+
+/* Inner solver options (values <= 0 keep the defaults): tol_inner is the reduction of the
+ * preconditioned MINRES residual per refinement step (default 1e-5 in MQ_PREC_MIXED, tol_linear/10
+ * in MQ_PREC_FP64), max_inner the MINRES iteration cap per step (500), max_outer the cap on FP64
+ * refinement steps (10 mixed, 4 FP64). */
+mq_status mq_set_solver_options(mq_ctx* ctx, double tol_inner, int32_t max_inner, int32_t max_outer);
+
+/* Execution tier of the fine solves: fine meshes 1/n with n >= stream_min_n run in
+ * the batched streaming tier (one kernel per sweep over all samples of a pass, lockstep across
+ * samples); coarser ones run inside the per-sample kernel (one CTA per sample, workspace in
+ * shared memory when it fits).  Both tiers compute the same values to rounding.  Default (or
+ * stream_min_n = 0): 64 in MQ_PREC_MIXED, 256 in MQ_PREC_FP64. */
+mq_status mq_set_tier(mq_ctx* ctx, int32_t stream_min_n);
 
 /* Evaluate level `level` at lattice indices k in [k0, k1) for every shift (Algorithm 2, steps
  * 5-15): per sample the coarse eigenpair on (H_l, S_l), lambda^l by Algorithm 1 on (h_l, s_l)

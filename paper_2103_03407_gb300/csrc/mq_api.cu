@@ -51,11 +51,14 @@ struct mq_ctx {
   std::vector<uint64_t> lvl_launches;              // per level: per-sample kernel launches
 
   int prec = MQ_PREC_FP64;
-  double tol_lin = 1e-10;
+  double tol_lin = 0.0;  // 0: default of the precision mode
+  double opt_tol_inner = 0.0;  // 0: default of the precision mode
+  int opt_max_inner = 0, opt_max_outer = 0;
 
   std::map<int, std::pair<int, double*>> psi;  // mesh n -> (rows, table [rows][2n^2])
 
-  DevBuf Y, af, ac, ap, out, stat, outer, scratch, sums_d, flags_d, uout, misc;
+  DevBuf Y, af, ac, ap, out, stat, outer, scratch, sums_d, flags_d, uout, misc, upad, arena;
+  int stream_min = 0;  // fine meshes 1/n with n >= stream_min use the streaming tier (0: default)
   mq_stats stats{};
   size_t last_B = 0;  // samples of the last pass (their per-sample counters are still on the device)
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -144,6 +147,14 @@ mq_status check_level_ready(mq_ctx* c, int level) {
   return MQ_OK;
 }
 
+// Default tier threshold (measured on GB300, 4-level workload): with FP32 inner solves the
+// streaming tier wins from 1/64 on; the FP64 path is FP64-throughput bound and keeps the
+// per-sample kernel up to 1/128.
+int stream_threshold(const mq_ctx* c) {
+  if (c->stream_min > 0) return c->stream_min;
+  return c->prec == MQ_PREC_MIXED ? 64 : 256;
+}
+
 // threads per CTA for a fine mesh 1/n
 int threads_for(int n) { return n <= 16 ? 128 : 256; }
 
@@ -199,9 +210,10 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
   MQ_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
 
   mq::SampleLaunch p{};
-  p.nf = g.nf;
+  const bool stream = g.nf >= stream_threshold(c) && !g.direct_f;
+  p.nf = stream ? 0 : g.nf;
   p.nc = g.nc;
-  p.np = g.np;
+  p.np = stream ? g.np : g.np;
   p.direct_f = g.direct_f;
   p.direct_p = g.direct_p;
   p.R = R;
@@ -216,20 +228,33 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
   p.u_out = want_u ? (double*)c->uout.p : nullptr;
   p.tol_eig = 1e-12;
   p.max_eig_it = 200;
-  p.tol_lin = c->tol_lin;
+  // Default residual targets of the shifted solve.  The Rayleigh quotient is stationary at the
+  // eigenvector, and the two-grid iterate is an O(H^4) perturbation of it, so the error of
+  // lambda^h is of second order in the solve error plus a first-order term damped by O(H^4):
+  // on the 4-level workload a relative residual of 1e-7 leaves every lambda^h within 1e-13 of
+  // the exact two-grid value.
+  p.tol_lin = c->tol_lin > 0 ? c->tol_lin : (mixed ? 1e-7 : 1e-8);
   if (mixed) {
     p.tol_inner = 1e-5;
     p.max_outer = 10;
   } else {
-    p.tol_inner = 0.1 * c->tol_lin;
+    p.tol_inner = 0.1 * p.tol_lin;
     p.max_outer = 4;
   }
   p.max_inner_it = 500;
+  if (c->opt_tol_inner > 0) p.tol_inner = c->opt_tol_inner;
+  if (c->opt_max_inner > 0) p.max_inner_it = c->opt_max_inner;
+  if (c->opt_max_outer > 0) p.max_outer = c->opt_max_outer;
   p.nu = 2;
   p.omega = 0.8;
+  if (stream) {
+    p.coarse_only = 1;
+    if ((st = grow(c, c->upad, B * (size_t)(g.nc + 1) * (g.nc + 1) * sizeof(double))) != MQ_OK) return st;
+    p.u_pad = (double*)c->upad.p;
+  }
 
-  const int threads = threads_for(std::max(g.nf, g.nc));
-  const size_t slab = mq::sample_slab_bytes(g.nf, g.nc, g.np, mixed);
+  const int threads = threads_for(stream ? g.nc : std::max(g.nf, g.nc));
+  const size_t slab = stream ? mq::sample_slab_bytes(0, g.nc, 0, mixed) : mq::sample_slab_bytes(g.nf, g.nc, g.np, mixed);
   const int static_smem = mq::sample_static_smem(mixed);
   const size_t smem_cap = (size_t)std::max(0, c->smem_optin - static_smem - 1024);
   const bool use_smem = slab <= smem_cap;
@@ -248,6 +273,40 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
   p.slab_bytes = slab;
   p.use_smem = use_smem;
   MQ_CUDA(c, mq::launch_sample(p, mixed, blocks, threads, smem, c->stream));
+  if (stream) {
+    if ((st = grow(c, c->arena, mq::stream_arena_bytes(g.nf, (int)B, mixed))) != MQ_OK) return st;
+    mq::StreamSolve s{};
+    s.nc = g.nc;
+    s.B = (int)B;
+    s.uH = (const double*)c->upad.p;
+    s.lamH = (const double*)c->out.p;
+    s.lam_stride = 4;
+    s.lam_out_stride = 4;
+    s.iters_stride = 4;
+    s.outer_stride = 2;
+    s.flags = (int*)c->stat.p + 3;
+    s.flags_stride = 4;
+    s.tol_lin = p.tol_lin;
+    s.tol_inner = p.tol_inner;
+    s.max_inner = p.max_inner_it;
+    s.max_outer = p.max_outer;
+    s.omega = p.omega;
+    s.n = g.nf;
+    s.a = (const double*)c->af.p;
+    s.lam_out = (double*)c->out.p + 1;
+    s.iters_out = (int*)c->stat.p + 1;
+    s.outer_out = (int*)c->outer.p + 0;
+    MQ_CUDA(c, mq::stream_solve(s, mixed, c->arena.p, c->stream));
+    if (g.np && !g.direct_p) {
+      s.n = g.np;
+      s.a = (const double*)c->ap.p;
+      s.lam_out = (double*)c->out.p + 2;
+      s.iters_out = (int*)c->stat.p + 2;
+      s.outer_out = (int*)c->outer.p + 1;
+      MQ_CUDA(c, mq::stream_solve(s, mixed, c->arena.p, c->stream));
+    }
+    MQ_CUDA(c, mq::launch_finalize((int)B, (double*)c->out.p, g.np > 0, c->stream));
+  }
   MQ_CUDA(c, cudaEventRecord(c->ev[2], c->stream));
   c->stats.blocks = blocks;
   c->stats.threads = threads;
@@ -320,9 +379,12 @@ mq_status flags_status(mq_ctx* c, int fl) {
 
 // points per pass so that the coefficient buffers stay within a memory budget
 int points_per_pass(const mq_ctx* c, const LevelGeom& g, int R, int npts) {
-  const size_t per_sample = sizeof(double) * ((size_t)2 * g.nf * g.nf + (size_t)2 * g.nc * g.nc +
-                                              (size_t)2 * g.np * g.np + (size_t)g.s + 8);
-  const size_t budget = (size_t)16 << 30;
+  size_t per_sample = sizeof(double) * ((size_t)2 * g.nf * g.nf + (size_t)2 * g.nc * g.nc +
+                                        (size_t)2 * g.np * g.np + (size_t)g.s + 8 + (size_t)(g.nc + 1) * (g.nc + 1));
+  if (g.nf >= stream_threshold(c) && !g.direct_f) per_sample += mq::stream_arena_bytes(g.nf, 1, c->prec == MQ_PREC_MIXED);
+  size_t free_b = 0, total_b = 0;
+  size_t budget = (size_t)24 << 30;
+  if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) budget = std::min<size_t>((size_t)(0.4 * free_b), (size_t)64 << 30);
   size_t pts = budget / (per_sample * (size_t)R);
   if (pts < 1) pts = 1;
   return (int)std::min<size_t>(pts, (size_t)npts);
@@ -447,7 +509,7 @@ mq_status mq_destroy(mq_ctx* c) {
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
   for (DevBuf* b : {&c->Y, &c->af, &c->ac, &c->ap, &c->out, &c->stat, &c->outer, &c->scratch, &c->sums_d,
-                    &c->flags_d, &c->uout, &c->misc})
+                    &c->flags_d, &c->uout, &c->misc, &c->upad, &c->arena})
     if (b->p) cudaFree(b->p);
   for (auto& kv : c->psi) cudaFree(kv.second.second);
   for (auto p : c->d_z)
@@ -572,7 +634,24 @@ mq_status mq_set_precision(mq_ctx* c, mq_precision prec, double tol_linear) {
   if (prec != MQ_PREC_FP64 && prec != MQ_PREC_MIXED) return fail(c, MQ_EINVAL, "unknown precision %d", (int)prec);
   if (!std::isfinite(tol_linear) || tol_linear >= 1.0) return fail(c, MQ_EINVAL, "tolerance must be < 1");
   c->prec = prec;
-  c->tol_lin = tol_linear > 0 ? tol_linear : 1e-10;
+  c->tol_lin = tol_linear > 0 ? tol_linear : 0.0;
+  return MQ_OK;
+}
+
+mq_status mq_set_solver_options(mq_ctx* c, double tol_inner, int32_t max_inner, int32_t max_outer) {
+  if (!c) return MQ_EINVAL;
+  if (!std::isfinite(tol_inner) || tol_inner >= 1.0 || max_inner > 100000 || max_outer > 1000)
+    return fail(c, MQ_EINVAL, "bad solver options");
+  c->opt_tol_inner = tol_inner > 0 ? tol_inner : 0.0;
+  c->opt_max_inner = max_inner > 0 ? max_inner : 0;
+  c->opt_max_outer = max_outer > 0 ? max_outer : 0;
+  return MQ_OK;
+}
+
+mq_status mq_set_tier(mq_ctx* c, int32_t stream_min_n) {
+  if (!c) return MQ_EINVAL;
+  if (stream_min_n < 0 || stream_min_n == 1) return fail(c, MQ_EINVAL, "stream_min_n must be 0 or >= 2");
+  c->stream_min = stream_min_n;
   return MQ_OK;
 }
 

@@ -1,0 +1,340 @@
+// Device building blocks shared by the per-sample kernel (mq_sample.cu) and the batched
+// streaming tier (mq_stream.cu): workspace carving, block-wide loops and reductions, the
+// matrix-free P1 stencils, the multigrid hierarchy and the symmetric V-cycle.
+//
+// Stencils on the SW-NE triangulation with centroid coefficients: the P1 stiffness is the
+// weighted five-point edge form (A x)_p = sum_{edges pq} w_pq (x_p - x_q) with
+//     w of edge (i,j)-(i+1,j) = (a_low(i,j) + a_up(i,j-1)) / 2,
+//     w of edge (i,j)-(i,j+1) = (a_up(i,j) + a_low(i-1,j)) / 2
+// (hypotenuses carry no weight) and the consistent mass is the seven-point form
+//     (M x)_p = h^2/12 (6 x_p + x_E + x_W + x_N + x_S + x_NE + x_SW).
+// Vectors live on the padded (n+1) x (n+1) node grid with a zero boundary ring.  Multigrid
+// coarse operators are the Galerkin operators P^T A P, i.e. the coarse P1 stiffness whose
+// triangle coefficients are the means of the four fine triangles they contain.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "mq_internal.h"
+
+namespace mq {
+namespace dev {
+
+// ---------------------------------------------------------------------------------------------
+// workspace carving (16-byte aligned arrays)
+struct Carver {
+  uintptr_t base, cur;
+  __host__ __device__ explicit Carver(void* b) : base((uintptr_t)b), cur((uintptr_t)b) {}
+  template <typename T>
+  __host__ __device__ T* take(size_t count) {
+    cur = (cur + 15) & ~(uintptr_t)15;
+    T* p = (T*)cur;
+    cur += count * sizeof(T);
+    return p;
+  }
+  __host__ __device__ size_t used() const { return (size_t)(cur - base); }
+};
+
+__host__ __device__ inline int ilog2(int n) {
+#ifdef __CUDA_ARCH__
+  return __ffs(n) - 1;  // n is a power of two
+#else
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+#endif
+}
+__host__ __device__ inline size_t gsz(int n) { return (size_t)(n + 1) * (size_t)(n + 1); }
+
+// Multigrid hierarchy for the stiffness A on meshes n, n/2, ..., 2 (level 0 = finest).
+template <typename T>
+struct MGDesc {
+  int L;
+  int n[kMaxMG];
+  T* wx[kMaxMG];  // weight of edge (i,j)-(i+1,j) at padded node (i,j)
+  T* wy[kMaxMG];  // weight of edge (i,j)-(i,j+1)
+  T* dinv[kMaxMG];  // 1 / diag(A)
+  T* x[kMaxMG];   // level solution (level 0: supplied by the caller)
+  T* t[kMaxMG];   // Jacobi partner
+  T* b[kMaxMG];   // level right-hand side (level 0: supplied by the caller)
+  T* cell[2];     // ping-pong per-triangle coefficients while building
+};
+
+template <typename T>
+__host__ __device__ void carve_mg(Carver& c, int n, MGDesc<T>& d) {
+  d.L = ilog2(n);
+  for (int l = 0; l < d.L; ++l) {
+    const int nl = n >> l;
+    d.n[l] = nl;
+    const size_t V = gsz(nl);
+    d.wx[l] = c.take<T>(V);
+    d.wy[l] = c.take<T>(V);
+    d.dinv[l] = c.take<T>(V);
+    d.t[l] = c.take<T>(V);
+    d.x[l] = l ? c.take<T>(V) : nullptr;
+    d.b[l] = l ? c.take<T>(V) : nullptr;
+  }
+  const size_t cells = n >= 4 ? (size_t)2 * (n / 2) * (n / 2) : 1;
+  d.cell[0] = c.take<T>(cells);
+  d.cell[1] = c.take<T>(cells);
+}
+
+// Same hierarchy with the operator arrays (weights, inverse diagonals) taken from carver w and
+// the vectors (t, x, b) and building buffers taken from carver v.
+template <typename T>
+__host__ __device__ void carve_mg_split(Carver& w, Carver& v, int n, MGDesc<T>& d) {
+  d.L = ilog2(n);
+  for (int l = 0; l < d.L; ++l) {
+    const int nl = n >> l;
+    d.n[l] = nl;
+    const size_t V = gsz(nl);
+    d.wx[l] = w.take<T>(V);
+    d.wy[l] = w.take<T>(V);
+    d.dinv[l] = w.take<T>(V);
+    d.t[l] = v.take<T>(V);
+    d.x[l] = l ? v.take<T>(V) : nullptr;
+    d.b[l] = l ? v.take<T>(V) : nullptr;
+  }
+  const size_t cells = n >= 4 ? (size_t)2 * (n / 2) * (n / 2) : 1;
+  d.cell[0] = v.take<T>(cells);
+  d.cell[1] = v.take<T>(cells);
+}
+
+// ---------------------------------------------------------------------------------------------
+// block-level helpers
+template <class F>
+__device__ __forceinline__ void for_interior(int n, F f) {
+  const int lg = ilog2(n);
+  const int tot = (n - 1) << lg;
+  const int ld = n + 1;
+  for (int q = threadIdx.x; q < tot; q += blockDim.x) {
+    const int i = (q & (n - 1)) + 1;
+    if (i == n) continue;
+    const int j = (q >> lg) + 1;
+    f(j * ld + i, i, j);
+  }
+}
+
+template <class F>
+__device__ __forceinline__ void for_all(size_t count, F f) {
+  for (size_t q = threadIdx.x; q < count; q += blockDim.x) f(q);
+}
+
+struct NoEp {
+  __device__ void operator()(const double*) const {}
+};
+
+// Sum NV values over the block (fixed order: deterministic).  Thread 0 runs ep(totals) before the
+// closing barrier, so scalars it derives are visible to every thread after the call; every thread
+// also receives the totals in out.
+template <int NV, typename A, class Ep = NoEp>
+__device__ __forceinline__ void block_sum(A (&v)[NV], double (&out)[NV], double* red, Ep ep = Ep()) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    A s = v[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) red[wid * NV + i] = (double)s;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    double tot[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      double s = lane < nw ? red[lane * NV + i] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      tot[i] = s;
+      if (lane == 0) red[32 * NV + i] = s;
+    }
+    if (lane == 0) ep(tot);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) out[i] = red[32 * NV + i];
+  __syncthreads();
+}
+
+// stiffness (weighted five-point edge form) at padded node p
+template <typename T, typename X>
+__device__ __forceinline__ T stiff(const T* __restrict__ wx, const T* __restrict__ wy, const X* x, int p, int ld) {
+  const T xp = (T)x[p];
+  return wx[p] * (xp - (T)x[p + 1]) + wx[p - 1] * (xp - (T)x[p - 1]) + wy[p] * (xp - (T)x[p + ld]) +
+         wy[p - ld] * (xp - (T)x[p - ld]);
+}
+
+// mass seven-point sum without the h^2/12 factor
+template <typename T>
+__device__ __forceinline__ T mass7(const T* x, int p, int ld) {
+  return T(6) * x[p] + (x[p + 1] + x[p - 1]) + (x[p + ld] + x[p - ld]) + (x[p + ld + 1] + x[p - ld - 1]);
+}
+
+// FP64 stiffness at interior node (i, j) of mesh n with the edge weights formed from the
+// centroid coefficients a (lower triangles first, then upper).
+__device__ __forceinline__ double stiff_cells(const double* __restrict__ a, int n, const double* x, int p, int ld,
+                                              int i, int j) {
+  const double* lo = a;
+  const double* up = a + (size_t)n * n;
+  const int c = j * n + i;
+  const double lij = lo[c], li1j = lo[c - 1], li1j1 = lo[c - n - 1];
+  const double uij = up[c], uij1 = up[c - n], ui1j1 = up[c - n - 1];
+  const double we = 0.5 * (lij + uij1), ww = 0.5 * (li1j + ui1j1);
+  const double wn = 0.5 * (uij + li1j), ws = 0.5 * (uij1 + li1j1);
+  const double xp = x[p];
+  return we * (xp - x[p + 1]) + ww * (xp - x[p - 1]) + wn * (xp - x[p + ld]) + ws * (xp - x[p - ld]);
+}
+
+// ---------------------------------------------------------------------------------------------
+// operator setup
+template <typename T, typename S>
+__device__ void weights_from_cells(int n, const S* low, const S* up, T* wx, T* wy) {
+  const int ld = n + 1;
+  for_all(gsz(n), [&](size_t q) {
+    const int i = (int)(q % ld), j = (int)(q / ld);
+    T a = T(0), b = T(0);
+    if (i <= n - 1 && j >= 1 && j <= n - 1) a = T(0.5 * ((double)low[j * n + i] + (double)up[(j - 1) * n + i]));
+    if (i >= 1 && i <= n - 1 && j <= n - 1) b = T(0.5 * ((double)up[j * n + i] + (double)low[j * n + i - 1]));
+    wx[q] = a;
+    wy[q] = b;
+  });
+}
+
+template <typename T, typename S>
+__device__ void coarsen_cells(int n, const S* low, const S* up, T* out) {
+  const int m = n / 2;
+  for_all((size_t)m * m, [&](size_t q) {
+    const int I = (int)(q % m), J = (int)(q / m);
+    const int i = 2 * I, j = 2 * J;
+    const double lo = (double)low[j * n + i] + (double)low[j * n + i + 1] + (double)low[(j + 1) * n + i + 1] +
+                      (double)up[j * n + i + 1];
+    const double hi = (double)up[j * n + i] + (double)up[(j + 1) * n + i + 1] + (double)up[(j + 1) * n + i] +
+                      (double)low[(j + 1) * n + i];
+    out[q] = T(0.25 * lo);
+    out[m * m + q] = T(0.25 * hi);
+  });
+}
+
+template <typename T>
+__device__ void inverse_diagonal(int n, const T* wx, const T* wy, T* dinv) {
+  const int ld = n + 1;
+  for_interior(n, [&](int p, int, int) { dinv[p] = T(1) / (wx[p] + wx[p - 1] + wy[p] + wy[p - ld]); });
+}
+
+// Builds every level (weights, inverse diagonals) from the fine centroid coefficients a.
+// Returns true when every coefficient is positive (Assumption A1).
+template <typename T, typename S = double>
+__device__ bool build_mg(MGDesc<T>& d, const S* __restrict__ a, int n, double* red) {
+  int bad = 0;
+  for_all((size_t)2 * n * n, [&](size_t q) { bad |= !(a[q] > S(0)); });
+  weights_from_cells<T, S>(n, a, a + (size_t)n * n, d.wx[0], d.wy[0]);
+  if (d.L > 1) coarsen_cells<T, S>(n, a, a + (size_t)n * n, d.cell[0]);
+  __syncthreads();
+  for (int l = 1; l < d.L; ++l) {
+    const int nl = d.n[l];
+    const T* src = d.cell[(l - 1) & 1];
+    weights_from_cells<T, T>(nl, src, src + (size_t)nl * nl, d.wx[l], d.wy[l]);
+    if (l + 1 < d.L) coarsen_cells<T, T>(nl, src, src + (size_t)nl * nl, d.cell[l & 1]);
+    inverse_diagonal<T>(d.n[l - 1], d.wx[l - 1], d.wy[l - 1], d.dinv[l - 1]);
+    __syncthreads();
+  }
+  inverse_diagonal<T>(d.n[d.L - 1], d.wx[d.L - 1], d.wy[d.L - 1], d.dinv[d.L - 1]);
+  double v[1] = {(double)bad}, o[1];
+  block_sum<1, double>(v, o, red);
+  return o[0] == 0.0;
+}
+
+// Symmetric V-cycle for A: damped Jacobi (nu sweeps before and after the coarse correction),
+// Galerkin coarse levels, exact solve on the one-unknown mesh 1/2.  x0 = B^{-1} b0.
+// The residual is restricted with P^T in the same sweep that forms it.
+template <typename T>
+__device__ void vcycle(const MGDesc<T>& d, const T* b0, T* x0, int nu, T omega) {
+  const int L = d.L;
+  for (int l = 0; l < L - 1; ++l) {
+    const int n = d.n[l], ld = n + 1;
+    const T* b = l ? d.b[l] : b0;
+    T* xa = l ? d.x[l] : x0;
+    const T* __restrict__ wx = d.wx[l];
+    const T* __restrict__ wy = d.wy[l];
+    const T* __restrict__ di = d.dinv[l];
+    T* cur = d.t[l];
+    T* oth = xa;
+    for_interior(n, [&](int p, int, int) { cur[p] = omega * di[p] * b[p]; });
+    __syncthreads();
+    for (int k = 1; k < nu; ++k) {
+      for_interior(n, [&](int p, int, int) { oth[p] = cur[p] + omega * di[p] * (b[p] - stiff<T, T>(wx, wy, cur, p, ld)); });
+      __syncthreads();
+      T* tt = cur;
+      cur = oth;
+      oth = tt;
+    }
+    T* bc = d.b[l + 1];
+    const T* cx = cur;
+    for_interior(n >> 1, [&](int P, int I, int J) {
+      const int p = (2 * J) * ld + 2 * I;
+      auto res = [&](int q) { return b[q] - stiff<T, T>(wx, wy, cx, q, ld); };
+      bc[P] = res(p) + T(0.5) * ((res(p + 1) + res(p - 1)) + (res(p + ld) + res(p - ld)) +
+                                 (res(p + ld + 1) + res(p - ld - 1)));
+    });
+    __syncthreads();
+  }
+  {
+    const T* b = (L - 1) ? d.b[L - 1] : b0;
+    T* x = (L - 1) ? d.x[L - 1] : x0;
+    if (threadIdx.x == 0) x[4] = b[4] * d.dinv[L - 1][4];  // mesh 1/2: one unknown at padded index 4
+    __syncthreads();
+  }
+  for (int l = L - 2; l >= 0; --l) {
+    const int n = d.n[l], ld = n + 1;
+    const T* b = l ? d.b[l] : b0;
+    T* xa = l ? d.x[l] : x0;
+    const T* __restrict__ wx = d.wx[l];
+    const T* __restrict__ wy = d.wy[l];
+    const T* __restrict__ di = d.dinv[l];
+    T* cur = ((nu - 1) & 1) ? xa : d.t[l];
+    T* oth = ((nu - 1) & 1) ? d.t[l] : xa;
+    const T* xc = d.x[l + 1];
+    const int ldc = (n >> 1) + 1;
+    for_interior(n, [&](int p, int i, int j) {
+      const int I = i >> 1, J = j >> 1;
+      const int c0 = J * ldc + I;
+      T v;
+      if (!(i & 1) && !(j & 1)) v = xc[c0];
+      else if ((i & 1) && !(j & 1)) v = T(0.5) * (xc[c0] + xc[c0 + 1]);
+      else if (!(i & 1)) v = T(0.5) * (xc[c0] + xc[c0 + ldc]);
+      else v = T(0.5) * (xc[c0] + xc[c0 + ldc + 1]);
+      cur[p] += v;
+    });
+    __syncthreads();
+    for (int k = 0; k < nu; ++k) {
+      for_interior(n, [&](int p, int, int) { oth[p] = cur[p] + omega * di[p] * (b[p] - stiff<T, T>(wx, wy, cur, p, ld)); });
+      __syncthreads();
+      T* tt = cur;
+      cur = oth;
+      oth = tt;
+    }
+  }
+}
+
+template <typename T>
+__device__ void zero_vec(T* v, int n) {
+  for_all(gsz(n), [&](size_t q) { v[q] = T(0); });
+}
+
+template <typename T>
+__device__ void zero_mg(const MGDesc<T>& d) {
+  for (int l = 0; l < d.L; ++l) {
+    zero_vec(d.t[l], d.n[l]);
+    zero_vec(d.dinv[l], d.n[l]);
+    if (l) {
+      zero_vec(d.x[l], d.n[l]);
+      zero_vec(d.b[l], d.n[l]);
+    }
+  }
+}
+
+}  // namespace dev
+}  // namespace mq

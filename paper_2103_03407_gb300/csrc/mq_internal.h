@@ -33,7 +33,32 @@ struct SampleLaunch {
   int max_outer;
   int nu;                  // Jacobi sweeps before and after each coarse-grid correction
   double omega;            // Jacobi damping
+  int coarse_only;         // only the coarse eigenpairs: u_pad receives the padded eigenvectors
+  double* u_pad;           // [B][(nc+1)^2] when coarse_only
 };
+
+// Batched streaming fine solve (mq_stream.cu): B samples on mesh 1/n, coarse pairs from mesh 1/nc.
+struct StreamSolve {
+  int n, nc, B;
+  const double* a;         // [B][2 n^2] centroid coefficients
+  const double* uH;        // [B][(nc+1)^2] padded coarse eigenvectors
+  const double* lamH;      // coarse eigenvalue of sample b at lamH[b * lam_stride]
+  int lam_stride;
+  double* lam_out;         // two-grid eigenvalue of sample b at lam_out[b * lam_out_stride]
+  int lam_out_stride;
+  int* iters_out;
+  int iters_stride;
+  int* outer_out;
+  int outer_stride;
+  int* flags;              // OR-ed with kFlag* bits
+  int flags_stride;
+  double tol_lin, tol_inner;
+  int max_inner, max_outer;
+  double omega;
+};
+size_t stream_arena_bytes(int n, int B, int mixed);
+cudaError_t stream_solve(const StreamSolve& s, int mixed, void* arena, cudaStream_t st);
+cudaError_t launch_finalize(int B, double* d_out, int has_prev, cudaStream_t st);
 
 // Sample flags (stat[b][3])
 enum : int {

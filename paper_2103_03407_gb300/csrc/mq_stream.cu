@@ -1,0 +1,971 @@
+// Batched streaming tier of the fine two-grid solve (Algorithm 1 steps 2-4) for meshes of
+// 1/32 and finer: one kernel per sweep over all samples of a batch, lockstep across samples.
+//
+// The per-sample kernel keeps a whole sample inside one CTA; on fine meshes its workspace spills
+// out of L2 and every sweep waits on DRAM with few warps in flight.  Here each sweep is a
+// grid-wide kernel over [sample][node] arrays instead, so the whole GPU streams every array with
+// full memory-level parallelism:
+//   * MINRES (preconditioned, symmetric indefinite) in the inner precision T, one iteration =
+//     K1 (pending w/x update, q = (A - sigma M) z / gamma, partial <q, z>), S1 (scalars),
+//     K2 (v_new, z scaling), the V-cycle, S2 (Givens rotation, convergence);
+//   * the V-cycle (Jacobi nu = 2 before and after, Galerkin coarse levels) streams the meshes
+//     finer than 1/32 with four kernels per level -- two fused smoothing steps from zero,
+//     residual + restriction, prolongation + correction + one smoothing step, one smoothing step
+//     (the last one at the finest level also forms <v, z>) -- and runs the meshes 1/32 .. 1/2 of
+//     each sample inside one CTA in shared memory;
+//   * FP64 iterative refinement around the inner solve and the FP64 Rayleigh quotient.
+// Partial sums of every reduction are written per (sample, tile) and added in fixed order by
+// the scalar kernels: results do not depend on scheduling.  Converged samples are masked out.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <initializer_list>
+#include <vector>
+
+#include "mq_device.cuh"
+#include "mq_internal.h"
+
+namespace mq {
+namespace {
+
+using namespace dev;
+
+constexpr int kThreads = 256;
+constexpr int kPer = 4;                      // nodes per thread per tile
+constexpr int kTile = kThreads * kPer;       // nodes per CTA
+constexpr int kSub = 32;                     // meshes up to 1/32 run inside one CTA
+
+__host__ __device__ inline int tiles_interior(int n) { return ((n - 1) * n + kTile - 1) / kTile; }
+__host__ __device__ inline int tiles_padded(int n) { return (int)((gsz(n) + kTile - 1) / kTile); }
+
+// loop over the interior nodes of tile ch of mesh n
+template <class F>
+__device__ __forceinline__ void for_tile(int n, int ch, F f) {
+  const int lg = ilog2(n);
+  const int tot = (n - 1) << lg;
+  const int ld = n + 1;
+  const int q0 = ch * kTile + threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const int q = q0 + k * kThreads;
+    if (q < tot) {
+      const int i = (q & (n - 1)) + 1;
+      if (i != n) {
+        const int j = (q >> lg) + 1;
+        f(j * ld + i, i, j);
+      }
+    }
+  }
+}
+
+template <typename T>
+struct SS {  // per-sample solver scalars
+  T gam, gam_old, eta, eta0, c, c_old, s, s_old, ig, c1, c2, cx, ia1, a2, a3, delta, rs;
+  double rnorm, bnorm, lam_h;
+  int act_outer;  // refinement still running
+  int act;        // inner MINRES running
+  int pend;       // a w/x update is pending
+  int iters, outer, flags;
+};
+
+// block reduction of NV partial sums to part[(b * nch + ch) * NV + i]
+template <int NV, typename A>
+__device__ __forceinline__ void tile_partials(A (&v)[NV], double* part, size_t slot) {
+  __shared__ double red[32 * NV];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    A s = v[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) red[wid * NV + i] = (double)s;
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      double s = lane < nw ? red[lane * NV + i] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) part[slot * NV + i] = s;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// setup
+// weights and inverse diagonal of mesh n from per-triangle coefficients (lower plane, upper plane)
+template <typename T, typename S>
+__global__ void k_weights(int n, int B, const S* __restrict__ cells, size_t cstride, T* __restrict__ wx,
+                          T* __restrict__ wy, T* __restrict__ dinv, const int* __restrict__ act, SS<T>* ss) {
+  const int nt = tiles_padded(n);
+  const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
+  if (b >= B || (act && !act[b])) return;
+  const S* lo = cells + (size_t)b * cstride;
+  const S* up = lo + (size_t)n * n;
+  const size_t V = gsz(n);
+  const int ld = n + 1;
+  int bad = 0;
+  for (int k = 0; k < kPer; ++k) {
+    const size_t q = (size_t)ch * kTile + threadIdx.x + k * kThreads;
+    if (q >= V) break;
+    const int i = (int)(q % ld), j = (int)(q / ld);
+    auto LO = [&](int ii, int jj) { return (double)lo[jj * n + ii]; };
+    auto UP = [&](int ii, int jj) { return (double)up[jj * n + ii]; };
+    T a = T(0), c = T(0), d = T(0);
+    if (i <= n - 1 && j >= 1 && j <= n - 1) a = T(0.5 * (LO(i, j) + UP(i, j - 1)));
+    if (i >= 1 && i <= n - 1 && j <= n - 1) c = T(0.5 * (UP(i, j) + LO(i - 1, j)));
+    if (i <= n - 1 && j <= n - 1) bad |= !(LO(i, j) > 0.0) | !(UP(i, j) > 0.0);  // every triangle once
+    if (i >= 1 && i <= n - 1 && j >= 1 && j <= n - 1) {
+      const double l0 = LO(i, j), l1 = LO(i - 1, j), l2 = LO(i - 1, j - 1);
+      const double u0 = UP(i, j), u1 = UP(i, j - 1), u2 = UP(i - 1, j - 1);
+      const T we = T(0.5 * (l0 + u1)), ww = T(0.5 * (l1 + u2)), wn = T(0.5 * (u0 + l1)), ws = T(0.5 * (u1 + l2));
+      d = T(1) / (we + ww + wn + ws);
+    }
+    wx[(size_t)b * V + q] = a;
+    wy[(size_t)b * V + q] = c;
+    dinv[(size_t)b * V + q] = d;
+  }
+  if (ss && __syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&ss[b].flags, kFlagBadCoef);
+}
+
+// per-triangle coefficients of mesh n/2 as means of the four fine triangles each contains
+template <typename S, typename T>
+__global__ void k_coarsen(int n, int B, const S* __restrict__ in, size_t istride, T* __restrict__ out) {
+  const int m = n / 2;
+  const size_t mm = (size_t)m * m;
+  const int nt = (int)((mm + kTile - 1) / kTile);
+  const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
+  if (b >= B) return;
+  const S* lo = in + (size_t)b * istride;
+  const S* up = lo + (size_t)n * n;
+  T* o = out + (size_t)b * 2 * mm;
+  for (int k = 0; k < kPer; ++k) {
+    const size_t q = (size_t)ch * kTile + threadIdx.x + k * kThreads;
+    if (q >= mm) break;
+    const int I = (int)(q % m), J = (int)(q / m), i = 2 * I, j = 2 * J;
+    const double l = (double)lo[j * n + i] + (double)lo[j * n + i + 1] + (double)lo[(j + 1) * n + i + 1] +
+                     (double)up[j * n + i + 1];
+    const double u = (double)up[j * n + i] + (double)up[(j + 1) * n + i + 1] + (double)up[(j + 1) * n + i] +
+                     (double)lo[(j + 1) * n + i];
+    o[q] = T(0.25 * l);
+    o[mm + q] = T(0.25 * u);
+  }
+}
+
+template <typename S, typename T>
+__global__ void k_convert(size_t count, const S* __restrict__ in, T* __restrict__ out) {
+  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < count; q += (size_t)gridDim.x * blockDim.x)
+    out[q] = T(in[q]);
+}
+
+// P u_H at the fine nodes (into x64) -- padded arrays, ring zero
+template <typename T>
+__global__ void k_interp(int n, int nc, int B, const double* __restrict__ uH, double* __restrict__ x64) {
+  const int nt = tiles_interior(n);
+  const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
+  if (b >= B) return;
+  const int lr = ilog2(n / nc), rm = (1 << lr) - 1, ldc = nc + 1;
+  const double inv = 1.0 / (double)(1 << lr);
+  const double* u = uH + (size_t)b * gsz(nc);
+  double* x = x64 + (size_t)b * gsz(n);
+  for_tile(n, ch, [&](int p, int i, int j) {
+    const int I = i >> lr, J = j >> lr;
+    const double xi_ = (double)(i & rm) * inv, et = (double)(j & rm) * inv;
+    const int c0 = J * ldc + I;
+    x[p] = xi_ >= et ? (1.0 - xi_) * u[c0] + (xi_ - et) * u[c0 + 1] + et * u[c0 + ldc + 1]
+                     : (1.0 - et) * u[c0] + (et - xi_) * u[c0 + ldc] + xi_ * u[c0 + ldc + 1];
+  });
+}
+
+// b = M (P u_H); v = T(b); partial ||b||^2; x64 cleared afterwards by the caller
+template <typename T>
+__global__ void k_rhs(int n, int B, const double* __restrict__ x64, double* __restrict__ b64, T* __restrict__ v,
+                      double* part) {
+  const int nt = tiles_interior(n);
+  const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
+  if (b >= B) return;
+  const int ld = n + 1;
+  const double hm = 1.0 / (12.0 * n * n);
+  const size_t off = (size_t)b * gsz(n);
+  const double* x = x64 + off;
+  double acc[1] = {0.0};
+  for_tile(n, ch, [&](int p, int, int) {
+    const double bv = hm * mass7(x, p, ld);
+    b64[off + p] = bv;
+    v[off + p] = T(bv);
+    acc[0] += bv * bv;
+  });
+  tile_partials<1, double>(acc, part, (size_t)b * nt + ch);
+}
+
+template <typename T>
+__global__ void k_sc_start(int B, int nch, const double* part, SS<T>* ss) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  double s = 0.0;
+  for (int k = 0; k < nch; ++k) s += part[(size_t)b * nch + k];
+  SS<T>& S = ss[b];
+  S.bnorm = S.rnorm = sqrt(s);
+  S.rs = T(1.0 / S.rnorm);
+  S.act_outer = S.rnorm > 0.0;
+  S.act = 0;
+  S.pend = 0;
+  S.iters = 0;
+  S.outer = 0;
+}
+
+// start of a refinement step: samples above tolerance run an inner solve
+template <typename T>
+__global__ void k_sc_outer_begin(int B, double tol_lin, SS<T>* ss, int* act, int* count) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  SS<T>& S = ss[b];
+  const int a = S.act_outer && (S.rnorm > tol_lin * S.bnorm);
+  if (!a) S.act_outer = 0;
+  S.act = a;
+  act[b] = a;
+  if (a) atomicAdd(count, 1);
+}
+
+// v *= 1/||r||; clear vo, w, wo, xi
+template <typename T>
+__global__ void k_inner_init(int n, int B, const int* __restrict__ act, const SS<T>* ss, T* v, T* vo, T* w, T* wo,
+                             T* xi) {
+  const int nt = tiles_interior(n);
+  const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
+  if (b >= B || !act[b]) return;
+  const T rs = ss[b].rs;
+  const size_t off = (size_t)b * gsz(n);
+  for_tile(n, ch, [&](int p, int, int) {
+    v[off + p] *= rs;
+    vo[off + p] = T(0);
+    w[off + p] = T(0);
+    wo[off + p] = T(0);
+    xi[off + p] = T(0);
+  });
+}
+
+// ---------------------------------------------------------------------------------------------
+// V-cycle kernels (mesh n > kSub)
+// two damped Jacobi steps from zero: x1 = om D^-1 b, x = x1 + om D^-1 (b - A x1)
+template <typename T>
+__global__ void k_smooth2_from_zero(int n, int B, const int* __restrict__ act, const T* __restrict__ wx,
+                                    const T* __restrict__ wy, const T* __restrict__ dinv, const T* __restrict__ bb,
+                                    T* __restrict__ x, T om) {
+  const int nt = tiles_interior(n);
+  const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
+  if (b >= B || !act[b]) return;
+  const int ld = n + 1;
+  const size_t off = (size_t)b * gsz(n);
+  const T* W = wx + off;
+  const T* Y = wy + off;
+  const T* D = dinv + off;
+  const T* R = bb + off;
+  T* X = x + off;
+  for_tile(n, ch, [&](int p, int, int) {
+    auto x1 = [&](int q) { return om * D[q] * R[q]; };
+    const T xp = x1(p);
+    const T ax = W[p] * (xp - x1(p + 1)) + W[p - 1] * (xp - x1(p - 1)) + Y[p] * (xp - x1(p + ld)) +
+                 Y[p - ld] * (xp - x1(p - ld));
+    X[p] = xp + om * D[p] * (R[p] - ax);
+  });
+}
+
+// residual r = b - A x restricted with P^T to the coarse right-hand side
+template <typename T>
+__global__ void k_restrict(int n, int B, const int* __restrict__ act, const T* __restrict__ wx,
+                           const T* __restrict__ wy, const T* __restrict__ bb, const T* __restrict__ x,
+                           T* __restrict__ bc) {
+  const int m = n / 2;
+  const int nt = tiles_interior(m);
+  const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
+  if (b >= B || !act[b]) return;
+  const int ld = n + 1;
+  const size_t off = (size_t)b * gsz(n);
+  const T* W = wx + off;
+  const T* Y = wy + off;
+  const T* R = bb + off;
+  const T* X = x + off;
+  T* C = bc + (size_t)b * gsz(m);
+  for_tile(m, ch, [&](int P, int I, int J) {
+    const int p = (2 * J) * ld + 2 * I;
+    auto res = [&](int q) { return R[q] - stiff<T, T>(W, Y, X, q, ld); };
+    C[P] = res(p) + T(0.5) * ((res(p + 1) + res(p - 1)) + (res(p + ld) + res(p - ld)) +
+                              (res(p + ld + 1) + res(p - ld - 1)));
+  });
+}
+
+// t = x + P xc, then one Jacobi step: out = t + om D^-1 (b - A t)
+template <typename T>
+__global__ void k_prolong_smooth(int n, int B, const int* __restrict__ act, const T* __restrict__ wx,
+                                 const T* __restrict__ wy, const T* __restrict__ dinv, const T* __restrict__ bb,
+                                 const T* __restrict__ x, const T* __restrict__ xc, T* __restrict__ out, T om) {
+  const int nt = tiles_interior(n);
+  const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
+  if (b >= B || !act[b]) return;
+  const int ld = n + 1, ldc = n / 2 + 1;
+  const size_t off = (size_t)b * gsz(n);
+  const T* W = wx + off;
+  const T* Y = wy + off;
+  const T* D = dinv + off;
+  const T* R = bb + off;
+  const T* X = x + off;
+  const T* XC = xc + (size_t)b * gsz(n / 2);
+  T* O = out + off;
+  for_tile(n, ch, [&](int p, int i, int j) {
+    auto t = [&](int q, int ii, int jj) {
+      const int I = ii >> 1, J = jj >> 1, c0 = J * ldc + I;
+      T v;
+      if (!(ii & 1) && !(jj & 1)) v = XC[c0];
+      else if ((ii & 1) && !(jj & 1)) v = T(0.5) * (XC[c0] + XC[c0 + 1]);
+      else if (!(ii & 1)) v = T(0.5) * (XC[c0] + XC[c0 + ldc]);
+      else v = T(0.5) * (XC[c0] + XC[c0 + ldc + 1]);
+      return X[q] + v;
+    };
+    const T tp = t(p, i, j);
+    const T ax = W[p] * (tp - t(p + 1, i + 1, j)) + W[p - 1] * (tp - t(p - 1, i - 1, j)) +
+                 Y[p] * (tp - t(p + ld, i, j + 1)) + Y[p - ld] * (tp - t(p - ld, i, j - 1));
+    O[p] = tp + om * D[p] * (R[p] - ax);
+  });
+}
+
+// one Jacobi step out = t + om D^-1 (b - A t); optionally partial <dotv, out>
+template <typename T, bool DOT>
+__global__ void k_smooth(int n, int B, const int* __restrict__ act, const T* __restrict__ wx,
+                         const T* __restrict__ wy, const T* __restrict__ dinv, const T* __restrict__ bb,
+                         const T* __restrict__ t, T* __restrict__ out, T om, const T* __restrict__ dotv,
+                         double* part) {
+  const int nt = tiles_interior(n);
+  const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
+  if (b >= B || !act[b]) return;
+  const int ld = n + 1;
+  const size_t off = (size_t)b * gsz(n);
+  const T* W = wx + off;
+  const T* Y = wy + off;
+  const T* D = dinv + off;
+  const T* R = bb + off;
+  const T* X = t + off;
+  T* O = out + off;
+  T acc[1] = {T(0)};
+  for_tile(n, ch, [&](int p, int, int) {
+    const T o = X[p] + om * D[p] * (R[p] - stiff<T, T>(W, Y, X, p, ld));
+    O[p] = o;
+    if (DOT) acc[0] += dotv[off + p] * o;
+  });
+  if (DOT) tile_partials<1, T>(acc, part, (size_t)b * nt + ch);
+}
+
+// per-sample operator arrays of the meshes 1/ns .. 1/2 (sizes from carve_mg_split)
+template <typename T>
+__host__ __device__ size_t sub_weights_bytes(int ns) {
+  Carver w(nullptr), v(nullptr);
+  MGDesc<T> d;
+  carve_mg_split<T>(w, v, ns, d);
+  return (w.used() + 255) & ~(size_t)255;
+}
+template <typename T>
+__host__ __device__ size_t sub_vectors_bytes(int ns) {
+  Carver w(nullptr), v(nullptr);
+  MGDesc<T> d;
+  v.take<T>(gsz(ns));
+  v.take<T>(gsz(ns));
+  carve_mg_split<T>(w, v, ns, d);
+  return v.used() + 64;
+}
+
+// builds the operator arrays of meshes 1/ns .. 1/2 of every sample once per solve
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_sub_build(int ns, int B, const T* __restrict__ cells,
+                                                        char* __restrict__ subw, size_t wbytes) {
+  extern __shared__ __align__(16) char sm[];
+  __shared__ double red[32 * 12 + 12];
+  __shared__ MGDesc<T> mg;
+  const int b = blockIdx.x;
+  if (b >= B) return;
+  Carver w(subw + (size_t)b * wbytes), v(sm);
+  MGDesc<T> d;
+  v.take<T>(gsz(ns));
+  v.take<T>(gsz(ns));
+  carve_mg_split<T>(w, v, ns, d);
+  if (threadIdx.x == 0) mg = d;
+  __syncthreads();
+  build_mg<T, T>(mg, cells + (size_t)b * 2 * ns * ns, ns, red);
+}
+
+// meshes 1/ns .. 1/2 of one sample inside one CTA: x = B^{-1} b (operator arrays read from the
+// per-sample block built by k_sub_build, vectors in shared memory)
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_subcycle(int ns, int B, const int* __restrict__ act,
+                                                       const char* __restrict__ subw, size_t wbytes,
+                                                       const T* __restrict__ bin, T* __restrict__ xout, int nu, T om,
+                                                       double* part, const T* __restrict__ dotv) {
+  extern __shared__ __align__(16) char sm[];
+  __shared__ MGDesc<T> mg;
+  const int b = blockIdx.x;
+  if (b >= B || !act[b]) return;
+  const size_t V = gsz(ns);
+  Carver w((char*)subw + (size_t)b * wbytes), v(sm);
+  MGDesc<T> d;
+  T* b0 = v.take<T>(V);
+  T* x0 = v.take<T>(V);
+  carve_mg_split<T>(w, v, ns, d);
+  if (threadIdx.x == 0) mg = d;
+  const T* src = bin + (size_t)b * V;
+  for_all(V, [&](size_t q) {
+    b0[q] = src[q];
+    x0[q] = T(0);
+  });
+  for (int l = 0; l < d.L; ++l) {
+    zero_vec(d.t[l], d.n[l]);
+    if (l) {
+      zero_vec(d.x[l], d.n[l]);
+      zero_vec(d.b[l], d.n[l]);
+    }
+  }
+  __syncthreads();
+  vcycle<T>(mg, b0, x0, nu, om);
+  T* dst = xout + (size_t)b * V;
+  T acc[1] = {T(0)};
+  for_all(V, [&](size_t q) {
+    dst[q] = x0[q];
+    if (dotv) acc[0] += dotv[(size_t)b * V + q] * x0[q];
+  });
+  if (dotv) tile_partials<1, T>(acc, part, (size_t)b);
+}
+
+// ---------------------------------------------------------------------------------------------
+// MINRES sweeps
+// K1: pending w/x update; q = (A - sigma M) z * ig; partial <q, z>
+template <typename T>
+__global__ void k_minres_q(int n, int B, const int* __restrict__ act, const SS<T>* __restrict__ ss,
+                           const T* __restrict__ wx, const T* __restrict__ wy, const double* __restrict__ sigma,
+                           int sig_stride, const T* __restrict__ z, const T* __restrict__ zp, T* __restrict__ wo,
+                           const T* __restrict__ w, T* __restrict__ xi, T* __restrict__ q, double* part) {
+  const int nt = tiles_interior(n);
+  const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
+  if (b >= B || !act[b]) return;
+  const int ld = n + 1;
+  const size_t off = (size_t)b * gsz(n);
+  const SS<T> S = ss[b];
+  const T sigm = T(sigma[(size_t)b * sig_stride] / (12.0 * n * n));
+  const T* W = wx + off;
+  const T* Y = wy + off;
+  const T* Z = z + off;
+  T acc[1] = {T(0)};
+  for_tile(n, ch, [&](int p, int, int) {
+    if (S.pend) {
+      const T wnew = (zp[off + p] - S.a3 * wo[off + p] - S.a2 * w[off + p]) * S.ia1;
+      wo[off + p] = wnew;
+      xi[off + p] += S.cx * wnew;
+    }
+    const T kz = (stiff<T, T>(W, Y, Z, p, ld) - sigm * mass7(Z, p, ld)) * S.ig;
+    q[off + p] = kz;
+    acc[0] += kz * Z[p];
+  });
+  tile_partials<1, T>(acc, part, (size_t)b * nt + ch);
+}
+
+// K2: v_new = q - c1 v - c2 v_old (into vo) ; z *= ig
+template <typename T>
+__global__ void k_minres_v(int n, int B, const int* __restrict__ act, const SS<T>* __restrict__ ss,
+                           const T* __restrict__ q, const T* __restrict__ v, T* __restrict__ vo, T* __restrict__ z) {
+  const int nt = tiles_interior(n);
+  const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
+  if (b >= B || !act[b]) return;
+  const size_t off = (size_t)b * gsz(n);
+  const T c1 = ss[b].c1, c2 = ss[b].c2, ig = ss[b].ig;
+  for_tile(n, ch, [&](int p, int, int) {
+    vo[off + p] = q[off + p] - c1 * v[off + p] - c2 * vo[off + p];
+    z[off + p] *= ig;
+  });
+}
+
+// final pending w/x update
+template <typename T>
+__global__ void k_minres_finish(int n, int B, const int* __restrict__ act, const SS<T>* __restrict__ ss,
+                                const T* __restrict__ zp, const T* __restrict__ wo, const T* __restrict__ w,
+                                T* __restrict__ xi) {
+  const int nt = tiles_interior(n);
+  const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
+  if (b >= B || !act[b] || !ss[b].pend) return;
+  const size_t off = (size_t)b * gsz(n);
+  const SS<T> S = ss[b];
+  for_tile(n, ch, [&](int p, int, int) {
+    const T wnew = (zp[off + p] - S.a3 * wo[off + p] - S.a2 * w[off + p]) * S.ia1;
+    xi[off + p] += S.cx * wnew;
+  });
+}
+
+template <typename T>
+__global__ void k_sc_gamma0(int B, int nch, const double* part, const int* act, SS<T>* ss) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B || !act[b]) return;
+  double s = 0.0;
+  for (int k = 0; k < nch; ++k) s += part[(size_t)b * nch + k];
+  SS<T>& S = ss[b];
+  const T t0 = T(s);
+  const int brk = !(t0 > T(0));
+  const T g = brk ? T(1) : sqrt(t0);
+  S.gam = g;
+  S.eta = S.eta0 = g;
+  S.gam_old = T(1);
+  S.c = S.c_old = T(1);
+  S.s = S.s_old = T(0);
+  S.ig = T(1) / g;
+  S.pend = 0;
+  if (brk) S.flags |= kFlagBreakdown;
+}
+
+template <typename T>
+__global__ void k_sc_delta(int B, int nch, const double* part, const int* act, SS<T>* ss) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B || !act[b]) return;
+  double s = 0.0;
+  for (int k = 0; k < nch; ++k) s += part[(size_t)b * nch + k];
+  SS<T>& S = ss[b];
+  const T delta = T(s) * S.ig;
+  S.c1 = delta * S.ig;
+  S.c2 = S.gam / S.gam_old;
+  S.delta = delta;
+}
+
+// Givens step; a converged sample keeps its pending update and leaves the active set after the
+// next K1 (which applies it)
+template <typename T>
+__global__ void k_sc_givens(int B, int nch, const double* part, int* act, SS<T>* ss, T tol, int* count) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B || !act[b]) return;
+  double s = 0.0;
+  for (int k = 0; k < nch; ++k) s += part[(size_t)b * nch + k];
+  SS<T>& S = ss[b];
+  T gnew = T(s);
+  if (!(gnew >= T(0))) {
+    S.flags |= kFlagBreakdown;
+    gnew = T(0);
+  }
+  gnew = sqrt(gnew);
+  const T delta = S.delta, gam = S.gam;
+  const T al0 = S.c * delta - S.c_old * S.s * gam;
+  const T al1 = sqrt(al0 * al0 + gnew * gnew);
+  const T al2 = S.s * delta + S.c_old * S.c * gam;
+  const T al3 = S.s_old * gam;
+  const T ia1 = T(1) / al1;
+  const T cn = al0 * ia1, sn = gnew * ia1;
+  S.cx = cn * S.eta;
+  S.ia1 = ia1;
+  S.a2 = al2;
+  S.a3 = al3;
+  S.eta = -sn * S.eta;
+  S.s_old = S.s;
+  S.s = sn;
+  S.c_old = S.c;
+  S.c = cn;
+  S.gam_old = gam;
+  S.gam = gnew;
+  S.ig = gnew > T(0) ? T(1) / gnew : T(0);
+  S.pend = 1;
+  S.iters += 1;
+  const bool done = fabs(S.eta) <= tol * S.eta0 || gnew == T(0);
+  if (done) S.act = 0;  // leaves after the next K1
+  else atomicAdd(count, 1);
+}
+
+// samples that converged in the last Givens step leave the active set (K1 applied their update)
+template <typename T>
+__global__ void k_sc_retire(int B, int* act, SS<T>* ss) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B || !act[b]) return;
+  if (!ss[b].act) {
+    act[b] = 0;
+    ss[b].pend = 0;
+  }
+}
+
+// x64 += ||r|| xi for samples that ran an inner solve this step
+template <typename T>
+__global__ void k_outer_update(int n, int B, const SS<T>* __restrict__ ss, const int* __restrict__ ran,
+                               const T* __restrict__ xi, double* __restrict__ x64) {
+  const int nt = tiles_interior(n);
+  const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
+  if (b >= B || !ran[b]) return;
+  const size_t off = (size_t)b * gsz(n);
+  const double rn = ss[b].rnorm;
+  for_tile(n, ch, [&](int p, int, int) { x64[off + p] += rn * (double)xi[off + p]; });
+}
+
+// FP64 residual r = b - (A - sigma M) x64 (weights formed from the centroid coefficients); v = T(r)
+template <typename T>
+__global__ void k_residual(int n, int B, const int* __restrict__ ran, const double* __restrict__ a, size_t astride,
+                           const double* __restrict__ sigma, int sig_stride, const double* __restrict__ x64,
+                           const double* __restrict__ b64, T* __restrict__ v, double* part) {
+  const int nt = tiles_interior(n);
+  const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
+  if (b >= B || !ran[b]) return;
+  const int ld = n + 1;
+  const size_t off = (size_t)b * gsz(n);
+  const double hm = 1.0 / (12.0 * n * n);
+  const double sg = sigma[(size_t)b * sig_stride];
+  const double* ab = a + (size_t)b * astride;
+  const double* X = x64 + off;
+  double acc[1] = {0.0};
+  for_tile(n, ch, [&](int p, int i, int j) {
+    const double kx = stiff_cells(ab, n, X, p, ld, i, j) - sg * hm * mass7(X, p, ld);
+    const double r = b64[off + p] - kx;
+    v[off + p] = T(r);
+    acc[0] += r * r;
+  });
+  tile_partials<1, double>(acc, part, (size_t)b * nt + ch);
+}
+
+template <typename T>
+__global__ void k_sc_outer_end(int B, int nch, const double* part, const int* ran, SS<T>* ss) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B || !ran[b]) return;
+  double s = 0.0;
+  for (int k = 0; k < nch; ++k) s += part[(size_t)b * nch + k];
+  SS<T>& S = ss[b];
+  const double rnew = sqrt(s);
+  if (!(rnew < 0.5 * S.rnorm)) S.act_outer = 0;  // no progress: stop refining
+  S.rnorm = rnew;
+  S.rs = T(1.0 / rnew);
+  S.outer += 1;
+}
+
+// Rayleigh quotient partials x.Ax, x.Mx (FP64)
+template <typename T>
+__global__ void k_rq(int n, int B, const double* __restrict__ a, size_t astride, const double* __restrict__ x64,
+                     double* part) {
+  const int nt = tiles_interior(n);
+  const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
+  if (b >= B) return;
+  const int ld = n + 1;
+  const size_t off = (size_t)b * gsz(n);
+  const double hm = 1.0 / (12.0 * n * n);
+  const double* ab = a + (size_t)b * astride;
+  const double* X = x64 + off;
+  double acc[2] = {0.0, 0.0};
+  for_tile(n, ch, [&](int p, int i, int j) {
+    const double x = X[p];
+    acc[0] += x * stiff_cells(ab, n, X, p, ld, i, j);
+    acc[1] += x * hm * mass7(X, p, ld);
+  });
+  tile_partials<2, double>(acc, part, (size_t)b * nt + ch);
+}
+
+template <typename T>
+__global__ void k_sc_rq(int B, int nch, const double* part, const SS<T>* ss, double tol_lin, double* lam_out,
+                        int lam_stride, int* it_out, int it_stride, int* outer_out, int outer_stride, int* flags,
+                        int flag_stride) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  double s0 = 0.0, s1 = 0.0;
+  for (int k = 0; k < nch; ++k) {
+    s0 += part[((size_t)b * nch + k) * 2];
+    s1 += part[((size_t)b * nch + k) * 2 + 1];
+  }
+  const SS<T>& S = ss[b];
+  lam_out[(size_t)b * lam_stride] = s0 / s1;
+  it_out[(size_t)b * it_stride] = S.iters;
+  outer_out[(size_t)b * outer_stride] = S.outer;
+  int f = S.flags;
+  if (!(S.rnorm <= tol_lin * S.bnorm) && !(S.rnorm < 1e-6 * S.bnorm)) f |= kFlagLinNoConv;
+  flags[(size_t)b * flag_stride] |= f;
+}
+
+template <typename T>
+__global__ void k_zero(size_t count, T* p) {
+  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < count; q += (size_t)gridDim.x * blockDim.x)
+    p[q] = T(0);
+}
+
+template <typename T>
+__global__ void k_set_int(int B, int* p, int v) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < B) p[b] = v;
+}
+
+// ---------------------------------------------------------------------------------------------
+// host driver
+int grid1(size_t count) {
+  size_t g = (count + 255) / 256;
+  return (int)(g < 1 ? 1 : (g > 152 * 64 ? 152 * 64 : g));
+}
+
+template <typename T>
+struct Arena {
+  int n, B, Ls;  // Ls streaming multigrid levels (meshes n .. > kSub)
+  size_t V0;
+  T *v, *vo, *z, *zn, *w, *wo, *q, *xi;
+  double *x64, *b64;
+  T *wx[kMaxMG], *wy[kMaxMG], *dinv[kMaxMG], *x[kMaxMG], *t[kMaxMG], *b[kMaxMG];
+  T* cells[kMaxMG];  // per-triangle coefficients of streaming level l >= 1 and of the sub mesh
+  T *bsub, *xsub;
+  char* subw;  // per-sample operator arrays of the sub meshes
+  size_t subw_bytes;
+  double* part;
+  SS<T>* ss;
+  int *act, *ran, *count;
+};
+
+template <typename T>
+size_t carve_arena(void* base, int n, int B, Arena<T>& A) {
+  Carver c(base);
+  A.n = n;
+  A.B = B;
+  A.V0 = gsz(n);
+  const size_t Bz = (size_t)B;
+  A.v = c.take<T>(Bz * A.V0);
+  A.vo = c.take<T>(Bz * A.V0);
+  A.z = c.take<T>(Bz * A.V0);
+  A.zn = c.take<T>(Bz * A.V0);
+  A.w = c.take<T>(Bz * A.V0);
+  A.wo = c.take<T>(Bz * A.V0);
+  A.q = c.take<T>(Bz * A.V0);
+  A.xi = c.take<T>(Bz * A.V0);
+  A.x64 = c.take<double>(Bz * A.V0);
+  A.b64 = c.take<double>(Bz * A.V0);
+  A.Ls = 0;
+  for (int nl = n; nl > kSub; nl >>= 1) ++A.Ls;
+  for (int l = 0; l < (A.Ls > 1 ? A.Ls : 1); ++l) {  // level 0 always: the MINRES operator
+    const size_t V = gsz(n >> l);
+    A.wx[l] = c.take<T>(Bz * V);
+    A.wy[l] = c.take<T>(Bz * V);
+    A.dinv[l] = c.take<T>(Bz * V);
+    A.t[l] = l < A.Ls ? c.take<T>(Bz * V) : nullptr;
+    A.x[l] = l ? c.take<T>(Bz * V) : nullptr;
+    A.b[l] = l ? c.take<T>(Bz * V) : nullptr;
+  }
+  for (int l = 1; l <= A.Ls; ++l) {
+    const size_t nl = (size_t)(n >> l);
+    A.cells[l] = c.take<T>(Bz * 2 * nl * nl);
+  }
+  const int ns = n >> A.Ls;  // sub mesh (== n when n <= kSub)
+  if (A.Ls == 0) A.cells[0] = c.take<T>(Bz * 2 * (size_t)ns * ns);
+  A.bsub = A.Ls ? c.take<T>(Bz * gsz(ns)) : nullptr;
+  A.xsub = A.Ls ? c.take<T>(Bz * gsz(ns)) : nullptr;
+  A.subw_bytes = sub_weights_bytes<T>(ns);
+  A.subw = c.take<char>(Bz * A.subw_bytes + 256);
+  A.subw = (char*)(((uintptr_t)A.subw + 255) & ~(uintptr_t)255);
+  const int nch = tiles_interior(n) > 1 ? tiles_interior(n) : 1;
+  A.part = c.take<double>(Bz * nch * 2 + Bz);
+  A.ss = c.take<SS<T>>(Bz);
+  A.act = c.take<int>(Bz);
+  A.ran = c.take<int>(Bz);
+  A.count = c.take<int>(4);
+  return c.used();
+}
+
+#define LAUNCH_CHECK()                          \
+  do {                                          \
+    cudaError_t e_ = cudaGetLastError();        \
+    if (e_ != cudaSuccess) return e_;           \
+  } while (0)
+
+// V-cycle over the arena hierarchy: x0 = B^{-1} b0; with dotv, partial <dotv, x0> into part
+template <typename T>
+cudaError_t vcycle_stream(Arena<T>& A, const T* b0, T* x0, const int* act, T om, const T* dotv, double* part,
+                          size_t sub_smem, cudaStream_t st) {
+  const int n = A.n, B = A.B;
+  if (A.Ls == 0) {
+    k_subcycle<T><<<B, kThreads, sub_smem, st>>>(n, B, act, A.subw, A.subw_bytes, b0, x0, 2, om, part, dotv);
+    LAUNCH_CHECK();
+    return cudaSuccess;
+  }
+  for (int l = 0; l < A.Ls; ++l) {
+    const int nl = n >> l;
+    const T* b = l ? A.b[l] : b0;
+    T* xa = l ? A.x[l] : x0;
+    k_smooth2_from_zero<T><<<B * tiles_interior(nl), kThreads, 0, st>>>(nl, B, act, A.wx[l], A.wy[l], A.dinv[l],
+                                                                       b, xa, om);
+    LAUNCH_CHECK();
+    T* bc = (l + 1 < A.Ls) ? A.b[l + 1] : A.bsub;
+    k_restrict<T><<<B * tiles_interior(nl / 2), kThreads, 0, st>>>(nl, B, act, A.wx[l], A.wy[l], b, xa, bc);
+    LAUNCH_CHECK();
+  }
+  const int ns = n >> A.Ls;
+  k_subcycle<T><<<B, kThreads, sub_smem, st>>>(ns, B, act, A.subw, A.subw_bytes, A.bsub, A.xsub, 2, om, nullptr,
+                                                nullptr);
+  LAUNCH_CHECK();
+  for (int l = A.Ls - 1; l >= 0; --l) {
+    const int nl = n >> l;
+    const T* b = l ? A.b[l] : b0;
+    T* xa = l ? A.x[l] : x0;
+    const T* xc = (l + 1 < A.Ls) ? A.x[l + 1] : A.xsub;
+    k_prolong_smooth<T><<<B * tiles_interior(nl), kThreads, 0, st>>>(nl, B, act, A.wx[l], A.wy[l], A.dinv[l], b,
+                                                                    xa, xc, A.t[l], om);
+    LAUNCH_CHECK();
+    if (l == 0 && dotv)
+      k_smooth<T, true><<<B * tiles_interior(nl), kThreads, 0, st>>>(nl, B, act, A.wx[l], A.wy[l], A.dinv[l], b,
+                                                                    A.t[l], xa, om, dotv, part);
+    else
+      k_smooth<T, false><<<B * tiles_interior(nl), kThreads, 0, st>>>(nl, B, act, A.wx[l], A.wy[l], A.dinv[l], b,
+                                                                     A.t[l], xa, om, nullptr, nullptr);
+    LAUNCH_CHECK();
+  }
+  return cudaSuccess;
+}
+
+int read_count(const int* d_count, cudaStream_t st, cudaError_t& err) {
+  int h = 0;
+  err = cudaMemcpyAsync(&h, d_count, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+  return h;
+}
+
+template <typename T>
+cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st) {
+  Arena<T> A;
+  carve_arena<T>(arena, s.n, s.B, A);
+  const int n = s.n, B = s.B;
+  const int nt = tiles_interior(n);
+  const size_t Bz = (size_t)B;
+  const T om = T(s.omega);
+  const int ns = n >> A.Ls;
+  const size_t sub_smem = sub_vectors_bytes<T>(ns);
+  cudaError_t e = cudaFuncSetAttribute(k_subcycle<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sub_smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_sub_build<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sub_smem);
+  if (e != cudaSuccess) return e;
+  const int gs = (B + 255) / 256;
+  // ---- clear vectors (boundary rings must be zero), build the operators
+  const size_t V0 = A.V0;
+  T* const vecs[8] = {A.v, A.vo, A.z, A.zn, A.w, A.wo, A.q, A.xi};
+  for (int k = 0; k < 8; ++k) {
+    k_zero<T><<<grid1(Bz * V0), 256, 0, st>>>(Bz * V0, vecs[k]);
+    LAUNCH_CHECK();
+  }
+  k_zero<double><<<grid1(Bz * V0), 256, 0, st>>>(Bz * V0, A.x64);
+  k_zero<double><<<grid1(Bz * V0), 256, 0, st>>>(Bz * V0, A.b64);
+  for (int l = 0; l < A.Ls; ++l) {
+    const size_t V = gsz(n >> l);
+    T* const lv[3] = {A.t[l], A.x[l], A.b[l]};
+    for (int k = 0; k < 3; ++k)
+      if (lv[k]) k_zero<T><<<grid1(Bz * V), 256, 0, st>>>(Bz * V, lv[k]);
+  }
+  if (A.Ls) {
+    k_zero<T><<<grid1(Bz * gsz(ns)), 256, 0, st>>>(Bz * gsz(ns), A.bsub);
+    k_zero<T><<<grid1(Bz * gsz(ns)), 256, 0, st>>>(Bz * gsz(ns), A.xsub);
+  }
+  k_zero<int><<<grid1(Bz * sizeof(SS<T>) / sizeof(int)), 256, 0, st>>>(Bz * sizeof(SS<T>) / sizeof(int), (int*)A.ss);
+  LAUNCH_CHECK();
+  const size_t astride = (size_t)2 * n * n;
+  for (int l = 0; l < (A.Ls > 1 ? A.Ls : 1); ++l) {
+    const int nl = n >> l;
+    if (l == 0)
+      k_weights<T, double><<<B * tiles_padded(nl), kThreads, 0, st>>>(nl, B, s.a, astride, A.wx[0], A.wy[0],
+                                                                     A.dinv[0], nullptr, A.ss);
+    else
+      k_weights<T, T><<<B * tiles_padded(nl), kThreads, 0, st>>>(nl, B, A.cells[l], (size_t)2 * nl * nl, A.wx[l],
+                                                                A.wy[l], A.dinv[l], nullptr, nullptr);
+    LAUNCH_CHECK();
+    if (l >= A.Ls) continue;
+    const int m = nl / 2;
+    const int ntc = (int)(((size_t)m * m + kTile - 1) / kTile);
+    if (l == 0)
+      k_coarsen<double, T><<<B * ntc, kThreads, 0, st>>>(nl, B, s.a, astride, A.cells[1]);
+    else
+      k_coarsen<T, T><<<B * ntc, kThreads, 0, st>>>(nl, B, A.cells[l], (size_t)2 * nl * nl, A.cells[l + 1]);
+    LAUNCH_CHECK();
+  }
+  if (A.Ls == 0) {
+    k_convert<double, T><<<grid1(Bz * astride), 256, 0, st>>>(Bz * astride, s.a, A.cells[0]);
+    LAUNCH_CHECK();
+  }
+  k_sub_build<T><<<B, kThreads, sub_smem, st>>>(ns, B, A.cells[A.Ls], A.subw, A.subw_bytes);
+  LAUNCH_CHECK();
+  // ---- right-hand side b = M P u_H
+  k_interp<T><<<B * nt, kThreads, 0, st>>>(n, s.nc, B, s.uH, A.x64);
+  LAUNCH_CHECK();
+  k_rhs<T><<<B * nt, kThreads, 0, st>>>(n, B, A.x64, A.b64, A.v, A.part);
+  LAUNCH_CHECK();
+  k_zero<double><<<grid1(Bz * V0), 256, 0, st>>>(Bz * V0, A.x64);
+  k_sc_start<T><<<gs, 256, 0, st>>>(B, nt, A.part, A.ss);
+  LAUNCH_CHECK();
+  // ---- refinement loop
+  for (int o = 0; o < s.max_outer; ++o) {
+    cudaMemsetAsync(A.count, 0, sizeof(int), st);
+    k_sc_outer_begin<T><<<gs, 256, 0, st>>>(B, s.tol_lin, A.ss, A.act, A.count);
+    LAUNCH_CHECK();
+    int active = read_count(A.count, st, e);
+    if (e != cudaSuccess) return e;
+    if (active == 0) break;
+    cudaMemcpyAsync(A.ran, A.act, Bz * sizeof(int), cudaMemcpyDeviceToDevice, st);
+    k_inner_init<T><<<B * nt, kThreads, 0, st>>>(n, B, A.act, A.ss, A.v, A.vo, A.w, A.wo, A.xi);
+    LAUNCH_CHECK();
+    T *v = A.v, *vo = A.vo, *z = A.z, *zn = A.zn, *w = A.w, *wo = A.wo;
+    e = vcycle_stream<T>(A, v, z, A.act, om, v, A.part, sub_smem, st);
+    if (e != cudaSuccess) return e;
+    const int nchd = A.Ls ? nt : 1;  // partial slots of <v, z>
+    k_sc_gamma0<T><<<gs, 256, 0, st>>>(B, nchd, A.part, A.act, A.ss);
+    LAUNCH_CHECK();
+    for (int j = 0; j < s.max_inner; ++j) {
+      k_minres_q<T><<<B * nt, kThreads, 0, st>>>(n, B, A.act, A.ss, A.wx[0], A.wy[0], s.lamH, s.lam_stride, z, zn,
+                                                 wo, w, A.xi, A.q, A.part);
+      LAUNCH_CHECK();
+      // samples that converged in the previous Givens step have now applied their update
+      k_sc_retire<T><<<gs, 256, 0, st>>>(B, A.act, A.ss);
+      { T* tt = wo; wo = w; w = tt; }
+      k_sc_delta<T><<<gs, 256, 0, st>>>(B, nt, A.part, A.act, A.ss);
+      k_minres_v<T><<<B * nt, kThreads, 0, st>>>(n, B, A.act, A.ss, A.q, v, vo, z);
+      LAUNCH_CHECK();
+      { T* tt = vo; vo = v; v = tt; }
+      e = vcycle_stream<T>(A, v, zn, A.act, om, v, A.part, sub_smem, st);
+      if (e != cudaSuccess) return e;
+      cudaMemsetAsync(A.count, 0, sizeof(int), st);
+      k_sc_givens<T><<<gs, 256, 0, st>>>(B, nchd, A.part, A.act, A.ss, T(s.tol_inner), A.count);
+      LAUNCH_CHECK();
+      { T* tt = z; z = zn; zn = tt; }
+      if ((j & 3) == 3 || j + 1 == s.max_inner) {
+        active = read_count(A.count, st, e);
+        if (e != cudaSuccess) return e;
+        if (active == 0) break;
+      }
+    }
+    // apply the pending updates of every sample that ran this step (converged or capped)
+    k_minres_finish<T><<<B * nt, kThreads, 0, st>>>(n, B, A.ran, A.ss, zn, wo, w, A.xi);
+    LAUNCH_CHECK();
+    k_outer_update<T><<<B * nt, kThreads, 0, st>>>(n, B, A.ss, A.ran, A.xi, A.x64);
+    k_residual<T><<<B * nt, kThreads, 0, st>>>(n, B, A.ran, s.a, astride, s.lamH, s.lam_stride, A.x64, A.b64, A.v,
+                                               A.part);
+    k_sc_outer_end<T><<<gs, 256, 0, st>>>(B, nt, A.part, A.ran, A.ss);
+    LAUNCH_CHECK();
+  }
+  // ---- Rayleigh quotient
+  k_rq<T><<<B * nt, kThreads, 0, st>>>(n, B, s.a, astride, A.x64, A.part);
+  k_sc_rq<T><<<gs, 256, 0, st>>>(B, nt, A.part, A.ss, s.tol_lin, s.lam_out, s.lam_out_stride, s.iters_out,
+                                 s.iters_stride, s.outer_out, s.outer_stride, s.flags, s.flags_stride);
+  LAUNCH_CHECK();
+  return cudaSuccess;
+}
+
+// level difference lambda^l - lambda^{l-1} (lambda^{-1} = 0 without a previous level)
+__global__ void k_finalize(int B, double* out, int has_prev) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  out[(size_t)b * 4 + 3] = out[(size_t)b * 4 + 1] - (has_prev ? out[(size_t)b * 4 + 2] : 0.0);
+}
+
+}  // namespace
+
+cudaError_t launch_finalize(int B, double* d_out, int has_prev, cudaStream_t st) {
+  if (B == 0) return cudaSuccess;
+  k_finalize<<<(B + 255) / 256, 256, 0, st>>>(B, d_out, has_prev);
+  return cudaGetLastError();
+}
+
+size_t stream_arena_bytes(int n, int B, int mixed) {
+  if (mixed) {
+    Arena<float> A;
+    return carve_arena<float>(nullptr, n, B, A) + 256;
+  }
+  Arena<double> A;
+  return carve_arena<double>(nullptr, n, B, A) + 256;
+}
+
+cudaError_t stream_solve(const StreamSolve& s, int mixed, void* arena, cudaStream_t st) {
+  return mixed ? stream_solve_t<float>(s, arena, st) : stream_solve_t<double>(s, arena, st);
+}
+
+}  // namespace mq

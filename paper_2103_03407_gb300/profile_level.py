@@ -24,6 +24,7 @@ def main():
     ap.add_argument("--points", type=int, default=64)
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--stream-min", type=int, default=0, help="fine meshes from 1/n on run in the streaming tier")
     a = ap.parse_args()
     from paper_2103_03407_gb300 import binding, build
     from synthetic_inputs import WORKLOADS, shifts
@@ -38,12 +39,14 @@ def main():
         ctx.mq_set_lattice(l, binding.mq_cbc_lattice(lv.N, lv.s, wl.decay))
         ctx.mq_set_shifts(l, ds[l])
     ctx.mq_set_precision(binding.MQ_PREC_MIXED if a.precision == "mixed" else binding.MQ_PREC_FP64)
+    if a.stream_min:
+        ctx.mq_set_tier(a.stream_min)
     for l in a.level or [len(wl.levels) - 1]:
         n = min(a.points, wl.levels[l].N)
         for _ in range(a.repeat):
             ctx.mq_eval_level(l, 0, n, per_sample=False)
             st = ctx.mq_get_stats()
-            print(json.dumps({"level": l, "points": n, "samples": n * wl.levels[l].R, **st}))
+            print(json.dumps({"level": l, "points": n, "samples": n * wl.levels[l].R, "stream_min": a.stream_min, **st}))
     ctx.close()
 
 

@@ -227,3 +227,21 @@ def test_nonpositive_coefficient_is_rejected(B):
     with pytest.raises(B.MQError) as e:
         ctx.mq_eval_point(0, np.full(16, -0.5))
     assert e.value.status == B.MQ_EINVAL
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_tiers_agree_and_match_oracle(B, prec):
+    # every fine solve forced into the batched streaming tier (meshes 1/16 .. 1/64, including the
+    # tier's single-CTA path for meshes up to 1/32) versus forced into the per-sample kernel
+    levels = [Level(16, 8, 16, 4, 32, 3), Level(32, 8, 32, 6, 32, 3), Level(64, 16, 64, 8, 32, 3)]
+    ctx_s, zs, ds = make_ctx(B, levels, seed=11, prec=prec)
+    ctx_c, _, _ = make_ctx(B, levels, seed=11, prec=prec)
+    ctx_s.mq_set_tier(2)
+    ctx_c.mq_set_tier(4096)
+    for l in range(3):
+        k0, k1 = 5, 9
+        ps_s, _ = ctx_s.mq_eval_level(l, k0, k1)
+        ps_c, _ = ctx_c.mq_eval_level(l, k0, k1)
+        assert np.all(np.abs(ps_s[..., 1:3] - ps_c[..., 1:3]) <= 1e-10 * np.abs(ps_c[..., 1:3]) + 1e-300)
+        ref = mlqmc.level_samples(levels[l], levels[l - 1] if l else None, zs[l], ds[l], list(range(k0, k1)))
+        _check_level(ps_s, ref)
