@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 OBJDIR = os.path.join(LIBDIR, "obj")
 LIB = os.path.join(LIBDIR, "libmlqmc_evp.so")
-SOURCES = ["mq_api.cu", "mq_coef.cu", "mq_sample.cu", "mq_stream.cu", "mq_noalloc.cu"]
+SOURCES = ["mq_api.cu", "mq_coef.cu", "mq_tc.cu", "mq_sample.cu", "mq_stream.cu", "mq_noalloc.cu"]
 HEADERS = [os.path.join(CSRC, "mq_internal.h"), os.path.join(CSRC, "mq_device.cuh"), os.path.join(ROOT, "include", "mlqmc_evp.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

@@ -56,8 +56,9 @@ struct mq_ctx {
   int opt_max_inner = 0, opt_max_outer = 0;
 
   std::map<int, std::pair<int, double*>> psi;  // mesh n -> (rows, table [rows][2n^2])
+  std::map<int, std::pair<int, void*>> psi_sl;  // mesh n -> (K pad, BF16 slices [6][nT pad][K pad])
 
-  DevBuf Y, af, ac, ap, out, stat, outer, scratch, sums_d, flags_d, uout, misc, upad, arena;
+  DevBuf Y, af, ac, ap, out, stat, outer, scratch, sums_d, flags_d, uout, misc, upad, arena, ysl, tc_err;
   int stream_min = 0;  // fine meshes 1/n with n >= stream_min use the streaming tier (0: default)
   mq_stats stats{};
   size_t last_B = 0;  // samples of the last pass (their per-sample counters are still on the device)
@@ -138,6 +139,64 @@ mq_status ensure_psi(mq_ctx* c, int n, int rows, const double** out) {
   return MQ_OK;
 }
 
+// BF16 slices of the Psi table of mesh n for the tensor-core path (cached per mesh)
+mq_status ensure_psi_slices(mq_ctx* c, int n, const void** out, int* kpad) {
+  auto it = c->psi_sl.find(n);
+  const int rows = std::max(c->s_max, 1);
+  if (it != c->psi_sl.end()) {
+    *out = it->second.second;
+    *kpad = it->second.first;
+    return MQ_OK;
+  }
+  const double* psi = nullptr;
+  mq_status st = ensure_psi(c, n, rows, &psi);
+  if (st != MQ_OK) return st;
+  const int nT = 2 * n * n;
+  void* d = nullptr;
+  const size_t bytes = mq::tc_slices_bytes(nT, rows);
+  if (cudaMalloc(&d, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, MQ_ENOMEM, "psi slices for n=%d (%zu bytes)", n, bytes);
+  }
+  MQ_CUDA(c, mq::launch_psi_slices(psi, rows, nT, d, c->stream));
+  c->psi_sl[n] = {mq::tc_pad_k(rows), d};
+  *out = d;
+  *kpad = mq::tc_pad_k(rows);
+  return MQ_OK;
+}
+
+// a[b][t] = a0 + sum_{j<K} Y[b][j] psi_j(c_t) for B rows of Y (stride ldy) on mesh n: FP64 GEMM in
+// MQ_PREC_FP64, tensor-core split GEMM in MQ_PREC_MIXED
+mq_status coefficients(mq_ctx* c, int n, int K, const double* d_Y, int B, int ldy, double* d_a) {
+  const int nT = 2 * n * n;
+  if (c->prec == MQ_PREC_MIXED && K > 0) {
+    const void* ps = nullptr;
+    int kps = 0;
+    mq_status st = ensure_psi_slices(c, n, &ps, &kps);
+    if (st != MQ_OK) return st;
+    const int kpad = mq::tc_pad_k(K);
+    if ((st = grow(c, c->ysl, mq::tc_slices_bytes(B, K))) != MQ_OK) return st;
+    if ((st = grow(c, c->tc_err, sizeof(int))) != MQ_OK) return st;
+    MQ_CUDA(c, mq::launch_y_slices(d_Y, B, ldy, K, kpad, c->ysl.p, c->stream));
+    MQ_CUDA(c, mq::launch_coef_tc(c->ysl.p, B, kpad, ps, nT, kps, c->a0, d_a, (int*)c->tc_err.p, c->stream));
+    return MQ_OK;
+  }
+  const double* psi = nullptr;
+  mq_status st = ensure_psi(c, n, std::max(c->s_max, 1), &psi);
+  if (st != MQ_OK) return st;
+  MQ_CUDA(c, mq::launch_coef_gemm_f64(d_Y, ldy, B, K, psi, nT, c->a0, d_a, c->stream));
+  return MQ_OK;
+}
+
+mq_status check_tc_error(mq_ctx* c) {
+  if (c->prec != MQ_PREC_MIXED || !c->tc_err.p) return MQ_OK;
+  int e = 0;
+  MQ_CUDA(c, cudaMemcpyAsync(&e, c->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  MQ_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (e) return fail(c, MQ_ETIMEOUT, "a bounded wait in the tensor-core coefficient kernel ran out");
+  return MQ_OK;
+}
+
 mq_status check_level_ready(mq_ctx* c, int level) {
   if (!c->coef_set) return fail(c, MQ_ESTATE, "coefficient not set");
   if (c->levels.empty()) return fail(c, MQ_ESTATE, "levels not set");
@@ -183,13 +242,7 @@ LevelGeom geom(const mq_ctx* c, int level) {
 // Writes c->out / c->stat / c->outer; returns timings in stats.
 mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk, bool want_u) {
   const size_t B = (size_t)R * npts;
-  const double* psi_f = nullptr;
-  const double* psi_c = nullptr;
-  const double* psi_p = nullptr;
   mq_status st;
-  if ((st = ensure_psi(c, g.nc, c->s_max, &psi_c)) != MQ_OK) return st;
-  if (!g.direct_f && (st = ensure_psi(c, g.nf, c->s_max, &psi_f)) != MQ_OK) return st;
-  if (g.np && !g.direct_p && (st = ensure_psi(c, g.np, c->s_max, &psi_p)) != MQ_OK) return st;
   const size_t nTf = (size_t)2 * g.nf * g.nf, nTc = (size_t)2 * g.nc * g.nc, nTp = (size_t)2 * g.np * g.np;
   if ((st = grow(c, c->ac, B * nTc * sizeof(double))) != MQ_OK) return st;
   if (!g.direct_f && (st = grow(c, c->af, B * nTf * sizeof(double))) != MQ_OK) return st;
@@ -200,13 +253,12 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
   if (want_u && (st = grow(c, c->uout, B * (size_t)(g.nc - 1) * (g.nc - 1) * sizeof(double))) != MQ_OK) return st;
 
   const int mixed = c->prec == MQ_PREC_MIXED;
+  if (c->prec == MQ_PREC_MIXED && c->tc_err.p) MQ_CUDA(c, cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), c->stream));
   MQ_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
   const double* Y = (const double*)c->Y.p;
-  MQ_CUDA(c, mq::launch_coef_gemm_f64(Y, g.s, (int)B, g.S, psi_c, (int)nTc, c->a0, (double*)c->ac.p, c->stream));
-  if (!g.direct_f)
-    MQ_CUDA(c, mq::launch_coef_gemm_f64(Y, g.s, (int)B, g.s, psi_f, (int)nTf, c->a0, (double*)c->af.p, c->stream));
-  if (g.np && !g.direct_p)
-    MQ_CUDA(c, mq::launch_coef_gemm_f64(Y, g.s, (int)B, g.sp, psi_p, (int)nTp, c->a0, (double*)c->ap.p, c->stream));
+  if ((st = coefficients(c, g.nc, g.S, Y, (int)B, g.s, (double*)c->ac.p)) != MQ_OK) return st;
+  if (!g.direct_f && (st = coefficients(c, g.nf, g.s, Y, (int)B, g.s, (double*)c->af.p)) != MQ_OK) return st;
+  if (g.np && !g.direct_p && (st = coefficients(c, g.np, g.sp, Y, (int)B, g.s, (double*)c->ap.p)) != MQ_OK) return st;
   MQ_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
 
   mq::SampleLaunch p{};
@@ -443,6 +495,7 @@ mq_status eval_level_impl(mq_ctx* c, int level, uint32_t k0, uint32_t k1, double
     }
     MQ_CUDA(c, cudaStreamSynchronize(c->stream));
     if ((st = timing(c, level)) != MQ_OK) return st;
+    if ((st = check_tc_error(c)) != MQ_OK) return st;
     if (per_sample) {
       for (int r = 0; r < R; ++r)
         std::memcpy(per_sample + ((size_t)r * npts + p0) * 4, host_out.data() + (size_t)r * pn * 4,
@@ -509,9 +562,10 @@ mq_status mq_destroy(mq_ctx* c) {
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
   for (DevBuf* b : {&c->Y, &c->af, &c->ac, &c->ap, &c->out, &c->stat, &c->outer, &c->scratch, &c->sums_d,
-                    &c->flags_d, &c->uout, &c->misc, &c->upad, &c->arena})
+                    &c->flags_d, &c->uout, &c->misc, &c->upad, &c->arena, &c->ysl, &c->tc_err})
     if (b->p) cudaFree(b->p);
   for (auto& kv : c->psi) cudaFree(kv.second.second);
+  for (auto& kv : c->psi_sl) cudaFree(kv.second.second);
   for (auto p : c->d_z)
     if (p) cudaFree(p);
   for (auto p : c->d_delta)
@@ -541,6 +595,8 @@ mq_status mq_set_coefficient(mq_ctx* c, double a0, int32_t s_max, int32_t family
   for (int j = 0; j < (int)cj.size(); ++j) cj[j] = std::pow((double)(j + 1), -decay);
   for (auto& kv : c->psi) cudaFree(kv.second.second);
   c->psi.clear();
+  for (auto& kv : c->psi_sl) cudaFree(kv.second.second);
+  c->psi_sl.clear();
   if (c->d_k1) cudaFree(c->d_k1);
   if (c->d_k2) cudaFree(c->d_k2);
   if (c->d_cj) cudaFree(c->d_cj);
@@ -733,6 +789,7 @@ mq_status mq_eval_point(mq_ctx* c, int32_t level, const double* y, double* lam_H
                                cudaMemcpyDeviceToHost, c->stream));
   MQ_CUDA(c, cudaStreamSynchronize(c->stream));
   if ((st = timing(c, -1)) != MQ_OK) return st;
+  if ((st = check_tc_error(c)) != MQ_OK) return st;
   int fl = 0;
   c->last_B = 1;
   if ((st = collect_stats(c, 1, &fl)) != MQ_OK) return st;
@@ -802,12 +859,11 @@ mq_status mq_coefficients_device(mq_ctx* c, int32_t n, int32_t s, const double* 
   if (!pow2(n) || n < 2 || n > 4096 || s < 0 || s > c->s_max || B < 0 || ldy < s || (!d_Y && B * s) || (!d_a && B))
     return fail(c, MQ_EINVAL, "bad coefficient arguments");
   MQ_CUDA(c, cudaSetDevice(c->device));
-  const double* psi = nullptr;
-  mq_status st = ensure_psi(c, n, std::max(c->s_max, 1), &psi);
+  if (c->prec == MQ_PREC_MIXED && c->tc_err.p) MQ_CUDA(c, cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), c->stream));
+  mq_status st = coefficients(c, n, s, d_Y, B, ldy, d_a);
   if (st != MQ_OK) return st;
-  MQ_CUDA(c, mq::launch_coef_gemm_f64(d_Y, ldy, B, s, psi, 2 * n * n, c->a0, d_a, c->stream));
   MQ_CUDA(c, cudaStreamSynchronize(c->stream));
-  return MQ_OK;
+  return check_tc_error(c);
 }
 
 mq_status mq_apply_operator_device(mq_ctx* c, int32_t n, int32_t B, const double* d_a, int32_t which, double sigma,

@@ -60,6 +60,15 @@ size_t stream_arena_bytes(int n, int B, int mixed);
 cudaError_t stream_solve(const StreamSolve& s, int mixed, void* arena, cudaStream_t st);
 cudaError_t launch_finalize(int B, double* d_out, int has_prev, cudaStream_t st);
 
+// Tensor-core (tcgen05) coefficient GEMM with exact BF16 slices (mq_tc.cu); slices are [7][rows pad][K pad]
+size_t tc_slices_bytes(int rows, int k);
+int tc_pad_rows(int rows);
+int tc_pad_k(int k);
+cudaError_t launch_psi_slices(const double* d_psi, int s_rows, int nT, void* d_out, cudaStream_t st);
+cudaError_t launch_y_slices(const double* d_Y, int B, int ldy, int k, int kpad, void* d_out, cudaStream_t st);
+cudaError_t launch_coef_tc(const void* d_yslices, int B, int kpad, const void* d_pslices, int nT, int kpad_psi,
+                           double a0, double* d_a, int* d_err, cudaStream_t st);
+
 // Sample flags (stat[b][3])
 enum : int {
   kFlagEigNoConv = 1,

@@ -65,6 +65,21 @@ def test_coefficients_match_oracle(B, n, s):
         assert np.abs(got[b] - fem.coefficient(n, Y[b])).max() < 1e-14
 
 
+@pytest.mark.parametrize("n,s,nb", [(2, 1, 3), (8, 16, 5), (16, 37, 130), (32, 128, 200), (16, 300, 7)])
+def test_tensor_core_coefficients_match_oracle(B, n, s, nb):
+    # mixed precision: exact BF16 slices on tcgen05 tensor cores, FP64-accurate result; ragged
+    # sample counts (130, 200: two 128-row tiles), K not a multiple of 16 (37), several 128-wide
+    # exact accumulation chunks (300)
+    ctx, _, _ = make_ctx(B, [Level(n, n, s, s, 8, 2)], prec=1)
+    Y = random_points(n + s + nb, nb, s)
+    dY = torch.from_numpy(Y).cuda()
+    da = torch.empty((nb, 2 * n * n), dtype=torch.float64, device="cuda")
+    ctx.mq_coefficients_device(n, s, dY, nb, s, da)
+    got = da.cpu().numpy()
+    ref = np.stack([fem.coefficient(n, Y[b]) for b in range(nb)])
+    assert np.abs(got - ref).max() < 5e-15
+
+
 @pytest.mark.parametrize("n", [2, 4, 8, 16, 64])
 def test_operator_apply_matches_assembled_matrices(B, n):
     ctx, _, _ = make_ctx(B, [Level(8, 8, 1, 1, 8, 2)])
