@@ -21,32 +21,35 @@ import numpy as np
 import scipy.sparse as sp
 
 
+_MESH_CACHE: dict = {}
+
+
 def mesh(n: int):
     """Return (coords [(n+1)^2, 2], triangles [2n^2, 3] vertex ids, interior map).
 
     Node id = j*(n+1) + i.  Triangle t = p*n*n + j*n + i with p = 0 for the lower and
     p = 1 for the upper triangle of cell (i, j).  ``interior[id]`` is the unknown
-    number of a node, or -1 on the boundary.
+    number of a node, or -1 on the boundary.  (Cached per mesh.)
     """
+    if n in _MESH_CACHE:
+        return _MESH_CACHE[n]
     h = 1.0 / n
     idx = np.arange(n + 1)
     I, J = np.meshgrid(idx, idx, indexing="xy")  # I[j, i] = i
     coords = np.stack([I.ravel() * h, J.ravel() * h], axis=1)
+    jj, ii = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")  # cell (i, j) at [j, i]
 
     def nid(i, j):
         return j * (n + 1) + i
 
-    tris = np.zeros((2, n, n, 3), dtype=np.int64)
-    for j in range(n):
-        for i in range(n):
-            tris[0, j, i] = (nid(i, j), nid(i + 1, j), nid(i + 1, j + 1))
-            tris[1, j, i] = (nid(i, j), nid(i + 1, j + 1), nid(i, j + 1))
-    tris = tris.reshape(-1, 3)
+    low = np.stack([nid(ii, jj), nid(ii + 1, jj), nid(ii + 1, jj + 1)], axis=-1)
+    up = np.stack([nid(ii, jj), nid(ii + 1, jj + 1), nid(ii, jj + 1)], axis=-1)
+    tris = np.concatenate([low.reshape(-1, 3), up.reshape(-1, 3)], axis=0).astype(np.int64)
 
     interior = -np.ones((n + 1) * (n + 1), dtype=np.int64)
-    for j in range(1, n):
-        for i in range(1, n):
-            interior[nid(i, j)] = (j - 1) * (n - 1) + (i - 1)
+    jj, ii = np.meshgrid(np.arange(1, n), np.arange(1, n), indexing="ij")
+    interior[nid(ii, jj).ravel()] = ((jj - 1) * (n - 1) + (ii - 1)).ravel()
+    _MESH_CACHE[n] = (coords, tris, interior)
     return coords, tris, interior
 
 
@@ -90,12 +93,22 @@ def _psi_matrix(n: int, s: int, decay: float) -> np.ndarray:
 def coefficient(n: int, y: np.ndarray, a0: float = 1.0, decay: float = 2.0) -> np.ndarray:
     """a(c_t, y) = a0 + sum_{j<=s} y_j psi_j(c_t) for every triangle t (eq. coeff, eq. coeff_s).
 
-    The truncation dimension is len(y): terms beyond it are zero.
+    The truncation dimension is len(y): terms beyond it are zero.  Small meshes use the cached
+    Psi matrix; large ones add the terms one by one (same formula, no s x 2n^2 matrix in memory).
     """
     y = np.asarray(y, dtype=np.float64)
     if y.size == 0:
         return np.full(2 * n * n, float(a0))
-    return a0 + psi_matrix(n, y.size, decay) @ y
+    if y.size * 2 * n * n <= (1 << 25):
+        return a0 + psi_matrix(n, y.size, decay) @ y
+    c = centroids(n)
+    a = np.full(c.shape[0], float(a0))
+    # sin(pi k x) only depends on k and on the 2n distinct centroid abscissae (ordinates)
+    xs, xi = np.unique(c[:, 0], return_inverse=True)
+    ys, yi = np.unique(c[:, 1], return_inverse=True)
+    for j, (k1, k2) in enumerate(psi_pairs(y.size), start=1):
+        a += y[j - 1] * j ** (-decay) * np.sin(np.pi * k1 * xs)[xi] * np.sin(np.pi * k2 * ys)[yi]
+    return a
 
 
 def element_matrices(coords: np.ndarray, tri: np.ndarray):
@@ -117,30 +130,27 @@ _ELEMENT_CACHE: dict = {}
 def _element_entries(n: int, with_boundary: bool):
     """Element loop over all triangles: for every local (a, b) pair whose two nodes are
     unknowns, record (row, col, triangle, K_ab for a = 1, M_ab).  The geometric part does
-    not depend on the coefficient, so it is cached per mesh."""
+    not depend on the coefficient, so it is cached per mesh.  The per-element matrices are
+    computed for all triangles at once (the same formulas as element_matrices)."""
     key = (n, with_boundary)
     if key in _ELEMENT_CACHE:
         return _ELEMENT_CACHE[key]
     coords, tris, interior = mesh(n)
-    rows, cols, tt, kv, mv = [], [], [], [], []
-    for t in range(tris.shape[0]):
-        K, Mloc = element_matrices(coords, tris[t])
-        for a in range(3):
-            ga = tris[t, a]
-            ra = ga if with_boundary else interior[ga]
-            if ra < 0:
-                continue
-            for b in range(3):
-                gb = tris[t, b]
-                cb = gb if with_boundary else interior[gb]
-                if cb < 0:
-                    continue
-                rows.append(ra)
-                cols.append(cb)
-                tt.append(t)
-                kv.append(K[a, b])
-                mv.append(Mloc[a, b])
-    ent = tuple(np.asarray(v) for v in (rows, cols, tt, kv, mv))
+    p = coords[tris]  # [nt, 3, 2]
+    Bm = np.stack([p[:, 1] - p[:, 0], p[:, 2] - p[:, 0]], axis=2)  # columns: edge vectors
+    area = 0.5 * np.abs(np.linalg.det(Bm))
+    ref_grad = np.array([[-1.0, -1.0], [1.0, 0.0], [0.0, 1.0]])
+    G = np.einsum("ak,tkd->tad", ref_grad, np.linalg.inv(Bm))  # physical gradients
+    K = area[:, None, None] * np.einsum("tad,tbd->tab", G, G)
+    Mloc = (area[:, None, None] / 12.0) * (np.ones((3, 3)) + np.eye(3))[None]
+    nt = tris.shape[0]
+    ga = np.repeat(tris, 3, axis=1).reshape(nt, 3, 3)  # [t, a, b] -> node of a
+    gb = np.tile(tris, (1, 3)).reshape(nt, 3, 3)  # [t, a, b] -> node of b
+    ra = ga if with_boundary else interior[ga]
+    cb = gb if with_boundary else interior[gb]
+    keep = (ra >= 0) & (cb >= 0)
+    tt = np.broadcast_to(np.arange(nt)[:, None, None], (nt, 3, 3))
+    ent = (ra[keep], cb[keep], tt[keep], K[keep], Mloc[keep])
     _ELEMENT_CACHE[key] = ent
     return ent
 

@@ -112,8 +112,10 @@ def twogrid_update(n_fine: int, y_fine: np.ndarray, lam_H: float, u_H: np.ndarra
     b = M @ Pu
     K = (A - lam_H * M).tocsc()
     w = spla.splu(K).solve(b)
+    # sanity check of the direct solve: its backward error grows with the conditioning of the
+    # nearly singular shifted matrix (about 1e-8 relative on the 1/512 mesh)
     res = np.linalg.norm(b - K @ w) / np.linalg.norm(b)
-    if not np.isfinite(res) or res > 1e-9:
+    if not np.isfinite(res) or res > 1e-6:
         raise RuntimeError(f"shifted solve failed: relative residual {res:.3e}")
     w = w / np.sqrt(w @ (M @ w))  # step 3
     lam = float(w @ (A @ w))  # step 4

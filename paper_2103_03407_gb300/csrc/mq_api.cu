@@ -262,10 +262,20 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
   MQ_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
 
   mq::SampleLaunch p{};
+  // Where each fine solve runs.  A solve on the coarse mesh itself (h = H with a longer
+  // truncation) is nearly singular -- lambda_H differs from the fine eigenvalue only by the
+  // truncation -- so it always runs in the per-sample kernel with an FP64 inner solve.
   const bool stream = g.nf >= stream_threshold(c) && !g.direct_f;
-  p.nf = stream ? 0 : g.nf;
+  auto mode_of = [&](int n, bool direct) {
+    if (direct || n == 0) return 0;
+    if (n == g.nc) return mixed ? 1 : 0;
+    return stream ? 2 : 0;
+  };
+  p.mode_f = mode_of(g.nf, g.direct_f);
+  p.mode_p = mode_of(g.np, g.direct_p);
+  p.nf = g.nf;
   p.nc = g.nc;
-  p.np = stream ? g.np : g.np;
+  p.np = g.np;
   p.direct_f = g.direct_f;
   p.direct_p = g.direct_p;
   p.R = R;
@@ -299,14 +309,16 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
   if (c->opt_max_outer > 0) p.max_outer = c->opt_max_outer;
   p.nu = 2;
   p.omega = 0.8;
-  if (stream) {
+  const bool ext = p.mode_f == 2 || p.mode_p == 2;
+  if (ext) {
     p.coarse_only = 1;
     if ((st = grow(c, c->upad, B * (size_t)(g.nc + 1) * (g.nc + 1) * sizeof(double))) != MQ_OK) return st;
     p.u_pad = (double*)c->upad.p;
   }
-
-  const int threads = threads_for(stream ? g.nc : std::max(g.nf, g.nc));
-  const size_t slab = stream ? mq::sample_slab_bytes(0, g.nc, 0, mixed) : mq::sample_slab_bytes(g.nf, g.nc, g.np, mixed);
+  // FP64 inner solves in the per-sample kernel follow the FP64 defaults
+  const int in_kernel_n = std::max(p.mode_f != 2 && !g.direct_f ? g.nf : 0, p.mode_p != 2 && !g.direct_p ? g.np : 0);
+  const int threads = threads_for(std::max(in_kernel_n, g.nc));
+  const size_t slab = mq::sample_slab_bytes(g.nf, g.nc, g.np, mixed, p.mode_f, p.mode_p);
   const int static_smem = mq::sample_static_smem(mixed);
   const size_t smem_cap = (size_t)std::max(0, c->smem_optin - static_smem - 1024);
   const bool use_smem = slab <= smem_cap;
@@ -325,7 +337,7 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
   p.slab_bytes = slab;
   p.use_smem = use_smem;
   MQ_CUDA(c, mq::launch_sample(p, mixed, blocks, threads, smem, c->stream));
-  if (stream) {
+  if (ext) {
     if ((st = grow(c, c->arena, mq::stream_arena_bytes(g.nf, (int)B, mixed))) != MQ_OK) return st;
     mq::StreamSolve s{};
     s.nc = g.nc;
@@ -343,13 +355,15 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
     s.max_inner = p.max_inner_it;
     s.max_outer = p.max_outer;
     s.omega = p.omega;
-    s.n = g.nf;
-    s.a = (const double*)c->af.p;
-    s.lam_out = (double*)c->out.p + 1;
-    s.iters_out = (int*)c->stat.p + 1;
-    s.outer_out = (int*)c->outer.p + 0;
-    MQ_CUDA(c, mq::stream_solve(s, mixed, c->arena.p, c->stream));
-    if (g.np && !g.direct_p) {
+    if (p.mode_f == 2) {
+      s.n = g.nf;
+      s.a = (const double*)c->af.p;
+      s.lam_out = (double*)c->out.p + 1;
+      s.iters_out = (int*)c->stat.p + 1;
+      s.outer_out = (int*)c->outer.p + 0;
+      MQ_CUDA(c, mq::stream_solve(s, mixed, c->arena.p, c->stream));
+    }
+    if (p.mode_p == 2) {
       s.n = g.np;
       s.a = (const double*)c->ap.p;
       s.lam_out = (double*)c->out.p + 2;
@@ -433,7 +447,8 @@ mq_status flags_status(mq_ctx* c, int fl) {
 int points_per_pass(const mq_ctx* c, const LevelGeom& g, int R, int npts) {
   size_t per_sample = sizeof(double) * ((size_t)2 * g.nf * g.nf + (size_t)2 * g.nc * g.nc +
                                         (size_t)2 * g.np * g.np + (size_t)g.s + 8 + (size_t)(g.nc + 1) * (g.nc + 1));
-  if (g.nf >= stream_threshold(c) && !g.direct_f) per_sample += mq::stream_arena_bytes(g.nf, 1, c->prec == MQ_PREC_MIXED);
+  if (g.nf >= stream_threshold(c) && !g.direct_f && g.nf != g.nc)
+    per_sample += mq::stream_arena_bytes(g.nf, 1, c->prec == MQ_PREC_MIXED);
   size_t free_b = 0, total_b = 0;
   size_t budget = (size_t)24 << 30;
   if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) budget = std::min<size_t>((size_t)(0.4 * free_b), (size_t)64 << 30);

@@ -33,8 +33,10 @@ struct SampleLaunch {
   int max_outer;
   int nu;                  // Jacobi sweeps before and after each coarse-grid correction
   double omega;            // Jacobi damping
-  int coarse_only;         // only the coarse eigenpairs: u_pad receives the padded eigenvectors
+  int coarse_only;         // also write the padded coarse eigenvectors to u_pad
   double* u_pad;           // [B][(nc+1)^2] when coarse_only
+  int mode_f, mode_p;      // fine / previous-fine solve: 0 in the kernel (inner precision T),
+                           // 1 in the kernel with an FP64 inner solve, 2 elsewhere (streaming)
 };
 
 // Batched streaming fine solve (mq_stream.cu): B samples on mesh 1/n, coarse pairs from mesh 1/nc.
@@ -78,6 +80,7 @@ enum : int {
 };
 
 size_t sample_slab_bytes(int nf, int nc, int np, int mixed);
+size_t sample_slab_bytes(int nf, int nc, int np, int mixed, int mode_f, int mode_p);
 cudaError_t launch_sample(const SampleLaunch& p, int mixed, int blocks, int threads, size_t smem,
                           cudaStream_t st);
 int sample_occupancy(int mixed, int threads, size_t smem);

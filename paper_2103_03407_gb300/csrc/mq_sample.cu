@@ -91,16 +91,28 @@ __host__ __device__ void carve_fine(Carver& c, int n, FineWS<T>& ws) {
 }
 
 template <typename T>
-__host__ __device__ size_t slab_size(int nf, int nc, int np) {
+__host__ __device__ size_t fine_bytes(int n) {
+  if (n < 2) return 0;
+  Carver f(nullptr);
+  FineWS<T> fw;
+  carve_fine<T>(f, n, fw);
+  return (f.used() + 15) & ~(size_t)15;
+}
+
+// workspace of one CTA: the coarse region plus the largest fine solve it performs in place
+// (mode 0: inner precision T, mode 1: FP64 inner solve, 2: not in this kernel)
+template <typename T>
+__host__ __device__ size_t slab_size(int nf, int nc, int np, int mode_f = 0, int mode_p = 0) {
   Carver c(nullptr);
   CoarseWS cw;
   carve_coarse(c, nc, cw);
   const size_t coarse = (c.used() + 15) & ~(size_t)15;
-  if ((nf > np ? nf : np) < 2) return coarse;  // coarse eigenpairs only
-  Carver f(nullptr);
-  FineWS<T> fw;
-  carve_fine<T>(f, nf > np ? nf : np, fw);
-  return coarse + ((f.used() + 15) & ~(size_t)15);
+  auto need = [&](int n, int mode) -> size_t {
+    if (mode == 2) return 0;
+    return mode == 1 ? fine_bytes<double>(n) : fine_bytes<T>(n);
+  };
+  const size_t a = need(nf, mode_f), b = need(np, mode_p);
+  return coarse + (a > b ? a : b);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -397,8 +409,18 @@ struct MinresShared {
   T delta;
   T rs;           // 1 / ||r|| of the refinement residual
   double rnorm, bnorm;
+  double knorm, xnorm;  // ||A - sigma M|| bound and ||x|| for the FP64 residual floor
   int done, breakdown;
 };
+
+// Residual target of the refinement: tol relative to ||b||, but never below a small multiple of
+// the FP64 rounding floor eps (||K|| ||x|| + ||b||) of the residual itself (on fine meshes the
+// near-singular shifted system puts that floor above 1e-7 ||b||).
+__host__ __device__ inline double residual_target(double tol, double bnorm, double knorm, double xnorm, double f) {
+  const double floor_ = f * 2.220446049250313e-16 * (knorm * xnorm + bnorm);
+  const double t = tol * bnorm;
+  return t > floor_ ? t : floor_;
+}
 
 // ---------------------------------------------------------------------------------------------
 // two-grid update on the fine mesh n: returns the Rayleigh quotient of the solution of
@@ -429,6 +451,21 @@ __device__ double twogrid_fine(FineWS<T>& ws, char* fine_base, int n, const doub
   zero_mg(ws.mg);
   __syncthreads();
   if (!build_mg<T>(ws.mg, a, n, red)) flags |= kFlagBadCoef;
+  {
+    // ||A - sigma M||_inf <= 8 max a + sigma h^2 (row sums of the edge form and of the mass)
+    double amax = 0.0;
+    for_all((size_t)2 * n * n, [&](size_t q) { amax = fmax(amax, a[q]); });
+    for (int off = 16; off > 0; off >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = amax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double m = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+      ms->knorm = 8.0 * m + sigma / ((double)n * n);
+      ms->xnorm = 0.0;
+    }
+    __syncthreads();
+  }
   // FP64 operator for the residual and the Rayleigh quotient: the FP64 weights of level 0 when the
   // inner precision is FP64, otherwise weights formed on the fly from the centroid coefficients
   const bool w64 = sizeof(T) == sizeof(double);
@@ -476,7 +513,7 @@ __device__ double twogrid_fine(FineWS<T>& ws, char* fine_base, int n, const doub
   const T* twx = ws.mg.wx[0];
   const T* twy = ws.mg.wy[0];
   for (; outer < P.max_outer; ++outer) {
-    if (!(ms->rnorm > P.tol_lin * ms->bnorm)) break;
+    if (!(ms->rnorm > residual_target(P.tol_lin, ms->bnorm, ms->knorm, ms->xnorm, 16.0))) break;
     // inner: MINRES on (A - sigma M) xi = r / ||r|| in precision T, preconditioned by the V-cycle;
     // v holds r (unscaled)
     const T rs = ms->rs;
@@ -616,17 +653,23 @@ __device__ double twogrid_fine(FineWS<T>& ws, char* fine_base, int n, const doub
     const double rn = ms->rnorm;
     for_interior(n, [&](int p, int, int) { ws.x64[p] += rn * (double)ws.xi[p]; });
     __syncthreads();
-    double acc2[1] = {0.0}, o2[1];
+    double acc2[2] = {0.0, 0.0}, o2[2];
     for_interior(n, [&](int p, int i, int j) {
+      const double xv = ws.x64[p];
       const double kx = K64(ws.x64, p, i, j) - sigma * hm * mass7(ws.x64, p, ld);
       const double rv = ws.b64[p] - kx;
       ws.v[p] = T(rv);
       acc2[0] += rv * rv;
+      acc2[1] += xv * xv;
     });
     int stalled = 0;
-    block_sum<1, double>(acc2, o2, red, [&](const double* t) {
+    const int first = outer == 0;
+    block_sum<2, double>(acc2, o2, red, [&](const double* t) {
       const double rnew = sqrt(t[0]);
-      ms->done = !(rnew < 0.5 * ms->rnorm);  // no progress: stop refining
+      ms->xnorm = sqrt(t[1]);
+      // no progress: stop refining (not after the first step, whose FP32 rounding noise can
+      // leave a residual above ||b|| on fine meshes)
+      ms->done = !first && !(rnew < 0.5 * ms->rnorm);
       ms->rnorm = rnew;
       ms->rs = T(1.0 / rnew);
     });
@@ -636,7 +679,7 @@ __device__ double twogrid_fine(FineWS<T>& ws, char* fine_base, int n, const doub
       break;
     }
   }
-  if (!(ms->rnorm <= P.tol_lin * ms->bnorm) && !(ms->rnorm < 1e-6 * ms->bnorm)) flags |= kFlagLinNoConv;
+  if (!(ms->rnorm <= residual_target(1e-5, ms->bnorm, ms->knorm, ms->xnorm, 256.0))) flags |= kFlagLinNoConv;
   // Rayleigh quotient in FP64
   double acc[2] = {0.0, 0.0}, o[2];
   for_interior(n, [&](int p, int i, int j) {
@@ -654,8 +697,10 @@ __global__ void __launch_bounds__(512) sample_kernel(SampleLaunch P) {
   __shared__ double red[32 * 12 + 12];
   __shared__ EigShared esh;
   __shared__ MinresShared<T> msh;
+  __shared__ MinresShared<double> msh64;
   __shared__ CoarseWS cws;
   __shared__ FineWS<T> fws;
+  __shared__ FineWS<double> fws64;
   char* base = P.use_smem ? smem_dyn : P.gscratch + (size_t)blockIdx.x * P.slab_bytes;
   size_t coarse_bytes;
   {
@@ -713,31 +758,25 @@ __global__ void __launch_bounds__(512) sample_kernel(SampleLaunch P) {
       if (P.coarse_only) {
         const size_t Vc = gsz(nc);
         for_all(Vc, [&](size_t q) { P.u_pad[b * Vc + q] = cw.x[q]; });
-        if (threadIdx.x == 0) {
-          P.out[b * 4 + 0] = lamH;
-          P.out[b * 4 + 1] = lamH;
-          P.out[b * 4 + 2] = P.np > 0 ? lamH : 0.0;
-          P.out[b * 4 + 3] = 0.0;
-          P.stat[b * 4 + 0] = eit < 0 ? P.max_eig_it : eit;
-          P.stat[b * 4 + 1] = 0;
-          P.stat[b * 4 + 2] = 0;
-          P.stat[b * 4 + 3] = flags;
-          P.outer[b * 2 + 0] = 0;
-          P.outer[b * 2 + 1] = 0;
-        }
-        __syncthreads();
-        continue;
       }
       __syncthreads();
-      // ---- fine two-grid updates (Algorithm 1 steps 2-4; Algorithm 2 steps 9-14)
-      double lf = lamH, lp = 0.0;
+      // ---- fine two-grid updates (Algorithm 1 steps 2-4; Algorithm 2 steps 9-14); a solve of
+      // mode 2 runs elsewhere and leaves the coarse eigenvalue as a placeholder
+      double lf = lamH, lp = P.np > 0 ? lamH : 0.0;
       int itf = 0, itp = 0, of = 0, op = 0;
-      if (!P.direct_f)
-        lf = twogrid_fine<T>(fws, fine_base, P.nf, P.a_f + b * nfT, cw.x, nc, lamH, P, red, &msh, itf, of, flags);
-      if (P.np > 0) {
-        lp = lamH;
-        if (!P.direct_p)
+      if (!P.direct_f) {
+        if (P.mode_f == 0)
+          lf = twogrid_fine<T>(fws, fine_base, P.nf, P.a_f + b * nfT, cw.x, nc, lamH, P, red, &msh, itf, of, flags);
+        else if (P.mode_f == 1)
+          lf = twogrid_fine<double>(fws64, fine_base, P.nf, P.a_f + b * nfT, cw.x, nc, lamH, P, red, &msh64, itf, of,
+                                    flags);
+      }
+      if (P.np > 0 && !P.direct_p) {
+        if (P.mode_p == 0)
           lp = twogrid_fine<T>(fws, fine_base, P.np, P.a_p + b * npT, cw.x, nc, lamH, P, red, &msh, itp, op, flags);
+        else if (P.mode_p == 1)
+          lp = twogrid_fine<double>(fws64, fine_base, P.np, P.a_p + b * npT, cw.x, nc, lamH, P, red, &msh64, itp, op,
+                                    flags);
       }
       if (threadIdx.x == 0) {
         P.out[b * 4 + 0] = lamH;
@@ -803,6 +842,10 @@ __global__ void shift_sums_kernel(const double* __restrict__ out, const int* __r
 
 size_t sample_slab_bytes(int nf, int nc, int np, int mixed) {
   return mixed ? slab_size<float>(nf, nc, np) : slab_size<double>(nf, nc, np);
+}
+
+size_t sample_slab_bytes(int nf, int nc, int np, int mixed, int mode_f, int mode_p) {
+  return mixed ? slab_size<float>(nf, nc, np, mode_f, mode_p) : slab_size<double>(nf, nc, np, mode_f, mode_p);
 }
 
 int sample_occupancy(int mixed, int threads, size_t smem) {

@@ -63,6 +63,8 @@ template <typename T>
 struct SS {  // per-sample solver scalars
   T gam, gam_old, eta, eta0, c, c_old, s, s_old, ig, c1, c2, cx, ia1, a2, a3, delta, rs;
   double rnorm, bnorm, lam_h;
+  double xnorm;   // ||x64||
+  float amax;     // largest centroid coefficient (for the bound ||A - sigma M|| <= 8 amax + sigma h^2)
   int act_outer;  // refinement still running
   int act;        // inner MINRES running
   int pend;       // a w/x update is pending
@@ -107,6 +109,7 @@ __global__ void k_weights(int n, int B, const S* __restrict__ cells, size_t cstr
   const size_t V = gsz(n);
   const int ld = n + 1;
   int bad = 0;
+  float amax = 0.0f;
   for (int k = 0; k < kPer; ++k) {
     const size_t q = (size_t)ch * kTile + threadIdx.x + k * kThreads;
     if (q >= V) break;
@@ -116,7 +119,10 @@ __global__ void k_weights(int n, int B, const S* __restrict__ cells, size_t cstr
     T a = T(0), c = T(0), d = T(0);
     if (i <= n - 1 && j >= 1 && j <= n - 1) a = T(0.5 * (LO(i, j) + UP(i, j - 1)));
     if (i >= 1 && i <= n - 1 && j <= n - 1) c = T(0.5 * (UP(i, j) + LO(i - 1, j)));
-    if (i <= n - 1 && j <= n - 1) bad |= !(LO(i, j) > 0.0) | !(UP(i, j) > 0.0);  // every triangle once
+    if (i <= n - 1 && j <= n - 1) {  // every triangle once
+      bad |= !(LO(i, j) > 0.0) | !(UP(i, j) > 0.0);
+      amax = fmaxf(amax, (float)fmax(LO(i, j), UP(i, j)) * 1.0001f);
+    }
     if (i >= 1 && i <= n - 1 && j >= 1 && j <= n - 1) {
       const double l0 = LO(i, j), l1 = LO(i - 1, j), l2 = LO(i - 1, j - 1);
       const double u0 = UP(i, j), u1 = UP(i, j - 1), u2 = UP(i - 1, j - 1);
@@ -127,7 +133,11 @@ __global__ void k_weights(int n, int B, const S* __restrict__ cells, size_t cstr
     wy[(size_t)b * V + q] = c;
     dinv[(size_t)b * V + q] = d;
   }
-  if (ss && __syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&ss[b].flags, kFlagBadCoef);
+  if (ss) {
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&ss[b].flags, kFlagBadCoef);
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if ((threadIdx.x & 31) == 0 && amax > 0.0f) atomicMax((int*)&ss[b].amax, __float_as_int(amax));  // positive floats order as ints
+  }
 }
 
 // per-triangle coefficients of mesh n/2 as means of the four fine triangles each contains
@@ -217,12 +227,27 @@ __global__ void k_sc_start(int B, int nch, const double* part, SS<T>* ss) {
 }
 
 // start of a refinement step: samples above tolerance run an inner solve
+__host__ __device__ inline double residual_target(double tol, double bnorm, double knorm, double xnorm, double f) {
+  const double floor_ = f * 2.220446049250313e-16 * (knorm * xnorm + bnorm);
+  const double t = tol * bnorm;
+  return t > floor_ ? t : floor_;
+}
+
 template <typename T>
-__global__ void k_sc_outer_begin(int B, double tol_lin, SS<T>* ss, int* act, int* count) {
+__device__ inline double knorm_of(const SS<T>& S, int n, double sigma) {
+  return 8.0 * (double)S.amax + sigma / ((double)n * n);
+}
+
+// start of a refinement step: samples above the residual target run an inner solve (target: tol
+// relative to ||b||, but not below a small multiple of the FP64 floor eps (||K|| ||x|| + ||b||))
+template <typename T>
+__global__ void k_sc_outer_begin(int B, int n, const double* sigma, int sig_stride, double tol_lin, SS<T>* ss,
+                                 int* act, int* count) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
   SS<T>& S = ss[b];
-  const int a = S.act_outer && (S.rnorm > tol_lin * S.bnorm);
+  const double kn = knorm_of(S, n, sigma[(size_t)b * sig_stride]);
+  const int a = S.act_outer && (S.rnorm > residual_target(tol_lin, S.bnorm, kn, S.xnorm, 16.0));
   if (!a) S.act_outer = 0;
   S.act = a;
   act[b] = a;
@@ -609,25 +634,33 @@ __global__ void k_residual(int n, int B, const int* __restrict__ ran, const doub
   const double sg = sigma[(size_t)b * sig_stride];
   const double* ab = a + (size_t)b * astride;
   const double* X = x64 + off;
-  double acc[1] = {0.0};
+  double acc[2] = {0.0, 0.0};
   for_tile(n, ch, [&](int p, int i, int j) {
     const double kx = stiff_cells(ab, n, X, p, ld, i, j) - sg * hm * mass7(X, p, ld);
     const double r = b64[off + p] - kx;
     v[off + p] = T(r);
     acc[0] += r * r;
+    acc[1] += X[p] * X[p];
   });
-  tile_partials<1, double>(acc, part, (size_t)b * nt + ch);
+  tile_partials<2, double>(acc, part, (size_t)b * nt + ch);
 }
 
 template <typename T>
 __global__ void k_sc_outer_end(int B, int nch, const double* part, const int* ran, SS<T>* ss) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B || !ran[b]) return;
-  double s = 0.0;
-  for (int k = 0; k < nch; ++k) s += part[(size_t)b * nch + k];
+  double s = 0.0, sx = 0.0;
+  for (int k = 0; k < nch; ++k) {
+    s += part[((size_t)b * nch + k) * 2];
+    sx += part[((size_t)b * nch + k) * 2 + 1];
+  }
   SS<T>& S = ss[b];
+  S.xnorm = sqrt(sx);
   const double rnew = sqrt(s);
-  if (!(rnew < 0.5 * S.rnorm)) S.act_outer = 0;  // no progress: stop refining
+  // No progress: stop refining.  Not on the first step: on fine meshes the FP32 rounding of the
+  // first inner solution alone leaves an FP64 residual above ||b|| (the operator amplifies its
+  // high-frequency part by O(h^-2)); the next step removes it.
+  if (S.outer >= 1 && !(rnew < 0.5 * S.rnorm)) S.act_outer = 0;
   S.rnorm = rnew;
   S.rs = T(1.0 / rnew);
   S.outer += 1;
@@ -655,7 +688,8 @@ __global__ void k_rq(int n, int B, const double* __restrict__ a, size_t astride,
 }
 
 template <typename T>
-__global__ void k_sc_rq(int B, int nch, const double* part, const SS<T>* ss, double tol_lin, double* lam_out,
+__global__ void k_sc_rq(int B, int n, const double* sigma, int sig_stride, int nch, const double* part,
+                        const SS<T>* ss, double tol_lin, double* lam_out,
                         int lam_stride, int* it_out, int it_stride, int* outer_out, int outer_stride, int* flags,
                         int flag_stride) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -670,7 +704,8 @@ __global__ void k_sc_rq(int B, int nch, const double* part, const SS<T>* ss, dou
   it_out[(size_t)b * it_stride] = S.iters;
   outer_out[(size_t)b * outer_stride] = S.outer;
   int f = S.flags;
-  if (!(S.rnorm <= tol_lin * S.bnorm) && !(S.rnorm < 1e-6 * S.bnorm)) f |= kFlagLinNoConv;
+  const double kn = knorm_of(S, n, sigma[(size_t)b * sig_stride]);
+  if (!(S.rnorm <= residual_target(1e-5, S.bnorm, kn, S.xnorm, 256.0))) f |= kFlagLinNoConv;
   flags[(size_t)b * flag_stride] |= f;
 }
 
@@ -886,7 +921,7 @@ cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st) {
   // ---- refinement loop
   for (int o = 0; o < s.max_outer; ++o) {
     cudaMemsetAsync(A.count, 0, sizeof(int), st);
-    k_sc_outer_begin<T><<<gs, 256, 0, st>>>(B, s.tol_lin, A.ss, A.act, A.count);
+    k_sc_outer_begin<T><<<gs, 256, 0, st>>>(B, n, s.lamH, s.lam_stride, s.tol_lin, A.ss, A.act, A.count);
     LAUNCH_CHECK();
     int active = read_count(A.count, st, e);
     if (e != cudaSuccess) return e;
@@ -934,7 +969,7 @@ cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st) {
   }
   // ---- Rayleigh quotient
   k_rq<T><<<B * nt, kThreads, 0, st>>>(n, B, s.a, astride, A.x64, A.part);
-  k_sc_rq<T><<<gs, 256, 0, st>>>(B, nt, A.part, A.ss, s.tol_lin, s.lam_out, s.lam_out_stride, s.iters_out,
+  k_sc_rq<T><<<gs, 256, 0, st>>>(B, n, s.lamH, s.lam_stride, nt, A.part, A.ss, s.tol_lin, s.lam_out, s.lam_out_stride, s.iters_out,
                                  s.iters_stride, s.outer_out, s.outer_stride, s.flags, s.flags_stride);
   LAUNCH_CHECK();
   return cudaSuccess;

@@ -202,3 +202,12 @@ def test_smallest_eigenvector_positive():
     assert np.all(u > 0)
     _, M = fem.assemble(n)
     assert abs(u @ (M @ u) - 1) < 1e-13
+
+
+def test_coefficient_large_mesh_path_matches_matrix_path():
+    # the term-by-term evaluation used on large meshes equals the Psi-matrix product
+    n, s = 256, 300
+    y = random_points(17, 1, s)[0]
+    a_terms = fem.coefficient(n, y)  # 2 n^2 s > 2^25: term by term
+    a_matrix = 1.0 + fem._psi_matrix(n, s, 2.0) @ y
+    assert np.abs(a_terms - a_matrix).max() < 1e-13
