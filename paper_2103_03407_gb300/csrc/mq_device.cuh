@@ -61,6 +61,8 @@ struct MGDesc {
   T* t[kMaxMG];   // Jacobi partner
   T* b[kMaxMG];   // level right-hand side (level 0: supplied by the caller)
   T* cell[2];     // ping-pong per-triangle coefficients while building
+  T* cinv;        // symmetric inverse of the operator on the 3 x 3-unknown mesh 1/4 (exact coarse solve)
+  int Lc;         // level solved exactly: mesh 1/4 when present, else mesh 1/2
 };
 
 template <typename T>
@@ -80,6 +82,8 @@ __host__ __device__ void carve_mg(Carver& c, int n, MGDesc<T>& d) {
   const size_t cells = n >= 4 ? (size_t)2 * (n / 2) * (n / 2) : 1;
   d.cell[0] = c.take<T>(cells);
   d.cell[1] = c.take<T>(cells);
+  d.cinv = c.take<T>(81);
+  d.Lc = d.L >= 2 ? d.L - 2 : d.L - 1;
 }
 
 // Same hierarchy with the operator arrays (weights, inverse diagonals) taken from carver w and
@@ -101,6 +105,8 @@ __host__ __device__ void carve_mg_split(Carver& w, Carver& v, int n, MGDesc<T>& 
   const size_t cells = n >= 4 ? (size_t)2 * (n / 2) * (n / 2) : 1;
   d.cell[0] = v.take<T>(cells);
   d.cell[1] = v.take<T>(cells);
+  d.cinv = w.take<T>(81);
+  d.Lc = d.L >= 2 ? d.L - 2 : d.L - 1;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -123,6 +129,9 @@ __device__ __forceinline__ void for_all(size_t count, F f) {
   for (size_t q = threadIdx.x; q < count; q += blockDim.x) f(q);
 }
 
+// size of the shared reduction buffer every block_sum caller must provide
+constexpr int kRedSlots = 32 * 12 + 12;
+
 struct NoEp {
   __device__ void operator()(const double*) const {}
 };
@@ -132,7 +141,12 @@ struct NoEp {
 // also receives the totals in out.
 template <int NV, typename A, class Ep = NoEp>
 __device__ __forceinline__ void block_sum(A (&v)[NV], double (&out)[NV], double* red, Ep ep = Ep()) {
+  static_assert(NV <= 12, "block_sum reduces at most 12 values");
+  // red: kRedSlots doubles = 32 * 12 partial slots followed by 12 total slots.  The totals never overlap the partials,
+  // so two barriers suffice: the next call writes partials only after passing this call's second
+  // barrier, and writes totals only after its own first barrier (every thread has read ours).
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double* tot = red + 32 * 12;
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
     A s = v[i];
@@ -142,21 +156,20 @@ __device__ __forceinline__ void block_sum(A (&v)[NV], double (&out)[NV], double*
   }
   __syncthreads();
   if (wid == 0) {
-    double tot[NV];
+    double t[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
       double s = lane < nw ? red[lane * NV + i] : 0.0;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      tot[i] = s;
-      if (lane == 0) red[32 * NV + i] = s;
+      t[i] = s;
+      if (lane == 0) tot[i] = s;
     }
-    if (lane == 0) ep(tot);
+    if (lane == 0) ep(t);
   }
   __syncthreads();
 #pragma unroll
-  for (int i = 0; i < NV; ++i) out[i] = red[32 * NV + i];
-  __syncthreads();
+  for (int i = 0; i < NV; ++i) out[i] = tot[i];
 }
 
 // stiffness (weighted five-point edge form) at padded node p
@@ -218,10 +231,80 @@ __device__ void coarsen_cells(int n, const S* low, const S* up, T* out) {
   });
 }
 
+// 1 / diag(A) at the interior nodes and 0 on the boundary ring (the fused smoothing phase of the
+// V-cycle reads it at the neighbours of every interior node)
 template <typename T>
 __device__ void inverse_diagonal(int n, const T* wx, const T* wy, T* dinv) {
   const int ld = n + 1;
-  for_interior(n, [&](int p, int, int) { dinv[p] = T(1) / (wx[p] + wx[p - 1] + wy[p] + wy[p - ld]); });
+  for_all(gsz(n), [&](size_t q) {
+    const int i = (int)(q % ld), j = (int)(q / ld);
+    const int p = (int)q;
+    dinv[q] = (i >= 1 && i <= n - 1 && j >= 1 && j <= n - 1) ? T(1) / (wx[p] + wx[p - 1] + wy[p] + wy[p - ld]) : T(0);
+  });
+}
+
+// Exact coarse solve on mesh 1/4 (3 x 3 unknowns): the inverse of the weighted five-point
+// operator by an FP32 Cholesky factorisation (one thread, fully unrolled so the 9 x 9 factor stays
+// in registers), written symmetrised.  The V-cycle only needs a symmetric positive definite
+// approximation of A^{-1} on this level; this one is exact to FP32 rounding.
+template <typename T>
+__device__ void coarse_inverse4(const T* wx, const T* wy, T* cinv) {
+  constexpr int ld = 5;
+  float L[9][9];
+#pragma unroll
+  for (int r = 0; r < 9; ++r)
+#pragma unroll
+    for (int c = 0; c < 9; ++c) L[r][c] = 0.0f;
+#pragma unroll
+  for (int r = 0; r < 9; ++r) {
+    const int i = r % 3 + 1, j = r / 3 + 1, p = j * ld + i;
+    L[r][r] = (float)(wx[p] + wx[p - 1] + wy[p] + wy[p - ld]);
+    if (i > 1) L[r][r - 1] = -(float)wx[p - 1];
+    if (j > 1) L[r][r - 3] = -(float)wy[p - ld];
+  }
+  // in-place Cholesky of the lower triangle
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    float d = L[k][k];
+#pragma unroll
+    for (int m = 0; m < k; ++m) d -= L[k][m] * L[k][m];
+    d = sqrtf(d);
+    L[k][k] = d;
+    const float id = 1.0f / d;
+#pragma unroll
+    for (int r = k + 1; r < 9; ++r) {
+      float v = L[r][k];
+#pragma unroll
+      for (int m = 0; m < k; ++m) v -= L[r][m] * L[k][m];
+      L[r][k] = v * id;
+    }
+  }
+  // columns of the inverse: L L^T x = e_c
+#pragma unroll
+  for (int c = 0; c < 9; ++c) {
+    float y[9];
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+      float v = (r == c) ? 1.0f : 0.0f;
+#pragma unroll
+      for (int m = 0; m < r; ++m) v -= L[r][m] * y[m];
+      y[r] = v / L[r][r];
+    }
+#pragma unroll
+    for (int r = 8; r >= 0; --r) {
+      float v = y[r];
+#pragma unroll
+      for (int m = r + 1; m < 9; ++m) v -= L[m][r] * y[m];
+      y[r] = v / L[r][r];
+    }
+#pragma unroll
+    for (int r = 0; r < 9; ++r)
+      if (r >= c) cinv[r * 9 + c] = T(y[r]);
+  }
+#pragma unroll
+  for (int r = 0; r < 9; ++r)
+#pragma unroll
+    for (int c = r + 1; c < 9; ++c) cinv[r * 9 + c] = cinv[c * 9 + r];
 }
 
 // Builds every level (weights, inverse diagonals) from the fine centroid coefficients a.
@@ -242,37 +325,37 @@ __device__ bool build_mg(MGDesc<T>& d, const S* __restrict__ a, int n, double* r
     __syncthreads();
   }
   inverse_diagonal<T>(d.n[d.L - 1], d.wx[d.L - 1], d.wy[d.L - 1], d.dinv[d.L - 1]);
+  if (d.L >= 2 && threadIdx.x == 0) coarse_inverse4<T>(d.wx[d.L - 2], d.wy[d.L - 2], d.cinv);
   double v[1] = {(double)bad}, o[1];
   block_sum<1, double>(v, o, red);
   return o[0] == 0.0;
 }
 
-// Symmetric V-cycle for A: damped Jacobi (nu sweeps before and after the coarse correction),
-// Galerkin coarse levels, exact solve on the one-unknown mesh 1/2.  x0 = B^{-1} b0.
-// The residual is restricted with P^T in the same sweep that forms it.
+// Symmetric V-cycle for A with two damped Jacobi steps before and after each coarse-grid
+// correction, Galerkin coarse levels and an exact solve on mesh 1/4 (or 1/2): x0 = B^{-1} b0.
+// Phases per level: [two Jacobi steps from zero, fused] -> [residual restricted with P^T] going
+// down; [prolongation + correction + one Jacobi step, fused] -> [one Jacobi step] going up.
+// With dotv, returns this thread's share of <dotv, x0> (formed in the last phase).
 template <typename T>
-__device__ void vcycle(const MGDesc<T>& d, const T* b0, T* x0, int nu, T omega) {
-  const int L = d.L;
-  for (int l = 0; l < L - 1; ++l) {
+__device__ T vcycle(const MGDesc<T>& d, const T* b0, T* x0, T omega, const T* dotv = nullptr) {
+  const int Lc = d.Lc;
+  for (int l = 0; l < Lc; ++l) {
     const int n = d.n[l], ld = n + 1;
     const T* b = l ? d.b[l] : b0;
     T* xa = l ? d.x[l] : x0;
     const T* __restrict__ wx = d.wx[l];
     const T* __restrict__ wy = d.wy[l];
     const T* __restrict__ di = d.dinv[l];
-    T* cur = d.t[l];
-    T* oth = xa;
-    for_interior(n, [&](int p, int, int) { cur[p] = omega * di[p] * b[p]; });
+    for_interior(n, [&](int p, int, int) {
+      auto x1 = [&](int q) { return omega * di[q] * b[q]; };
+      const T xp = x1(p);
+      const T ax = wx[p] * (xp - x1(p + 1)) + wx[p - 1] * (xp - x1(p - 1)) + wy[p] * (xp - x1(p + ld)) +
+                   wy[p - ld] * (xp - x1(p - ld));
+      xa[p] = xp + omega * di[p] * (b[p] - ax);
+    });
     __syncthreads();
-    for (int k = 1; k < nu; ++k) {
-      for_interior(n, [&](int p, int, int) { oth[p] = cur[p] + omega * di[p] * (b[p] - stiff<T, T>(wx, wy, cur, p, ld)); });
-      __syncthreads();
-      T* tt = cur;
-      cur = oth;
-      oth = tt;
-    }
     T* bc = d.b[l + 1];
-    const T* cx = cur;
+    const T* cx = xa;
     for_interior(n >> 1, [&](int P, int I, int J) {
       const int p = (2 * J) * ld + 2 * I;
       auto res = [&](int q) { return b[q] - stiff<T, T>(wx, wy, cx, q, ld); };
@@ -282,41 +365,57 @@ __device__ void vcycle(const MGDesc<T>& d, const T* b0, T* x0, int nu, T omega) 
     __syncthreads();
   }
   {
-    const T* b = (L - 1) ? d.b[L - 1] : b0;
-    T* x = (L - 1) ? d.x[L - 1] : x0;
-    if (threadIdx.x == 0) x[4] = b[4] * d.dinv[L - 1][4];  // mesh 1/2: one unknown at padded index 4
+    const T* b = Lc ? d.b[Lc] : b0;
+    T* x = Lc ? d.x[Lc] : x0;
+    if (d.n[Lc] == 4) {
+      // 3 x 3 unknowns at padded indices (i, j) -> j * 5 + i
+      if (threadIdx.x < 9) {
+        const int r = threadIdx.x;
+        T s = T(0);
+#pragma unroll
+        for (int c = 0; c < 9; ++c) s += d.cinv[r * 9 + c] * b[(c / 3 + 1) * 5 + (c % 3 + 1)];
+        x[(r / 3 + 1) * 5 + (r % 3 + 1)] = s;
+      }
+    } else if (threadIdx.x == 0) {
+      x[4] = b[4] * d.dinv[Lc][4];  // mesh 1/2: one unknown
+    }
     __syncthreads();
   }
-  for (int l = L - 2; l >= 0; --l) {
+  T dot = T(0);
+  for (int l = Lc - 1; l >= 0; --l) {
     const int n = d.n[l], ld = n + 1;
     const T* b = l ? d.b[l] : b0;
     T* xa = l ? d.x[l] : x0;
+    T* tt = d.t[l];
     const T* __restrict__ wx = d.wx[l];
     const T* __restrict__ wy = d.wy[l];
     const T* __restrict__ di = d.dinv[l];
-    T* cur = ((nu - 1) & 1) ? xa : d.t[l];
-    T* oth = ((nu - 1) & 1) ? d.t[l] : xa;
     const T* xc = d.x[l + 1];
     const int ldc = (n >> 1) + 1;
     for_interior(n, [&](int p, int i, int j) {
-      const int I = i >> 1, J = j >> 1;
-      const int c0 = J * ldc + I;
-      T v;
-      if (!(i & 1) && !(j & 1)) v = xc[c0];
-      else if ((i & 1) && !(j & 1)) v = T(0.5) * (xc[c0] + xc[c0 + 1]);
-      else if (!(i & 1)) v = T(0.5) * (xc[c0] + xc[c0 + ldc]);
-      else v = T(0.5) * (xc[c0] + xc[c0 + ldc + 1]);
-      cur[p] += v;
+      // P1 interpolation on the SW-NE mesh, branch-free: the mean of the coarse values at the two
+      // ends of the coarse edge through the fine node (both ends coincide at coarse nodes)
+      auto t = [&](int q, int ii, int jj) {
+        const int c0 = (jj >> 1) * ldc + (ii >> 1);
+        return xa[q] + T(0.5) * (xc[c0] + xc[c0 + (ii & 1) + (jj & 1) * ldc]);
+      };
+      const T tp = t(p, i, j);
+      const T ax = wx[p] * (tp - t(p + 1, i + 1, j)) + wx[p - 1] * (tp - t(p - 1, i - 1, j)) +
+                   wy[p] * (tp - t(p + ld, i, j + 1)) + wy[p - ld] * (tp - t(p - ld, i, j - 1));
+      tt[p] = tp + omega * di[p] * (b[p] - ax);
     });
     __syncthreads();
-    for (int k = 0; k < nu; ++k) {
-      for_interior(n, [&](int p, int, int) { oth[p] = cur[p] + omega * di[p] * (b[p] - stiff<T, T>(wx, wy, cur, p, ld)); });
-      __syncthreads();
-      T* tt = cur;
-      cur = oth;
-      oth = tt;
-    }
+    const bool last = (l == 0) && dotv;
+    for_interior(n, [&](int p, int, int) {
+      const T o = tt[p] + omega * di[p] * (b[p] - stiff<T, T>(wx, wy, tt, p, ld));
+      xa[p] = o;
+      if (last) dot += dotv[p] * o;
+    });
+    __syncthreads();
   }
+  if (Lc == 0 && dotv)
+    for_interior(d.n[0], [&](int p, int, int) { dot += dotv[p] * x0[p]; });
+  return dot;
 }
 
 template <typename T>

@@ -278,7 +278,7 @@ __device__ int lobpcg(CoarseWS& ws, int n, double tol, int maxit, int nu, float 
         break;
       }
     }
-    vcycle<float>(ws.mg, ws.r32, ws.w32, nu, omega);
+    vcycle<float>(ws.mg, ws.r32, ws.w32, omega);
     for_interior(n, [&](int p, int, int) { ws.w[p] = (double)ws.w32[p]; });
     __syncthreads();
     double g[12];
@@ -531,11 +531,9 @@ __device__ double twogrid_fine(FineWS<T>& ws, char* fine_base, int n, const doub
     T* zn = ws.zn;
     T* wo = ws.wo;
     T* w = ws.w;
-    vcycle<T>(ws.mg, v, z, P.nu, om);
     {
-      T acc1[1] = {T(0)};
+      T acc1[1] = {vcycle<T>(ws.mg, v, z, om, v)};  // z = B^{-1} v and <v, z>
       double o1[1];
-      for_interior(n, [&](int p, int, int) { acc1[0] += v[p] * z[p]; });
       block_sum<1, T>(acc1, o1, red, [&](const double* t) {
         const T t0 = T(t[0]);
         ms->breakdown = !(t0 > T(0));
@@ -598,11 +596,9 @@ __device__ double twogrid_fine(FineWS<T>& ws, char* fine_base, int n, const doub
         vo = v;
         v = tt;
       }
-      vcycle<T>(ws.mg, v, zn, P.nu, om);
       {
-        T acc1[1] = {T(0)};
+        T acc1[1] = {vcycle<T>(ws.mg, v, zn, om, v)};  // zn = B^{-1} v_new and <v_new, zn>
         double o1[1];
-        for_interior(n, [&](int p, int, int) { acc1[0] += v[p] * zn[p]; });
         const T tol = T(P.tol_inner);
         block_sum<1, T>(acc1, o1, red, [&](const double* t) {
           T gnew = T(t[0]);
@@ -694,7 +690,7 @@ __device__ double twogrid_fine(FineWS<T>& ws, char* fine_base, int n, const doub
 template <typename T>
 __global__ void __launch_bounds__(512) sample_kernel(SampleLaunch P) {
   extern __shared__ __align__(16) char smem_dyn[];
-  __shared__ double red[32 * 12 + 12];
+  __shared__ double red[kRedSlots];
   __shared__ EigShared esh;
   __shared__ MinresShared<T> msh;
   __shared__ MinresShared<double> msh64;
@@ -824,7 +820,7 @@ __global__ void apply_kernel(int n, const double* __restrict__ a, int which, dou
 // fixed reduction order (deterministic).  flags receives the OR of all sample flags.
 __global__ void shift_sums_kernel(const double* __restrict__ out, const int* __restrict__ stat, int npts,
                                   double* __restrict__ sums, int* __restrict__ flags) {
-  __shared__ double red[32 * 2 + 2];
+  __shared__ double red[kRedSlots];
   const int r = blockIdx.x;
   double acc[1] = {0.0}, o[1];
   int f = 0;

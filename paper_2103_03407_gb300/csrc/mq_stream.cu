@@ -340,14 +340,9 @@ __global__ void k_prolong_smooth(int n, int B, const int* __restrict__ act, cons
   const T* XC = xc + (size_t)b * gsz(n / 2);
   T* O = out + off;
   for_tile(n, ch, [&](int p, int i, int j) {
-    auto t = [&](int q, int ii, int jj) {
-      const int I = ii >> 1, J = jj >> 1, c0 = J * ldc + I;
-      T v;
-      if (!(ii & 1) && !(jj & 1)) v = XC[c0];
-      else if ((ii & 1) && !(jj & 1)) v = T(0.5) * (XC[c0] + XC[c0 + 1]);
-      else if (!(ii & 1)) v = T(0.5) * (XC[c0] + XC[c0 + ldc]);
-      else v = T(0.5) * (XC[c0] + XC[c0 + ldc + 1]);
-      return X[q] + v;
+    auto t = [&](int q, int ii, int jj) {  // branch-free P1 interpolation (see vcycle)
+      const int c0 = (jj >> 1) * ldc + (ii >> 1);
+      return X[q] + T(0.5) * (XC[c0] + XC[c0 + (ii & 1) + (jj & 1) * ldc]);
     };
     const T tp = t(p, i, j);
     const T ax = W[p] * (tp - t(p + 1, i + 1, j)) + W[p - 1] * (tp - t(p - 1, i - 1, j)) +
@@ -405,7 +400,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_sub_build(int ns, int B, const T* __restrict__ cells,
                                                         char* __restrict__ subw, size_t wbytes) {
   extern __shared__ __align__(16) char sm[];
-  __shared__ double red[32 * 12 + 12];
+  __shared__ double red[kRedSlots];
   __shared__ MGDesc<T> mg;
   const int b = blockIdx.x;
   if (b >= B) return;
@@ -450,13 +445,11 @@ __global__ void __launch_bounds__(kThreads) k_subcycle(int ns, int B, const int*
     }
   }
   __syncthreads();
-  vcycle<T>(mg, b0, x0, nu, om);
+  // with dotv (the right-hand side itself, copied to b0) also <v, x>
+  T acc[1] = {vcycle<T>(mg, b0, x0, om, dotv ? b0 : nullptr)};
+  (void)nu;
   T* dst = xout + (size_t)b * V;
-  T acc[1] = {T(0)};
-  for_all(V, [&](size_t q) {
-    dst[q] = x0[q];
-    if (dotv) acc[0] += dotv[(size_t)b * V + q] * x0[q];
-  });
+  for_all(V, [&](size_t q) { dst[q] = x0[q]; });
   if (dotv) tile_partials<1, T>(acc, part, (size_t)b);
 }
 
