@@ -232,6 +232,7 @@ struct EigShared {
 __device__ int lobpcg(CoarseWS& ws, int n, double tol, int maxit, int nu, float omega, double* red, EigShared* sh,
                       double& lam) {
   const int ld = n + 1;
+  const int nact = (n - 1) * n;  // threads for_interior gives work to
   const double hm = 1.0 / (12.0 * n * n);
   const double* __restrict__ wx = ws.wx;
   const double* __restrict__ wy = ws.wy;
@@ -245,7 +246,8 @@ __device__ int lobpcg(CoarseWS& ws, int n, double tol, int maxit, int nu, float 
       acc[0] += u[p] * au;
       acc[1] += u[p] * mu;
     });
-    block_sum<2, double>(acc, o, red, [&](const double* t) { sh->scale = (double)rsqrtf((float)t[1]); sh->theta = t[0] / t[1]; });
+    block_sum<2, double>(
+        acc, o, red, [&](const double* t) { sh->scale = (double)rsqrtf((float)t[1]); sh->theta = t[0] / t[1]; }, nact);
     uAu = o[0];
     uMu = o[1];
   };
@@ -272,7 +274,8 @@ __device__ int lobpcg(CoarseWS& ws, int n, double tol, int maxit, int nu, float 
         acc[0] += rv * rv;
         acc[1] += ws.Mx[p] * ws.Mx[p];
       });
-      block_sum<2, double>(acc, o, red, [&](const double* t) { sh->conv = t[0] <= tol * tol * theta * theta * t[1]; });
+      block_sum<2, double>(
+          acc, o, red, [&](const double* t) { sh->conv = t[0] <= tol * tol * theta * theta * t[1]; }, nact);
       if (sh->conv) {
         conv = 1;
         break;
@@ -361,7 +364,7 @@ __device__ int lobpcg(CoarseWS& ws, int n, double tol, int maxit, int nu, float 
           sh->theta = ca / cm;
         }
         sh->k = k;
-      });
+      }, nact);
     }
     const int k = sh->k;
     if (k == 0) break;
@@ -390,7 +393,7 @@ __device__ int lobpcg(CoarseWS& ws, int n, double tol, int maxit, int nu, float 
   block_sum<1, double>(sacc, so, red, [&](const double* t) {
     sh->scale = (t[0] < 0 ? -1.0 : 1.0) / sqrt(xM);
     sh->theta = xA / xM;
-  });
+  }, nact);
   const double sc = sh->scale;
   for_interior(n, [&](int p, int, int) { ws.x[p] *= sc; });
   __syncthreads();

@@ -62,6 +62,7 @@ __device__ __forceinline__ void for_tile(int n, int ch, F f) {
 template <typename T>
 struct SS {  // per-sample solver scalars
   T gam, gam_old, eta, eta0, c, c_old, s, s_old, ig, c1, c2, cx, ia1, a2, a3, delta, rs;
+  T sigm;         // lambda_H h^2 / 12: the mass factor of the shifted operator
   double rnorm, bnorm, lam_h;
   double xnorm;   // ||x64||
   float amax;     // largest centroid coefficient (for the bound ||A - sigma M|| <= 8 amax + sigma h^2)
@@ -71,27 +72,20 @@ struct SS {  // per-sample solver scalars
   int iters, outer, flags;
 };
 
-// block reduction of NV partial sums to part[(b * nch + ch) * NV + i]
+// block reduction of NV partial sums to part[(b * nch + ch) * NV + i] (butterfly within each warp,
+// then a fixed-order sum over the warps)
 template <int NV, typename A>
 __device__ __forceinline__ void tile_partials(A (&v)[NV], double* part, size_t slot) {
   __shared__ double red[32 * NV];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    A s = v[i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) red[wid * NV + i] = (double)s;
-  }
+  int base = 0, c = NV;
+  Butterfly<NV, 16, A>::run(v, lane, base, c);
+  if (c >= 1) red[wid * NV + base] = (double)v[0];
   __syncthreads();
-  if (wid == 0) {
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-      double s = lane < nw ? red[lane * NV + i] : 0.0;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) part[slot * NV + i] = s;
-    }
+  if (wid == 0 && lane < NV) {
+    double s = red[lane];
+    for (int w = 1; w < nw; ++w) s += red[w * NV + lane];
+    part[slot * NV + lane] = s;
   }
 }
 
@@ -211,9 +205,11 @@ __global__ void k_rhs(int n, int B, const double* __restrict__ x64, double* __re
 }
 
 template <typename T>
-__global__ void k_sc_start(int B, int nch, const double* part, SS<T>* ss) {
+__global__ void k_sc_start(int B, int n, const double* sigma, int sig_stride, int nch, const double* part,
+                           SS<T>* ss) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
+  ss[b].sigm = T(sigma[(size_t)b * sig_stride] / (12.0 * n * n));
   double s = 0.0;
   for (int k = 0; k < nch; ++k) s += part[(size_t)b * nch + k];
   SS<T>& S = ss[b];
@@ -467,7 +463,7 @@ __global__ void k_minres_q(int n, int B, const int* __restrict__ act, const SS<T
   const int ld = n + 1;
   const size_t off = (size_t)b * gsz(n);
   const SS<T> S = ss[b];
-  const T sigm = T(sigma[(size_t)b * sig_stride] / (12.0 * n * n));
+  const T sigm = S.sigm;
   const T* W = wx + off;
   const T* Y = wy + off;
   const T* Z = z + off;
@@ -909,7 +905,7 @@ cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st) {
   k_rhs<T><<<B * nt, kThreads, 0, st>>>(n, B, A.x64, A.b64, A.v, A.part);
   LAUNCH_CHECK();
   k_zero<double><<<grid1(Bz * V0), 256, 0, st>>>(Bz * V0, A.x64);
-  k_sc_start<T><<<gs, 256, 0, st>>>(B, nt, A.part, A.ss);
+  k_sc_start<T><<<gs, 256, 0, st>>>(B, n, s.lamH, s.lam_stride, nt, A.part, A.ss);
   LAUNCH_CHECK();
   // ---- refinement loop
   for (int o = 0; o < s.max_outer; ++o) {

@@ -216,15 +216,26 @@ __global__ void __launch_bounds__(128) k_coef_tc(const __nv_bfloat16* __restrict
       if (!ok) break;
     }
     if (!ok) break;
-    // fold the exact group sums of this chunk into FP64
+    // fold the exact group sums of this chunk: they are integers below 2^24, so the combination
+    // sum_g S_g 2^{8(6-g)} is formed exactly in two 64-bit integers (groups 0-3 and 4-6) and
+    // rounded once to FP64 -- three FP64 operations per output instead of two per group
+    long long hi[kTN], lo[kTN];
+#pragma unroll
+    for (int i = 0; i < kTN; ++i) hi[i] = lo[i] = 0;
 #pragma unroll
     for (int g = 0; g < kGroups; ++g) {
       float v[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(g * kTN), v);
-      const double sc = ldexp(1.0, -15 - 8 * g);
 #pragma unroll
-      for (int i = 0; i < kTN; ++i) acc[i] += sc * (double)v[i];
+      for (int i = 0; i < kTN; ++i) {
+        const long long s = (long long)__float2int_rn(v[i]);
+        if (g < 4) hi[i] = hi[i] * 256 + s;
+        else lo[i] = lo[i] * 256 + s;
+      }
     }
+    // value of the chunk = (hi 2^24 + lo) 2^{-15-48}; hi < 2^56 and lo < 2^40 in magnitude
+#pragma unroll
+    for (int i = 0; i < kTN; ++i) acc[i] += fma((double)hi[i], 0x1p-39, (double)lo[i] * 0x1p-63);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
