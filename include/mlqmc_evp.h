@@ -104,16 +104,25 @@ mq_status mq_set_lattice(mq_ctx* ctx, int32_t level, const uint32_t* z, int32_t 
 mq_status mq_set_shifts(mq_ctx* ctx, int32_t level, const double* delta);
 
 /* Precision mode and the relative residual target ||b - (A - lambda_H M) w|| / ||b|| of the fine
- * shifted solve (tol_linear <= 0: default 1e-7 for MQ_PREC_MIXED, 1e-8 for MQ_PREC_FP64; the
- * Rayleigh quotient is second-order accurate in the solve error, so these keep lambda^h within
- * ~1e-13 of the exact two-grid value). */
+ * shifted solve (tol_linear <= 0: default 1e-5 for MQ_PREC_MIXED, 1e-6 for MQ_PREC_FP64).  The
+ * Rayleigh quotient lambda^h moves to first order in the solve error with a constant damped by
+ * the two-grid error (about 3e-7 on meshes 1/16..1/128), so the defaults keep lambda^h within
+ * ~3e-13 of the exact two-grid value.  Samples whose final residual is above max(1e-5,
+ * 10 tol_linear) (or a small multiple of the FP64 rounding floor) are flagged. */
 mq_status mq_set_precision(mq_ctx* ctx, mq_precision prec, double tol_linear);
 
 /* Inner solver options (values <= 0 keep the defaults): tol_inner is the reduction of the
- * preconditioned MINRES residual per refinement step (default 1e-5 in MQ_PREC_MIXED, tol_linear/10
+ * preconditioned MINRES residual per refinement step (default in MQ_PREC_MIXED 1e-4 for fine
+ * meshes up to 1/128, 1e-5 beyond; tol_linear/10
  * in MQ_PREC_FP64), max_inner the MINRES iteration cap per step (500), max_outer the cap on FP64
  * refinement steps (10 mixed, 4 FP64). */
 mq_status mq_set_solver_options(mq_ctx* ctx, double tol_inner, int32_t max_inner, int32_t max_outer);
+
+/* Coarse eigensolver options (values <= 0 keep the defaults): tol_eig is the target of the
+ * relative eigen-residual ||A_H x - theta M_H x|| / (theta ||M_H x||) of LOBPCG (default 1e-8),
+ * max_eig the iteration cap (200).  The Rayleigh quotient theta = lambda_H is accurate to about
+ * the square of tol_eig. */
+mq_status mq_set_eig_options(mq_ctx* ctx, double tol_eig, int32_t max_eig);
 
 /* Execution tier of the fine solves: fine meshes 1/n with n >= stream_min_n run in
  * the batched streaming tier (one kernel per sweep over all samples of a pass, lockstep across

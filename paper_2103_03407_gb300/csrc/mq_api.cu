@@ -54,6 +54,8 @@ struct mq_ctx {
   double tol_lin = 0.0;  // 0: default of the precision mode
   double opt_tol_inner = 0.0;  // 0: default of the precision mode
   int opt_max_inner = 0, opt_max_outer = 0;
+  double opt_tol_eig = 0.0;  // 0: default
+  int opt_max_eig = 0;
 
   std::map<int, std::pair<int, double*>> psi;  // mesh n -> (rows, table [rows][2n^2])
   std::map<int, std::pair<int, void*>> psi_sl;  // mesh n -> (K pad, BF16 slices [6][nT pad][K pad])
@@ -188,6 +190,16 @@ mq_status coefficients(mq_ctx* c, int n, int K, const double* d_Y, int B, int ld
   return MQ_OK;
 }
 
+// Zeroes the error word of the tensor-core coefficient kernel (allocated here on first use:
+// fresh device memory holds whatever a previous owner left there).
+mq_status reset_tc_error(mq_ctx* c) {
+  if (c->prec != MQ_PREC_MIXED) return MQ_OK;
+  mq_status st = grow(c, c->tc_err, sizeof(int));
+  if (st != MQ_OK) return st;
+  MQ_CUDA(c, cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), c->stream));
+  return MQ_OK;
+}
+
 mq_status check_tc_error(mq_ctx* c) {
   if (c->prec != MQ_PREC_MIXED || !c->tc_err.p) return MQ_OK;
   int e = 0;
@@ -253,7 +265,7 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
   if (want_u && (st = grow(c, c->uout, B * (size_t)(g.nc - 1) * (g.nc - 1) * sizeof(double))) != MQ_OK) return st;
 
   const int mixed = c->prec == MQ_PREC_MIXED;
-  if (c->prec == MQ_PREC_MIXED && c->tc_err.p) MQ_CUDA(c, cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), c->stream));
+  if ((st = reset_tc_error(c)) != MQ_OK) return st;
   MQ_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
   const double* Y = (const double*)c->Y.p;
   if ((st = coefficients(c, g.nc, g.S, Y, (int)B, g.s, (double*)c->ac.p)) != MQ_OK) return st;
@@ -288,16 +300,23 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
   p.stat = (int*)c->stat.p;
   p.outer = (int*)c->outer.p;
   p.u_out = want_u ? (double*)c->uout.p : nullptr;
-  p.tol_eig = 1e-12;
-  p.max_eig_it = 200;
-  // Default residual targets of the shifted solve.  The Rayleigh quotient is stationary at the
-  // eigenvector, and the two-grid iterate is an O(H^4) perturbation of it, so the error of
-  // lambda^h is of second order in the solve error plus a first-order term damped by O(H^4):
-  // on the 4-level workload a relative residual of 1e-7 leaves every lambda^h within 1e-13 of
-  // the exact two-grid value.
-  p.tol_lin = c->tol_lin > 0 ? c->tol_lin : (mixed ? 1e-7 : 1e-8);
+  // Default tolerances.  lambda_H is the Rayleigh quotient of the LOBPCG iterate, accurate to the
+  // square of its relative eigen-residual, so 1e-8 leaves it at the FP64 rounding floor.  The
+  // Rayleigh quotient lambda^h of the shifted-solve iterate is stationary only at an eigenvector;
+  // the two-grid iterate is an O(H^4) perturbation of one, so lambda^h moves to first order in the
+  // solve error with a small constant: on the 4-level workload (meshes 1/16..1/128) the largest
+  // relative change of lambda^h is about 3e-7 times the relative residual.  An FP64 residual of
+  // 1e-6 keeps lambda^h within ~3e-13 of the exact two-grid value.  The mixed path refines
+  // twice whatever the targets (the FP32 rounding of the first correction, which is
+  // amplified by the near-singular shift, leaves a residual of ~1e-4): inner reductions of 1e-4
+  // and a target of 1e-5 leave lambda^h within ~2e-13 (1e-5 inner reductions above mesh 1/128).
+  p.tol_eig = c->opt_tol_eig > 0 ? c->opt_tol_eig : 1e-8;
+  p.max_eig_it = c->opt_max_eig > 0 ? c->opt_max_eig : 200;
+  p.tol_lin = c->tol_lin > 0 ? c->tol_lin : (mixed ? 1e-5 : 1e-6);
   if (mixed) {
-    p.tol_inner = 1e-5;
+    // the preconditioned residual MINRES reduces understates the 2-norm one by a factor growing
+    // like 1/h: finer meshes take a smaller inner reduction per refinement step
+    p.tol_inner = g.nf > 128 ? 1e-5 : 1e-4;
     p.max_outer = 10;
   } else {
     p.tol_inner = 0.1 * p.tol_lin;
@@ -719,6 +738,14 @@ mq_status mq_set_solver_options(mq_ctx* c, double tol_inner, int32_t max_inner, 
   return MQ_OK;
 }
 
+mq_status mq_set_eig_options(mq_ctx* c, double tol_eig, int32_t max_eig) {
+  if (!c) return MQ_EINVAL;
+  if (!std::isfinite(tol_eig) || tol_eig >= 1.0 || max_eig > 100000) return fail(c, MQ_EINVAL, "bad eigensolver options");
+  c->opt_tol_eig = tol_eig > 0 ? tol_eig : 0.0;
+  c->opt_max_eig = max_eig > 0 ? max_eig : 0;
+  return MQ_OK;
+}
+
 mq_status mq_set_tier(mq_ctx* c, int32_t stream_min_n) {
   if (!c) return MQ_EINVAL;
   if (stream_min_n < 0 || stream_min_n == 1) return fail(c, MQ_EINVAL, "stream_min_n must be 0 or >= 2");
@@ -874,8 +901,9 @@ mq_status mq_coefficients_device(mq_ctx* c, int32_t n, int32_t s, const double* 
   if (!pow2(n) || n < 2 || n > 4096 || s < 0 || s > c->s_max || B < 0 || ldy < s || (!d_Y && B * s) || (!d_a && B))
     return fail(c, MQ_EINVAL, "bad coefficient arguments");
   MQ_CUDA(c, cudaSetDevice(c->device));
-  if (c->prec == MQ_PREC_MIXED && c->tc_err.p) MQ_CUDA(c, cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), c->stream));
-  mq_status st = coefficients(c, n, s, d_Y, B, ldy, d_a);
+  mq_status st = reset_tc_error(c);
+  if (st != MQ_OK) return st;
+  st = coefficients(c, n, s, d_Y, B, ldy, d_a);
   if (st != MQ_OK) return st;
   MQ_CUDA(c, cudaStreamSynchronize(c->stream));
   return check_tc_error(c);

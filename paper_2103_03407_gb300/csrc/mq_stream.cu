@@ -694,7 +694,7 @@ __global__ void k_sc_rq(int B, int n, const double* sigma, int sig_stride, int n
   outer_out[(size_t)b * outer_stride] = S.outer;
   int f = S.flags;
   const double kn = knorm_of(S, n, sigma[(size_t)b * sig_stride]);
-  if (!(S.rnorm <= residual_target(1e-5, S.bnorm, kn, S.xnorm, 256.0))) f |= kFlagLinNoConv;
+  if (!(S.rnorm <= residual_target(fmax(1e-5, 10.0 * tol_lin), S.bnorm, kn, S.xnorm, 256.0))) f |= kFlagLinNoConv;
   flags[(size_t)b * flag_stride] |= f;
 }
 

@@ -1,7 +1,8 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
 Tolerances: integer and lattice-point work bit-exact; coefficients 1e-14 absolute (a ~ 1);
-operator applications 1e-13 relative; coarse eigenvalues 1e-12 relative; two-grid
+operator applications 1e-13 relative; coarse eigenvalues 1e-12 relative, coarse eigenvectors ten
+times the eigen-residual target; two-grid
 eigenvalues and level differences 1e-10 relative (FP64 and mixed paths), the workload target.
 """
 import numpy as np
@@ -15,6 +16,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 TOL_LAMBDA = 1e-10
+TOL_EIG = 1e-8  # default relative eigen-residual target of the coarse eigensolve
 
 
 @pytest.fixture(scope="module")
@@ -122,7 +124,9 @@ def test_eval_point_matches_oracle(B, case, prec):
         assert lh == pytest.approx(rh, rel=TOL_LAMBDA)
         assert lp == pytest.approx(rp, rel=TOL_LAMBDA, abs=0 if pv else 1e-300)
         _, uref = twogrid.coarse_pair(lv.n_coarse, y[: lv.S])
-        assert np.abs(u - uref).max() < 1e-9
+        # the eigenvector is accurate to the eigen-residual target (1e-8 by default) over the
+        # relative spectral gap (about 1.5 for these coefficients); the eigenvalue to its square
+        assert np.abs(u - uref).max() < 10 * TOL_EIG * np.abs(uref).max()
 
 
 def _check_level(per_sample, ref):
@@ -186,8 +190,10 @@ def test_warm_start_does_not_change_results(B):
     Y = lattice.points(zs[0], lv.N, ds[0][1], np.arange(20))
     for k in (0, 1, 7, 19):
         lH, lh, _ = ctx.mq_eval_point(0, Y[k])  # a single cold-started sample
+        # both starts converge to the same eigenpair; lambda^h then differs by the solve
+        # tolerance's effect only (first order, ~3e-7 times the relative residual)
         assert ps[1, k, 0] == pytest.approx(lH, rel=1e-12)
-        assert ps[1, k, 1] == pytest.approx(lh, rel=1e-12)
+        assert ps[1, k, 1] == pytest.approx(lh, rel=1e-11)
 
 
 def test_device_outputs_equal_host_outputs(B):
