@@ -413,6 +413,7 @@ struct MinresShared {
   T rs;           // 1 / ||r|| of the refinement residual
   double rnorm, bnorm;
   double knorm, xnorm;  // ||A - sigma M|| bound and ||x|| for the FP64 residual floor
+  double xax, xmx;      // x.Ax and x.Mx of the last FP64 residual pass (the Rayleigh quotient)
   int done, breakdown;
 };
 
@@ -466,6 +467,7 @@ __device__ double twogrid_fine(FineWS<T>& ws, char* fine_base, int n, const doub
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
       ms->knorm = 8.0 * m + sigma / ((double)n * n);
       ms->xnorm = 0.0;
+      ms->xax = ms->xmx = 0.0;
     }
     __syncthreads();
   }
@@ -652,20 +654,26 @@ __device__ double twogrid_fine(FineWS<T>& ws, char* fine_base, int n, const doub
     const double rn = ms->rnorm;
     for_interior(n, [&](int p, int, int) { ws.x64[p] += rn * (double)ws.xi[p]; });
     __syncthreads();
-    double acc2[2] = {0.0, 0.0}, o2[2];
+    // the same pass forms x.Ax and x.Mx: the last one gives the Rayleigh quotient of the result
+    double acc2[4] = {0.0, 0.0, 0.0, 0.0}, o2[4];
     for_interior(n, [&](int p, int i, int j) {
       const double xv = ws.x64[p];
-      const double kx = K64(ws.x64, p, i, j) - sigma * hm * mass7(ws.x64, p, ld);
-      const double rv = ws.b64[p] - kx;
+      const double ax = K64(ws.x64, p, i, j);
+      const double mx = hm * mass7(ws.x64, p, ld);
+      const double rv = ws.b64[p] - (ax - sigma * mx);
       ws.v[p] = T(rv);
       acc2[0] += rv * rv;
       acc2[1] += xv * xv;
+      acc2[2] += xv * ax;
+      acc2[3] += xv * mx;
     });
     int stalled = 0;
     const int first = outer == 0;
-    block_sum<2, double>(acc2, o2, red, [&](const double* t) {
+    block_sum<4, double>(acc2, o2, red, [&](const double* t) {
       const double rnew = sqrt(t[0]);
       ms->xnorm = sqrt(t[1]);
+      ms->xax = t[2];
+      ms->xmx = t[3];
       // no progress: stop refining (not after the first step, whose FP32 rounding noise can
       // leave a residual above ||b|| on fine meshes)
       ms->done = !first && !(rnew < 0.5 * ms->rnorm);
@@ -681,15 +689,8 @@ __device__ double twogrid_fine(FineWS<T>& ws, char* fine_base, int n, const doub
   // flagged only well above the target (or the FP64 floor): the refinement may stop a little short
   if (!(ms->rnorm <= residual_target(fmax(1e-5, 10.0 * P.tol_lin), ms->bnorm, ms->knorm, ms->xnorm, 256.0)))
     flags |= kFlagLinNoConv;
-  // Rayleigh quotient in FP64
-  double acc[2] = {0.0, 0.0}, o[2];
-  for_interior(n, [&](int p, int i, int j) {
-    const double x = ws.x64[p];
-    acc[0] += x * K64(ws.x64, p, i, j);
-    acc[1] += x * hm * mass7(ws.x64, p, ld);
-  });
-  block_sum<2, double>(acc, o, red);
-  return o[0] / o[1];
+  // Rayleigh quotient in FP64, from the residual pass over the final iterate
+  return ms->xax / ms->xmx;
 }
 
 template <typename T>

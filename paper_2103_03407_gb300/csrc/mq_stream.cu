@@ -65,6 +65,7 @@ struct SS {  // per-sample solver scalars
   T sigm;         // lambda_H h^2 / 12: the mass factor of the shifted operator
   double rnorm, bnorm, lam_h;
   double xnorm;   // ||x64||
+  double xax, xmx;  // x.Ax and x.Mx of the last FP64 residual pass (the Rayleigh quotient)
   float amax;     // largest centroid coefficient (for the bound ||A - sigma M|| <= 8 amax + sigma h^2)
   int act_outer;  // refinement still running
   int act;        // inner MINRES running
@@ -172,7 +173,7 @@ __global__ void k_interp(int n, int nc, int B, const double* __restrict__ uH, do
   if (b >= B) return;
   const int lr = ilog2(n / nc), rm = (1 << lr) - 1, ldc = nc + 1;
   const double inv = 1.0 / (double)(1 << lr);
-  const double* u = uH + (size_t)b * gsz(nc);
+  const double* __restrict__ u = uH + (size_t)b * gsz(nc);
   double* x = x64 + (size_t)b * gsz(n);
   for_tile(n, ch, [&](int p, int i, int j) {
     const int I = i >> lr, J = j >> lr;
@@ -193,7 +194,7 @@ __global__ void k_rhs(int n, int B, const double* __restrict__ x64, double* __re
   const int ld = n + 1;
   const double hm = 1.0 / (12.0 * n * n);
   const size_t off = (size_t)b * gsz(n);
-  const double* x = x64 + off;
+  const double* __restrict__ x = x64 + off;
   double acc[1] = {0.0};
   for_tile(n, ch, [&](int p, int, int) {
     const double bv = hm * mass7(x, p, ld);
@@ -280,11 +281,11 @@ __global__ void k_smooth2_from_zero(int n, int B, const int* __restrict__ act, c
   if (b >= B || !act[b]) return;
   const int ld = n + 1;
   const size_t off = (size_t)b * gsz(n);
-  const T* W = wx + off;
-  const T* Y = wy + off;
-  const T* D = dinv + off;
-  const T* R = bb + off;
-  T* X = x + off;
+  const T* __restrict__ W = wx + off;
+  const T* __restrict__ Y = wy + off;
+  const T* __restrict__ D = dinv + off;
+  const T* __restrict__ R = bb + off;
+  T* __restrict__ X = x + off;
   for_tile(n, ch, [&](int p, int, int) {
     auto x1 = [&](int q) { return om * D[q] * R[q]; };
     const T xp = x1(p);
@@ -305,11 +306,11 @@ __global__ void k_restrict(int n, int B, const int* __restrict__ act, const T* _
   if (b >= B || !act[b]) return;
   const int ld = n + 1;
   const size_t off = (size_t)b * gsz(n);
-  const T* W = wx + off;
-  const T* Y = wy + off;
-  const T* R = bb + off;
-  const T* X = x + off;
-  T* C = bc + (size_t)b * gsz(m);
+  const T* __restrict__ W = wx + off;
+  const T* __restrict__ Y = wy + off;
+  const T* __restrict__ R = bb + off;
+  const T* __restrict__ X = x + off;
+  T* __restrict__ C = bc + (size_t)b * gsz(m);
   for_tile(m, ch, [&](int P, int I, int J) {
     const int p = (2 * J) * ld + 2 * I;
     auto res = [&](int q) { return R[q] - stiff<T, T>(W, Y, X, q, ld); };
@@ -328,13 +329,13 @@ __global__ void k_prolong_smooth(int n, int B, const int* __restrict__ act, cons
   if (b >= B || !act[b]) return;
   const int ld = n + 1, ldc = n / 2 + 1;
   const size_t off = (size_t)b * gsz(n);
-  const T* W = wx + off;
-  const T* Y = wy + off;
-  const T* D = dinv + off;
-  const T* R = bb + off;
-  const T* X = x + off;
-  const T* XC = xc + (size_t)b * gsz(n / 2);
-  T* O = out + off;
+  const T* __restrict__ W = wx + off;
+  const T* __restrict__ Y = wy + off;
+  const T* __restrict__ D = dinv + off;
+  const T* __restrict__ R = bb + off;
+  const T* __restrict__ X = x + off;
+  const T* __restrict__ XC = xc + (size_t)b * gsz(n / 2);
+  T* __restrict__ O = out + off;
   for_tile(n, ch, [&](int p, int i, int j) {
     auto t = [&](int q, int ii, int jj) {  // branch-free P1 interpolation (see vcycle)
       const int c0 = (jj >> 1) * ldc + (ii >> 1);
@@ -358,12 +359,12 @@ __global__ void k_smooth(int n, int B, const int* __restrict__ act, const T* __r
   if (b >= B || !act[b]) return;
   const int ld = n + 1;
   const size_t off = (size_t)b * gsz(n);
-  const T* W = wx + off;
-  const T* Y = wy + off;
-  const T* D = dinv + off;
-  const T* R = bb + off;
-  const T* X = t + off;
-  T* O = out + off;
+  const T* __restrict__ W = wx + off;
+  const T* __restrict__ Y = wy + off;
+  const T* __restrict__ D = dinv + off;
+  const T* __restrict__ R = bb + off;
+  const T* __restrict__ X = t + off;
+  T* __restrict__ O = out + off;
   T acc[1] = {T(0)};
   for_tile(n, ch, [&](int p, int, int) {
     const T o = X[p] + om * D[p] * (R[p] - stiff<T, T>(W, Y, X, p, ld));
@@ -464,9 +465,9 @@ __global__ void k_minres_q(int n, int B, const int* __restrict__ act, const SS<T
   const size_t off = (size_t)b * gsz(n);
   const SS<T> S = ss[b];
   const T sigm = S.sigm;
-  const T* W = wx + off;
-  const T* Y = wy + off;
-  const T* Z = z + off;
+  const T* __restrict__ W = wx + off;
+  const T* __restrict__ Y = wy + off;
+  const T* __restrict__ Z = z + off;
   T acc[1] = {T(0)};
   for_tile(n, ch, [&](int p, int, int) {
     if (S.pend) {
@@ -609,7 +610,8 @@ __global__ void k_outer_update(int n, int B, const SS<T>* __restrict__ ss, const
   for_tile(n, ch, [&](int p, int, int) { x64[off + p] += rn * (double)xi[off + p]; });
 }
 
-// FP64 residual r = b - (A - sigma M) x64 (weights formed from the centroid coefficients); v = T(r)
+// FP64 residual r = b - (A - sigma M) x64 (weights formed from the centroid coefficients); v = T(r).
+// Partials r.r, x.x, x.Ax, x.Mx: the last pass of a sample gives its Rayleigh quotient.
 template <typename T>
 __global__ void k_residual(int n, int B, const int* __restrict__ ran, const double* __restrict__ a, size_t astride,
                            const double* __restrict__ sigma, int sig_stride, const double* __restrict__ x64,
@@ -621,30 +623,39 @@ __global__ void k_residual(int n, int B, const int* __restrict__ ran, const doub
   const size_t off = (size_t)b * gsz(n);
   const double hm = 1.0 / (12.0 * n * n);
   const double sg = sigma[(size_t)b * sig_stride];
-  const double* ab = a + (size_t)b * astride;
-  const double* X = x64 + off;
-  double acc[2] = {0.0, 0.0};
+  const double* __restrict__ ab = a + (size_t)b * astride;
+  const double* __restrict__ X = x64 + off;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for_tile(n, ch, [&](int p, int i, int j) {
-    const double kx = stiff_cells(ab, n, X, p, ld, i, j) - sg * hm * mass7(X, p, ld);
-    const double r = b64[off + p] - kx;
+    const double xv = X[p];
+    const double ax = stiff_cells(ab, n, X, p, ld, i, j);
+    const double mx = hm * mass7(X, p, ld);
+    const double r = b64[off + p] - (ax - sg * mx);
     v[off + p] = T(r);
     acc[0] += r * r;
-    acc[1] += X[p] * X[p];
+    acc[1] += xv * xv;
+    acc[2] += xv * ax;
+    acc[3] += xv * mx;
   });
-  tile_partials<2, double>(acc, part, (size_t)b * nt + ch);
+  tile_partials<4, double>(acc, part, (size_t)b * nt + ch);
 }
 
 template <typename T>
 __global__ void k_sc_outer_end(int B, int nch, const double* part, const int* ran, SS<T>* ss) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B || !ran[b]) return;
-  double s = 0.0, sx = 0.0;
+  double s = 0.0, sx = 0.0, sa = 0.0, sm = 0.0;
   for (int k = 0; k < nch; ++k) {
-    s += part[((size_t)b * nch + k) * 2];
-    sx += part[((size_t)b * nch + k) * 2 + 1];
+    const double* pk = part + ((size_t)b * nch + k) * 4;
+    s += pk[0];
+    sx += pk[1];
+    sa += pk[2];
+    sm += pk[3];
   }
   SS<T>& S = ss[b];
   S.xnorm = sqrt(sx);
+  S.xax = sa;
+  S.xmx = sm;
   const double rnew = sqrt(s);
   // No progress: stop refining.  Not on the first step: on fine meshes the FP32 rounding of the
   // first inner solution alone leaves an FP64 residual above ||b|| (the operator amplifies its
@@ -655,41 +666,15 @@ __global__ void k_sc_outer_end(int B, int nch, const double* part, const int* ra
   S.outer += 1;
 }
 
-// Rayleigh quotient partials x.Ax, x.Mx (FP64)
 template <typename T>
-__global__ void k_rq(int n, int B, const double* __restrict__ a, size_t astride, const double* __restrict__ x64,
-                     double* part) {
-  const int nt = tiles_interior(n);
-  const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
-  if (b >= B) return;
-  const int ld = n + 1;
-  const size_t off = (size_t)b * gsz(n);
-  const double hm = 1.0 / (12.0 * n * n);
-  const double* ab = a + (size_t)b * astride;
-  const double* X = x64 + off;
-  double acc[2] = {0.0, 0.0};
-  for_tile(n, ch, [&](int p, int i, int j) {
-    const double x = X[p];
-    acc[0] += x * stiff_cells(ab, n, X, p, ld, i, j);
-    acc[1] += x * hm * mass7(X, p, ld);
-  });
-  tile_partials<2, double>(acc, part, (size_t)b * nt + ch);
-}
-
-template <typename T>
-__global__ void k_sc_rq(int B, int n, const double* sigma, int sig_stride, int nch, const double* part,
-                        const SS<T>* ss, double tol_lin, double* lam_out,
+__global__ void k_sc_rq(int B, int n, const double* sigma, int sig_stride, const SS<T>* ss, double tol_lin,
+                        double* lam_out,
                         int lam_stride, int* it_out, int it_stride, int* outer_out, int outer_stride, int* flags,
                         int flag_stride) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
-  double s0 = 0.0, s1 = 0.0;
-  for (int k = 0; k < nch; ++k) {
-    s0 += part[((size_t)b * nch + k) * 2];
-    s1 += part[((size_t)b * nch + k) * 2 + 1];
-  }
   const SS<T>& S = ss[b];
-  lam_out[(size_t)b * lam_stride] = s0 / s1;
+  lam_out[(size_t)b * lam_stride] = S.xax / S.xmx;
   it_out[(size_t)b * it_stride] = S.iters;
   outer_out[(size_t)b * outer_stride] = S.outer;
   int f = S.flags;
@@ -773,7 +758,7 @@ size_t carve_arena(void* base, int n, int B, Arena<T>& A) {
   A.subw = c.take<char>(Bz * A.subw_bytes + 256);
   A.subw = (char*)(((uintptr_t)A.subw + 255) & ~(uintptr_t)255);
   const int nch = tiles_interior(n) > 1 ? tiles_interior(n) : 1;
-  A.part = c.take<double>(Bz * nch * 2 + Bz);
+  A.part = c.take<double>(Bz * nch * 4 + Bz);
   A.ss = c.take<SS<T>>(Bz);
   A.act = c.take<int>(Bz);
   A.ran = c.take<int>(Bz);
@@ -956,9 +941,8 @@ cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st) {
     k_sc_outer_end<T><<<gs, 256, 0, st>>>(B, nt, A.part, A.ran, A.ss);
     LAUNCH_CHECK();
   }
-  // ---- Rayleigh quotient
-  k_rq<T><<<B * nt, kThreads, 0, st>>>(n, B, s.a, astride, A.x64, A.part);
-  k_sc_rq<T><<<gs, 256, 0, st>>>(B, n, s.lamH, s.lam_stride, nt, A.part, A.ss, s.tol_lin, s.lam_out, s.lam_out_stride, s.iters_out,
+  // ---- Rayleigh quotient (from each sample's last residual pass)
+  k_sc_rq<T><<<gs, 256, 0, st>>>(B, n, s.lamH, s.lam_stride, A.ss, s.tol_lin, s.lam_out, s.lam_out_stride, s.iters_out,
                                  s.iters_stride, s.outer_out, s.outer_stride, s.flags, s.flags_stride);
   LAUNCH_CHECK();
   return cudaSuccess;
