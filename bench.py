@@ -136,13 +136,14 @@ def time_device(binding, torch, wl, prec, steps, warmup, stream, seed_offset=0):
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
     # per-level device time of the timed region (CUDA events on the launching stream)
-    timing = [ctx.mq_get_level_timing(l) for l in range(len(wl.levels))]
+    timing = [ctx.mq_get_level_timing(l) + ctx.mq_get_kernel_timing(l) for l in range(len(wl.levels))]
+    launches = ctx.mq_get_launch_count()
     # iteration counts from one more (untimed, identical) pass
     kstats = {}
     for l, lv in enumerate(wl.levels):
         ctx.mq_eval_level_device(l, 0, lv.N, outs[l], sums[l])
         kstats[l] = [ctx.mq_get_stats()]
-    return ctx, ms, timing, kstats, outs
+    return ctx, ms, timing, kstats, outs, launches
 
 
 def time_e2e(binding, wl, prec, steps, stream_ptr):
@@ -229,39 +230,88 @@ def _pool_init():
 
 
 # ------------------------------------------------------------------------------------------
-# Bytes the per-sample kernel moves per unknown if every array access of every sweep goes to
-# memory once (the design's algorithmic traffic; derivation in the design doc section 6):
-#   fine solve, per inner MINRES + V-cycle iteration: 55 words of the inner precision;
-#   per FP64 refinement step: 52 inner words + 48 bytes; per solve (setup, RHS, Rayleigh
-#   quotient, clearing): 18 inner words + 88 bytes;
-#   coarse LOBPCG, per iteration: 390 bytes per coarse unknown.
-def sample_kernel_bytes(wl, level, st, prec):
-    e = 4 if prec == "mixed" else 8
+# Roofline models (derivations in the design doc, section 6).
+#
+# Per-sample kernel (one CTA per sample, workspace on chip): bounded by the FP64 units, whose
+# peak is 152 SMs x 2 FP64 FMA lanes per cycle x 2 flops x the SM clock.  FP64 operations
+# counted from the kernel source (a fused multiply-add counts two):
+#   coarse LOBPCG: 73 per coarse unknown and iteration (residual 6, A w and M w 19, Gram matrix
+#   24, update of x, Ax, Mx, p, Ap, Mp 24) + 46 per unknown and eigensolve (two operator
+#   applications with normalisation);
+#   fine solve with FP32 inner iterations: 23 per fine unknown (interpolation and right-hand side
+#   19, FP64 edge weights of the preconditioner 4) + 40 per unknown and refinement step (solution
+#   update 2, FP64 residual with the Rayleigh-quotient partials 38);
+#   fine solve with FP64 inner iterations (FP64 path, same-mesh solves): + 135 per unknown and
+#   inner iteration (operator 24, MINRES updates 12, V-cycle 99).
+FP64_EIG_IT, FP64_EIG_CALL, FP64_FINE_SETUP, FP64_FINE_OUTER, FP64_INNER = 73, 46, 23, 40, 135
+
+
+def stream_min_default(prec):
+    return 64 if prec == "mixed" else 256
+
+
+def percta_fp64_flops(wl, level, st, prec):
+    """FP64 operations of one launch of the per-sample kernel on `level` (all its samples)."""
     lv = wl.levels[level]
-    fine = []
-    if not (lv.n_fine == lv.n_coarse and lv.s == lv.S):
-        fine.append((lv.n_fine - 1) ** 2)
+    nc = lv.n_coarse
+    per = (nc - 1) ** 2 * (FP64_EIG_IT * st["coarse_iters_mean"] + FP64_EIG_CALL)
+    solves = []
+    if not (lv.n_fine == nc and lv.s == lv.S):
+        solves.append(lv.n_fine)
     if level > 0:
         pv = wl.levels[level - 1]
-        if not (pv.n_fine == lv.n_coarse and pv.s == lv.S):
-            fine.append((pv.n_fine - 1) ** 2)
+        if not (pv.n_fine == nc and pv.s == lv.S):
+            solves.append(pv.n_fine)
     I, O = st["fine_iters_mean"], st["outer_iters_mean"]
-    per_solve = lambda n: n * (55 * e * I + (52 * e + 48) * O + 18 * e + 88)
-    coarse = (lv.n_coarse - 1) ** 2 * 390 * st["coarse_iters_mean"]
-    return lv.N * lv.R * (sum(per_solve(n) for n in fine) + coarse)
+    for n in solves:
+        if n >= stream_min_default(prec) and n != nc:
+            continue  # batched streaming tier
+        inner64 = prec == "fp64" or n == nc
+        per += (n - 1) ** 2 * (FP64_FINE_SETUP + FP64_FINE_OUTER * O + (FP64_INNER * I if inner64 else 0))
+    return per * lv.N * lv.R
 
 
-# ncu DRAM traffic of the per-sample kernel, valid only for the source it was measured on
-# (profiles/sample_kernel_mlqmc4_h16_128.md); scaled per sample from a smaller capture
-SAMPLE_KERNEL_TRAFFIC = {"source_sha256": "18dde7f9e22ceb93a4d3dd9acfbb27fb013fd4ba22a94cb5482b15c6b21ad8a4",
-                         "level": 3, "bytes_per_sample": 61.458284e9 / 1024}
+# Streaming tier (fine meshes >= 1/64 mixed): bounded by HBM.  Bytes per fine unknown with every
+# kernel reading and writing each of its arrays once (e = 4 bytes, FP32 inner vectors):
+#   per inner MINRES iteration: MINRES sweeps 16 e (operator + pending update 10 e, Lanczos
+#   vector 6 e) + V-cycle 22.5 e on the fine level (two Jacobi sweeps from zero 5 e, residual
+#   restriction 4.25 e, prolongation + Jacobi 6.25 e, Jacobi + dot 7 e) + 21.5 e / 4 and / 16 on
+#   the two coarser levels above the on-chip sub-cycle;
+#   per refinement step: 12 e + 48 bytes (inner start 6 e, final update 5 e, FP64 solution update
+#   e + 16, FP64 residual e + 32) + one V-cycle;
+#   per solve: 20 e + 56 bytes (clearing 8 e + 16, weights 3 e + 16, interpolation and
+#   right-hand side e + 24, operators of the coarser levels ~8 e).
+def stream_bytes(wl, level, st, prec):
+    e = 4 if prec == "mixed" else 8
+    lv = wl.levels[level]
+    vcyc = 22.5 * e + 21.5 * e * (1 / 4 + 1 / 16)
+    I, O = st["fine_iters_mean"], st["outer_iters_mean"]
+    solves = []
+    if lv.n_fine >= stream_min_default(prec) and not (lv.n_fine == lv.n_coarse and lv.s == lv.S):
+        solves.append(lv.n_fine)
+    if level > 0:
+        pv = wl.levels[level - 1]
+        if pv.n_fine >= stream_min_default(prec) and pv.n_fine != lv.n_coarse:
+            solves.append(pv.n_fine)
+    per = 0.0
+    for n in solves:
+        per += (n - 1) ** 2 * ((16 * e + vcyc) * I + (12 * e + 48 + vcyc) * O + 20 * e + 56)
+    return per * lv.N * lv.R
 
 
-def _sample_source_hash():
+# ncu DRAM traffic of the per-sample kernel's launch on a level, valid only for the kernel source
+# it was measured on (profiles/sample_kernel_mlqmc4_h16_128_level1.md; one full-size launch)
+SAMPLE_KERNEL_TRAFFIC = {"source_sha256": "c93b91324d65bd97eede49493e7f1831b33a3a501456b12caabd2dedd3b8d12f",
+                         "level": 1, "precision": "mixed", "bytes_per_launch": 716.9984e6 + 29.254656e6}
+
+
+def _percta_source_hash():
     import hashlib
 
-    path = os.path.join(ROOT, "paper_2103_03407_gb300", "csrc", "mq_sample.cu")
-    return hashlib.sha256(open(path, "rb").read()).hexdigest()
+    h = hashlib.sha256()
+    for f in ("mq_sample.cu", "mq_device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2103_03407_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
 
 
 def hbm_peak():
@@ -276,26 +326,38 @@ def hbm_peak():
     return 6800.0, "fallback"
 
 
-def sample_kernel_roofline(wl, level, st, prec, ms_per_launch):
-    nbytes = sample_kernel_bytes(wl, level, st, prec)
+def fp64_peak_tflops(sm_max_mhz=None):
+    """FP64 FMA throughput from the unit counts: 152 SMs x 2 lanes x 2 flops per cycle."""
+    mhz = sm_max_mhz or 2070.0
+    return 152 * 2 * 2 * mhz * 1e6 / 1e12
+
+
+def percta_roofline(wl, level, st, prec, ms_per_launch, sm_max_mhz):
+    flops = percta_fp64_flops(wl, level, st, prec)
+    achieved = flops / (ms_per_launch * 1e-3) / 1e12
+    peak = fp64_peak_tflops(sm_max_mhz)
+    lv = wl.levels[level]
+    t = SAMPLE_KERNEL_TRAFFIC
+    traffic = None
+    if t["source_sha256"] == _percta_source_hash() and t["level"] == level and t["precision"] == prec:
+        traffic = t["bytes_per_launch"]
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": traffic,
+            "kernel": f"sample_kernel (level {level}: {lv.N * lv.R} samples per launch, "
+                      f"{ms_per_launch:.2f} ms per launch)",
+            "algorithmic_flops": flops,
+            "peak_kind": f"derived: FP64 units, 152 SMs x 4 flop/cycle x {sm_max_mhz or 2070:.0f} MHz"}
+
+
+def stream_roofline(wl, level, st, prec, ms_per_launch):
+    nbytes = stream_bytes(wl, level, st, prec)
     achieved = nbytes / (ms_per_launch * 1e-3) / 1e9
     peak, kind = hbm_peak()
     lv = wl.levels[level]
-    traffic = None
-    t = SAMPLE_KERNEL_TRAFFIC
-    if t["source_sha256"] and t["source_sha256"] == _sample_source_hash() and t["level"] == level:
-        traffic = t["bytes_per_sample"] * lv.N * lv.R
-    return {"bound": "hbm", "kernel": f"sample_kernel (level {level}, {lv.N * lv.R} samples per launch)",
-            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": f"streaming fine solves (level {level}: {lv.N * lv.R} samples, "
+                                       f"{ms_per_launch:.2f} ms per pass, all kernels of the stage)",
             "algorithmic_bytes": nbytes, "peak_kind": kind}
-
-
-def fp64_peak_tflops(clock_mhz=None):
-    """Nominal FP64 rate of a GB300 (1.25 TFLOP/s at the boost clock), scaled to the sampled clock."""
-    nominal = 1.25
-    if clock_mhz:
-        return nominal * clock_mhz / 2070.0
-    return nominal
 
 
 def main():
@@ -322,8 +384,8 @@ def main():
     torch.cuda.synchronize()
     with torch.cuda.stream(stream):
         with sampler:
-            ctx, ms, timing, kstats, outs = time_device(binding, torch, wl, args.precision, args.steps,
-                                                        args.warmup, stream, seed_offset=rank)
+            ctx, ms, timing, kstats, outs, launches = time_device(binding, torch, wl, args.precision, args.steps,
+                                                                  args.warmup, stream, seed_offset=rank)
     if world > 1:
         t = torch.tensor([ms], dtype=torch.float64, device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -332,7 +394,7 @@ def main():
     value = samples_per_step * args.steps / (ms / 1e3)
     plain = None
     if not args.no_plain and args.precision == "mixed" and rank == 0:
-        ctxp, msp, _, _, _ = time_device(binding, torch, wl, "fp64", 1, 1, stream)
+        ctxp, msp, _, _, _, _ = time_device(binding, torch, wl, "fp64", 1, 1, stream)
         plain = {"value": wl.samples / (msp / 1e3), "unit": "samples/s", "ms_per_step": msp, "steps": 1}
         ctxp.close()
     e2e = None
@@ -340,34 +402,37 @@ def main():
         dt, h2d, d2h = time_e2e(binding, wl, args.precision, max(1, args.steps), stream.cuda_stream)
         e2e = {"value": wl.samples * max(1, args.steps) / dt, "unit": "samples/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
-    # dominant kernel: the per-sample kernel of the level with the largest device time
-    lst = [kstats[l][-1] for l in range(len(wl.levels))]
-    sample_ms = [timing[l][1] / max(1, timing[l][2]) for l in range(len(wl.levels))]  # per launch
-    coef_ms = [timing[l][0] / max(1, timing[l][2]) for l in range(len(wl.levels))]
-    top = int(np.argmax(sample_ms))
+    # dominant kernel: the per-sample kernel launch with the largest device time; the streaming
+    # stage of the level where it takes longest is reported beside it
+    nl = len(wl.levels)
+    lst = [kstats[l][-1] for l in range(nl)]
+    per = lambda l, i: timing[l][i] / max(1, timing[l][2])  # per launch
+    coef_ms = [per(l, 0) for l in range(nl)]
+    sample_ms = [per(l, 1) for l in range(nl)]
+    percta_ms = [per(l, 3) for l in range(nl)]
+    stream_ms = [per(l, 4) for l in range(nl)]
     clocks = sampler.summary()
-    roofline = sample_kernel_roofline(wl, top, lst[top], args.precision, sample_ms[top])
+    top = int(np.argmax(percta_ms))
+    roofline = percta_roofline(wl, top, lst[top], args.precision, percta_ms[top], clocks.get("sm_max_mhz"))
+    stop = int(np.argmax(stream_ms))
+    roofline_stream = (stream_roofline(wl, stop, lst[stop], args.precision, stream_ms[stop])
+                       if stream_ms[stop] > 0 else None)
     result = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
-        "config": {"workload": wl.name, "levels": [lv.__dict__ for lv in wl.levels], "samples_per_step": wl.samples,
-                   "precision": args.precision, "l2": "inputs larger than L2 (coefficient fields of the finest "
-                   "level exceed 129 MB)", "parallelism": f"dp{world} (independent shifts per rank)"},
-        "e2e": e2e, "gpu_launches": None, "roofline": roofline, "clocks": clocks,
+        "config": workload_config(wl, args.precision, world),
+        "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "roofline_stream": roofline_stream,
+        "clocks": clocks,
         "per_level": [{"level": l, "kernel_ms": coef_ms[l] + sample_ms[l], "coef_ms": coef_ms[l],
-                       "sample_ms": sample_ms[l], "coarse_iters_mean": lst[l]["coarse_iters_mean"],
+                       "sample_ms": sample_ms[l], "percta_ms": percta_ms[l], "stream_ms": stream_ms[l],
+                       "coarse_iters_mean": lst[l]["coarse_iters_mean"],
                        "fine_iters_mean": lst[l]["fine_iters_mean"], "outer_iters_mean": lst[l]["outer_iters_mean"],
                        "blocks": lst[l]["blocks"], "threads": lst[l]["threads"], "smem": lst[l]["smem_bytes"],
                        "workspace": lst[l]["workspace_bytes"]} for l in range(len(wl.levels))],
         "plain_fp64": plain,
+        "gpu_launches_note": "kernels launched in the timed region, counted by the library",
     }
-    # kernels launched per step: per level lattice + 2-3 GEMMs + sample + shift sums
-    launches = 0
-    for l in range(len(wl.levels)):
-        launches += 1 + 1 + (0 if wl.levels[l].n_fine == wl.levels[l].n_coarse and wl.levels[l].s == wl.levels[l].S
-                             else 1) + (1 if l > 0 else 0) + 1 + 1
-    result["gpu_launches"] = launches * args.steps
     if rank == 0 and not args.no_baseline:
         result["cpu_baseline"] = cpu_baseline(wl, args.baseline_seconds, ctx_lattices(wl, binding),
                                               shifts(wl.seed, wl.levels))
@@ -375,6 +440,12 @@ def main():
         print(json.dumps(result))
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def workload_config(wl, precision, world):
+    return {"workload": wl.name, "levels": [lv.__dict__ for lv in wl.levels], "samples_per_step": wl.samples,
+            "precision": precision, "l2": "inputs larger than L2 (coefficient fields of the finest level exceed "
+            "129 MB)", "parallelism": f"dp{world} (independent shifts per rank)"}
 
 
 def ctx_lattices(wl, binding):
@@ -400,7 +471,7 @@ def main_reference(args, wl, rank, world):
     out = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": {"workload": wl.name, "samples_per_step": wl.samples},
+           "config": workload_config(wl, "fp64 (CPU oracle)", world),
            "cpu_baseline": {"kind": "oracle", "cores": info["cores"], "sample": info["sample"], "value": value,
                             "unit": "samples/s"},
            "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

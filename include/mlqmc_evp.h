@@ -131,6 +131,12 @@ mq_status mq_set_eig_options(mq_ctx* ctx, double tol_eig, int32_t max_eig);
  * stream_min_n = 0): 64 in MQ_PREC_MIXED, 256 in MQ_PREC_FP64. */
 mq_status mq_set_tier(mq_ctx* ctx, int32_t stream_min_n);
 
+/* Threads per CTA of the per-sample kernel (one CTA per sample) on level `level` (0 <= level < 64):
+ * 0 restores the default (128 for meshes up to 1/16, else 256), otherwise a multiple of 32 in
+ * [32, 512].  Fewer threads per sample let more samples share an SM; the results do not depend
+ * on it beyond rounding order. */
+mq_status mq_set_cta_threads(mq_ctx* ctx, int32_t level, int32_t threads);
+
 /* Evaluate level `level` at lattice indices k in [k0, k1) for every shift (Algorithm 2, steps
  * 5-15): per sample the coarse eigenpair on (H_l, S_l), lambda^l by Algorithm 1 on (h_l, s_l)
  * and, for l > 0, lambda^{l-1} on (h_{l-1}, s_{l-1}) from the same coarse pair.
@@ -164,6 +170,16 @@ mq_status mq_reset_sums(mq_ctx* ctx);
  * (sample_ms) and the number of per-sample kernel launches.  Any output may be NULL. */
 mq_status mq_get_level_timing(mq_ctx* ctx, int32_t level, double* coef_ms, double* sample_ms,
                               uint64_t* launches);
+
+/* The sample_ms of mq_get_level_timing split at the end of the per-sample kernel: percta_ms is the
+ * per-sample kernel launch alone (events on either side of it), stream_ms the batched streaming
+ * fine solves that follow it (zero when the level runs entirely in the per-sample kernel).  Any
+ * output may be NULL. */
+mq_status mq_get_kernel_timing(mq_ctx* ctx, int32_t level, double* percta_ms, double* stream_ms);
+
+/* Number of CUDA kernels this context has launched since mq_set_levels or mq_reset_sums (every
+ * call that evaluates samples, coefficients, lattice points or operators counts its launches). */
+mq_status mq_get_launch_count(mq_ctx* ctx, uint64_t* launches);
 
 /* Single explicit parameter vector y[0..s_l-1] on level `level`: the coarse eigenvalue
  * lambda_{H_l,S_l}(y), lambda^l(y) and (l > 0) lambda^{l-1}(y) (Algorithm 1).  Any output may

@@ -25,8 +25,8 @@ STATUS_NAMES = {0: "MQ_OK", 1: "MQ_EINVAL", 2: "MQ_ENOMEM", 3: "MQ_ECUDA", 4: "M
 # every symbol the header declares
 EXPORTS = [
     "mq_create", "mq_destroy", "mq_set_coefficient", "mq_set_levels", "mq_set_lattice", "mq_set_shifts",
-    "mq_set_precision", "mq_set_solver_options", "mq_set_eig_options", "mq_set_tier", "mq_eval_level", "mq_eval_level_device", "mq_estimate", "mq_reset_sums",
-    "mq_get_level_timing", "mq_eval_point",
+    "mq_set_precision", "mq_set_solver_options", "mq_set_eig_options", "mq_set_tier", "mq_set_cta_threads", "mq_eval_level", "mq_eval_level_device", "mq_estimate", "mq_reset_sums",
+    "mq_get_level_timing", "mq_get_kernel_timing", "mq_get_launch_count", "mq_eval_point",
     "mq_get_stats", "mq_last_error", "mq_cbc_lattice", "mq_lattice_points_device", "mq_coefficients_device",
     "mq_apply_operator_device", "mq_twogrid_samples_noalloc",
 ]
@@ -83,11 +83,14 @@ def load(path: str = LIB_PATH):
         "mq_set_tier": ([P, i32], C.c_int),
         "mq_set_solver_options": ([P, f64, i32, i32], C.c_int),
         "mq_set_eig_options": ([P, f64, i32], C.c_int),
+        "mq_set_cta_threads": ([P, i32, i32], C.c_int),
         "mq_eval_level": ([P, i32, u32, u32, dp, dp], C.c_int),
         "mq_eval_level_device": ([P, i32, u32, u32, P, P], C.c_int),
         "mq_estimate": ([P, dp, dp, dp, dp], C.c_int),
         "mq_reset_sums": ([P], C.c_int),
         "mq_get_level_timing": ([P, i32, dp, dp, C.POINTER(C.c_uint64)], C.c_int),
+        "mq_get_kernel_timing": ([P, i32, C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
+        "mq_get_launch_count": ([P, C.POINTER(C.c_uint64)], C.c_int),
         "mq_eval_point": ([P, i32, dp, dp, dp, dp, dp], C.c_int),
         "mq_get_stats": ([P, P, sz], C.c_int),
         "mq_last_error": ([P], C.c_char_p),
@@ -183,6 +186,9 @@ class Context:
     def mq_set_eig_options(self, tol_eig=0.0, max_eig=0):
         self._check(self.lib.mq_set_eig_options(self.h, float(tol_eig), int(max_eig)))
 
+    def mq_set_cta_threads(self, level, threads=0):
+        self._check(self.lib.mq_set_cta_threads(self.h, int(level), int(threads)))
+
     def mq_set_tier(self, stream_min_n=0):
         self._check(self.lib.mq_set_tier(self.h, int(stream_min_n)))
 
@@ -216,6 +222,17 @@ class Context:
         a, b, n = C.c_double(), C.c_double(), C.c_uint64()
         self._check(self.lib.mq_get_level_timing(self.h, int(level), C.byref(a), C.byref(b), C.byref(n)))
         return a.value, b.value, n.value
+
+    def mq_get_kernel_timing(self, level):
+        """(percta_ms, stream_ms): the per-sample kernel alone and the streaming solves."""
+        a, b = C.c_double(), C.c_double()
+        self._check(self.lib.mq_get_kernel_timing(self.h, int(level), C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def mq_get_launch_count(self):
+        n = C.c_uint64()
+        self._check(self.lib.mq_get_launch_count(self.h, C.byref(n)))
+        return n.value
 
     def mq_eval_point(self, level, y, want_u=False):
         y = np.ascontiguousarray(y, dtype=np.float64)

@@ -31,6 +31,8 @@ struct mq_ctx {
   bool own_stream = false;
   int sm_count = 0;
   int smem_optin = 0;
+  uint64_t n_launches = 0;  // kernels launched since mq_set_levels / mq_reset_sums
+  std::vector<int> cta_threads;  // per level: threads per CTA of the per-sample kernel (0: default)
   std::string err;
 
   bool coef_set = false;
@@ -49,6 +51,7 @@ struct mq_ctx {
   std::vector<uint64_t> npoints;          // per level: points evaluated
   std::vector<double> lvl_coef_ms, lvl_sample_ms;  // per level: accumulated device time
   std::vector<uint64_t> lvl_launches;              // per level: per-sample kernel launches
+  std::vector<double> lvl_percta_ms, lvl_stream_ms;  // per level: the per-sample kernel alone, the streaming tier
 
   int prec = MQ_PREC_FP64;
   double tol_lin = 0.0;  // 0: default of the precision mode
@@ -64,7 +67,7 @@ struct mq_ctx {
   int stream_min = 0;  // fine meshes 1/n with n >= stream_min use the streaming tier (0: default)
   mq_stats stats{};
   size_t last_B = 0;  // samples of the last pass (their per-sample counters are still on the device)
-  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace {
@@ -83,6 +86,13 @@ mq_status fail(mq_ctx* c, mq_status s, const char* fmt, ...) {
   do {                                                                                    \
     cudaError_t e_ = (call);                                                              \
     if (e_ != cudaSuccess) return fail(c, MQ_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+// a launch wrapper that starts exactly one kernel; counted for mq_get_launch_count
+#define MQ_LAUNCH(c, call) \
+  do {                     \
+    MQ_CUDA(c, call);      \
+    ++(c)->n_launches;     \
   } while (0)
 
 mq_status grow(mq_ctx* c, DevBuf& b, size_t bytes) {
@@ -135,7 +145,7 @@ mq_status ensure_psi(mq_ctx* c, int n, int rows, const double** out) {
     cudaGetLastError();
     return fail(c, MQ_ENOMEM, "psi table for n=%d, s=%d (%zu bytes)", n, rows, bytes);
   }
-  MQ_CUDA(c, mq::launch_psi_table(n, rows, c->d_k1, c->d_k2, c->d_cj, d, c->stream));
+  MQ_LAUNCH(c, mq::launch_psi_table(n, rows, c->d_k1, c->d_k2, c->d_cj, d, c->stream));
   c->psi[n] = {rows, d};
   *out = d;
   return MQ_OK;
@@ -160,7 +170,7 @@ mq_status ensure_psi_slices(mq_ctx* c, int n, const void** out, int* kpad) {
     cudaGetLastError();
     return fail(c, MQ_ENOMEM, "psi slices for n=%d (%zu bytes)", n, bytes);
   }
-  MQ_CUDA(c, mq::launch_psi_slices(psi, rows, nT, d, c->stream));
+  MQ_LAUNCH(c, mq::launch_psi_slices(psi, rows, nT, d, c->stream));
   c->psi_sl[n] = {mq::tc_pad_k(rows), d};
   *out = d;
   *kpad = mq::tc_pad_k(rows);
@@ -179,14 +189,14 @@ mq_status coefficients(mq_ctx* c, int n, int K, const double* d_Y, int B, int ld
     const int kpad = mq::tc_pad_k(K);
     if ((st = grow(c, c->ysl, mq::tc_slices_bytes(B, K))) != MQ_OK) return st;
     if ((st = grow(c, c->tc_err, sizeof(int))) != MQ_OK) return st;
-    MQ_CUDA(c, mq::launch_y_slices(d_Y, B, ldy, K, kpad, c->ysl.p, c->stream));
-    MQ_CUDA(c, mq::launch_coef_tc(c->ysl.p, B, kpad, ps, nT, kps, c->a0, d_a, (int*)c->tc_err.p, c->stream));
+    MQ_LAUNCH(c, mq::launch_y_slices(d_Y, B, ldy, K, kpad, c->ysl.p, c->stream));
+    MQ_LAUNCH(c, mq::launch_coef_tc(c->ysl.p, B, kpad, ps, nT, kps, c->a0, d_a, (int*)c->tc_err.p, c->stream));
     return MQ_OK;
   }
   const double* psi = nullptr;
   mq_status st = ensure_psi(c, n, std::max(c->s_max, 1), &psi);
   if (st != MQ_OK) return st;
-  MQ_CUDA(c, mq::launch_coef_gemm_f64(d_Y, ldy, B, K, psi, nT, c->a0, d_a, c->stream));
+  MQ_LAUNCH(c, mq::launch_coef_gemm_f64(d_Y, ldy, B, K, psi, nT, c->a0, d_a, c->stream));
   return MQ_OK;
 }
 
@@ -231,6 +241,7 @@ int threads_for(int n) { return n <= 16 ? 128 : 256; }
 
 struct LevelGeom {
   int nf, nc, np, s, S, sp, direct_f, direct_p;
+  int threads;  // requested threads per CTA of the per-sample kernel (0: default)
 };
 
 LevelGeom geom(const mq_ctx* c, int level) {
@@ -247,6 +258,7 @@ LevelGeom geom(const mq_ctx* c, int level) {
     g.sp = pv.s;
     g.direct_p = (pv.n_fine == lv.n_coarse && pv.s == lv.S);
   }
+  g.threads = level < (int)c->cta_threads.size() ? c->cta_threads[level] : 0;
   return g;
 }
 
@@ -336,7 +348,7 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
   }
   // FP64 inner solves in the per-sample kernel follow the FP64 defaults
   const int in_kernel_n = std::max(p.mode_f != 2 && !g.direct_f ? g.nf : 0, p.mode_p != 2 && !g.direct_p ? g.np : 0);
-  const int threads = threads_for(std::max(in_kernel_n, g.nc));
+  const int threads = g.threads > 0 ? g.threads : threads_for(std::max(in_kernel_n, g.nc));
   const size_t slab = mq::sample_slab_bytes(g.nf, g.nc, g.np, mixed, p.mode_f, p.mode_p);
   const int static_smem = mq::sample_static_smem(mixed);
   const size_t smem_cap = (size_t)std::max(0, c->smem_optin - static_smem - 1024);
@@ -355,8 +367,10 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
   p.gscratch = (char*)c->scratch.p;
   p.slab_bytes = slab;
   p.use_smem = use_smem;
-  MQ_CUDA(c, mq::launch_sample(p, mixed, blocks, threads, smem, c->stream));
+  MQ_LAUNCH(c, mq::launch_sample(p, mixed, blocks, threads, smem, c->stream));
+  MQ_CUDA(c, cudaEventRecord(c->ev[3], c->stream));
   if (ext) {
+    const uint64_t launched0 = mq::stream_launches();
     if ((st = grow(c, c->arena, mq::stream_arena_bytes(g.nf, (int)B, mixed))) != MQ_OK) return st;
     mq::StreamSolve s{};
     s.nc = g.nc;
@@ -391,6 +405,7 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
       MQ_CUDA(c, mq::stream_solve(s, mixed, c->arena.p, c->stream));
     }
     MQ_CUDA(c, mq::launch_finalize((int)B, (double*)c->out.p, g.np > 0, c->stream));
+    c->n_launches += mq::stream_launches() - launched0;
   }
   MQ_CUDA(c, cudaEventRecord(c->ev[2], c->stream));
   c->stats.blocks = blocks;
@@ -438,16 +453,19 @@ mq_status collect_stats(mq_ctx* c, size_t B, int* any_flags) {
 }
 
 mq_status timing(mq_ctx* c, int level) {
-  float t0 = 0, t1 = 0;
+  float t0 = 0, t1 = 0, t2 = 0;
   MQ_CUDA(c, cudaEventSynchronize(c->ev[2]));
   MQ_CUDA(c, cudaEventElapsedTime(&t0, c->ev[0], c->ev[1]));
   MQ_CUDA(c, cudaEventElapsedTime(&t1, c->ev[1], c->ev[2]));
+  MQ_CUDA(c, cudaEventElapsedTime(&t2, c->ev[1], c->ev[3]));
   c->stats.coef_ms += t0;
   c->stats.sample_ms += t1;
   c->stats.kernel_ms += t0 + t1;
   if (level >= 0 && level < (int)c->lvl_coef_ms.size()) {
     c->lvl_coef_ms[level] += t0;
     c->lvl_sample_ms[level] += t1;
+    c->lvl_percta_ms[level] += t2;
+    c->lvl_stream_ms[level] += t1 - t2;
     c->lvl_launches[level] += 1;
   }
   return MQ_OK;
@@ -503,13 +521,13 @@ mq_status eval_level_impl(mq_ctx* c, int level, uint32_t k0, uint32_t k1, double
     const int pn = std::min(ppp, npts - p0);
     const size_t B = (size_t)R * pn;
     if ((st = grow(c, c->Y, B * g.s * sizeof(double))) != MQ_OK) return st;
-    MQ_CUDA(c, mq::launch_lattice_points(c->d_z[level], lv.N, c->d_delta[level], R, g.s, k0 + p0, pn,
+    MQ_LAUNCH(c, mq::launch_lattice_points(c->d_z[level], lv.N, c->d_delta[level], R, g.s, k0 + p0, pn,
                                          (double*)c->Y.p, c->stream));
     if ((st = run_samples(c, g, R, pn, chunk_for(c, R, pn), false)) != MQ_OK) return st;
     if ((st = grow(c, c->sums_d, R * sizeof(double))) != MQ_OK) return st;
     if ((st = grow(c, c->flags_d, sizeof(int))) != MQ_OK) return st;
     MQ_CUDA(c, cudaMemsetAsync(c->flags_d.p, 0, sizeof(int), c->stream));
-    MQ_CUDA(c, mq::launch_shift_sums((const double*)c->out.p, (const int*)c->stat.p, R, pn, (double*)c->sums_d.p,
+    MQ_LAUNCH(c, mq::launch_shift_sums((const double*)c->out.p, (const int*)c->stat.p, R, pn, (double*)c->sums_d.p,
                                      (int*)c->flags_d.p, c->stream));
     std::vector<double> sums(R);
     int fl = 0;
@@ -683,6 +701,9 @@ mq_status mq_set_levels(mq_ctx* c, int32_t L_plus_1, const mq_level* levels) {
   c->lvl_coef_ms.assign(L_plus_1, 0.0);
   c->lvl_sample_ms.assign(L_plus_1, 0.0);
   c->lvl_launches.assign(L_plus_1, 0);
+  c->lvl_percta_ms.assign(L_plus_1, 0.0);
+  c->n_launches = 0;
+  c->lvl_stream_ms.assign(L_plus_1, 0.0);
   return MQ_OK;
 }
 
@@ -746,6 +767,16 @@ mq_status mq_set_eig_options(mq_ctx* c, double tol_eig, int32_t max_eig) {
   return MQ_OK;
 }
 
+mq_status mq_set_cta_threads(mq_ctx* c, int32_t level, int32_t threads) {
+  if (!c) return MQ_EINVAL;
+  if (level < 0 || level >= 64) return fail(c, MQ_EINVAL, "level %d out of range", (int)level);
+  if (threads != 0 && (threads < 32 || threads > 512 || threads % 32 != 0))
+    return fail(c, MQ_EINVAL, "threads must be 0 or a multiple of 32 in [32, 512]");
+  if ((int)c->cta_threads.size() <= level) c->cta_threads.resize(level + 1, 0);
+  c->cta_threads[level] = threads;
+  return MQ_OK;
+}
+
 mq_status mq_set_tier(mq_ctx* c, int32_t stream_min_n) {
   if (!c) return MQ_EINVAL;
   if (stream_min_n < 0 || stream_min_n == 1) return fail(c, MQ_EINVAL, "stream_min_n must be 0 or >= 2");
@@ -771,6 +802,9 @@ mq_status mq_reset_sums(mq_ctx* c) {
   std::fill(c->lvl_coef_ms.begin(), c->lvl_coef_ms.end(), 0.0);
   std::fill(c->lvl_sample_ms.begin(), c->lvl_sample_ms.end(), 0.0);
   std::fill(c->lvl_launches.begin(), c->lvl_launches.end(), 0);
+  std::fill(c->lvl_percta_ms.begin(), c->lvl_percta_ms.end(), 0.0);
+  c->n_launches = 0;
+  std::fill(c->lvl_stream_ms.begin(), c->lvl_stream_ms.end(), 0.0);
   return MQ_OK;
 }
 
@@ -780,6 +814,20 @@ mq_status mq_get_level_timing(mq_ctx* c, int32_t level, double* coef_ms, double*
   if (coef_ms) *coef_ms = c->lvl_coef_ms[level];
   if (sample_ms) *sample_ms = c->lvl_sample_ms[level];
   if (launches) *launches = c->lvl_launches[level];
+  return MQ_OK;
+}
+
+mq_status mq_get_kernel_timing(mq_ctx* c, int32_t level, double* percta_ms, double* stream_ms) {
+  if (!c) return MQ_EINVAL;
+  if (level < 0 || level >= (int)c->lvl_percta_ms.size()) return fail(c, MQ_EINVAL, "level %d out of range", level);
+  if (percta_ms) *percta_ms = c->lvl_percta_ms[level];
+  if (stream_ms) *stream_ms = c->lvl_stream_ms[level];
+  return MQ_OK;
+}
+
+mq_status mq_get_launch_count(mq_ctx* c, uint64_t* launches) {
+  if (!c || !launches) return MQ_EINVAL;
+  *launches = c->n_launches;
   return MQ_OK;
 }
 
@@ -888,7 +936,7 @@ mq_status mq_lattice_points_device(mq_ctx* c, int32_t level, uint32_t k0, uint32
   const mq_level& lv = c->levels[level];
   if (k1 < k0 || k1 > lv.N || !d_Y) return fail(c, MQ_EINVAL, "bad point range or output");
   MQ_CUDA(c, cudaSetDevice(c->device));
-  MQ_CUDA(c, mq::launch_lattice_points(c->d_z[level], lv.N, c->d_delta[level], lv.R, lv.s, k0, (int)(k1 - k0), d_Y,
+  MQ_LAUNCH(c, mq::launch_lattice_points(c->d_z[level], lv.N, c->d_delta[level], lv.R, lv.s, k0, (int)(k1 - k0), d_Y,
                                        c->stream));
   MQ_CUDA(c, cudaStreamSynchronize(c->stream));
   return MQ_OK;
@@ -917,7 +965,7 @@ mq_status mq_apply_operator_device(mq_ctx* c, int32_t n, int32_t B, const double
   MQ_CUDA(c, cudaSetDevice(c->device));
   mq_status st = grow(c, c->misc, (size_t)B * 3 * (n + 1) * (n + 1) * sizeof(double));
   if (st != MQ_OK) return st;
-  MQ_CUDA(c, mq::launch_apply_operator(n, B, d_a, which, sigma, d_x, d_y, (double*)c->misc.p, c->stream));
+  MQ_LAUNCH(c, mq::launch_apply_operator(n, B, d_a, which, sigma, d_x, d_y, (double*)c->misc.p, c->stream));
   MQ_CUDA(c, cudaStreamSynchronize(c->stream));
   return MQ_OK;
 }

@@ -60,6 +60,8 @@ struct StreamSolve {
 };
 size_t stream_arena_bytes(int n, int B, int mixed);
 cudaError_t stream_solve(const StreamSolve& s, int mixed, void* arena, cudaStream_t st);
+// kernels the streaming tier has launched from the calling thread (monotone counter)
+uint64_t stream_launches();
 cudaError_t launch_finalize(int B, double* d_out, int has_prev, cudaStream_t st);
 
 // Tensor-core (tcgen05) coefficient GEMM with exact BF16 slices (mq_tc.cu); slices are [7][rows pad][K pad]

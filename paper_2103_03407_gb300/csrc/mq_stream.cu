@@ -31,6 +31,9 @@ namespace {
 
 using namespace dev;
 
+// kernels launched by this thread from this file (read by the host API to report launch counts)
+thread_local uint64_t tl_launches = 0;
+
 constexpr int kThreads = 256;
 constexpr int kPer = 4;                      // nodes per thread per tile
 constexpr int kTile = kThreads * kPer;       // nodes per CTA
@@ -95,7 +98,7 @@ __device__ __forceinline__ void tile_partials(A (&v)[NV], double* part, size_t s
 // weights and inverse diagonal of mesh n from per-triangle coefficients (lower plane, upper plane)
 template <typename T, typename S>
 __global__ void k_weights(int n, int B, const S* __restrict__ cells, size_t cstride, T* __restrict__ wx,
-                          T* __restrict__ wy, T* __restrict__ dinv, const int* __restrict__ act, SS<T>* ss) {
+                          T* __restrict__ wy, T* __restrict__ dinv, T om, const int* __restrict__ act, SS<T>* ss) {
   const int nt = tiles_padded(n);
   const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
   if (b >= B || (act && !act[b])) return;
@@ -122,7 +125,7 @@ __global__ void k_weights(int n, int B, const S* __restrict__ cells, size_t cstr
       const double l0 = LO(i, j), l1 = LO(i - 1, j), l2 = LO(i - 1, j - 1);
       const double u0 = UP(i, j), u1 = UP(i, j - 1), u2 = UP(i - 1, j - 1);
       const T we = T(0.5 * (l0 + u1)), ww = T(0.5 * (l1 + u2)), wn = T(0.5 * (u0 + l1)), ws = T(0.5 * (u1 + l2));
-      d = T(1) / (we + ww + wn + ws);
+      d = om / (we + ww + wn + ws);  // the damped Jacobi factor omega D^-1
     }
     wx[(size_t)b * V + q] = a;
     wy[(size_t)b * V + q] = c;
@@ -271,11 +274,11 @@ __global__ void k_inner_init(int n, int B, const int* __restrict__ act, const SS
 
 // ---------------------------------------------------------------------------------------------
 // V-cycle kernels (mesh n > kSub)
-// two damped Jacobi steps from zero: x1 = om D^-1 b, x = x1 + om D^-1 (b - A x1)
+// two damped Jacobi steps from zero: x1 = om D^-1 b, x = x1 + om D^-1 (b - A x1); dinv holds om D^-1
 template <typename T>
 __global__ void k_smooth2_from_zero(int n, int B, const int* __restrict__ act, const T* __restrict__ wx,
                                     const T* __restrict__ wy, const T* __restrict__ dinv, const T* __restrict__ bb,
-                                    T* __restrict__ x, T om) {
+                                    T* __restrict__ x) {
   const int nt = tiles_interior(n);
   const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
   if (b >= B || !act[b]) return;
@@ -287,11 +290,11 @@ __global__ void k_smooth2_from_zero(int n, int B, const int* __restrict__ act, c
   const T* __restrict__ R = bb + off;
   T* __restrict__ X = x + off;
   for_tile(n, ch, [&](int p, int, int) {
-    auto x1 = [&](int q) { return om * D[q] * R[q]; };
+    auto x1 = [&](int q) { return D[q] * R[q]; };
     const T xp = x1(p);
     const T ax = W[p] * (xp - x1(p + 1)) + W[p - 1] * (xp - x1(p - 1)) + Y[p] * (xp - x1(p + ld)) +
                  Y[p - ld] * (xp - x1(p - ld));
-    X[p] = xp + om * D[p] * (R[p] - ax);
+    X[p] = xp + D[p] * (R[p] - ax);
   });
 }
 
@@ -323,7 +326,7 @@ __global__ void k_restrict(int n, int B, const int* __restrict__ act, const T* _
 template <typename T>
 __global__ void k_prolong_smooth(int n, int B, const int* __restrict__ act, const T* __restrict__ wx,
                                  const T* __restrict__ wy, const T* __restrict__ dinv, const T* __restrict__ bb,
-                                 const T* __restrict__ x, const T* __restrict__ xc, T* __restrict__ out, T om) {
+                                 const T* __restrict__ x, const T* __restrict__ xc, T* __restrict__ out) {
   const int nt = tiles_interior(n);
   const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
   if (b >= B || !act[b]) return;
@@ -344,7 +347,7 @@ __global__ void k_prolong_smooth(int n, int B, const int* __restrict__ act, cons
     const T tp = t(p, i, j);
     const T ax = W[p] * (tp - t(p + 1, i + 1, j)) + W[p - 1] * (tp - t(p - 1, i - 1, j)) +
                  Y[p] * (tp - t(p + ld, i, j + 1)) + Y[p - ld] * (tp - t(p - ld, i, j - 1));
-    O[p] = tp + om * D[p] * (R[p] - ax);
+    O[p] = tp + D[p] * (R[p] - ax);
   });
 }
 
@@ -352,7 +355,7 @@ __global__ void k_prolong_smooth(int n, int B, const int* __restrict__ act, cons
 template <typename T, bool DOT>
 __global__ void k_smooth(int n, int B, const int* __restrict__ act, const T* __restrict__ wx,
                          const T* __restrict__ wy, const T* __restrict__ dinv, const T* __restrict__ bb,
-                         const T* __restrict__ t, T* __restrict__ out, T om, const T* __restrict__ dotv,
+                         const T* __restrict__ t, T* __restrict__ out, const T* __restrict__ dotv,
                          double* part) {
   const int nt = tiles_interior(n);
   const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
@@ -367,7 +370,7 @@ __global__ void k_smooth(int n, int B, const int* __restrict__ act, const T* __r
   T* __restrict__ O = out + off;
   T acc[1] = {T(0)};
   for_tile(n, ch, [&](int p, int, int) {
-    const T o = X[p] + om * D[p] * (R[p] - stiff<T, T>(W, Y, X, p, ld));
+    const T o = X[p] + D[p] * (R[p] - stiff<T, T>(W, Y, X, p, ld));
     O[p] = o;
     if (DOT) acc[0] += dotv[off + p] * o;
   });
@@ -778,7 +781,7 @@ cudaError_t vcycle_stream(Arena<T>& A, const T* b0, T* x0, const int* act, T om,
                           size_t sub_smem, cudaStream_t st) {
   const int n = A.n, B = A.B;
   if (A.Ls == 0) {
-    k_subcycle<T><<<B, kThreads, sub_smem, st>>>(n, B, act, A.subw, A.subw_bytes, b0, x0, 2, om, part, dotv);
+    ++tl_launches, k_subcycle<T><<<B, kThreads, sub_smem, st>>>(n, B, act, A.subw, A.subw_bytes, b0, x0, 2, om, part, dotv);
     LAUNCH_CHECK();
     return cudaSuccess;
   }
@@ -786,15 +789,15 @@ cudaError_t vcycle_stream(Arena<T>& A, const T* b0, T* x0, const int* act, T om,
     const int nl = n >> l;
     const T* b = l ? A.b[l] : b0;
     T* xa = l ? A.x[l] : x0;
-    k_smooth2_from_zero<T><<<B * tiles_interior(nl), kThreads, 0, st>>>(nl, B, act, A.wx[l], A.wy[l], A.dinv[l],
-                                                                       b, xa, om);
+    ++tl_launches, k_smooth2_from_zero<T><<<B * tiles_interior(nl), kThreads, 0, st>>>(nl, B, act, A.wx[l], A.wy[l], A.dinv[l],
+                                                                       b, xa);
     LAUNCH_CHECK();
     T* bc = (l + 1 < A.Ls) ? A.b[l + 1] : A.bsub;
-    k_restrict<T><<<B * tiles_interior(nl / 2), kThreads, 0, st>>>(nl, B, act, A.wx[l], A.wy[l], b, xa, bc);
+    ++tl_launches, k_restrict<T><<<B * tiles_interior(nl / 2), kThreads, 0, st>>>(nl, B, act, A.wx[l], A.wy[l], b, xa, bc);
     LAUNCH_CHECK();
   }
   const int ns = n >> A.Ls;
-  k_subcycle<T><<<B, kThreads, sub_smem, st>>>(ns, B, act, A.subw, A.subw_bytes, A.bsub, A.xsub, 2, om, nullptr,
+  ++tl_launches, k_subcycle<T><<<B, kThreads, sub_smem, st>>>(ns, B, act, A.subw, A.subw_bytes, A.bsub, A.xsub, 2, om, nullptr,
                                                 nullptr);
   LAUNCH_CHECK();
   for (int l = A.Ls - 1; l >= 0; --l) {
@@ -802,15 +805,15 @@ cudaError_t vcycle_stream(Arena<T>& A, const T* b0, T* x0, const int* act, T om,
     const T* b = l ? A.b[l] : b0;
     T* xa = l ? A.x[l] : x0;
     const T* xc = (l + 1 < A.Ls) ? A.x[l + 1] : A.xsub;
-    k_prolong_smooth<T><<<B * tiles_interior(nl), kThreads, 0, st>>>(nl, B, act, A.wx[l], A.wy[l], A.dinv[l], b,
-                                                                    xa, xc, A.t[l], om);
+    ++tl_launches, k_prolong_smooth<T><<<B * tiles_interior(nl), kThreads, 0, st>>>(nl, B, act, A.wx[l], A.wy[l], A.dinv[l], b,
+                                                                    xa, xc, A.t[l]);
     LAUNCH_CHECK();
     if (l == 0 && dotv)
-      k_smooth<T, true><<<B * tiles_interior(nl), kThreads, 0, st>>>(nl, B, act, A.wx[l], A.wy[l], A.dinv[l], b,
-                                                                    A.t[l], xa, om, dotv, part);
+      ++tl_launches, k_smooth<T, true><<<B * tiles_interior(nl), kThreads, 0, st>>>(nl, B, act, A.wx[l], A.wy[l], A.dinv[l], b,
+                                                                    A.t[l], xa, dotv, part);
     else
-      k_smooth<T, false><<<B * tiles_interior(nl), kThreads, 0, st>>>(nl, B, act, A.wx[l], A.wy[l], A.dinv[l], b,
-                                                                     A.t[l], xa, om, nullptr, nullptr);
+      ++tl_launches, k_smooth<T, false><<<B * tiles_interior(nl), kThreads, 0, st>>>(nl, B, act, A.wx[l], A.wy[l], A.dinv[l], b,
+                                                                     A.t[l], xa, nullptr, nullptr);
     LAUNCH_CHECK();
   }
   return cudaSuccess;
@@ -842,88 +845,88 @@ cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st) {
   const size_t V0 = A.V0;
   T* const vecs[8] = {A.v, A.vo, A.z, A.zn, A.w, A.wo, A.q, A.xi};
   for (int k = 0; k < 8; ++k) {
-    k_zero<T><<<grid1(Bz * V0), 256, 0, st>>>(Bz * V0, vecs[k]);
+    ++tl_launches, k_zero<T><<<grid1(Bz * V0), 256, 0, st>>>(Bz * V0, vecs[k]);
     LAUNCH_CHECK();
   }
-  k_zero<double><<<grid1(Bz * V0), 256, 0, st>>>(Bz * V0, A.x64);
-  k_zero<double><<<grid1(Bz * V0), 256, 0, st>>>(Bz * V0, A.b64);
+  ++tl_launches, k_zero<double><<<grid1(Bz * V0), 256, 0, st>>>(Bz * V0, A.x64);
+  ++tl_launches, k_zero<double><<<grid1(Bz * V0), 256, 0, st>>>(Bz * V0, A.b64);
   for (int l = 0; l < A.Ls; ++l) {
     const size_t V = gsz(n >> l);
     T* const lv[3] = {A.t[l], A.x[l], A.b[l]};
     for (int k = 0; k < 3; ++k)
-      if (lv[k]) k_zero<T><<<grid1(Bz * V), 256, 0, st>>>(Bz * V, lv[k]);
+      if (lv[k]) ++tl_launches, k_zero<T><<<grid1(Bz * V), 256, 0, st>>>(Bz * V, lv[k]);
   }
   if (A.Ls) {
-    k_zero<T><<<grid1(Bz * gsz(ns)), 256, 0, st>>>(Bz * gsz(ns), A.bsub);
-    k_zero<T><<<grid1(Bz * gsz(ns)), 256, 0, st>>>(Bz * gsz(ns), A.xsub);
+    ++tl_launches, k_zero<T><<<grid1(Bz * gsz(ns)), 256, 0, st>>>(Bz * gsz(ns), A.bsub);
+    ++tl_launches, k_zero<T><<<grid1(Bz * gsz(ns)), 256, 0, st>>>(Bz * gsz(ns), A.xsub);
   }
-  k_zero<int><<<grid1(Bz * sizeof(SS<T>) / sizeof(int)), 256, 0, st>>>(Bz * sizeof(SS<T>) / sizeof(int), (int*)A.ss);
+  ++tl_launches, k_zero<int><<<grid1(Bz * sizeof(SS<T>) / sizeof(int)), 256, 0, st>>>(Bz * sizeof(SS<T>) / sizeof(int), (int*)A.ss);
   LAUNCH_CHECK();
   const size_t astride = (size_t)2 * n * n;
   for (int l = 0; l < (A.Ls > 1 ? A.Ls : 1); ++l) {
     const int nl = n >> l;
     if (l == 0)
-      k_weights<T, double><<<B * tiles_padded(nl), kThreads, 0, st>>>(nl, B, s.a, astride, A.wx[0], A.wy[0],
-                                                                     A.dinv[0], nullptr, A.ss);
+      ++tl_launches, k_weights<T, double><<<B * tiles_padded(nl), kThreads, 0, st>>>(nl, B, s.a, astride, A.wx[0], A.wy[0],
+                                                                     A.dinv[0], om, nullptr, A.ss);
     else
-      k_weights<T, T><<<B * tiles_padded(nl), kThreads, 0, st>>>(nl, B, A.cells[l], (size_t)2 * nl * nl, A.wx[l],
-                                                                A.wy[l], A.dinv[l], nullptr, nullptr);
+      ++tl_launches, k_weights<T, T><<<B * tiles_padded(nl), kThreads, 0, st>>>(nl, B, A.cells[l], (size_t)2 * nl * nl, A.wx[l],
+                                                                A.wy[l], A.dinv[l], om, nullptr, nullptr);
     LAUNCH_CHECK();
     if (l >= A.Ls) continue;
     const int m = nl / 2;
     const int ntc = (int)(((size_t)m * m + kTile - 1) / kTile);
     if (l == 0)
-      k_coarsen<double, T><<<B * ntc, kThreads, 0, st>>>(nl, B, s.a, astride, A.cells[1]);
+      ++tl_launches, k_coarsen<double, T><<<B * ntc, kThreads, 0, st>>>(nl, B, s.a, astride, A.cells[1]);
     else
-      k_coarsen<T, T><<<B * ntc, kThreads, 0, st>>>(nl, B, A.cells[l], (size_t)2 * nl * nl, A.cells[l + 1]);
+      ++tl_launches, k_coarsen<T, T><<<B * ntc, kThreads, 0, st>>>(nl, B, A.cells[l], (size_t)2 * nl * nl, A.cells[l + 1]);
     LAUNCH_CHECK();
   }
   if (A.Ls == 0) {
-    k_convert<double, T><<<grid1(Bz * astride), 256, 0, st>>>(Bz * astride, s.a, A.cells[0]);
+    ++tl_launches, k_convert<double, T><<<grid1(Bz * astride), 256, 0, st>>>(Bz * astride, s.a, A.cells[0]);
     LAUNCH_CHECK();
   }
-  k_sub_build<T><<<B, kThreads, sub_smem, st>>>(ns, B, A.cells[A.Ls], A.subw, A.subw_bytes);
+  ++tl_launches, k_sub_build<T><<<B, kThreads, sub_smem, st>>>(ns, B, A.cells[A.Ls], A.subw, A.subw_bytes);
   LAUNCH_CHECK();
   // ---- right-hand side b = M P u_H
-  k_interp<T><<<B * nt, kThreads, 0, st>>>(n, s.nc, B, s.uH, A.x64);
+  ++tl_launches, k_interp<T><<<B * nt, kThreads, 0, st>>>(n, s.nc, B, s.uH, A.x64);
   LAUNCH_CHECK();
-  k_rhs<T><<<B * nt, kThreads, 0, st>>>(n, B, A.x64, A.b64, A.v, A.part);
+  ++tl_launches, k_rhs<T><<<B * nt, kThreads, 0, st>>>(n, B, A.x64, A.b64, A.v, A.part);
   LAUNCH_CHECK();
-  k_zero<double><<<grid1(Bz * V0), 256, 0, st>>>(Bz * V0, A.x64);
-  k_sc_start<T><<<gs, 256, 0, st>>>(B, n, s.lamH, s.lam_stride, nt, A.part, A.ss);
+  ++tl_launches, k_zero<double><<<grid1(Bz * V0), 256, 0, st>>>(Bz * V0, A.x64);
+  ++tl_launches, k_sc_start<T><<<gs, 256, 0, st>>>(B, n, s.lamH, s.lam_stride, nt, A.part, A.ss);
   LAUNCH_CHECK();
   // ---- refinement loop
   for (int o = 0; o < s.max_outer; ++o) {
     cudaMemsetAsync(A.count, 0, sizeof(int), st);
-    k_sc_outer_begin<T><<<gs, 256, 0, st>>>(B, n, s.lamH, s.lam_stride, s.tol_lin, A.ss, A.act, A.count);
+    ++tl_launches, k_sc_outer_begin<T><<<gs, 256, 0, st>>>(B, n, s.lamH, s.lam_stride, s.tol_lin, A.ss, A.act, A.count);
     LAUNCH_CHECK();
     int active = read_count(A.count, st, e);
     if (e != cudaSuccess) return e;
     if (active == 0) break;
     cudaMemcpyAsync(A.ran, A.act, Bz * sizeof(int), cudaMemcpyDeviceToDevice, st);
-    k_inner_init<T><<<B * nt, kThreads, 0, st>>>(n, B, A.act, A.ss, A.v, A.vo, A.w, A.wo, A.xi);
+    ++tl_launches, k_inner_init<T><<<B * nt, kThreads, 0, st>>>(n, B, A.act, A.ss, A.v, A.vo, A.w, A.wo, A.xi);
     LAUNCH_CHECK();
     T *v = A.v, *vo = A.vo, *z = A.z, *zn = A.zn, *w = A.w, *wo = A.wo;
     e = vcycle_stream<T>(A, v, z, A.act, om, v, A.part, sub_smem, st);
     if (e != cudaSuccess) return e;
     const int nchd = A.Ls ? nt : 1;  // partial slots of <v, z>
-    k_sc_gamma0<T><<<gs, 256, 0, st>>>(B, nchd, A.part, A.act, A.ss);
+    ++tl_launches, k_sc_gamma0<T><<<gs, 256, 0, st>>>(B, nchd, A.part, A.act, A.ss);
     LAUNCH_CHECK();
     for (int j = 0; j < s.max_inner; ++j) {
-      k_minres_q<T><<<B * nt, kThreads, 0, st>>>(n, B, A.act, A.ss, A.wx[0], A.wy[0], s.lamH, s.lam_stride, z, zn,
+      ++tl_launches, k_minres_q<T><<<B * nt, kThreads, 0, st>>>(n, B, A.act, A.ss, A.wx[0], A.wy[0], s.lamH, s.lam_stride, z, zn,
                                                  wo, w, A.xi, A.q, A.part);
       LAUNCH_CHECK();
       // samples that converged in the previous Givens step have now applied their update
-      k_sc_retire<T><<<gs, 256, 0, st>>>(B, A.act, A.ss);
+      ++tl_launches, k_sc_retire<T><<<gs, 256, 0, st>>>(B, A.act, A.ss);
       { T* tt = wo; wo = w; w = tt; }
-      k_sc_delta<T><<<gs, 256, 0, st>>>(B, nt, A.part, A.act, A.ss);
-      k_minres_v<T><<<B * nt, kThreads, 0, st>>>(n, B, A.act, A.ss, A.q, v, vo, z);
+      ++tl_launches, k_sc_delta<T><<<gs, 256, 0, st>>>(B, nt, A.part, A.act, A.ss);
+      ++tl_launches, k_minres_v<T><<<B * nt, kThreads, 0, st>>>(n, B, A.act, A.ss, A.q, v, vo, z);
       LAUNCH_CHECK();
       { T* tt = vo; vo = v; v = tt; }
       e = vcycle_stream<T>(A, v, zn, A.act, om, v, A.part, sub_smem, st);
       if (e != cudaSuccess) return e;
       cudaMemsetAsync(A.count, 0, sizeof(int), st);
-      k_sc_givens<T><<<gs, 256, 0, st>>>(B, nchd, A.part, A.act, A.ss, T(s.tol_inner), A.count);
+      ++tl_launches, k_sc_givens<T><<<gs, 256, 0, st>>>(B, nchd, A.part, A.act, A.ss, T(s.tol_inner), A.count);
       LAUNCH_CHECK();
       { T* tt = z; z = zn; zn = tt; }
       if ((j & 3) == 3 || j + 1 == s.max_inner) {
@@ -933,16 +936,16 @@ cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st) {
       }
     }
     // apply the pending updates of every sample that ran this step (converged or capped)
-    k_minres_finish<T><<<B * nt, kThreads, 0, st>>>(n, B, A.ran, A.ss, zn, wo, w, A.xi);
+    ++tl_launches, k_minres_finish<T><<<B * nt, kThreads, 0, st>>>(n, B, A.ran, A.ss, zn, wo, w, A.xi);
     LAUNCH_CHECK();
-    k_outer_update<T><<<B * nt, kThreads, 0, st>>>(n, B, A.ss, A.ran, A.xi, A.x64);
-    k_residual<T><<<B * nt, kThreads, 0, st>>>(n, B, A.ran, s.a, astride, s.lamH, s.lam_stride, A.x64, A.b64, A.v,
+    ++tl_launches, k_outer_update<T><<<B * nt, kThreads, 0, st>>>(n, B, A.ss, A.ran, A.xi, A.x64);
+    ++tl_launches, k_residual<T><<<B * nt, kThreads, 0, st>>>(n, B, A.ran, s.a, astride, s.lamH, s.lam_stride, A.x64, A.b64, A.v,
                                                A.part);
-    k_sc_outer_end<T><<<gs, 256, 0, st>>>(B, nt, A.part, A.ran, A.ss);
+    ++tl_launches, k_sc_outer_end<T><<<gs, 256, 0, st>>>(B, nt, A.part, A.ran, A.ss);
     LAUNCH_CHECK();
   }
   // ---- Rayleigh quotient (from each sample's last residual pass)
-  k_sc_rq<T><<<gs, 256, 0, st>>>(B, n, s.lamH, s.lam_stride, A.ss, s.tol_lin, s.lam_out, s.lam_out_stride, s.iters_out,
+  ++tl_launches, k_sc_rq<T><<<gs, 256, 0, st>>>(B, n, s.lamH, s.lam_stride, A.ss, s.tol_lin, s.lam_out, s.lam_out_stride, s.iters_out,
                                  s.iters_stride, s.outer_out, s.outer_stride, s.flags, s.flags_stride);
   LAUNCH_CHECK();
   return cudaSuccess;
@@ -959,7 +962,7 @@ __global__ void k_finalize(int B, double* out, int has_prev) {
 
 cudaError_t launch_finalize(int B, double* d_out, int has_prev, cudaStream_t st) {
   if (B == 0) return cudaSuccess;
-  k_finalize<<<(B + 255) / 256, 256, 0, st>>>(B, d_out, has_prev);
+  ++tl_launches, k_finalize<<<(B + 255) / 256, 256, 0, st>>>(B, d_out, has_prev);
   return cudaGetLastError();
 }
 
@@ -971,6 +974,8 @@ size_t stream_arena_bytes(int n, int B, int mixed) {
   Arena<double> A;
   return carve_arena<double>(nullptr, n, B, A) + 256;
 }
+
+uint64_t stream_launches() { return tl_launches; }
 
 cudaError_t stream_solve(const StreamSolve& s, int mixed, void* arena, cudaStream_t st) {
   return mixed ? stream_solve_t<float>(s, arena, st) : stream_solve_t<double>(s, arena, st);
