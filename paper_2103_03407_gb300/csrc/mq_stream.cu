@@ -38,6 +38,7 @@ constexpr int kThreads = 256;
 constexpr int kPer = 4;                      // nodes per thread per tile
 constexpr int kTile = kThreads * kPer;       // nodes per CTA
 constexpr int kSub = 32;                     // meshes up to 1/32 run inside one CTA
+constexpr int kSubThreads = 128;             // threads of that CTA (more samples per SM than 256)
 
 __host__ __device__ inline int tiles_interior(int n) { return ((n - 1) * n + kTile - 1) / kTile; }
 __host__ __device__ inline int tiles_padded(int n) { return (int)((gsz(n) + kTile - 1) / kTile); }
@@ -98,7 +99,8 @@ __device__ __forceinline__ void tile_partials(A (&v)[NV], double* part, size_t s
 // weights and inverse diagonal of mesh n from per-triangle coefficients (lower plane, upper plane)
 template <typename T, typename S>
 __global__ void k_weights(int n, int B, const S* __restrict__ cells, size_t cstride, T* __restrict__ wx,
-                          T* __restrict__ wy, T* __restrict__ dinv, T om, const int* __restrict__ act, SS<T>* ss) {
+                          T* __restrict__ wy, T* __restrict__ dinv, T om, double* __restrict__ wx64,
+                          double* __restrict__ wy64, const int* __restrict__ act, SS<T>* ss) {
   const int nt = tiles_padded(n);
   const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
   if (b >= B || (act && !act[b])) return;
@@ -114,9 +116,11 @@ __global__ void k_weights(int n, int B, const S* __restrict__ cells, size_t cstr
     const int i = (int)(q % ld), j = (int)(q / ld);
     auto LO = [&](int ii, int jj) { return (double)lo[jj * n + ii]; };
     auto UP = [&](int ii, int jj) { return (double)up[jj * n + ii]; };
-    T a = T(0), c = T(0), d = T(0);
-    if (i <= n - 1 && j >= 1 && j <= n - 1) a = T(0.5 * (LO(i, j) + UP(i, j - 1)));
-    if (i >= 1 && i <= n - 1 && j <= n - 1) c = T(0.5 * (UP(i, j) + LO(i - 1, j)));
+    T d = T(0);
+    double a64 = 0.0, c64 = 0.0;
+    if (i <= n - 1 && j >= 1 && j <= n - 1) a64 = 0.5 * (LO(i, j) + UP(i, j - 1));
+    if (i >= 1 && i <= n - 1 && j <= n - 1) c64 = 0.5 * (UP(i, j) + LO(i - 1, j));
+    const T a = T(a64), c = T(c64);
     if (i <= n - 1 && j <= n - 1) {  // every triangle once
       bad |= !(LO(i, j) > 0.0) | !(UP(i, j) > 0.0);
       amax = fmaxf(amax, (float)fmax(LO(i, j), UP(i, j)) * 1.0001f);
@@ -130,6 +134,10 @@ __global__ void k_weights(int n, int B, const S* __restrict__ cells, size_t cstr
     wx[(size_t)b * V + q] = a;
     wy[(size_t)b * V + q] = c;
     dinv[(size_t)b * V + q] = d;
+    if (wx64) {
+      wx64[(size_t)b * V + q] = a64;
+      wy64[(size_t)b * V + q] = c64;
+    }
   }
   if (ss) {
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&ss[b].flags, kFlagBadCoef);
@@ -417,7 +425,7 @@ __global__ void __launch_bounds__(kThreads) k_sub_build(int ns, int B, const T* 
 // meshes 1/ns .. 1/2 of one sample inside one CTA: x = B^{-1} b (operator arrays read from the
 // per-sample block built by k_sub_build, vectors in shared memory)
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_subcycle(int ns, int B, const int* __restrict__ act,
+__global__ void __launch_bounds__(kSubThreads) k_subcycle(int ns, int B, const int* __restrict__ act,
                                                        const char* __restrict__ subw, size_t wbytes,
                                                        const T* __restrict__ bin, T* __restrict__ xout, int nu, T om,
                                                        double* part, const T* __restrict__ dotv) {
@@ -613,10 +621,11 @@ __global__ void k_outer_update(int n, int B, const SS<T>* __restrict__ ss, const
   for_tile(n, ch, [&](int p, int, int) { x64[off + p] += rn * (double)xi[off + p]; });
 }
 
-// FP64 residual r = b - (A - sigma M) x64 (weights formed from the centroid coefficients); v = T(r).
+// FP64 residual r = b - (A - sigma M) x64 (FP64 edge weights); v = T(r).
 // Partials r.r, x.x, x.Ax, x.Mx: the last pass of a sample gives its Rayleigh quotient.
 template <typename T>
-__global__ void k_residual(int n, int B, const int* __restrict__ ran, const double* __restrict__ a, size_t astride,
+__global__ void k_residual(int n, int B, const int* __restrict__ ran, const double* __restrict__ wx64,
+                           const double* __restrict__ wy64,
                            const double* __restrict__ sigma, int sig_stride, const double* __restrict__ x64,
                            const double* __restrict__ b64, T* __restrict__ v, double* part) {
   const int nt = tiles_interior(n);
@@ -626,12 +635,13 @@ __global__ void k_residual(int n, int B, const int* __restrict__ ran, const doub
   const size_t off = (size_t)b * gsz(n);
   const double hm = 1.0 / (12.0 * n * n);
   const double sg = sigma[(size_t)b * sig_stride];
-  const double* __restrict__ ab = a + (size_t)b * astride;
+  const double* __restrict__ WX = wx64 + off;
+  const double* __restrict__ WY = wy64 + off;
   const double* __restrict__ X = x64 + off;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  for_tile(n, ch, [&](int p, int i, int j) {
+  for_tile(n, ch, [&](int p, int, int) {
     const double xv = X[p];
-    const double ax = stiff_cells(ab, n, X, p, ld, i, j);
+    const double ax = stiff<double, double>(WX, WY, X, p, ld);
     const double mx = hm * mass7(X, p, ld);
     const double r = b64[off + p] - (ax - sg * mx);
     v[off + p] = T(r);
@@ -711,6 +721,7 @@ struct Arena {
   size_t V0;
   T *v, *vo, *z, *zn, *w, *wo, *q, *xi;
   double *x64, *b64;
+  double *wx64, *wy64;  // FP64 edge weights of the finest mesh (the residual operator)
   T *wx[kMaxMG], *wy[kMaxMG], *dinv[kMaxMG], *x[kMaxMG], *t[kMaxMG], *b[kMaxMG];
   T* cells[kMaxMG];  // per-triangle coefficients of streaming level l >= 1 and of the sub mesh
   T *bsub, *xsub;
@@ -738,6 +749,8 @@ size_t carve_arena(void* base, int n, int B, Arena<T>& A) {
   A.xi = c.take<T>(Bz * A.V0);
   A.x64 = c.take<double>(Bz * A.V0);
   A.b64 = c.take<double>(Bz * A.V0);
+  A.wx64 = c.take<double>(Bz * A.V0);
+  A.wy64 = c.take<double>(Bz * A.V0);
   A.Ls = 0;
   for (int nl = n; nl > kSub; nl >>= 1) ++A.Ls;
   for (int l = 0; l < (A.Ls > 1 ? A.Ls : 1); ++l) {  // level 0 always: the MINRES operator
@@ -781,7 +794,7 @@ cudaError_t vcycle_stream(Arena<T>& A, const T* b0, T* x0, const int* act, T om,
                           size_t sub_smem, cudaStream_t st) {
   const int n = A.n, B = A.B;
   if (A.Ls == 0) {
-    ++tl_launches, k_subcycle<T><<<B, kThreads, sub_smem, st>>>(n, B, act, A.subw, A.subw_bytes, b0, x0, 2, om, part, dotv);
+    ++tl_launches, k_subcycle<T><<<B, kSubThreads, sub_smem, st>>>(n, B, act, A.subw, A.subw_bytes, b0, x0, 2, om, part, dotv);
     LAUNCH_CHECK();
     return cudaSuccess;
   }
@@ -797,7 +810,7 @@ cudaError_t vcycle_stream(Arena<T>& A, const T* b0, T* x0, const int* act, T om,
     LAUNCH_CHECK();
   }
   const int ns = n >> A.Ls;
-  ++tl_launches, k_subcycle<T><<<B, kThreads, sub_smem, st>>>(ns, B, act, A.subw, A.subw_bytes, A.bsub, A.xsub, 2, om, nullptr,
+  ++tl_launches, k_subcycle<T><<<B, kSubThreads, sub_smem, st>>>(ns, B, act, A.subw, A.subw_bytes, A.bsub, A.xsub, 2, om, nullptr,
                                                 nullptr);
   LAUNCH_CHECK();
   for (int l = A.Ls - 1; l >= 0; --l) {
@@ -867,10 +880,10 @@ cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st) {
     const int nl = n >> l;
     if (l == 0)
       ++tl_launches, k_weights<T, double><<<B * tiles_padded(nl), kThreads, 0, st>>>(nl, B, s.a, astride, A.wx[0], A.wy[0],
-                                                                     A.dinv[0], om, nullptr, A.ss);
+                                                                     A.dinv[0], om, A.wx64, A.wy64, nullptr, A.ss);
     else
       ++tl_launches, k_weights<T, T><<<B * tiles_padded(nl), kThreads, 0, st>>>(nl, B, A.cells[l], (size_t)2 * nl * nl, A.wx[l],
-                                                                A.wy[l], A.dinv[l], om, nullptr, nullptr);
+                                                                A.wy[l], A.dinv[l], om, nullptr, nullptr, nullptr, nullptr);
     LAUNCH_CHECK();
     if (l >= A.Ls) continue;
     const int m = nl / 2;
@@ -939,7 +952,7 @@ cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st) {
     ++tl_launches, k_minres_finish<T><<<B * nt, kThreads, 0, st>>>(n, B, A.ran, A.ss, zn, wo, w, A.xi);
     LAUNCH_CHECK();
     ++tl_launches, k_outer_update<T><<<B * nt, kThreads, 0, st>>>(n, B, A.ss, A.ran, A.xi, A.x64);
-    ++tl_launches, k_residual<T><<<B * nt, kThreads, 0, st>>>(n, B, A.ran, s.a, astride, s.lamH, s.lam_stride, A.x64, A.b64, A.v,
+    ++tl_launches, k_residual<T><<<B * nt, kThreads, 0, st>>>(n, B, A.ran, A.wx64, A.wy64, s.lamH, s.lam_stride, A.x64, A.b64, A.v,
                                                A.part);
     ++tl_launches, k_sc_outer_end<T><<<gs, 256, 0, st>>>(B, nt, A.part, A.ran, A.ss);
     LAUNCH_CHECK();
