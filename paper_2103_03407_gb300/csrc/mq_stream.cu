@@ -40,8 +40,25 @@ constexpr int kTile = kThreads * kPer;       // nodes per CTA
 constexpr int kSub = 32;                     // meshes up to 1/32 run inside one CTA
 constexpr int kSubThreads = 128;             // threads of that CTA (more samples per SM than 256)
 
-__host__ __device__ inline int tiles_interior(int n) { return ((n - 1) * n + kTile - 1) / kTile; }
+// tiles of kTile interior nodes per sample; n * n / kTile (n a power of two) also covers the
+// column walk below, whose threads own one column and kPer rows each
+__host__ __device__ inline int tiles_interior(int n) { return n * n > kTile ? n * n / kTile : 1; }
 __host__ __device__ inline int tiles_padded(int n) { return (int)((gsz(n) + kTile - 1) / kTile); }
+
+// Column walk over tile ch of mesh n: the thread owns column i and the nr = j1 - j0 (1..kPer)
+// rows j0 .. j1-1; consecutive threads own consecutive columns, so every row access is coalesced.
+// Stencil kernels load the column strip of every operand once (rows j0-1 .. j1 of the stenciled
+// vector, the columns beside it, the weights) as one batch of independent loads, then compute the
+// nr nodes from registers: per node three values of the stenciled vector instead of five or
+// seven, and all of a thread's memory latency overlapped.  Loads past row j1 - 1 are clamped to
+// rows the thread owns (their values are unused).  Returns false when the thread owns no node.
+__device__ __forceinline__ bool column_walk(int n, int ch, int& i, int& j0, int& nr) {
+  const int g = ch * kThreads + threadIdx.x;
+  i = (g & (n - 1)) + 1;
+  j0 = (g >> ilog2(n)) * kPer + 1;
+  nr = min(kPer, n - j0);
+  return i < n && j0 < n;
+}
 
 // loop over the interior nodes of tile ch of mesh n
 template <class F>
@@ -66,6 +83,7 @@ __device__ __forceinline__ void for_tile(int n, int ch, F f) {
 template <typename T>
 struct SS {  // per-sample solver scalars
   T gam, gam_old, eta, eta0, c, c_old, s, s_old, ig, c1, c2, cx, ia1, a2, a3, delta, rs;
+  T igp;          // 1 / gamma of the previous step: the pending update normalises z_j on the fly
   T sigm;         // lambda_H h^2 / 12: the mass factor of the shifted operator
   double rnorm, bnorm, lam_h;
   double xnorm;   // ||x64||
@@ -297,13 +315,38 @@ __global__ void k_smooth2_from_zero(int n, int B, const int* __restrict__ act, c
   const T* __restrict__ D = dinv + off;
   const T* __restrict__ R = bb + off;
   T* __restrict__ X = x + off;
-  for_tile(n, ch, [&](int p, int, int) {
-    auto x1 = [&](int q) { return D[q] * R[q]; };
-    const T xp = x1(p);
-    const T ax = W[p] * (xp - x1(p + 1)) + W[p - 1] * (xp - x1(p - 1)) + Y[p] * (xp - x1(p + ld)) +
-                 Y[p - ld] * (xp - x1(p - ld));
-    X[p] = xp + D[p] * (R[p] - ax);
-  });
+  int i, j0, nr;
+  if (!column_walk(n, ch, i, j0, nr)) return;
+  const int p0 = j0 * ld + i;
+  // x1 = om D^-1 b: centre column rows j0-1 .. j0+kPer (clamped), west and east columns
+  T dc[kPer + 2], rc[kPer + 2], dw[kPer], rw[kPer], de[kPer], re[kPer], wE[kPer], wW[kPer], yv[kPer + 1];
+#pragma unroll
+  for (int k = -1; k <= kPer; ++k) {
+    const int q = p0 + min(k, nr) * ld;
+    dc[k + 1] = D[q];
+    rc[k + 1] = R[q];
+  }
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const int q = p0 + min(k, nr - 1) * ld;
+    dw[k] = D[q - 1];
+    rw[k] = R[q - 1];
+    de[k] = D[q + 1];
+    re[k] = R[q + 1];
+    wE[k] = W[q];
+    wW[k] = W[q - 1];
+  }
+#pragma unroll
+  for (int k = -1; k < kPer; ++k) yv[k + 1] = Y[p0 + min(k, nr - 1) * ld];
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    if (k < nr) {
+      const T xc = dc[k + 1] * rc[k + 1];
+      const T ax = wE[k] * (xc - de[k] * re[k]) + wW[k] * (xc - dw[k] * rw[k]) +
+                   yv[k + 1] * (xc - dc[k + 2] * rc[k + 2]) + yv[k] * (xc - dc[k] * rc[k]);
+      X[p0 + k * ld] = xc + dc[k + 1] * (rc[k + 1] - ax);
+    }
+  }
 }
 
 // residual r = b - A x restricted with P^T to the coarse right-hand side
@@ -347,16 +390,40 @@ __global__ void k_prolong_smooth(int n, int B, const int* __restrict__ act, cons
   const T* __restrict__ X = x + off;
   const T* __restrict__ XC = xc + (size_t)b * gsz(n / 2);
   T* __restrict__ O = out + off;
-  for_tile(n, ch, [&](int p, int i, int j) {
-    auto t = [&](int q, int ii, int jj) {  // branch-free P1 interpolation (see vcycle)
-      const int c0 = (jj >> 1) * ldc + (ii >> 1);
-      return X[q] + T(0.5) * (XC[c0] + XC[c0 + (ii & 1) + (jj & 1) * ldc]);
-    };
-    const T tp = t(p, i, j);
-    const T ax = W[p] * (tp - t(p + 1, i + 1, j)) + W[p - 1] * (tp - t(p - 1, i - 1, j)) +
-                 Y[p] * (tp - t(p + ld, i, j + 1)) + Y[p - ld] * (tp - t(p - ld, i, j - 1));
-    O[p] = tp + D[p] * (R[p] - ax);
-  });
+  int i, j0, nr;
+  if (!column_walk(n, ch, i, j0, nr)) return;
+  auto t = [&](int q, int ii, int jj) {  // x + P xc, branch-free P1 interpolation (see vcycle)
+    const int c0 = (jj >> 1) * ldc + (ii >> 1);
+    return X[q] + T(0.5) * (XC[c0] + XC[c0 + (ii & 1) + (jj & 1) * ldc]);
+  };
+  const int p0 = j0 * ld + i;
+  T tc[kPer + 2], tw[kPer], te[kPer], wE[kPer], wW[kPer], yv[kPer + 1], dd[kPer], rr[kPer];
+#pragma unroll
+  for (int k = -1; k <= kPer; ++k) {
+    const int kk = min(k, nr);
+    tc[k + 1] = t(p0 + kk * ld, i, j0 + kk);
+  }
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const int kk = min(k, nr - 1);
+    const int q = p0 + kk * ld;
+    tw[k] = t(q - 1, i - 1, j0 + kk);
+    te[k] = t(q + 1, i + 1, j0 + kk);
+    wE[k] = W[q];
+    wW[k] = W[q - 1];
+    dd[k] = D[q];
+    rr[k] = R[q];
+  }
+#pragma unroll
+  for (int k = -1; k < kPer; ++k) yv[k + 1] = Y[p0 + min(k, nr - 1) * ld];
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    if (k < nr) {
+      const T c = tc[k + 1];
+      const T ax = wE[k] * (c - te[k]) + wW[k] * (c - tw[k]) + yv[k + 1] * (c - tc[k + 2]) + yv[k] * (c - tc[k]);
+      O[p0 + k * ld] = c + dd[k] * (rr[k] - ax);
+    }
+  }
 }
 
 // one Jacobi step out = t + om D^-1 (b - A t); optionally partial <dotv, out>
@@ -377,11 +444,36 @@ __global__ void k_smooth(int n, int B, const int* __restrict__ act, const T* __r
   const T* __restrict__ X = t + off;
   T* __restrict__ O = out + off;
   T acc[1] = {T(0)};
-  for_tile(n, ch, [&](int p, int, int) {
-    const T o = X[p] + D[p] * (R[p] - stiff<T, T>(W, Y, X, p, ld));
-    O[p] = o;
-    if (DOT) acc[0] += dotv[off + p] * o;
-  });
+  int i, j0, nr;
+  if (column_walk(n, ch, i, j0, nr)) {
+    const int p0 = j0 * ld + i;
+    T xc[kPer + 2], xw[kPer], xe[kPer], wE[kPer], wW[kPer], yv[kPer + 1], dd[kPer], rr[kPer], dv[kPer];
+#pragma unroll
+    for (int k = -1; k <= kPer; ++k) xc[k + 1] = X[p0 + min(k, nr) * ld];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int q = p0 + min(k, nr - 1) * ld;
+      xw[k] = X[q - 1];
+      xe[k] = X[q + 1];
+      wE[k] = W[q];
+      wW[k] = W[q - 1];
+      dd[k] = D[q];
+      rr[k] = R[q];
+      if (DOT) dv[k] = dotv[off + q];
+    }
+#pragma unroll
+    for (int k = -1; k < kPer; ++k) yv[k + 1] = Y[p0 + min(k, nr - 1) * ld];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      if (k < nr) {
+        const T c = xc[k + 1];
+        const T ax = wE[k] * (c - xe[k]) + wW[k] * (c - xw[k]) + yv[k + 1] * (c - xc[k + 2]) + yv[k] * (c - xc[k]);
+        const T o = c + dd[k] * (rr[k] - ax);
+        O[p0 + k * ld] = o;
+        if (DOT) acc[0] += dv[k] * o;
+      }
+    }
+  }
   if (DOT) tile_partials<1, T>(acc, part, (size_t)b * nt + ch);
 }
 
@@ -468,7 +560,7 @@ template <typename T>
 __global__ void k_minres_q(int n, int B, const int* __restrict__ act, const SS<T>* __restrict__ ss,
                            const T* __restrict__ wx, const T* __restrict__ wy, const double* __restrict__ sigma,
                            int sig_stride, const T* __restrict__ z, const T* __restrict__ zp, T* __restrict__ wo,
-                           const T* __restrict__ w, T* __restrict__ xi, T* __restrict__ q, double* part) {
+                           const T* __restrict__ w, T* __restrict__ xi, T* __restrict__ qv, double* part) {
   const int nt = tiles_interior(n);
   const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
   if (b >= B || !act[b]) return;
@@ -480,32 +572,68 @@ __global__ void k_minres_q(int n, int B, const int* __restrict__ act, const SS<T
   const T* __restrict__ Y = wy + off;
   const T* __restrict__ Z = z + off;
   T acc[1] = {T(0)};
-  for_tile(n, ch, [&](int p, int, int) {
-    if (S.pend) {
-      const T wnew = (zp[off + p] - S.a3 * wo[off + p] - S.a2 * w[off + p]) * S.ia1;
-      wo[off + p] = wnew;
-      xi[off + p] += S.cx * wnew;
+  int i, j0, nr;
+  if (column_walk(n, ch, i, j0, nr)) {
+    // z on the centre column rows j0-1 .. j0+nr, the west column rows j0-1 .. (south-west and
+    // west neighbours) and the east column rows j0 .. j0+nr (east and north-east neighbours)
+    const int p0 = j0 * ld + i;
+    T zc[kPer + 2], zw[kPer + 1], ze[kPer + 1], wE[kPer], wW[kPer], yv[kPer + 1];
+    T zpv[kPer], wov[kPer], wv[kPer], xiv[kPer];
+#pragma unroll
+    for (int k = -1; k <= kPer; ++k) zc[k + 1] = Z[p0 + min(k, nr) * ld];
+#pragma unroll
+    for (int k = -1; k < kPer; ++k) {
+      const int q = p0 + min(k, nr - 1) * ld;
+      zw[k + 1] = Z[q - 1];
+      yv[k + 1] = Y[q];
     }
-    const T kz = (stiff<T, T>(W, Y, Z, p, ld) - sigm * mass7(Z, p, ld)) * S.ig;
-    q[off + p] = kz;
-    acc[0] += kz * Z[p];
-  });
+#pragma unroll
+    for (int k = 0; k <= kPer; ++k) ze[k] = Z[p0 + min(k, nr) * ld + 1];
+    const bool pend = S.pend;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int q = p0 + min(k, nr - 1) * ld;
+      wE[k] = W[q];
+      wW[k] = W[q - 1];
+      if (pend) {
+        zpv[k] = zp[off + q];
+        wov[k] = wo[off + q];
+        wv[k] = w[off + q];
+        xiv[k] = xi[off + q];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      if (k < nr) {
+        const int q = off + p0 + k * ld;
+        if (pend) {
+          const T wnew = (zpv[k] * S.igp - S.a3 * wov[k] - S.a2 * wv[k]) * S.ia1;
+          wo[q] = wnew;
+          xi[q] = xiv[k] + S.cx * wnew;
+        }
+        const T c = zc[k + 1];
+        const T az = wE[k] * (c - ze[k]) + wW[k] * (c - zw[k + 1]) + yv[k + 1] * (c - zc[k + 2]) + yv[k] * (c - zc[k]);
+        const T mz = T(6) * c + (ze[k] + zw[k + 1]) + (zc[k + 2] + zc[k]) + (ze[k + 1] + zw[k]);
+        const T kz = (az - sigm * mz) * S.ig;
+        qv[q] = kz;
+        acc[0] += kz * c;
+      }
+    }
+  }
   tile_partials<1, T>(acc, part, (size_t)b * nt + ch);
 }
 
-// K2: v_new = q - c1 v - c2 v_old (into vo) ; z *= ig
+// K2: v_new = q - c1 v - c2 v_old (into vo).  z_j stays unnormalised: the next pending update
+// scales it by 1 / gamma_j (saves a read and a write of z per step)
 template <typename T>
 __global__ void k_minres_v(int n, int B, const int* __restrict__ act, const SS<T>* __restrict__ ss,
-                           const T* __restrict__ q, const T* __restrict__ v, T* __restrict__ vo, T* __restrict__ z) {
+                           const T* __restrict__ q, const T* __restrict__ v, T* __restrict__ vo) {
   const int nt = tiles_interior(n);
   const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
   if (b >= B || !act[b]) return;
   const size_t off = (size_t)b * gsz(n);
-  const T c1 = ss[b].c1, c2 = ss[b].c2, ig = ss[b].ig;
-  for_tile(n, ch, [&](int p, int, int) {
-    vo[off + p] = q[off + p] - c1 * v[off + p] - c2 * vo[off + p];
-    z[off + p] *= ig;
-  });
+  const T c1 = ss[b].c1, c2 = ss[b].c2;
+  for_tile(n, ch, [&](int p, int, int) { vo[off + p] = q[off + p] - c1 * v[off + p] - c2 * vo[off + p]; });
 }
 
 // final pending w/x update
@@ -519,7 +647,7 @@ __global__ void k_minres_finish(int n, int B, const int* __restrict__ act, const
   const size_t off = (size_t)b * gsz(n);
   const SS<T> S = ss[b];
   for_tile(n, ch, [&](int p, int, int) {
-    const T wnew = (zp[off + p] - S.a3 * wo[off + p] - S.a2 * w[off + p]) * S.ia1;
+    const T wnew = (zp[off + p] * S.igp - S.a3 * wo[off + p] - S.a2 * w[off + p]) * S.ia1;
     xi[off + p] += S.cx * wnew;
   });
 }
@@ -590,6 +718,7 @@ __global__ void k_sc_givens(int B, int nch, const double* part, int* act, SS<T>*
   S.c = cn;
   S.gam_old = gam;
   S.gam = gnew;
+  S.igp = S.ig;
   S.ig = gnew > T(0) ? T(1) / gnew : T(0);
   S.pend = 1;
   S.iters += 1;
@@ -933,7 +1062,7 @@ cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st) {
       ++tl_launches, k_sc_retire<T><<<gs, 256, 0, st>>>(B, A.act, A.ss);
       { T* tt = wo; wo = w; w = tt; }
       ++tl_launches, k_sc_delta<T><<<gs, 256, 0, st>>>(B, nt, A.part, A.act, A.ss);
-      ++tl_launches, k_minres_v<T><<<B * nt, kThreads, 0, st>>>(n, B, A.act, A.ss, A.q, v, vo, z);
+      ++tl_launches, k_minres_v<T><<<B * nt, kThreads, 0, st>>>(n, B, A.act, A.ss, A.q, v, vo);
       LAUNCH_CHECK();
       { T* tt = vo; vo = v; v = tt; }
       e = vcycle_stream<T>(A, v, zn, A.act, om, v, A.part, sub_smem, st);
