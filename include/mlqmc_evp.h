@@ -132,7 +132,8 @@ mq_status mq_set_eig_options(mq_ctx* ctx, double tol_eig, int32_t max_eig);
 mq_status mq_set_tier(mq_ctx* ctx, int32_t stream_min_n);
 
 /* Threads per CTA of the per-sample kernel (one CTA per sample) on level `level` (0 <= level < 64):
- * 0 restores the default (128 for meshes up to 1/16, else 256), otherwise a multiple of 32 in
+ * 0 restores the default (64 when the largest fine mesh solved in the kernel is at most 1/16,
+ * 128 for coarse eigensolves on meshes up to 1/16, else 256), otherwise a multiple of 32 in
  * [32, 512].  Fewer threads per sample let more samples share an SM; the results do not depend
  * on it beyond rounding order. */
 mq_status mq_set_cta_threads(mq_ctx* ctx, int32_t level, int32_t threads);

@@ -236,8 +236,15 @@ int stream_threshold(const mq_ctx* c) {
   return c->prec == MQ_PREC_MIXED ? 64 : 256;
 }
 
-// threads per CTA for a fine mesh 1/n
-int threads_for(int n) { return n <= 16 ? 128 : 256; }
+// Threads per CTA of the per-sample kernel: n_fine is the largest mesh solved inside the kernel
+// (0: coarse eigensolves only).  Meshes up to 1/16 run with two warps: their workspace (~24 KB)
+// lets seven samples share an SM, which hides the barrier latency of the small phases better
+// than more threads per sample (measured on GB300).
+int threads_for(int n_fine, int n_coarse) {
+  if (n_fine > 0 && n_fine <= 16) return 64;
+  const int n = n_fine > n_coarse ? n_fine : n_coarse;
+  return n <= 16 ? 128 : 256;
+}
 
 struct LevelGeom {
   int nf, nc, np, s, S, sp, direct_f, direct_p;
@@ -348,7 +355,7 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
   }
   // FP64 inner solves in the per-sample kernel follow the FP64 defaults
   const int in_kernel_n = std::max(p.mode_f != 2 && !g.direct_f ? g.nf : 0, p.mode_p != 2 && !g.direct_p ? g.np : 0);
-  const int threads = g.threads > 0 ? g.threads : threads_for(std::max(in_kernel_n, g.nc));
+  const int threads = g.threads > 0 ? g.threads : threads_for(in_kernel_n, g.nc);
   const size_t slab = mq::sample_slab_bytes(g.nf, g.nc, g.np, mixed, p.mode_f, p.mode_p);
   const int static_smem = mq::sample_static_smem(mixed);
   const size_t smem_cap = (size_t)std::max(0, c->smem_optin - static_smem - 1024);

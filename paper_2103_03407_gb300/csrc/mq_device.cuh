@@ -374,7 +374,7 @@ __device__ bool build_mg(MGDesc<T>& d, const S* __restrict__ a, int n, double* r
 // down; [prolongation + correction + one Jacobi step, fused] -> [one Jacobi step] going up.
 // With dotv, returns this thread's share of <dotv, x0> (formed in the last phase).
 template <typename T>
-__device__ T vcycle(const MGDesc<T>& d, const T* b0, T* x0, T omega, const T* dotv = nullptr) {
+__device__ __noinline__ T vcycle(const MGDesc<T>& d, const T* b0, T* x0, T omega, const T* dotv = nullptr) {
   const int Lc = d.Lc;
   for (int l = 0; l < Lc; ++l) {
     const int n = d.n[l], ld = n + 1;

@@ -47,8 +47,13 @@ struct CoarseWS {
   float *r32, *w32;
 };
 
-__host__ __device__ void carve_coarse(Carver& c, int nc, CoarseWS& ws) {
+// uprev comes first: it holds the coarse eigenvector through the fine solves (and as the warm
+// start of the next point), while the rest of the coarse workspace is dead during the fine solves
+// and shares its memory with the fine workspace.  *persist receives the bytes of that head.
+__host__ __device__ void carve_coarse(Carver& c, int nc, CoarseWS& ws, size_t* persist = nullptr) {
   const size_t V = gsz(nc);
+  ws.uprev = c.take<double>(V);
+  if (persist) *persist = c.used();
   ws.wx = c.take<double>(V);
   ws.wy = c.take<double>(V);
   ws.x = c.take<double>(V);
@@ -60,7 +65,6 @@ __host__ __device__ void carve_coarse(Carver& c, int nc, CoarseWS& ws) {
   ws.p = c.take<double>(V);
   ws.Ap = c.take<double>(V);
   ws.Mp = c.take<double>(V);
-  ws.uprev = c.take<double>(V);
   ws.r32 = c.take<float>(V);
   ws.w32 = c.take<float>(V);
   carve_mg<float>(c, nc, ws.mg);
@@ -105,14 +109,18 @@ template <typename T>
 __host__ __device__ size_t slab_size(int nf, int nc, int np, int mode_f = 0, int mode_p = 0) {
   Carver c(nullptr);
   CoarseWS cw;
-  carve_coarse(c, nc, cw);
+  size_t persist = 0;
+  carve_coarse(c, nc, cw, &persist);
   const size_t coarse = (c.used() + 15) & ~(size_t)15;
   auto need = [&](int n, int mode) -> size_t {
     if (mode == 2) return 0;
     return mode == 1 ? fine_bytes<double>(n) : fine_bytes<T>(n);
   };
+  size_t m = coarse - persist;
   const size_t a = need(nf, mode_f), b = need(np, mode_p);
-  return coarse + (a > b ? a : b);
+  if (a > m) m = a;
+  if (b > m) m = b;
+  return persist + m;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -229,7 +237,7 @@ struct EigShared {
 // x holds the start vector.  Returns the iterations used, or -1 when the tolerance was not
 // reached.  On return x is the M-normalised eigenvector with a positive sum and lam its
 // Rayleigh quotient.
-__device__ int lobpcg(CoarseWS& ws, int n, double tol, int maxit, int nu, float omega, double* red, EigShared* sh,
+__device__ __noinline__ int lobpcg(CoarseWS& ws, int n, double tol, int maxit, int nu, float omega, double* red, EigShared* sh,
                       double& lam) {
   const int ld = n + 1;
   const int nact = (n - 1) * n;  // threads for_interior gives work to
@@ -431,7 +439,7 @@ __host__ __device__ inline double residual_target(double tol, double bnorm, doub
 // (A - sigma M) w = M P u_H.  iters / outer report the inner MINRES iterations and refinement
 // steps; flags receives kFlag* bits.
 template <typename T>
-__device__ double twogrid_fine(FineWS<T>& ws, char* fine_base, int n, const double* __restrict__ a,
+__device__ __noinline__ double twogrid_fine(FineWS<T>& ws, char* fine_base, int n, const double* __restrict__ a,
                                const double* uH, int nc, double sigma, const SampleLaunch& P, double* red,
                                MinresShared<T>* ms, int& iters, int& outer, int& flags) {
   const int ld = n + 1;
@@ -704,30 +712,22 @@ __global__ void __launch_bounds__(512) sample_kernel(SampleLaunch P) {
   __shared__ FineWS<T> fws;
   __shared__ FineWS<double> fws64;
   char* base = P.use_smem ? smem_dyn : P.gscratch + (size_t)blockIdx.x * P.slab_bytes;
-  size_t coarse_bytes;
+  size_t persist_bytes;
   {
     Carver c(base);
     CoarseWS tmp;
-    carve_coarse(c, P.nc, tmp);
-    coarse_bytes = (c.used() + 15) & ~(size_t)15;
+    carve_coarse(c, P.nc, tmp, &persist_bytes);
     if (threadIdx.x == 0) cws = tmp;
   }
-  char* fine_base = base + coarse_bytes;
+  char* fine_base = base + persist_bytes;  // the fine workspace overlays the coarse one
   __syncthreads();
   const int nc = P.nc;
   const int cpr = (P.npts + P.chunk - 1) / P.chunk;
   const int nchunks = cpr * P.R;
   const size_t ncT = (size_t)2 * nc * nc, nfT = (size_t)2 * P.nf * P.nf, npT = (size_t)2 * P.np * P.np;
-  // coarse vectors: zero once (rings stay zero; interiors are always written before use)
-  {
-    CoarseWS& w = cws;
-    double* vs[12] = {w.wx, w.wy, w.x, w.Ax, w.Mx, w.w, w.Aw, w.Mw, w.p, w.Ap, w.Mp, w.uprev};
-    for (int i = 0; i < 12; ++i) zero_vec(vs[i], nc);
-    zero_vec(w.r32, nc);
-    zero_vec(w.w32, nc);
-    zero_mg(w.mg);
-    __syncthreads();
-  }
+  // the persistent coarse eigenvector: zero once (its ring stays zero)
+  zero_vec(cws.uprev, nc);
+  __syncthreads();
   const float omega = (float)P.omega;
   for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     const int r = ch / cpr;
@@ -738,6 +738,16 @@ __global__ void __launch_bounds__(512) sample_kernel(SampleLaunch P) {
       int flags = 0;
       // ---- coarse eigenpair (Algorithm 1 step 1; Algorithm 2 steps 6-7)
       CoarseWS& cw = cws;
+      {
+        // the fine solves of the previous point reused this memory: clear the coarse vectors
+        // (rings must be zero; interiors are written before use)
+        double* vs[11] = {cw.wx, cw.wy, cw.x, cw.Ax, cw.Mx, cw.w, cw.Aw, cw.Mw, cw.p, cw.Ap, cw.Mp};
+        for (int i = 0; i < 11; ++i) zero_vec(vs[i], nc);
+        zero_vec(cw.r32, nc);
+        zero_vec(cw.w32, nc);
+        zero_mg(cw.mg);
+        __syncthreads();
+      }
       const double* ac = P.a_c + b * ncT;
       if (!build_mg<float>(cw.mg, ac, nc, red)) flags |= kFlagBadCoef;
       weights_from_cells<double, double>(nc, ac, ac + (size_t)nc * nc, cw.wx, cw.wy);
@@ -768,16 +778,16 @@ __global__ void __launch_bounds__(512) sample_kernel(SampleLaunch P) {
       int itf = 0, itp = 0, of = 0, op = 0;
       if (!P.direct_f) {
         if (P.mode_f == 0)
-          lf = twogrid_fine<T>(fws, fine_base, P.nf, P.a_f + b * nfT, cw.x, nc, lamH, P, red, &msh, itf, of, flags);
+          lf = twogrid_fine<T>(fws, fine_base, P.nf, P.a_f + b * nfT, cw.uprev, nc, lamH, P, red, &msh, itf, of, flags);
         else if (P.mode_f == 1)
-          lf = twogrid_fine<double>(fws64, fine_base, P.nf, P.a_f + b * nfT, cw.x, nc, lamH, P, red, &msh64, itf, of,
+          lf = twogrid_fine<double>(fws64, fine_base, P.nf, P.a_f + b * nfT, cw.uprev, nc, lamH, P, red, &msh64, itf, of,
                                     flags);
       }
       if (P.np > 0 && !P.direct_p) {
         if (P.mode_p == 0)
-          lp = twogrid_fine<T>(fws, fine_base, P.np, P.a_p + b * npT, cw.x, nc, lamH, P, red, &msh, itp, op, flags);
+          lp = twogrid_fine<T>(fws, fine_base, P.np, P.a_p + b * npT, cw.uprev, nc, lamH, P, red, &msh, itp, op, flags);
         else if (P.mode_p == 1)
-          lp = twogrid_fine<double>(fws64, fine_base, P.np, P.a_p + b * npT, cw.x, nc, lamH, P, red, &msh64, itp, op,
+          lp = twogrid_fine<double>(fws64, fine_base, P.np, P.a_p + b * npT, cw.uprev, nc, lamH, P, red, &msh64, itp, op,
                                     flags);
       }
       if (threadIdx.x == 0) {
