@@ -247,7 +247,7 @@ FP64_EIG_IT, FP64_EIG_CALL, FP64_FINE_SETUP, FP64_FINE_OUTER, FP64_INNER = 73, 4
 
 
 def stream_min_default(prec):
-    return 64 if prec == "mixed" else 256
+    return 32 if prec == "mixed" else 256
 
 
 def percta_fp64_flops(wl, level, st, prec):
@@ -271,7 +271,7 @@ def percta_fp64_flops(wl, level, st, prec):
     return per * lv.N * lv.R
 
 
-# Streaming tier (fine meshes >= 1/64 mixed): bounded by HBM.  Bytes per fine unknown with every
+# Streaming tier (fine meshes >= 1/32 mixed): bounded by HBM.  Bytes per fine unknown with every
 # kernel reading and writing each of its arrays once (e = 4 bytes, FP32 inner vectors):
 #   per inner MINRES iteration: MINRES sweeps 16 e (operator + pending update 10 e, Lanczos
 #   vector 6 e) + V-cycle 22.5 e on the fine level (two Jacobi sweeps from zero 5 e, residual

@@ -124,11 +124,17 @@ mq_status mq_set_solver_options(mq_ctx* ctx, double tol_inner, int32_t max_inner
  * the square of tol_eig. */
 mq_status mq_set_eig_options(mq_ctx* ctx, double tol_eig, int32_t max_eig);
 
+/* Damped Jacobi steps before and after each coarse-grid correction of the multigrid V-cycle that
+ * preconditions the shifted solves and the coarse eigensolver: 1 or 2 for every solve (0: the
+ * default, 2 in the per-sample kernel and 1 in the streaming tier).  The
+ * V-cycle is a preconditioner only: results agree to the solver tolerances either way. */
+mq_status mq_set_smoothing(mq_ctx* ctx, int32_t nu);
+
 /* Execution tier of the fine solves: fine meshes 1/n with n >= stream_min_n run in
  * the batched streaming tier (one kernel per sweep over all samples of a pass, lockstep across
  * samples); coarser ones run inside the per-sample kernel (one CTA per sample, workspace in
  * shared memory when it fits).  Both tiers compute the same values to rounding.  Default (or
- * stream_min_n = 0): 64 in MQ_PREC_MIXED, 256 in MQ_PREC_FP64. */
+ * stream_min_n = 0): 32 in MQ_PREC_MIXED, 256 in MQ_PREC_FP64. */
 mq_status mq_set_tier(mq_ctx* ctx, int32_t stream_min_n);
 
 /* Threads per CTA of the per-sample kernel (one CTA per sample) on level `level` (0 <= level < 64):

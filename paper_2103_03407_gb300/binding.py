@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "MQ_OK", 1: "MQ_EINVAL", 2: "MQ_ENOMEM", 3: "MQ_ECUDA", 4: "M
 # every symbol the header declares
 EXPORTS = [
     "mq_create", "mq_destroy", "mq_set_coefficient", "mq_set_levels", "mq_set_lattice", "mq_set_shifts",
-    "mq_set_precision", "mq_set_solver_options", "mq_set_eig_options", "mq_set_tier", "mq_set_cta_threads", "mq_eval_level", "mq_eval_level_device", "mq_estimate", "mq_reset_sums",
+    "mq_set_precision", "mq_set_solver_options", "mq_set_eig_options", "mq_set_smoothing", "mq_set_tier", "mq_set_cta_threads", "mq_eval_level", "mq_eval_level_device", "mq_estimate", "mq_reset_sums",
     "mq_get_level_timing", "mq_get_kernel_timing", "mq_get_launch_count", "mq_eval_point",
     "mq_get_stats", "mq_last_error", "mq_cbc_lattice", "mq_lattice_points_device", "mq_coefficients_device",
     "mq_apply_operator_device", "mq_twogrid_samples_noalloc",
@@ -83,6 +83,7 @@ def load(path: str = LIB_PATH):
         "mq_set_tier": ([P, i32], C.c_int),
         "mq_set_solver_options": ([P, f64, i32, i32], C.c_int),
         "mq_set_eig_options": ([P, f64, i32], C.c_int),
+        "mq_set_smoothing": ([P, i32], C.c_int),
         "mq_set_cta_threads": ([P, i32, i32], C.c_int),
         "mq_eval_level": ([P, i32, u32, u32, dp, dp], C.c_int),
         "mq_eval_level_device": ([P, i32, u32, u32, P, P], C.c_int),
@@ -185,6 +186,9 @@ class Context:
 
     def mq_set_eig_options(self, tol_eig=0.0, max_eig=0):
         self._check(self.lib.mq_set_eig_options(self.h, float(tol_eig), int(max_eig)))
+
+    def mq_set_smoothing(self, nu=0):
+        self._check(self.lib.mq_set_smoothing(self.h, int(nu)))
 
     def mq_set_cta_threads(self, level, threads=0):
         self._check(self.lib.mq_set_cta_threads(self.h, int(level), int(threads)))

@@ -59,6 +59,7 @@ struct mq_ctx {
   int opt_max_inner = 0, opt_max_outer = 0;
   double opt_tol_eig = 0.0;  // 0: default
   int opt_max_eig = 0;
+  int opt_nu = 0;  // Jacobi sweeps per side of the V-cycle (0: default)
 
   std::map<int, std::pair<int, double*>> psi;  // mesh n -> (rows, table [rows][2n^2])
   std::map<int, std::pair<int, void*>> psi_sl;  // mesh n -> (K pad, BF16 slices [6][nT pad][K pad])
@@ -229,11 +230,11 @@ mq_status check_level_ready(mq_ctx* c, int level) {
 }
 
 // Default tier threshold (measured on GB300, 4-level workload): with FP32 inner solves the
-// streaming tier wins from 1/64 on; the FP64 path is FP64-throughput bound and keeps the
-// per-sample kernel up to 1/128.
+// streaming tier wins from 1/32 on (the per-sample kernel fits only two samples of mesh 1/32 per
+// SM); the FP64 path is FP64-throughput bound and keeps the per-sample kernel up to 1/128.
 int stream_threshold(const mq_ctx* c) {
   if (c->stream_min > 0) return c->stream_min;
-  return c->prec == MQ_PREC_MIXED ? 64 : 256;
+  return c->prec == MQ_PREC_MIXED ? 32 : 256;
 }
 
 // Threads per CTA of the per-sample kernel: n_fine is the largest mesh solved inside the kernel
@@ -345,7 +346,11 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
   if (c->opt_tol_inner > 0) p.tol_inner = c->opt_tol_inner;
   if (c->opt_max_inner > 0) p.max_inner_it = c->opt_max_inner;
   if (c->opt_max_outer > 0) p.max_outer = c->opt_max_outer;
-  p.nu = 2;
+  // Smoothing per tier, measured on GB300 (4-level workload): V(1,1) needs ~10 % more MINRES
+  // iterations than V(2,2) (and ~15 % more LOBPCG iterations) but moves about a third fewer bytes
+  // per iteration, so it wins for the bandwidth-bound streaming tier; the latency-bound per-sample
+  // kernel keeps V(2,2)
+  p.nu = c->opt_nu > 0 ? c->opt_nu : 2;
   p.omega = 0.8;
   const bool ext = p.mode_f == 2 || p.mode_p == 2;
   if (ext) {
@@ -395,6 +400,7 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
     s.max_inner = p.max_inner_it;
     s.max_outer = p.max_outer;
     s.omega = p.omega;
+    s.nu = c->opt_nu > 0 ? c->opt_nu : 1;
     if (p.mode_f == 2) {
       s.n = g.nf;
       s.a = (const double*)c->af.p;
@@ -781,6 +787,13 @@ mq_status mq_set_cta_threads(mq_ctx* c, int32_t level, int32_t threads) {
     return fail(c, MQ_EINVAL, "threads must be 0 or a multiple of 32 in [32, 512]");
   if ((int)c->cta_threads.size() <= level) c->cta_threads.resize(level + 1, 0);
   c->cta_threads[level] = threads;
+  return MQ_OK;
+}
+
+mq_status mq_set_smoothing(mq_ctx* c, int32_t nu) {
+  if (!c) return MQ_EINVAL;
+  if (nu < 0 || nu > 2) return fail(c, MQ_EINVAL, "nu must be 0 (default), 1 or 2");
+  c->opt_nu = nu;
   return MQ_OK;
 }
 

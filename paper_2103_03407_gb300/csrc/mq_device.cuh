@@ -368,13 +368,15 @@ __device__ bool build_mg(MGDesc<T>& d, const S* __restrict__ a, int n, double* r
   return o[0] == 0.0;
 }
 
-// Symmetric V-cycle for A with two damped Jacobi steps before and after each coarse-grid
+// Symmetric V-cycle for A with nu (2 or 1) damped Jacobi steps before and after each coarse-grid
 // correction, Galerkin coarse levels and an exact solve on mesh 1/4 (or 1/2): x0 = B^{-1} b0.
 // Phases per level: [two Jacobi steps from zero, fused] -> [residual restricted with P^T] going
 // down; [prolongation + correction + one Jacobi step, fused] -> [one Jacobi step] going up.
-// With dotv, returns this thread's share of <dotv, x0> (formed in the last phase).
+// nu = 1: [residual of x1 = omega D^-1 b, restricted] down, [prolongation + correction + one
+// Jacobi step] up -- two phases per level, and x1 is never stored.  With dotv, returns this thread's share of <dotv, x0> (formed in the last phase).
 template <typename T>
-__device__ __noinline__ T vcycle(const MGDesc<T>& d, const T* b0, T* x0, T omega, const T* dotv = nullptr) {
+__device__ __noinline__ T vcycle(const MGDesc<T>& d, const T* b0, T* x0, T omega, const T* dotv = nullptr,
+                                int nu = 2) {
   const int Lc = d.Lc;
   for (int l = 0; l < Lc; ++l) {
     const int n = d.n[l], ld = n + 1;
@@ -383,6 +385,24 @@ __device__ __noinline__ T vcycle(const MGDesc<T>& d, const T* b0, T* x0, T omega
     const T* __restrict__ wx = d.wx[l];
     const T* __restrict__ wy = d.wy[l];
     const T* __restrict__ di = d.dinv[l];
+    if (nu == 1) {
+      // V(1,1): the one Jacobi step from zero is x1 = omega D^-1 b, pointwise; the restriction
+      // forms it on the fly and nothing is stored
+      T* bc = d.b[l + 1];
+      for_interior(n >> 1, [&](int P, int I, int J) {
+        const int p = (2 * J) * ld + 2 * I;
+        auto x1 = [&](int q) { return omega * di[q] * b[q]; };
+        auto res = [&](int q) {
+          const T xq = x1(q);
+          return b[q] - (wx[q] * (xq - x1(q + 1)) + wx[q - 1] * (xq - x1(q - 1)) + wy[q] * (xq - x1(q + ld)) +
+                         wy[q - ld] * (xq - x1(q - ld)));
+        };
+        bc[P] = res(p) + T(0.5) * ((res(p + 1) + res(p - 1)) + (res(p + ld) + res(p - ld)) +
+                                   (res(p + ld + 1) + res(p - ld - 1)));
+      });
+      __syncthreads();
+      continue;
+    }
     for_interior(n, [&](int p, int, int) {
       auto x1 = [&](int q) { return omega * di[q] * b[q]; };
       const T xp = x1(p);
@@ -429,6 +449,24 @@ __device__ __noinline__ T vcycle(const MGDesc<T>& d, const T* b0, T* x0, T omega
     const T* __restrict__ di = d.dinv[l];
     const T* xc = d.x[l + 1];
     const int ldc = (n >> 1) + 1;
+    if (nu == 1) {
+      // V(1,1): t = omega D^-1 b + P xc, then the one post-smoothing step, in one phase
+      const bool last = (l == 0) && dotv;
+      for_interior(n, [&](int p, int i, int j) {
+        auto t = [&](int q, int ii, int jj) {
+          const int c0 = (jj >> 1) * ldc + (ii >> 1);
+          return omega * di[q] * b[q] + T(0.5) * (xc[c0] + xc[c0 + (ii & 1) + (jj & 1) * ldc]);
+        };
+        const T tp = t(p, i, j);
+        const T ax = wx[p] * (tp - t(p + 1, i + 1, j)) + wx[p - 1] * (tp - t(p - 1, i - 1, j)) +
+                     wy[p] * (tp - t(p + ld, i, j + 1)) + wy[p - ld] * (tp - t(p - ld, i, j - 1));
+        const T o = tp + omega * di[p] * (b[p] - ax);
+        xa[p] = o;
+        if (last) dot += dotv[p] * o;
+      });
+      __syncthreads();
+      continue;
+    }
     for_interior(n, [&](int p, int i, int j) {
       // P1 interpolation on the SW-NE mesh, branch-free: the mean of the coarse values at the two
       // ends of the coarse edge through the fine node (both ends coincide at coarse nodes)

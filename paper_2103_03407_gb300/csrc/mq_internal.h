@@ -57,6 +57,7 @@ struct StreamSolve {
   double tol_lin, tol_inner;
   int max_inner, max_outer;
   double omega;
+  int nu;                  // Jacobi sweeps before and after each coarse-grid correction (1 or 2)
 };
 size_t stream_arena_bytes(int n, int B, int mixed);
 cudaError_t stream_solve(const StreamSolve& s, int mixed, void* arena, cudaStream_t st);

@@ -289,7 +289,7 @@ __device__ __noinline__ int lobpcg(CoarseWS& ws, int n, double tol, int maxit, i
         break;
       }
     }
-    vcycle<float>(ws.mg, ws.r32, ws.w32, omega);
+    vcycle<float>(ws.mg, ws.r32, ws.w32, omega, nullptr, nu);
     for_interior(n, [&](int p, int, int) { ws.w[p] = (double)ws.w32[p]; });
     __syncthreads();
     double g[12];
@@ -545,7 +545,7 @@ __device__ __noinline__ double twogrid_fine(FineWS<T>& ws, char* fine_base, int 
     T* wo = ws.wo;
     T* w = ws.w;
     {
-      T acc1[1] = {vcycle<T>(ws.mg, v, z, om, v)};  // z = B^{-1} v and <v, z>
+      T acc1[1] = {vcycle<T>(ws.mg, v, z, om, v, P.nu)};  // z = B^{-1} v and <v, z>
       double o1[1];
       block_sum<1, T>(acc1, o1, red, [&](const double* t) {
         const T t0 = T(t[0]);
@@ -610,7 +610,7 @@ __device__ __noinline__ double twogrid_fine(FineWS<T>& ws, char* fine_base, int 
         v = tt;
       }
       {
-        T acc1[1] = {vcycle<T>(ws.mg, v, zn, om, v)};  // zn = B^{-1} v_new and <v_new, zn>
+        T acc1[1] = {vcycle<T>(ws.mg, v, zn, om, v, P.nu)};  // zn = B^{-1} v_new and <v_new, zn>
         double o1[1];
         const T tol = T(P.tol_inner);
         block_sum<1, T>(acc1, o1, red, [&](const double* t) {

@@ -7,12 +7,14 @@
 // full memory-level parallelism:
 //   * MINRES (preconditioned, symmetric indefinite) in the inner precision T, one iteration =
 //     K1 (pending w/x update, q = (A - sigma M) z / gamma, partial <q, z>), S1 (scalars),
-//     K2 (v_new, z scaling), the V-cycle, S2 (Givens rotation, convergence);
-//   * the V-cycle (Jacobi nu = 2 before and after, Galerkin coarse levels) streams the meshes
-//     finer than 1/32 with four kernels per level -- two fused smoothing steps from zero,
-//     residual + restriction, prolongation + correction + one smoothing step, one smoothing step
-//     (the last one at the finest level also forms <v, z>) -- and runs the meshes 1/32 .. 1/2 of
-//     each sample inside one CTA in shared memory;
+//     K2 (v_new; z_j is normalised inside the next pending update), the V-cycle, S2 (Givens
+//     rotation, convergence);
+//   * the V-cycle (nu = 1 or 2 Jacobi steps before and after, Galerkin coarse levels) streams the
+//     meshes finer than 1/32.  nu = 2: four kernels per level -- two fused smoothing steps from
+//     zero, residual + restriction, prolongation + correction + one smoothing step, one smoothing
+//     step (the last one at the finest level also forms <v, z>).  nu = 1: two kernels per level --
+//     the residual of x1 = om D^-1 b restricted, prolongation + correction + one smoothing step
+//     (+ <v, z>).  The meshes 1/32 .. 1/2 of each sample run inside one CTA in shared memory;
 //   * FP64 iterative refinement around the inner solve and the FP64 Rayleigh quotient.
 // Partial sums of every reduction are written per (sample, tile) and added in fixed order by
 // the scalar kernels: results do not depend on scheduling.  Converged samples are masked out.
@@ -426,6 +428,96 @@ __global__ void k_prolong_smooth(int n, int B, const int* __restrict__ act, cons
   }
 }
 
+// V(1,1) down-sweep: the one Jacobi step from zero, x1 = om D^-1 b, is pointwise; its residual
+// b - A x1 is formed on the fly and restricted with P^T (nothing stored on the fine mesh)
+template <typename T>
+__global__ void k_restrict1(int n, int B, const int* __restrict__ act, const T* __restrict__ wx,
+                            const T* __restrict__ wy, const T* __restrict__ dinv, const T* __restrict__ bb,
+                            T* __restrict__ bc) {
+  const int m = n / 2;
+  const int nt = tiles_interior(m);
+  const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
+  if (b >= B || !act[b]) return;
+  const int ld = n + 1;
+  const size_t off = (size_t)b * gsz(n);
+  const T* __restrict__ W = wx + off;
+  const T* __restrict__ Y = wy + off;
+  const T* __restrict__ D = dinv + off;
+  const T* __restrict__ R = bb + off;
+  T* __restrict__ C = bc + (size_t)b * gsz(m);
+  for_tile(m, ch, [&](int P, int I, int J) {
+    const int p = (2 * J) * ld + 2 * I;
+    auto x1 = [&](int q) { return D[q] * R[q]; };
+    auto res = [&](int q) {
+      const T xq = x1(q);
+      return R[q] - (W[q] * (xq - x1(q + 1)) + W[q - 1] * (xq - x1(q - 1)) + Y[q] * (xq - x1(q + ld)) +
+                     Y[q - ld] * (xq - x1(q - ld)));
+    };
+    C[P] = res(p) + T(0.5) * ((res(p + 1) + res(p - 1)) + (res(p + ld) + res(p - ld)) +
+                              (res(p + ld + 1) + res(p - ld - 1)));
+  });
+}
+
+// V(1,1) up-sweep: t = om D^-1 b + P xc, then one Jacobi step out = t + om D^-1 (b - A t);
+// optionally partial <dotv, out>.  Column strips as in k_prolong_smooth.
+template <typename T, bool DOT>
+__global__ void k_prolong_smooth1(int n, int B, const int* __restrict__ act, const T* __restrict__ wx,
+                                  const T* __restrict__ wy, const T* __restrict__ dinv, const T* __restrict__ bb,
+                                  const T* __restrict__ xc, T* __restrict__ out, const T* __restrict__ dotv,
+                                  double* part) {
+  const int nt = tiles_interior(n);
+  const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
+  if (b >= B || !act[b]) return;
+  const int ld = n + 1, ldc = n / 2 + 1;
+  const size_t off = (size_t)b * gsz(n);
+  const T* __restrict__ W = wx + off;
+  const T* __restrict__ Y = wy + off;
+  const T* __restrict__ D = dinv + off;
+  const T* __restrict__ R = bb + off;
+  const T* __restrict__ XC = xc + (size_t)b * gsz(n / 2);
+  T* __restrict__ O = out + off;
+  T acc[1] = {T(0)};
+  int i, j0, nr;
+  if (column_walk(n, ch, i, j0, nr)) {
+    auto t = [&](int q, int ii, int jj) {
+      const int c0 = (jj >> 1) * ldc + (ii >> 1);
+      return D[q] * R[q] + T(0.5) * (XC[c0] + XC[c0 + (ii & 1) + (jj & 1) * ldc]);
+    };
+    const int p0 = j0 * ld + i;
+    T tc[kPer + 2], tw[kPer], te[kPer], wE[kPer], wW[kPer], yv[kPer + 1], dd[kPer], rr[kPer], dv[kPer];
+#pragma unroll
+    for (int k = -1; k <= kPer; ++k) {
+      const int kk = min(k, nr);
+      tc[k + 1] = t(p0 + kk * ld, i, j0 + kk);
+    }
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int kk = min(k, nr - 1);
+      const int q = p0 + kk * ld;
+      tw[k] = t(q - 1, i - 1, j0 + kk);
+      te[k] = t(q + 1, i + 1, j0 + kk);
+      wE[k] = W[q];
+      wW[k] = W[q - 1];
+      dd[k] = D[q];
+      rr[k] = R[q];
+      if (DOT) dv[k] = dotv[off + q];
+    }
+#pragma unroll
+    for (int k = -1; k < kPer; ++k) yv[k + 1] = Y[p0 + min(k, nr - 1) * ld];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      if (k < nr) {
+        const T c = tc[k + 1];
+        const T ax = wE[k] * (c - te[k]) + wW[k] * (c - tw[k]) + yv[k + 1] * (c - tc[k + 2]) + yv[k] * (c - tc[k]);
+        const T o = c + dd[k] * (rr[k] - ax);
+        O[p0 + k * ld] = o;
+        if (DOT) acc[0] += dv[k] * o;
+      }
+    }
+  }
+  if (DOT) tile_partials<1, T>(acc, part, (size_t)b * nt + ch);
+}
+
 // one Jacobi step out = t + om D^-1 (b - A t); optionally partial <dotv, out>
 template <typename T, bool DOT>
 __global__ void k_smooth(int n, int B, const int* __restrict__ act, const T* __restrict__ wx,
@@ -546,8 +638,7 @@ __global__ void __launch_bounds__(kSubThreads) k_subcycle(int ns, int B, const i
   }
   __syncthreads();
   // with dotv (the right-hand side itself, copied to b0) also <v, x>
-  T acc[1] = {vcycle<T>(mg, b0, x0, om, dotv ? b0 : nullptr)};
-  (void)nu;
+  T acc[1] = {vcycle<T>(mg, b0, x0, om, dotv ? b0 : nullptr, nu)};
   T* dst = xout + (size_t)b * V;
   for_all(V, [&](size_t q) { dst[q] = x0[q]; });
   if (dotv) tile_partials<1, T>(acc, part, (size_t)b);
@@ -847,6 +938,7 @@ int grid1(size_t count) {
 template <typename T>
 struct Arena {
   int n, B, Ls;  // Ls streaming multigrid levels (meshes n .. > kSub)
+  int nu;        // Jacobi sweeps per side of the V-cycle (1 or 2)
   size_t V0;
   T *v, *vo, *z, *zn, *w, *wo, *q, *xi;
   double *x64, *b64;
@@ -923,8 +1015,37 @@ cudaError_t vcycle_stream(Arena<T>& A, const T* b0, T* x0, const int* act, T om,
                           size_t sub_smem, cudaStream_t st) {
   const int n = A.n, B = A.B;
   if (A.Ls == 0) {
-    ++tl_launches, k_subcycle<T><<<B, kSubThreads, sub_smem, st>>>(n, B, act, A.subw, A.subw_bytes, b0, x0, 2, om, part, dotv);
+    ++tl_launches, k_subcycle<T><<<B, kSubThreads, sub_smem, st>>>(n, B, act, A.subw, A.subw_bytes, b0, x0, A.nu, om,
+                                                                   part, dotv);
     LAUNCH_CHECK();
+    return cudaSuccess;
+  }
+  if (A.nu == 1) {
+    for (int l = 0; l < A.Ls; ++l) {
+      const int nl = n >> l;
+      const T* b = l ? A.b[l] : b0;
+      T* bc = (l + 1 < A.Ls) ? A.b[l + 1] : A.bsub;
+      ++tl_launches, k_restrict1<T><<<B * tiles_interior(nl / 2), kThreads, 0, st>>>(nl, B, act, A.wx[l], A.wy[l],
+                                                                                   A.dinv[l], b, bc);
+      LAUNCH_CHECK();
+    }
+    const int ns = n >> A.Ls;
+    ++tl_launches, k_subcycle<T><<<B, kSubThreads, sub_smem, st>>>(ns, B, act, A.subw, A.subw_bytes, A.bsub, A.xsub, 1,
+                                                                   om, nullptr, nullptr);
+    LAUNCH_CHECK();
+    for (int l = A.Ls - 1; l >= 0; --l) {
+      const int nl = n >> l;
+      const T* b = l ? A.b[l] : b0;
+      T* xa = l ? A.x[l] : x0;
+      const T* xc = (l + 1 < A.Ls) ? A.x[l + 1] : A.xsub;
+      if (l == 0 && dotv)
+        ++tl_launches, k_prolong_smooth1<T, true><<<B * tiles_interior(nl), kThreads, 0, st>>>(
+            nl, B, act, A.wx[l], A.wy[l], A.dinv[l], b, xc, xa, dotv, part);
+      else
+        ++tl_launches, k_prolong_smooth1<T, false><<<B * tiles_interior(nl), kThreads, 0, st>>>(
+            nl, B, act, A.wx[l], A.wy[l], A.dinv[l], b, xc, xa, nullptr, nullptr);
+      LAUNCH_CHECK();
+    }
     return cudaSuccess;
   }
   for (int l = 0; l < A.Ls; ++l) {
@@ -939,7 +1060,7 @@ cudaError_t vcycle_stream(Arena<T>& A, const T* b0, T* x0, const int* act, T om,
     LAUNCH_CHECK();
   }
   const int ns = n >> A.Ls;
-  ++tl_launches, k_subcycle<T><<<B, kSubThreads, sub_smem, st>>>(ns, B, act, A.subw, A.subw_bytes, A.bsub, A.xsub, 2, om, nullptr,
+  ++tl_launches, k_subcycle<T><<<B, kSubThreads, sub_smem, st>>>(ns, B, act, A.subw, A.subw_bytes, A.bsub, A.xsub, A.nu, om, nullptr,
                                                 nullptr);
   LAUNCH_CHECK();
   for (int l = A.Ls - 1; l >= 0; --l) {
@@ -972,6 +1093,7 @@ template <typename T>
 cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st) {
   Arena<T> A;
   carve_arena<T>(arena, s.n, s.B, A);
+  A.nu = s.nu == 1 ? 1 : 2;
   const int n = s.n, B = s.B;
   const int nt = tiles_interior(n);
   const size_t Bz = (size_t)B;

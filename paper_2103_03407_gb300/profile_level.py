@@ -26,6 +26,7 @@ def main():
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--stream-min", type=int, default=0, help="fine meshes from 1/n on run in the streaming tier")
     ap.add_argument("--threads", type=int, default=0, help="threads per CTA of the per-sample kernel (0: default)")
+    ap.add_argument("--nu", type=int, default=0, help="Jacobi steps per side of the V-cycle (0: default)")
     a = ap.parse_args()
     from paper_2103_03407_gb300 import binding, build
     from synthetic_inputs import WORKLOADS, shifts
@@ -42,6 +43,8 @@ def main():
     ctx.mq_set_precision(binding.MQ_PREC_MIXED if a.precision == "mixed" else binding.MQ_PREC_FP64)
     if a.stream_min:
         ctx.mq_set_tier(a.stream_min)
+    if a.nu:
+        ctx.mq_set_smoothing(a.nu)
     if a.threads:
         for l in range(len(wl.levels)):
             ctx.mq_set_cta_threads(l, a.threads)
@@ -51,7 +54,7 @@ def main():
             ctx.mq_eval_level(l, 0, n, per_sample=False)
             st = ctx.mq_get_stats()
             print(json.dumps({"level": l, "points": n, "samples": n * wl.levels[l].R, "stream_min": a.stream_min,
-                              "threads_req": a.threads, **st}))
+                              "threads_req": a.threads, "nu": a.nu, **st}))
     ctx.close()
 
 

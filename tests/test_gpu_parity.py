@@ -266,3 +266,18 @@ def test_tiers_agree_and_match_oracle(B, prec):
         assert np.all(np.abs(ps_s[..., 1:3] - ps_c[..., 1:3]) <= 1e-10 * np.abs(ps_c[..., 1:3]) + 1e-300)
         ref = mlqmc.level_samples(levels[l], levels[l - 1] if l else None, zs[l], ds[l], list(range(k0, k1)))
         _check_level(ps_s, ref)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_smoothing_variants_agree(B, prec):
+    # V(1,1) and V(2,2) precondition the same systems: the eigenvalues agree to the solver
+    # tolerances, in both tiers (meshes 1/16 in the per-sample kernel, 1/64 streamed)
+    levels = [Level(16, 8, 16, 4, 16, 2), Level(64, 16, 64, 8, 16, 2)]
+    out = []
+    for nu in (1, 2):
+        ctx, zs, ds = make_ctx(B, levels, seed=5, prec=prec)
+        ctx.mq_set_smoothing(nu)
+        out.append([ctx.mq_eval_level(l, 2, 6)[0] for l in range(2)])
+    for l in range(2):
+        a, b = out[0][l], out[1][l]
+        assert np.all(np.abs(a[..., :3] - b[..., :3]) <= 1e-10 * np.abs(b[..., :3]) + 1e-300)
