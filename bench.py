@@ -263,8 +263,9 @@ def percta_fp64_flops(wl, level, st, prec):
         if not (pv.n_fine == nc and pv.s == lv.S):
             solves.append(pv.n_fine)
     I, O = st["fine_iters_mean"], st["outer_iters_mean"]
+    streamed = lv.n_fine >= stream_min_default(prec) and not (lv.n_fine == nc and lv.s == lv.S)
     for n in solves:
-        if n >= stream_min_default(prec) and n != nc:
+        if streamed and n != nc:
             continue  # batched streaming tier
         inner64 = prec == "fp64" or n == nc
         per += (n - 1) ** 2 * (FP64_FINE_SETUP + FP64_FINE_OUTER * O + (FP64_INNER * I if inner64 else 0))
@@ -272,37 +273,38 @@ def percta_fp64_flops(wl, level, st, prec):
 
 
 # Streaming tier (fine meshes >= 1/32 mixed): bounded by HBM.  Bytes per fine unknown with every
-# kernel reading and writing each of its arrays once (e = 4 bytes, FP32 inner vectors):
-#   per inner MINRES iteration: MINRES sweeps 16 e (operator + pending update 10 e, Lanczos
-#   vector 6 e) + V-cycle 22.5 e on the fine level (two Jacobi sweeps from zero 5 e, residual
-#   restriction 4.25 e, prolongation + Jacobi 6.25 e, Jacobi + dot 7 e) + 21.5 e / 4 and / 16 on
-#   the two coarser levels above the on-chip sub-cycle;
+# kernel reading and writing each of its arrays once (e = 4 bytes, FP32 inner vectors; the
+# default V(1,1) smoothing of this tier):
+#   per inner MINRES iteration: MINRES sweeps 14 e (operator + pending update 10 e, Lanczos
+#   vector 4 e) + V-cycle 11.5 e on the fine level (restriction of the first sweep's residual
+#   4.25 e, prolongation + sweep + dot 7.25 e) + 10.5 e / 4 and / 16 on the coarser streamed
+#   levels (the on-chip sub-cycle below 1/32 is not counted);
 #   per refinement step: 12 e + 48 bytes (inner start 6 e, final update 5 e, FP64 solution update
-#   e + 16, FP64 residual e + 32) + one V-cycle;
-#   per solve: 20 e + 56 bytes (clearing 8 e + 16, weights 3 e + 16, interpolation and
-#   right-hand side e + 24, operators of the coarser levels ~8 e).
+#   e + 16, FP64 residual with FP64 weights e + 32) + one V-cycle;
+#   per solve: 20 e + 72 bytes (clearing 8 e + 16, FP32 and FP64 weights 3 e + 32, interpolation
+#   and right-hand side e + 24, operators of the coarser levels ~8 e).
 def stream_bytes(wl, level, st, prec):
     e = 4 if prec == "mixed" else 8
     lv = wl.levels[level]
-    vcyc = 22.5 * e + 21.5 * e * (1 / 4 + 1 / 16)
+    vcyc = 11.5 * e + 10.5 * e * (1 / 4 + 1 / 16)
     I, O = st["fine_iters_mean"], st["outer_iters_mean"]
     solves = []
     if lv.n_fine >= stream_min_default(prec) and not (lv.n_fine == lv.n_coarse and lv.s == lv.S):
         solves.append(lv.n_fine)
     if level > 0:
         pv = wl.levels[level - 1]
-        if pv.n_fine >= stream_min_default(prec) and pv.n_fine != lv.n_coarse:
+        if lv.n_fine >= stream_min_default(prec) and pv.n_fine != lv.n_coarse:
             solves.append(pv.n_fine)
     per = 0.0
     for n in solves:
-        per += (n - 1) ** 2 * ((16 * e + vcyc) * I + (12 * e + 48 + vcyc) * O + 20 * e + 56)
+        per += (n - 1) ** 2 * ((14 * e + vcyc) * I + (12 * e + 48 + vcyc) * O + 20 * e + 72)
     return per * lv.N * lv.R
 
 
 # ncu DRAM traffic of the per-sample kernel's launch on a level, valid only for the kernel source
-# it was measured on (profiles/sample_kernel_mlqmc4_h16_128_level1.md; one full-size launch)
-SAMPLE_KERNEL_TRAFFIC = {"source_sha256": "c93b91324d65bd97eede49493e7f1831b33a3a501456b12caabd2dedd3b8d12f",
-                         "level": 1, "precision": "mixed", "bytes_per_launch": 716.9984e6 + 29.254656e6}
+# it was measured on (profiles/sample_kernel_mlqmc4_h16_128_level0.md; one full-size launch)
+SAMPLE_KERNEL_TRAFFIC = {"source_sha256": "018b22b84c84152daa9202de9f9d8662624b3d90215e11de6d8fba0a1b718246",
+                         "level": 0, "precision": "mixed", "bytes_per_launch": 366.075648e6 + 27.624704e6}
 
 
 def _percta_source_hash():

@@ -477,44 +477,18 @@ __global__ void k_prolong_smooth1(int n, int B, const int* __restrict__ act, con
   const T* __restrict__ XC = xc + (size_t)b * gsz(n / 2);
   T* __restrict__ O = out + off;
   T acc[1] = {T(0)};
-  int i, j0, nr;
-  if (column_walk(n, ch, i, j0, nr)) {
+  for_tile(n, ch, [&](int p, int i, int j) {
     auto t = [&](int q, int ii, int jj) {
       const int c0 = (jj >> 1) * ldc + (ii >> 1);
       return D[q] * R[q] + T(0.5) * (XC[c0] + XC[c0 + (ii & 1) + (jj & 1) * ldc]);
     };
-    const int p0 = j0 * ld + i;
-    T tc[kPer + 2], tw[kPer], te[kPer], wE[kPer], wW[kPer], yv[kPer + 1], dd[kPer], rr[kPer], dv[kPer];
-#pragma unroll
-    for (int k = -1; k <= kPer; ++k) {
-      const int kk = min(k, nr);
-      tc[k + 1] = t(p0 + kk * ld, i, j0 + kk);
-    }
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-      const int kk = min(k, nr - 1);
-      const int q = p0 + kk * ld;
-      tw[k] = t(q - 1, i - 1, j0 + kk);
-      te[k] = t(q + 1, i + 1, j0 + kk);
-      wE[k] = W[q];
-      wW[k] = W[q - 1];
-      dd[k] = D[q];
-      rr[k] = R[q];
-      if (DOT) dv[k] = dotv[off + q];
-    }
-#pragma unroll
-    for (int k = -1; k < kPer; ++k) yv[k + 1] = Y[p0 + min(k, nr - 1) * ld];
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-      if (k < nr) {
-        const T c = tc[k + 1];
-        const T ax = wE[k] * (c - te[k]) + wW[k] * (c - tw[k]) + yv[k + 1] * (c - tc[k + 2]) + yv[k] * (c - tc[k]);
-        const T o = c + dd[k] * (rr[k] - ax);
-        O[p0 + k * ld] = o;
-        if (DOT) acc[0] += dv[k] * o;
-      }
-    }
-  }
+    const T tp = t(p, i, j);
+    const T ax = W[p] * (tp - t(p + 1, i + 1, j)) + W[p - 1] * (tp - t(p - 1, i - 1, j)) +
+                 Y[p] * (tp - t(p + ld, i, j + 1)) + Y[p - ld] * (tp - t(p - ld, i, j - 1));
+    const T o = tp + D[p] * (R[p] - ax);
+    O[p] = o;
+    if (DOT) acc[0] += dotv[off + p] * o;
+  });
   if (DOT) tile_partials<1, T>(acc, part, (size_t)b * nt + ch);
 }
 
@@ -663,54 +637,16 @@ __global__ void k_minres_q(int n, int B, const int* __restrict__ act, const SS<T
   const T* __restrict__ Y = wy + off;
   const T* __restrict__ Z = z + off;
   T acc[1] = {T(0)};
-  int i, j0, nr;
-  if (column_walk(n, ch, i, j0, nr)) {
-    // z on the centre column rows j0-1 .. j0+nr, the west column rows j0-1 .. (south-west and
-    // west neighbours) and the east column rows j0 .. j0+nr (east and north-east neighbours)
-    const int p0 = j0 * ld + i;
-    T zc[kPer + 2], zw[kPer + 1], ze[kPer + 1], wE[kPer], wW[kPer], yv[kPer + 1];
-    T zpv[kPer], wov[kPer], wv[kPer], xiv[kPer];
-#pragma unroll
-    for (int k = -1; k <= kPer; ++k) zc[k + 1] = Z[p0 + min(k, nr) * ld];
-#pragma unroll
-    for (int k = -1; k < kPer; ++k) {
-      const int q = p0 + min(k, nr - 1) * ld;
-      zw[k + 1] = Z[q - 1];
-      yv[k + 1] = Y[q];
+  for_tile(n, ch, [&](int p, int, int) {
+    if (S.pend) {
+      const T wnew = (zp[off + p] * S.igp - S.a3 * wo[off + p] - S.a2 * w[off + p]) * S.ia1;
+      wo[off + p] = wnew;
+      xi[off + p] += S.cx * wnew;
     }
-#pragma unroll
-    for (int k = 0; k <= kPer; ++k) ze[k] = Z[p0 + min(k, nr) * ld + 1];
-    const bool pend = S.pend;
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-      const int q = p0 + min(k, nr - 1) * ld;
-      wE[k] = W[q];
-      wW[k] = W[q - 1];
-      if (pend) {
-        zpv[k] = zp[off + q];
-        wov[k] = wo[off + q];
-        wv[k] = w[off + q];
-        xiv[k] = xi[off + q];
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-      if (k < nr) {
-        const int q = off + p0 + k * ld;
-        if (pend) {
-          const T wnew = (zpv[k] * S.igp - S.a3 * wov[k] - S.a2 * wv[k]) * S.ia1;
-          wo[q] = wnew;
-          xi[q] = xiv[k] + S.cx * wnew;
-        }
-        const T c = zc[k + 1];
-        const T az = wE[k] * (c - ze[k]) + wW[k] * (c - zw[k + 1]) + yv[k + 1] * (c - zc[k + 2]) + yv[k] * (c - zc[k]);
-        const T mz = T(6) * c + (ze[k] + zw[k + 1]) + (zc[k + 2] + zc[k]) + (ze[k + 1] + zw[k]);
-        const T kz = (az - sigm * mz) * S.ig;
-        qv[q] = kz;
-        acc[0] += kz * c;
-      }
-    }
-  }
+    const T kz = (stiff<T, T>(W, Y, Z, p, ld) - sigm * mass7(Z, p, ld)) * S.ig;
+    qv[off + p] = kz;
+    acc[0] += kz * Z[p];
+  });
   tile_partials<1, T>(acc, part, (size_t)b * nt + ch);
 }
 
