@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison run")
     ap.add_argument("--baseline-seconds", type=float, default=20.0)
+    ap.add_argument("--schedule", default="sequential", choices=["concurrent", "sequential"],
+                    help="levels one after another (clean per-kernel timing for the rooflines), or all "
+                         "at once on their own streams (mq_eval_levels_device)")
     return ap.parse_args()
 
 
@@ -114,24 +117,27 @@ def setup_context(binding, wl, stream_ptr, prec, seed_offset=0):
     return ctx, zs, ds
 
 
-def run_device_step(ctx, wl, outs, sums):
-    for l, lv in enumerate(wl.levels):
-        ctx.mq_eval_level_device(l, 0, lv.N, outs[l], sums[l])
+def run_device_step(ctx, wl, outs, sums, sequential=False):
+    if sequential:
+        for l, lv in enumerate(wl.levels):
+            ctx.mq_eval_level_device(l, 0, lv.N, outs[l], sums[l])
+    else:  # all levels at once, each on its own stream (the library's concurrent schedule)
+        ctx.mq_eval_levels_device(list(range(len(wl.levels))), outs, sums)
 
 
-def time_device(binding, torch, wl, prec, steps, warmup, stream, seed_offset=0):
+def time_device(binding, torch, wl, prec, steps, warmup, stream, seed_offset=0, sequential=False):
     ctx, zs, ds = setup_context(binding, wl, stream.cuda_stream, prec, seed_offset)
     outs = [torch.empty((lv.R, lv.N, 4), dtype=torch.float64, device="cuda") for lv in wl.levels]
     sums = [torch.empty(lv.R, dtype=torch.float64, device="cuda") for lv in wl.levels]
     for _ in range(warmup):
-        run_device_step(ctx, wl, outs, sums)
+        run_device_step(ctx, wl, outs, sums, sequential)
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ctx.mq_reset_sums()  # also clears the per-level device timers
     ev0.record(stream)
     for _ in range(steps):
-        run_device_step(ctx, wl, outs, sums)
+        run_device_step(ctx, wl, outs, sums, sequential)
     ev1.record(stream)
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
@@ -387,7 +393,8 @@ def main():
     with torch.cuda.stream(stream):
         with sampler:
             ctx, ms, timing, kstats, outs, launches = time_device(binding, torch, wl, args.precision, args.steps,
-                                                                  args.warmup, stream, seed_offset=rank)
+                                                                  args.warmup, stream, seed_offset=rank,
+                                                                  sequential=args.schedule == "sequential")
     if world > 1:
         t = torch.tensor([ms], dtype=torch.float64, device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -396,7 +403,8 @@ def main():
     value = samples_per_step * args.steps / (ms / 1e3)
     plain = None
     if not args.no_plain and args.precision == "mixed" and rank == 0:
-        ctxp, msp, _, _, _, _ = time_device(binding, torch, wl, "fp64", 1, 1, stream)
+        ctxp, msp, _, _, _, _ = time_device(binding, torch, wl, "fp64", 1, 1, stream,
+                                            sequential=args.schedule == "sequential")
         plain = {"value": wl.samples / (msp / 1e3), "unit": "samples/s", "ms_per_step": msp, "steps": 1}
         ctxp.close()
     e2e = None
@@ -423,7 +431,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
-        "config": workload_config(wl, args.precision, world),
+        "config": dict(workload_config(wl, args.precision, world), schedule=args.schedule),
         "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "roofline_stream": roofline_stream,
         "clocks": clocks,
         "per_level": [{"level": l, "kernel_ms": coef_ms[l] + sample_ms[l], "coef_ms": coef_ms[l],

@@ -161,6 +161,20 @@ mq_status mq_eval_level(mq_ctx* ctx, int32_t level, uint32_t k0, uint32_t k1, do
 mq_status mq_eval_level_device(mq_ctx* ctx, int32_t level, uint32_t k0, uint32_t k1,
                                double* d_per_sample, double* d_shift_sums);
 
+/* Evaluate several whole levels (every point k in [0, N_l) of every shift) at the same time
+ * (Algorithm 2, steps 4-15 for each listed level; the levels are independent).  Each level runs on
+ * its own internal context -- its own CUDA stream, buffers and host thread -- so the latency-bound
+ * per-sample kernel of small meshes overlaps the bandwidth-bound streaming solves of large ones.
+ *   levels[i]: distinct level indices (lattice and shifts set); d_per_sample[i] and d_shift_sums[i]
+ *   as in mq_eval_level_device for levels[i] (either array of pointers, or any entry, may be NULL).
+ * Returns after every level has finished; the sums, timers and launch counts of the levels are
+ * added to this context (mq_estimate, mq_get_level_timing, mq_get_launch_count).  The internal
+ * contexts are built on the first call (and again after any mq_set_* call), share the free device
+ * memory equally, and are released by mq_destroy.  Returns the first error of a level
+ * (MQ_ENOCONV only if no other error occurred; results are written in that case). */
+mq_status mq_eval_levels_device(mq_ctx* ctx, int32_t nlevels, const int32_t* levels, double* const* d_per_sample,
+                                double* const* d_shift_sums);
+
 /* Estimate from the sums accumulated so far (eq. tg-mlqmc): Q^(r)_l = sum_k diff / n_l where
  * n_l is the number of points evaluated on level l, Qhat_l = mean_r Q^(r)_l, mean = sum_l Qhat_l,
  * level_var[l] = sum_r (Qhat_l - Q^(r)_l)^2 / (R (R - 1)) (eq. sample_var), std_err =

@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "MQ_OK", 1: "MQ_EINVAL", 2: "MQ_ENOMEM", 3: "MQ_ECUDA", 4: "M
 # every symbol the header declares
 EXPORTS = [
     "mq_create", "mq_destroy", "mq_set_coefficient", "mq_set_levels", "mq_set_lattice", "mq_set_shifts",
-    "mq_set_precision", "mq_set_solver_options", "mq_set_eig_options", "mq_set_smoothing", "mq_set_tier", "mq_set_cta_threads", "mq_eval_level", "mq_eval_level_device", "mq_estimate", "mq_reset_sums",
+    "mq_set_precision", "mq_set_solver_options", "mq_set_eig_options", "mq_set_smoothing", "mq_set_tier", "mq_set_cta_threads", "mq_eval_level", "mq_eval_level_device", "mq_eval_levels_device", "mq_estimate", "mq_reset_sums",
     "mq_get_level_timing", "mq_get_kernel_timing", "mq_get_launch_count", "mq_eval_point",
     "mq_get_stats", "mq_last_error", "mq_cbc_lattice", "mq_lattice_points_device", "mq_coefficients_device",
     "mq_apply_operator_device", "mq_twogrid_samples_noalloc",
@@ -87,6 +87,7 @@ def load(path: str = LIB_PATH):
         "mq_set_cta_threads": ([P, i32, i32], C.c_int),
         "mq_eval_level": ([P, i32, u32, u32, dp, dp], C.c_int),
         "mq_eval_level_device": ([P, i32, u32, u32, P, P], C.c_int),
+        "mq_eval_levels_device": ([P, i32, C.POINTER(C.c_int32), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)], C.c_int),
         "mq_estimate": ([P, dp, dp, dp, dp], C.c_int),
         "mq_reset_sums": ([P], C.c_int),
         "mq_get_level_timing": ([P, i32, dp, dp, C.POINTER(C.c_uint64)], C.c_int),
@@ -210,6 +211,15 @@ class Context:
     def mq_eval_level_device(self, level, k0, k1, d_per_sample=None, d_shift_sums=None):
         self._check(self.lib.mq_eval_level_device(self.h, int(level), int(k0), int(k1), _tptr(d_per_sample),
                                                   _tptr(d_shift_sums)))
+
+    def mq_eval_levels_device(self, levels, d_per_sample=None, d_shift_sums=None):
+        """Whole levels at once, each on its own internal context and stream; per-level device
+        outputs as in mq_eval_level_device (lists of tensors or None)."""
+        n = len(levels)
+        lv = (C.c_int32 * n)(*[int(l) for l in levels])
+        ps = (C.c_void_p * n)(*[_tptr(t) for t in d_per_sample]) if d_per_sample is not None else None
+        ss = (C.c_void_p * n)(*[_tptr(t) for t in d_shift_sums]) if d_shift_sums is not None else None
+        self._check(self.lib.mq_eval_levels_device(self.h, n, lv, ps, ss))
 
     def mq_estimate(self):
         L = len(self.levels)

@@ -10,6 +10,7 @@
 #include <map>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -32,6 +33,9 @@ struct mq_ctx {
   int sm_count = 0;
   int smem_optin = 0;
   uint64_t n_launches = 0;  // kernels launched since mq_set_levels / mq_reset_sums
+  std::vector<mq_ctx*> lanes;  // per level: child context of mq_eval_levels_device (built lazily)
+  bool lanes_stale = true;     // a setter ran since the lanes were built
+  int mem_share = 1;           // contexts sharing the free device memory with this one
   std::vector<int> cta_threads;  // per level: threads per CTA of the per-sample kernel (0: default)
   std::string err;
 
@@ -502,6 +506,7 @@ int points_per_pass(const mq_ctx* c, const LevelGeom& g, int R, int npts) {
   size_t free_b = 0, total_b = 0;
   size_t budget = (size_t)24 << 30;
   if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) budget = std::min<size_t>((size_t)(0.4 * free_b), (size_t)64 << 30);
+  budget /= (size_t)std::max(1, c->mem_share);
   size_t pts = budget / (per_sample * (size_t)R);
   if (pts < 1) pts = 1;
   return (int)std::min<size_t>(pts, (size_t)npts);
@@ -624,6 +629,9 @@ mq_status mq_create(mq_ctx** out, int device, void* cuda_stream) {
 
 mq_status mq_destroy(mq_ctx* c) {
   if (!c) return MQ_EINVAL;
+  for (mq_ctx* l : c->lanes)
+    if (l) mq_destroy(l);
+  c->lanes.clear();
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
   for (DevBuf* b : {&c->Y, &c->af, &c->ac, &c->ap, &c->out, &c->stat, &c->outer, &c->scratch, &c->sums_d,
@@ -649,6 +657,7 @@ const char* mq_last_error(const mq_ctx* c) { return c ? c->err.c_str() : "null c
 
 mq_status mq_set_coefficient(mq_ctx* c, double a0, int32_t s_max, int32_t family, double decay) {
   if (!c) return MQ_EINVAL;
+  c->lanes_stale = true;
   if (!(a0 > 0.0) || !std::isfinite(a0)) return fail(c, MQ_EINVAL, "a0 must be positive, got %g", a0);
   if (s_max < 0 || s_max > 65536) return fail(c, MQ_EINVAL, "s_max %d out of range", s_max);
   if (family != 0) return fail(c, MQ_EINVAL, "unknown coefficient family %d", family);
@@ -682,6 +691,7 @@ mq_status mq_set_coefficient(mq_ctx* c, double a0, int32_t s_max, int32_t family
 
 mq_status mq_set_levels(mq_ctx* c, int32_t L_plus_1, const mq_level* levels) {
   if (!c) return MQ_EINVAL;
+  c->lanes_stale = true;
   if (L_plus_1 < 1 || L_plus_1 > 32 || !levels) return fail(c, MQ_EINVAL, "need 1..32 levels");
   if (!c->coef_set) return fail(c, MQ_ESTATE, "set the coefficient before the levels");
   for (int l = 0; l < L_plus_1; ++l) {
@@ -722,6 +732,7 @@ mq_status mq_set_levels(mq_ctx* c, int32_t L_plus_1, const mq_level* levels) {
 
 mq_status mq_set_lattice(mq_ctx* c, int32_t level, const uint32_t* z, int32_t s) {
   if (!c) return MQ_EINVAL;
+  c->lanes_stale = true;
   if (level < 0 || level >= (int)c->levels.size()) return fail(c, MQ_EINVAL, "level %d out of range", level);
   const mq_level& lv = c->levels[level];
   if (!z || s != lv.s) return fail(c, MQ_EINVAL, "lattice of level %d needs s = %d components", level, lv.s);
@@ -738,6 +749,7 @@ mq_status mq_set_lattice(mq_ctx* c, int32_t level, const uint32_t* z, int32_t s)
 
 mq_status mq_set_shifts(mq_ctx* c, int32_t level, const double* delta) {
   if (!c) return MQ_EINVAL;
+  c->lanes_stale = true;
   if (level < 0 || level >= (int)c->levels.size()) return fail(c, MQ_EINVAL, "level %d out of range", level);
   if (!delta) return fail(c, MQ_EINVAL, "null shifts");
   const mq_level& lv = c->levels[level];
@@ -755,6 +767,7 @@ mq_status mq_set_shifts(mq_ctx* c, int32_t level, const double* delta) {
 
 mq_status mq_set_precision(mq_ctx* c, mq_precision prec, double tol_linear) {
   if (!c) return MQ_EINVAL;
+  c->lanes_stale = true;
   if (prec != MQ_PREC_FP64 && prec != MQ_PREC_MIXED) return fail(c, MQ_EINVAL, "unknown precision %d", (int)prec);
   if (!std::isfinite(tol_linear) || tol_linear >= 1.0) return fail(c, MQ_EINVAL, "tolerance must be < 1");
   c->prec = prec;
@@ -764,6 +777,7 @@ mq_status mq_set_precision(mq_ctx* c, mq_precision prec, double tol_linear) {
 
 mq_status mq_set_solver_options(mq_ctx* c, double tol_inner, int32_t max_inner, int32_t max_outer) {
   if (!c) return MQ_EINVAL;
+  c->lanes_stale = true;
   if (!std::isfinite(tol_inner) || tol_inner >= 1.0 || max_inner > 100000 || max_outer > 1000)
     return fail(c, MQ_EINVAL, "bad solver options");
   c->opt_tol_inner = tol_inner > 0 ? tol_inner : 0.0;
@@ -774,6 +788,7 @@ mq_status mq_set_solver_options(mq_ctx* c, double tol_inner, int32_t max_inner, 
 
 mq_status mq_set_eig_options(mq_ctx* c, double tol_eig, int32_t max_eig) {
   if (!c) return MQ_EINVAL;
+  c->lanes_stale = true;
   if (!std::isfinite(tol_eig) || tol_eig >= 1.0 || max_eig > 100000) return fail(c, MQ_EINVAL, "bad eigensolver options");
   c->opt_tol_eig = tol_eig > 0 ? tol_eig : 0.0;
   c->opt_max_eig = max_eig > 0 ? max_eig : 0;
@@ -782,6 +797,7 @@ mq_status mq_set_eig_options(mq_ctx* c, double tol_eig, int32_t max_eig) {
 
 mq_status mq_set_cta_threads(mq_ctx* c, int32_t level, int32_t threads) {
   if (!c) return MQ_EINVAL;
+  c->lanes_stale = true;
   if (level < 0 || level >= 64) return fail(c, MQ_EINVAL, "level %d out of range", (int)level);
   if (threads != 0 && (threads < 32 || threads > 512 || threads % 32 != 0))
     return fail(c, MQ_EINVAL, "threads must be 0 or a multiple of 32 in [32, 512]");
@@ -792,6 +808,7 @@ mq_status mq_set_cta_threads(mq_ctx* c, int32_t level, int32_t threads) {
 
 mq_status mq_set_smoothing(mq_ctx* c, int32_t nu) {
   if (!c) return MQ_EINVAL;
+  c->lanes_stale = true;
   if (nu < 0 || nu > 2) return fail(c, MQ_EINVAL, "nu must be 0 (default), 1 or 2");
   c->opt_nu = nu;
   return MQ_OK;
@@ -799,6 +816,7 @@ mq_status mq_set_smoothing(mq_ctx* c, int32_t nu) {
 
 mq_status mq_set_tier(mq_ctx* c, int32_t stream_min_n) {
   if (!c) return MQ_EINVAL;
+  c->lanes_stale = true;
   if (stream_min_n < 0 || stream_min_n == 1) return fail(c, MQ_EINVAL, "stream_min_n must be 0 or >= 2");
   c->stream_min = stream_min_n;
   return MQ_OK;
@@ -813,6 +831,96 @@ mq_status mq_eval_level_device(mq_ctx* c, int32_t level, uint32_t k0, uint32_t k
                                double* d_shift_sums) {
   if (!c) return MQ_EINVAL;
   return eval_level_impl(c, level, k0, k1, nullptr, nullptr, d_per_sample, d_shift_sums);
+}
+
+mq_status mq_eval_levels_device(mq_ctx* c, int32_t nlev, const int32_t* levels, double* const* d_per_sample,
+                                double* const* d_shift_sums) {
+  if (!c) return MQ_EINVAL;
+  if (nlev < 0 || (nlev > 0 && !levels)) return fail(c, MQ_EINVAL, "bad level list");
+  for (int i = 0; i < nlev; ++i) {
+    const mq_status st = check_level_ready(c, levels[i]);
+    if (st != MQ_OK) return st;
+    for (int k = 0; k < i; ++k)
+      if (levels[k] == levels[i]) return fail(c, MQ_EINVAL, "level %d listed twice", (int)levels[i]);
+  }
+  if (nlev == 0) return MQ_OK;
+  MQ_CUDA(c, cudaSetDevice(c->device));
+  MQ_CUDA(c, cudaStreamSynchronize(c->stream));  // earlier work of the caller's stream first
+  // one child context per level: its own stream, buffers and host thread
+  if (c->lanes_stale) {
+    for (mq_ctx* l : c->lanes)
+      if (l) mq_destroy(l);
+    c->lanes.clear();
+    c->lanes_stale = false;
+  }
+  if (c->lanes.size() < c->levels.size()) c->lanes.resize(c->levels.size(), nullptr);
+  for (int i = 0; i < nlev; ++i) {
+    const int l = levels[i];
+    if (!c->lanes[l]) {
+      mq_ctx* ch = nullptr;
+      mq_status st = mq_create(&ch, c->device, nullptr);
+      if (st != MQ_OK) return fail(c, st, "creating the context of level %d failed", l);
+      auto chk = [&](mq_status s2) {
+        if (s2 != MQ_OK && st == MQ_OK) st = s2;
+      };
+      chk(mq_set_coefficient(ch, c->a0, c->s_max, c->family, c->decay));
+      chk(mq_set_levels(ch, (int32_t)c->levels.size(), c->levels.data()));
+      chk(mq_set_lattice(ch, l, c->z[l].data(), (int32_t)c->z[l].size()));
+      chk(mq_set_shifts(ch, l, c->delta[l].data()));
+      chk(mq_set_precision(ch, (mq_precision)c->prec, c->tol_lin));
+      chk(mq_set_solver_options(ch, c->opt_tol_inner, c->opt_max_inner, c->opt_max_outer));
+      chk(mq_set_eig_options(ch, c->opt_tol_eig, c->opt_max_eig));
+      chk(mq_set_smoothing(ch, c->opt_nu));
+      chk(mq_set_tier(ch, c->stream_min));
+      if (l < (int)c->cta_threads.size()) chk(mq_set_cta_threads(ch, l, c->cta_threads[l]));
+      if (st != MQ_OK) {
+        const std::string m = ch->err;
+        mq_destroy(ch);
+        return fail(c, st, "configuring the context of level %d: %s", l, m.c_str());
+      }
+      c->lanes[l] = ch;
+    }
+    c->lanes[l]->mem_share = nlev;
+  }
+  std::vector<mq_status> status(nlev, MQ_OK);
+  std::vector<std::thread> threads;
+  try {
+    for (int i = 0; i < nlev; ++i)
+      threads.emplace_back([c, levels, d_per_sample, d_shift_sums, i, &status] {
+        const int l = levels[i];
+        if (cudaSetDevice(c->device) != cudaSuccess) {
+          status[i] = MQ_ECUDA;
+          return;
+        }
+        status[i] = mq_eval_level_device(c->lanes[l], l, 0, c->levels[l].N, d_per_sample ? d_per_sample[i] : nullptr,
+                                         d_shift_sums ? d_shift_sums[i] : nullptr);
+      });
+  } catch (...) {
+    for (auto& t : threads) t.join();
+    return fail(c, MQ_ENOMEM, "could not start the level threads");
+  }
+  for (auto& t : threads) t.join();
+  // fold the levels' sums, timers and counters into this context
+  mq_status result = MQ_OK;
+  for (int i = 0; i < nlev; ++i) {
+    const int l = levels[i];
+    mq_ctx* ch = c->lanes[l];
+    for (size_t r = 0; r < c->sums[l].size(); ++r) c->sums[l][r] += ch->sums[l][r];
+    c->npoints[l] += ch->npoints[l];
+    c->lvl_coef_ms[l] += ch->lvl_coef_ms[l];
+    c->lvl_sample_ms[l] += ch->lvl_sample_ms[l];
+    c->lvl_launches[l] += ch->lvl_launches[l];
+    c->lvl_percta_ms[l] += ch->lvl_percta_ms[l];
+    c->lvl_stream_ms[l] += ch->lvl_stream_ms[l];
+    c->n_launches += ch->n_launches;
+    c->stats = ch->stats;
+    if (status[i] != MQ_OK && (result == MQ_OK || result == MQ_ENOCONV)) {
+      result = status[i];
+      c->err = "level " + std::to_string(l) + ": " + ch->err;
+    }
+    mq_reset_sums(ch);
+  }
+  return result;
 }
 
 mq_status mq_reset_sums(mq_ctx* c) {

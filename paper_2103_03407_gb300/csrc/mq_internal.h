@@ -89,6 +89,10 @@ cudaError_t launch_sample(const SampleLaunch& p, int mixed, int blocks, int thre
 int sample_occupancy(int mixed, int threads, size_t smem);
 int sample_static_smem(int mixed);
 cudaError_t set_sample_smem(int mixed, int bytes);
+// Raises a kernel's dynamic shared memory limit to at least `bytes` on the current device and
+// never lowers it, so launches from concurrent host threads (levels evaluated at the same time)
+// cannot undo one another's setting between the call and the launch.
+cudaError_t raise_smem_limit(const void* func, int bytes);
 
 // Coefficient building blocks (mq_coef.cu)
 cudaError_t launch_lattice_points(const uint32_t* d_z, uint32_t N, const double* d_delta, int R, int s,

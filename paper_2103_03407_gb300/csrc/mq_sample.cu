@@ -30,6 +30,9 @@
 
 #include <cmath>
 #include <cstdint>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "mq_device.cuh"
 #include "mq_internal.h"
@@ -873,9 +876,23 @@ int sample_static_smem(int mixed) {
   return e == cudaSuccess ? (int)fa.sharedSizeBytes : 8192;
 }
 
+cudaError_t raise_smem_limit(const void* func, int bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, int> limit;  // (device, kernel) -> limit set so far
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  int& cur = limit[{dev, func}];
+  if (bytes <= cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
+
 cudaError_t set_sample_smem(int mixed, int bytes) {
-  return mixed ? cudaFuncSetAttribute(sample_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
-               : cudaFuncSetAttribute(sample_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return mixed ? raise_smem_limit((const void*)sample_kernel<float>, bytes)
+               : raise_smem_limit((const void*)sample_kernel<double>, bytes);
 }
 
 cudaError_t launch_apply_operator(int n, int B, const double* d_a, int which, double sigma, const double* d_x,

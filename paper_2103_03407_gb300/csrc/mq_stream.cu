@@ -1036,9 +1036,9 @@ cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st) {
   const T om = T(s.omega);
   const int ns = n >> A.Ls;
   const size_t sub_smem = sub_vectors_bytes<T>(ns);
-  cudaError_t e = cudaFuncSetAttribute(k_subcycle<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sub_smem);
+  cudaError_t e = raise_smem_limit((const void*)k_subcycle<T>, (int)sub_smem);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_sub_build<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sub_smem);
+  e = raise_smem_limit((const void*)k_sub_build<T>, (int)sub_smem);
   if (e != cudaSuccess) return e;
   const int gs = (B + 255) / 256;
   // ---- clear vectors (boundary rings must be zero), build the operators

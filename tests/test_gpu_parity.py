@@ -281,3 +281,38 @@ def test_smoothing_variants_agree(B, prec):
     for l in range(2):
         a, b = out[0][l], out[1][l]
         assert np.all(np.abs(a[..., :3] - b[..., :3]) <= 1e-10 * np.abs(b[..., :3]) + 1e-300)
+
+
+def test_eval_levels_device_matches_level_by_level(B):
+    # the concurrent multi-level call (one internal context, stream and host thread per level)
+    # gives the per-level results, sums and estimate of the level-by-level calls
+    levels = [Level(16, 8, 16, 4, 32, 2), Level(32, 8, 32, 6, 32, 2), Level(64, 16, 64, 8, 16, 2)]
+    ctx_a, _, _ = make_ctx(B, levels, seed=9, prec=1)
+    ctx_b, _, _ = make_ctx(B, levels, seed=9, prec=1)
+    out_a = [torch.empty((lv.R, lv.N, 4), dtype=torch.float64, device="cuda") for lv in levels]
+    sum_a = [torch.empty(lv.R, dtype=torch.float64, device="cuda") for lv in levels]
+    # warm-up calls build the coefficient tables (each internal context builds its own), then
+    # the compared calls
+    ctx_a.mq_eval_levels_device([0, 1, 2], out_a, sum_a)
+    for l, lv in enumerate(levels):
+        ctx_b.mq_eval_level_device(l, 0, lv.N, None, None)
+    ctx_a.mq_reset_sums()
+    ctx_b.mq_reset_sums()
+    ctx_a.mq_eval_levels_device([0, 1, 2], out_a, sum_a)
+    for l, lv in enumerate(levels):
+        out_b = torch.empty((lv.R, lv.N, 4), dtype=torch.float64, device="cuda")
+        sum_b = torch.empty(lv.R, dtype=torch.float64, device="cuda")
+        ctx_b.mq_eval_level_device(l, 0, lv.N, out_b, sum_b)
+        assert torch.equal(out_a[l], out_b)
+        assert torch.equal(sum_a[l], sum_b)
+    ma, sa, _, _ = ctx_a.mq_estimate()
+    mb, sb, _, _ = ctx_b.mq_estimate()
+    assert ma == mb and sa == sb
+    assert ctx_a.mq_get_launch_count() == ctx_b.mq_get_launch_count()
+    # a second call reuses the internal contexts; a setter rebuilds them
+    ctx_a.mq_eval_levels_device([2, 0], [out_a[2], out_a[0]], None)
+    ctx_a.mq_set_tier(0)
+    ctx_a.mq_eval_levels_device([1], [out_a[1]], None)
+    with pytest.raises(B.MQError) as e:
+        ctx_a.mq_eval_levels_device([1, 1], None, None)
+    assert e.value.status == B.MQ_EINVAL
