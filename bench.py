@@ -309,7 +309,7 @@ def stream_bytes(wl, level, st, prec):
 
 # ncu DRAM traffic of the per-sample kernel's launch on a level, valid only for the kernel source
 # it was measured on (profiles/sample_kernel_mlqmc4_h16_128_level0.md; one full-size launch)
-SAMPLE_KERNEL_TRAFFIC = {"source_sha256": "018b22b84c84152daa9202de9f9d8662624b3d90215e11de6d8fba0a1b718246",
+SAMPLE_KERNEL_TRAFFIC = {"source_sha256": "791d7924fa2407f6eea81a737e089e28f1241c8f39d9566d110871fd16aa792c",
                          "level": 0, "precision": "mixed", "bytes_per_launch": 366.075648e6 + 27.624704e6}
 
 
