@@ -49,6 +49,29 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(ms, world, device="cuda"):
+    """The slowest rank's time: the whole job ends when its last rank does."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(samples_per_rank, world, steps, ms):
+    """Samples per second of all ranks together (weak scaling: every rank evaluates its own
+    shifts of the full workload)."""
+    return samples_per_rank * world * steps / (ms / 1e3)
+
+
+def shard_seed(seed, rank):
+    """Rank r draws the shifts of its shard from seed + r (rank 0: the workload's own shifts)."""
+    return seed + rank
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -109,7 +132,7 @@ def setup_context(binding, wl, stream_ptr, prec, seed_offset=0):
     ctx.mq_set_coefficient(wl.a0, max(lv.s for lv in wl.levels), 0, wl.decay)
     ctx.mq_set_levels(wl.levels)
     zs = [binding.mq_cbc_lattice(lv.N, lv.s, wl.decay) for lv in wl.levels]
-    ds = shifts(wl.seed + seed_offset, wl.levels)
+    ds = shifts(shard_seed(wl.seed, seed_offset), wl.levels)
     for l in range(len(wl.levels)):
         ctx.mq_set_lattice(l, zs[l])
         ctx.mq_set_shifts(l, ds[l])
@@ -396,11 +419,9 @@ def main():
                                                                   args.warmup, stream, seed_offset=rank,
                                                                   sequential=args.schedule == "sequential")
     if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    samples_per_step = wl.samples * world
-    value = samples_per_step * args.steps / (ms / 1e3)
+        torch.distributed.barrier()
+    ms = max_over_ranks(ms, world, "cuda")
+    value = whole_job_rate(wl.samples, world, args.steps, ms)
     plain = None
     if not args.no_plain and args.precision == "mixed" and rank == 0:
         ctxp, msp, _, _, _, _ = time_device(binding, torch, wl, "fp64", 1, 1, stream,
