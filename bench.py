@@ -67,6 +67,18 @@ def whole_job_rate(samples_per_rank, world, steps, ms):
     return samples_per_rank * world * steps / (ms / 1e3)
 
 
+def fine_dof_solves(wl):
+    """Fine unknowns solved per step: every sample of level l solves on mesh h_l and, for l > 0, on
+    h_{l-1} (direct levels count their eigensolve's unknowns once)."""
+    tot = 0
+    for l, lv in enumerate(wl.levels):
+        per = (lv.n_fine - 1) ** 2
+        if l > 0:
+            per += (wl.levels[l - 1].n_fine - 1) ** 2
+        tot += lv.N * lv.R * per
+    return tot
+
+
 def shard_seed(seed, rank):
     """Rank r draws the shifts of its shard from seed + r (rank 0: the workload's own shifts)."""
     return seed + rank
@@ -422,6 +434,7 @@ def main():
         torch.distributed.barrier()
     ms = max_over_ranks(ms, world, "cuda")
     value = whole_job_rate(wl.samples, world, args.steps, ms)
+    dof_rate = whole_job_rate(fine_dof_solves(wl), world, args.steps, ms)
     plain = None
     if not args.no_plain and args.precision == "mixed" and rank == 0:
         ctxp, msp, _, _, _, _ = time_device(binding, torch, wl, "fp64", 1, 1, stream,
@@ -462,6 +475,7 @@ def main():
                        "blocks": lst[l]["blocks"], "threads": lst[l]["threads"], "smem": lst[l]["smem_bytes"],
                        "workspace": lst[l]["workspace_bytes"]} for l in range(len(wl.levels))],
         "plain_fp64": plain,
+        "fine_dof_solves_per_s": dof_rate,
         "gpu_launches_note": "kernels launched in the timed region, counted by the library",
     }
     if rank == 0 and not args.no_baseline:

@@ -59,3 +59,12 @@ def test_bench_reference_arm_prints_the_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert d["config"]["workload"] == "qmc_h16_s16"
+
+
+def test_fine_dof_solves_counts_both_meshes_of_a_level():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    wl = WORKLOADS["mlqmc4_h16_128"]
+    # 4096*16*15^2 + 2048*16*(31^2+15^2) + 1024*16*(63^2+31^2) + 512*16*(127^2+63^2)
+    assert bench.fine_dof_solves(wl) == 65536 * 225 + 32768 * 1186 + 16384 * 4930 + 8192 * 20098
