@@ -141,7 +141,7 @@ class ClockSampler:
 # ------------------------------------------------------------------------------------------
 def setup_context(binding, wl, stream_ptr, prec, seed_offset=0):
     ctx = binding.Context(0, stream_ptr)
-    ctx.mq_set_coefficient(wl.a0, max(lv.s for lv in wl.levels), 0, wl.decay)
+    ctx.mq_set_coefficient(wl.a0, max(lv.s for lv in wl.levels), wl.family, wl.decay)
     ctx.mq_set_levels(wl.levels)
     zs = [binding.mq_cbc_lattice(lv.N, lv.s, wl.decay) for lv in wl.levels]
     ds = shifts(shard_seed(wl.seed, seed_offset), wl.levels)
@@ -223,9 +223,9 @@ def _oracle_sample(args):
     _os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
     from oracle import mlqmc
 
-    lv, pv, z, delta_row, k = args
+    lv, pv, z, delta_row, k, coef = args
     t = time.perf_counter()
-    mlqmc.level_samples(lv, pv, z, delta_row[None, :], [k])
+    mlqmc.level_samples(lv, pv, z, delta_row[None, :], [k], *coef)
     return time.perf_counter() - t
 
 
@@ -235,6 +235,7 @@ def cpu_baseline(wl, seconds_budget, zs, ds):
     import multiprocessing as mp
 
     cores = os.cpu_count() or 1
+    coef = (wl.a0, wl.decay, wl.family)
     ctx = mp.get_context("spawn")
     per_level = []
     total_t = 0.0
@@ -242,18 +243,18 @@ def cpu_baseline(wl, seconds_budget, zs, ds):
         # one warm sample per level (imports, caches), then a timed batch per level
         for l, lv in enumerate(wl.levels):
             pv = wl.levels[l - 1] if l > 0 else None
-            pool.map(_oracle_sample, [(lv, pv, zs[l], ds[l][0], 0)] * cores)
+            pool.map(_oracle_sample, [(lv, pv, zs[l], ds[l][0], 0, coef)] * cores)
         budget_per_level = seconds_budget / len(wl.levels)
         for l, lv in enumerate(wl.levels):
             pv = wl.levels[l - 1] if l > 0 else None
             # probe the per-sample cost with one wave, then size the timed wave
             t0 = time.perf_counter()
-            pool.map(_oracle_sample, [(lv, pv, zs[l], ds[l][i % lv.R], i) for i in range(cores)])
+            pool.map(_oracle_sample, [(lv, pv, zs[l], ds[l][i % lv.R], i, coef) for i in range(cores)])
             wave = time.perf_counter() - t0
             waves = max(1, int(budget_per_level / max(wave, 1e-3)))
             n = waves * cores
             t0 = time.perf_counter()
-            pool.map(_oracle_sample, [(lv, pv, zs[l], ds[l][i % lv.R], (i * 7) % lv.N) for i in range(n)])
+            pool.map(_oracle_sample, [(lv, pv, zs[l], ds[l][i % lv.R], (i * 7) % lv.N, coef) for i in range(n)])
             dt = time.perf_counter() - t0
             per_level.append((n, dt))
             total_t += dt

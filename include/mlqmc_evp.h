@@ -88,8 +88,10 @@ mq_status mq_create(mq_ctx** out, int device, void* cuda_stream);
 mq_status mq_destroy(mq_ctx* ctx);
 
 /* Coefficient a(x, y) = a0 + sum_{j<=s} y_j psi_j(x) (Sec. 2, eq. coeff; truncated as in
- * eq. coeff_s).  family 0: psi_j(x) = j^-decay sin(pi k1_j x1) sin(pi k2_j x2) with (k1, k2)
- * the j-th pair with k1, k2 >= 1 ordered by k1^2 + k2^2, ties by smaller k1.  s_max bounds the
+ * eq. coeff_s), psi_j(x) = j^-decay sin(pi k1_j x1) sin(pi k2_j x2).  family 0: (k1, k2) the
+ * j-th pair with k1, k2 >= 1 ordered by k1^2 + k2^2, ties by smaller k1; family 1: (j, j+1), the
+ * first test problem of Sec. 5 (decay p~ = 4/3, 2 or 3 there; a0 = pi / sqrt(2) keeps a > 0 for
+ * p~ = 4/3).  Other families give MQ_EINVAL.  s_max bounds the
  * truncation of every level.  a0 > 0.  Requires a >= a_min > 0 at all centroids (checked per
  * evaluation: a non-positive value gives MQ_EINVAL). */
 mq_status mq_set_coefficient(mq_ctx* ctx, double a0, int32_t s_max, int32_t family, double decay);

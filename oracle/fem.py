@@ -59,11 +59,17 @@ def centroids(n: int) -> np.ndarray:
     return coords[tris].mean(axis=1)
 
 
-def psi_pairs(s: int):
-    """Frequency pairs (k1, k2) of the first s terms of the synthetic coefficient family.
+def psi_pairs(s: int, family: int = 0):
+    """Frequency pairs (k1, k2) of the first s terms of a coefficient family.
 
-    All pairs with k1, k2 >= 1 ordered by k1^2 + k2^2, ties broken by smaller k1.
+    family 0 (the synthetic workload family): all pairs with k1, k2 >= 1 ordered by
+    k1^2 + k2^2, ties broken by smaller k1.  family 1 (the paper's first test problem, Sec. 5):
+    psi_j uses sin(j pi x1) sin((j+1) pi x2), i.e. (k1, k2) = (j, j+1).
     """
+    if family == 1:
+        return [(j, j + 1) for j in range(1, s + 1)]
+    if family != 0:
+        raise ValueError(f"unknown coefficient family {family}")
     K = int(np.ceil(2.0 * np.sqrt(max(s, 1)))) + 2
     pairs = [(k1, k2) for k1 in range(1, K + 1) for k2 in range(1, K + 1)]
     pairs.sort(key=lambda p: (p[0] ** 2 + p[1] ** 2, p[0]))
@@ -73,24 +79,24 @@ def psi_pairs(s: int):
 _PSI_CACHE: dict = {}
 
 
-def psi_matrix(n: int, s: int, decay: float = 2.0) -> np.ndarray:
+def psi_matrix(n: int, s: int, decay: float = 2.0, family: int = 0) -> np.ndarray:
     """Psi[t, j-1] = psi_j(c_t) = j^-decay sin(pi k1_j x1) sin(pi k2_j x2) at triangle centroids
-    (cached per mesh, truncation and decay; callers must not modify the result)."""
-    key = (n, s, decay)
+    (cached per mesh, truncation, decay and family; callers must not modify the result)."""
+    key = (n, s, decay, family)
     if key not in _PSI_CACHE:
-        _PSI_CACHE[key] = _psi_matrix(n, s, decay)
+        _PSI_CACHE[key] = _psi_matrix(n, s, decay, family)
     return _PSI_CACHE[key]
 
 
-def _psi_matrix(n: int, s: int, decay: float) -> np.ndarray:
+def _psi_matrix(n: int, s: int, decay: float, family: int = 0) -> np.ndarray:
     c = centroids(n)
     out = np.zeros((c.shape[0], s))
-    for j, (k1, k2) in enumerate(psi_pairs(s), start=1):
+    for j, (k1, k2) in enumerate(psi_pairs(s, family), start=1):
         out[:, j - 1] = j ** (-decay) * np.sin(np.pi * k1 * c[:, 0]) * np.sin(np.pi * k2 * c[:, 1])
     return out
 
 
-def coefficient(n: int, y: np.ndarray, a0: float = 1.0, decay: float = 2.0) -> np.ndarray:
+def coefficient(n: int, y: np.ndarray, a0: float = 1.0, decay: float = 2.0, family: int = 0) -> np.ndarray:
     """a(c_t, y) = a0 + sum_{j<=s} y_j psi_j(c_t) for every triangle t (eq. coeff, eq. coeff_s).
 
     The truncation dimension is len(y): terms beyond it are zero.  Small meshes use the cached
@@ -100,13 +106,13 @@ def coefficient(n: int, y: np.ndarray, a0: float = 1.0, decay: float = 2.0) -> n
     if y.size == 0:
         return np.full(2 * n * n, float(a0))
     if y.size * 2 * n * n <= (1 << 25):
-        return a0 + psi_matrix(n, y.size, decay) @ y
+        return a0 + psi_matrix(n, y.size, decay, family) @ y
     c = centroids(n)
     a = np.full(c.shape[0], float(a0))
     # sin(pi k x) only depends on k and on the 2n distinct centroid abscissae (ordinates)
     xs, xi = np.unique(c[:, 0], return_inverse=True)
     ys, yi = np.unique(c[:, 1], return_inverse=True)
-    for j, (k1, k2) in enumerate(psi_pairs(y.size), start=1):
+    for j, (k1, k2) in enumerate(psi_pairs(y.size, family), start=1):
         a += y[j - 1] * j ** (-decay) * np.sin(np.pi * k1 * xs)[xi] * np.sin(np.pi * k2 * ys)[yi]
     return a
 

@@ -26,26 +26,28 @@ import numpy as np
 from . import lattice, twogrid
 
 
-def sample_level(level, prev, y, a0: float = 1.0, decay: float = 2.0):
+def sample_level(level, prev, y, a0: float = 1.0, decay: float = 2.0, family: int = 0):
     """(lambda_H, lambda^l, lambda^{l-1}, difference) for one parameter vector y (len >= s_l).
 
     ``level`` and ``prev`` carry n_fine, n_coarse, s, S (``prev`` is None on level 0).
     """
-    lam_H, u_H = twogrid.coarse_pair(level.n_coarse, y[: level.S], a0, decay)
+    lam_H, u_H = twogrid.coarse_pair(level.n_coarse, y[: level.S], a0, decay, family)
     if level.n_fine == level.n_coarse and level.s == level.S:
         lam_l = lam_H
     else:
-        lam_l = twogrid.twogrid_update(level.n_fine, y[: level.s], lam_H, u_H, level.n_coarse, a0, decay)
+        lam_l = twogrid.twogrid_update(level.n_fine, y[: level.s], lam_H, u_H, level.n_coarse, a0, decay,
+                                       family=family)
     if prev is None:
         return lam_H, lam_l, 0.0, lam_l
     if prev.n_fine == level.n_coarse and prev.s == level.S:
         lam_p = lam_H
     else:
-        lam_p = twogrid.twogrid_update(prev.n_fine, y[: prev.s], lam_H, u_H, level.n_coarse, a0, decay)
+        lam_p = twogrid.twogrid_update(prev.n_fine, y[: prev.s], lam_H, u_H, level.n_coarse, a0, decay,
+                                       family=family)
     return lam_H, lam_l, lam_p, lam_l - lam_p
 
 
-def level_samples(level, prev, z, delta, ks, a0: float = 1.0, decay: float = 2.0) -> np.ndarray:
+def level_samples(level, prev, z, delta, ks, a0: float = 1.0, decay: float = 2.0, family: int = 0) -> np.ndarray:
     """Per-sample results [R, len(ks), 4] = (lambda_H, lambda^l, lambda^{l-1}, diff) at lattice
     indices ks for every shift row of ``delta`` [R, s_l]."""
     delta = np.atleast_2d(delta)
@@ -53,7 +55,7 @@ def level_samples(level, prev, z, delta, ks, a0: float = 1.0, decay: float = 2.0
     for r in range(delta.shape[0]):
         Y = lattice.points(z, level.N, delta[r], ks)
         for i in range(len(ks)):
-            out[r, i] = sample_level(level, prev, Y[i], a0, decay)
+            out[r, i] = sample_level(level, prev, Y[i], a0, decay, family)
     return out
 
 

@@ -91,18 +91,18 @@ def interpolate(u_coarse: np.ndarray, n_coarse: int, n_fine: int) -> np.ndarray:
     return interpolation_matrix(n_coarse, n_fine) @ u_coarse
 
 
-def coarse_pair(n_coarse: int, y_coarse: np.ndarray, a0: float = 1.0, decay: float = 2.0):
+def coarse_pair(n_coarse: int, y_coarse: np.ndarray, a0: float = 1.0, decay: float = 2.0, family: int = 0):
     """Step 1 of Algorithm 1: the smallest eigenpair on the coarse mesh with S terms."""
-    a = fem.coefficient(n_coarse, y_coarse, a0, decay)
+    a = fem.coefficient(n_coarse, y_coarse, a0, decay, family)
     A = fem.stiffness(n_coarse, a)
     M = fem.mass(n_coarse)
     return smallest_eigpair(A, M)
 
 
 def twogrid_update(n_fine: int, y_fine: np.ndarray, lam_H: float, u_H: np.ndarray, n_coarse: int,
-                   a0: float = 1.0, decay: float = 2.0, return_vector: bool = False):
+                   a0: float = 1.0, decay: float = 2.0, return_vector: bool = False, family: int = 0):
     """Steps 2-4 of Algorithm 1 for a given coarse pair: one shifted solve and a Rayleigh quotient."""
-    a = fem.coefficient(n_fine, y_fine, a0, decay)
+    a = fem.coefficient(n_fine, y_fine, a0, decay, family)
     A = fem.stiffness(n_fine, a)
     M = fem.mass(n_fine)
     if n_fine == n_coarse:
@@ -123,16 +123,16 @@ def twogrid_update(n_fine: int, y_fine: np.ndarray, lam_H: float, u_H: np.ndarra
 
 
 def twogrid(n_fine: int, s: int, n_coarse: int, S: int, y: np.ndarray, a0: float = 1.0,
-            decay: float = 2.0) -> float:
+            decay: float = 2.0, family: int = 0) -> float:
     """Algorithm 1 for one parameter vector y (len(y) >= s >= S).  Degenerate H = h, S = s:
     the coarse eigenvalue itself."""
-    lam_H, u_H = coarse_pair(n_coarse, y[:S], a0, decay)
+    lam_H, u_H = coarse_pair(n_coarse, y[:S], a0, decay, family)
     if n_fine == n_coarse and s == S:
         return lam_H
-    return twogrid_update(n_fine, y[:s], lam_H, u_H, n_coarse, a0, decay)
+    return twogrid_update(n_fine, y[:s], lam_H, u_H, n_coarse, a0, decay, family=family)
 
 
-def fine_eigenvalue(n: int, y: np.ndarray, a0: float = 1.0, decay: float = 2.0) -> float:
+def fine_eigenvalue(n: int, y: np.ndarray, a0: float = 1.0, decay: float = 2.0, family: int = 0) -> float:
     """lambda_{h,s}(y): the smallest FE eigenvalue on mesh 1/n with s = len(y) terms."""
-    a = fem.coefficient(n, y, a0, decay)
+    a = fem.coefficient(n, y, a0, decay, family)
     return smallest_eigpair(fem.stiffness(n, a), fem.mass(n))[0]

@@ -117,7 +117,19 @@ mq_status grow(mq_ctx* c, DevBuf& b, size_t bytes) {
 bool pow2(int n) { return n >= 1 && (n & (n - 1)) == 0; }
 
 // frequency pairs of the synthetic family: k1, k2 >= 1 ordered by k1^2 + k2^2, then k1
-void psi_pairs(int s, std::vector<int>& k1, std::vector<int>& k2) {
+// Wave numbers (k1, k2) of the first s terms psi_j ~ sin(pi k1 x1) sin(pi k2 x2) of a family:
+// 0: all pairs k1, k2 >= 1 ordered by k1^2 + k2^2, ties by smaller k1 (the workload family);
+// 1: (j, j+1), the first test problem of Sec. 5.
+void psi_pairs(int s, int family, std::vector<int>& k1, std::vector<int>& k2) {
+  if (family == 1) {
+    k1.resize(s);
+    k2.resize(s);
+    for (int j = 0; j < s; ++j) {
+      k1[j] = j + 1;
+      k2[j] = j + 2;
+    }
+    return;
+  }
   const int K = (int)std::ceil(2.0 * std::sqrt((double)std::max(s, 1))) + 2;
   std::vector<std::pair<int, int>> pr;
   for (int a = 1; a <= K; ++a)
@@ -660,11 +672,11 @@ mq_status mq_set_coefficient(mq_ctx* c, double a0, int32_t s_max, int32_t family
   c->lanes_stale = true;
   if (!(a0 > 0.0) || !std::isfinite(a0)) return fail(c, MQ_EINVAL, "a0 must be positive, got %g", a0);
   if (s_max < 0 || s_max > 65536) return fail(c, MQ_EINVAL, "s_max %d out of range", s_max);
-  if (family != 0) return fail(c, MQ_EINVAL, "unknown coefficient family %d", family);
+  if (family != 0 && family != 1) return fail(c, MQ_EINVAL, "unknown coefficient family %d", family);
   if (!std::isfinite(decay)) return fail(c, MQ_EINVAL, "decay must be finite");
   MQ_CUDA(c, cudaSetDevice(c->device));
   std::vector<int> k1, k2;
-  psi_pairs(std::max(s_max, 1), k1, k2);
+  psi_pairs(std::max(s_max, 1), family, k1, k2);
   std::vector<double> cj(std::max(s_max, 1));
   for (int j = 0; j < (int)cj.size(); ++j) cj[j] = std::pow((double)(j + 1), -decay);
   for (auto& kv : c->psi) cudaFree(kv.second.second);

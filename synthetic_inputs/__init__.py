@@ -42,6 +42,7 @@ class Workload:
     tol: float  # relative tolerance on each per-sample eigenvalue versus the oracle
     a0: float = 1.0
     decay: float = 2.0
+    family: int = 0  # 0: the workload sine family; 1: the paper's first test problem (Sec. 5)
     notes: str = ""
     extra: dict = field(default_factory=dict)
 
@@ -89,6 +90,14 @@ WORKLOADS = {
         [Level(32, 32, 32, 32, 16384, 16)]
         + [Level(32 << l, 32, 32 << l, _ceil_sqrt(32 << l), 16384 >> l, 16) for l in range(1, 6)],
         seed=3, precision="mixed", tol=1e-7,
+    ),
+    # the paper's first test problem (Sec. 5): psi_j = j^-p sin(j pi x1) sin((j+1) pi x2) with
+    # p = 4/3 and a0 = pi / sqrt(2), s = 64 terms, S = 8, H = 1/8, h_l = 2^-(l+3) (level 0 direct),
+    # R = 8 shifts; point counts halve level by level
+    "paper_p1_h8_64": Workload(
+        "paper_p1_h8_64",
+        [Level(8, 8, 64, 64, 2048, 8)] + [Level(8 << l, 8, 64, _ceil_sqrt(64), 2048 >> l, 8) for l in range(1, 4)],
+        seed=5, precision="mixed", tol=1e-10, a0=float(np.pi / np.sqrt(2.0)), decay=4.0 / 3.0, family=1,
     ),
     # h = 1/1024 (1,046,529 dofs), H = 1/64, s = 1024, S = 32, 32 points x 16 shifts
     "stress_h1024_s1024": Workload(

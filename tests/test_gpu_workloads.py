@@ -24,7 +24,7 @@ def B():
 
 def setup(B, wl):
     ctx = B.Context(0)
-    ctx.mq_set_coefficient(wl.a0, max(lv.s for lv in wl.levels), 0, wl.decay)
+    ctx.mq_set_coefficient(wl.a0, max(lv.s for lv in wl.levels), wl.family, wl.decay)
     ctx.mq_set_levels(wl.levels)
     zs = [lattice.cbc(lv.N, lv.s, wl.decay) for lv in wl.levels]
     ds = shifts(wl.seed, wl.levels)
@@ -39,7 +39,7 @@ def check_samples(wl, l, ps, zs, ds, picks):
     lv = wl.levels[l]
     pv = wl.levels[l - 1] if l > 0 else None
     for r, k in picks:
-        ref = mlqmc.level_samples(lv, pv, zs[l], ds[l][r : r + 1], [k])[0, 0]
+        ref = mlqmc.level_samples(lv, pv, zs[l], ds[l][r : r + 1], [k], wl.a0, wl.decay, wl.family)[0, 0]
         got = ps[r, k]
         assert got[0] == pytest.approx(ref[0], rel=1e-12), (l, r, k)
         assert got[1] == pytest.approx(ref[1], rel=wl.tol), (l, r, k)

@@ -211,3 +211,52 @@ def test_coefficient_large_mesh_path_matches_matrix_path():
     a_terms = fem.coefficient(n, y)  # 2 n^2 s > 2^25: term by term
     a_matrix = 1.0 + fem._psi_matrix(n, s, 2.0) @ y
     assert np.abs(a_terms - a_matrix).max() < 1e-13
+
+
+# ---- the paper's first test problem (Sec. 5): psi_j = j^-p sin(j pi x1) sin((j+1) pi x2)
+def test_family1_pairs():
+    assert fem.psi_pairs(5, family=1) == [(1, 2), (2, 3), (3, 4), (4, 5), (5, 6)]
+    with pytest.raises(ValueError):
+        fem.psi_pairs(3, family=7)
+
+
+@pytest.mark.parametrize("j", [1, 2, 5])
+def test_family1_term_has_wave_numbers_j_and_j_plus_1(j):
+    # centroid rule of psi_j * sin(j pi x1) sin((j+1) pi x2): with equal wave numbers in each
+    # direction the moment is j^-p / 4 (the rule is exact for these products: the centroids sit
+    # symmetrically in every cell); with the wave numbers swapped the integrand's integral is zero
+    # and the rule's value vanishes as the mesh is refined
+    p = 4.0 / 3.0
+    sw = []
+    for n in (32, 64):
+        c = fem.centroids(n)
+        area = 0.5 / n ** 2
+        Psi = fem.psi_matrix(n, j, p, family=1)[:, j - 1]
+        probe = np.sin(j * np.pi * c[:, 0]) * np.sin((j + 1) * np.pi * c[:, 1])
+        swapped = np.sin((j + 1) * np.pi * c[:, 0]) * np.sin(j * np.pi * c[:, 1])
+        assert abs(area * Psi @ probe - j ** (-p) / 4) < 1e-14
+        sw.append(abs(area * Psi @ swapped))
+    assert sw[1] < 1e-8 * j ** (-p) and sw[1] < sw[0] / 4
+
+
+def test_family1_coefficient_bound_and_positivity():
+    p, a0, n, s = 4.0 / 3.0, np.pi / np.sqrt(2.0), 16, 64
+    bound = 0.5 * sum(j ** (-p) for j in range(1, s + 1))
+    for yy in random_points(21, 4, s):
+        a = fem.coefficient(n, yy, a0, p, family=1)
+        assert np.all(np.abs(a - a0) <= bound + 1e-14)
+        assert a.min() > 0
+    # the extreme parameter y = -1/2 sign(psi_j) stays positive for a0 = pi / sqrt(2)
+    assert a0 - bound > 0.7
+
+
+def test_family1_two_grid_between_fine_and_coarse_eigenvalues():
+    p, a0 = 4.0 / 3.0, np.pi / np.sqrt(2.0)
+    y = random_points(23, 1, 64)[0]
+    lam_h = twogrid.fine_eigenvalue(32, y, a0, p, family=1)
+    lam_H = twogrid.coarse_pair(8, y[:8], a0, p, family=1)[0]
+    lam_tg = twogrid.twogrid(32, 64, 8, 8, y, a0, p, family=1)
+    # the two-grid value is a Rayleigh quotient (>= lambda_h) and far closer to lambda_h than the
+    # coarse eigenvalue is
+    assert lam_tg >= lam_h - 1e-12 * lam_h
+    assert abs(lam_tg - lam_h) < 0.1 * abs(lam_H - lam_h)
