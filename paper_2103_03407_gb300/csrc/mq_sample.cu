@@ -106,14 +106,19 @@ __host__ __device__ size_t fine_bytes(int n) {
   return (f.used() + 15) & ~(size_t)15;
 }
 
-// workspace of one CTA: the coarse region plus the largest fine solve it performs in place
-// (mode 0: inner precision T, mode 1: FP64 inner solve, 2: not in this kernel)
+// workspace of one CTA: the persistent head, then the larger of the rest of the coarse region
+// and the largest fine solve it performs in place (mode 0: inner precision T, mode 1: FP64 inner
+// solve, 2: not in this kernel).  A multiple of 256 bytes: the slabs of a global scratch lie back
+// to back, so every slab then starts as aligned as the scratch itself and the kernel carves it
+// exactly as sized here (an unaligned slab start would shift its arrays by up to 15 bytes into
+// the next slab).
 template <typename T>
 __host__ __device__ size_t slab_size(int nf, int nc, int np, int mode_f = 0, int mode_p = 0) {
   Carver c(nullptr);
   CoarseWS cw;
   size_t persist = 0;
   carve_coarse(c, nc, cw, &persist);
+  persist = (persist + 15) & ~(size_t)15;  // the fine region starts 16-byte aligned
   const size_t coarse = (c.used() + 15) & ~(size_t)15;
   auto need = [&](int n, int mode) -> size_t {
     if (mode == 2) return 0;
@@ -123,7 +128,7 @@ __host__ __device__ size_t slab_size(int nf, int nc, int np, int mode_f = 0, int
   const size_t a = need(nf, mode_f), b = need(np, mode_p);
   if (a > m) m = a;
   if (b > m) m = b;
-  return persist + m;
+  return (persist + m + 255) & ~(size_t)255;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -722,7 +727,7 @@ __global__ void __launch_bounds__(512) sample_kernel(SampleLaunch P) {
     carve_coarse(c, P.nc, tmp, &persist_bytes);
     if (threadIdx.x == 0) cws = tmp;
   }
-  char* fine_base = base + persist_bytes;  // the fine workspace overlays the coarse one
+  char* fine_base = base + ((persist_bytes + 15) & ~(size_t)15);  // the fine workspace overlays the coarse one
   __syncthreads();
   const int nc = P.nc;
   const int cpr = (P.npts + P.chunk - 1) / P.chunk;
