@@ -345,7 +345,7 @@ def stream_bytes(wl, level, st, prec):
 
 # ncu DRAM traffic of the per-sample kernel's launch on a level, valid only for the kernel source
 # it was measured on (profiles/sample_kernel_mlqmc4_h16_128_level0.md; one full-size launch)
-SAMPLE_KERNEL_TRAFFIC = {"source_sha256": "791d7924fa2407f6eea81a737e089e28f1241c8f39d9566d110871fd16aa792c",
+SAMPLE_KERNEL_TRAFFIC = {"source_sha256": "ea104697312beb4c1049dd2e4748a39fb69098d045db313210a6548ea7eab8d1",
                          "level": 0, "precision": "mixed", "bytes_per_launch": 366.075648e6 + 27.624704e6}
 
 
