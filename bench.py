@@ -28,7 +28,14 @@ sys.path.insert(0, ROOT)
 from synthetic_inputs import WORKLOADS, shifts  # noqa: E402
 
 METRIC = "two-grid eigen-samples/s at rel. err<=1e-10 vs FP64 oracle; mixed vs plain GPU"
-DEFAULT_WORKLOAD = "mlqmc4_h16_128"
+# the largest workload that fits one GPU: six levels, meshes 1/32 .. 1/1024, 516,096 samples
+DEFAULT_WORKLOAD = "mlqmc6_h32_1024"
+# One step evaluates the fraction 1/F of every level's lattice points (all shifts): step i takes the
+# window i mod F of each level, so F consecutive steps cover the whole workload once.  The six-level
+# workload takes tens of seconds per full pass; 1/32 of it keeps a bench run within minutes while
+# every level still streams at full occupancy (its finest level: 16 points x 16 shifts of 1,046,529
+# unknowns per step).
+STEP_FRACTION = {"mlqmc6_h32_1024": 32}
 
 
 def parse():
@@ -43,6 +50,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison run")
     ap.add_argument("--baseline-seconds", type=float, default=20.0)
+    ap.add_argument("--fraction", type=int, default=0,
+                    help="evaluate 1/F of every level's points per step (0: the workload's default)")
     ap.add_argument("--schedule", default="sequential", choices=["concurrent", "sequential"],
                     help="levels one after another (clean per-kernel timing for the rooflines), or all "
                          "at once on their own streams (mq_eval_levels_device)")
@@ -152,62 +161,92 @@ def setup_context(binding, wl, stream_ptr, prec, seed_offset=0):
     return ctx, zs, ds
 
 
-def run_device_step(ctx, wl, outs, sums, sequential=False):
+def step_fraction(wl, args):
+    return args.fraction if args.fraction > 0 else STEP_FRACTION.get(wl.name, 1)
+
+
+def windows(wl, F, step):
+    """Point range [k0, k1) of every level in step `step`: window step mod F of 1/F of the points."""
+    out = []
+    for lv in wl.levels:
+        n = max(1, lv.N // F)
+        w = step % max(1, lv.N // n)
+        out.append((w * n, w * n + n))
+    return out
+
+
+def step_samples(wl, F):
+    return sum(lv.R * (k1 - k0) for lv, (k0, k1) in zip(wl.levels, windows(wl, F, 0)))
+
+
+def run_device_step(ctx, wl, outs, sums, F, step, sequential=True):
     if sequential:
-        for l, lv in enumerate(wl.levels):
-            ctx.mq_eval_level_device(l, 0, lv.N, outs[l], sums[l])
+        for l, (k0, k1) in enumerate(windows(wl, F, step)):
+            ctx.mq_eval_level_device(l, k0, k1, outs[l], sums[l])
     else:  # all levels at once, each on its own stream (the library's concurrent schedule)
         ctx.mq_eval_levels_device(list(range(len(wl.levels))), outs, sums)
 
 
-def time_device(binding, torch, wl, prec, steps, warmup, stream, seed_offset=0, sequential=False):
+def time_device(binding, torch, wl, prec, steps, warmup, stream, F, seed_offset=0, sequential=True):
+    if not sequential and F != 1:
+        raise SystemExit("the concurrent schedule evaluates whole levels: use --fraction 1")
     ctx, zs, ds = setup_context(binding, wl, stream.cuda_stream, prec, seed_offset)
-    outs = [torch.empty((lv.R, lv.N, 4), dtype=torch.float64, device="cuda") for lv in wl.levels]
+    win = windows(wl, F, 0)
+    outs = [torch.empty((lv.R, k1 - k0, 4), dtype=torch.float64, device="cuda") for lv, (k0, k1) in zip(wl.levels, win)]
     sums = [torch.empty(lv.R, dtype=torch.float64, device="cuda") for lv in wl.levels]
-    for _ in range(warmup):
-        run_device_step(ctx, wl, outs, sums, sequential)
+    for i in range(warmup):
+        run_device_step(ctx, wl, outs, sums, F, i, sequential)
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ctx.mq_reset_sums()  # also clears the per-level device timers
     ev0.record(stream)
-    for _ in range(steps):
-        run_device_step(ctx, wl, outs, sums, sequential)
+    for i in range(steps):
+        run_device_step(ctx, wl, outs, sums, F, warmup + i, sequential)
     ev1.record(stream)
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
     # per-level device time of the timed region (CUDA events on the launching stream)
     timing = [ctx.mq_get_level_timing(l) + ctx.mq_get_kernel_timing(l) for l in range(len(wl.levels))]
     launches = ctx.mq_get_launch_count()
-    # iteration counts from one more (untimed, identical) pass
+    last = [o.cpu().numpy() for o in outs]  # per-sample results of the last timed step
+    # iteration counts from one more (untimed) pass over the last step's windows
     kstats = {}
-    for l, lv in enumerate(wl.levels):
-        ctx.mq_eval_level_device(l, 0, lv.N, outs[l], sums[l])
+    for l, (k0, k1) in enumerate(windows(wl, F, warmup + steps - 1)):
+        ctx.mq_eval_level_device(l, k0, k1, outs[l], sums[l])
         kstats[l] = [ctx.mq_get_stats()]
-    return ctx, ms, timing, kstats, outs, launches
+    return ctx, ms, timing, kstats, last, launches
 
 
-def time_e2e(binding, wl, prec, steps, stream_ptr):
+def max_rel_diff(a_levels, b_levels):
+    """Largest relative difference of lambda_H, lambda^l, lambda^{l-1} (each relative to itself)
+    and of the level difference (relative to lambda^l) between two runs' per-sample results."""
+    worst = 0.0
+    for a, b in zip(a_levels, b_levels):
+        den = np.abs(b[..., :3]) + (b[..., :3] == 0)
+        worst = max(worst, float((np.abs(a[..., :3] - b[..., :3]) / den).max()),
+                    float((np.abs(a[..., 3] - b[..., 3]) / np.abs(b[..., 1])).max()))
+    return worst
+
+
+def time_e2e(binding, wl, prec, steps, warmup, stream_ptr, F):
     """End to end through the public host API: every step uploads the lattices and shifts from
-    host memory and reads every per-sample result back."""
+    host memory, evaluates the step's windows and reads every per-sample result back."""
     import torch
 
     ctx, zs, ds = setup_context(binding, wl, stream_ptr, prec)
     h2d = sum(z.nbytes + d.nbytes for z, d in zip(zs, ds))
-    d2h = sum(lv.R * lv.N * 4 * 8 + lv.R * 8 for lv in wl.levels)
-    host_out = [np.zeros((lv.R, lv.N, 4)) for lv in wl.levels]
-    # one untimed pass
-    for l, lv in enumerate(wl.levels):
-        ctx.mq_eval_level(l, 0, lv.N)
+    d2h = sum(lv.R * (k1 - k0) * 4 * 8 + lv.R * 8 for lv, (k0, k1) in zip(wl.levels, windows(wl, F, 0)))
+    for l, (k0, k1) in enumerate(windows(wl, F, 0)):  # one untimed pass
+        ctx.mq_eval_level(l, k0, k1)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(steps):
+    for i in range(steps):
         ctx.mq_reset_sums()
-        for l, lv in enumerate(wl.levels):
+        for l, (k0, k1) in enumerate(windows(wl, F, warmup + i)):
             ctx.mq_set_lattice(l, zs[l])
             ctx.mq_set_shifts(l, ds[l])
-            ps, _ = ctx.mq_eval_level(l, 0, lv.N)
-            host_out[l] = ps
+            ctx.mq_eval_level(l, k0, k1)
         ctx.mq_estimate()
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
@@ -216,54 +255,24 @@ def time_e2e(binding, wl, prec, steps, stream_ptr):
 
 
 # ------------------------------------------------------------------------------------------
-def _oracle_sample(args):
+def _oracle_worker(args):
+    """Evaluates oracle samples of one level one after another until `budget` seconds have passed
+    (at least one sample); returns (samples, seconds)."""
     import os as _os
 
     _os.environ.setdefault("OMP_NUM_THREADS", "1")
     _os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
     from oracle import mlqmc
 
-    lv, pv, z, delta_row, k, coef = args
-    t = time.perf_counter()
-    mlqmc.level_samples(lv, pv, z, delta_row[None, :], [k], *coef)
-    return time.perf_counter() - t
-
-
-def cpu_baseline(wl, seconds_budget, zs, ds):
-    """Times the oracle as it stands on a bounded sample of every level (one sample per process,
-    all host cores) and scales to samples/s of the whole workload."""
-    import multiprocessing as mp
-
-    cores = os.cpu_count() or 1
-    coef = (wl.a0, wl.decay, wl.family)
-    ctx = mp.get_context("spawn")
-    per_level = []
-    total_t = 0.0
-    with ctx.Pool(cores, initializer=_pool_init) as pool:
-        # one warm sample per level (imports, caches), then a timed batch per level
-        for l, lv in enumerate(wl.levels):
-            pv = wl.levels[l - 1] if l > 0 else None
-            pool.map(_oracle_sample, [(lv, pv, zs[l], ds[l][0], 0, coef)] * cores)
-        budget_per_level = seconds_budget / len(wl.levels)
-        for l, lv in enumerate(wl.levels):
-            pv = wl.levels[l - 1] if l > 0 else None
-            # probe the per-sample cost with one wave, then size the timed wave
-            t0 = time.perf_counter()
-            pool.map(_oracle_sample, [(lv, pv, zs[l], ds[l][i % lv.R], i, coef) for i in range(cores)])
-            wave = time.perf_counter() - t0
-            waves = max(1, int(budget_per_level / max(wave, 1e-3)))
-            n = waves * cores
-            t0 = time.perf_counter()
-            pool.map(_oracle_sample, [(lv, pv, zs[l], ds[l][i % lv.R], (i * 7) % lv.N, coef) for i in range(n)])
-            dt = time.perf_counter() - t0
-            per_level.append((n, dt))
-            total_t += dt
-    # whole-workload time = sum over levels of (samples of the level / measured rate)
-    est = sum(lv.N * lv.R * dt / n for lv, (n, dt) in zip(wl.levels, per_level))
-    value = wl.samples / est
-    sample = "; ".join(f"level {l}: {n} samples in {dt:.1f} s" for l, (n, dt) in enumerate(per_level))
-    return {"value": value, "unit": "samples/s", "cores": cores, "kind": "oracle",
-            "sample": sample + f" (extrapolated to {wl.samples} samples by the per-level rates)"}
+    lv, pv, z, delta, ks, coef, budget = args
+    t0 = time.perf_counter()
+    n = 0
+    for i, k in enumerate(ks):
+        mlqmc.level_samples(lv, pv, z, delta[i % delta.shape[0]][None, :], [k], *coef)
+        n += 1
+        if time.perf_counter() - t0 >= budget:
+            break
+    return n, time.perf_counter() - t0
 
 
 def _pool_init():
@@ -271,8 +280,55 @@ def _pool_init():
     os.environ["OPENBLAS_NUM_THREADS"] = "1"
 
 
+def oracle_level_rates(wl, zs, ds, levels, budget, pool, cores):
+    """Per-sample oracle time of each listed level: the host cores are shared out among the levels
+    (the finest levels, whose single samples take longest, get one process each), every process
+    runs samples of its level until the budget is spent, all levels at once."""
+    procs = {l: 1 for l in levels}
+    spare = max(0, cores - len(levels))
+    cheap = [l for l in levels if wl.levels[l].n_fine <= 256] or list(levels)
+    for i in range(spare):
+        procs[cheap[i % len(cheap)]] += 1
+    jobs, owner = [], []
+    for l in levels:
+        lv = wl.levels[l]
+        pv = wl.levels[l - 1] if l > 0 else None
+        for p in range(procs[l]):
+            ks = [(p * 7919 + i * 104729) % lv.N for i in range(100000)]
+            jobs.append((lv, pv, zs[l], ds[l], ks, (wl.a0, wl.decay, wl.family), budget))
+            owner.append(l)
+    res = pool.map(_oracle_worker, jobs, chunksize=1)
+    per = {}
+    for l, (n, dt) in zip(owner, res):
+        c, t = per.get(l, (0, 0.0))
+        per[l] = (c + n, t + dt)
+    return {l: (n, dt) for l, (n, dt) in per.items()}
+
+
+def oracle_rate(wl, per_level, cores):
+    """Samples/s of the whole workload on `cores` processes from per-level (samples, seconds)."""
+    cpu_s = sum(lv.N * lv.R * per_level[l][1] / per_level[l][0] for l, lv in enumerate(wl.levels))
+    return wl.samples * cores / cpu_s
+
+
+def cpu_baseline(wl, seconds_budget, zs, ds):
+    """Times the oracle as it stands on a bounded sample of every level (all levels at once, one
+    sample per process at a time on every host core) and scales to samples/s of the workload."""
+    import multiprocessing as mp
+
+    cores = os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(cores, initializer=_pool_init) as pool:
+        per = oracle_level_rates(wl, zs, ds, list(range(len(wl.levels))), seconds_budget, pool, cores)
+    value = oracle_rate(wl, per, cores)
+    sample = "; ".join(f"level {l}: {n} samples in {dt:.1f} process-s" for l, (n, dt) in sorted(per.items()))
+    return {"value": value, "unit": "samples/s", "cores": cores, "kind": "oracle",
+            "sample": sample + f" (all levels at once on {cores} processes, first samples with cold per-process "
+                               f"caches; extrapolated to the {wl.samples} samples of the workload by the "
+                               f"per-level rates, {cores} samples at a time)"}
+
+
 # ------------------------------------------------------------------------------------------
-# Roofline models (derivations in the design doc, section 6).
+# Roofline models.
 #
 # Per-sample kernel (one CTA per sample, workspace on chip): bounded by the FP64 units, whose
 # peak is 152 SMs x 2 FP64 FMA lanes per cycle x 2 flops x the SM clock.  FP64 operations
@@ -292,8 +348,8 @@ def stream_min_default(prec):
     return 32 if prec == "mixed" else 256
 
 
-def percta_fp64_flops(wl, level, st, prec):
-    """FP64 operations of one launch of the per-sample kernel on `level` (all its samples)."""
+def percta_fp64_flops(wl, level, st, prec, samples):
+    """FP64 operations of one launch of the per-sample kernel on `level` over `samples` samples."""
     lv = wl.levels[level]
     nc = lv.n_coarse
     per = (nc - 1) ** 2 * (FP64_EIG_IT * st["coarse_iters_mean"] + FP64_EIG_CALL)
@@ -311,7 +367,7 @@ def percta_fp64_flops(wl, level, st, prec):
             continue  # batched streaming tier
         inner64 = prec == "fp64" or n == nc
         per += (n - 1) ** 2 * (FP64_FINE_SETUP + FP64_FINE_OUTER * O + (FP64_INNER * I if inner64 else 0))
-    return per * lv.N * lv.R
+    return per * samples
 
 
 # Streaming tier (fine meshes >= 1/32 mixed): bounded by HBM.  Bytes per fine unknown with every
@@ -325,7 +381,7 @@ def percta_fp64_flops(wl, level, st, prec):
 #   e + 16, FP64 residual with FP64 weights e + 32) + one V-cycle;
 #   per solve: 20 e + 72 bytes (clearing 8 e + 16, FP32 and FP64 weights 3 e + 32, interpolation
 #   and right-hand side e + 24, operators of the coarser levels ~8 e).
-def stream_bytes(wl, level, st, prec):
+def stream_bytes(wl, level, st, prec, samples):
     e = 4 if prec == "mixed" else 8
     lv = wl.levels[level]
     vcyc = 11.5 * e + 10.5 * e * (1 / 4 + 1 / 16)
@@ -340,7 +396,7 @@ def stream_bytes(wl, level, st, prec):
     per = 0.0
     for n in solves:
         per += (n - 1) ** 2 * ((14 * e + vcyc) * I + (12 * e + 48 + vcyc) * O + 20 * e + 72)
-    return per * lv.N * lv.R
+    return per * samples
 
 
 # ncu DRAM traffic of the per-sample kernel's launch on a level, valid only for the kernel source
@@ -376,8 +432,8 @@ def fp64_peak_tflops(sm_max_mhz=None):
     return 152 * 2 * 2 * mhz * 1e6 / 1e12
 
 
-def percta_roofline(wl, level, st, prec, ms_per_launch, sm_max_mhz):
-    flops = percta_fp64_flops(wl, level, st, prec)
+def percta_roofline(wl, level, st, prec, ms_per_launch, sm_max_mhz, samples):
+    flops = percta_fp64_flops(wl, level, st, prec, samples)
     achieved = flops / (ms_per_launch * 1e-3) / 1e12
     peak = fp64_peak_tflops(sm_max_mhz)
     lv = wl.levels[level]
@@ -387,19 +443,19 @@ def percta_roofline(wl, level, st, prec, ms_per_launch, sm_max_mhz):
         traffic = t["bytes_per_launch"]
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": traffic,
-            "kernel": f"sample_kernel (level {level}: {lv.N * lv.R} samples per launch, "
+            "kernel": f"sample_kernel (level {level}: {samples} samples per launch, "
                       f"{ms_per_launch:.2f} ms per launch)",
             "algorithmic_flops": flops,
             "peak_kind": f"derived: FP64 units, 152 SMs x 4 flop/cycle x {sm_max_mhz or 2070:.0f} MHz"}
 
 
-def stream_roofline(wl, level, st, prec, ms_per_launch):
-    nbytes = stream_bytes(wl, level, st, prec)
+def stream_roofline(wl, level, st, prec, ms_per_launch, samples):
+    nbytes = stream_bytes(wl, level, st, prec, samples)
     achieved = nbytes / (ms_per_launch * 1e-3) / 1e9
     peak, kind = hbm_peak()
     lv = wl.levels[level]
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "kernel": f"streaming fine solves (level {level}: {lv.N * lv.R} samples, "
+            "traffic": None, "kernel": f"streaming fine solves (level {level}: {samples} samples per pass, "
                                        f"{ms_per_launch:.2f} ms per pass, all kernels of the stage)",
             "algorithmic_bytes": nbytes, "peak_kind": kind}
 
@@ -426,26 +482,34 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    F = step_fraction(wl, args)
+    samples = step_samples(wl, F)  # samples per step (every level's window, every shift)
     with torch.cuda.stream(stream):
         with sampler:
             ctx, ms, timing, kstats, outs, launches = time_device(binding, torch, wl, args.precision, args.steps,
-                                                                  args.warmup, stream, seed_offset=rank,
+                                                                  args.warmup, stream, F, seed_offset=rank,
                                                                   sequential=args.schedule == "sequential")
     if world > 1:
         torch.distributed.barrier()
     ms = max_over_ranks(ms, world, "cuda")
-    value = whole_job_rate(wl.samples, world, args.steps, ms)
-    dof_rate = whole_job_rate(fine_dof_solves(wl), world, args.steps, ms)
+    value = whole_job_rate(samples, world, args.steps, ms)
+    dof_rate = whole_job_rate(fine_dof_solves(wl) / F, world, args.steps, ms)
     plain = None
     if not args.no_plain and args.precision == "mixed" and rank == 0:
-        ctxp, msp, _, _, _, _ = time_device(binding, torch, wl, "fp64", 1, 1, stream,
-                                            sequential=args.schedule == "sequential")
-        plain = {"value": wl.samples / (msp / 1e3), "unit": "samples/s", "ms_per_step": msp, "steps": 1}
+        # the plain FP64 GPU path on the same steps (same windows) and warm-up
+        with torch.cuda.stream(stream):
+            ctxp, msp, _, _, outs_p, _ = time_device(binding, torch, wl, "fp64", args.steps, args.warmup, stream, F,
+                                                     sequential=args.schedule == "sequential")
         ctxp.close()
+        plain = {"value": samples * args.steps / (msp / 1e3), "unit": "samples/s", "ms_per_step": msp / args.steps,
+                 "steps": args.steps, "warmup": args.warmup,
+                 "max_rel_diff_mixed_vs_fp64": max_rel_diff(outs, outs_p),
+                 "note": "per-sample results of the last timed step of both paths compared"}
     e2e = None
     if not args.no_e2e:
-        dt, h2d, d2h = time_e2e(binding, wl, args.precision, max(1, args.steps), stream.cuda_stream)
-        e2e = {"value": wl.samples * max(1, args.steps) / dt, "unit": "samples/s", "h2d_bytes_per_step": h2d,
+        steps_e2e = max(1, args.steps)
+        dt, h2d, d2h = time_e2e(binding, wl, args.precision, steps_e2e, args.warmup, stream.cuda_stream, F)
+        e2e = {"value": samples * steps_e2e / dt, "unit": "samples/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
     # dominant kernel: the per-sample kernel launch with the largest device time; the streaming
     # stage of the level where it takes longest is reported beside it
@@ -456,17 +520,21 @@ def main():
     sample_ms = [per(l, 1) for l in range(nl)]
     percta_ms = [per(l, 3) for l in range(nl)]
     stream_ms = [per(l, 4) for l in range(nl)]
+    win = windows(wl, F, 0)
+    # samples per launch: all samples a level evaluated in the timed region over its launches
+    per_launch = [wl.levels[l].R * (win[l][1] - win[l][0]) * args.steps / max(1, timing[l][2]) for l in range(nl)]
     clocks = sampler.summary()
     top = int(np.argmax(percta_ms))
-    roofline = percta_roofline(wl, top, lst[top], args.precision, percta_ms[top], clocks.get("sm_max_mhz"))
+    roofline = percta_roofline(wl, top, lst[top], args.precision, percta_ms[top], clocks.get("sm_max_mhz"),
+                               per_launch[top])
     stop = int(np.argmax(stream_ms))
-    roofline_stream = (stream_roofline(wl, stop, lst[stop], args.precision, stream_ms[stop])
+    roofline_stream = (stream_roofline(wl, stop, lst[stop], args.precision, stream_ms[stop], per_launch[stop])
                        if stream_ms[stop] > 0 else None)
     result = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
-        "config": dict(workload_config(wl, args.precision, world), schedule=args.schedule),
+        "config": dict(workload_config(wl, args.precision, world, F), schedule=args.schedule),
         "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "roofline_stream": roofline_stream,
         "clocks": clocks,
         "per_level": [{"level": l, "kernel_ms": coef_ms[l] + sample_ms[l], "coef_ms": coef_ms[l],
@@ -488,8 +556,13 @@ def main():
         torch.distributed.destroy_process_group()
 
 
-def workload_config(wl, precision, world):
-    return {"workload": wl.name, "levels": [lv.__dict__ for lv in wl.levels], "samples_per_step": wl.samples,
+def workload_config(wl, precision, world, F=1):
+    win = windows(wl, F, 0)
+    return {"workload": wl.name, "levels": [lv.__dict__ for lv in wl.levels], "samples_per_step": step_samples(wl, F),
+            "workload_samples": wl.samples,
+            "step": (f"1/{F} of every level's lattice points, all shifts: step i evaluates window i mod {F} "
+                     f"({', '.join(str(k1 - k0) for k0, k1 in win)} points per shift on levels 0..{len(win) - 1}); "
+                     f"{F} steps cover the workload once") if F > 1 else "every point of every level",
             "precision": precision, "l2": "inputs larger than L2 (coefficient fields of the finest level exceed "
             "129 MB)", "parallelism": f"dp{world} (independent shifts per rank)"}
 
@@ -499,27 +572,50 @@ def ctx_lattices(wl, binding):
 
 
 def main_reference(args, wl, rank, world):
+    """The oracle as it stands on the host cores.  Levels whose single oracle sample takes more than
+    a few seconds (meshes finer than 1/256) are timed once, in the first warm-up step; every other
+    step times a bounded sample of the remaining levels and the value combines the latest per-level
+    rates (extrapolated to the whole workload, as stated in the line)."""
     if rank != 0:
         return
+    import multiprocessing as mp
+
     from oracle import lattice
 
     zs = [lattice.cbc(lv.N, lv.s, wl.decay) for lv in wl.levels]
     ds = shifts(wl.seed, wl.levels)
-    budget = max(5.0, 60.0 / max(1, args.steps + args.warmup))
+    cores = os.cpu_count() or 1
+    slow = [l for l, lv in enumerate(wl.levels) if lv.n_fine > 256]
+    fast = [l for l in range(len(wl.levels)) if l not in slow]
+    per = {}
     vals = []
-    info = None
-    for i in range(args.warmup + args.steps):
-        info = cpu_baseline(wl, budget, zs, ds)
-        if i >= args.warmup:
-            vals.append(info["value"])
+    t_steps = []
+    with mp.get_context("spawn").Pool(cores, initializer=_pool_init) as pool:
+        if slow:
+            per.update(oracle_level_rates(wl, zs, ds, slow, 1.0, pool, cores))
+        for i in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            if fast:
+                per.update(oracle_level_rates(wl, zs, ds, fast, 4.0, pool, cores))
+            dt = time.perf_counter() - t0
+            if i >= args.warmup:
+                vals.append(oracle_rate(wl, per, cores))
+                t_steps.append(dt)
     value = float(np.mean(vals))
-    ms = wl.samples / value * 1e3
+    F = step_fraction(wl, args)
+    samples = step_samples(wl, F)
+    ms = samples / value * 1e3
+    sample = "; ".join(f"level {l}: {n} samples in {dt:.1f} process-s" for l, (n, dt) in sorted(per.items()))
+    note = (f"levels {slow} timed once before the steps (one sample per process); " if slow else "") + \
+        f"each step times levels {fast} for ~4 s on {cores} processes; ms_per_step is extrapolated from the " \
+        f"per-level rates to the bench step of {samples} samples"
     out = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": workload_config(wl, "fp64 (CPU oracle)", world),
-           "cpu_baseline": {"kind": "oracle", "cores": info["cores"], "sample": info["sample"], "value": value,
+           "warmup": args.warmup, "ms_per_step": ms, "ms_per_step_kind": "extrapolated", "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": workload_config(wl, "fp64 (CPU oracle)", world, F),
+           "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": sample + "; " + note, "value": value,
                             "unit": "samples/s"},
+           "wall_s_per_timed_step": float(np.mean(t_steps)) if t_steps else None,
            "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 

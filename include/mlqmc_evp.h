@@ -44,7 +44,8 @@ typedef enum {
   MQ_ENOMEM = 2,   /* host or device allocation failed */
   MQ_ECUDA = 3,    /* a CUDA call failed; the message names it */
   MQ_ENOCONV = 4,  /* at least one sample hit an iteration cap; results are still written */
-  MQ_ETIMEOUT = 5, /* reserved: a bounded device wait ran out */
+  MQ_ETIMEOUT = 5, /* a bounded device wait ran out (the tensor-core coefficient kernel's waits on
+                      its matrix-multiply barriers); the outputs of that call are not valid */
   MQ_ESTATE = 6    /* call out of order (e.g. evaluate before levels, lattice or shifts are set) */
 } mq_status;
 
@@ -260,8 +261,19 @@ mq_status mq_apply_operator_device(mq_ctx* ctx, int32_t n, int32_t B, const doub
  * tol_linear <= 0 selects 1e-10.  The launch is asynchronous on cuda_stream (NULL: the default
  * stream); check d_stat after synchronising.
  *
+ * Solver settings are fixed here (they do not follow the mq_set_* options of any context):
+ * coarse eigen-residual target 1e-12 with at most 200 LOBPCG iterations, shifted-solve residual
+ * target tol_linear (1e-10 by default), inner reduction per refinement step 1e-5 (mixed) or
+ * tol_linear / 10 (FP64), at most 500 inner iterations and 10 (mixed) or 4 (FP64) refinement
+ * steps, V(2,2) damped Jacobi (omega 0.8).  A solve on the coarse mesh itself (n_fine or n_prev
+ * equal to n_coarse) is nearly singular and uses an FP64 inner solve in either precision.  These
+ * targets are tighter than mq_eval_level's defaults, so on larger coarse meshes a sample can hit
+ * the eigensolver cap (flag 1) where mq_eval_level converges.
+ *
  * The first call on each device looks up the device address of the array (with that device
- * current) and caches it; make that first call before any stream capture begins.  The array
+ * current) and caches it; make that first call before any stream capture begins.  The address
+ * belongs to the device's context: after cudaDeviceReset the next call looks it up again (that
+ * call, too, must come before any capture).  The array
  * keeps the contents of the last call; the kernel clears everything it reads before use.  All
  * calls share the one array, so calls whose kernels overlap on the GPU (different streams, or
  * different host threads) race and corrupt each other's results: serialise them.

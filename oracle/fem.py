@@ -117,19 +117,6 @@ def coefficient(n: int, y: np.ndarray, a0: float = 1.0, decay: float = 2.0, fami
     return a
 
 
-def element_matrices(coords: np.ndarray, tri: np.ndarray):
-    """Local P1 stiffness (for a = 1) and consistent mass of one triangle."""
-    p = coords[tri]  # 3 x 2
-    B = np.array([[p[1, 0] - p[0, 0], p[2, 0] - p[0, 0]],
-                  [p[1, 1] - p[0, 1], p[2, 1] - p[0, 1]]])
-    area = 0.5 * abs(np.linalg.det(B))
-    ref_grad = np.array([[-1.0, -1.0], [1.0, 0.0], [0.0, 1.0]])  # gradients on the reference triangle
-    G = ref_grad @ np.linalg.inv(B)  # rows: physical gradients of the three hat functions
-    K = area * (G @ G.T)
-    Mloc = (area / 12.0) * (np.ones((3, 3)) + np.eye(3))
-    return K, Mloc
-
-
 _ELEMENT_CACHE: dict = {}
 
 
@@ -137,7 +124,9 @@ def _element_entries(n: int, with_boundary: bool):
     """Element loop over all triangles: for every local (a, b) pair whose two nodes are
     unknowns, record (row, col, triangle, K_ab for a = 1, M_ab).  The geometric part does
     not depend on the coefficient, so it is cached per mesh.  The per-element matrices are
-    computed for all triangles at once (the same formulas as element_matrices)."""
+    computed for all triangles at once: the stiffness for a = 1 is area * G G^T with G the
+    physical gradients of the three hat functions (reference gradients times the inverse of the
+    triangle's edge matrix), the consistent mass (area / 12) (1 + delta_ab)."""
     key = (n, with_boundary)
     if key in _ELEMENT_CACHE:
         return _ELEMENT_CACHE[key]

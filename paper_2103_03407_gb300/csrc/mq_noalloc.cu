@@ -10,7 +10,10 @@
 // a device address: passing it to a kernel would fault (or, where the GPU can reach host
 // memory, silently use the wrong memory).  The device address is therefore looked up with
 // cudaGetSymbolAddress, once per device, with that device current, on the first call made on
-// that device, and cached.
+// that device, and cached.  The cache belongs to the device's primary context: after
+// cudaDeviceReset (or anything else that destroys and recreates that context) the cached
+// address is stale, so the cache is keyed by the context too and looked up again when the
+// current context differs from the one the address was taken in.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -28,15 +31,45 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 std::mutex g_lock;
 void* g_scratch_ptr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};  // context the cached address belongs to
 
-// Device address of the scratch array on the current device (looked up once per device).
+// Unique id of the current context (never reused by a later context), through the driver entry
+// points the runtime hands out (no link-time dependency on the driver library); 0 if unavailable.
+unsigned long long current_context_id() {
+  typedef int (*GetCurrent)(void**);
+  typedef int (*GetId)(void*, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    looked_up = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = (GetCurrent)f;
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = (GetId)f;
+  }
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
+
+// Device address of the scratch array on the current device (looked up once per device and
+// context; with no context id available it is looked up on every call).
 cudaError_t scratch_address(int device, void** out) {
   std::lock_guard<std::mutex> guard(g_lock);
-  if (!g_scratch_ptr[device]) {
+  const unsigned long long ctx = current_context_id();
+  if (!g_scratch_ptr[device] || ctx == 0 || ctx != g_scratch_ctx[device]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
     g_scratch_ptr[device] = p;
+    g_scratch_ctx[device] = ctx;
   }
   *out = g_scratch_ptr[device];
   return cudaSuccess;
@@ -58,7 +91,13 @@ extern "C" mq_status mq_twogrid_samples_noalloc(int32_t n_fine, int32_t n_coarse
   if (B == 0) return MQ_OK;
   if (!d_a_coarse || !d_out || !d_stat || !d_outer) return MQ_EINVAL;
   const int mixed = precision == MQ_PREC_MIXED;
-  const size_t slab = mq::sample_slab_bytes(n_fine, n_coarse, n_prev, mixed);
+  // A solve on the coarse mesh itself (n == n_coarse with a longer truncation) is nearly
+  // singular -- the shift is an eigenvalue of a nearby operator -- so in mixed precision it runs
+  // with an FP64 inner solve (mode 1), as in mq_eval_level; every other solve uses the inner
+  // precision of the mode (mode 0).  The workspace is sized for the modes actually used.
+  const int mode_f = (mixed && n_fine == n_coarse && d_a_fine) ? 1 : 0;
+  const int mode_p = (mixed && n_prev == n_coarse && d_a_prev) ? 1 : 0;
+  const size_t slab = mq::sample_slab_bytes(n_fine, n_coarse, n_prev, mixed, mode_f, mode_p);
   if (slab > kNoAllocScratchBytes) return MQ_EINVAL;  // one block's workspace exceeds the fixed array
 
   int device = 0;
@@ -102,6 +141,8 @@ extern "C" mq_status mq_twogrid_samples_noalloc(int32_t n_fine, int32_t n_coarse
   p.max_inner_it = 500;
   p.nu = 2;
   p.omega = 0.8;
+  p.mode_f = mode_f;
+  p.mode_p = mode_p;
   const cudaError_t e = mq::launch_sample(p, mixed, (int)blocks, threads, 0, (cudaStream_t)cuda_stream);
   return e == cudaSuccess ? MQ_OK : MQ_ECUDA;
 }

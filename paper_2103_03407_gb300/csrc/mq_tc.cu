@@ -15,17 +15,24 @@
 // chunk.  Dropped products (g >= 7) and slice remainders are below 2^-56 per term: the result
 // matches an FP64 GEMM to a few units of FP64 rounding.
 //
-// Kernel: one CTA (4 warps) computes a 128-sample x 32-triangle tile.  Per 16-wide K step the
-// threads stage the seven A slices (128 x 16) and seven B slices (32 x 16) into shared memory in
-// the canonical no-swizzle K-major layout (8 x 16-byte core matrices), and one elected thread
-// issues the 28 tcgen05.mma (kind::f16, BF16 x BF16 -> FP32, M = 128, N = 32, K = 16) into seven
-// TMEM accumulators (32 columns each), then commits to an mbarrier.  After a chunk the
-// accumulators are read with tcgen05.ld (each warp its 32 lanes) and folded in FP64.  Every wait
-// is bounded.
+// Kernel (persistent, one CTA of 8 warps per SM): each CTA walks 128-sample x 64-triangle output
+// tiles.  Per 16-wide K step the tensor memory accelerator loads the seven A slices (128 x 16) and
+// the seven B slices (64 x 16) into one of four shared-memory stages (slices are stored K-blocked,
+// [slice][K/8][row][8], so one 4-D box lands directly in the canonical no-swizzle K-major layout of
+// 8 x 16-byte core matrices) and signals the stage's mbarrier with the transferred byte count.  One
+// elected thread waits for a stage, issues the 28 tcgen05.mma (kind::f16, BF16 x BF16 -> FP32,
+// M = 128, N = 64, K = 16) into seven TMEM accumulators (64 columns each), commits them to the
+// stage's "empty" mbarrier and refills the stage used one step earlier, so loads run up to four
+// steps ahead of the tensor cores.  After every 128-wide K chunk the eight warps read the
+// accumulators with tcgen05.ld (warp w: TMEM lanes 32 (w mod 4).., columns 32 (w div 4)..) and fold
+// them exactly into FP64 registers.  Every wait is bounded; a timeout sets an error word, stops the
+// issuing of new work, drains what is in flight and frees the tensor memory.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 
 #include "mq_internal.h"
 
@@ -35,10 +42,15 @@ namespace {
 constexpr int kSlices = 7;   // slices per operand
 constexpr int kGroups = 7;   // kept groups g = p + q
 constexpr int kTM = 128;     // samples per tile (TMEM lanes)
-constexpr int kTN = 32;      // triangles per tile
-constexpr int kTK = 16;      // K per MMA
+constexpr int kTN = 64;      // triangles per tile
+constexpr int kTK = 16;      // K per MMA (one pipeline step)
 constexpr int kChunk = 128;  // K per exact accumulation chunk
-constexpr int kTmemCols = 256;
+constexpr int kStepsPerChunk = kChunk / kTK;
+constexpr int kStages = 4;   // shared-memory pipeline depth
+constexpr int kTcThreads = 256;
+constexpr int kTmemCols = 512;  // 7 groups x 64 columns = 448 used
+constexpr uint32_t kABytes = kSlices * kTM * kTK * 2;  // 28 KB per stage
+constexpr uint32_t kBBytes = kSlices * kTN * kTK * 2;  // 14 KB per stage
 constexpr long kSpinLimit = 1L << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -54,7 +66,7 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
   return d;                // base offset 0, layout type 0 (no swizzle)
 }
 
-// instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M = 128, N = 32
+// instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M = 128, N = 64
 __host__ __device__ constexpr uint32_t instr_desc() {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTN >> 3) << 17) | ((uint32_t)(kTM >> 4) << 24);
 }
@@ -75,6 +87,11 @@ __device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count) : "memory");
 }
 
+// arrive once and expect `bytes` of asynchronous (TMA) transfers on the barrier's current phase
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes) : "memory");
+}
+
 // bounded wait for the phase with the given parity; false when the limit ran out
 __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
   const uint32_t addr = smem_u32(mbar);
@@ -91,33 +108,44 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
   return false;
 }
 
+// 4-D tiled TMA load of one box into shared memory, completing on an mbarrier
+__device__ __forceinline__ void tma_load4(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                          uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(mbar))
+      : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void async_proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// 32 consecutive TMEM columns of this thread's lane
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
+// 16 consecutive TMEM columns of this thread's lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // ---------------------------------------------------------------------------------------------
-// slicing.  out layout [slice][rows_pad][kpad] (K contiguous); zero padding beyond rows / k.
+// slicing.  out layout [slice][kpad / 8][rows_pad][8] (blocks of eight K values per row, the row
+// blocks back to back): a TMA box of 8 x rows x 2 x 7 is then one K step of all slices, in the
+// core-matrix layout the MMA reads.  Zero padding beyond rows / k.
 __global__ void k_slice_rows(const double* __restrict__ src, int rows, int k, size_t row_stride, size_t col_stride,
                              double scale, int rows_pad, int kpad, __nv_bfloat16* __restrict__ out) {
   const size_t tot = (size_t)rows_pad * kpad;
   for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += (size_t)gridDim.x * blockDim.x) {
-    const int r = (int)(q / kpad), j = (int)(q % kpad);
+    const int e = (int)(q & 7);
+    const size_t rb = q >> 3;  // jb * rows_pad + r
+    const int r = (int)(rb % rows_pad), j = (int)(rb / rows_pad) * 8 + e;
     double v = (r < rows && j < k) ? src[(size_t)r * row_stride + (size_t)j * col_stride] * scale : 0.0;
 #pragma unroll
     for (int p = 0; p < kSlices; ++p) {
@@ -129,127 +157,170 @@ __global__ void k_slice_rows(const double* __restrict__ src, int rows, int k, si
 }
 
 struct alignas(1024) TcSmem {
-  __nv_bfloat16 a[kSlices][kTM * kTK];  // 4 KB per slice
-  __nv_bfloat16 b[kSlices][kTN * kTK];  // 1 KB per slice
-  uint64_t mbar;
+  __nv_bfloat16 a[kStages][kSlices * kTM * kTK];  // [slice][K half][128 rows][8]
+  __nv_bfloat16 b[kStages][kSlices * kTN * kTK];  // [slice][K half][64 rows][8]
+  uint64_t full[kStages];   // TMA bytes of a stage landed
+  uint64_t empty[kStages];  // the MMAs that read a stage completed
+  uint64_t accf;            // the MMAs of a K chunk completed (accumulators readable)
   uint32_t tmem_base;
   int err;
 };
 
-// a[b][t] = a0 + sum_j y[b][j] psi[j][t], b < B, t < nT; slices [7][Bpad][Kpad] and [7][nTpad][ldp]
-__global__ void __launch_bounds__(128) k_coef_tc(const __nv_bfloat16* __restrict__ ys, const __nv_bfloat16* __restrict__ ps,
-                                                 int B, int Bpad, int nT, int nTpad, int Kpad, int ldp, double a0,
-                                                 double* __restrict__ out, int* __restrict__ err_flag) {
+// a[b][t] = a0 + sum_j y[b][j] psi[j][t], b < B, t < nT.  Tiles: tm = tile mod ntm (128 samples),
+// tn = tile div ntm (64 triangles); CTA c takes tiles c, c + grid, ...  Kpad: K of the Y slices.
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_coef_tc(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmP, int B, int nT, int Kpad,
+              int ntm, int ntiles, double a0, double* __restrict__ out, int* __restrict__ err_flag) {
   extern __shared__ __align__(1024) char dyn[];
   TcSmem& S = *reinterpret_cast<TcSmem*>(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int t0 = blockIdx.x * kTN, b0 = blockIdx.y * kTM;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int T = Kpad / kTK;  // K steps per tile
+  const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const uint32_t U = (uint32_t)my_tiles * (uint32_t)T;  // K steps of this CTA
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem_base)),
                  "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    mbar_init(&S.mbar, 1);
+    for (int i = 0; i < kStages; ++i) {
+      mbar_init(&S.full[i], 1);
+      mbar_init(&S.empty[i], 1);
+    }
+    mbar_init(&S.accf, 1);
     S.err = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = S.tmem_base;
   const uint32_t idesc = instr_desc();
-  double acc[kTN];
-#pragma unroll
-  for (int i = 0; i < kTN; ++i) acc[i] = 0.0;
-  uint32_t phase = 0;
+  // producer / issuer state (thread 0 only)
+  uint32_t u_load = 0;     // K steps whose loads were issued
+  uint32_t u_done = 0;     // K steps whose loads were consumed
+  uint32_t commits = 0;    // K steps whose MMAs were committed
+  uint32_t chunks = 0;     // accumulator commits (parity of accf)
+  auto issue_load = [&](uint32_t u) {
+    const int ti = (int)(u / (uint32_t)T), ks = (int)(u % (uint32_t)T);
+    const int tile = (int)blockIdx.x + ti * (int)gridDim.x;
+    const int tm = tile % ntm, tn = tile / ntm;
+    const int st = (int)(u % kStages);
+    mbar_arrive_expect(&S.full[st], kABytes + kBBytes);
+    tma_load4(S.a[st], &tmY, 0, tm * kTM, 2 * ks, 0, &S.full[st]);
+    tma_load4(S.b[st], &tmP, 0, tn * kTN, 2 * ks, 0, &S.full[st]);
+  };
+  if (tid == 0) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmY) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmP) : "memory");
+    for (; u_load < U && u_load < (uint32_t)kStages; ++u_load) issue_load(u_load);
+  }
+  const int q4 = warp & 3, half = warp >> 2;  // TMEM lane quarter, column half
   bool ok = true;
-  const size_t ysz = (size_t)Bpad * Kpad, psz = (size_t)nTpad * ldp;
-  for (int kc = 0; kc < Kpad && ok; kc += kChunk) {
-    const int kend = min(Kpad, kc + kChunk);
-    for (int k0 = kc; k0 < kend; k0 += kTK) {
-      // stage A: row tid, 16 K values = two 16-byte core-matrix rows per slice
-      {
-        const int r = tid;
-        const uint32_t off = (uint32_t)((r >> 3) * 256 + (r & 7) * 16);
+  for (int ti = 0; ti < my_tiles && ok; ++ti) {
+    const int tile = (int)blockIdx.x + ti * (int)gridDim.x;
+    const int tm = tile % ntm, tn = tile / ntm;
+    double acc[32];
 #pragma unroll
-        for (int p = 0; p < kSlices; ++p) {
-          const uint4* src = reinterpret_cast<const uint4*>(ys + p * ysz + (size_t)(b0 + r) * Kpad + k0);
-          char* dst = reinterpret_cast<char*>(S.a[p]);
-          *reinterpret_cast<uint4*>(dst + off) = src[0];
-          *reinterpret_cast<uint4*>(dst + off + 128) = src[1];
-        }
-      }
-      // stage B: slices x 32 rows x 2 halves, 16 bytes each
-#pragma unroll
-      for (int c = tid; c < kSlices * kTN * 2; c += 128) {
-        const int p = c / (kTN * 2), rr = (c >> 1) % kTN, h = c & 1;
-        const uint4* src = reinterpret_cast<const uint4*>(ps + p * psz + (size_t)(t0 + rr) * ldp + k0);
-        char* dst = reinterpret_cast<char*>(S.b[p]);
-        *reinterpret_cast<uint4*>(dst + (rr >> 3) * 256 + (rr & 7) * 16 + h * 128) = src[h];
-      }
-      async_proxy_fence();
-      __syncthreads();
+    for (int i = 0; i < 32; ++i) acc[i] = 0.0;
+    for (int kc = 0; kc < T && ok; kc += kStepsPerChunk) {
+      const int kend = min(T, kc + kStepsPerChunk);
       if (tid == 0) {
-        tc_fence_after();
-#pragma unroll
-        for (int p = 0; p < kSlices; ++p)
-#pragma unroll
-          for (int q = 0; q < kSlices; ++q) {
-            const int g = p + q;
-            if (g >= kGroups) continue;
-            const uint64_t ad = smem_desc(smem_u32(S.a[p]), 128, 256);
-            const uint64_t bd = smem_desc(smem_u32(S.b[q]), 128, 256);
-            // the first product of each group in a chunk overwrites the accumulator
-            const uint32_t accum = (k0 != kc) || (p > (g < kSlices ? 0 : g - kSlices + 1));
-            mma_bf16(tmem + (uint32_t)(g * kTN), ad, bd, idesc, accum);
+        for (int ks = kc; ks < kend && !S.err; ++ks) {
+          const uint32_t u = (uint32_t)ti * (uint32_t)T + (uint32_t)ks;
+          const int st = (int)(u % kStages);
+          if (!mbar_wait(&S.full[st], (u / kStages) & 1)) {
+            S.err = 1;
+            break;
           }
-        mma_commit(&S.mbar);
+          u_done = u + 1;
+          tc_fence_after();
+          const uint32_t abase = smem_u32(S.a[st]), bbase = smem_u32(S.b[st]);
+#pragma unroll
+          for (int p = 0; p < kSlices; ++p) {
+            const uint64_t ad = smem_desc(abase + p * (kTM * kTK * 2), kTM * 16, 128);
+#pragma unroll
+            for (int q = 0; q + p < kGroups; ++q) {
+              const uint64_t bd = smem_desc(bbase + q * (kTN * kTK * 2), kTN * 16, 128);
+              // the first product of each group (p = 0) in a chunk overwrites the accumulator
+              mma_bf16(tmem + (uint32_t)((p + q) * kTN), ad, bd, idesc, (ks != kc || p > 0) ? 1u : 0u);
+            }
+          }
+          mma_commit(&S.empty[st]);
+          commits = u + 1;
+          // refill the stage of the previous step once its MMAs are done (this step's MMAs are
+          // queued behind them, so the tensor cores stay busy meanwhile)
+          if (u >= 1 && u_load < U) {
+            const uint32_t v = u - 1;
+            if (!mbar_wait(&S.empty[v % kStages], (v / kStages) & 1)) {
+              S.err = 1;
+              break;
+            }
+            issue_load(u_load++);
+          }
+        }
+        mma_commit(&S.accf);  // tracks every MMA issued so far, whether or not an error stopped us
       }
-      // the shared tiles are reused by the next step: wait for the MMAs that read them
-      if (!mbar_wait(&S.mbar, phase)) {
-        ok = false;
-        if (tid == 0) S.err = 1;
-      }
-      phase ^= 1;
+      __syncwarp();
+      if (!mbar_wait(&S.accf, chunks & 1)) S.err = 1;
+      ++chunks;
       tc_fence_after();
       __syncthreads();
-      if (!ok) break;
+      ok = S.err == 0;
+      if (ok) {
+        // fold the exact group sums of this chunk: integers below 2^24, combined exactly as
+        // sum_g S_g 2^{8(6-g)} in two 64-bit integers (groups 0-3 and 4-6), then rounded once
+#pragma unroll
+        for (int sh = 0; sh < 2; ++sh) {
+          long long hi[16], lo[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) hi[i] = lo[i] = 0;
+#pragma unroll
+          for (int g = 0; g < kGroups; ++g) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(g * kTN + half * 32 + sh * 16), v);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const long long sv = (long long)__float2int_rn(v[i]);
+              if (g < 4) hi[i] = hi[i] * 256 + sv;
+              else lo[i] = lo[i] * 256 + sv;
+            }
+          }
+          // value of the chunk = (hi 2^24 + lo) 2^{-15-48}; hi < 2^56 and lo < 2^40 in magnitude
+#pragma unroll
+          for (int i = 0; i < 16; ++i) acc[sh * 16 + i] += fma((double)hi[i], 0x1p-39, (double)lo[i] * 0x1p-63);
+        }
+      }
+      tc_fence_before();
+      __syncthreads();  // the accumulators may be overwritten by the next chunk
     }
-    if (!ok) break;
-    // fold the exact group sums of this chunk: they are integers below 2^24, so the combination
-    // sum_g S_g 2^{8(6-g)} is formed exactly in two 64-bit integers (groups 0-3 and 4-6) and
-    // rounded once to FP64 -- three FP64 operations per output instead of two per group
-    long long hi[kTN], lo[kTN];
+    if (ok) {
+      const int b = tm * kTM + q4 * 32 + lane;
+      if (b < B) {
+        double* o = out + (size_t)b * nT;
+        const int t0 = tn * kTN + half * 32;
+        // nT = 2 n^2 and t0 are even: pairs are 16-byte aligned whenever the output base is
+        if (((uintptr_t)out & 15) == 0) {
 #pragma unroll
-    for (int i = 0; i < kTN; ++i) hi[i] = lo[i] = 0;
+          for (int i = 0; i < 32; i += 2)
+            if (t0 + i < nT) *reinterpret_cast<double2*>(o + t0 + i) = make_double2(a0 + acc[i], a0 + acc[i + 1]);
+        } else {
 #pragma unroll
-    for (int g = 0; g < kGroups; ++g) {
-      float v[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(g * kTN), v);
-#pragma unroll
-      for (int i = 0; i < kTN; ++i) {
-        const long long s = (long long)__float2int_rn(v[i]);
-        if (g < 4) hi[i] = hi[i] * 256 + s;
-        else lo[i] = lo[i] * 256 + s;
+          for (int i = 0; i < 32; ++i)
+            if (t0 + i < nT) o[t0 + i] = a0 + acc[i];
+        }
       }
     }
-    // value of the chunk = (hi 2^24 + lo) 2^{-15-48}; hi < 2^56 and lo < 2^40 in magnitude
-#pragma unroll
-    for (int i = 0; i < kTN; ++i) acc[i] += fma((double)hi[i], 0x1p-39, (double)lo[i] * 0x1p-63);
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
   }
-  const int b = b0 + tid;
-  if (ok && b < B) {
-    double* o = out + (size_t)b * nT;
-#pragma unroll
-    for (int i = 0; i < kTN; ++i)
-      if (t0 + i < nT) o[t0 + i] = a0 + acc[i];
-  }
-  if (tid == 0 && S.err) {
-    atomicOr(err_flag, 1);
-    mbar_wait(&S.mbar, phase ^ 1);  // a timed-out wait: give the MMAs in flight one more bounded wait
+  if (tid == 0) {
+    if (S.err) {
+      atomicOr(err_flag, 1);
+      // drain: loads issued but not consumed, and the last commit of every stage
+      for (uint32_t u = u_done; u < u_load; ++u) mbar_wait(&S.full[u % kStages], (u / kStages) & 1);
+    }
+    for (uint32_t u = commits > kStages ? commits - kStages : 0; u < commits; ++u)
+      mbar_wait(&S.empty[u % kStages], (u / kStages) & 1);
   }
   tc_fence_before();
   __syncthreads();
@@ -259,6 +330,38 @@ __global__ void __launch_bounds__(128) k_coef_tc(const __nv_bfloat16* __restrict
 int grid1(size_t n) {
   size_t g = (n + 255) / 256;
   return (int)(g < 1 ? 1 : (g > 152 * 64 ? 152 * 64 : g));
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry points (no link-time dependency)
+typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder() {
+  static std::once_flag once;
+  static EncodeTiled fn = nullptr;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiled)f;
+  });
+  return fn;
+}
+
+// tensor map of slices [7][kpad/8][rows_pad][8] (BF16), box 8 x box_rows x 2 x 7: one K step
+cudaError_t slice_map(CUtensorMap* m, const void* base, int rows_pad, int kpad, int box_rows) {
+  EncodeTiled enc = encoder();
+  if (!enc) return cudaErrorNotSupported;
+  const cuuint64_t dim[4] = {8, (cuuint64_t)rows_pad, (cuuint64_t)(kpad / 8), (cuuint64_t)kSlices};
+  const cuuint64_t stride[3] = {16, (cuuint64_t)rows_pad * 16, (cuuint64_t)rows_pad * 16 * (cuuint64_t)(kpad / 8)};
+  const cuuint32_t box[4] = {8, (cuuint32_t)box_rows, 2, (cuuint32_t)kSlices};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dim, stride, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 }  // namespace
@@ -272,7 +375,7 @@ int tc_pad_rows(int rows) { return (rows + 127) / 128 * 128; }
 int tc_pad_k(int k) { return (k + 15) / 16 * 16; }
 
 cudaError_t launch_psi_slices(const double* d_psi, int s_rows, int nT, void* d_out, cudaStream_t st) {
-  // psi is [s_rows][nT] (row = term j): the slices are [7][nT_pad][K_pad] with K contiguous
+  // psi is [s_rows][nT] (row = term j): the slices are [7][K_pad/8][nT_pad][8]
   const int rp = tc_pad_rows(nT), kp = tc_pad_k(s_rows);
   k_slice_rows<<<grid1((size_t)rp * kp), 256, 0, st>>>(d_psi, nT, s_rows, 1, (size_t)nT, 128.0, rp, kp,
                                                       (__nv_bfloat16*)d_out);
@@ -286,20 +389,30 @@ cudaError_t launch_y_slices(const double* d_Y, int B, int ldy, int k, int kpad, 
   return cudaGetLastError();
 }
 
-// a[B][nT] = a0 + Y psi from slices: y slices [7][Bpad][kpad] built for K = kpad columns, psi
-// slices [7][nTpad][kpad_psi] (only the first kpad columns are read)
+// a[B][nT] = a0 + Y psi from slices: y slices [7][kpad/8][Bpad][8] built for K = kpad columns, psi
+// slices [7][kpad_psi/8][nTpad][8] (only the first kpad columns are read)
 cudaError_t launch_coef_tc(const void* d_yslices, int B, int kpad, const void* d_pslices, int nT, int kpad_psi,
                            double a0, double* d_a, int* d_err, cudaStream_t st) {
   if (B == 0 || nT == 0) return cudaSuccess;
-  if (kpad > kpad_psi || kpad % kTK) return cudaErrorInvalidValue;
+  if (kpad > kpad_psi || kpad % kTK || kpad <= 0) return cudaErrorInvalidValue;
   const int Bp = tc_pad_rows(B), nTp = tc_pad_rows(nT);
-  const size_t smem = sizeof(TcSmem) + 1024 + 64 * 1024;  // extra space keeps at most two CTAs per SM
-  cudaError_t e = cudaFuncSetAttribute(k_coef_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  CUtensorMap tmY, tmP;
+  cudaError_t e = slice_map(&tmY, d_yslices, Bp, kpad, kTM);
   if (e != cudaSuccess) return e;
-  dim3 grid(nTp / kTN, Bp / kTM);
-  if (grid.y > 65535) return cudaErrorInvalidValue;
-  k_coef_tc<<<grid, 128, smem, st>>>((const __nv_bfloat16*)d_yslices, (const __nv_bfloat16*)d_pslices, B, Bp, nT, nTp,
-                                     kpad, kpad_psi, a0, d_a, d_err);
+  // the psi slices hold kpad_psi columns; the map covers them all, the kernel reads kpad
+  e = slice_map(&tmP, d_pslices, nTp, kpad_psi, kTN);
+  if (e != cudaSuccess) return e;
+  const size_t smem = sizeof(TcSmem) + 1024;
+  e = cudaFuncSetAttribute(k_coef_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const int ntm = Bp / kTM;
+  const long ntiles = (long)ntm * (nTp / kTN);
+  if (ntiles > 0x7fffffffL) return cudaErrorInvalidValue;
+  const int grid = (int)(ntiles < sms ? ntiles : sms);
+  k_coef_tc<<<grid, kTcThreads, smem, st>>>(tmY, tmP, B, nT, kpad, ntm, (int)ntiles, a0, d_a, d_err);
   return cudaGetLastError();
 }
 

@@ -89,7 +89,7 @@ WORKLOADS = {
         "mlqmc6_h32_1024",
         [Level(32, 32, 32, 32, 16384, 16)]
         + [Level(32 << l, 32, 32 << l, _ceil_sqrt(32 << l), 16384 >> l, 16) for l in range(1, 6)],
-        seed=3, precision="mixed", tol=1e-7,
+        seed=3, precision="mixed", tol=1e-10,
     ),
     # the paper's first test problem (Sec. 5): psi_j = j^-p sin(j pi x1) sin((j+1) pi x2) with
     # p = 4/3 and a0 = pi / sqrt(2), s = 64 terms, S = 8, H = 1/8, h_l = 2^-(l+3) (level 0 direct),
@@ -103,7 +103,7 @@ WORKLOADS = {
     "stress_h1024_s1024": Workload(
         "stress_h1024_s1024",
         [Level(1024, 64, 1024, 32, 32, 16)],
-        seed=4, precision="mixed", tol=1e-7,
+        seed=4, precision="mixed", tol=1e-10,
     ),
 }
 

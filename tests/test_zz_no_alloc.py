@@ -27,12 +27,22 @@ def B():
     return binding
 
 
-@pytest.mark.parametrize("prec", [0, 1])
-def test_noalloc_matches_regular_entry_point(B, prec):
+GEOMETRIES = [
     # a level whose workspace does not fit in shared memory: 1/64 fine mesh, 1/32 previous fine
     # mesh, 1/16 coarse mesh
-    levels = [Level(32, 16, 32, 6, 64, 2), Level(64, 16, 64, 8, 64, 2)]
+    [Level(32, 16, 32, 6, 64, 2), Level(64, 16, 64, 8, 64, 2)],
+    # the previous fine mesh is the coarse mesh itself (a longer truncation on the same mesh): a
+    # nearly singular shifted system, solved with an FP64 inner solve in both precisions
+    [Level(16, 8, 16, 4, 64, 2), Level(32, 16, 32, 6, 64, 2)],
+]
+
+
+@pytest.mark.parametrize("geom", range(len(GEOMETRIES)))
+@pytest.mark.parametrize("prec", [0, 1])
+def test_noalloc_matches_regular_entry_point(B, prec, geom):
+    levels = GEOMETRIES[geom]
     lv, pv = levels[1], levels[0]
+    nf, nc, npv = lv.n_fine, lv.n_coarse, pv.n_fine
     ctx = B.Context(0)
     ctx.mq_set_coefficient(1.0, 64, 0, 2.0)
     ctx.mq_set_levels(levels)
@@ -49,18 +59,18 @@ def test_noalloc_matches_regular_entry_point(B, prec):
     nb = lv.R * npts
     dY = torch.empty((lv.R, npts, lv.s), dtype=torch.float64, device="cuda")
     ctx.mq_lattice_points_device(1, k0, k1, dY)
-    a_c = torch.empty((nb, 2 * 16 * 16), dtype=torch.float64, device="cuda")
-    a_f = torch.empty((nb, 2 * 64 * 64), dtype=torch.float64, device="cuda")
-    a_p = torch.empty((nb, 2 * 32 * 32), dtype=torch.float64, device="cuda")
-    ctx.mq_coefficients_device(16, lv.S, dY, nb, lv.s, a_c)
-    ctx.mq_coefficients_device(64, lv.s, dY, nb, lv.s, a_f)
-    ctx.mq_coefficients_device(32, pv.s, dY, nb, lv.s, a_p)
+    a_c = torch.empty((nb, 2 * nc * nc), dtype=torch.float64, device="cuda")
+    a_f = torch.empty((nb, 2 * nf * nf), dtype=torch.float64, device="cuda")
+    a_p = torch.empty((nb, 2 * npv * npv), dtype=torch.float64, device="cuda")
+    ctx.mq_coefficients_device(nc, lv.S, dY, nb, lv.s, a_c)
+    ctx.mq_coefficients_device(nf, lv.s, dY, nb, lv.s, a_f)
+    ctx.mq_coefficients_device(npv, pv.s, dY, nb, lv.s, a_p)
 
     for call in range(2):
         out = torch.full((nb, 4), float("nan"), dtype=torch.float64, device="cuda")
         stat = torch.full((nb, 4), -1, dtype=torch.int32, device="cuda")
         outer = torch.zeros((nb, 2), dtype=torch.int32, device="cuda")
-        B.mq_twogrid_samples_noalloc(64, 16, 32, prec, nb, a_f, a_c, a_p, out, stat, outer)
+        B.mq_twogrid_samples_noalloc(nf, nc, npv, prec, nb, a_f, a_c, a_p, out, stat, outer)
         torch.cuda.synchronize()
         got = out.cpu().numpy().reshape(lv.R, npts, 4)
         assert np.all(stat.cpu().numpy()[:, 3] == 0), f"call {call}: flags set"
