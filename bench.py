@@ -25,7 +25,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from synthetic_inputs import WORKLOADS, shifts  # noqa: E402
+from synthetic_inputs import WORKLOADS, shared_shifts, shifts, shifts_for_rank  # noqa: E402
 
 METRIC = "two-grid eigen-samples/s at rel. err<=1e-10 vs FP64 oracle; mixed vs plain GPU"
 # the largest workload that fits one GPU: six levels, meshes 1/32 .. 1/1024, 516,096 samples
@@ -88,9 +88,34 @@ def fine_dof_solves(wl):
     return tot
 
 
-def shard_seed(seed, rank):
-    """Rank r draws the shifts of its shard from seed + r (rank 0: the workload's own shifts)."""
-    return seed + rank
+def gather_rank_sums(level_sums, world):
+    """All ranks' per-level shift sums, shifts of rank 0 first: [level][R * world] (one exchange of
+    (L+1) x R doubles per rank at the end; nothing on the data path)."""
+    if world <= 1:
+        return [np.asarray(x, dtype=np.float64) for x in level_sums]
+    import torch
+    import torch.distributed as dist
+
+    flat = torch.tensor(np.concatenate(level_sums), dtype=torch.float64)
+    if dist.get_backend() == "nccl":
+        flat = flat.cuda()
+    parts = [torch.empty_like(flat) for _ in range(world)]
+    dist.all_gather(parts, flat)
+    parts = [p.cpu().numpy() for p in parts]
+    out, off = [], 0
+    for x in level_sums:
+        out.append(np.concatenate([p[off:off + len(x)] for p in parts]))
+        off += len(x)
+    return out
+
+
+def merged_estimate(binding, level_sums, npoints, world, shared=False):
+    """The workload's estimate from every rank's shifts (mq_estimate_sums over R * world shifts)."""
+    allsums = gather_rank_sums(level_sums, world)
+    m, se, lm, lv = binding.mq_estimate_sums(allsums, npoints, shared)
+    return {"mean": m, "std_err": se, "level_mean": list(lm), "level_var": list(lv),
+            "shifts_per_level": [len(x) for x in allsums], "points_per_shift": list(npoints),
+            "ranks": world}
 
 
 def dist_env():
@@ -148,16 +173,30 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------------------
-def setup_context(binding, wl, stream_ptr, prec, seed_offset=0):
+def setup_context(binding, wl, stream_ptr, prec, rank=0, world=1):
+    """A context on the workload; with several ranks, this rank's share of the workload's shifts.
+    The reuse workload (shared shifts) uses one embedded lattice and the library's reuse scheme."""
     ctx = binding.Context(0, stream_ptr)
     ctx.mq_set_coefficient(wl.a0, max(lv.s for lv in wl.levels), wl.family, wl.decay)
     ctx.mq_set_levels(wl.levels)
-    zs = [binding.mq_cbc_lattice(lv.N, lv.s, wl.decay) for lv in wl.levels]
-    ds = shifts(shard_seed(wl.seed, seed_offset), wl.levels)
+    shared = wl.extra.get("shared", False)
+    if shared:
+        z = binding.mq_cbc_embedded_lattice(wl.extra["m_min"], wl.extra["m_max"], max(lv.s for lv in wl.levels),
+                                            wl.decay)
+        zs = [z[: lv.s] for lv in wl.levels]
+        ds = shared_shifts(wl.seed, wl.levels, rank, world)
+    else:
+        zs = [binding.mq_cbc_lattice(lv.N, lv.s, wl.decay) for lv in wl.levels]
+        ds = shifts_for_rank(wl.seed, wl.levels, rank, world)
     for l in range(len(wl.levels)):
-        ctx.mq_set_lattice(l, zs[l])
+        if shared:
+            ctx.mq_set_lattice_embedded(l, zs[l], wl.extra["m_max"])
+        else:
+            ctx.mq_set_lattice(l, zs[l])
         ctx.mq_set_shifts(l, ds[l])
     ctx.mq_set_precision(binding.MQ_PREC_MIXED if prec == "mixed" else binding.MQ_PREC_FP64)
+    if shared:
+        ctx.mq_set_reuse(1)
     return ctx, zs, ds
 
 
@@ -187,10 +226,10 @@ def run_device_step(ctx, wl, outs, sums, F, step, sequential=True):
         ctx.mq_eval_levels_device(list(range(len(wl.levels))), outs, sums)
 
 
-def time_device(binding, torch, wl, prec, steps, warmup, stream, F, seed_offset=0, sequential=True):
+def time_device(binding, torch, wl, prec, steps, warmup, stream, F, rank=0, world=1, sequential=True):
     if not sequential and F != 1:
         raise SystemExit("the concurrent schedule evaluates whole levels: use --fraction 1")
-    ctx, zs, ds = setup_context(binding, wl, stream.cuda_stream, prec, seed_offset)
+    ctx, zs, ds = setup_context(binding, wl, stream.cuda_stream, prec, rank, world)
     win = windows(wl, F, 0)
     outs = [torch.empty((lv.R, k1 - k0, 4), dtype=torch.float64, device="cuda") for lv, (k0, k1) in zip(wl.levels, win)]
     sums = [torch.empty(lv.R, dtype=torch.float64, device="cuda") for lv in wl.levels]
@@ -209,13 +248,14 @@ def time_device(binding, torch, wl, prec, steps, warmup, stream, F, seed_offset=
     # per-level device time of the timed region (CUDA events on the launching stream)
     timing = [ctx.mq_get_level_timing(l) + ctx.mq_get_kernel_timing(l) for l in range(len(wl.levels))]
     launches = ctx.mq_get_launch_count()
+    level_sums = [ctx.mq_get_sums(l) for l in range(len(wl.levels))]  # estimator state of the timed steps
     last = [o.cpu().numpy() for o in outs]  # per-sample results of the last timed step
     # iteration counts from one more (untimed) pass over the last step's windows
     kstats = {}
     for l, (k0, k1) in enumerate(windows(wl, F, warmup + steps - 1)):
         ctx.mq_eval_level_device(l, k0, k1, outs[l], sums[l])
         kstats[l] = [ctx.mq_get_stats()]
-    return ctx, ms, timing, kstats, last, launches
+    return ctx, ms, timing, kstats, last, launches, level_sums
 
 
 def max_rel_diff(a_levels, b_levels):
@@ -243,9 +283,16 @@ def time_e2e(binding, wl, prec, steps, warmup, stream_ptr, F):
     t0 = time.perf_counter()
     for i in range(steps):
         ctx.mq_reset_sums()
-        for l, (k0, k1) in enumerate(windows(wl, F, warmup + i)):
-            ctx.mq_set_lattice(l, zs[l])
+        shared = wl.extra.get("shared", False)
+        for l in range(len(wl.levels)):
+            if shared:
+                ctx.mq_set_lattice_embedded(l, zs[l], wl.extra["m_max"])
+            else:
+                ctx.mq_set_lattice(l, zs[l])
             ctx.mq_set_shifts(l, ds[l])
+        if shared:
+            ctx.mq_set_reuse(1)
+        for l, (k0, k1) in enumerate(windows(wl, F, warmup + i)):
             ctx.mq_eval_level(l, k0, k1)
         ctx.mq_estimate()
     torch.cuda.synchronize()
@@ -486,9 +533,12 @@ def main():
     samples = step_samples(wl, F)  # samples per step (every level's window, every shift)
     with torch.cuda.stream(stream):
         with sampler:
-            ctx, ms, timing, kstats, outs, launches = time_device(binding, torch, wl, args.precision, args.steps,
-                                                                  args.warmup, stream, F, seed_offset=rank,
-                                                                  sequential=args.schedule == "sequential")
+            ctx, ms, timing, kstats, outs, launches, lsums = time_device(
+                binding, torch, wl, args.precision, args.steps, args.warmup, stream, F, rank=rank, world=world,
+                sequential=args.schedule == "sequential")
+    # one exchange of the per-level shift sums: the estimate over every rank's shifts
+    estimate = merged_estimate(binding, [x[0] for x in lsums], [x[1] for x in lsums], world,
+                               shared=wl.extra.get("shared", False))
     if world > 1:
         torch.distributed.barrier()
     ms = max_over_ranks(ms, world, "cuda")
@@ -498,8 +548,8 @@ def main():
     if not args.no_plain and args.precision == "mixed" and rank == 0:
         # the plain FP64 GPU path on the same steps (same windows) and warm-up
         with torch.cuda.stream(stream):
-            ctxp, msp, _, _, outs_p, _ = time_device(binding, torch, wl, "fp64", args.steps, args.warmup, stream, F,
-                                                     sequential=args.schedule == "sequential")
+            ctxp, msp, _, _, outs_p, _, _ = time_device(binding, torch, wl, "fp64", args.steps, args.warmup, stream,
+                                                        F, sequential=args.schedule == "sequential")
         ctxp.close()
         plain = {"value": samples * args.steps / (msp / 1e3), "unit": "samples/s", "ms_per_step": msp / args.steps,
                  "steps": args.steps, "warmup": args.warmup,
@@ -544,6 +594,7 @@ def main():
                        "blocks": lst[l]["blocks"], "threads": lst[l]["threads"], "smem": lst[l]["smem_bytes"],
                        "workspace": lst[l]["workspace_bytes"]} for l in range(len(wl.levels))],
         "plain_fp64": plain,
+        "estimate": estimate,
         "fine_dof_solves_per_s": dof_rate,
         "gpu_launches_note": "kernels launched in the timed region, counted by the library",
     }
@@ -564,7 +615,8 @@ def workload_config(wl, precision, world, F=1):
                      f"({', '.join(str(k1 - k0) for k0, k1 in win)} points per shift on levels 0..{len(win) - 1}); "
                      f"{F} steps cover the workload once") if F > 1 else "every point of every level",
             "precision": precision, "l2": "inputs larger than L2 (coefficient fields of the finest level exceed "
-            "129 MB)", "parallelism": f"dp{world} (independent shifts per rank)"}
+            "129 MB)", "parallelism": f"dp{world} (the workload's shifts partitioned across ranks; per-level shift "
+            f"sums merged once at the end)"}
 
 
 def ctx_lattices(wl, binding):

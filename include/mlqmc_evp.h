@@ -103,8 +103,36 @@ mq_status mq_set_levels(mq_ctx* ctx, int32_t L_plus_1, const mq_level* levels);
 /* Generating vector z[0..s-1] of level `level` (copied), 0 < z_j < N (Sec. 2.5). */
 mq_status mq_set_lattice(mq_ctx* ctx, int32_t level, const uint32_t* z, int32_t s);
 
+/* Level `level` uses an embedded lattice rule (Sec. 2.5: one generating vector for every
+ * N = 2^m, nested point sets) in radical-inverse order: point k (0 <= k < 2^m_max) is
+ *     y_k = {rev(k) z / 2^m_max + Delta_r} - 1/2,  rev(k) = the m_max-bit reversal of k,
+ * so the first 2^m points are exactly the 2^m-point rule and doubling the points of a level adds
+ * the next 2^m.  z[0..s-1] odd and < 2^m_max (copied); the level's N must be a power of two
+ * <= 2^m_max (1 <= m_max <= 31).  mq_set_lattice switches the level back to the plain order. */
+mq_status mq_set_lattice_embedded(mq_ctx* ctx, int32_t level, const uint32_t* z, int32_t s, int32_t m_max);
+
 /* Random shifts Delta[R][s_l] of level `level`, row-major, each in [0, 1) (copied). */
 mq_status mq_set_shifts(mq_ctx* ctx, int32_t level, const double* delta);
+
+/* The reuse scheme across levels (Sec. 4.3, the closing paragraphs after Algorithm 2): every level
+ * uses the same shifts and the same embedded lattice (each level's z and shifts are prefixes of
+ * the longest level's), level 0 is a direct eigensolve (n_coarse = n_fine, S = s) and every level
+ * l >= 1 has n_coarse = n_fine of level 0 and S = s of level 0.  Point k of level l is then point
+ * k of level 0 in the first s_0 components, so the coarse pair of level l at point k is the
+ * level-0 eigenpair computed there, and lambda^{l-1} at point k is the value level l-1 computed:
+ * levels l >= 1 skip the coarse eigensolve and the previous-level solve (Algorithm 2 steps 6-8 and
+ * 12-14) and take both from a device store the library keeps per shift and point.  Consequently
+ * mq_eval_level(l, k0, k1) with l >= 1 requires levels 0 and l-1 to have been evaluated at every
+ * point of [k0, k1) since the scheme was switched on (MQ_ESTATE otherwise), and N_l must not
+ * exceed N_{l-1}.  With shared shifts the levels are not independent: mq_estimate takes the
+ * standard error from the per-shift totals sum_l Q^(r)_l (eq. sample_var applied to them)
+ * instead of adding the level variances (level_var still reports eq. sample_var per level).
+ * on = 1: validate, allocate the store (R N_0 (n_0+1)^2 + R sum_l N_l doubles; kept for the next
+ * mq_set_reuse(1)) and mark every point empty; on = 0: free the store.  A later mq_set_lattice* or
+ * mq_set_shifts switches the scheme off (call mq_set_reuse(1) again after them); mq_set_levels
+ * also frees the store.
+ * mq_eval_levels_device is not available in this scheme (MQ_ESTATE). */
+mq_status mq_set_reuse(mq_ctx* ctx, int32_t on);
 
 /* Precision mode and the relative residual target ||b - (A - lambda_H M) w|| / ||b|| of the fine
  * shifted solve (tol_linear <= 0: default 1e-5 for MQ_PREC_MIXED, 1e-6 for MQ_PREC_FP64).  The
@@ -186,6 +214,22 @@ mq_status mq_eval_levels_device(mq_ctx* ctx, int32_t nlevels, const int32_t* lev
 mq_status mq_estimate(mq_ctx* ctx, double* mean, double* std_err, double* level_mean,
                       double* level_var);
 
+/* The estimator state of level `level`: sums[r] = sum over the evaluated points of the level
+ * differences of shift r (host [R], copied out) and the number of points evaluated.  Several
+ * processes that evaluate disjoint sets of shifts of one workload (one per GPU) exchange these and
+ * combine them with mq_estimate_sums.  Either output may be NULL. */
+mq_status mq_get_sums(mq_ctx* ctx, int32_t level, double* sums, uint64_t* npoints);
+
+/* The estimate of eq. tg-mlqmc from per-level, per-shift sums (no context, no GPU): level l has
+ * R[l] >= 2 shifts whose sums are sums[off_l .. off_l + R[l]) with off_l = R[0] + .. + R[l-1], and
+ * npoints[l] > 0 points per shift.  Q^(r)_l = sums / npoints, Qhat_l their mean, level_var[l] =
+ * eq. sample_var; std_err = sqrt(sum_l level_var[l]) for independent levels (shared = 0), or the
+ * standard error of the per-shift totals sum_l Q^(r)_l when every level uses the same shifts
+ * (shared = 1, all R[l] equal; as mq_estimate in the reuse scheme).  level_mean / level_var:
+ * NULL or host [nlevels]. */
+mq_status mq_estimate_sums(int32_t nlevels, const int32_t* R, const double* sums, const uint64_t* npoints,
+                           int32_t shared, double* mean, double* std_err, double* level_mean, double* level_var);
+
 /* Clear the estimator sums and the per-level timers (keeps levels, lattices and shifts). */
 mq_status mq_reset_sums(mq_ctx* ctx);
 
@@ -222,7 +266,18 @@ const char* mq_last_error(const mq_ctx* ctx);
  * whose error is within an absolute 1e-12 of the minimum.  z_out: host [s].  N >= 2. */
 mq_status mq_cbc_lattice(uint32_t N, int32_t s, double decay, uint32_t* z_out);
 
-/* Lattice points of level `level` for k in [k0, k1) (eq. t_kl, eq. rqmc):
+/* Generating vector of an embedded lattice rule for N = 2^m, m_min <= m <= m_max (host; Sec. 2.5).
+ * The paper uses embedded rules without stating their construction criterion; here component j
+ * takes the odd candidate c < 2^(m_max-1) minimising max over m of e^2_{2^m}(z_1..z_{j-1}, c) /
+ * min_c' e^2_{2^m}(z_1..z_{j-1}, c'), with e^2 the shift-averaged worst-case error of
+ * mq_cbc_lattice (product weights gamma_j = j^-decay), formed as the mean of the excess of the
+ * running products over one; ratios within a relative 1e-6 of the minimum tie and the smallest
+ * candidate wins.
+ * 0 <= m_min <= m_max <= 24; z_out: host [s]. */
+mq_status mq_cbc_embedded_lattice(int32_t m_min, int32_t m_max, int32_t s, double decay, uint32_t* z_out);
+
+/* Lattice points of level `level` for k in [k0, k1) (eq. t_kl, eq. rqmc; radical-inverse order on
+ * a level with an embedded lattice):
  * d_Y [R][k1-k0][s_l], y = {k z / N + Delta_r} - 1/2. */
 mq_status mq_lattice_points_device(mq_ctx* ctx, int32_t level, uint32_t k0, uint32_t k1,
                                    double* d_Y);

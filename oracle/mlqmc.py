@@ -81,3 +81,58 @@ def estimate(level_shift_means):
         qhat.append(m)
         vhat.append(((m - q) ** 2).sum() / (R * (R - 1)))
     return float(sum(qhat)), float(np.sqrt(sum(vhat))), qhat, vhat
+
+
+# ---------------------------------------------------------------------------------------------
+# Shared shifts, nested points and reuse across levels (Sec. 4.3, the paragraphs after Algorithm
+# 2).  Every level uses the same random shifts (drawn once with s_L components; level l uses the
+# first s_l of them) and the same embedded lattice rule in radical-inverse order, so point k of
+# level l is point k of level 0 in the first s_0 components and point k of level l-1 in the first
+# s_{l-1}.  With H_l = h_0 and S_l = s_0 on every level l >= 1, the coarse pair of level l at
+# point k is the level-0 (direct) eigenpair at point k, and lambda^{l-1} at point k is the value
+# level l-1 computed there: steps 6-8 and 12-14 of Algorithm 2 are skipped and only the fine
+# two-grid update (h_l, s_l) remains per level.
+
+def shared_samples(levels, z, m_max: int, delta_row, ks, a0: float = 1.0, decay: float = 2.0,
+                   family: int = 0) -> np.ndarray:
+    """Per-sample results [L+1, len(ks), 4] = (lambda_H, lambda^l, lambda^{l-1}, diff) of the reuse
+    scheme for one shift row (length >= s_L) at embedded-rule indices ks; entries of levels whose
+    N_l <= k are NaN.  Level 0 must be direct (n_coarse = n_fine, S = s); levels l >= 1 must have
+    n_coarse = n_fine of level 0 and S = s_0."""
+    lv0 = levels[0]
+    assert lv0.n_fine == lv0.n_coarse and lv0.S == lv0.s
+    for lv in levels[1:]:
+        assert lv.n_coarse == lv0.n_fine and lv.S == lv0.s
+    out = np.full((len(levels), len(ks), 4), np.nan)
+    s_max = max(lv.s for lv in levels)
+    Y = lattice.embedded_points(z[:s_max], m_max, np.asarray(delta_row)[:s_max], ks)
+    for i, k in enumerate(ks):
+        y = Y[i]
+        lam0, u0 = twogrid.coarse_pair(lv0.n_fine, y[: lv0.s], a0, decay, family)
+        out[0, i] = (lam0, lam0, 0.0, lam0)
+        prev = lam0
+        for l in range(1, len(levels)):
+            lv = levels[l]
+            if k >= lv.N:
+                break
+            lam = twogrid.twogrid_update(lv.n_fine, y[: lv.s], lam0, u0, lv0.n_fine, a0, decay, family=family)
+            out[l, i] = (lam0, lam, prev, lam - prev)
+            prev = lam
+    return out
+
+
+def estimate_shared(level_shift_means):
+    """Estimate and standard error with shared shifts.  The levels are no longer independent, but
+    the per-shift totals Q^(r) = sum_l Q^(r)_l are (one independent shift each): the estimate is
+    their mean and its variance is estimated by their sample variance (eq. sample_var applied to
+    the totals).  Returns (Qhat^ML, SE, Qhat_l[], Vhat_l[]) with the per-level values of eq.
+    sample_var for information."""
+    q = np.asarray(level_shift_means, dtype=np.float64)  # [L+1, R]
+    R = q.shape[1]
+    if R < 2:
+        raise ValueError("the sample-variance estimate needs R >= 2 shifts")
+    tot = q.sum(axis=0)
+    m = tot.sum() / R
+    var = ((m - tot) ** 2).sum() / (R * (R - 1))
+    _, _, qhat, vhat = estimate(q)
+    return float(m), float(np.sqrt(var)), qhat, vhat

@@ -28,7 +28,8 @@ EXPORTS = [
     "mq_set_precision", "mq_set_solver_options", "mq_set_eig_options", "mq_set_smoothing", "mq_set_tier", "mq_set_cta_threads", "mq_eval_level", "mq_eval_level_device", "mq_eval_levels_device", "mq_estimate", "mq_reset_sums",
     "mq_get_level_timing", "mq_get_kernel_timing", "mq_get_launch_count", "mq_eval_point",
     "mq_get_stats", "mq_last_error", "mq_cbc_lattice", "mq_lattice_points_device", "mq_coefficients_device",
-    "mq_apply_operator_device", "mq_twogrid_samples_noalloc",
+    "mq_apply_operator_device", "mq_twogrid_samples_noalloc", "mq_set_lattice_embedded", "mq_set_reuse",
+    "mq_cbc_embedded_lattice", "mq_get_sums", "mq_estimate_sums",
 ]
 
 
@@ -79,6 +80,11 @@ def load(path: str = LIB_PATH):
         "mq_set_levels": ([P, i32, C.POINTER(mq_level)], C.c_int),
         "mq_set_lattice": ([P, i32, C.POINTER(u32), i32], C.c_int),
         "mq_set_shifts": ([P, i32, dp], C.c_int),
+        "mq_set_lattice_embedded": ([P, i32, C.POINTER(u32), i32, i32], C.c_int),
+        "mq_set_reuse": ([P, i32], C.c_int),
+        "mq_cbc_embedded_lattice": ([i32, i32, i32, f64, C.POINTER(u32)], C.c_int),
+        "mq_get_sums": ([P, i32, dp, C.POINTER(C.c_uint64)], C.c_int),
+        "mq_estimate_sums": ([i32, C.POINTER(i32), dp, C.POINTER(C.c_uint64), i32, dp, dp, dp, dp], C.c_int),
         "mq_set_precision": ([P, C.c_int, f64], C.c_int),
         "mq_set_tier": ([P, i32], C.c_int),
         "mq_set_solver_options": ([P, f64, i32, i32], C.c_int),
@@ -175,6 +181,14 @@ class Context:
         z = np.ascontiguousarray(z, dtype=np.uint32)
         self._check(self.lib.mq_set_lattice(self.h, int(level), z.ctypes.data_as(C.POINTER(C.c_uint32)), z.size))
 
+    def mq_set_lattice_embedded(self, level, z, m_max):
+        z = np.ascontiguousarray(z, dtype=np.uint32)
+        self._check(self.lib.mq_set_lattice_embedded(self.h, int(level), z.ctypes.data_as(C.POINTER(C.c_uint32)),
+                                                     z.size, int(m_max)))
+
+    def mq_set_reuse(self, on=1):
+        self._check(self.lib.mq_set_reuse(self.h, int(on)))
+
     def mq_set_shifts(self, level, delta):
         d = np.ascontiguousarray(delta, dtype=np.float64)
         self._check(self.lib.mq_set_shifts(self.h, int(level), _dptr(d)))
@@ -227,6 +241,13 @@ class Context:
         lm, lv = np.zeros(L), np.zeros(L)
         self._check(self.lib.mq_estimate(self.h, C.byref(m), C.byref(se), _dptr(lm), _dptr(lv)))
         return m.value, se.value, lm, lv
+
+    def mq_get_sums(self, level):
+        """(sums [R], points) of one level's estimator state."""
+        R = self.levels[level].R
+        sums, n = np.zeros(R), C.c_uint64()
+        self._check(self.lib.mq_get_sums(self.h, int(level), _dptr(sums), C.byref(n)))
+        return sums, n.value
 
     def mq_reset_sums(self):
         self._check(self.lib.mq_reset_sums(self.h))
@@ -287,6 +308,32 @@ def mq_twogrid_samples_noalloc(n_fine, n_coarse, n_prev, precision, B, d_a_fine,
                                         C.c_void_p(stream) if stream else None)
     if st != MQ_OK:
         raise MQError(st, "mq_twogrid_samples_noalloc failed")
+
+
+def mq_estimate_sums(level_sums, npoints, shared=False):
+    """Estimate from per-level shift sums (list of arrays [R_l]) and points per level: returns
+    (mean, std_err, level_mean [L+1], level_var [L+1])."""
+    lib = load()
+    L1 = len(level_sums)
+    R = (C.c_int32 * L1)(*[len(x) for x in level_sums])
+    flat = np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.float64) for x in level_sums]))
+    n = (C.c_uint64 * L1)(*[int(v) for v in npoints])
+    m, se = C.c_double(), C.c_double()
+    lm, lv = np.zeros(L1), np.zeros(L1)
+    st = lib.mq_estimate_sums(L1, R, _dptr(flat), n, int(bool(shared)), C.byref(m), C.byref(se), _dptr(lm), _dptr(lv))
+    if st != MQ_OK:
+        raise MQError(st, "mq_estimate_sums: bad arguments")
+    return m.value, se.value, lm, lv
+
+
+def mq_cbc_embedded_lattice(m_min: int, m_max: int, s: int, decay: float = 2.0) -> np.ndarray:
+    lib = load()
+    z = np.zeros(s, dtype=np.uint32)
+    st = lib.mq_cbc_embedded_lattice(int(m_min), int(m_max), int(s), float(decay),
+                                     z.ctypes.data_as(C.POINTER(C.c_uint32)))
+    if st != MQ_OK:
+        raise MQError(st, "mq_cbc_embedded_lattice: bad arguments")
+    return z
 
 
 def mq_cbc_lattice(N: int, s: int, decay: float = 2.0) -> np.ndarray:

@@ -48,6 +48,7 @@ struct mq_ctx {
 
   std::vector<mq_level> levels;
   std::vector<std::vector<uint32_t>> z;
+  std::vector<int> mbits;  // per level: 0 = plain lattice order, else the embedded rule of 2^mbits points
   std::vector<uint32_t*> d_z;
   std::vector<std::vector<double>> delta;
   std::vector<double*> d_delta;
@@ -56,6 +57,13 @@ struct mq_ctx {
   std::vector<double> lvl_coef_ms, lvl_sample_ms;  // per level: accumulated device time
   std::vector<uint64_t> lvl_launches;              // per level: per-sample kernel launches
   std::vector<double> lvl_percta_ms, lvl_stream_ms;  // per level: the per-sample kernel alone, the streaming tier
+
+  // reuse scheme across levels (shared shifts, nested points): the level-0 eigenpairs and every
+  // level's two-grid values, per shift and point, and which points hold values
+  bool reuse = false;
+  DevBuf ru0;                            // [R][N_0][(n_0+1)^2] padded level-0 eigenvectors
+  std::vector<DevBuf> rlam;              // per level: [R][N_l] lambda^l (level 0: lambda_{h_0,s_0})
+  std::vector<std::vector<uint8_t>> rfilled;  // per level: point k has values
 
   int prec = MQ_PREC_FP64;
   double tol_lin = 0.0;  // 0: default of the precision mode
@@ -115,6 +123,22 @@ mq_status grow(mq_ctx* c, DevBuf& b, size_t bytes) {
 }
 
 bool pow2(int n) { return n >= 1 && (n & (n - 1)) == 0; }
+
+// switches the reuse scheme off but keeps its device store for a later mq_set_reuse(1)
+void invalidate_reuse(mq_ctx* c) {
+  c->reuse = false;
+  c->rfilled.clear();
+}
+
+void free_reuse(mq_ctx* c) {
+  if (c->ru0.p) cudaFree(c->ru0.p);
+  c->ru0 = DevBuf{};
+  for (DevBuf& b : c->rlam)
+    if (b.p) cudaFree(b.p);
+  c->rlam.clear();
+  c->rfilled.clear();
+  c->reuse = false;
+}
 
 // frequency pairs of the synthetic family: k1, k2 >= 1 ordered by k1^2 + k2^2, then k1
 // Wave numbers (k1, k2) of the first s terms psi_j ~ sin(pi k1 x1) sin(pi k2 x2) of a family:
@@ -287,26 +311,42 @@ LevelGeom geom(const mq_ctx* c, int level) {
 }
 
 // Runs the per-sample pipeline on B = R * npts samples whose parameters are in c->Y (ldy = s).
-// Writes c->out / c->stat / c->outer; returns timings in stats.
-mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk, bool want_u) {
+// Writes c->out / c->stat / c->outer; returns timings in stats.  In the reuse scheme, `level`
+// and the first point `kbase` of the pass locate the stored level-0 pairs and lower-level values:
+// levels l >= 1 take them instead of solving the coarse problem and the previous-level problem.
+mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk, bool want_u, int level = -1,
+                      uint32_t kbase = 0) {
   const size_t B = (size_t)R * npts;
   mq_status st;
+  const bool given = c->reuse && level >= 1;  // coarse pair and lambda^{l-1} come from the store
   const size_t nTf = (size_t)2 * g.nf * g.nf, nTc = (size_t)2 * g.nc * g.nc, nTp = (size_t)2 * g.np * g.np;
-  if ((st = grow(c, c->ac, B * nTc * sizeof(double))) != MQ_OK) return st;
+  const size_t Vc = (size_t)(g.nc + 1) * (g.nc + 1);
+  if (!given && (st = grow(c, c->ac, B * nTc * sizeof(double))) != MQ_OK) return st;
   if (!g.direct_f && (st = grow(c, c->af, B * nTf * sizeof(double))) != MQ_OK) return st;
-  if (g.np && !g.direct_p && (st = grow(c, c->ap, B * nTp * sizeof(double))) != MQ_OK) return st;
+  if (!given && g.np && !g.direct_p && (st = grow(c, c->ap, B * nTp * sizeof(double))) != MQ_OK) return st;
   if ((st = grow(c, c->out, B * 4 * sizeof(double))) != MQ_OK) return st;
   if ((st = grow(c, c->stat, B * 4 * sizeof(int))) != MQ_OK) return st;
   if ((st = grow(c, c->outer, B * 2 * sizeof(int))) != MQ_OK) return st;
   if (want_u && (st = grow(c, c->uout, B * (size_t)(g.nc - 1) * (g.nc - 1) * sizeof(double))) != MQ_OK) return st;
+  if (c->reuse && (st = grow(c, c->upad, B * Vc * sizeof(double))) != MQ_OK) return st;
 
   const int mixed = c->prec == MQ_PREC_MIXED;
   if ((st = reset_tc_error(c)) != MQ_OK) return st;
   MQ_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
   const double* Y = (const double*)c->Y.p;
-  if ((st = coefficients(c, g.nc, g.S, Y, (int)B, g.s, (double*)c->ac.p)) != MQ_OK) return st;
+  if (given) {
+    const uint32_t N0 = c->levels[0].N, Np = c->levels[level - 1].N;
+    MQ_LAUNCH(c, mq::launch_reuse_gather(R, npts, kbase, Vc, (const double*)c->ru0.p, (const double*)c->rlam[0].p, N0,
+                                         (const double*)c->rlam[level - 1].p, Np, (double*)c->upad.p,
+                                         (double*)c->out.p, c->stream));
+    MQ_CUDA(c, cudaMemsetAsync(c->stat.p, 0, B * 4 * sizeof(int), c->stream));
+    MQ_CUDA(c, cudaMemsetAsync(c->outer.p, 0, B * 2 * sizeof(int), c->stream));
+  } else {
+    if ((st = coefficients(c, g.nc, g.S, Y, (int)B, g.s, (double*)c->ac.p)) != MQ_OK) return st;
+  }
   if (!g.direct_f && (st = coefficients(c, g.nf, g.s, Y, (int)B, g.s, (double*)c->af.p)) != MQ_OK) return st;
-  if (g.np && !g.direct_p && (st = coefficients(c, g.np, g.sp, Y, (int)B, g.s, (double*)c->ap.p)) != MQ_OK) return st;
+  if (!given && g.np && !g.direct_p && (st = coefficients(c, g.np, g.sp, Y, (int)B, g.s, (double*)c->ap.p)) != MQ_OK)
+    return st;
   MQ_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
 
   mq::SampleLaunch p{};
@@ -320,7 +360,9 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
     return stream ? 2 : 0;
   };
   p.mode_f = mode_of(g.nf, g.direct_f);
-  p.mode_p = mode_of(g.np, g.direct_p);
+  p.mode_p = given ? 0 : mode_of(g.np, g.direct_p);
+  p.u_in = given ? (const double*)c->upad.p : nullptr;
+  p.prev_given = given ? 1 : 0;
   p.nf = g.nf;
   p.nc = g.nc;
   p.np = g.np;
@@ -369,15 +411,17 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
   p.nu = c->opt_nu > 0 ? c->opt_nu : 2;
   p.omega = 0.8;
   const bool ext = p.mode_f == 2 || p.mode_p == 2;
-  if (ext) {
-    p.coarse_only = 1;
-    if ((st = grow(c, c->upad, B * (size_t)(g.nc + 1) * (g.nc + 1) * sizeof(double))) != MQ_OK) return st;
-    p.u_pad = (double*)c->upad.p;
+  if (ext || c->reuse) {
+    // the streaming tier (and the reuse store of level 0) reads the padded coarse eigenvectors
+    p.coarse_only = ext ? 1 : 0;
+    if ((st = grow(c, c->upad, B * Vc * sizeof(double))) != MQ_OK) return st;
+    if (!given) p.u_pad = (double*)c->upad.p;
   }
   // FP64 inner solves in the per-sample kernel follow the FP64 defaults
-  const int in_kernel_n = std::max(p.mode_f != 2 && !g.direct_f ? g.nf : 0, p.mode_p != 2 && !g.direct_p ? g.np : 0);
+  const int np_k = given ? 0 : g.np;  // the previous-level solve runs here only without the store
+  const int in_kernel_n = std::max(p.mode_f != 2 && !g.direct_f ? g.nf : 0, p.mode_p != 2 && !g.direct_p ? np_k : 0);
   const int threads = g.threads > 0 ? g.threads : threads_for(in_kernel_n, g.nc);
-  const size_t slab = mq::sample_slab_bytes(g.nf, g.nc, g.np, mixed, p.mode_f, p.mode_p);
+  const size_t slab = mq::sample_slab_bytes(g.nf, g.nc, np_k, mixed, p.mode_f, p.mode_p);
   const int static_smem = mq::sample_static_smem(mixed);
   const size_t smem_cap = (size_t)std::max(0, c->smem_optin - static_smem - 1024);
   const bool use_smem = slab <= smem_cap;
@@ -395,7 +439,9 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
   p.gscratch = (char*)c->scratch.p;
   p.slab_bytes = slab;
   p.use_smem = use_smem;
-  MQ_LAUNCH(c, mq::launch_sample(p, mixed, blocks, threads, smem, c->stream));
+  // with the coarse pairs and lambda^{l-1} given and the fine solve streamed, the per-sample
+  // kernel has nothing to do
+  if (!(given && p.mode_f == 2)) MQ_LAUNCH(c, mq::launch_sample(p, mixed, blocks, threads, smem, c->stream));
   MQ_CUDA(c, cudaEventRecord(c->ev[3], c->stream));
   if (ext) {
     const uint64_t launched0 = mq::stream_launches();
@@ -425,7 +471,7 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
       s.outer_out = (int*)c->outer.p + 0;
       MQ_CUDA(c, mq::stream_solve(s, mixed, c->arena.p, c->stream));
     }
-    if (p.mode_p == 2) {
+    if (p.mode_p == 2 && !given) {
       s.n = g.np;
       s.a = (const double*)c->ap.p;
       s.lam_out = (double*)c->out.p + 2;
@@ -543,6 +589,12 @@ mq_status eval_level_impl(mq_ctx* c, int level, uint32_t k0, uint32_t k1, double
   const int npts = (int)(k1 - k0);
   c->stats = mq_stats{};
   if (npts == 0) return MQ_OK;
+  if (c->reuse && level >= 1) {
+    // the stored level-0 pairs and level l-1 values of these points must exist
+    for (uint32_t k = k0; k < k1; ++k)
+      if (!c->rfilled[0][k] || !c->rfilled[level - 1][k])
+        return fail(c, MQ_ESTATE, "reuse: evaluate levels 0 and %d at point %u before level %d", level - 1, k, level);
+  }
   const int ppp = points_per_pass(c, g, R, npts);
   std::vector<double> host_out;
   std::vector<double> level_add(R, 0.0);
@@ -551,9 +603,17 @@ mq_status eval_level_impl(mq_ctx* c, int level, uint32_t k0, uint32_t k1, double
     const int pn = std::min(ppp, npts - p0);
     const size_t B = (size_t)R * pn;
     if ((st = grow(c, c->Y, B * g.s * sizeof(double))) != MQ_OK) return st;
-    MQ_LAUNCH(c, mq::launch_lattice_points(c->d_z[level], lv.N, c->d_delta[level], R, g.s, k0 + p0, pn,
-                                         (double*)c->Y.p, c->stream));
-    if ((st = run_samples(c, g, R, pn, chunk_for(c, R, pn), false)) != MQ_OK) return st;
+    const int mb = c->mbits[level];
+    MQ_LAUNCH(c, mq::launch_lattice_points(c->d_z[level], mb ? (1u << mb) : lv.N, c->d_delta[level], R, g.s, k0 + p0,
+                                         pn, mb, (double*)c->Y.p, c->stream));
+    if ((st = run_samples(c, g, R, pn, chunk_for(c, R, pn), false, level, k0 + p0)) != MQ_OK) return st;
+    if (c->reuse) {
+      const mq_level& l0 = c->levels[0];
+      const size_t V0 = (size_t)(l0.n_fine + 1) * (l0.n_fine + 1);
+      MQ_LAUNCH(c, mq::launch_reuse_scatter(R, pn, k0 + p0, V0, (const double*)c->upad.p, (const double*)c->out.p,
+                                            (double*)c->rlam[level].p, lv.N, level == 0 ? (double*)c->ru0.p : nullptr,
+                                            nullptr, l0.N, c->stream));
+    }
     if ((st = grow(c, c->sums_d, R * sizeof(double))) != MQ_OK) return st;
     if ((st = grow(c, c->flags_d, sizeof(int))) != MQ_OK) return st;
     MQ_CUDA(c, cudaMemsetAsync(c->flags_d.p, 0, sizeof(int), c->stream));
@@ -595,12 +655,26 @@ mq_status eval_level_impl(mq_ctx* c, int level, uint32_t k0, uint32_t k1, double
     if (shift_sums) shift_sums[r] += level_add[r];
   }
   c->npoints[level] += (uint64_t)npts;
+  if (c->reuse)
+    for (uint32_t k = k0; k < k1; ++k) c->rfilled[level][k] = 1;
   if (any_flags) {
     int dummy;
     if ((st = collect_stats(c, c->last_B, &dummy)) != MQ_OK) return st;
   }
   c->stats.samples = (uint64_t)R * npts;
   return flags_status(c, any_flags);
+}
+
+// pairwise sum of f(0) .. f(n-1) (rounding error grows like log n, not n)
+template <class F>
+double pairwise_sum(uint32_t lo, uint32_t n, const F& f) {
+  if (n <= 16) {
+    double s = 0.0;
+    for (uint32_t k = lo; k < lo + n; ++k) s += f(k);
+    return s;
+  }
+  const uint32_t h = n / 2;
+  return pairwise_sum(lo, h, f) + pairwise_sum(lo + h, n - h, f);
 }
 
 }  // namespace
@@ -651,6 +725,7 @@ mq_status mq_destroy(mq_ctx* c) {
     if (b->p) cudaFree(b->p);
   for (auto& kv : c->psi) cudaFree(kv.second.second);
   for (auto& kv : c->psi_sl) cudaFree(kv.second.second);
+  free_reuse(c);
   for (auto p : c->d_z)
     if (p) cudaFree(p);
   for (auto p : c->d_delta)
@@ -725,8 +800,10 @@ mq_status mq_set_levels(mq_ctx* c, int32_t L_plus_1, const mq_level* levels) {
     if (p) cudaFree(p);
   for (auto p : c->d_delta)
     if (p) cudaFree(p);
+  free_reuse(c);
   c->levels.assign(levels, levels + L_plus_1);
   c->z.assign(L_plus_1, {});
+  c->mbits.assign(L_plus_1, 0);
   c->delta.assign(L_plus_1, {});
   c->d_z.assign(L_plus_1, nullptr);
   c->d_delta.assign(L_plus_1, nullptr);
@@ -756,6 +833,27 @@ mq_status mq_set_lattice(mq_ctx* c, int32_t level, const uint32_t* z, int32_t s)
   MQ_CUDA(c, cudaMalloc(&c->d_z[level], s * sizeof(uint32_t)));
   MQ_CUDA(c, cudaMemcpy(c->d_z[level], z, s * sizeof(uint32_t), cudaMemcpyHostToDevice));
   c->z[level].assign(z, z + s);
+  c->mbits[level] = 0;
+  invalidate_reuse(c);
+  return MQ_OK;
+}
+
+mq_status mq_set_lattice_embedded(mq_ctx* c, int32_t level, const uint32_t* z, int32_t s, int32_t m_max) {
+  if (!c) return MQ_EINVAL;
+  if (level < 0 || level >= (int)c->levels.size()) return fail(c, MQ_EINVAL, "level %d out of range", level);
+  if (m_max < 1 || m_max > 31) return fail(c, MQ_EINVAL, "m_max %d not in [1, 31]", m_max);
+  const mq_level& lv = c->levels[level];
+  if (!pow2((int)std::min<uint32_t>(lv.N, 1u << 30)) || lv.N > (1u << m_max))
+    return fail(c, MQ_EINVAL, "level %d: N = %u must be a power of two <= 2^m_max", level, lv.N);
+  if (!z || s != lv.s) return fail(c, MQ_EINVAL, "lattice of level %d needs s = %d components", level, lv.s);
+  for (int j = 0; j < s; ++j)
+    if (z[j] % 2 == 0 || z[j] >= (1u << m_max)) return fail(c, MQ_EINVAL, "z[%d] = %u must be odd and < 2^m_max", j, z[j]);
+  const uint32_t N = lv.N;
+  c->levels[level].N = 1u << m_max;  // validated against the embedded modulus, then restored
+  mq_status st = mq_set_lattice(c, level, z, s);
+  c->levels[level].N = N;
+  if (st != MQ_OK) return st;
+  c->mbits[level] = m_max;
   return MQ_OK;
 }
 
@@ -774,6 +872,63 @@ mq_status mq_set_shifts(mq_ctx* c, int32_t level, const double* delta) {
   MQ_CUDA(c, cudaMalloc(&c->d_delta[level], m * sizeof(double)));
   MQ_CUDA(c, cudaMemcpy(c->d_delta[level], delta, m * sizeof(double), cudaMemcpyHostToDevice));
   c->delta[level].assign(delta, delta + m);
+  invalidate_reuse(c);
+  return MQ_OK;
+}
+
+mq_status mq_set_reuse(mq_ctx* c, int32_t on) {
+  if (!c) return MQ_EINVAL;
+  c->lanes_stale = true;
+  if (!on) {
+    free_reuse(c);
+    return MQ_OK;
+  }
+  invalidate_reuse(c);
+  const int L1 = (int)c->levels.size();
+  if (L1 == 0) return fail(c, MQ_ESTATE, "levels not set");
+  const mq_level& l0 = c->levels[0];
+  if (l0.n_coarse != l0.n_fine || l0.S != l0.s) return fail(c, MQ_EINVAL, "reuse: level 0 must be a direct eigensolve");
+  int top = 0;
+  for (int l = 0; l < L1; ++l) {
+    const mq_level& lv = c->levels[l];
+    if (l > 0 && (lv.n_coarse != l0.n_fine || lv.S != l0.s))
+      return fail(c, MQ_EINVAL, "reuse: level %d must use level 0's coarse problem (n_coarse = %d, S = %d)", l, l0.n_fine,
+                  l0.s);
+    if (lv.R != l0.R) return fail(c, MQ_EINVAL, "reuse: every level needs the same R");
+    if (l > 0 && lv.N > c->levels[l - 1].N) return fail(c, MQ_EINVAL, "reuse: N must not grow with the level");
+    if (!c->d_z[l] || !c->d_delta[l]) return fail(c, MQ_ESTATE, "reuse: lattice and shifts of level %d not set", l);
+    if (c->mbits[l] == 0 || c->mbits[l] != c->mbits[0])
+      return fail(c, MQ_EINVAL, "reuse: every level needs the same embedded lattice (mq_set_lattice_embedded)");
+    if (lv.s > c->levels[top].s) top = l;
+  }
+  // one generating vector and one set of shifts: every level's are prefixes of the longest
+  for (int l = 0; l < L1; ++l) {
+    const int s = c->levels[l].s, sT = c->levels[top].s;
+    for (int j = 0; j < s; ++j)
+      if (c->z[l][j] != c->z[top][j]) return fail(c, MQ_EINVAL, "reuse: level %d lattice is not a prefix of level %d's", l, top);
+    for (int r = 0; r < l0.R; ++r)
+      for (int j = 0; j < s; ++j)
+        if (c->delta[l][(size_t)r * s + j] != c->delta[top][(size_t)r * sT + j])
+          return fail(c, MQ_EINVAL, "reuse: level %d shifts are not a prefix of level %d's", l, top);
+  }
+  MQ_CUDA(c, cudaSetDevice(c->device));
+  const size_t V0 = (size_t)(l0.n_fine + 1) * (l0.n_fine + 1);
+  mq_status st = grow(c, c->ru0, (size_t)l0.R * l0.N * V0 * sizeof(double));
+  if (st != MQ_OK) return st;
+  if ((int)c->rlam.size() != L1) {
+    for (DevBuf& b : c->rlam)
+      if (b.p) cudaFree(b.p);
+    c->rlam.assign(L1, DevBuf{});
+  }
+  c->rfilled.assign(L1, {});
+  for (int l = 0; l < L1; ++l) {
+    if ((st = grow(c, c->rlam[l], (size_t)l0.R * c->levels[l].N * sizeof(double))) != MQ_OK) {
+      free_reuse(c);
+      return st;
+    }
+    c->rfilled[l].assign(c->levels[l].N, 0);
+  }
+  c->reuse = true;
   return MQ_OK;
 }
 
@@ -856,6 +1011,7 @@ mq_status mq_eval_levels_device(mq_ctx* c, int32_t nlev, const int32_t* levels, 
       if (levels[k] == levels[i]) return fail(c, MQ_EINVAL, "level %d listed twice", (int)levels[i]);
   }
   if (nlev == 0) return MQ_OK;
+  if (c->reuse) return fail(c, MQ_ESTATE, "reuse: the levels depend on one another; evaluate them in order");
   MQ_CUDA(c, cudaSetDevice(c->device));
   MQ_CUDA(c, cudaStreamSynchronize(c->stream));  // earlier work of the caller's stream first
   // one child context per level: its own stream, buffers and host thread
@@ -877,7 +1033,10 @@ mq_status mq_eval_levels_device(mq_ctx* c, int32_t nlev, const int32_t* levels, 
       };
       chk(mq_set_coefficient(ch, c->a0, c->s_max, c->family, c->decay));
       chk(mq_set_levels(ch, (int32_t)c->levels.size(), c->levels.data()));
-      chk(mq_set_lattice(ch, l, c->z[l].data(), (int32_t)c->z[l].size()));
+      if (c->mbits[l])
+        chk(mq_set_lattice_embedded(ch, l, c->z[l].data(), (int32_t)c->z[l].size(), c->mbits[l]));
+      else
+        chk(mq_set_lattice(ch, l, c->z[l].data(), (int32_t)c->z[l].size()));
       chk(mq_set_shifts(ch, l, c->delta[l].data()));
       chk(mq_set_precision(ch, (mq_precision)c->prec, c->tol_lin));
       chk(mq_set_solver_options(ch, c->opt_tol_inner, c->opt_max_inner, c->opt_max_outer));
@@ -935,6 +1094,56 @@ mq_status mq_eval_levels_device(mq_ctx* c, int32_t nlev, const int32_t* levels, 
   return result;
 }
 
+mq_status mq_get_sums(mq_ctx* c, int32_t level, double* sums, uint64_t* npoints) {
+  if (!c) return MQ_EINVAL;
+  if (level < 0 || level >= (int)c->sums.size()) return fail(c, MQ_EINVAL, "level %d out of range", level);
+  if (sums) std::copy(c->sums[level].begin(), c->sums[level].end(), sums);
+  if (npoints) *npoints = c->npoints[level];
+  return MQ_OK;
+}
+
+mq_status mq_estimate_sums(int32_t nlevels, const int32_t* R, const double* sums, const uint64_t* npoints,
+                           int32_t shared, double* mean, double* std_err, double* level_mean, double* level_var) {
+  if (nlevels < 1 || !R || !sums || !npoints) return MQ_EINVAL;
+  for (int l = 0; l < nlevels; ++l) {
+    if (R[l] < 2 || npoints[l] == 0) return MQ_EINVAL;
+    if (shared && R[l] != R[0]) return MQ_EINVAL;
+  }
+  double tot = 0.0, var = 0.0;
+  std::vector<double> qtot(shared ? R[0] : 0, 0.0);
+  size_t off = 0;
+  for (int l = 0; l < nlevels; ++l) {
+    const int Rl = R[l];
+    std::vector<double> q(Rl);
+    double m = 0.0;
+    for (int r = 0; r < Rl; ++r) {
+      q[r] = sums[off + r] / (double)npoints[l];
+      m += q[r];
+    }
+    m /= Rl;
+    double v = 0.0;
+    for (int r = 0; r < Rl; ++r) v += (m - q[r]) * (m - q[r]);
+    v /= (double)Rl * (Rl - 1);
+    tot += m;
+    var += v;
+    for (size_t r = 0; r < qtot.size(); ++r) qtot[r] += q[r];
+    if (level_mean) level_mean[l] = m;
+    if (level_var) level_var[l] = v;
+    off += (size_t)Rl;
+  }
+  if (shared) {
+    const int Rs = (int)qtot.size();
+    double m = 0.0, v = 0.0;
+    for (int r = 0; r < Rs; ++r) m += qtot[r];
+    m /= Rs;
+    for (int r = 0; r < Rs; ++r) v += (m - qtot[r]) * (m - qtot[r]);
+    var = v / ((double)Rs * (Rs - 1));
+  }
+  if (mean) *mean = tot;
+  if (std_err) *std_err = std::sqrt(var);
+  return MQ_OK;
+}
+
 mq_status mq_reset_sums(mq_ctx* c) {
   if (!c) return MQ_EINVAL;
   for (size_t l = 0; l < c->sums.size(); ++l) std::fill(c->sums[l].begin(), c->sums[l].end(), 0.0);
@@ -975,6 +1184,9 @@ mq_status mq_estimate(mq_ctx* c, double* mean, double* std_err, double* level_me
   if (!c) return MQ_EINVAL;
   if (c->levels.empty()) return fail(c, MQ_ESTATE, "levels not set");
   double tot = 0.0, var = 0.0;
+  // reuse scheme: one set of shifts for every level, so the per-shift totals sum_l Q^(r)_l are the
+  // independent replicates; their sample variance replaces the sum of the level variances
+  std::vector<double> qtot(c->reuse ? c->levels[0].R : 0, 0.0);
   for (size_t l = 0; l < c->levels.size(); ++l) {
     const int R = c->levels[l].R;
     if (c->npoints[l] == 0) return fail(c, MQ_ESTATE, "level %zu has no evaluated points", l);
@@ -991,8 +1203,17 @@ mq_status mq_estimate(mq_ctx* c, double* mean, double* std_err, double* level_me
     v /= (double)R * (R - 1);
     tot += m;
     var += v;
+    for (size_t r = 0; r < qtot.size(); ++r) qtot[r] += q[r];
     if (level_mean) level_mean[l] = m;
     if (level_var) level_var[l] = v;
+  }
+  if (c->reuse) {
+    const int R = (int)qtot.size();
+    double m = 0.0, v = 0.0;
+    for (int r = 0; r < R; ++r) m += qtot[r];
+    m /= R;
+    for (int r = 0; r < R; ++r) v += (m - qtot[r]) * (m - qtot[r]);
+    var = v / ((double)R * (R - 1));
   }
   if (mean) *mean = tot;
   if (std_err) *std_err = std::sqrt(var);
@@ -1069,6 +1290,58 @@ mq_status mq_cbc_lattice(uint32_t N, int32_t s, double decay, uint32_t* z_out) {
   return MQ_OK;
 }
 
+mq_status mq_cbc_embedded_lattice(int32_t m_min, int32_t m_max, int32_t s, double decay, uint32_t* z_out) {
+  if (m_min < 0 || m_max < m_min || m_max > 24 || s < 1 || !z_out || !std::isfinite(decay)) return MQ_EINVAL;
+  const uint32_t Nmax = 1u << m_max;
+  std::vector<uint32_t> cand;
+  for (uint32_t q = 1; q < std::max<uint32_t>(2, Nmax / 2); q += 2) cand.push_back(q);
+  const int nm = m_max - m_min + 1;
+  // excess[i][k] = prod over the chosen components of (1 + gamma_j B2({k z_j / N})) - 1, N = 2^(m_min+i):
+  // the squared error is its mean, formed without cancelling against the constant 1
+  std::vector<std::vector<double>> excess(nm), tab(nm);
+  for (int i = 0; i < nm; ++i) {
+    const uint32_t N = 1u << (m_min + i);
+    excess[i].assign(N, 0.0);
+    tab[i].resize(N);
+    for (uint32_t k = 0; k < N; ++k) {
+      const double x = (double)k / (double)N;
+      tab[i][k] = x * x - x + 1.0 / 6.0;  // Bernoulli polynomial B2
+    }
+  }
+  std::vector<double> worst(cand.size()), e2(cand.size());
+  for (int j = 0; j < s; ++j) {
+    const double gam = std::pow((double)(j + 1), -decay);
+    std::fill(worst.begin(), worst.end(), 0.0);
+    for (int i = 0; i < nm; ++i) {
+      const uint32_t N = 1u << (m_min + i), mask = N - 1;
+      const double* q = excess[i].data();
+      const double* tb = tab[i].data();
+      for (size_t ci = 0; ci < cand.size(); ++ci) {
+        const uint64_t zc = cand[ci];
+        const double acc = pairwise_sum(0, N, [&](uint32_t k) {
+          const double a = gam * tb[(uint32_t)(((uint64_t)k * zc) & mask)];
+          return q[k] + a * (1.0 + q[k]);
+        });
+        e2[ci] = acc / N;
+      }
+      const double emin = *std::min_element(e2.begin(), e2.end());
+      for (size_t ci = 0; ci < cand.size(); ++ci) worst[ci] = std::max(worst[ci], e2[ci] / emin);
+    }
+    const double best = *std::min_element(worst.begin(), worst.end());
+    size_t pick = 0;
+    while (!(worst[pick] <= best * (1.0 + 1e-6))) ++pick;  // ties within a relative 1e-6: smallest candidate
+    z_out[j] = cand[pick];
+    for (int i = 0; i < nm; ++i) {
+      const uint32_t N = 1u << (m_min + i), mask = N - 1;
+      for (uint32_t k = 0; k < N; ++k) {
+        const double a = gam * tab[i][(uint32_t)(((uint64_t)k * cand[pick]) & mask)];
+        excess[i][k] += a * (1.0 + excess[i][k]);
+      }
+    }
+  }
+  return MQ_OK;
+}
+
 mq_status mq_lattice_points_device(mq_ctx* c, int32_t level, uint32_t k0, uint32_t k1, double* d_Y) {
   if (!c) return MQ_EINVAL;
   mq_status st = check_level_ready(c, level);
@@ -1076,8 +1349,9 @@ mq_status mq_lattice_points_device(mq_ctx* c, int32_t level, uint32_t k0, uint32
   const mq_level& lv = c->levels[level];
   if (k1 < k0 || k1 > lv.N || !d_Y) return fail(c, MQ_EINVAL, "bad point range or output");
   MQ_CUDA(c, cudaSetDevice(c->device));
-  MQ_LAUNCH(c, mq::launch_lattice_points(c->d_z[level], lv.N, c->d_delta[level], lv.R, lv.s, k0, (int)(k1 - k0), d_Y,
-                                       c->stream));
+  const int mb = c->mbits[level];
+  MQ_LAUNCH(c, mq::launch_lattice_points(c->d_z[level], mb ? (1u << mb) : lv.N, c->d_delta[level], lv.R, lv.s, k0,
+                                       (int)(k1 - k0), mb, d_Y, c->stream));
   MQ_CUDA(c, cudaStreamSynchronize(c->stream));
   return MQ_OK;
 }

@@ -16,15 +16,19 @@
 namespace mq {
 namespace {
 
+// mbits > 0: the embedded rule of 2^mbits points in radical-inverse order, point k taking the
+// lattice index rev(k) (the mbits-bit reversal of k) with N = 2^mbits, so the first 2^m points are
+// the 2^m-point rule (Sec. 2.5, embedded lattice rules)
 __global__ void lattice_kernel(const uint32_t* __restrict__ z, uint32_t N, const double* __restrict__ delta, int R,
-                               int s, uint32_t k0, int npts, double* __restrict__ Y) {
+                               int s, uint32_t k0, int npts, int mbits, double* __restrict__ Y) {
   const size_t tot = (size_t)R * npts * s;
   for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += (size_t)gridDim.x * blockDim.x) {
     const int j = (int)(q % s);
     const size_t b = q / s;
     const int kk = (int)(b % npts);
     const int r = (int)(b / npts);
-    const uint64_t k = (uint64_t)k0 + (uint64_t)kk;
+    uint64_t k = (uint64_t)k0 + (uint64_t)kk;
+    if (mbits > 0) k = (uint64_t)(__brev((uint32_t)k) >> (32 - mbits));
     const uint64_t m = (k * (uint64_t)z[j]) % (uint64_t)N;
     double t = (double)m / (double)N + delta[(size_t)r * s + j];
     if (t >= 1.0) t -= 1.0;
@@ -114,10 +118,11 @@ int grid_for(size_t tot, int threads) {
 }  // namespace
 
 cudaError_t launch_lattice_points(const uint32_t* d_z, uint32_t N, const double* d_delta, int R, int s, uint32_t k0,
-                                  int npts, double* d_Y, cudaStream_t st) {
+                                  int npts, int mbits, double* d_Y, cudaStream_t st) {
   const size_t tot = (size_t)R * npts * s;
   if (tot == 0) return cudaSuccess;
-  lattice_kernel<<<grid_for(tot, 256), 256, 0, st>>>(d_z, N, d_delta, R, s, k0, npts, d_Y);
+  if (mbits < 0 || mbits > 31 || (mbits > 0 && N != (1u << mbits))) return cudaErrorInvalidValue;
+  lattice_kernel<<<grid_for(tot, 256), 256, 0, st>>>(d_z, N, d_delta, R, s, k0, npts, mbits, d_Y);
   return cudaGetLastError();
 }
 

@@ -33,8 +33,11 @@ struct SampleLaunch {
   int max_outer;
   int nu;                  // Jacobi sweeps before and after each coarse-grid correction
   double omega;            // Jacobi damping
-  int coarse_only;         // also write the padded coarse eigenvectors to u_pad
-  double* u_pad;           // [B][(nc+1)^2] when coarse_only
+  int coarse_only;         // the fine solves of mode 2 run elsewhere (streaming tier)
+  double* u_pad;           // NULL or [B][(nc+1)^2]: the padded coarse eigenvectors are written here
+  const double* u_in;      // NULL or [B][(nc+1)^2]: coarse pairs given (no coarse eigensolve), with
+                           // lambda_H in out[b][0] (the reuse scheme across levels)
+  int prev_given;          // lambda^{l-1} given in out[b][2] (no previous-level solve)
   int mode_f, mode_p;      // fine / previous-fine solve: 0 in the kernel (inner precision T),
                            // 1 in the kernel with an FP64 inner solve, 2 elsewhere (streaming)
 };
@@ -95,14 +98,26 @@ cudaError_t set_sample_smem(int mixed, int bytes);
 cudaError_t raise_smem_limit(const void* func, int bytes);
 
 // Coefficient building blocks (mq_coef.cu)
+// mbits > 0: embedded rule in radical-inverse order with N = 2^mbits (point k uses index rev(k))
 cudaError_t launch_lattice_points(const uint32_t* d_z, uint32_t N, const double* d_delta, int R, int s,
-                                  uint32_t k0, int npts, double* d_Y, cudaStream_t st);
+                                  uint32_t k0, int npts, int mbits, double* d_Y, cudaStream_t st);
 cudaError_t launch_psi_table(int n, int s, const int* d_k1, const int* d_k2, const double* d_cj,
                              double* d_psi, cudaStream_t st);
 cudaError_t launch_coef_gemm_f64(const double* d_Y, int ldy, int B, int s, const double* d_psi, int nT,
                                  double a0, double* d_a, cudaStream_t st);
 cudaError_t launch_apply_operator(int n, int B, const double* d_a, int which, double sigma,
                                   const double* d_x, double* d_y, double* d_scratch, cudaStream_t st);
+// reuse scheme store: u0 [R][N0][V] padded level-0 eigenvectors, lam [R][N_l] per level.
+// Gather for the samples b = r * npts + i of a pass (point k = k0 + i): u_pad[b] = u0[r][k],
+// out[b][0] = lam0[r][k], out[b][2] = lamp[r][k] (lamp may be NULL).
+cudaError_t launch_reuse_gather(int R, int npts, uint32_t k0, size_t V, const double* d_u0, const double* d_lam0,
+                                uint32_t ld0, const double* d_lamp, uint32_t ldp, double* d_upad, double* d_out,
+                                cudaStream_t st);
+// Scatter after a pass: lam[r][k] = out[b][1]; with d_u0, also u0[r][k] = u_pad[b] and
+// lam0[r][k] = out[b][0].
+cudaError_t launch_reuse_scatter(int R, int npts, uint32_t k0, size_t V, const double* d_upad, const double* d_out,
+                                 double* d_lam, uint32_t ldl, double* d_u0, double* d_lam0, uint32_t ld0,
+                                 cudaStream_t st);
 cudaError_t launch_shift_sums(const double* d_out, const int* d_stat, int R, int npts, double* d_sums,
                               int* d_flags, cudaStream_t st);
 

@@ -744,9 +744,17 @@ __global__ void __launch_bounds__(512) sample_kernel(SampleLaunch P) {
     for (int kk = k0; kk < k1; ++kk) {
       const size_t b = (size_t)r * P.npts + kk;
       int flags = 0;
-      // ---- coarse eigenpair (Algorithm 1 step 1; Algorithm 2 steps 6-7)
+      // ---- coarse eigenpair (Algorithm 1 step 1; Algorithm 2 steps 6-7), or, in the reuse scheme
+      // across levels, the level-0 eigenpair of this point given in u_in / out[b][0]
       CoarseWS& cw = cws;
-      {
+      double lamH;
+      int eit = 0;
+      if (P.u_in) {
+        const size_t Vc = gsz(nc);
+        for_all(Vc, [&](size_t q) { cw.uprev[q] = P.u_in[b * Vc + q]; });
+        lamH = P.out[b * 4 + 0];
+        __syncthreads();
+      } else {
         // the fine solves of the previous point reused this memory: clear the coarse vectors
         // (rings must be zero; interiors are written before use)
         double* vs[11] = {cw.wx, cw.wy, cw.x, cw.Ax, cw.Mx, cw.w, cw.Aw, cw.Mw, cw.p, cw.Ap, cw.Mp};
@@ -755,31 +763,30 @@ __global__ void __launch_bounds__(512) sample_kernel(SampleLaunch P) {
         zero_vec(cw.w32, nc);
         zero_mg(cw.mg);
         __syncthreads();
+        const double* ac = P.a_c + b * ncT;
+        if (!build_mg<float>(cw.mg, ac, nc, red)) flags |= kFlagBadCoef;
+        weights_from_cells<double, double>(nc, ac, ac + (size_t)nc * nc, cw.wx, cw.wy);
+        if (kk == k0) {
+          const float inc = 1.0f / (float)nc;
+          for_interior(nc, [&](int p, int i, int j) { cw.x[p] = (double)(sinpif(i * inc) * sinpif(j * inc)); });
+        } else {
+          for_interior(nc, [&](int p, int, int) { cw.x[p] = cw.uprev[p]; });
+        }
+        __syncthreads();
+        eit = lobpcg(cw, nc, P.tol_eig, P.max_eig_it, P.nu, omega, red, &esh, lamH);
+        if (eit < 0) flags |= kFlagEigNoConv;
+        for_interior(nc, [&](int p, int, int) { cw.uprev[p] = cw.x[p]; });
+        if (P.u_out) {
+          for_interior(nc, [&](int p, int i, int j) {
+            P.u_out[b * (size_t)(nc - 1) * (nc - 1) + (j - 1) * (nc - 1) + (i - 1)] = cw.x[p];
+          });
+        }
+        if (P.u_pad) {
+          const size_t Vc = gsz(nc);
+          for_all(Vc, [&](size_t q) { P.u_pad[b * Vc + q] = cw.x[q]; });
+        }
+        __syncthreads();
       }
-      const double* ac = P.a_c + b * ncT;
-      if (!build_mg<float>(cw.mg, ac, nc, red)) flags |= kFlagBadCoef;
-      weights_from_cells<double, double>(nc, ac, ac + (size_t)nc * nc, cw.wx, cw.wy);
-      if (kk == k0) {
-        const float inc = 1.0f / (float)nc;
-        for_interior(nc, [&](int p, int i, int j) { cw.x[p] = (double)(sinpif(i * inc) * sinpif(j * inc)); });
-      } else {
-        for_interior(nc, [&](int p, int, int) { cw.x[p] = cw.uprev[p]; });
-      }
-      __syncthreads();
-      double lamH;
-      const int eit = lobpcg(cw, nc, P.tol_eig, P.max_eig_it, P.nu, omega, red, &esh, lamH);
-      if (eit < 0) flags |= kFlagEigNoConv;
-      for_interior(nc, [&](int p, int, int) { cw.uprev[p] = cw.x[p]; });
-      if (P.u_out) {
-        for_interior(nc, [&](int p, int i, int j) {
-          P.u_out[b * (size_t)(nc - 1) * (nc - 1) + (j - 1) * (nc - 1) + (i - 1)] = cw.x[p];
-        });
-      }
-      if (P.coarse_only) {
-        const size_t Vc = gsz(nc);
-        for_all(Vc, [&](size_t q) { P.u_pad[b * Vc + q] = cw.x[q]; });
-      }
-      __syncthreads();
       // ---- fine two-grid updates (Algorithm 1 steps 2-4; Algorithm 2 steps 9-14); a solve of
       // mode 2 runs elsewhere and leaves the coarse eigenvalue as a placeholder
       double lf = lamH, lp = P.np > 0 ? lamH : 0.0;
@@ -791,7 +798,9 @@ __global__ void __launch_bounds__(512) sample_kernel(SampleLaunch P) {
           lf = twogrid_fine<double>(fws64, fine_base, P.nf, P.a_f + b * nfT, cw.uprev, nc, lamH, P, red, &msh64, itf, of,
                                     flags);
       }
-      if (P.np > 0 && !P.direct_p) {
+      if (P.prev_given) {
+        lp = P.out[b * 4 + 2];  // every thread reads it before thread 0 rewrites the same value below
+      } else if (P.np > 0 && !P.direct_p) {
         if (P.mode_p == 0)
           lp = twogrid_fine<T>(fws, fine_base, P.np, P.a_p + b * npT, cw.uprev, nc, lamH, P, red, &msh, itp, op, flags);
         else if (P.mode_p == 1)
@@ -858,7 +867,62 @@ __global__ void shift_sums_kernel(const double* __restrict__ out, const int* __r
   if (threadIdx.x == 0) sums[r] = o[0];
 }
 
+// reuse scheme: gather the stored level-0 pairs (and the level below's values) of a pass's samples
+__global__ void reuse_gather_kernel(int R, int npts, uint32_t k0, size_t V, const double* __restrict__ u0,
+                                    const double* __restrict__ lam0, uint32_t ld0, const double* __restrict__ lamp,
+                                    uint32_t ldp, double* __restrict__ upad, double* __restrict__ out) {
+  const size_t B = (size_t)R * npts, tot = B * V;
+  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += (size_t)gridDim.x * blockDim.x) {
+    const size_t b = q / V, e = q % V;
+    const size_t r = b / npts, k = k0 + b % npts;
+    upad[q] = u0[(r * ld0 + k) * V + e];
+    if (e == 0) {
+      out[b * 4 + 0] = lam0[r * ld0 + k];
+      out[b * 4 + 2] = lamp ? lamp[r * ldp + k] : 0.0;
+    }
+  }
+}
+
+__global__ void reuse_scatter_kernel(int R, int npts, uint32_t k0, size_t V, const double* __restrict__ upad,
+                                     const double* __restrict__ out, double* __restrict__ lam, uint32_t ldl,
+                                     double* __restrict__ u0, double* __restrict__ lam0, uint32_t ld0) {
+  const size_t B = (size_t)R * npts, tot = B * (u0 ? V : 1);
+  const size_t per = u0 ? V : 1;
+  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += (size_t)gridDim.x * blockDim.x) {
+    const size_t b = q / per, e = q % per;
+    const size_t r = b / npts, k = k0 + b % npts;
+    if (u0) u0[(r * ld0 + k) * V + e] = upad[q];
+    if (e == 0) {
+      lam[r * ldl + k] = out[b * 4 + 1];
+      if (lam0) lam0[r * ld0 + k] = out[b * 4 + 0];
+    }
+  }
+}
+
+int grid_of(size_t n) {
+  size_t g = (n + 255) / 256;
+  return (int)(g < 1 ? 1 : (g > 152 * 32 ? 152 * 32 : g));
+}
+
 }  // namespace
+
+cudaError_t launch_reuse_gather(int R, int npts, uint32_t k0, size_t V, const double* d_u0, const double* d_lam0,
+                                uint32_t ld0, const double* d_lamp, uint32_t ldp, double* d_upad, double* d_out,
+                                cudaStream_t st) {
+  const size_t tot = (size_t)R * npts * V;
+  if (tot == 0) return cudaSuccess;
+  reuse_gather_kernel<<<grid_of(tot), 256, 0, st>>>(R, npts, k0, V, d_u0, d_lam0, ld0, d_lamp, ldp, d_upad, d_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reuse_scatter(int R, int npts, uint32_t k0, size_t V, const double* d_upad, const double* d_out,
+                                 double* d_lam, uint32_t ldl, double* d_u0, double* d_lam0, uint32_t ld0,
+                                 cudaStream_t st) {
+  const size_t tot = (size_t)R * npts * (d_u0 ? V : 1);
+  if (tot == 0) return cudaSuccess;
+  reuse_scatter_kernel<<<grid_of(tot), 256, 0, st>>>(R, npts, k0, V, d_upad, d_out, d_lam, ldl, d_u0, d_lam0, ld0);
+  return cudaGetLastError();
+}
 
 size_t sample_slab_bytes(int nf, int nc, int np, int mixed) {
   return mixed ? slab_size<float>(nf, nc, np) : slab_size<double>(nf, nc, np);

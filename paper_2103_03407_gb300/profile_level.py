@@ -4,6 +4,11 @@
         --precision mixed [--repeat 2]
 
 Prints the device time and iteration statistics of each evaluation as JSON lines.
+
+    python -m paper_2103_03407_gb300.profile_level --gemm 256 1024 256 [--repeat 2]
+
+runs only the coefficient evaluation a = a0 + Y Psi (mixed precision: the tensor-core GEMM) on
+mesh 1/n with s terms for B random parameter vectors.
 """
 from __future__ import annotations
 
@@ -27,7 +32,11 @@ def main():
     ap.add_argument("--stream-min", type=int, default=0, help="fine meshes from 1/n on run in the streaming tier")
     ap.add_argument("--threads", type=int, default=0, help="threads per CTA of the per-sample kernel (0: default)")
     ap.add_argument("--nu", type=int, default=0, help="Jacobi steps per side of the V-cycle (0: default)")
+    ap.add_argument("--gemm", type=int, nargs=3, metavar=("N", "S", "B"),
+                    help="time the coefficient evaluation alone on mesh 1/N with S terms for B samples")
     a = ap.parse_args()
+    if a.gemm:
+        return gemm(a)
     from paper_2103_03407_gb300 import binding, build
     from synthetic_inputs import WORKLOADS, shifts
 
@@ -55,6 +64,34 @@ def main():
             st = ctx.mq_get_stats()
             print(json.dumps({"level": l, "points": n, "samples": n * wl.levels[l].R, "stream_min": a.stream_min,
                               "threads_req": a.threads, "nu": a.nu, **st}))
+    ctx.close()
+
+
+def gemm(a):
+    import time
+
+    import torch
+
+    from paper_2103_03407_gb300 import binding, build
+    from synthetic_inputs import Level, random_points
+
+    build.build()
+    n, s, B = a.gemm
+    ctx = binding.Context(0)
+    ctx.mq_set_coefficient(1.0, s, 0, 2.0)
+    ctx.mq_set_levels([Level(n, n, s, s, 1, 2)])
+    ctx.mq_set_precision(binding.MQ_PREC_MIXED if a.precision == "mixed" else binding.MQ_PREC_FP64)
+    Y = torch.from_numpy(random_points(1, B, s)).cuda()
+    out = torch.empty((B, 2 * n * n), dtype=torch.float64, device="cuda")
+    ctx.mq_coefficients_device(n, s, Y, B, s, out)  # builds the tables
+    for _ in range(a.repeat):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        ctx.mq_coefficients_device(n, s, Y, B, s, out)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        flops = 2.0 * B * s * 2 * n * n
+        print(json.dumps({"gemm": [n, s, B], "ms": dt * 1e3, "algorithmic_tflops": flops / dt / 1e12}))
     ctx.close()
 
 

@@ -99,6 +99,15 @@ WORKLOADS = {
         [Level(8, 8, 64, 64, 2048, 8)] + [Level(8 << l, 8, 64, _ceil_sqrt(64), 2048 >> l, 8) for l in range(1, 4)],
         seed=5, precision="mixed", tol=1e-10, a0=float(np.pi / np.sqrt(2.0)), decay=4.0 / 3.0, family=1,
     ),
+    # shared shifts and nested points with reuse (Sec. 4.3, after Algorithm 2): h_l = 1/16 .. 1/128,
+    # s_l = 16 .. 128, level 0 direct on (h_0, s_0) = (1/16, 16); every level l >= 1 takes its coarse
+    # pair from level 0 (H_l = h_0, S_l = s_0); one embedded lattice rule for N = 2^9 .. 2^12 in
+    # radical-inverse order; one set of 16 shifts drawn with s_L = 128 components
+    "shared_mlqmc4_h16_128": Workload(
+        "shared_mlqmc4_h16_128",
+        [Level(16, 16, 16, 16, 4096, 16)] + [Level(16 << l, 16, 16 << l, 16, 4096 >> l, 16) for l in range(1, 4)],
+        seed=6, precision="mixed", tol=1e-10, extra={"shared": True, "m_min": 9, "m_max": 12},
+    ),
     # h = 1/1024 (1,046,529 dofs), H = 1/64, s = 1024, S = 32, 32 points x 16 shifts
     "stress_h1024_s1024": Workload(
         "stress_h1024_s1024",
@@ -112,6 +121,24 @@ def shifts(seed: int, levels: List[Level]) -> List[np.ndarray]:
     """Random shifts Delta_l in [0,1)^{R x s_l}, drawn level by level from one generator."""
     rng = np.random.default_rng(seed)
     return [rng.random((lv.R, lv.s)) for lv in levels]
+
+
+def shifts_for_rank(seed: int, levels: List[Level], rank: int, world: int) -> List[np.ndarray]:
+    """The shifts of one rank when `world` processes share one workload: R * world shifts per level
+    drawn as in ``shifts`` (level by level from one generator), rank i taking rows
+    [i R, (i + 1) R).  With world = 1 these are the workload's own shifts."""
+    rng = np.random.default_rng(seed)
+    return [rng.random((lv.R * world, lv.s))[rank * lv.R:(rank + 1) * lv.R] for lv in levels]
+
+
+def shared_shifts(seed: int, levels: List[Level], rank: int = 0, world: int = 1) -> List[np.ndarray]:
+    """One set of shifts Delta in [0,1)^{R x s_L} for every level (the reuse scheme): level l takes
+    the first s_l components.  With `world` processes, R * world shifts are drawn and rank i takes
+    rows [i R, (i + 1) R)."""
+    rng = np.random.default_rng(seed)
+    R = levels[0].R
+    full = rng.random((R * world, max(lv.s for lv in levels)))[rank * R:(rank + 1) * R]
+    return [full[:, : lv.s].copy() for lv in levels]
 
 
 def random_points(seed: int, count: int, s: int) -> np.ndarray:

@@ -9,7 +9,7 @@ import sys
 import numpy as np
 import pytest
 
-from synthetic_inputs import WORKLOADS, shifts
+from synthetic_inputs import WORKLOADS, shared_shifts, shifts
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -21,10 +21,19 @@ def _pow2(n):
 @pytest.mark.parametrize("name", sorted(WORKLOADS))
 def test_workload_levels_follow_the_readings(name):
     wl = WORKLOADS[name]
+    shared = wl.extra.get("shared", False)
     for l, lv in enumerate(wl.levels):
         # nested uniform meshes: powers of two, the coarse mesh divides the fine one
         assert _pow2(lv.n_fine) and _pow2(lv.n_coarse) and lv.n_coarse <= lv.n_fine
         direct = lv.n_fine == lv.n_coarse and lv.s == lv.S
+        if shared:
+            # reuse scheme: level 0 direct, every other level on level 0's coarse problem
+            # (H_l = h_0, S_l = s_0 >= ceil(sqrt(s_l))), point counts powers of two
+            lv0 = wl.levels[0]
+            assert (l == 0 and direct) or (lv.n_coarse == lv0.n_fine and lv.S == lv0.s)
+            assert lv.S >= math.isqrt(lv.s - 1) + 1 and _pow2(lv.N) and lv.N <= 1 << wl.extra["m_max"]
+            assert lv.N >= 1 << wl.extra["m_min"] and lv.R == lv0.R
+            continue
         # coarse truncation S = ceil(sqrt(s)) on two-grid levels (a direct level uses S = s)
         assert direct or lv.S == math.isqrt(lv.s - 1) + 1
         assert 1 <= lv.S <= lv.s and lv.N >= 1 and lv.R >= 2
@@ -43,6 +52,14 @@ def test_shifts_are_seeded_uniform_draws(name):
     for lv, d, e in zip(wl.levels, ds, again):
         assert d.shape == (lv.R, lv.s) and np.array_equal(d, e)
         assert np.all((d >= 0.0) & (d < 1.0))
+
+
+def test_shared_shifts_are_prefixes_of_one_draw():
+    wl = WORKLOADS["shared_mlqmc4_h16_128"]
+    ds = shared_shifts(wl.seed, wl.levels)
+    for lv, d in zip(wl.levels, ds):
+        assert d.shape == (lv.R, lv.s) and np.array_equal(d, ds[-1][:, : lv.s])
+    assert np.array_equal(ds[-1], shared_shifts(wl.seed, wl.levels)[-1])
 
 
 def test_bench_reference_arm_prints_the_contract_line():

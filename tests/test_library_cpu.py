@@ -37,7 +37,14 @@ def test_cbc_matches_oracle(lib, N, s):
     assert np.array_equal(binding.mq_cbc_lattice(N, s), lattice.cbc(N, s))
 
 
+@pytest.mark.parametrize("m_min,m_max,s", [(1, 4, 4), (3, 7, 6), (5, 5, 5), (6, 9, 12)])
+def test_embedded_cbc_matches_oracle(lib, m_min, m_max, s):
+    assert np.array_equal(binding.mq_cbc_embedded_lattice(m_min, m_max, s), lattice.embedded_cbc(m_min, m_max, s))
+
+
 def test_cbc_rejects_bad_arguments(lib):
+    with pytest.raises(binding.MQError):
+        binding.mq_cbc_embedded_lattice(4, 3, 2)
     with pytest.raises(binding.MQError):
         binding.mq_cbc_lattice(1, 3)
 

@@ -110,3 +110,80 @@ def test_sample_level_difference_uses_one_coarse_pair():
     assert d == lam_l - lam_p
     # level 0: lambda^{-1} = 0
     assert mlqmc.sample_level(pv, None, y)[3] == mlqmc.sample_level(pv, None, y)[1]
+
+
+# ---- embedded lattice rules and the shared-shift reuse scheme (Sec. 2.5; Sec. 4.3 after Alg. 2)
+
+@pytest.mark.parametrize("m,s", [(3, 3), (5, 4), (7, 5)])
+def test_embedded_cbc_with_one_size_is_the_fixed_size_cbc(m, s):
+    # one N: the worst ratio orders the candidates as the error itself, over the same candidates
+    assert np.array_equal(lattice.embedded_cbc(m, m, s), lattice.cbc(1 << m, s))
+
+
+def test_embedded_cbc_brute_force():
+    # every component re-derived with the plain double-loop error formula: the smallest candidate
+    # whose worst ratio over N = 2, 4, 8, 16 is (within 1e-12) the minimum
+    m_min, m_max, s = 1, 4, 4
+    gamma = [(j + 1) ** -2.0 for j in range(s)]
+    z = lattice.embedded_cbc(m_min, m_max, s)
+    cands = list(range(1, (1 << m_max) // 2, 2))
+    for j in range(s):
+        worst = []
+        for c in cands:
+            ratios = []
+            for m in range(m_min, m_max + 1):
+                N = 1 << m
+                errs = [lattice.cbc_error2(list(z[:j]) + [cc], N, gamma[: j + 1]) for cc in cands]
+                ratios.append(lattice.cbc_error2(list(z[:j]) + [c], N, gamma[: j + 1]) / min(errs))
+            worst.append(max(ratios))
+        best = min(worst)
+        assert z[j] == next(c for c, w in zip(cands, worst) if w <= best + 1e-12)
+
+
+def test_embedded_points_are_nested_rules():
+    # the first 2^m points in radical-inverse order are the 2^m-point rule, for every m
+    m_max, s = 6, 3
+    z = lattice.embedded_cbc(2, m_max, s)
+    delta = np.array([0.3, 0.71, 0.05])
+    for m in range(0, m_max + 1):
+        N = 1 << m
+        emb = lattice.embedded_points(z, m_max, delta, np.arange(N))
+        rule = lattice.points(z, N, delta, np.arange(N))
+        key = lambda P: sorted(map(tuple, np.round(P, 12)))
+        assert key(emb) == key(rule)
+    assert np.array_equal(np.sort(lattice.bit_reverse(np.arange(64), 6)), np.arange(64))
+    assert lattice.bit_reverse(1, 6) == 32 and lattice.bit_reverse(3, 6) == 48
+
+
+def test_shared_samples_equal_algorithm_2_recomputed():
+    # reusing the level-0 eigenpair and the level below's value gives exactly what Algorithm 2
+    # computes from scratch at the same point with H_l = h_0 and S_l = s_0
+    levels = [Level(8, 8, 4, 4, 16, 2), Level(16, 8, 8, 4, 8, 2), Level(32, 8, 16, 4, 4, 2)]
+    z = lattice.embedded_cbc(2, 4, 16)
+    delta = np.random.default_rng(0).random(16)
+    ks = [0, 1, 3, 5, 9]
+    out = mlqmc.shared_samples(levels, z, 4, delta, ks)
+    Y = lattice.embedded_points(z, 4, delta, ks)
+    for i, k in enumerate(ks):
+        for l, lv in enumerate(levels):
+            if k >= lv.N:
+                assert np.all(np.isnan(out[l, i]))
+                continue
+            ref = mlqmc.sample_level(lv, levels[l - 1] if l else None, Y[i])
+            assert np.array_equal(out[l, i], np.array(ref))
+
+
+def test_shared_shift_estimate():
+    # per-shift totals 1.0+0.1, 2.0-0.1, 3.0+0.3: mean 2.1, sample variance of the mean
+    q = np.array([[1.0, 2.0, 3.0], [0.1, -0.1, 0.3]])
+    m, se, qhat, vhat = mlqmc.estimate_shared(q)
+    tot = np.array([1.1, 1.9, 3.3])
+    assert m == pytest.approx(2.1, rel=1e-15)
+    assert se == pytest.approx(math.sqrt(((tot - 2.1) ** 2).sum() / 6.0), rel=1e-14)
+    assert qhat[0] == pytest.approx(2.0) and qhat[1] == pytest.approx(0.1)
+    # one level: the same as the independent-level estimate
+    m1, se1, _, _ = mlqmc.estimate_shared(q[:1])
+    m2, se2, _, _ = mlqmc.estimate([q[0]])
+    assert m1 == pytest.approx(m2, rel=1e-15) and se1 == pytest.approx(se2, rel=1e-14)
+    with pytest.raises(ValueError):
+        mlqmc.estimate_shared(q[:, :1])
