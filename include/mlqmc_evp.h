@@ -175,6 +175,32 @@ mq_status mq_set_tier(mq_ctx* ctx, int32_t stream_min_n);
  * on it beyond rounding order. */
 mq_status mq_set_cta_threads(mq_ctx* ctx, int32_t level, int32_t threads);
 
+/* Launch configuration of one level (0 <= level < 64), overriding the context-wide defaults:
+ * tier -1 (fine solve tier by mesh size, mq_set_tier), 0 (fine solves inside the per-sample
+ * kernel) or 1 (streaming tier); threads as in mq_set_cta_threads (0: default); nu as in
+ * mq_set_smoothing for every solve of the level (0: default).  Results agree to the solver
+ * tolerances whatever the configuration. */
+mq_status mq_set_level_config(mq_ctx* ctx, int32_t level, int32_t tier, int32_t threads, int32_t nu);
+
+/* Chosen configuration of a level (mq_autotune_level). */
+typedef struct {
+  int32_t tier, threads, nu;  /* as in mq_set_level_config */
+  double ms;                  /* device time of the probe with it (or the cached time) */
+  int32_t from_cache;         /* 1: read from the cache file, nothing was timed */
+  int32_t tried;              /* configurations timed */
+} mq_tune_choice;
+
+/* Autotuner: times the level on its first `points` lattice points (all shifts) with every
+ * candidate configuration -- the fine solve's tier when the fine mesh lies between 1/16 and 1/128,
+ * the per-sample kernel's threads per CTA (64, 128, 256) and the smoothing (1 or 2 Jacobi steps per
+ * side) -- each twice, keeps the fastest (CUDA events around the level's evaluation, second run)
+ * and applies it with mq_set_level_config.  cache_path: NULL, or a text file of earlier choices
+ * keyed by the GPU, the precision, the level's meshes, truncations, shifts and probe size: a hit
+ * applies the stored choice without timing; a miss appends the new one.  The probes leave the
+ * estimator sums, timers and launch count as they were. */
+mq_status mq_autotune_level(mq_ctx* ctx, int32_t level, uint32_t points, const char* cache_path,
+                            mq_tune_choice* choice);
+
 /* Evaluate level `level` at lattice indices k in [k0, k1) for every shift (Algorithm 2, steps
  * 5-15): per sample the coarse eigenpair on (H_l, S_l), lambda^l by Algorithm 1 on (h_l, s_l)
  * and, for l > 0, lambda^{l-1} on (h_{l-1}, s_{l-1}) from the same coarse pair.
@@ -206,6 +232,29 @@ mq_status mq_eval_level_device(mq_ctx* ctx, int32_t level, uint32_t k0, uint32_t
 mq_status mq_eval_levels_device(mq_ctx* ctx, int32_t nlevels, const int32_t* levels, double* const* d_per_sample,
                                 double* const* d_shift_sums);
 
+/* Graph schedule (Algorithm 2 over several levels as one CUDA graph).  mq_graph_capture records,
+ * as one CUDA graph, the evaluation of the point ranges [k0s[i], k1s[i]) of levels levels[i] in
+ * the order given, with the device outputs of mq_eval_level_device (d_per_sample[i],
+ * d_shift_sums[i]; either array, or any entry, may be NULL; the buffers must stay valid while
+ * the graph is kept).  It first runs the same evaluations once as a rehearsal (which allocates
+ * every buffer and builds the tables; the estimator state is put back afterwards), then captures
+ * them on the context stream: the streaming tier's refinement and MINRES loops become
+ * conditional WHILE nodes whose conditions the kernels set on the device (no host reads), and the
+ * per-shift sums and sample flags accumulate on the device.  mq_graph_launch replays the graph
+ * with one cudaGraphLaunch, waits for it and adds its sums to the context (mq_estimate), as the
+ * level-by-level calls would; the per-sample results equal theirs bit for bit.  k0s: NULL to
+ * replay the captured ranges, or new start points for ranges of the captured lengths (the offset
+ * reaches the kernels through device memory).  The per-level timers are not updated by the graph.
+ * Any setter, and any call that has to enlarge a buffer the graph uses, drops the graph
+ * (mq_graph_launch then returns MQ_ESTATE).  The context stream must not be the legacy default
+ * stream. */
+mq_status mq_graph_capture(mq_ctx* ctx, int32_t nranges, const int32_t* levels, const uint32_t* k0s,
+                           const uint32_t* k1s, double* const* d_per_sample, double* const* d_shift_sums);
+mq_status mq_graph_launch(mq_ctx* ctx, const uint32_t* k0s);
+/* captured: 1 while a graph is held; kernel_nodes: the kernels captured into it (the loop bodies
+ * counted once).  Either output may be NULL. */
+mq_status mq_get_graph_info(mq_ctx* ctx, int32_t* captured, uint64_t* kernel_nodes);
+
 /* Estimate from the sums accumulated so far (eq. tg-mlqmc): Q^(r)_l = sum_k diff / n_l where
  * n_l is the number of points evaluated on level l, Qhat_l = mean_r Q^(r)_l, mean = sum_l Qhat_l,
  * level_var[l] = sum_r (Qhat_l - Q^(r)_l)^2 / (R (R - 1)) (eq. sample_var), std_err =
@@ -229,6 +278,35 @@ mq_status mq_get_sums(mq_ctx* ctx, int32_t level, double* sums, uint64_t* npoint
  * NULL or host [nlevels]. */
 mq_status mq_estimate_sums(int32_t nlevels, const int32_t* R, const double* sums, const uint64_t* npoints,
                            int32_t shared, double* mean, double* std_err, double* level_mean, double* level_var);
+
+/* Result of mq_run_adaptive. */
+typedef struct {
+  int32_t L;               /* finest level used */
+  int32_t converged;       /* 1: variance and bias tests passed; 0: stopped at the last level or at
+                              the point capacity of the levels */
+  int32_t doublings;       /* point doublings performed */
+  int32_t levels_added;    /* levels started (three initial ones included) */
+  uint32_t N[32];          /* points per shift on levels 0..L (0 beyond) */
+  double mean, std_err;    /* estimate over levels 0..L, std_err = sqrt(sum_l level_var[l]) */
+  double level_mean[32], level_var[32];  /* Qhat_l and eq. sample_var per level */
+} mq_adaptive_result;
+
+/* The adaptive choice of the point counts N_l and of the number of levels (Sec. 4.2: the paper
+ * chooses them with the Giles-Waterhouse algorithm for multilevel QMC).  Reading implemented:
+ *   1. levels 0..2 start with n_init points each (every level needs an embedded lattice,
+ *      mq_set_lattice_embedded, so its points can be doubled; its N is the largest count allowed);
+ *   2. while sum_l level_var > eps^2 / 2 (eq. sample_var): double the points of the level with the
+ *      largest level_var / (C_l N_l) among those that can still double (ties: the lower level),
+ *      C_l = the fine unknowns solved per sample ((n_l - 1)^2, plus (n_{l-1} - 1)^2 on a two-grid
+ *      level l > 0); stop (converged = 0) when no level can double;
+ *   3. bias test with weak order alpha (level differences shrink like 2^(-alpha l); 2 for the
+ *      O(h^2) eigenvalue error): max(|Qhat_L|, |Qhat_{L-1}| / 2^alpha) <= (2^alpha - 1) eps / sqrt(2)
+ *      ends the run (converged = 1); otherwise level L + 1 starts with n_init points and step 2
+ *      repeats (converged = 0 when no level is left).
+ * Independent shifts per level (MQ_ESTATE in the reuse scheme).  The context's estimator sums are
+ * reset first and hold the run's sums afterwards.  Returns MQ_ENOCONV (result written) when any
+ * sample hit an iteration cap. */
+mq_status mq_run_adaptive(mq_ctx* ctx, double eps, double alpha, uint32_t n_init, mq_adaptive_result* result);
 
 /* Clear the estimator sums and the per-level timers (keeps levels, lattices and shifts). */
 mq_status mq_reset_sums(mq_ctx* ctx);

@@ -136,3 +136,77 @@ def estimate_shared(level_shift_means):
     var = ((m - tot) ** 2).sum() / (R * (R - 1))
     _, _, qhat, vhat = estimate(q)
     return float(m), float(np.sqrt(var)), qhat, vhat
+
+
+# ---------------------------------------------------------------------------------------------
+# Adaptive choice of the point counts and the number of levels (Sec. 4.2: the adaptive algorithm
+# the paper takes from Giles & Waterhouse for multilevel QMC).  Reading used here:
+#   1. start with levels 0..2, each with n_init points (an embedded rule, so a level's points can
+#      be doubled by evaluating the next n of them);
+#   2. while the sum of the level variances (eq. sample_var) exceeds eps^2 / 2: double the points
+#      of the level with the largest Vhat_l / (C_l N_l) -- the largest variance per unit of the cost
+#      of doubling it (C_l: cost per sample) -- among the levels that can still double (ties: the
+#      lowest level); stop unconverged when none can;
+#   3. bias test with weak order alpha (the level differences shrink like 2^(-alpha l)):
+#      max(|Qhat_L|, |Qhat_{L-1}| / 2^alpha) <= (2^alpha - 1) eps / sqrt(2) ends the run; otherwise
+#      add level L + 1 with n_init points and return to 2 (unconverged when no level is left).
+# Estimate: sum_l Qhat_l with SE = sqrt(sum_l Vhat_l) (independent shifts per level).
+
+def adaptive(evaluate, cost, R: int, eps: float, alpha: float = 2.0, n_init: int = 8, n_max=None,
+             L_max: int = None):
+    """Runs the adaptive algorithm.  evaluate(l, k0, k1) returns the level differences [R, k1 - k0]
+    of level l at points k0 .. k1 - 1; cost[l] is the cost per sample of level l; n_max[l] the
+    points level l can have (default unbounded); L_max the last level available (default
+    len(cost) - 1).  Returns a dict with L, N (points per level), mean, std_err, level_mean,
+    level_var, converged, and the history of (level, new N) doublings and level additions."""
+    L_max = len(cost) - 1 if L_max is None else L_max
+    n_max = n_max or [1 << 62] * (L_max + 1)
+    sums, N, history = [], [], []
+
+    def add(l, n_new):
+        if l == len(N):
+            sums.append(np.zeros(R))
+            N.append(0)
+        d = np.asarray(evaluate(l, N[l], n_new), dtype=np.float64)
+        sums[l] = sums[l] + d.sum(axis=1)
+        N[l] = n_new
+        history.append((l, n_new))
+
+    def level_stats():
+        means, vars_ = [], []
+        for l in range(len(N)):
+            q = sums[l] / N[l]
+            m = q.sum() / R
+            means.append(m)
+            vars_.append(((m - q) ** 2).sum() / (R * (R - 1)))
+        return means, vars_
+
+    for l in range(min(3, L_max + 1)):
+        add(l, n_init)
+    converged = False
+    while True:
+        means, vars_ = level_stats()
+        stuck = False
+        while sum(vars_) > eps * eps / 2.0:
+            score = [vars_[l] / (cost[l] * N[l]) if 2 * N[l] <= n_max[l] else -1.0 for l in range(len(N))]
+            best = max(score)
+            if best < 0.0:
+                stuck = True
+                break
+            l = score.index(best)
+            add(l, 2 * N[l])
+            means, vars_ = level_stats()
+        if stuck:
+            break
+        L = len(N) - 1
+        if L >= 2:
+            bias = max(abs(means[L]), abs(means[L - 1]) / 2.0 ** alpha)
+            if bias <= (2.0 ** alpha - 1.0) * eps / np.sqrt(2.0):
+                converged = True
+                break
+        if L >= L_max:
+            break
+        add(L + 1, n_init)
+    means, vars_ = level_stats()
+    return {"L": len(N) - 1, "N": list(N), "mean": float(sum(means)), "std_err": float(np.sqrt(sum(vars_))),
+            "level_mean": means, "level_var": vars_, "converged": converged, "history": history}

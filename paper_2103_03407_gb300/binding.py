@@ -29,7 +29,8 @@ EXPORTS = [
     "mq_get_level_timing", "mq_get_kernel_timing", "mq_get_launch_count", "mq_eval_point",
     "mq_get_stats", "mq_last_error", "mq_cbc_lattice", "mq_lattice_points_device", "mq_coefficients_device",
     "mq_apply_operator_device", "mq_twogrid_samples_noalloc", "mq_set_lattice_embedded", "mq_set_reuse",
-    "mq_cbc_embedded_lattice", "mq_get_sums", "mq_estimate_sums",
+    "mq_cbc_embedded_lattice", "mq_get_sums", "mq_estimate_sums", "mq_run_adaptive", "mq_set_level_config",
+    "mq_autotune_level", "mq_graph_capture", "mq_graph_launch", "mq_get_graph_info",
 ]
 
 
@@ -46,6 +47,17 @@ class MQNoConvergence(MQError):
 class mq_level(C.Structure):
     _fields_ = [("n_fine", C.c_int32), ("n_coarse", C.c_int32), ("s", C.c_int32), ("S", C.c_int32),
                 ("N", C.c_uint32), ("R", C.c_int32)]
+
+
+class mq_adaptive_result(C.Structure):
+    _fields_ = [("L", C.c_int32), ("converged", C.c_int32), ("doublings", C.c_int32), ("levels_added", C.c_int32),
+                ("N", C.c_uint32 * 32), ("mean", C.c_double), ("std_err", C.c_double),
+                ("level_mean", C.c_double * 32), ("level_var", C.c_double * 32)]
+
+
+class mq_tune_choice(C.Structure):
+    _fields_ = [("tier", C.c_int32), ("threads", C.c_int32), ("nu", C.c_int32), ("ms", C.c_double),
+                ("from_cache", C.c_int32), ("tried", C.c_int32)]
 
 
 class mq_stats(C.Structure):
@@ -84,6 +96,13 @@ def load(path: str = LIB_PATH):
         "mq_set_reuse": ([P, i32], C.c_int),
         "mq_cbc_embedded_lattice": ([i32, i32, i32, f64, C.POINTER(u32)], C.c_int),
         "mq_get_sums": ([P, i32, dp, C.POINTER(C.c_uint64)], C.c_int),
+        "mq_run_adaptive": ([P, f64, f64, u32, C.POINTER(mq_adaptive_result)], C.c_int),
+        "mq_set_level_config": ([P, i32, i32, i32, i32], C.c_int),
+        "mq_graph_capture": ([P, i32, C.POINTER(i32), C.POINTER(u32), C.POINTER(u32), C.POINTER(C.c_void_p),
+                              C.POINTER(C.c_void_p)], C.c_int),
+        "mq_graph_launch": ([P, C.POINTER(u32)], C.c_int),
+        "mq_get_graph_info": ([P, C.POINTER(i32), C.POINTER(C.c_uint64)], C.c_int),
+        "mq_autotune_level": ([P, i32, u32, C.c_char_p, C.POINTER(mq_tune_choice)], C.c_int),
         "mq_estimate_sums": ([i32, C.POINTER(i32), dp, C.POINTER(C.c_uint64), i32, dp, dp, dp, dp], C.c_int),
         "mq_set_precision": ([P, C.c_int, f64], C.c_int),
         "mq_set_tier": ([P, i32], C.c_int),
@@ -208,6 +227,15 @@ class Context:
     def mq_set_cta_threads(self, level, threads=0):
         self._check(self.lib.mq_set_cta_threads(self.h, int(level), int(threads)))
 
+    def mq_set_level_config(self, level, tier=-1, threads=0, nu=0):
+        self._check(self.lib.mq_set_level_config(self.h, int(level), int(tier), int(threads), int(nu)))
+
+    def mq_autotune_level(self, level, points, cache_path=None):
+        ch = mq_tune_choice()
+        path = cache_path.encode() if cache_path else None
+        self._check(self.lib.mq_autotune_level(self.h, int(level), int(points), path, C.byref(ch)))
+        return {k: getattr(ch, k) for k, _ in ch._fields_}
+
     def mq_set_tier(self, stream_min_n=0):
         self._check(self.lib.mq_set_tier(self.h, int(stream_min_n)))
 
@@ -235,6 +263,26 @@ class Context:
         ss = (C.c_void_p * n)(*[_tptr(t) for t in d_shift_sums]) if d_shift_sums is not None else None
         self._check(self.lib.mq_eval_levels_device(self.h, n, lv, ps, ss))
 
+    def mq_graph_capture(self, ranges, d_per_sample=None, d_shift_sums=None):
+        """ranges: list of (level, k0, k1) evaluated in order as one CUDA graph; device outputs as in
+        mq_eval_level_device (lists of tensors or None)."""
+        n = len(ranges)
+        lv = (C.c_int32 * n)(*[int(r[0]) for r in ranges])
+        k0 = (C.c_uint32 * n)(*[int(r[1]) for r in ranges])
+        k1 = (C.c_uint32 * n)(*[int(r[2]) for r in ranges])
+        ps = (C.c_void_p * n)(*[_tptr(t) for t in d_per_sample]) if d_per_sample is not None else None
+        ss = (C.c_void_p * n)(*[_tptr(t) for t in d_shift_sums]) if d_shift_sums is not None else None
+        self._check(self.lib.mq_graph_capture(self.h, n, lv, k0, k1, ps, ss))
+
+    def mq_graph_launch(self, k0s=None):
+        k = (C.c_uint32 * len(k0s))(*[int(x) for x in k0s]) if k0s is not None else None
+        self._check(self.lib.mq_graph_launch(self.h, k))
+
+    def mq_get_graph_info(self):
+        cap, nodes = C.c_int32(), C.c_uint64()
+        self._check(self.lib.mq_get_graph_info(self.h, C.byref(cap), C.byref(nodes)))
+        return bool(cap.value), nodes.value
+
     def mq_estimate(self):
         L = len(self.levels)
         m, se = C.c_double(), C.c_double()
@@ -248,6 +296,16 @@ class Context:
         sums, n = np.zeros(R), C.c_uint64()
         self._check(self.lib.mq_get_sums(self.h, int(level), _dptr(sums), C.byref(n)))
         return sums, n.value
+
+    def mq_run_adaptive(self, eps, alpha=2.0, n_init=8):
+        """Adaptive N_l and L (see the header); returns the result as a dict."""
+        r = mq_adaptive_result()
+        self._check(self.lib.mq_run_adaptive(self.h, float(eps), float(alpha), int(n_init), C.byref(r)))
+        L = r.L
+        return {"L": L, "converged": bool(r.converged), "doublings": r.doublings, "levels_added": r.levels_added,
+                "N": [int(r.N[l]) for l in range(L + 1)], "mean": r.mean, "std_err": r.std_err,
+                "level_mean": [r.level_mean[l] for l in range(L + 1)],
+                "level_var": [r.level_var[l] for l in range(L + 1)]}
 
     def mq_reset_sums(self):
         self._check(self.lib.mq_reset_sums(self.h))

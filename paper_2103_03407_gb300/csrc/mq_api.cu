@@ -37,6 +37,8 @@ struct mq_ctx {
   bool lanes_stale = true;     // a setter ran since the lanes were built
   int mem_share = 1;           // contexts sharing the free device memory with this one
   std::vector<int> cta_threads;  // per level: threads per CTA of the per-sample kernel (0: default)
+  std::vector<int> lvl_tier;     // per level: -1 tier by mesh size, 0 per-sample kernel, 1 streaming tier
+  std::vector<int> lvl_nu;       // per level: Jacobi sweeps per side of the V-cycle (0: default)
   std::string err;
 
   bool coef_set = false;
@@ -64,6 +66,21 @@ struct mq_ctx {
   DevBuf ru0;                            // [R][N_0][(n_0+1)^2] padded level-0 eigenvectors
   std::vector<DevBuf> rlam;              // per level: [R][N_l] lambda^l (level 0: lambda_{h_0,s_0})
   std::vector<std::vector<uint8_t>> rfilled;  // per level: point k has values
+
+  // graph schedule (mq_graph_capture / mq_graph_launch): the captured evaluation, its body-capture
+  // streams, the device loop counters of the streaming tier, and the device accumulators of the
+  // per-shift sums and sample flags of the captured ranges
+  bool capturing = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t gbody[2] = {nullptr, nullptr};
+  DevBuf gcount, gsums, gflags, gk0;  // gk0: per captured range, the offset of its replayed start
+  std::vector<int> g_levels;
+  std::vector<uint32_t> g_k0, g_k1;      // the ranges of the last launch
+  std::vector<uint32_t> g_cap_k0, g_shift;  // the captured starts; the device offsets (host copy)
+  std::vector<size_t> g_off;       // offset of each captured range's sums in gsums
+  std::vector<int> last_ppp;       // per level: points per pass of the last evaluation
+  uint64_t graph_kernels = 0;      // kernel nodes captured (loop bodies counted once)
 
   int prec = MQ_PREC_FP64;
   double tol_lin = 0.0;  // 0: default of the precision mode
@@ -108,8 +125,28 @@ mq_status fail(mq_ctx* c, mq_status s, const char* fmt, ...) {
     ++(c)->n_launches;     \
   } while (0)
 
+// Drops the captured graph (its nodes hold the addresses of the context's buffers and its
+// settings): called before any buffer it may use is freed or reallocated and by every setter.
+// while a graph is captured: the device offset of the range being captured (the graph can be
+// replayed on ranges that start elsewhere); otherwise none
+const uint32_t* kshift(const mq_ctx* c) {
+  return c->capturing && !c->g_off.empty() ? (const uint32_t*)c->gk0.p + (c->g_off.size() - 1) : nullptr;
+}
+
+void graph_release(mq_ctx* c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  c->gexec = nullptr;
+  c->graph = nullptr;
+  c->g_levels.clear();
+  c->g_k0.clear();
+  c->g_k1.clear();
+  c->g_off.clear();
+}
+
 mq_status grow(mq_ctx* c, DevBuf& b, size_t bytes) {
   if (bytes <= b.bytes) return MQ_OK;
+  graph_release(c);
   if (b.p) cudaFree(b.p);
   b.p = nullptr;
   b.bytes = 0;
@@ -177,6 +214,7 @@ mq_status ensure_psi(mq_ctx* c, int n, int rows, const double** out) {
     return MQ_OK;
   }
   if (it != c->psi.end()) {
+    graph_release(c);
     cudaFree(it->second.second);
     c->psi.erase(it);
   }
@@ -290,6 +328,8 @@ int threads_for(int n_fine, int n_coarse) {
 struct LevelGeom {
   int nf, nc, np, s, S, sp, direct_f, direct_p;
   int threads;  // requested threads per CTA of the per-sample kernel (0: default)
+  int tier;     // -1: by mesh size; 0: fine solves in the per-sample kernel; 1: streaming tier
+  int nu;       // Jacobi sweeps per side of the V-cycle for this level (0: default)
 };
 
 LevelGeom geom(const mq_ctx* c, int level) {
@@ -307,7 +347,16 @@ LevelGeom geom(const mq_ctx* c, int level) {
     g.direct_p = (pv.n_fine == lv.n_coarse && pv.s == lv.S);
   }
   g.threads = level < (int)c->cta_threads.size() ? c->cta_threads[level] : 0;
+  g.tier = level < (int)c->lvl_tier.size() ? c->lvl_tier[level] : -1;
+  g.nu = level < (int)c->lvl_nu.size() ? c->lvl_nu[level] : 0;
   return g;
+}
+
+// whether the fine solve of mesh g.nf runs in the streaming tier
+bool streams(const mq_ctx* c, const LevelGeom& g) {
+  if (g.direct_f) return false;
+  if (g.tier >= 0) return g.tier == 1;
+  return g.nf >= stream_threshold(c);
 }
 
 // Runs the per-sample pipeline on B = R * npts samples whose parameters are in c->Y (ldy = s).
@@ -332,13 +381,13 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
 
   const int mixed = c->prec == MQ_PREC_MIXED;
   if ((st = reset_tc_error(c)) != MQ_OK) return st;
-  MQ_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
+  if (!c->capturing) MQ_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
   const double* Y = (const double*)c->Y.p;
   if (given) {
     const uint32_t N0 = c->levels[0].N, Np = c->levels[level - 1].N;
     MQ_LAUNCH(c, mq::launch_reuse_gather(R, npts, kbase, Vc, (const double*)c->ru0.p, (const double*)c->rlam[0].p, N0,
                                          (const double*)c->rlam[level - 1].p, Np, (double*)c->upad.p,
-                                         (double*)c->out.p, c->stream));
+                                         (double*)c->out.p, c->stream, kshift(c)));
     MQ_CUDA(c, cudaMemsetAsync(c->stat.p, 0, B * 4 * sizeof(int), c->stream));
     MQ_CUDA(c, cudaMemsetAsync(c->outer.p, 0, B * 2 * sizeof(int), c->stream));
   } else {
@@ -347,13 +396,13 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
   if (!g.direct_f && (st = coefficients(c, g.nf, g.s, Y, (int)B, g.s, (double*)c->af.p)) != MQ_OK) return st;
   if (!given && g.np && !g.direct_p && (st = coefficients(c, g.np, g.sp, Y, (int)B, g.s, (double*)c->ap.p)) != MQ_OK)
     return st;
-  MQ_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
+  if (!c->capturing) MQ_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
 
   mq::SampleLaunch p{};
   // Where each fine solve runs.  A solve on the coarse mesh itself (h = H with a longer
   // truncation) is nearly singular -- lambda_H differs from the fine eigenvalue only by the
   // truncation -- so it always runs in the per-sample kernel with an FP64 inner solve.
-  const bool stream = g.nf >= stream_threshold(c) && !g.direct_f;
+  const bool stream = streams(c, g);
   auto mode_of = [&](int n, bool direct) {
     if (direct || n == 0) return 0;
     if (n == g.nc) return mixed ? 1 : 0;
@@ -408,7 +457,7 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
   // iterations than V(2,2) (and ~15 % more LOBPCG iterations) but moves about a third fewer bytes
   // per iteration, so it wins for the bandwidth-bound streaming tier; the latency-bound per-sample
   // kernel keeps V(2,2)
-  p.nu = c->opt_nu > 0 ? c->opt_nu : 2;
+  p.nu = g.nu > 0 ? g.nu : (c->opt_nu > 0 ? c->opt_nu : 2);
   p.omega = 0.8;
   const bool ext = p.mode_f == 2 || p.mode_p == 2;
   if (ext || c->reuse) {
@@ -442,11 +491,12 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
   // with the coarse pairs and lambda^{l-1} given and the fine solve streamed, the per-sample
   // kernel has nothing to do
   if (!(given && p.mode_f == 2)) MQ_LAUNCH(c, mq::launch_sample(p, mixed, blocks, threads, smem, c->stream));
-  MQ_CUDA(c, cudaEventRecord(c->ev[3], c->stream));
+  if (!c->capturing) MQ_CUDA(c, cudaEventRecord(c->ev[3], c->stream));
   if (ext) {
     const uint64_t launched0 = mq::stream_launches();
     if ((st = grow(c, c->arena, mq::stream_arena_bytes(g.nf, (int)B, mixed))) != MQ_OK) return st;
     mq::StreamSolve s{};
+    mq::StreamGraph sg{{c->gbody[0], c->gbody[1]}, (int*)c->gcount.p};
     s.nc = g.nc;
     s.B = (int)B;
     s.uH = (const double*)c->upad.p;
@@ -462,14 +512,14 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
     s.max_inner = p.max_inner_it;
     s.max_outer = p.max_outer;
     s.omega = p.omega;
-    s.nu = c->opt_nu > 0 ? c->opt_nu : 1;
+    s.nu = g.nu > 0 ? g.nu : (c->opt_nu > 0 ? c->opt_nu : 1);
     if (p.mode_f == 2) {
       s.n = g.nf;
       s.a = (const double*)c->af.p;
       s.lam_out = (double*)c->out.p + 1;
       s.iters_out = (int*)c->stat.p + 1;
       s.outer_out = (int*)c->outer.p + 0;
-      MQ_CUDA(c, mq::stream_solve(s, mixed, c->arena.p, c->stream));
+      MQ_CUDA(c, mq::stream_solve(s, mixed, c->arena.p, c->stream, c->capturing ? &sg : nullptr));
     }
     if (p.mode_p == 2 && !given) {
       s.n = g.np;
@@ -477,12 +527,12 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
       s.lam_out = (double*)c->out.p + 2;
       s.iters_out = (int*)c->stat.p + 2;
       s.outer_out = (int*)c->outer.p + 1;
-      MQ_CUDA(c, mq::stream_solve(s, mixed, c->arena.p, c->stream));
+      MQ_CUDA(c, mq::stream_solve(s, mixed, c->arena.p, c->stream, c->capturing ? &sg : nullptr));
     }
     MQ_CUDA(c, mq::launch_finalize((int)B, (double*)c->out.p, g.np > 0, c->stream));
     c->n_launches += mq::stream_launches() - launched0;
   }
-  MQ_CUDA(c, cudaEventRecord(c->ev[2], c->stream));
+  if (!c->capturing) MQ_CUDA(c, cudaEventRecord(c->ev[2], c->stream));
   c->stats.blocks = blocks;
   c->stats.threads = threads;
   c->stats.smem_bytes = (int)smem;
@@ -559,7 +609,7 @@ mq_status flags_status(mq_ctx* c, int fl) {
 int points_per_pass(const mq_ctx* c, const LevelGeom& g, int R, int npts) {
   size_t per_sample = sizeof(double) * ((size_t)2 * g.nf * g.nf + (size_t)2 * g.nc * g.nc +
                                         (size_t)2 * g.np * g.np + (size_t)g.s + 8 + (size_t)(g.nc + 1) * (g.nc + 1));
-  if (g.nf >= stream_threshold(c) && !g.direct_f && g.nf != g.nc)
+  if (streams(c, g) && g.nf != g.nc)
     per_sample += mq::stream_arena_bytes(g.nf, 1, c->prec == MQ_PREC_MIXED);
   size_t free_b = 0, total_b = 0;
   size_t budget = (size_t)24 << 30;
@@ -595,7 +645,14 @@ mq_status eval_level_impl(mq_ctx* c, int level, uint32_t k0, uint32_t k1, double
       if (!c->rfilled[0][k] || !c->rfilled[level - 1][k])
         return fail(c, MQ_ESTATE, "reuse: evaluate levels 0 and %d at point %u before level %d", level - 1, k, level);
   }
-  const int ppp = points_per_pass(c, g, R, npts);
+  // while a graph is captured nothing may query the device: the pass size of the rehearsal is used
+  if ((int)c->last_ppp.size() < (int)c->levels.size()) c->last_ppp.resize(c->levels.size(), 0);
+  const int ppp = c->capturing && c->last_ppp[level] > 0 ? std::min(c->last_ppp[level], npts)
+                                                         : points_per_pass(c, g, R, npts);
+  c->last_ppp[level] = ppp;
+  // the captured range's slot in the graph's sum accumulators
+  double* gsum = nullptr;
+  if (c->capturing) gsum = (double*)c->gsums.p + c->g_off.back();
   std::vector<double> host_out;
   std::vector<double> level_add(R, 0.0);
   int any_flags = 0;
@@ -605,14 +662,27 @@ mq_status eval_level_impl(mq_ctx* c, int level, uint32_t k0, uint32_t k1, double
     if ((st = grow(c, c->Y, B * g.s * sizeof(double))) != MQ_OK) return st;
     const int mb = c->mbits[level];
     MQ_LAUNCH(c, mq::launch_lattice_points(c->d_z[level], mb ? (1u << mb) : lv.N, c->d_delta[level], R, g.s, k0 + p0,
-                                         pn, mb, (double*)c->Y.p, c->stream));
+                                         pn, mb, (double*)c->Y.p, c->stream, kshift(c)));
     if ((st = run_samples(c, g, R, pn, chunk_for(c, R, pn), false, level, k0 + p0)) != MQ_OK) return st;
     if (c->reuse) {
       const mq_level& l0 = c->levels[0];
       const size_t V0 = (size_t)(l0.n_fine + 1) * (l0.n_fine + 1);
       MQ_LAUNCH(c, mq::launch_reuse_scatter(R, pn, k0 + p0, V0, (const double*)c->upad.p, (const double*)c->out.p,
                                             (double*)c->rlam[level].p, lv.N, level == 0 ? (double*)c->ru0.p : nullptr,
-                                            nullptr, l0.N, c->stream));
+                                            nullptr, l0.N, c->stream, kshift(c)));
+    }
+    if (c->capturing) {
+      // graph schedule: sums and flags accumulate on the device; outputs go to device buffers
+      MQ_LAUNCH(c, mq::launch_shift_sums((const double*)c->out.p, (const int*)c->stat.p, R, pn, gsum,
+                                       (int*)c->gflags.p, c->stream, 1));
+      if (d_per_sample) {
+        for (int r = 0; r < R; ++r)
+          MQ_CUDA(c, cudaMemcpyAsync(d_per_sample + ((size_t)r * npts + p0) * 4,
+                                     (const double*)c->out.p + (size_t)r * pn * 4, (size_t)pn * 4 * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, c->stream));
+      }
+      c->last_B = B;
+      continue;
     }
     if ((st = grow(c, c->sums_d, R * sizeof(double))) != MQ_OK) return st;
     if ((st = grow(c, c->flags_d, sizeof(int))) != MQ_OK) return st;
@@ -646,6 +716,13 @@ mq_status eval_level_impl(mq_ctx* c, int level, uint32_t k0, uint32_t k1, double
     for (int r = 0; r < R; ++r) level_add[r] += sums[r];
     any_flags |= fl;
     c->last_B = B;
+  }
+  if (c->capturing) {
+    if (d_shift_sums)
+      MQ_CUDA(c, cudaMemcpyAsync(d_shift_sums, gsum, R * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    if (c->reuse)
+      for (uint32_t k = k0; k < k1; ++k) c->rfilled[level][k] = 1;
+    return MQ_OK;
   }
   if (d_shift_sums)
     MQ_CUDA(c, cudaMemcpyAsync(d_shift_sums, level_add.data(), R * sizeof(double), cudaMemcpyHostToDevice, c->stream));
@@ -720,6 +797,11 @@ mq_status mq_destroy(mq_ctx* c) {
   c->lanes.clear();
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
+  graph_release(c);
+  for (cudaStream_t& b : c->gbody)
+    if (b) cudaStreamDestroy(b);
+  for (DevBuf* b : {&c->gcount, &c->gsums, &c->gflags, &c->gk0})
+    if (b->p) cudaFree(b->p);
   for (DevBuf* b : {&c->Y, &c->af, &c->ac, &c->ap, &c->out, &c->stat, &c->outer, &c->scratch, &c->sums_d,
                     &c->flags_d, &c->uout, &c->misc, &c->upad, &c->arena, &c->ysl, &c->tc_err})
     if (b->p) cudaFree(b->p);
@@ -745,6 +827,7 @@ const char* mq_last_error(const mq_ctx* c) { return c ? c->err.c_str() : "null c
 mq_status mq_set_coefficient(mq_ctx* c, double a0, int32_t s_max, int32_t family, double decay) {
   if (!c) return MQ_EINVAL;
   c->lanes_stale = true;
+  graph_release(c);
   if (!(a0 > 0.0) || !std::isfinite(a0)) return fail(c, MQ_EINVAL, "a0 must be positive, got %g", a0);
   if (s_max < 0 || s_max > 65536) return fail(c, MQ_EINVAL, "s_max %d out of range", s_max);
   if (family != 0 && family != 1) return fail(c, MQ_EINVAL, "unknown coefficient family %d", family);
@@ -779,6 +862,7 @@ mq_status mq_set_coefficient(mq_ctx* c, double a0, int32_t s_max, int32_t family
 mq_status mq_set_levels(mq_ctx* c, int32_t L_plus_1, const mq_level* levels) {
   if (!c) return MQ_EINVAL;
   c->lanes_stale = true;
+  graph_release(c);
   if (L_plus_1 < 1 || L_plus_1 > 32 || !levels) return fail(c, MQ_EINVAL, "need 1..32 levels");
   if (!c->coef_set) return fail(c, MQ_ESTATE, "set the coefficient before the levels");
   for (int l = 0; l < L_plus_1; ++l) {
@@ -822,6 +906,7 @@ mq_status mq_set_levels(mq_ctx* c, int32_t L_plus_1, const mq_level* levels) {
 mq_status mq_set_lattice(mq_ctx* c, int32_t level, const uint32_t* z, int32_t s) {
   if (!c) return MQ_EINVAL;
   c->lanes_stale = true;
+  graph_release(c);
   if (level < 0 || level >= (int)c->levels.size()) return fail(c, MQ_EINVAL, "level %d out of range", level);
   const mq_level& lv = c->levels[level];
   if (!z || s != lv.s) return fail(c, MQ_EINVAL, "lattice of level %d needs s = %d components", level, lv.s);
@@ -860,6 +945,7 @@ mq_status mq_set_lattice_embedded(mq_ctx* c, int32_t level, const uint32_t* z, i
 mq_status mq_set_shifts(mq_ctx* c, int32_t level, const double* delta) {
   if (!c) return MQ_EINVAL;
   c->lanes_stale = true;
+  graph_release(c);
   if (level < 0 || level >= (int)c->levels.size()) return fail(c, MQ_EINVAL, "level %d out of range", level);
   if (!delta) return fail(c, MQ_EINVAL, "null shifts");
   const mq_level& lv = c->levels[level];
@@ -879,6 +965,7 @@ mq_status mq_set_shifts(mq_ctx* c, int32_t level, const double* delta) {
 mq_status mq_set_reuse(mq_ctx* c, int32_t on) {
   if (!c) return MQ_EINVAL;
   c->lanes_stale = true;
+  graph_release(c);
   if (!on) {
     free_reuse(c);
     return MQ_OK;
@@ -935,6 +1022,7 @@ mq_status mq_set_reuse(mq_ctx* c, int32_t on) {
 mq_status mq_set_precision(mq_ctx* c, mq_precision prec, double tol_linear) {
   if (!c) return MQ_EINVAL;
   c->lanes_stale = true;
+  graph_release(c);
   if (prec != MQ_PREC_FP64 && prec != MQ_PREC_MIXED) return fail(c, MQ_EINVAL, "unknown precision %d", (int)prec);
   if (!std::isfinite(tol_linear) || tol_linear >= 1.0) return fail(c, MQ_EINVAL, "tolerance must be < 1");
   c->prec = prec;
@@ -945,6 +1033,7 @@ mq_status mq_set_precision(mq_ctx* c, mq_precision prec, double tol_linear) {
 mq_status mq_set_solver_options(mq_ctx* c, double tol_inner, int32_t max_inner, int32_t max_outer) {
   if (!c) return MQ_EINVAL;
   c->lanes_stale = true;
+  graph_release(c);
   if (!std::isfinite(tol_inner) || tol_inner >= 1.0 || max_inner > 100000 || max_outer > 1000)
     return fail(c, MQ_EINVAL, "bad solver options");
   c->opt_tol_inner = tol_inner > 0 ? tol_inner : 0.0;
@@ -956,6 +1045,7 @@ mq_status mq_set_solver_options(mq_ctx* c, double tol_inner, int32_t max_inner, 
 mq_status mq_set_eig_options(mq_ctx* c, double tol_eig, int32_t max_eig) {
   if (!c) return MQ_EINVAL;
   c->lanes_stale = true;
+  graph_release(c);
   if (!std::isfinite(tol_eig) || tol_eig >= 1.0 || max_eig > 100000) return fail(c, MQ_EINVAL, "bad eigensolver options");
   c->opt_tol_eig = tol_eig > 0 ? tol_eig : 0.0;
   c->opt_max_eig = max_eig > 0 ? max_eig : 0;
@@ -965,6 +1055,7 @@ mq_status mq_set_eig_options(mq_ctx* c, double tol_eig, int32_t max_eig) {
 mq_status mq_set_cta_threads(mq_ctx* c, int32_t level, int32_t threads) {
   if (!c) return MQ_EINVAL;
   c->lanes_stale = true;
+  graph_release(c);
   if (level < 0 || level >= 64) return fail(c, MQ_EINVAL, "level %d out of range", (int)level);
   if (threads != 0 && (threads < 32 || threads > 512 || threads % 32 != 0))
     return fail(c, MQ_EINVAL, "threads must be 0 or a multiple of 32 in [32, 512]");
@@ -973,9 +1064,132 @@ mq_status mq_set_cta_threads(mq_ctx* c, int32_t level, int32_t threads) {
   return MQ_OK;
 }
 
+mq_status mq_set_level_config(mq_ctx* c, int32_t level, int32_t tier, int32_t threads, int32_t nu) {
+  if (!c) return MQ_EINVAL;
+  c->lanes_stale = true;
+  graph_release(c);
+  if (level < 0 || level >= 64) return fail(c, MQ_EINVAL, "level %d out of range", (int)level);
+  if (tier < -1 || tier > 1) return fail(c, MQ_EINVAL, "tier must be -1, 0 or 1");
+  if (nu < 0 || nu > 2) return fail(c, MQ_EINVAL, "nu must be 0, 1 or 2");
+  mq_status st = mq_set_cta_threads(c, level, threads);
+  if (st != MQ_OK) return st;
+  if ((int)c->lvl_tier.size() <= level) c->lvl_tier.resize(level + 1, -1);
+  if ((int)c->lvl_nu.size() <= level) c->lvl_nu.resize(level + 1, 0);
+  c->lvl_tier[level] = tier;
+  c->lvl_nu[level] = nu;
+  return MQ_OK;
+}
+
+mq_status mq_autotune_level(mq_ctx* c, int32_t level, uint32_t points, const char* cache_path, mq_tune_choice* out) {
+  if (!c || !out) return MQ_EINVAL;
+  mq_status st = check_level_ready(c, level);
+  if (st != MQ_OK) return st;
+  if (c->reuse) return fail(c, MQ_ESTATE, "autotune: switch the reuse scheme off first");
+  const mq_level& lv = c->levels[level];
+  if (points < 1 || points > lv.N) return fail(c, MQ_EINVAL, "autotune: need 1 <= points <= N");
+  MQ_CUDA(c, cudaSetDevice(c->device));
+  *out = mq_tune_choice{};
+  // cache key: the GPU, the precision and everything about the level that shapes its kernels
+  cudaDeviceProp prop;
+  MQ_CUDA(c, cudaGetDeviceProperties(&prop, c->device));
+  const LevelGeom g0 = geom(c, level);
+  char key[512];
+  snprintf(key, sizeof key, "gpu=%s|sms=%d|prec=%d|nf=%d|nc=%d|np=%d|s=%d|S=%d|sp=%d|R=%d|pts=%u|tol=%g|fam=%d",
+           prop.name, c->sm_count, c->prec, g0.nf, g0.nc, g0.np, g0.s, g0.S, g0.sp, lv.R, points, c->tol_lin,
+           c->family);
+  for (char* q = key; *q; ++q)
+    if (*q == ' ') *q = '_';
+  if (cache_path) {
+    if (FILE* f = fopen(cache_path, "r")) {
+      char line[1024];
+      while (fgets(line, sizeof line, f)) {
+        char k[600];
+        int tier, threads, nu;
+        double ms;
+        if (sscanf(line, "%599s %d %d %d %lf", k, &tier, &threads, &nu, &ms) == 5 && strcmp(k, key) == 0) {
+          fclose(f);
+          out->tier = tier;
+          out->threads = threads;
+          out->nu = nu;
+          out->ms = ms;
+          out->from_cache = 1;
+          return mq_set_level_config(c, level, tier, threads, nu);
+        }
+      }
+      fclose(f);
+    }
+  }
+  // candidates: the fine solve's tier (when it is a two-grid level whose mesh both tiers handle
+  // well), the per-sample kernel's threads per CTA, the smoothing steps
+  std::vector<int> tiers = {-1};
+  if (!g0.direct_f && g0.nf >= 16 && g0.nf <= 128) tiers = {0, 1};
+  const int thr[3] = {64, 128, 256};
+  // save the estimator state and the level's settings: probes must leave neither behind
+  const auto sums = c->sums;
+  const auto npoints = c->npoints;
+  const auto t_coef = c->lvl_coef_ms, t_samp = c->lvl_sample_ms, t_pc = c->lvl_percta_ms, t_st = c->lvl_stream_ms;
+  const auto t_l = c->lvl_launches;
+  const uint64_t nl0 = c->n_launches;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  MQ_CUDA(c, cudaEventCreate(&e0));
+  MQ_CUDA(c, cudaEventCreate(&e1));
+  double best = 1e300;
+  int bt = -1, bth = 0, bnu = 0, tried = 0;
+  mq_status result = MQ_OK;
+  for (int tier : tiers)
+    for (int th : thr)
+      for (int nu = 1; nu <= 2 && result == MQ_OK; ++nu) {
+        if ((result = mq_set_level_config(c, level, tier, th, nu)) != MQ_OK) break;
+        double ms = 1e300;
+        for (int rep = 0; rep < 2; ++rep) {  // the first run also builds tables and buffers
+          if (cudaEventRecord(e0, c->stream) != cudaSuccess) result = fail(c, MQ_ECUDA, "event record");
+          mq_status s2 = eval_level_impl(c, level, 0, points, nullptr, nullptr, nullptr, nullptr);
+          if (s2 != MQ_OK && s2 != MQ_ENOCONV) result = s2;
+          if (result != MQ_OK) break;
+          cudaEventRecord(e1, c->stream);
+          cudaEventSynchronize(e1);
+          float t = 0.0f;
+          cudaEventElapsedTime(&t, e0, e1);
+          if (rep == 1 && s2 == MQ_OK) ms = t;
+        }
+        ++tried;
+        if (ms < best) {
+          best = ms;
+          bt = tier;
+          bth = th;
+          bnu = nu;
+        }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->sums = sums;
+  c->npoints = npoints;
+  c->lvl_coef_ms = t_coef;
+  c->lvl_sample_ms = t_samp;
+  c->lvl_percta_ms = t_pc;
+  c->lvl_stream_ms = t_st;
+  c->lvl_launches = t_l;
+  c->n_launches = nl0;
+  if (result != MQ_OK) return result;
+  if (best >= 1e300) return fail(c, MQ_ENOCONV, "autotune: no configuration converged");
+  out->tier = bt;
+  out->threads = bth;
+  out->nu = bnu;
+  out->ms = best;
+  out->tried = tried;
+  if (cache_path) {
+    if (FILE* f = fopen(cache_path, "a")) {
+      fprintf(f, "%s %d %d %d %.6f\n", key, bt, bth, bnu, best);
+      fclose(f);
+    }
+  }
+  return mq_set_level_config(c, level, bt, bth, bnu);
+}
+
 mq_status mq_set_smoothing(mq_ctx* c, int32_t nu) {
   if (!c) return MQ_EINVAL;
   c->lanes_stale = true;
+  graph_release(c);
   if (nu < 0 || nu > 2) return fail(c, MQ_EINVAL, "nu must be 0 (default), 1 or 2");
   c->opt_nu = nu;
   return MQ_OK;
@@ -984,6 +1198,7 @@ mq_status mq_set_smoothing(mq_ctx* c, int32_t nu) {
 mq_status mq_set_tier(mq_ctx* c, int32_t stream_min_n) {
   if (!c) return MQ_EINVAL;
   c->lanes_stale = true;
+  graph_release(c);
   if (stream_min_n < 0 || stream_min_n == 1) return fail(c, MQ_EINVAL, "stream_min_n must be 0 or >= 2");
   c->stream_min = stream_min_n;
   return MQ_OK;
@@ -1044,6 +1259,9 @@ mq_status mq_eval_levels_device(mq_ctx* c, int32_t nlev, const int32_t* levels, 
       chk(mq_set_smoothing(ch, c->opt_nu));
       chk(mq_set_tier(ch, c->stream_min));
       if (l < (int)c->cta_threads.size()) chk(mq_set_cta_threads(ch, l, c->cta_threads[l]));
+      if (l < (int)c->lvl_tier.size())
+        chk(mq_set_level_config(ch, l, c->lvl_tier[l], l < (int)c->cta_threads.size() ? c->cta_threads[l] : 0,
+                                l < (int)c->lvl_nu.size() ? c->lvl_nu[l] : 0));
       if (st != MQ_OK) {
         const std::string m = ch->err;
         mq_destroy(ch);
@@ -1094,6 +1312,169 @@ mq_status mq_eval_levels_device(mq_ctx* c, int32_t nlev, const int32_t* levels, 
   return result;
 }
 
+mq_status mq_graph_capture(mq_ctx* c, int32_t nlev, const int32_t* levels, const uint32_t* k0s, const uint32_t* k1s,
+                           double* const* d_per_sample, double* const* d_shift_sums) {
+  if (!c) return MQ_EINVAL;
+  if (nlev < 1 || !levels || !k0s || !k1s) return fail(c, MQ_EINVAL, "graph: bad range list");
+  for (int i = 0; i < nlev; ++i) {
+    mq_status st = check_level_ready(c, levels[i]);
+    if (st != MQ_OK) return st;
+    if (k1s[i] < k0s[i] || k1s[i] > c->levels[levels[i]].N) return fail(c, MQ_EINVAL, "graph: range %d outside the level", i);
+  }
+  MQ_CUDA(c, cudaSetDevice(c->device));
+  graph_release(c);
+  // 1. rehearsal: the same evaluations run normally -- every buffer is allocated, the tables are
+  //    built and the pass sizes fixed -- then the estimator state is put back
+  const auto sums = c->sums;
+  const auto npoints = c->npoints;
+  const auto t_coef = c->lvl_coef_ms, t_samp = c->lvl_sample_ms, t_pc = c->lvl_percta_ms, t_st = c->lvl_stream_ms;
+  const auto t_l = c->lvl_launches;
+  const auto filled = c->rfilled;
+  const uint64_t nl0 = c->n_launches;
+  auto restore = [&] {
+    c->sums = sums;
+    c->npoints = npoints;
+    c->lvl_coef_ms = t_coef;
+    c->lvl_sample_ms = t_samp;
+    c->lvl_percta_ms = t_pc;
+    c->lvl_stream_ms = t_st;
+    c->lvl_launches = t_l;
+    c->rfilled = filled;
+    c->n_launches = nl0;
+  };
+  size_t nsum = 0;
+  for (int i = 0; i < nlev; ++i) {
+    mq_status st = eval_level_impl(c, levels[i], k0s[i], k1s[i], nullptr, nullptr,
+                                   d_per_sample ? d_per_sample[i] : nullptr, d_shift_sums ? d_shift_sums[i] : nullptr);
+    if (st != MQ_OK && st != MQ_ENOCONV) {
+      restore();
+      return st;
+    }
+    nsum += (size_t)c->levels[levels[i]].R;
+  }
+  restore();
+  // 2. the graph's own device state, and the streams its loop bodies are captured on
+  mq_status st;
+  if ((st = grow(c, c->gcount, 2 * sizeof(int))) != MQ_OK) return st;
+  if ((st = grow(c, c->gsums, nsum * sizeof(double))) != MQ_OK) return st;
+  if ((st = grow(c, c->gflags, sizeof(int))) != MQ_OK) return st;
+  if ((st = grow(c, c->gk0, nlev * sizeof(uint32_t))) != MQ_OK) return st;
+  if ((st = grow(c, c->tc_err, sizeof(int))) != MQ_OK) return st;
+  MQ_CUDA(c, cudaMemset(c->gk0.p, 0, nlev * sizeof(uint32_t)));
+  for (cudaStream_t& b : c->gbody)
+    if (!b) MQ_CUDA(c, cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking));
+  // 3. capture
+  MQ_CUDA(c, cudaStreamSynchronize(c->stream));
+  MQ_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  c->capturing = true;
+  c->g_off.clear();
+  cudaError_t ce = cudaMemsetAsync(c->gsums.p, 0, nsum * sizeof(double), c->stream);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(c->gflags.p, 0, sizeof(int), c->stream);
+  st = ce == cudaSuccess ? MQ_OK : fail(c, MQ_ECUDA, "graph: %s", cudaGetErrorString(ce));
+  size_t off = 0;
+  for (int i = 0; i < nlev && st == MQ_OK; ++i) {
+    c->g_off.push_back(off);
+    st = eval_level_impl(c, levels[i], k0s[i], k1s[i], nullptr, nullptr, d_per_sample ? d_per_sample[i] : nullptr,
+                         d_shift_sums ? d_shift_sums[i] : nullptr);
+    off += (size_t)c->levels[levels[i]].R;
+  }
+  c->capturing = false;
+  cudaGraph_t g = nullptr;
+  ce = cudaStreamEndCapture(c->stream, &g);
+  const uint64_t nodes = c->n_launches - nl0;
+  c->n_launches = nl0;
+  c->rfilled = filled;  // the graph's launches fill the reuse store, not its capture
+  if (st != MQ_OK || ce != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    c->g_off.clear();
+    cudaGetLastError();
+    return st != MQ_OK ? st : fail(c, MQ_ECUDA, "graph capture: %s", cudaGetErrorString(ce));
+  }
+  ce = cudaGraphInstantiate(&c->gexec, g, 0);
+  if (ce != cudaSuccess) {
+    cudaGraphDestroy(g);
+    c->gexec = nullptr;
+    c->g_off.clear();
+    return fail(c, MQ_ECUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+  }
+  c->graph = g;
+  c->g_levels.assign(levels, levels + nlev);
+  c->g_k0.assign(k0s, k0s + nlev);
+  c->g_k1.assign(k1s, k1s + nlev);
+  c->g_cap_k0.assign(k0s, k0s + nlev);
+  c->g_shift.assign(nlev, 0u);
+  c->graph_kernels = nodes;
+  return MQ_OK;
+}
+
+mq_status mq_graph_launch(mq_ctx* c, const uint32_t* k0s) {
+  if (!c) return MQ_EINVAL;
+  if (!c->gexec) return fail(c, MQ_ESTATE, "graph: nothing captured (or a later call invalidated the graph)");
+  MQ_CUDA(c, cudaSetDevice(c->device));
+  if (k0s) {
+    // replay on ranges of the captured lengths that start at k0s[i]: the kernels add the offset
+    // from the captured start (modulo 2^32) that the graph reads from device memory
+    for (size_t i = 0; i < c->g_levels.size(); ++i)
+      if ((uint64_t)k0s[i] + (c->g_k1[i] - c->g_k0[i]) > c->levels[c->g_levels[i]].N)
+        return fail(c, MQ_EINVAL, "graph: range %zu moved outside its level", i);
+    for (size_t i = 0; i < c->g_levels.size(); ++i) {
+      const uint32_t len = c->g_k1[i] - c->g_k0[i];
+      c->g_k0[i] = k0s[i];
+      c->g_k1[i] = k0s[i] + len;
+      c->g_shift[i] = k0s[i] - c->g_cap_k0[i];
+    }
+    MQ_CUDA(c, cudaMemcpyAsync(c->gk0.p, c->g_shift.data(), c->g_shift.size() * sizeof(uint32_t),
+                               cudaMemcpyHostToDevice, c->stream));
+  }
+  if (c->reuse) {
+    // levels >= 1 of the graph read what its levels below store; both are in the same graph, in order
+    for (size_t i = 0; i < c->g_levels.size(); ++i)
+      if (c->g_levels[i] >= 1)
+        for (uint32_t k = c->g_k0[i]; k < c->g_k1[i]; ++k) {
+          bool below = false;
+          for (size_t j = 0; j < i; ++j)
+            below |= c->g_levels[j] == c->g_levels[i] - 1 && c->g_k0[j] <= k && k < c->g_k1[j];
+          if (!below && !c->rfilled[c->g_levels[i] - 1][k])
+            return fail(c, MQ_ESTATE, "graph: level %d needs level %d at point %u first", c->g_levels[i],
+                        c->g_levels[i] - 1, k);
+        }
+  }
+  MQ_CUDA(c, cudaGraphLaunch(c->gexec, c->stream));
+  const size_t nsum = c->g_off.empty() ? 0 : c->g_off.back() + (size_t)c->levels[c->g_levels.back()].R;
+  std::vector<double> gs(nsum);
+  int fl = 0, te = 0;
+  MQ_CUDA(c, cudaMemcpyAsync(gs.data(), c->gsums.p, nsum * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  MQ_CUDA(c, cudaMemcpyAsync(&fl, c->gflags.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  if (c->prec == MQ_PREC_MIXED)
+    MQ_CUDA(c, cudaMemcpyAsync(&te, c->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  MQ_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (te) return fail(c, MQ_ETIMEOUT, "a bounded wait in the tensor-core coefficient kernel ran out");
+  uint64_t samples = 0;
+  for (size_t i = 0; i < c->g_levels.size(); ++i) {
+    const int l = c->g_levels[i];
+    for (int r = 0; r < c->levels[l].R; ++r) c->sums[l][r] += gs[c->g_off[i] + r];
+    c->npoints[l] += c->g_k1[i] - c->g_k0[i];
+    samples += (uint64_t)c->levels[l].R * (c->g_k1[i] - c->g_k0[i]);
+    if (c->reuse)
+      for (uint32_t k = c->g_k0[i]; k < c->g_k1[i]; ++k) c->rfilled[l][k] = 1;
+  }
+  c->stats = mq_stats{};
+  if (fl) {
+    int dummy;
+    mq_status st = collect_stats(c, c->last_B, &dummy);
+    if (st != MQ_OK) return st;
+  }
+  c->stats.samples = samples;
+  return flags_status(c, fl);
+}
+
+mq_status mq_get_graph_info(mq_ctx* c, int32_t* captured, uint64_t* kernel_nodes) {
+  if (!c) return MQ_EINVAL;
+  if (captured) *captured = c->gexec != nullptr;
+  if (kernel_nodes) *kernel_nodes = c->gexec ? c->graph_kernels : 0;
+  return MQ_OK;
+}
+
 mq_status mq_get_sums(mq_ctx* c, int32_t level, double* sums, uint64_t* npoints) {
   if (!c) return MQ_EINVAL;
   if (level < 0 || level >= (int)c->sums.size()) return fail(c, MQ_EINVAL, "level %d out of range", level);
@@ -1142,6 +1523,116 @@ mq_status mq_estimate_sums(int32_t nlevels, const int32_t* R, const double* sums
   if (mean) *mean = tot;
   if (std_err) *std_err = std::sqrt(var);
   return MQ_OK;
+}
+
+mq_status mq_run_adaptive(mq_ctx* c, double eps, double alpha, uint32_t n_init, mq_adaptive_result* res) {
+  if (!c || !res) return MQ_EINVAL;
+  if (!(eps > 0.0) || !std::isfinite(eps) || !(alpha > 0.0) || !std::isfinite(alpha) || n_init < 1)
+    return fail(c, MQ_EINVAL, "adaptive: need eps > 0, alpha > 0, n_init >= 1");
+  const int L1 = (int)c->levels.size();
+  if (L1 == 0) return fail(c, MQ_ESTATE, "levels not set");
+  if (L1 > 32) return fail(c, MQ_EINVAL, "adaptive: at most 32 levels");
+  if (c->reuse) return fail(c, MQ_ESTATE, "adaptive: switch the reuse scheme off (levels must be independent)");
+  for (int l = 0; l < L1; ++l) {
+    mq_status st = check_level_ready(c, l);
+    if (st != MQ_OK) return st;
+    if (c->mbits[l] == 0) return fail(c, MQ_ESTATE, "adaptive: level %d needs an embedded lattice", l);
+    if (c->levels[l].R < 2) return fail(c, MQ_EINVAL, "adaptive: level %d needs R >= 2", l);
+  }
+  // cost per sample: the fine unknowns it solves (the level's mesh, and the previous level's on a
+  // two-grid level l > 0)
+  std::vector<double> cost(L1);
+  for (int l = 0; l < L1; ++l) {
+    const mq_level& lv = c->levels[l];
+    const double nf = (double)(lv.n_fine - 1) * (lv.n_fine - 1);
+    const bool direct = lv.n_fine == lv.n_coarse && lv.s == lv.S;
+    cost[l] = nf + (l > 0 && !direct ? (double)(c->levels[l - 1].n_fine - 1) * (c->levels[l - 1].n_fine - 1) : 0.0);
+  }
+  mq_status st = mq_reset_sums(c);
+  if (st != MQ_OK) return st;
+  *res = mq_adaptive_result{};
+  std::vector<uint32_t> N;
+  bool noconv = false;
+  auto add = [&](int l, uint32_t n_new) -> mq_status {
+    if (l == (int)N.size()) N.push_back(0);
+    mq_status s2 = eval_level_impl(c, l, N[l], n_new, nullptr, nullptr, nullptr, nullptr);
+    if (s2 == MQ_ENOCONV) noconv = true;
+    else if (s2 != MQ_OK) return s2;
+    if (n_new > N[l] && N[l] > 0) ++res->doublings;
+    else ++res->levels_added;
+    N[l] = n_new;
+    return MQ_OK;
+  };
+  auto stats = [&](std::vector<double>& m, std::vector<double>& v) {
+    m.assign(N.size(), 0.0);
+    v.assign(N.size(), 0.0);
+    for (size_t l = 0; l < N.size(); ++l) {
+      const int R = c->levels[l].R;
+      double mm = 0.0;
+      for (int r = 0; r < R; ++r) mm += c->sums[l][r] / (double)N[l];
+      mm /= R;
+      double vv = 0.0;
+      for (int r = 0; r < R; ++r) {
+        const double q = c->sums[l][r] / (double)N[l];
+        vv += (mm - q) * (mm - q);
+      }
+      m[l] = mm;
+      v[l] = vv / ((double)R * (R - 1));
+    }
+  };
+  for (int l = 0; l < std::min(3, L1); ++l)
+    if ((st = add(l, std::min<uint32_t>(n_init, c->levels[l].N))) != MQ_OK) return st;
+  std::vector<double> m, v;
+  bool converged = false;
+  for (;;) {
+    stats(m, v);
+    bool stuck = false;
+    for (;;) {
+      double tot = 0.0;
+      for (double x : v) tot += x;
+      if (!(tot > eps * eps / 2.0)) break;
+      int best = -1;
+      double bs = -1.0;
+      for (size_t l = 0; l < N.size(); ++l) {
+        const double sc = 2ull * N[l] <= c->levels[l].N ? v[l] / (cost[l] * N[l]) : -1.0;
+        if (sc > bs) {
+          bs = sc;
+          best = (int)l;
+        }
+      }
+      if (bs < 0.0) {
+        stuck = true;
+        break;
+      }
+      if ((st = add(best, 2 * N[best])) != MQ_OK) return st;
+      stats(m, v);
+    }
+    if (stuck) break;
+    const int L = (int)N.size() - 1;
+    if (L >= 2) {
+      const double bias = std::max(std::fabs(m[L]), std::fabs(m[L - 1]) / std::pow(2.0, alpha));
+      if (bias <= (std::pow(2.0, alpha) - 1.0) * eps / std::sqrt(2.0)) {
+        converged = true;
+        break;
+      }
+    }
+    if (L + 1 >= L1) break;
+    if ((st = add(L + 1, std::min<uint32_t>(n_init, c->levels[L + 1].N))) != MQ_OK) return st;
+  }
+  stats(m, v);
+  res->L = (int32_t)N.size() - 1;
+  res->converged = converged ? 1 : 0;
+  double mean = 0.0, var = 0.0;
+  for (size_t l = 0; l < N.size(); ++l) {
+    res->N[l] = N[l];
+    res->level_mean[l] = m[l];
+    res->level_var[l] = v[l];
+    mean += m[l];
+    var += v[l];
+  }
+  res->mean = mean;
+  res->std_err = std::sqrt(var);
+  return noconv ? fail(c, MQ_ENOCONV, "adaptive: some samples hit an iteration cap (results written)") : MQ_OK;
 }
 
 mq_status mq_reset_sums(mq_ctx* c) {

@@ -19,8 +19,10 @@ namespace {
 // mbits > 0: the embedded rule of 2^mbits points in radical-inverse order, point k taking the
 // lattice index rev(k) (the mbits-bit reversal of k) with N = 2^mbits, so the first 2^m points are
 // the 2^m-point rule (Sec. 2.5, embedded lattice rules)
+// dk: NULL, or a device offset added to k0 (a captured graph replayed on another range)
 __global__ void lattice_kernel(const uint32_t* __restrict__ z, uint32_t N, const double* __restrict__ delta, int R,
-                               int s, uint32_t k0, int npts, int mbits, double* __restrict__ Y) {
+                               int s, uint32_t k0, int npts, int mbits, const uint32_t* dk, double* __restrict__ Y) {
+  if (dk) k0 += *dk;
   const size_t tot = (size_t)R * npts * s;
   for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += (size_t)gridDim.x * blockDim.x) {
     const int j = (int)(q % s);
@@ -118,11 +120,11 @@ int grid_for(size_t tot, int threads) {
 }  // namespace
 
 cudaError_t launch_lattice_points(const uint32_t* d_z, uint32_t N, const double* d_delta, int R, int s, uint32_t k0,
-                                  int npts, int mbits, double* d_Y, cudaStream_t st) {
+                                  int npts, int mbits, double* d_Y, cudaStream_t st, const uint32_t* d_kshift) {
   const size_t tot = (size_t)R * npts * s;
   if (tot == 0) return cudaSuccess;
   if (mbits < 0 || mbits > 31 || (mbits > 0 && N != (1u << mbits))) return cudaErrorInvalidValue;
-  lattice_kernel<<<grid_for(tot, 256), 256, 0, st>>>(d_z, N, d_delta, R, s, k0, npts, mbits, d_Y);
+  lattice_kernel<<<grid_for(tot, 256), 256, 0, st>>>(d_z, N, d_delta, R, s, k0, npts, mbits, d_kshift, d_Y);
   return cudaGetLastError();
 }
 

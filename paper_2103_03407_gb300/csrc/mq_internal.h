@@ -62,8 +62,16 @@ struct StreamSolve {
   double omega;
   int nu;                  // Jacobi sweeps before and after each coarse-grid correction (1 or 2)
 };
+// Graph mode of the streaming solve: the refinement and MINRES loops become conditional WHILE nodes
+// of the CUDA graph being captured on the solve's stream (no host reads); their bodies are
+// captured on two further streams; two device ints count the loop iterations.
+struct StreamGraph {
+  cudaStream_t body[2];
+  int* counters;
+};
 size_t stream_arena_bytes(int n, int B, int mixed);
-cudaError_t stream_solve(const StreamSolve& s, int mixed, void* arena, cudaStream_t st);
+cudaError_t stream_solve(const StreamSolve& s, int mixed, void* arena, cudaStream_t st,
+                         const StreamGraph* sg = nullptr);
 // kernels the streaming tier has launched from the calling thread (monotone counter)
 uint64_t stream_launches();
 cudaError_t launch_finalize(int B, double* d_out, int has_prev, cudaStream_t st);
@@ -100,7 +108,8 @@ cudaError_t raise_smem_limit(const void* func, int bytes);
 // Coefficient building blocks (mq_coef.cu)
 // mbits > 0: embedded rule in radical-inverse order with N = 2^mbits (point k uses index rev(k))
 cudaError_t launch_lattice_points(const uint32_t* d_z, uint32_t N, const double* d_delta, int R, int s,
-                                  uint32_t k0, int npts, int mbits, double* d_Y, cudaStream_t st);
+                                  uint32_t k0, int npts, int mbits, double* d_Y, cudaStream_t st,
+                                  const uint32_t* d_kshift = nullptr);
 cudaError_t launch_psi_table(int n, int s, const int* d_k1, const int* d_k2, const double* d_cj,
                              double* d_psi, cudaStream_t st);
 cudaError_t launch_coef_gemm_f64(const double* d_Y, int ldy, int B, int s, const double* d_psi, int nT,
@@ -112,13 +121,16 @@ cudaError_t launch_apply_operator(int n, int B, const double* d_a, int which, do
 // out[b][0] = lam0[r][k], out[b][2] = lamp[r][k] (lamp may be NULL).
 cudaError_t launch_reuse_gather(int R, int npts, uint32_t k0, size_t V, const double* d_u0, const double* d_lam0,
                                 uint32_t ld0, const double* d_lamp, uint32_t ldp, double* d_upad, double* d_out,
-                                cudaStream_t st);
+                                cudaStream_t st, const uint32_t* d_kshift = nullptr);
 // Scatter after a pass: lam[r][k] = out[b][1]; with d_u0, also u0[r][k] = u_pad[b] and
 // lam0[r][k] = out[b][0].
 cudaError_t launch_reuse_scatter(int R, int npts, uint32_t k0, size_t V, const double* d_upad, const double* d_out,
                                  double* d_lam, uint32_t ldl, double* d_u0, double* d_lam0, uint32_t ld0,
-                                 cudaStream_t st);
+                                 cudaStream_t st, const uint32_t* d_kshift = nullptr);
+// (d_kshift: NULL, or a device offset added to k0 -- a captured graph replayed on another range)
+// per-shift sums of the level differences of a pass (accumulate: added to d_sums instead of
+// overwriting it); d_flags receives the OR of the sample flags
 cudaError_t launch_shift_sums(const double* d_out, const int* d_stat, int R, int npts, double* d_sums,
-                              int* d_flags, cudaStream_t st);
+                              int* d_flags, cudaStream_t st, int accumulate = 0);
 
 }  // namespace mq

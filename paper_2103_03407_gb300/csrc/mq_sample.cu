@@ -852,7 +852,7 @@ __global__ void apply_kernel(int n, const double* __restrict__ a, int which, dou
 // Per-shift sums of the per-sample differences over the points of a batch: one CTA per shift,
 // fixed reduction order (deterministic).  flags receives the OR of all sample flags.
 __global__ void shift_sums_kernel(const double* __restrict__ out, const int* __restrict__ stat, int npts,
-                                  double* __restrict__ sums, int* __restrict__ flags) {
+                                  double* __restrict__ sums, int* __restrict__ flags, int accumulate) {
   __shared__ double red[kRedSlots];
   const int r = blockIdx.x;
   double acc[1] = {0.0}, o[1];
@@ -864,13 +864,15 @@ __global__ void shift_sums_kernel(const double* __restrict__ out, const int* __r
   }
   block_sum<1, double>(acc, o, red);
   if (f) atomicOr(flags, f);
-  if (threadIdx.x == 0) sums[r] = o[0];
+  if (threadIdx.x == 0) sums[r] = accumulate ? sums[r] + o[0] : o[0];
 }
 
 // reuse scheme: gather the stored level-0 pairs (and the level below's values) of a pass's samples
 __global__ void reuse_gather_kernel(int R, int npts, uint32_t k0, size_t V, const double* __restrict__ u0,
                                     const double* __restrict__ lam0, uint32_t ld0, const double* __restrict__ lamp,
-                                    uint32_t ldp, double* __restrict__ upad, double* __restrict__ out) {
+                                    uint32_t ldp, double* __restrict__ upad, double* __restrict__ out,
+                                    const uint32_t* dk) {
+  if (dk) k0 += *dk;
   const size_t B = (size_t)R * npts, tot = B * V;
   for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += (size_t)gridDim.x * blockDim.x) {
     const size_t b = q / V, e = q % V;
@@ -885,7 +887,9 @@ __global__ void reuse_gather_kernel(int R, int npts, uint32_t k0, size_t V, cons
 
 __global__ void reuse_scatter_kernel(int R, int npts, uint32_t k0, size_t V, const double* __restrict__ upad,
                                      const double* __restrict__ out, double* __restrict__ lam, uint32_t ldl,
-                                     double* __restrict__ u0, double* __restrict__ lam0, uint32_t ld0) {
+                                     double* __restrict__ u0, double* __restrict__ lam0, uint32_t ld0,
+                                     const uint32_t* dk) {
+  if (dk) k0 += *dk;
   const size_t B = (size_t)R * npts, tot = B * (u0 ? V : 1);
   const size_t per = u0 ? V : 1;
   for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += (size_t)gridDim.x * blockDim.x) {
@@ -908,19 +912,21 @@ int grid_of(size_t n) {
 
 cudaError_t launch_reuse_gather(int R, int npts, uint32_t k0, size_t V, const double* d_u0, const double* d_lam0,
                                 uint32_t ld0, const double* d_lamp, uint32_t ldp, double* d_upad, double* d_out,
-                                cudaStream_t st) {
+                                cudaStream_t st, const uint32_t* d_kshift) {
   const size_t tot = (size_t)R * npts * V;
   if (tot == 0) return cudaSuccess;
-  reuse_gather_kernel<<<grid_of(tot), 256, 0, st>>>(R, npts, k0, V, d_u0, d_lam0, ld0, d_lamp, ldp, d_upad, d_out);
+  reuse_gather_kernel<<<grid_of(tot), 256, 0, st>>>(R, npts, k0, V, d_u0, d_lam0, ld0, d_lamp, ldp, d_upad, d_out,
+                                                    d_kshift);
   return cudaGetLastError();
 }
 
 cudaError_t launch_reuse_scatter(int R, int npts, uint32_t k0, size_t V, const double* d_upad, const double* d_out,
                                  double* d_lam, uint32_t ldl, double* d_u0, double* d_lam0, uint32_t ld0,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, const uint32_t* d_kshift) {
   const size_t tot = (size_t)R * npts * (d_u0 ? V : 1);
   if (tot == 0) return cudaSuccess;
-  reuse_scatter_kernel<<<grid_of(tot), 256, 0, st>>>(R, npts, k0, V, d_upad, d_out, d_lam, ldl, d_u0, d_lam0, ld0);
+  reuse_scatter_kernel<<<grid_of(tot), 256, 0, st>>>(R, npts, k0, V, d_upad, d_out, d_lam, ldl, d_u0, d_lam0, ld0,
+                                                     d_kshift);
   return cudaGetLastError();
 }
 
@@ -972,9 +978,9 @@ cudaError_t launch_apply_operator(int n, int B, const double* d_a, int which, do
 }
 
 cudaError_t launch_shift_sums(const double* d_out, const int* d_stat, int R, int npts, double* d_sums, int* d_flags,
-                              cudaStream_t st) {
+                              cudaStream_t st, int accumulate) {
   if (R == 0) return cudaSuccess;
-  shift_sums_kernel<<<R, 256, 0, st>>>(d_out, d_stat, npts, d_sums, d_flags);
+  shift_sums_kernel<<<R, 256, 0, st>>>(d_out, d_stat, npts, d_sums, d_flags, accumulate);
   return cudaGetLastError();
 }
 

@@ -714,8 +714,12 @@ __global__ void k_sc_delta(int B, int nch, const double* part, const int* act, S
 
 // Givens step; a converged sample keeps its pending update and leaves the active set after the
 // next K1 (which applies it)
+// jc (graph mode): the device iteration counter of the inner loop; iteration *jc + joff is the
+// last one allowed when it reaches max_inner - 1, and every sample then counts as done (its pending
+// update is applied by the next operator sweep, as the host loop's final update would)
 template <typename T>
-__global__ void k_sc_givens(int B, int nch, const double* part, int* act, SS<T>* ss, T tol, int* count) {
+__global__ void k_sc_givens(int B, int nch, const double* part, int* act, SS<T>* ss, T tol, int* count,
+                            const int* jc = nullptr, int joff = 0, int max_inner = 0) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B || !act[b]) return;
   double s = 0.0;
@@ -749,7 +753,8 @@ __global__ void k_sc_givens(int B, int nch, const double* part, int* act, SS<T>*
   S.ig = gnew > T(0) ? T(1) / gnew : T(0);
   S.pend = 1;
   S.iters += 1;
-  const bool done = fabs(S.eta) <= tol * S.eta0 || gnew == T(0);
+  const bool capped = jc && *jc + joff + 1 >= max_inner;
+  const bool done = fabs(S.eta) <= tol * S.eta0 || gnew == T(0) || capped;
   if (done) S.act = 0;  // leaves after the next K1
   else atomicAdd(count, 1);
 }
@@ -850,6 +855,25 @@ __global__ void k_sc_rq(int B, int n, const double* sigma, int sig_stride, const
   const double kn = knorm_of(S, n, sigma[(size_t)b * sig_stride]);
   if (!(S.rnorm <= residual_target(fmax(1e-5, 10.0 * tol_lin), S.bnorm, kn, S.xnorm, 256.0))) f |= kFlagLinNoConv;
   flags[(size_t)b * flag_stride] |= f;
+}
+
+// ---------------------------------------------------------------------------------------------
+// loop control of the graph mode: conditional WHILE / IF nodes of a CUDA graph, set on the device
+__global__ void k_cond_init(cudaGraphConditionalHandle h, int* counter) {
+  *counter = 0;
+  cudaGraphSetConditional(h, 1u);
+}
+
+// after an outer step: continue while samples are still refining and steps are left
+__global__ void k_cond_outer(cudaGraphConditionalHandle h, int* counter, const int* count, int max_iter) {
+  const int o = ++*counter;
+  cudaGraphSetConditional(h, (*count > 0 && o < max_iter) ? 1u : 0u);
+}
+
+// after a pair of inner iterations: continue while samples are active and iterations are left
+__global__ void k_cond_inner(cudaGraphConditionalHandle h, int* counter, const int* count, int max_iter) {
+  *counter += 2;
+  cudaGraphSetConditional(h, (*count > 0 && *counter < max_iter) ? 1u : 0u);
 }
 
 template <typename T>
@@ -1025,8 +1049,47 @@ int read_count(const int* d_count, cudaStream_t st, cudaError_t& err) {
   return h;
 }
 
+// Graph mode: a WHILE node of the graph being captured on `st`, after the work captured so far; its
+// body is captured on `body` until close_while.  The node's condition starts at 1 (k_cond_init
+// before the node sets it, and resets the loop counter) and is set by a kernel at the body's end.
+// a conditional handle of the graph being captured on st
+cudaError_t make_handle(cudaStream_t st, cudaGraphConditionalHandle* h) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, nullptr, nullptr, nullptr);
+  if (e != cudaSuccess) return e;
+  if (cs != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+  return cudaGraphConditionalHandleCreate(h, g, 0u, 0u);
+}
+
+cudaError_t open_while(cudaStream_t st, cudaStream_t body, cudaGraphConditionalHandle h) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &nd);
+  if (e != cudaSuccess) return e;
+  if (cs != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  if ((e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &p)) != cudaSuccess) return e;
+  if ((e = cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies)) != cudaSuccess)
+    return e;
+  return cudaStreamBeginCaptureToGraph(body, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                       cudaStreamCaptureModeRelaxed);
+}
+
+cudaError_t close_while(cudaStream_t body) {
+  cudaGraph_t g = nullptr;
+  return cudaStreamEndCapture(body, &g);
+}
+
 template <typename T>
-cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st) {
+cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st, const StreamGraph* sg) {
   Arena<T> A;
   carve_arena<T>(arena, s.n, s.B, A);
   A.nu = s.nu == 1 ? 1 : 2;
@@ -1095,6 +1158,68 @@ cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st) {
   ++tl_launches, k_zero<double><<<grid1(Bz * V0), 256, 0, st>>>(Bz * V0, A.x64);
   ++tl_launches, k_sc_start<T><<<gs, 256, 0, st>>>(B, n, s.lamH, s.lam_stride, nt, A.part, A.ss);
   LAUNCH_CHECK();
+  if (sg) {
+    // ---- refinement loop as nested WHILE nodes: no host reads.  The inner loop runs iterations in
+    // pairs, so the rotating vectors (w/wo, v/vo, z/zn) end every pair where they started; the
+    // second iteration of a pair is a no-op for samples that finished in the first (converged, or
+    // capped at max_inner by the device counter, which marks every sample done), apart from
+    // applying their pending update -- which the host loop's final update does otherwise.  An outer
+    // step with nothing left to refine is a no-op too.
+    int* oc = sg->counters;      // outer step counter
+    int* ic = sg->counters + 1;  // inner iteration counter
+    int* cnt_o = A.count;        // samples refining in this step
+    int* cnt_i = A.count + 1;    // samples still iterating
+    const cudaStream_t b0 = sg->body[0], b1 = sg->body[1];
+    cudaGraphConditionalHandle ho, hi;
+    if ((e = make_handle(st, &ho)) != cudaSuccess) return e;
+    ++tl_launches, k_cond_init<<<1, 1, 0, st>>>(ho, oc);
+    LAUNCH_CHECK();
+    if ((e = open_while(st, b0, ho)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(cnt_o, 0, sizeof(int), b0)) != cudaSuccess) return e;
+    ++tl_launches, k_sc_outer_begin<T><<<gs, 256, 0, b0>>>(B, n, s.lamH, s.lam_stride, s.tol_lin, A.ss, A.act, cnt_o);
+    LAUNCH_CHECK();
+    if ((e = cudaMemcpyAsync(A.ran, A.act, Bz * sizeof(int), cudaMemcpyDeviceToDevice, b0)) != cudaSuccess) return e;
+    ++tl_launches, k_inner_init<T><<<B * nt, kThreads, 0, b0>>>(n, B, A.act, A.ss, A.v, A.vo, A.w, A.wo, A.xi);
+    LAUNCH_CHECK();
+    T *v = A.v, *vo = A.vo, *z = A.z, *zn = A.zn, *w = A.w, *wo = A.wo;
+    if ((e = vcycle_stream<T>(A, v, z, A.act, om, v, A.part, sub_smem, b0)) != cudaSuccess) return e;
+    const int nchd = A.Ls ? nt : 1;  // partial slots of <v, z>
+    ++tl_launches, k_sc_gamma0<T><<<gs, 256, 0, b0>>>(B, nchd, A.part, A.act, A.ss);
+    LAUNCH_CHECK();
+    if ((e = make_handle(b0, &hi)) != cudaSuccess) return e;
+    ++tl_launches, k_cond_init<<<1, 1, 0, b0>>>(hi, ic);
+    LAUNCH_CHECK();
+    if ((e = open_while(b0, b1, hi)) != cudaSuccess) return e;
+    for (int half = 0; half < 2; ++half) {
+      ++tl_launches, k_minres_q<T><<<B * nt, kThreads, 0, b1>>>(n, B, A.act, A.ss, A.wx[0], A.wy[0], s.lamH,
+                                                              s.lam_stride, z, zn, wo, w, A.xi, A.q, A.part);
+      LAUNCH_CHECK();
+      ++tl_launches, k_sc_retire<T><<<gs, 256, 0, b1>>>(B, A.act, A.ss);
+      { T* tt = wo; wo = w; w = tt; }
+      ++tl_launches, k_sc_delta<T><<<gs, 256, 0, b1>>>(B, nt, A.part, A.act, A.ss);
+      ++tl_launches, k_minres_v<T><<<B * nt, kThreads, 0, b1>>>(n, B, A.act, A.ss, A.q, v, vo);
+      LAUNCH_CHECK();
+      { T* tt = vo; vo = v; v = tt; }
+      if ((e = vcycle_stream<T>(A, v, zn, A.act, om, v, A.part, sub_smem, b1)) != cudaSuccess) return e;
+      if ((e = cudaMemsetAsync(cnt_i, 0, sizeof(int), b1)) != cudaSuccess) return e;
+      ++tl_launches, k_sc_givens<T><<<gs, 256, 0, b1>>>(B, nchd, A.part, A.act, A.ss, T(s.tol_inner), cnt_i, ic, half,
+                                                       s.max_inner);
+      LAUNCH_CHECK();
+      { T* tt = z; z = zn; zn = tt; }
+    }
+    ++tl_launches, k_cond_inner<<<1, 1, 0, b1>>>(hi, ic, cnt_i, s.max_inner);
+    LAUNCH_CHECK();
+    if ((e = close_while(b1)) != cudaSuccess) return e;
+    // an even number of iterations: the rotating vectors are back where they started
+    ++tl_launches, k_minres_finish<T><<<B * nt, kThreads, 0, b0>>>(n, B, A.ran, A.ss, zn, wo, w, A.xi);
+    ++tl_launches, k_outer_update<T><<<B * nt, kThreads, 0, b0>>>(n, B, A.ss, A.ran, A.xi, A.x64);
+    ++tl_launches, k_residual<T><<<B * nt, kThreads, 0, b0>>>(n, B, A.ran, A.wx64, A.wy64, s.lamH, s.lam_stride, A.x64,
+                                                             A.b64, A.v, A.part);
+    ++tl_launches, k_sc_outer_end<T><<<gs, 256, 0, b0>>>(B, nt, A.part, A.ran, A.ss);
+    ++tl_launches, k_cond_outer<<<1, 1, 0, b0>>>(ho, oc, cnt_o, s.max_outer);
+    LAUNCH_CHECK();
+    if ((e = close_while(b0)) != cudaSuccess) return e;
+  } else {
   // ---- refinement loop
   for (int o = 0; o < s.max_outer; ++o) {
     cudaMemsetAsync(A.count, 0, sizeof(int), st);
@@ -1144,6 +1269,7 @@ cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st) {
     ++tl_launches, k_sc_outer_end<T><<<gs, 256, 0, st>>>(B, nt, A.part, A.ran, A.ss);
     LAUNCH_CHECK();
   }
+  }
   // ---- Rayleigh quotient (from each sample's last residual pass)
   ++tl_launches, k_sc_rq<T><<<gs, 256, 0, st>>>(B, n, s.lamH, s.lam_stride, A.ss, s.tol_lin, s.lam_out, s.lam_out_stride, s.iters_out,
                                  s.iters_stride, s.outer_out, s.outer_stride, s.flags, s.flags_stride);
@@ -1177,8 +1303,8 @@ size_t stream_arena_bytes(int n, int B, int mixed) {
 
 uint64_t stream_launches() { return tl_launches; }
 
-cudaError_t stream_solve(const StreamSolve& s, int mixed, void* arena, cudaStream_t st) {
-  return mixed ? stream_solve_t<float>(s, arena, st) : stream_solve_t<double>(s, arena, st);
+cudaError_t stream_solve(const StreamSolve& s, int mixed, void* arena, cudaStream_t st, const StreamGraph* sg) {
+  return mixed ? stream_solve_t<float>(s, arena, st, sg) : stream_solve_t<double>(s, arena, st, sg);
 }
 
 }  // namespace mq

@@ -403,8 +403,8 @@ cudaError_t launch_coef_tc(const void* d_yslices, int B, int kpad, const void* d
   e = slice_map(&tmP, d_pslices, nTp, kpad_psi, kTN);
   if (e != cudaSuccess) return e;
   const size_t smem = sizeof(TcSmem) + 1024;
-  e = cudaFuncSetAttribute(k_coef_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  // raised once per device (never lowered), so the launch can also be captured into a graph
+  if ((e = raise_smem_limit((const void*)k_coef_tc, (int)smem)) != cudaSuccess) return e;
   int dev = 0, sms = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;

@@ -397,3 +397,33 @@ def test_iteration_caps_report_noconvergence(B, prec):
     ref = mlqmc.level_samples(levels[0], None, lattice.cbc(16, 16), shifts(3, levels)[0], list(range(4)))
     _check_level(ps, ref)
     ctx.close()
+
+
+def test_autotuner_keeps_results_and_caches_its_choice(B, tmp_path):
+    # the tuner times the candidate configurations of a level on a probe, applies the fastest and
+    # stores it; the results stay those of the default configuration to the solver tolerances,
+    # and the probes leave the estimator state untouched
+    levels = [Level(16, 8, 16, 4, 32, 2), Level(32, 8, 32, 6, 32, 2), Level(64, 16, 64, 8, 16, 2)]
+    ctx, zs, ds = make_ctx(B, levels, seed=13, prec=1)
+    ref = [ctx.mq_eval_level(l, 0, 8)[0] for l in range(3)]
+    before = [ctx.mq_get_sums(l) for l in range(3)]
+    cache = str(tmp_path / "tune.txt")
+    choices = [ctx.mq_autotune_level(l, 8, cache) for l in range(3)]
+    for (sa, na), (sb, nb) in zip(before, [ctx.mq_get_sums(l) for l in range(3)]):
+        assert na == nb and np.array_equal(sa, sb)
+    for l, ch in enumerate(choices):
+        assert ch["from_cache"] == 0 and ch["tried"] >= 6 and ch["ms"] > 0
+        assert ch["threads"] in (64, 128, 256) and ch["nu"] in (1, 2)
+    # meshes 1/16 .. 1/64 can run in either tier: both were timed
+    assert all(ch["tier"] in (0, 1) and ch["tried"] == 12 for ch in choices)
+    for l in range(3):
+        got, _ = ctx.mq_eval_level(l, 0, 8)
+        assert np.all(np.abs(got[..., :3] - ref[l][..., :3]) <= 1e-10 * np.abs(ref[l][..., :3]) + 1e-300)
+    # a second context reads the choices from the cache without timing
+    ctx2, _, _ = make_ctx(B, levels, seed=13, prec=1)
+    for l in range(3):
+        ch = ctx2.mq_autotune_level(l, 8, cache)
+        assert ch["from_cache"] == 1 and (ch["tier"], ch["threads"], ch["nu"]) == (
+            choices[l]["tier"], choices[l]["threads"], choices[l]["nu"])
+    ctx.close()
+    ctx2.close()

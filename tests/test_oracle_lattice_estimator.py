@@ -187,3 +187,49 @@ def test_shared_shift_estimate():
     assert m1 == pytest.approx(m2, rel=1e-15) and se1 == pytest.approx(se2, rel=1e-14)
     with pytest.raises(ValueError):
         mlqmc.estimate_shared(q[:, :1])
+
+
+# ---- the adaptive algorithm (Sec. 4.2, Giles-Waterhouse choice of N_l and L)
+
+@pytest.mark.parametrize("bdecay", [4.0, 2.0])
+def test_adaptive_decisions_follow_the_closed_form(bdecay):
+    # a synthetic level whose differences are b_l + a_l w_r at point 0 and b_l elsewhere: after N
+    # points Q^(r)_l = b_l + a_l w_r / N, so Vhat_l(N) = (a_l / N)^2 S_w and Qhat_l = b_l + a_l wbar / N
+    # in closed form; the greedy rule is re-derived from those formulas and compared
+    R = 4
+    w = np.array([1.0, -1.0, 2.0, 0.0])
+    wbar, Sw = w.mean(), ((w.mean() - w) ** 2).sum() / (R * (R - 1))
+    a = [2.0 ** -l for l in range(5)]
+    b = [bdecay ** -l for l in range(5)]  # bdecay 2: the bias test fails until level 4
+    cost = [4.0 ** l for l in range(5)]
+    eps, alpha, n_init = 0.05, 2.0, 2
+
+    def evaluate(l, k0, k1):
+        d = np.full((R, k1 - k0), b[l])
+        if k0 == 0 and k1 > 0:
+            d[:, 0] += a[l] * w
+        return d
+
+    res = mlqmc.adaptive(evaluate, cost, R, eps, alpha, n_init)
+    # re-derivation
+    N, hist = [n_init] * 3, [(0, 2), (1, 2), (2, 2)]
+    V = lambda l: (a[l] / N[l]) ** 2 * Sw
+    Q = lambda l: b[l] + a[l] * wbar / N[l]
+    while True:
+        while sum(V(l) for l in range(len(N))) > eps ** 2 / 2:
+            sc = [V(l) / (cost[l] * N[l]) for l in range(len(N))]
+            l = sc.index(max(sc))
+            N[l] *= 2
+            hist.append((l, N[l]))
+        L = len(N) - 1
+        if max(abs(Q(L)), abs(Q(L - 1)) / 4.0) <= 3.0 * eps / math.sqrt(2.0):
+            break
+        N.append(n_init)
+        hist.append((L + 1, n_init))
+    assert res["history"] == hist and res["N"] == N and res["converged"]
+    assert res["L"] == len(N) - 1 == (2 if bdecay == 4.0 else 4)
+    assert res["mean"] == pytest.approx(sum(Q(l) for l in range(len(N))), rel=1e-13)
+    assert res["std_err"] == pytest.approx(math.sqrt(sum(V(l) for l in range(len(N)))), rel=1e-12)
+    # a cap on the points per level that blocks every doubling ends the run unconverged
+    capped = mlqmc.adaptive(evaluate, cost, R, 1e-6, alpha, n_init, n_max=[4] * 5)
+    assert not capped["converged"] and all(n <= 4 for n in capped["N"])
