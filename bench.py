@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-baseline", action="store_true", help="skip the timed CPU oracle sample")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison run")
+    ap.add_argument("--no-graph", action="store_true", help="skip the graph-schedule run")
     ap.add_argument("--baseline-seconds", type=float, default=20.0)
     ap.add_argument("--fraction", type=int, default=0,
                     help="evaluate 1/F of every level's points per step (0: the workload's default)")
@@ -239,12 +240,15 @@ def time_device(binding, torch, wl, prec, steps, warmup, stream, F, rank=0, worl
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ctx.mq_reset_sums()  # also clears the per-level device timers
+    ctx.mq_set_kernel_probe(1)  # live timing of the streaming operator sweep over the timed steps
     ev0.record(stream)
     for i in range(steps):
         run_device_step(ctx, wl, outs, sums, F, warmup + i, sequential)
     ev1.record(stream)
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
+    probe = ctx.mq_get_kernel_probe()
+    ctx.mq_set_kernel_probe(0)
     # per-level device time of the timed region (CUDA events on the launching stream)
     timing = [ctx.mq_get_level_timing(l) + ctx.mq_get_kernel_timing(l) for l in range(len(wl.levels))]
     launches = ctx.mq_get_launch_count()
@@ -255,7 +259,39 @@ def time_device(binding, torch, wl, prec, steps, warmup, stream, F, rank=0, worl
     for l, (k0, k1) in enumerate(windows(wl, F, warmup + steps - 1)):
         ctx.mq_eval_level_device(l, k0, k1, outs[l], sums[l])
         kstats[l] = [ctx.mq_get_stats()]
-    return ctx, ms, timing, kstats, last, launches, level_sums
+    return ctx, ms, timing, kstats, last, launches, level_sums, probe
+
+
+def time_graph(binding, torch, wl, prec, steps, warmup, stream, F, ref_outs):
+    """The graph schedule: the windows of every level captured once as one CUDA graph
+    (mq_graph_capture), replayed once per step on that step's windows (mq_graph_launch with the new
+    start points): one graph launch per step, no host reads inside it."""
+    ctx, zs, ds = setup_context(binding, wl, stream.cuda_stream, prec)
+    win = windows(wl, F, 0)
+    outs = [torch.empty((lv.R, k1 - k0, 4), dtype=torch.float64, device="cuda") for lv, (k0, k1) in zip(wl.levels, win)]
+    ranges = [(l, k0, k1) for l, (k0, k1) in enumerate(win)]
+    t0 = time.perf_counter()
+    ctx.mq_graph_capture(ranges, outs, None)
+    capture_s = time.perf_counter() - t0
+    _, nodes = ctx.mq_get_graph_info()
+    for i in range(warmup):
+        ctx.mq_graph_launch([k0 for k0, _ in windows(wl, F, i)])
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for i in range(steps):
+        ctx.mq_graph_launch([k0 for k0, _ in windows(wl, F, warmup + i)])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    same = all(torch.equal(torch.from_numpy(r).to(o.device), o) for r, o in zip(ref_outs, outs))
+    ctx.close()
+    samples = step_samples(wl, F)
+    return {"value": samples * steps / (ms / 1e3), "unit": "samples/s", "ms_per_step": ms / steps,
+            "graph_launches_per_step": 1, "kernel_nodes": nodes, "capture_s": capture_s,
+            "equal_to_sequential_bit_for_bit": bool(same),
+            "note": "one CUDA graph per step (all levels' windows; streaming loops as conditional WHILE nodes)"}
 
 
 def max_rel_diff(a_levels, b_levels):
@@ -452,6 +488,43 @@ SAMPLE_KERNEL_TRAFFIC = {"source_sha256": "ea104697312beb4c1049dd2e4748a39fb6909
                          "level": 0, "precision": "mixed", "bytes_per_launch": 366.075648e6 + 27.624704e6}
 
 
+# ncu DRAM traffic of the operator sweep k_minres_q per algorithmic byte (one launch on the level
+# with mesh 1/256 of the six-level workload, 1,024 samples; profiles/stream_kernels_*.md), valid only
+# for the kernel source it was measured on
+KMINRES_TRAFFIC = {"source_sha256": "", "dram_per_algorithmic": None}
+
+
+def _stream_source_hash():
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in ("mq_stream.cu", "mq_device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2103_03407_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def kminres_roofline(probe, steps):
+    """Roofline of the largest kernel of the step: the streaming operator sweep, timed live with
+    CUDA events around its launches over the timed region; algorithmic bytes counted on the device
+    (per active sample and node: 4 arrays, 10 with the pending MINRES update)."""
+    ms, launches, nbytes = probe
+    if launches == 0 or ms <= 0:
+        return None
+    per_launch_ms = ms / launches
+    bytes_per_launch = nbytes / launches
+    achieved = bytes_per_launch / (per_launch_ms * 1e-3) / 1e9
+    peak, kind = hbm_peak()
+    t = KMINRES_TRAFFIC
+    traffic = None
+    if t["dram_per_algorithmic"] and t["source_sha256"] == _stream_source_hash():
+        traffic = t["dram_per_algorithmic"] * bytes_per_launch
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": f"k_minres_q (streaming operator sweep: {launches // max(1, steps)} launches "
+                                          f"per step, {per_launch_ms:.3f} ms per launch)",
+            "algorithmic_bytes_per_launch": bytes_per_launch, "peak_kind": kind,
+            "traffic_note": "ncu DRAM bytes per algorithmic byte of one captured launch x this launch average"}
+
+
 def _percta_source_hash():
     import hashlib
 
@@ -479,10 +552,10 @@ def fp64_peak_tflops(sm_max_mhz=None):
     return 152 * 2 * 2 * mhz * 1e6 / 1e12
 
 
-def percta_roofline(wl, level, st, prec, ms_per_launch, sm_max_mhz, samples):
+def percta_roofline(wl, level, st, prec, ms_per_launch, sm_max_mhz, samples, measured_peak=None):
     flops = percta_fp64_flops(wl, level, st, prec, samples)
     achieved = flops / (ms_per_launch * 1e-3) / 1e12
-    peak = fp64_peak_tflops(sm_max_mhz)
+    peak = measured_peak or fp64_peak_tflops(sm_max_mhz)
     lv = wl.levels[level]
     t = SAMPLE_KERNEL_TRAFFIC
     traffic = None
@@ -493,7 +566,8 @@ def percta_roofline(wl, level, st, prec, ms_per_launch, sm_max_mhz, samples):
             "kernel": f"sample_kernel (level {level}: {samples} samples per launch, "
                       f"{ms_per_launch:.2f} ms per launch)",
             "algorithmic_flops": flops,
-            "peak_kind": f"derived: FP64 units, 152 SMs x 4 flop/cycle x {sm_max_mhz or 2070:.0f} MHz"}
+            "peak_kind": ("measured: FP64 FMA chains kernel (mq_measure_fp64_peak)" if measured_peak else
+                          f"derived: FP64 units, 152 SMs x 4 flop/cycle x {sm_max_mhz or 2070:.0f} MHz")}
 
 
 def stream_roofline(wl, level, st, prec, ms_per_launch, samples):
@@ -533,7 +607,7 @@ def main():
     samples = step_samples(wl, F)  # samples per step (every level's window, every shift)
     with torch.cuda.stream(stream):
         with sampler:
-            ctx, ms, timing, kstats, outs, launches, lsums = time_device(
+            ctx, ms, timing, kstats, outs, launches, lsums, probe = time_device(
                 binding, torch, wl, args.precision, args.steps, args.warmup, stream, F, rank=rank, world=world,
                 sequential=args.schedule == "sequential")
     # one exchange of the per-level shift sums: the estimate over every rank's shifts
@@ -548,13 +622,17 @@ def main():
     if not args.no_plain and args.precision == "mixed" and rank == 0:
         # the plain FP64 GPU path on the same steps (same windows) and warm-up
         with torch.cuda.stream(stream):
-            ctxp, msp, _, _, outs_p, _, _ = time_device(binding, torch, wl, "fp64", args.steps, args.warmup, stream,
-                                                        F, sequential=args.schedule == "sequential")
+            ctxp, msp, _, _, outs_p, _, _, _ = time_device(binding, torch, wl, "fp64", args.steps, args.warmup,
+                                                           stream, F, sequential=args.schedule == "sequential")
         ctxp.close()
         plain = {"value": samples * args.steps / (msp / 1e3), "unit": "samples/s", "ms_per_step": msp / args.steps,
                  "steps": args.steps, "warmup": args.warmup,
                  "max_rel_diff_mixed_vs_fp64": max_rel_diff(outs, outs_p),
                  "note": "per-sample results of the last timed step of both paths compared"}
+    graph = None
+    if not args.no_graph and world == 1 and args.schedule == "sequential":
+        with torch.cuda.stream(stream):
+            graph = time_graph(binding, torch, wl, args.precision, args.steps, args.warmup, stream, F, outs)
     e2e = None
     if not args.no_e2e:
         steps_e2e = max(1, args.steps)
@@ -575,8 +653,16 @@ def main():
     per_launch = [wl.levels[l].R * (win[l][1] - win[l][0]) * args.steps / max(1, timing[l][2]) for l in range(nl)]
     clocks = sampler.summary()
     top = int(np.argmax(percta_ms))
-    roofline = percta_roofline(wl, top, lst[top], args.precision, percta_ms[top], clocks.get("sm_max_mhz"),
-                               per_launch[top])
+    fp64_peak = None
+    try:
+        fp64_peak = binding.mq_measure_fp64_peak(0)[0]
+    except Exception:
+        pass
+    roofline_sample = percta_roofline(wl, top, lst[top], args.precision, percta_ms[top], clocks.get("sm_max_mhz"),
+                                      per_launch[top], fp64_peak)
+    # the dominant kernel of the step (largest share of the launch list): the streaming operator
+    # sweep where the workload streams; the per-sample kernel otherwise
+    roofline = kminres_roofline(probe, args.steps) or roofline_sample
     stop = int(np.argmax(stream_ms))
     roofline_stream = (stream_roofline(wl, stop, lst[stop], args.precision, stream_ms[stop], per_launch[stop])
                        if stream_ms[stop] > 0 else None)
@@ -586,6 +672,8 @@ def main():
         "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
         "config": dict(workload_config(wl, args.precision, world, F), schedule=args.schedule),
         "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "roofline_stream": roofline_stream,
+        "roofline_sample_kernel": roofline_sample, "fp64_peak_measured_tflops": fp64_peak,
+        "graph_schedule": graph,
         "clocks": clocks,
         "per_level": [{"level": l, "kernel_ms": coef_ms[l] + sample_ms[l], "coef_ms": coef_ms[l],
                        "sample_ms": sample_ms[l], "percta_ms": percta_ms[l], "stream_ms": stream_ms[l],

@@ -251,6 +251,23 @@ mq_status mq_eval_levels_device(mq_ctx* ctx, int32_t nlevels, const int32_t* lev
 mq_status mq_graph_capture(mq_ctx* ctx, int32_t nranges, const int32_t* levels, const uint32_t* k0s,
                            const uint32_t* k1s, double* const* d_per_sample, double* const* d_shift_sums);
 mq_status mq_graph_launch(mq_ctx* ctx, const uint32_t* k0s);
+/* Live timing of the streaming tier's operator sweep (its largest kernel: the MINRES operator
+ * application with the pending update, once per inner iteration): with on = 1, every later
+ * host-driven streaming solve records CUDA events on the context stream around each launch of
+ * that kernel and counts on the device the algorithmic bytes the launches move (per active sample
+ * and interior node: weights and operand 4 arrays, plus 6 for the pending MINRES update).  Turning
+ * it on (or off) clears the totals.  mq_get_kernel_probe returns the summed launch time (ms), the
+ * launches and the algorithmic bytes since then (any output may be NULL).  Graph launches are not
+ * timed. */
+mq_status mq_set_kernel_probe(mq_ctx* ctx, int32_t on);
+
+/* Measured FP64 throughput of device `device`: a kernel of independent fused multiply-add chains
+ * (8 per thread, 8 CTAs of 256 threads per SM), best of three timed launches after a warm-up;
+ * tflops counts an FMA as two operations, ms is that launch's time.  The denominator of the FP64
+ * roofline of the per-sample kernel. */
+mq_status mq_measure_fp64_peak(int device, double* tflops, double* ms);
+mq_status mq_get_kernel_probe(mq_ctx* ctx, double* ms, uint64_t* launches, uint64_t* bytes);
+
 /* captured: 1 while a graph is held; kernel_nodes: the kernels captured into it (the loop bodies
  * counted once).  Either output may be NULL. */
 mq_status mq_get_graph_info(mq_ctx* ctx, int32_t* captured, uint64_t* kernel_nodes);

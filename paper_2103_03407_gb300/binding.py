@@ -30,7 +30,8 @@ EXPORTS = [
     "mq_get_stats", "mq_last_error", "mq_cbc_lattice", "mq_lattice_points_device", "mq_coefficients_device",
     "mq_apply_operator_device", "mq_twogrid_samples_noalloc", "mq_set_lattice_embedded", "mq_set_reuse",
     "mq_cbc_embedded_lattice", "mq_get_sums", "mq_estimate_sums", "mq_run_adaptive", "mq_set_level_config",
-    "mq_autotune_level", "mq_graph_capture", "mq_graph_launch", "mq_get_graph_info",
+    "mq_autotune_level", "mq_graph_capture", "mq_graph_launch", "mq_get_graph_info", "mq_set_kernel_probe",
+    "mq_get_kernel_probe", "mq_measure_fp64_peak",
 ]
 
 
@@ -102,6 +103,9 @@ def load(path: str = LIB_PATH):
                               C.POINTER(C.c_void_p)], C.c_int),
         "mq_graph_launch": ([P, C.POINTER(u32)], C.c_int),
         "mq_get_graph_info": ([P, C.POINTER(i32), C.POINTER(C.c_uint64)], C.c_int),
+        "mq_set_kernel_probe": ([P, i32], C.c_int),
+        "mq_get_kernel_probe": ([P, dp, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)], C.c_int),
+        "mq_measure_fp64_peak": ([C.c_int, dp, dp], C.c_int),
         "mq_autotune_level": ([P, i32, u32, C.c_char_p, C.POINTER(mq_tune_choice)], C.c_int),
         "mq_estimate_sums": ([i32, C.POINTER(i32), dp, C.POINTER(C.c_uint64), i32, dp, dp, dp, dp], C.c_int),
         "mq_set_precision": ([P, C.c_int, f64], C.c_int),
@@ -283,6 +287,15 @@ class Context:
         self._check(self.lib.mq_get_graph_info(self.h, C.byref(cap), C.byref(nodes)))
         return bool(cap.value), nodes.value
 
+    def mq_set_kernel_probe(self, on=1):
+        self._check(self.lib.mq_set_kernel_probe(self.h, int(on)))
+
+    def mq_get_kernel_probe(self):
+        """(ms, launches, algorithmic bytes) of the operator sweep since the probe was switched on."""
+        ms, n, b = C.c_double(), C.c_uint64(), C.c_uint64()
+        self._check(self.lib.mq_get_kernel_probe(self.h, C.byref(ms), C.byref(n), C.byref(b)))
+        return ms.value, n.value, b.value
+
     def mq_estimate(self):
         L = len(self.levels)
         m, se = C.c_double(), C.c_double()
@@ -366,6 +379,16 @@ def mq_twogrid_samples_noalloc(n_fine, n_coarse, n_prev, precision, B, d_a_fine,
                                         C.c_void_p(stream) if stream else None)
     if st != MQ_OK:
         raise MQError(st, "mq_twogrid_samples_noalloc failed")
+
+
+def mq_measure_fp64_peak(device=0):
+    """(TFLOP/s, ms) of the library's FP64 fused multiply-add throughput kernel on `device`."""
+    lib = load()
+    tf, ms = C.c_double(), C.c_double()
+    st = lib.mq_measure_fp64_peak(int(device), C.byref(tf), C.byref(ms))
+    if st != MQ_OK:
+        raise MQError(st, "mq_measure_fp64_peak failed")
+    return tf.value, ms.value
 
 
 def mq_estimate_sums(level_sums, npoints, shared=False):

@@ -81,6 +81,9 @@ struct mq_ctx {
   std::vector<size_t> g_off;       // offset of each captured range's sums in gsums
   std::vector<int> last_ppp;       // per level: points per pass of the last evaluation
   uint64_t graph_kernels = 0;      // kernel nodes captured (loop bodies counted once)
+  bool probe_on = false;           // live timing of the streaming operator sweep
+  mq::KernelProbe probe;
+  DevBuf probe_bytes;
 
   int prec = MQ_PREC_FP64;
   double tol_lin = 0.0;  // 0: default of the precision mode
@@ -513,6 +516,7 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
     s.max_outer = p.max_outer;
     s.omega = p.omega;
     s.nu = g.nu > 0 ? g.nu : (c->opt_nu > 0 ? c->opt_nu : 1);
+    s.probe = (c->probe_on && !c->capturing) ? &c->probe : nullptr;
     if (p.mode_f == 2) {
       s.n = g.nf;
       s.a = (const double*)c->af.p;
@@ -580,6 +584,7 @@ mq_status collect_stats(mq_ctx* c, size_t B, int* any_flags) {
 mq_status timing(mq_ctx* c, int level) {
   float t0 = 0, t1 = 0, t2 = 0;
   MQ_CUDA(c, cudaEventSynchronize(c->ev[2]));
+  if (c->probe_on) MQ_CUDA(c, c->probe.collect());
   MQ_CUDA(c, cudaEventElapsedTime(&t0, c->ev[0], c->ev[1]));
   MQ_CUDA(c, cudaEventElapsedTime(&t1, c->ev[1], c->ev[2]));
   MQ_CUDA(c, cudaEventElapsedTime(&t2, c->ev[1], c->ev[3]));
@@ -800,7 +805,11 @@ mq_status mq_destroy(mq_ctx* c) {
   graph_release(c);
   for (cudaStream_t& b : c->gbody)
     if (b) cudaStreamDestroy(b);
-  for (DevBuf* b : {&c->gcount, &c->gsums, &c->gflags, &c->gk0})
+  for (auto& pe : c->probe.ev) {
+    cudaEventDestroy(pe.first);
+    cudaEventDestroy(pe.second);
+  }
+  for (DevBuf* b : {&c->gcount, &c->gsums, &c->gflags, &c->gk0, &c->probe_bytes})
     if (b->p) cudaFree(b->p);
   for (DevBuf* b : {&c->Y, &c->af, &c->ac, &c->ap, &c->out, &c->stat, &c->outer, &c->scratch, &c->sums_d,
                     &c->flags_d, &c->uout, &c->misc, &c->upad, &c->arena, &c->ysl, &c->tc_err})
@@ -1466,6 +1475,39 @@ mq_status mq_graph_launch(mq_ctx* c, const uint32_t* k0s) {
   }
   c->stats.samples = samples;
   return flags_status(c, fl);
+}
+
+mq_status mq_measure_fp64_peak(int device, double* tflops, double* ms) {
+  if (!tflops || !ms) return MQ_EINVAL;
+  return mq::measure_fp64_peak(device, tflops, ms) == cudaSuccess ? MQ_OK : MQ_ECUDA;
+}
+
+mq_status mq_set_kernel_probe(mq_ctx* c, int32_t on) {
+  if (!c) return MQ_EINVAL;
+  MQ_CUDA(c, cudaSetDevice(c->device));
+  mq_status st = grow(c, c->probe_bytes, sizeof(unsigned long long));
+  if (st != MQ_OK) return st;
+  MQ_CUDA(c, cudaStreamSynchronize(c->stream));
+  MQ_CUDA(c, cudaMemset(c->probe_bytes.p, 0, sizeof(unsigned long long)));
+  c->probe.ms = 0.0;
+  c->probe.launches = 0;
+  c->probe.used = 0;
+  c->probe.d_bytes = (unsigned long long*)c->probe_bytes.p;
+  c->probe_on = on != 0;
+  return MQ_OK;
+}
+
+mq_status mq_get_kernel_probe(mq_ctx* c, double* ms, uint64_t* launches, uint64_t* bytes) {
+  if (!c) return MQ_EINVAL;
+  MQ_CUDA(c, cudaSetDevice(c->device));
+  MQ_CUDA(c, cudaStreamSynchronize(c->stream));
+  MQ_CUDA(c, c->probe.collect());
+  unsigned long long b = 0;
+  if (c->probe_bytes.p) MQ_CUDA(c, cudaMemcpy(&b, c->probe_bytes.p, sizeof b, cudaMemcpyDeviceToHost));
+  if (ms) *ms = c->probe.ms;
+  if (launches) *launches = c->probe.launches;
+  if (bytes) *bytes = (uint64_t)b;
+  return MQ_OK;
 }
 
 mq_status mq_get_graph_info(mq_ctx* c, int32_t* captured, uint64_t* kernel_nodes) {

@@ -55,6 +55,22 @@ __global__ void psi_kernel(int n, int s, const int* __restrict__ k1, const int* 
   }
 }
 
+// FP64 fused multiply-add throughput: eight independent chains per thread keep the FP64 pipes
+// busy (the denominator of the per-sample kernel's FP64 roofline)
+__global__ void __launch_bounds__(256) fp64_fma_kernel(double* out, int iters, double a, double b) {
+  double x[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) x[i] = 1e-3 * threadIdx.x + i;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = fma(x[i], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s += x[i];
+  if (s == -1.0) out[0] = s;  // never true; keeps the chains alive
+}
+
 constexpr int GBM = 64, GBN = 128, GBK = 16;
 
 // C[b][t] = a0 + sum_j Y[b*ldy + j] Psi[j*nT + t]; 256 threads as 16 x 16, 4 x 8 outputs each.
@@ -118,6 +134,41 @@ int grid_for(size_t tot, int threads) {
 }
 
 }  // namespace
+
+cudaError_t measure_fp64_peak(int device, double* tflops, double* ms_out) {
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) return e;
+  int sms = 0;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess) return e;
+  double* d = nullptr;
+  if ((e = cudaMalloc(&d, sizeof(double))) != cudaSuccess) return e;
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  const int blocks = sms * 8, threads = 256, iters = 1 << 14;
+  float best = 1e30f;
+  for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+    cudaEventRecord(e0, st);
+    fp64_fma_kernel<<<blocks, threads, 0, st>>>(d, iters, 0.9999999, 1e-7);
+    cudaEventRecord(e1, st);
+    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+    float t = 0.0f;
+    cudaEventElapsedTime(&t, e0, e1);
+    if (rep > 0 && t < best) best = t;  // the first launch warms up
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st) cudaStreamDestroy(st);
+  cudaFree(d);
+  if (e != cudaSuccess) return e;
+  const double flops = 2.0 * 8.0 * iters * (double)blocks * threads;
+  *tflops = flops / (best * 1e-3) / 1e12;
+  *ms_out = best;
+  return cudaSuccess;
+}
 
 cudaError_t launch_lattice_points(const uint32_t* d_z, uint32_t N, const double* d_delta, int R, int s, uint32_t k0,
                                   int npts, int mbits, double* d_Y, cudaStream_t st, const uint32_t* d_kshift) {

@@ -5,6 +5,8 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <utility>
+#include <vector>
 
 namespace mq {
 
@@ -42,6 +44,20 @@ struct SampleLaunch {
                            // 1 in the kernel with an FP64 inner solve, 2 elsewhere (streaming)
 };
 
+// Live timing of the streaming tier's operator sweep (k_minres_q, the largest kernel of the
+// streaming solves): CUDA events around each of its launches (host-driven solves only) and a
+// device counter of the algorithmic bytes the launches moved (per active sample and interior node:
+// the operator's weights and vector plus the pending MINRES update).
+struct KernelProbe {
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;  // reused pool
+  size_t used = 0;
+  double ms = 0.0;
+  uint64_t launches = 0;
+  unsigned long long* d_bytes = nullptr;  // device counter
+  cudaError_t next(std::pair<cudaEvent_t, cudaEvent_t>** out);
+  cudaError_t collect();  // after the stream has been synchronised
+};
+
 // Batched streaming fine solve (mq_stream.cu): B samples on mesh 1/n, coarse pairs from mesh 1/nc.
 struct StreamSolve {
   int n, nc, B;
@@ -61,6 +77,7 @@ struct StreamSolve {
   int max_inner, max_outer;
   double omega;
   int nu;                  // Jacobi sweeps before and after each coarse-grid correction (1 or 2)
+  KernelProbe* probe;      // NULL, or the live timing of the operator sweep
 };
 // Graph mode of the streaming solve: the refinement and MINRES loops become conditional WHILE nodes
 // of the CUDA graph being captured on the solve's stream (no host reads); their bodies are
@@ -104,6 +121,9 @@ cudaError_t set_sample_smem(int mixed, int bytes);
 // never lowers it, so launches from concurrent host threads (levels evaluated at the same time)
 // cannot undo one another's setting between the call and the launch.
 cudaError_t raise_smem_limit(const void* func, int bytes);
+
+// FP64 FMA throughput of the device (TFLOP/s) from a kernel of independent FMA chains
+cudaError_t measure_fp64_peak(int device, double* tflops, double* ms);
 
 // Coefficient building blocks (mq_coef.cu)
 // mbits > 0: embedded rule in radical-inverse order with N = 2^mbits (point k uses index rev(k))

@@ -621,14 +621,23 @@ __global__ void __launch_bounds__(kSubThreads) k_subcycle(int ns, int B, const i
 // ---------------------------------------------------------------------------------------------
 // MINRES sweeps
 // K1: pending w/x update; q = (A - sigma M) z * ig; partial <q, z>
+// work: NULL, or a device counter of the algorithmic bytes moved (thread 0 of each active CTA adds
+// its tile's interior nodes times the bytes per node: 4 arrays without a pending update, 10 with)
 template <typename T>
 __global__ void k_minres_q(int n, int B, const int* __restrict__ act, const SS<T>* __restrict__ ss,
                            const T* __restrict__ wx, const T* __restrict__ wy, const double* __restrict__ sigma,
                            int sig_stride, const T* __restrict__ z, const T* __restrict__ zp, T* __restrict__ wo,
-                           const T* __restrict__ w, T* __restrict__ xi, T* __restrict__ qv, double* part) {
+                           const T* __restrict__ w, T* __restrict__ xi, T* __restrict__ qv, double* part,
+                           unsigned long long* work) {
   const int nt = tiles_interior(n);
   const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
   if (b >= B || !act[b]) return;
+  if (work && threadIdx.x == 0) {
+    const long tot = (long)(n - 1) << ilog2(n);
+    const long q0 = (long)ch * kTile, q1 = q0 + kTile < tot ? q0 + kTile : tot;
+    const long nodes = (q1 - q0) - (q1 / n - q0 / n);  // minus the i == n slots of the walk
+    atomicAdd(work, (unsigned long long)(nodes * (ss[b].pend ? 10 : 4) * (long)sizeof(T)));
+  }
   const int ld = n + 1;
   const size_t off = (size_t)b * gsz(n);
   const SS<T> S = ss[b];
@@ -1192,7 +1201,7 @@ cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st, c
     if ((e = open_while(b0, b1, hi)) != cudaSuccess) return e;
     for (int half = 0; half < 2; ++half) {
       ++tl_launches, k_minres_q<T><<<B * nt, kThreads, 0, b1>>>(n, B, A.act, A.ss, A.wx[0], A.wy[0], s.lamH,
-                                                              s.lam_stride, z, zn, wo, w, A.xi, A.q, A.part);
+                                                              s.lam_stride, z, zn, wo, w, A.xi, A.q, A.part, nullptr);
       LAUNCH_CHECK();
       ++tl_launches, k_sc_retire<T><<<gs, 256, 0, b1>>>(B, A.act, A.ss);
       { T* tt = wo; wo = w; w = tt; }
@@ -1238,9 +1247,15 @@ cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st, c
     ++tl_launches, k_sc_gamma0<T><<<gs, 256, 0, st>>>(B, nchd, A.part, A.act, A.ss);
     LAUNCH_CHECK();
     for (int j = 0; j < s.max_inner; ++j) {
+      std::pair<cudaEvent_t, cudaEvent_t>* pe = nullptr;
+      if (s.probe) {
+        if ((e = s.probe->next(&pe)) != cudaSuccess) return e;
+        cudaEventRecord(pe->first, st);
+      }
       ++tl_launches, k_minres_q<T><<<B * nt, kThreads, 0, st>>>(n, B, A.act, A.ss, A.wx[0], A.wy[0], s.lamH, s.lam_stride, z, zn,
-                                                 wo, w, A.xi, A.q, A.part);
+                                                 wo, w, A.xi, A.q, A.part, s.probe ? s.probe->d_bytes : nullptr);
       LAUNCH_CHECK();
+      if (pe) cudaEventRecord(pe->second, st);
       // samples that converged in the previous Givens step have now applied their update
       ++tl_launches, k_sc_retire<T><<<gs, 256, 0, st>>>(B, A.act, A.ss);
       { T* tt = wo; wo = w; w = tt; }
@@ -1302,6 +1317,30 @@ size_t stream_arena_bytes(int n, int B, int mixed) {
 }
 
 uint64_t stream_launches() { return tl_launches; }
+
+cudaError_t KernelProbe::next(std::pair<cudaEvent_t, cudaEvent_t>** out) {
+  if (used == ev.size()) {
+    std::pair<cudaEvent_t, cudaEvent_t> p{nullptr, nullptr};
+    cudaError_t e = cudaEventCreate(&p.first);
+    if (e == cudaSuccess) e = cudaEventCreate(&p.second);
+    if (e != cudaSuccess) return e;
+    ev.push_back(p);
+  }
+  *out = &ev[used++];
+  return cudaSuccess;
+}
+
+cudaError_t KernelProbe::collect() {
+  for (size_t i = 0; i < used; ++i) {
+    float t = 0.0f;
+    cudaError_t e = cudaEventElapsedTime(&t, ev[i].first, ev[i].second);
+    if (e != cudaSuccess) return e;
+    ms += t;
+  }
+  launches += used;
+  used = 0;
+  return cudaSuccess;
+}
 
 cudaError_t stream_solve(const StreamSolve& s, int mixed, void* arena, cudaStream_t st, const StreamGraph* sg) {
   return mixed ? stream_solve_t<float>(s, arena, st, sg) : stream_solve_t<double>(s, arena, st, sg);
