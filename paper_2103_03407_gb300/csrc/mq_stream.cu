@@ -42,10 +42,17 @@ constexpr int kTile = kThreads * kPer;       // nodes per CTA
 constexpr int kSub = 32;                     // meshes up to 1/32 run inside one CTA
 constexpr int kSubThreads = 128;             // threads of that CTA (more samples per SM than 256)
 
+// Node arrays of the streaming tier: n + 1 rows of sld(n) = n + 4 entries (a multiple of four,
+// so every row of an FP32 array starts on a 16-byte boundary and can be moved as float4), node
+// (i, j) at j sld(n) + i; the boundary ring (i or j in {0, n}) and the padding columns n+1..n+3
+// hold zeros.  The on-chip sub-cycle keeps its own (n+1) x (n+1) layout (bsub, xsub).
+__host__ __device__ inline int sld(int n) { return n + 4; }
+__host__ __device__ inline size_t ssz(int n) { return (size_t)(n + 1) * (size_t)sld(n); }
+
 // tiles of kTile interior nodes per sample; n * n / kTile (n a power of two) also covers the
 // column walk below, whose threads own one column and kPer rows each
 __host__ __device__ inline int tiles_interior(int n) { return n * n > kTile ? n * n / kTile : 1; }
-__host__ __device__ inline int tiles_padded(int n) { return (int)((gsz(n) + kTile - 1) / kTile); }
+__host__ __device__ inline int tiles_padded(int n) { return (int)((ssz(n) + kTile - 1) / kTile); }
 
 // Column walk over tile ch of mesh n: the thread owns column i and the nr = j1 - j0 (1..kPer)
 // rows j0 .. j1-1; consecutive threads own consecutive columns, so every row access is coalesced.
@@ -67,7 +74,7 @@ template <class F>
 __device__ __forceinline__ void for_tile(int n, int ch, F f) {
   const int lg = ilog2(n);
   const int tot = (n - 1) << lg;
-  const int ld = n + 1;
+  const int ld = sld(n);
   const int q0 = ch * kTile + threadIdx.x;
 #pragma unroll
   for (int k = 0; k < kPer; ++k) {
@@ -126,8 +133,8 @@ __global__ void k_weights(int n, int B, const S* __restrict__ cells, size_t cstr
   if (b >= B || (act && !act[b])) return;
   const S* lo = cells + (size_t)b * cstride;
   const S* up = lo + (size_t)n * n;
-  const size_t V = gsz(n);
-  const int ld = n + 1;
+  const size_t V = ssz(n);
+  const int ld = sld(n);
   int bad = 0;
   float amax = 0.0f;
   for (int k = 0; k < kPer; ++k) {
@@ -205,7 +212,7 @@ __global__ void k_interp(int n, int nc, int B, const double* __restrict__ uH, do
   const int lr = ilog2(n / nc), rm = (1 << lr) - 1, ldc = nc + 1;
   const double inv = 1.0 / (double)(1 << lr);
   const double* __restrict__ u = uH + (size_t)b * gsz(nc);
-  double* x = x64 + (size_t)b * gsz(n);
+  double* x = x64 + (size_t)b * ssz(n);
   for_tile(n, ch, [&](int p, int i, int j) {
     const int I = i >> lr, J = j >> lr;
     const double xi_ = (double)(i & rm) * inv, et = (double)(j & rm) * inv;
@@ -222,9 +229,9 @@ __global__ void k_rhs(int n, int B, const double* __restrict__ x64, double* __re
   const int nt = tiles_interior(n);
   const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
   if (b >= B) return;
-  const int ld = n + 1;
+  const int ld = sld(n);
   const double hm = 1.0 / (12.0 * n * n);
-  const size_t off = (size_t)b * gsz(n);
+  const size_t off = (size_t)b * ssz(n);
   const double* __restrict__ x = x64 + off;
   double acc[1] = {0.0};
   for_tile(n, ch, [&](int p, int, int) {
@@ -290,7 +297,7 @@ __global__ void k_inner_init(int n, int B, const int* __restrict__ act, const SS
   const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
   if (b >= B || !act[b]) return;
   const T rs = ss[b].rs;
-  const size_t off = (size_t)b * gsz(n);
+  const size_t off = (size_t)b * ssz(n);
   for_tile(n, ch, [&](int p, int, int) {
     v[off + p] *= rs;
     vo[off + p] = T(0);
@@ -310,8 +317,8 @@ __global__ void k_smooth2_from_zero(int n, int B, const int* __restrict__ act, c
   const int nt = tiles_interior(n);
   const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
   if (b >= B || !act[b]) return;
-  const int ld = n + 1;
-  const size_t off = (size_t)b * gsz(n);
+  const int ld = sld(n);
+  const size_t off = (size_t)b * ssz(n);
   const T* __restrict__ W = wx + off;
   const T* __restrict__ Y = wy + off;
   const T* __restrict__ D = dinv + off;
@@ -352,45 +359,47 @@ __global__ void k_smooth2_from_zero(int n, int B, const int* __restrict__ act, c
 }
 
 // residual r = b - A x restricted with P^T to the coarse right-hand side
+// bc: rows of ldo entries (sld(n/2) for a streamed level, n/2 + 1 for the sub-cycle's input)
 template <typename T>
 __global__ void k_restrict(int n, int B, const int* __restrict__ act, const T* __restrict__ wx,
                            const T* __restrict__ wy, const T* __restrict__ bb, const T* __restrict__ x,
-                           T* __restrict__ bc) {
+                           T* __restrict__ bc, int ldo) {
   const int m = n / 2;
   const int nt = tiles_interior(m);
   const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
   if (b >= B || !act[b]) return;
-  const int ld = n + 1;
-  const size_t off = (size_t)b * gsz(n);
+  const int ld = sld(n);
+  const size_t off = (size_t)b * ssz(n);
   const T* __restrict__ W = wx + off;
   const T* __restrict__ Y = wy + off;
   const T* __restrict__ R = bb + off;
   const T* __restrict__ X = x + off;
-  T* __restrict__ C = bc + (size_t)b * gsz(m);
-  for_tile(m, ch, [&](int P, int I, int J) {
+  T* __restrict__ C = bc + (size_t)b * (size_t)(m + 1) * ldo;
+  for_tile(m, ch, [&](int, int I, int J) {
     const int p = (2 * J) * ld + 2 * I;
     auto res = [&](int q) { return R[q] - stiff<T, T>(W, Y, X, q, ld); };
-    C[P] = res(p) + T(0.5) * ((res(p + 1) + res(p - 1)) + (res(p + ld) + res(p - ld)) +
+    C[J * ldo + I] = res(p) + T(0.5) * ((res(p + 1) + res(p - 1)) + (res(p + ld) + res(p - ld)) +
                               (res(p + ld + 1) + res(p - ld - 1)));
   });
 }
 
 // t = x + P xc, then one Jacobi step: out = t + om D^-1 (b - A t)
+// xc: rows of ldc entries (sld(n/2) for a streamed level, n/2 + 1 for the sub-cycle's output)
 template <typename T>
 __global__ void k_prolong_smooth(int n, int B, const int* __restrict__ act, const T* __restrict__ wx,
                                  const T* __restrict__ wy, const T* __restrict__ dinv, const T* __restrict__ bb,
-                                 const T* __restrict__ x, const T* __restrict__ xc, T* __restrict__ out) {
+                                 const T* __restrict__ x, const T* __restrict__ xc, T* __restrict__ out, int ldc) {
   const int nt = tiles_interior(n);
   const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
   if (b >= B || !act[b]) return;
-  const int ld = n + 1, ldc = n / 2 + 1;
-  const size_t off = (size_t)b * gsz(n);
+  const int ld = sld(n);
+  const size_t off = (size_t)b * ssz(n);
   const T* __restrict__ W = wx + off;
   const T* __restrict__ Y = wy + off;
   const T* __restrict__ D = dinv + off;
   const T* __restrict__ R = bb + off;
   const T* __restrict__ X = x + off;
-  const T* __restrict__ XC = xc + (size_t)b * gsz(n / 2);
+  const T* __restrict__ XC = xc + (size_t)b * (size_t)(n / 2 + 1) * ldc;
   T* __restrict__ O = out + off;
   int i, j0, nr;
   if (!column_walk(n, ch, i, j0, nr)) return;
@@ -433,19 +442,19 @@ __global__ void k_prolong_smooth(int n, int B, const int* __restrict__ act, cons
 template <typename T>
 __global__ void k_restrict1(int n, int B, const int* __restrict__ act, const T* __restrict__ wx,
                             const T* __restrict__ wy, const T* __restrict__ dinv, const T* __restrict__ bb,
-                            T* __restrict__ bc) {
+                            T* __restrict__ bc, int ldo) {
   const int m = n / 2;
   const int nt = tiles_interior(m);
   const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
   if (b >= B || !act[b]) return;
-  const int ld = n + 1;
-  const size_t off = (size_t)b * gsz(n);
+  const int ld = sld(n);
+  const size_t off = (size_t)b * ssz(n);
   const T* __restrict__ W = wx + off;
   const T* __restrict__ Y = wy + off;
   const T* __restrict__ D = dinv + off;
   const T* __restrict__ R = bb + off;
-  T* __restrict__ C = bc + (size_t)b * gsz(m);
-  for_tile(m, ch, [&](int P, int I, int J) {
+  T* __restrict__ C = bc + (size_t)b * (size_t)(m + 1) * ldo;
+  for_tile(m, ch, [&](int, int I, int J) {
     const int p = (2 * J) * ld + 2 * I;
     auto x1 = [&](int q) { return D[q] * R[q]; };
     auto res = [&](int q) {
@@ -453,8 +462,8 @@ __global__ void k_restrict1(int n, int B, const int* __restrict__ act, const T* 
       return R[q] - (W[q] * (xq - x1(q + 1)) + W[q - 1] * (xq - x1(q - 1)) + Y[q] * (xq - x1(q + ld)) +
                      Y[q - ld] * (xq - x1(q - ld)));
     };
-    C[P] = res(p) + T(0.5) * ((res(p + 1) + res(p - 1)) + (res(p + ld) + res(p - ld)) +
-                              (res(p + ld + 1) + res(p - ld - 1)));
+    C[J * ldo + I] = res(p) + T(0.5) * ((res(p + 1) + res(p - 1)) + (res(p + ld) + res(p - ld)) +
+                                        (res(p + ld + 1) + res(p - ld - 1)));
   });
 }
 
@@ -463,18 +472,18 @@ __global__ void k_restrict1(int n, int B, const int* __restrict__ act, const T* 
 template <typename T, bool DOT>
 __global__ void k_prolong_smooth1(int n, int B, const int* __restrict__ act, const T* __restrict__ wx,
                                   const T* __restrict__ wy, const T* __restrict__ dinv, const T* __restrict__ bb,
-                                  const T* __restrict__ xc, T* __restrict__ out, const T* __restrict__ dotv,
+                                  const T* __restrict__ xc, int ldc, T* __restrict__ out, const T* __restrict__ dotv,
                                   double* part) {
   const int nt = tiles_interior(n);
   const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
   if (b >= B || !act[b]) return;
-  const int ld = n + 1, ldc = n / 2 + 1;
-  const size_t off = (size_t)b * gsz(n);
+  const int ld = sld(n);
+  const size_t off = (size_t)b * ssz(n);
   const T* __restrict__ W = wx + off;
   const T* __restrict__ Y = wy + off;
   const T* __restrict__ D = dinv + off;
   const T* __restrict__ R = bb + off;
-  const T* __restrict__ XC = xc + (size_t)b * gsz(n / 2);
+  const T* __restrict__ XC = xc + (size_t)b * (size_t)(n / 2 + 1) * ldc;
   T* __restrict__ O = out + off;
   T acc[1] = {T(0)};
   for_tile(n, ch, [&](int p, int i, int j) {
@@ -501,8 +510,8 @@ __global__ void k_smooth(int n, int B, const int* __restrict__ act, const T* __r
   const int nt = tiles_interior(n);
   const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
   if (b >= B || !act[b]) return;
-  const int ld = n + 1;
-  const size_t off = (size_t)b * gsz(n);
+  const int ld = sld(n);
+  const size_t off = (size_t)b * ssz(n);
   const T* __restrict__ W = wx + off;
   const T* __restrict__ Y = wy + off;
   const T* __restrict__ D = dinv + off;
@@ -585,22 +594,26 @@ __global__ void __launch_bounds__(kThreads) k_sub_build(int ns, int B, const T* 
 template <typename T>
 __global__ void __launch_bounds__(kSubThreads) k_subcycle(int ns, int B, const int* __restrict__ act,
                                                        const char* __restrict__ subw, size_t wbytes,
-                                                       const T* __restrict__ bin, T* __restrict__ xout, int nu, T om,
-                                                       double* part, const T* __restrict__ dotv) {
+                                                       const T* __restrict__ bin, T* __restrict__ xout, int ldio,
+                                                       int nu, T om, double* part, const T* __restrict__ dotv) {
+  // bin / xout: rows of ldio entries (ns + 1 for the sub-cycle's own arrays, sld(ns) when the
+  // whole V-cycle of a streamed mesh runs here); the shared-memory copies have rows of ns + 1
   extern __shared__ __align__(16) char sm[];
   __shared__ MGDesc<T> mg;
   const int b = blockIdx.x;
   if (b >= B || !act[b]) return;
   const size_t V = gsz(ns);
+  const int ld = ns + 1;
   Carver w((char*)subw + (size_t)b * wbytes), v(sm);
   MGDesc<T> d;
   T* b0 = v.take<T>(V);
   T* x0 = v.take<T>(V);
   carve_mg_split<T>(w, v, ns, d);
   if (threadIdx.x == 0) mg = d;
-  const T* src = bin + (size_t)b * V;
+  const T* src = bin + (size_t)b * (size_t)(ns + 1) * ldio;
   for_all(V, [&](size_t q) {
-    b0[q] = src[q];
+    const int i = (int)(q % ld), j = (int)(q / ld);
+    b0[q] = src[j * ldio + i];
     x0[q] = T(0);
   });
   for (int l = 0; l < d.L; ++l) {
@@ -613,8 +626,11 @@ __global__ void __launch_bounds__(kSubThreads) k_subcycle(int ns, int B, const i
   __syncthreads();
   // with dotv (the right-hand side itself, copied to b0) also <v, x>
   T acc[1] = {vcycle<T>(mg, b0, x0, om, dotv ? b0 : nullptr, nu)};
-  T* dst = xout + (size_t)b * V;
-  for_all(V, [&](size_t q) { dst[q] = x0[q]; });
+  T* dst = xout + (size_t)b * (size_t)(ns + 1) * ldio;
+  for_all(V, [&](size_t q) {
+    const int i = (int)(q % ld), j = (int)(q / ld);
+    dst[j * ldio + i] = x0[q];
+  });
   if (dotv) tile_partials<1, T>(acc, part, (size_t)b);
 }
 
@@ -638,8 +654,8 @@ __global__ void k_minres_q(int n, int B, const int* __restrict__ act, const SS<T
     const long nodes = (q1 - q0) - (q1 / n - q0 / n);  // minus the i == n slots of the walk
     atomicAdd(work, (unsigned long long)(nodes * (ss[b].pend ? 10 : 4) * (long)sizeof(T)));
   }
-  const int ld = n + 1;
-  const size_t off = (size_t)b * gsz(n);
+  const int ld = sld(n);
+  const size_t off = (size_t)b * ssz(n);
   const SS<T> S = ss[b];
   const T sigm = S.sigm;
   const T* __restrict__ W = wx + off;
@@ -659,6 +675,167 @@ __global__ void k_minres_q(int n, int B, const int* __restrict__ act, const SS<T
   tile_partials<1, T>(acc, part, (size_t)b * nt + ch);
 }
 
+// ---------------------------------------------------------------------------------------------
+// Vectorised FP32 sweeps: each thread owns four consecutive nodes of one row (columns 4m .. 4m+3,
+// one float4 of every operand: rows of the streaming layout start on 16-byte boundaries), so a warp
+// moves 512 contiguous bytes per operand and row with one instruction.  Stencil neighbours across
+// the four-node group come from the float4s of the rows above and below and from two scalars at
+// columns 4m-1 and 4m+4.  Column 0 is the boundary: its outputs are written as zero.
+constexpr int kVec = 4;
+
+// CTAs per sample of a vectorised sweep over the interior rows of mesh n
+__host__ __device__ inline int tiles_vec(int n) {
+  const long t = (long)(n - 1) * (n / kVec);
+  return (int)((t + kThreads - 1) / kThreads);
+}
+
+// row j (1..n-1) and first column 4m of thread tid of tile ch; false beyond the last row
+__device__ __forceinline__ bool vec_walk(int n, int ch, int& j, int& c0) {
+  const int per_row = n / kVec;
+  const int g = ch * kThreads + threadIdx.x;
+  j = g / per_row + 1;
+  c0 = (g % per_row) * kVec;
+  return j < n;
+}
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ float at(const float4& v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
+
+// K1, vectorised: the pending w/x update, q = (A - sigma M) z * ig and the partial <q, z>
+__global__ void k_minres_q4(int n, int B, const int* __restrict__ act, const SS<float>* __restrict__ ss,
+                            const float* __restrict__ wx, const float* __restrict__ wy, const float* __restrict__ z,
+                            const float* __restrict__ zp, float* __restrict__ wo, const float* __restrict__ w,
+                            float* __restrict__ xi, float* __restrict__ qv, double* part, unsigned long long* work) {
+  const int nt = tiles_vec(n);
+  const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
+  if (b >= B || !act[b]) return;
+  const SS<float> S = ss[b];
+  if (work && threadIdx.x == 0) {
+    const long tot = (long)(n - 1) * (n / kVec);
+    const long g0 = (long)ch * kThreads, g1 = g0 + kThreads < tot ? g0 + kThreads : tot;
+    // interior nodes of the tile: four per thread, minus the boundary column of each row start
+    const long per_row = n / kVec;
+    const long nodes = kVec * (g1 - g0) - ((g1 + per_row - 1) / per_row - (g0 + per_row - 1) / per_row);
+    atomicAdd(work, (unsigned long long)(nodes * (S.pend ? 10 : 4) * (long)sizeof(float)));
+  }
+  const int ld = sld(n);
+  const size_t off = (size_t)b * ssz(n);
+  float acc[1] = {0.0f};
+  int j, c0;
+  if (vec_walk(n, ch, j, c0)) {
+    const size_t p = off + (size_t)j * ld + c0;
+    if (S.pend) {
+      const float4 a = ld4(zp + p), o = ld4(wo + p), ww = ld4(w + p);
+      float4 x = ld4(xi + p);
+      float4 wn;
+      wn.x = (a.x * S.igp - S.a3 * o.x - S.a2 * ww.x) * S.ia1;
+      wn.y = (a.y * S.igp - S.a3 * o.y - S.a2 * ww.y) * S.ia1;
+      wn.z = (a.z * S.igp - S.a3 * o.z - S.a2 * ww.z) * S.ia1;
+      wn.w = (a.w * S.igp - S.a3 * o.w - S.a2 * ww.w) * S.ia1;
+      x.x += S.cx * wn.x;
+      x.y += S.cx * wn.y;
+      x.z += S.cx * wn.z;
+      x.w += S.cx * wn.w;
+      st4(wo + p, wn);
+      st4(xi + p, x);
+    }
+    const float4 zc = ld4(z + p), zn = ld4(z + p + ld), zs = ld4(z + p - ld);
+    const float4 wc = ld4(wx + p), yc = ld4(wy + p), ys = ld4(wy + p - ld);
+    const bool first = c0 == 0;
+    const float zw = first ? 0.0f : z[p - 1], ze = z[p + kVec], zne = z[p + ld + kVec];
+    const float zsw = first ? 0.0f : z[p - ld - 1], wwest = first ? 0.0f : wx[p - 1];
+    float q[kVec];
+#pragma unroll
+    for (int k = 0; k < kVec; ++k) {
+      const float xp = at(zc, k);
+      const float xe = k < 3 ? at(zc, k + 1) : ze, xw = k > 0 ? at(zc, k - 1) : zw;
+      const float xn = at(zn, k), xs = at(zs, k);
+      const float xne = k < 3 ? at(zn, k + 1) : zne, xsw = k > 0 ? at(zs, k - 1) : zsw;
+      const float we = at(wc, k), wwv = k > 0 ? at(wc, k - 1) : wwest;
+      const float st = we * (xp - xe) + wwv * (xp - xw) + at(yc, k) * (xp - xn) + at(ys, k) * (xp - xs);
+      const float ms = 6.0f * xp + (xe + xw) + (xn + xs) + (xne + xsw);
+      const float kz = (st - S.sigm * ms) * S.ig;
+      q[k] = (first && k == 0) ? 0.0f : kz;
+      acc[0] += q[k] * xp;
+    }
+    st4(qv + p, make_float4(q[0], q[1], q[2], q[3]));
+  }
+  tile_partials<1, float>(acc, part, (size_t)b * nt + ch);
+}
+
+// K2, vectorised: v_new = q - c1 v - c2 v_old (into vo)
+__global__ void k_minres_v4(int n, int B, const int* __restrict__ act, const SS<float>* __restrict__ ss,
+                            const float* __restrict__ q, const float* __restrict__ v, float* __restrict__ vo) {
+  const int nt = tiles_vec(n);
+  const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
+  if (b >= B || !act[b]) return;
+  const float c1 = ss[b].c1, c2 = ss[b].c2;
+  int j, c0;
+  if (!vec_walk(n, ch, j, c0)) return;
+  const size_t p = (size_t)b * ssz(n) + (size_t)j * sld(n) + c0;
+  const float4 a = ld4(q + p), bv = ld4(v + p), o = ld4(vo + p);
+  st4(vo + p, make_float4(a.x - c1 * bv.x - c2 * o.x, a.y - c1 * bv.y - c2 * o.y, a.z - c1 * bv.z - c2 * o.z,
+                          a.w - c1 * bv.w - c2 * o.w));
+}
+
+// V(1,1) up-sweep, vectorised: t = om D^-1 b + P xc at the four nodes and their stencil
+// neighbours, then out = t + om D^-1 (b - A t); with DOT also the partial <dotv, out>.  The coarse
+// correction P xc (mean of the two coarse values on the coarse edge through each fine node) reads
+// the coarse vector with scalar loads (rows of ldc entries).
+template <bool DOT>
+__global__ void k_prolong_smooth1_4(int n, int B, const int* __restrict__ act, const float* __restrict__ wx,
+                                    const float* __restrict__ wy, const float* __restrict__ dinv,
+                                    const float* __restrict__ bb, const float* __restrict__ xc, int ldc,
+                                    float* __restrict__ out, const float* __restrict__ dotv, double* part) {
+  const int nt = tiles_vec(n);
+  const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
+  if (b >= B || !act[b]) return;
+  const int ld = sld(n);
+  const size_t off = (size_t)b * ssz(n);
+  const float* __restrict__ XC = xc + (size_t)b * (size_t)(n / 2 + 1) * ldc;
+  float acc[1] = {0.0f};
+  int j, c0;
+  if (vec_walk(n, ch, j, c0)) {
+    const size_t p = off + (size_t)j * ld + c0;
+    auto pc = [&](int ii, int jj) {  // P xc at fine node (ii, jj)
+      const int c = (jj >> 1) * ldc + (ii >> 1);
+      return 0.5f * (XC[c] + XC[c + (ii & 1) + (jj & 1) * ldc]);
+    };
+    const bool first = c0 == 0;
+    const float4 dc = ld4(dinv + p), rc = ld4(bb + p);
+    const float4 dn = ld4(dinv + p + ld), rn = ld4(bb + p + ld);
+    const float4 ds = ld4(dinv + p - ld), rs = ld4(bb + p - ld);
+    const float4 wc = ld4(wx + p), yc = ld4(wy + p), ys = ld4(wy + p - ld);
+    const float wwest = first ? 0.0f : wx[p - 1];
+    // t along row j at columns c0-1 .. c0+4, and at rows j+1, j-1 under the four nodes
+    float tr[kVec + 2], tn[kVec], ts[kVec];
+    tr[0] = first ? 0.0f : dinv[p - 1] * bb[p - 1] + pc(c0 - 1, j);
+    tr[kVec + 1] = dinv[p + kVec] * bb[p + kVec] + pc(c0 + kVec, j);
+#pragma unroll
+    for (int k = 0; k < kVec; ++k) {
+      tr[k + 1] = at(dc, k) * at(rc, k) + pc(c0 + k, j);
+      tn[k] = at(dn, k) * at(rn, k) + pc(c0 + k, j + 1);
+      ts[k] = at(ds, k) * at(rs, k) + pc(c0 + k, j - 1);
+    }
+    float o[kVec];
+#pragma unroll
+    for (int k = 0; k < kVec; ++k) {
+      const float tp = tr[k + 1];
+      const float wwv = k > 0 ? at(wc, k - 1) : wwest;
+      const float ax = at(wc, k) * (tp - tr[k + 2]) + wwv * (tp - tr[k]) + at(yc, k) * (tp - tn[k]) +
+                       at(ys, k) * (tp - ts[k]);
+      o[k] = (first && k == 0) ? 0.0f : tp + at(dc, k) * (at(rc, k) - ax);
+    }
+    st4(out + p, make_float4(o[0], o[1], o[2], o[3]));
+    if (DOT) {
+      const float4 dv = ld4(dotv + p);
+      acc[0] = dv.x * o[0] + dv.y * o[1] + dv.z * o[2] + dv.w * o[3];
+    }
+  }
+  if (DOT) tile_partials<1, float>(acc, part, (size_t)b * nt + ch);
+}
+
 // K2: v_new = q - c1 v - c2 v_old (into vo).  z_j stays unnormalised: the next pending update
 // scales it by 1 / gamma_j (saves a read and a write of z per step)
 template <typename T>
@@ -667,7 +844,7 @@ __global__ void k_minres_v(int n, int B, const int* __restrict__ act, const SS<T
   const int nt = tiles_interior(n);
   const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
   if (b >= B || !act[b]) return;
-  const size_t off = (size_t)b * gsz(n);
+  const size_t off = (size_t)b * ssz(n);
   const T c1 = ss[b].c1, c2 = ss[b].c2;
   for_tile(n, ch, [&](int p, int, int) { vo[off + p] = q[off + p] - c1 * v[off + p] - c2 * vo[off + p]; });
 }
@@ -680,7 +857,7 @@ __global__ void k_minres_finish(int n, int B, const int* __restrict__ act, const
   const int nt = tiles_interior(n);
   const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
   if (b >= B || !act[b] || !ss[b].pend) return;
-  const size_t off = (size_t)b * gsz(n);
+  const size_t off = (size_t)b * ssz(n);
   const SS<T> S = ss[b];
   for_tile(n, ch, [&](int p, int, int) {
     const T wnew = (zp[off + p] * S.igp - S.a3 * wo[off + p] - S.a2 * w[off + p]) * S.ia1;
@@ -786,7 +963,7 @@ __global__ void k_outer_update(int n, int B, const SS<T>* __restrict__ ss, const
   const int nt = tiles_interior(n);
   const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
   if (b >= B || !ran[b]) return;
-  const size_t off = (size_t)b * gsz(n);
+  const size_t off = (size_t)b * ssz(n);
   const double rn = ss[b].rnorm;
   for_tile(n, ch, [&](int p, int, int) { x64[off + p] += rn * (double)xi[off + p]; });
 }
@@ -801,8 +978,8 @@ __global__ void k_residual(int n, int B, const int* __restrict__ ran, const doub
   const int nt = tiles_interior(n);
   const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
   if (b >= B || !ran[b]) return;
-  const int ld = n + 1;
-  const size_t off = (size_t)b * gsz(n);
+  const int ld = sld(n);
+  const size_t off = (size_t)b * ssz(n);
   const double hm = 1.0 / (12.0 * n * n);
   const double sg = sigma[(size_t)b * sig_stride];
   const double* __restrict__ WX = wx64 + off;
@@ -899,6 +1076,32 @@ __global__ void k_set_int(int B, int* p, int v) {
 
 // ---------------------------------------------------------------------------------------------
 // host driver
+// The operator sweep and the Lanczos update: vectorised kernels for FP32, the row-mapped ones for
+// FP64.  Returns the number of partial-sum slots per sample the sweep wrote (for k_sc_delta).
+template <typename T>
+int launch_minres_q(int n, int B, const int* act, const SS<T>* ss, const T* wx, const T* wy, const double* lamH,
+                    int lam_stride, const T* z, const T* zp, T* wo, const T* w, T* xi, T* q, double* part,
+                    unsigned long long* work, cudaStream_t st) {
+  if constexpr (sizeof(T) == sizeof(float)) {
+    (void)lamH;
+    (void)lam_stride;
+    k_minres_q4<<<B * tiles_vec(n), kThreads, 0, st>>>(n, B, act, ss, wx, wy, z, zp, wo, w, xi, q, part, work);
+    return tiles_vec(n);
+  } else {
+    k_minres_q<T><<<B * tiles_interior(n), kThreads, 0, st>>>(n, B, act, ss, wx, wy, lamH, lam_stride, z, zp, wo, w,
+                                                            xi, q, part, work);
+    return tiles_interior(n);
+  }
+}
+
+template <typename T>
+void launch_minres_v(int n, int B, const int* act, const SS<T>* ss, const T* q, const T* v, T* vo, cudaStream_t st) {
+  if constexpr (sizeof(T) == sizeof(float))
+    k_minres_v4<<<B * tiles_vec(n), kThreads, 0, st>>>(n, B, act, ss, q, v, vo);
+  else
+    k_minres_v<T><<<B * tiles_interior(n), kThreads, 0, st>>>(n, B, act, ss, q, v, vo);
+}
+
 int grid1(size_t count) {
   size_t g = (count + 255) / 256;
   return (int)(g < 1 ? 1 : (g > 152 * 64 ? 152 * 64 : g));
@@ -927,7 +1130,7 @@ size_t carve_arena(void* base, int n, int B, Arena<T>& A) {
   Carver c(base);
   A.n = n;
   A.B = B;
-  A.V0 = gsz(n);
+  A.V0 = ssz(n);
   const size_t Bz = (size_t)B;
   A.v = c.take<T>(Bz * A.V0);
   A.vo = c.take<T>(Bz * A.V0);
@@ -944,7 +1147,7 @@ size_t carve_arena(void* base, int n, int B, Arena<T>& A) {
   A.Ls = 0;
   for (int nl = n; nl > kSub; nl >>= 1) ++A.Ls;
   for (int l = 0; l < (A.Ls > 1 ? A.Ls : 1); ++l) {  // level 0 always: the MINRES operator
-    const size_t V = gsz(n >> l);
+    const size_t V = ssz(n >> l);
     A.wx[l] = c.take<T>(Bz * V);
     A.wy[l] = c.take<T>(Bz * V);
     A.dinv[l] = c.take<T>(Bz * V);
@@ -984,8 +1187,8 @@ cudaError_t vcycle_stream(Arena<T>& A, const T* b0, T* x0, const int* act, T om,
                           size_t sub_smem, cudaStream_t st) {
   const int n = A.n, B = A.B;
   if (A.Ls == 0) {
-    ++tl_launches, k_subcycle<T><<<B, kSubThreads, sub_smem, st>>>(n, B, act, A.subw, A.subw_bytes, b0, x0, A.nu, om,
-                                                                   part, dotv);
+    ++tl_launches, k_subcycle<T><<<B, kSubThreads, sub_smem, st>>>(n, B, act, A.subw, A.subw_bytes, b0, x0, sld(n), A.nu,
+                                                                   om, part, dotv);
     LAUNCH_CHECK();
     return cudaSuccess;
   }
@@ -994,25 +1197,36 @@ cudaError_t vcycle_stream(Arena<T>& A, const T* b0, T* x0, const int* act, T om,
       const int nl = n >> l;
       const T* b = l ? A.b[l] : b0;
       T* bc = (l + 1 < A.Ls) ? A.b[l + 1] : A.bsub;
+      const int ldo = (l + 1 < A.Ls) ? sld(nl / 2) : nl / 2 + 1;
       ++tl_launches, k_restrict1<T><<<B * tiles_interior(nl / 2), kThreads, 0, st>>>(nl, B, act, A.wx[l], A.wy[l],
-                                                                                   A.dinv[l], b, bc);
+                                                                                   A.dinv[l], b, bc, ldo);
       LAUNCH_CHECK();
     }
     const int ns = n >> A.Ls;
-    ++tl_launches, k_subcycle<T><<<B, kSubThreads, sub_smem, st>>>(ns, B, act, A.subw, A.subw_bytes, A.bsub, A.xsub, 1,
-                                                                   om, nullptr, nullptr);
+    ++tl_launches, k_subcycle<T><<<B, kSubThreads, sub_smem, st>>>(ns, B, act, A.subw, A.subw_bytes, A.bsub, A.xsub,
+                                                                   ns + 1, 1, om, nullptr, nullptr);
     LAUNCH_CHECK();
     for (int l = A.Ls - 1; l >= 0; --l) {
       const int nl = n >> l;
       const T* b = l ? A.b[l] : b0;
       T* xa = l ? A.x[l] : x0;
       const T* xc = (l + 1 < A.Ls) ? A.x[l + 1] : A.xsub;
-      if (l == 0 && dotv)
-        ++tl_launches, k_prolong_smooth1<T, true><<<B * tiles_interior(nl), kThreads, 0, st>>>(
-            nl, B, act, A.wx[l], A.wy[l], A.dinv[l], b, xc, xa, dotv, part);
-      else
-        ++tl_launches, k_prolong_smooth1<T, false><<<B * tiles_interior(nl), kThreads, 0, st>>>(
-            nl, B, act, A.wx[l], A.wy[l], A.dinv[l], b, xc, xa, nullptr, nullptr);
+      const int ldc = (l + 1 < A.Ls) ? sld(nl / 2) : nl / 2 + 1;
+      if constexpr (sizeof(T) == sizeof(float)) {
+        if (l == 0 && dotv)
+          ++tl_launches, k_prolong_smooth1_4<true><<<B * tiles_vec(nl), kThreads, 0, st>>>(
+              nl, B, act, A.wx[l], A.wy[l], A.dinv[l], b, xc, ldc, xa, dotv, part);
+        else
+          ++tl_launches, k_prolong_smooth1_4<false><<<B * tiles_vec(nl), kThreads, 0, st>>>(
+              nl, B, act, A.wx[l], A.wy[l], A.dinv[l], b, xc, ldc, xa, nullptr, nullptr);
+      } else {
+        if (l == 0 && dotv)
+          ++tl_launches, k_prolong_smooth1<T, true><<<B * tiles_interior(nl), kThreads, 0, st>>>(
+              nl, B, act, A.wx[l], A.wy[l], A.dinv[l], b, xc, ldc, xa, dotv, part);
+        else
+          ++tl_launches, k_prolong_smooth1<T, false><<<B * tiles_interior(nl), kThreads, 0, st>>>(
+              nl, B, act, A.wx[l], A.wy[l], A.dinv[l], b, xc, ldc, xa, nullptr, nullptr);
+      }
       LAUNCH_CHECK();
     }
     return cudaSuccess;
@@ -1025,20 +1239,23 @@ cudaError_t vcycle_stream(Arena<T>& A, const T* b0, T* x0, const int* act, T om,
                                                                        b, xa);
     LAUNCH_CHECK();
     T* bc = (l + 1 < A.Ls) ? A.b[l + 1] : A.bsub;
-    ++tl_launches, k_restrict<T><<<B * tiles_interior(nl / 2), kThreads, 0, st>>>(nl, B, act, A.wx[l], A.wy[l], b, xa, bc);
+    const int ldo = (l + 1 < A.Ls) ? sld(nl / 2) : nl / 2 + 1;
+    ++tl_launches, k_restrict<T><<<B * tiles_interior(nl / 2), kThreads, 0, st>>>(nl, B, act, A.wx[l], A.wy[l], b, xa, bc,
+                                                                                ldo);
     LAUNCH_CHECK();
   }
   const int ns = n >> A.Ls;
-  ++tl_launches, k_subcycle<T><<<B, kSubThreads, sub_smem, st>>>(ns, B, act, A.subw, A.subw_bytes, A.bsub, A.xsub, A.nu, om, nullptr,
-                                                nullptr);
+  ++tl_launches, k_subcycle<T><<<B, kSubThreads, sub_smem, st>>>(ns, B, act, A.subw, A.subw_bytes, A.bsub, A.xsub, ns + 1,
+                                                                 A.nu, om, nullptr, nullptr);
   LAUNCH_CHECK();
   for (int l = A.Ls - 1; l >= 0; --l) {
     const int nl = n >> l;
     const T* b = l ? A.b[l] : b0;
     T* xa = l ? A.x[l] : x0;
     const T* xc = (l + 1 < A.Ls) ? A.x[l + 1] : A.xsub;
+    const int ldc = (l + 1 < A.Ls) ? sld(nl / 2) : nl / 2 + 1;
     ++tl_launches, k_prolong_smooth<T><<<B * tiles_interior(nl), kThreads, 0, st>>>(nl, B, act, A.wx[l], A.wy[l], A.dinv[l], b,
-                                                                    xa, xc, A.t[l]);
+                                                                    xa, xc, A.t[l], ldc);
     LAUNCH_CHECK();
     if (l == 0 && dotv)
       ++tl_launches, k_smooth<T, true><<<B * tiles_interior(nl), kThreads, 0, st>>>(nl, B, act, A.wx[l], A.wy[l], A.dinv[l], b,
@@ -1123,7 +1340,7 @@ cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st, c
   ++tl_launches, k_zero<double><<<grid1(Bz * V0), 256, 0, st>>>(Bz * V0, A.x64);
   ++tl_launches, k_zero<double><<<grid1(Bz * V0), 256, 0, st>>>(Bz * V0, A.b64);
   for (int l = 0; l < A.Ls; ++l) {
-    const size_t V = gsz(n >> l);
+    const size_t V = ssz(n >> l);
     T* const lv[3] = {A.t[l], A.x[l], A.b[l]};
     for (int k = 0; k < 3; ++k)
       if (lv[k]) ++tl_launches, k_zero<T><<<grid1(Bz * V), 256, 0, st>>>(Bz * V, lv[k]);
@@ -1192,7 +1409,9 @@ cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st, c
     LAUNCH_CHECK();
     T *v = A.v, *vo = A.vo, *z = A.z, *zn = A.zn, *w = A.w, *wo = A.wo;
     if ((e = vcycle_stream<T>(A, v, z, A.act, om, v, A.part, sub_smem, b0)) != cudaSuccess) return e;
-    const int nchd = A.Ls ? nt : 1;  // partial slots of <v, z>
+    // partial slots per sample of <v, z> (written by the V-cycle's last sweep: the vectorised one for
+    // FP32 with V(1,1), the row-mapped one otherwise; one slot when the sub-cycle does it all)
+    const int nchd = A.Ls ? ((sizeof(T) == sizeof(float) && A.nu == 1) ? tiles_vec(n) : nt) : 1;
     ++tl_launches, k_sc_gamma0<T><<<gs, 256, 0, b0>>>(B, nchd, A.part, A.act, A.ss);
     LAUNCH_CHECK();
     if ((e = make_handle(b0, &hi)) != cudaSuccess) return e;
@@ -1200,13 +1419,14 @@ cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st, c
     LAUNCH_CHECK();
     if ((e = open_while(b0, b1, hi)) != cudaSuccess) return e;
     for (int half = 0; half < 2; ++half) {
-      ++tl_launches, k_minres_q<T><<<B * nt, kThreads, 0, b1>>>(n, B, A.act, A.ss, A.wx[0], A.wy[0], s.lamH,
-                                                              s.lam_stride, z, zn, wo, w, A.xi, A.q, A.part, nullptr);
+      const int nq = launch_minres_q<T>(n, B, A.act, A.ss, A.wx[0], A.wy[0], s.lamH, s.lam_stride, z, zn, wo, w, A.xi,
+                                        A.q, A.part, nullptr, b1);
+      ++tl_launches;
       LAUNCH_CHECK();
       ++tl_launches, k_sc_retire<T><<<gs, 256, 0, b1>>>(B, A.act, A.ss);
       { T* tt = wo; wo = w; w = tt; }
-      ++tl_launches, k_sc_delta<T><<<gs, 256, 0, b1>>>(B, nt, A.part, A.act, A.ss);
-      ++tl_launches, k_minres_v<T><<<B * nt, kThreads, 0, b1>>>(n, B, A.act, A.ss, A.q, v, vo);
+      ++tl_launches, k_sc_delta<T><<<gs, 256, 0, b1>>>(B, nq, A.part, A.act, A.ss);
+      ++tl_launches, launch_minres_v<T>(n, B, A.act, A.ss, A.q, v, vo, b1);
       LAUNCH_CHECK();
       { T* tt = vo; vo = v; v = tt; }
       if ((e = vcycle_stream<T>(A, v, zn, A.act, om, v, A.part, sub_smem, b1)) != cudaSuccess) return e;
@@ -1243,7 +1463,9 @@ cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st, c
     T *v = A.v, *vo = A.vo, *z = A.z, *zn = A.zn, *w = A.w, *wo = A.wo;
     e = vcycle_stream<T>(A, v, z, A.act, om, v, A.part, sub_smem, st);
     if (e != cudaSuccess) return e;
-    const int nchd = A.Ls ? nt : 1;  // partial slots of <v, z>
+    // partial slots per sample of <v, z> (written by the V-cycle's last sweep: the vectorised one for
+    // FP32 with V(1,1), the row-mapped one otherwise; one slot when the sub-cycle does it all)
+    const int nchd = A.Ls ? ((sizeof(T) == sizeof(float) && A.nu == 1) ? tiles_vec(n) : nt) : 1;
     ++tl_launches, k_sc_gamma0<T><<<gs, 256, 0, st>>>(B, nchd, A.part, A.act, A.ss);
     LAUNCH_CHECK();
     for (int j = 0; j < s.max_inner; ++j) {
@@ -1252,15 +1474,16 @@ cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st, c
         if ((e = s.probe->next(&pe)) != cudaSuccess) return e;
         cudaEventRecord(pe->first, st);
       }
-      ++tl_launches, k_minres_q<T><<<B * nt, kThreads, 0, st>>>(n, B, A.act, A.ss, A.wx[0], A.wy[0], s.lamH, s.lam_stride, z, zn,
-                                                 wo, w, A.xi, A.q, A.part, s.probe ? s.probe->d_bytes : nullptr);
+      const int nq = launch_minres_q<T>(n, B, A.act, A.ss, A.wx[0], A.wy[0], s.lamH, s.lam_stride, z, zn, wo, w, A.xi,
+                                        A.q, A.part, s.probe ? s.probe->d_bytes : nullptr, st);
+      ++tl_launches;
       LAUNCH_CHECK();
       if (pe) cudaEventRecord(pe->second, st);
       // samples that converged in the previous Givens step have now applied their update
       ++tl_launches, k_sc_retire<T><<<gs, 256, 0, st>>>(B, A.act, A.ss);
       { T* tt = wo; wo = w; w = tt; }
-      ++tl_launches, k_sc_delta<T><<<gs, 256, 0, st>>>(B, nt, A.part, A.act, A.ss);
-      ++tl_launches, k_minres_v<T><<<B * nt, kThreads, 0, st>>>(n, B, A.act, A.ss, A.q, v, vo);
+      ++tl_launches, k_sc_delta<T><<<gs, 256, 0, st>>>(B, nq, A.part, A.act, A.ss);
+      ++tl_launches, launch_minres_v<T>(n, B, A.act, A.ss, A.q, v, vo, st);
       LAUNCH_CHECK();
       { T* tt = vo; vo = v; v = tt; }
       e = vcycle_stream<T>(A, v, zn, A.act, om, v, A.part, sub_smem, st);
