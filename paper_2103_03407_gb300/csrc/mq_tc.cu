@@ -46,7 +46,7 @@ constexpr int kTN = 64;      // triangles per tile
 constexpr int kTK = 16;      // K per MMA (one pipeline step)
 constexpr int kChunk = 128;  // K per exact accumulation chunk
 constexpr int kStepsPerChunk = kChunk / kTK;
-constexpr int kStages = 4;   // shared-memory pipeline depth
+constexpr int kStages = 5;   // shared-memory pipeline depth (5 x 42 KB)
 constexpr int kTcThreads = 256;
 constexpr int kTmemCols = 512;  // 7 groups x 64 columns = 448 used
 constexpr uint32_t kABytes = kSlices * kTM * kTK * 2;  // 28 KB per stage
@@ -121,18 +121,25 @@ __device__ __forceinline__ void tma_load4(void* dst, const CUtensorMap* map, int
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// 16 consecutive TMEM columns of this thread's lane
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
+// 16 consecutive TMEM columns of this thread's lane, without waiting: the registers are valid
+// only after tmem_wait on them (several loads can then share one wait)
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
       "%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
         "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// waits for this thread's outstanding TMEM loads; the registers are passed through so that no use
+// of them can be scheduled before the wait
+__device__ __forceinline__ void tmem_wait(uint32_t (&r)[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+               :
+               : "memory");
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -273,18 +280,36 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         // sum_g S_g 2^{8(6-g)} in two 64-bit integers (groups 0-3 and 4-6), then rounded once
 #pragma unroll
         for (int sh = 0; sh < 2; ++sh) {
+          const uint32_t tcol = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(half * 32 + sh * 16);
           long long hi[16], lo[16];
+          {
+            // groups 0-3: four loads in flight, one wait
+            uint32_t r[4][16];
 #pragma unroll
-          for (int i = 0; i < 16; ++i) hi[i] = lo[i] = 0;
+            for (int g = 0; g < 4; ++g) tmem_ld16_async(tcol + (uint32_t)(g * kTN), r[g]);
 #pragma unroll
-          for (int g = 0; g < kGroups; ++g) {
-            float v[16];
-            tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(g * kTN + half * 32 + sh * 16), v);
+            for (int g = 0; g < 4; ++g) tmem_wait(r[g]);
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
-              const long long sv = (long long)__float2int_rn(v[i]);
-              if (g < 4) hi[i] = hi[i] * 256 + sv;
-              else lo[i] = lo[i] * 256 + sv;
+              long long h = 0;
+#pragma unroll
+              for (int g = 0; g < 4; ++g) h = h * 256 + (long long)__float2int_rn(__uint_as_float(r[g][i]));
+              hi[i] = h;
+            }
+          }
+          {
+            // groups 4-6
+            uint32_t r[3][16];
+#pragma unroll
+            for (int g = 0; g < 3; ++g) tmem_ld16_async(tcol + (uint32_t)((4 + g) * kTN), r[g]);
+#pragma unroll
+            for (int g = 0; g < 3; ++g) tmem_wait(r[g]);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              long long l = 0;
+#pragma unroll
+              for (int g = 0; g < 3; ++g) l = l * 256 + (long long)__float2int_rn(__uint_as_float(r[g][i]));
+              lo[i] = l;
             }
           }
           // value of the chunk = (hi 2^24 + lo) 2^{-15-48}; hi < 2^56 and lo < 2^40 in magnitude
