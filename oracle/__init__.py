@@ -12,12 +12,17 @@ problems II):
 * ``fem``      -- P1 finite elements on the uniform SW-NE triangulation of the
                   unit square, assembled by element loops (Sec. 2.3), and the
                   affine coefficient a = a0 + sum_j y_j psi_j at element centroids
-                  (eq. coeff, truncated as in eq. coeff_s).
+                  (eq. coeff, truncated as in eq. coeff_s); the second test problem
+                  of Sec. 5 (four islands, piecewise a0 and b0, a parametric reaction
+                  b = b0 + sum_j y_j b_j and its reaction matrix); the integral of a
+                  P1 function.
 * ``lattice``  -- CBC generating vectors with product weights and randomly
                   shifted rank-1 lattice points (Sec. 2.5, eq. rqmc, eq. t_kl).
 * ``twogrid``  -- exact smallest eigenpairs, P1 interpolation between nested
-                  meshes and the two-grid-truncation step (Algorithm 1).
-* ``mlqmc``    -- per-sample level differences and the shift-averaged estimator
+                  meshes and the two-grid-truncation step (Algorithm 1); the
+                  eigenfunction functional G(u) = |integral of u| / ||u||_L2.
+* ``mlqmc``    -- per-sample level differences (of the eigenvalue or of G(u)) and
+                  the shift-averaged estimator
                   with its sample-variance error estimate (Algorithm 2,
                   eq. tg-mlqmc, eq. sample_var).
 

@@ -59,6 +59,67 @@ def centroids(n: int) -> np.ndarray:
     return coords[tris].mean(axis=1)
 
 
+# ---------------------------------------------------------------------------------------------
+# The second test problem of Sec. 5 (domain with four interior islands): family 2.
+#   D_f = four squares [1/8,3/8]^2, [5/8,7/8]^2, [1/8,3/8] x [5/8,7/8], [5/8,7/8] x [1/8,3/8]
+#   a0 = 0.01 on D_f, 0.011 elsewhere;  b0 = 2 on D_f, 0.3 elsewhere;
+#   term j: odd j -> k = (j+1)/2, supported on D_f:   a_j = 0.01 w_k(p_a),   b_j = 2 w_k(p_b);
+#           even j -> k = j/2, supported off D_f:      a_j = 0.011 w_k(p_a'), b_j = 0.3 w_k(p_b');
+#   w_k(q; x) = k^-q sin(8 k pi x1) sin(8 (k+1) pi x2) on its region, 0 on the other.
+# A zeroth term is scaled by pi / sqrt(2) when a decay below 2 belongs to it.  Reading: each
+# decay belongs to the part of the zeroth term on its own region (p_a to a0 on D_f, p_a' to a0 off
+# D_f, p_b and p_b' likewise for b0), the part whose positivity its terms put at risk.  A triangle
+# belongs to D_f when its centroid does (the meshes of width 1/8 and finer resolve the islands).
+
+SIG_A_IN, SIG_A_OUT, SIG_B_IN, SIG_B_OUT = 0.01, 0.011, 2.0, 0.3
+
+
+def in_islands(x: np.ndarray) -> np.ndarray:
+    """Whether each point x [.., 2] lies in the four closed islands D_f."""
+    def band(t):
+        return ((t >= 0.125) & (t <= 0.375)) | ((t >= 0.625) & (t <= 0.875))
+    return band(x[..., 0]) & band(x[..., 1])
+
+
+def problem2_decays(decay):
+    """(p_a, p_a', p_b, p_b') from one decay or a sequence of four."""
+    d = np.atleast_1d(np.asarray(decay, dtype=np.float64))
+    if d.size == 1:
+        d = np.repeat(d, 4)
+    if d.size != 4:
+        raise ValueError("the second test problem takes one decay or four")
+    return tuple(float(v) for v in d)
+
+
+def problem2_terms(n: int, s: int, decay=2.0):
+    """(a0_t, Psi_a [nT, s], b0_t, Psi_b [nT, s]) at the triangle centroids of mesh 1/n;
+    ``decay`` is (p_a, p_a', p_b, p_b') or one value for all four."""
+    pa, pa2, pb, pb2 = problem2_decays(decay)
+    c = centroids(n)
+    inside = in_islands(c)
+    sc = lambda p: np.pi / np.sqrt(2.0) if p < 2.0 else 1.0  # noqa: E731
+    a0 = np.where(inside, SIG_A_IN * sc(pa), SIG_A_OUT * sc(pa2))
+    b0 = np.where(inside, SIG_B_IN * sc(pb), SIG_B_OUT * sc(pb2))
+    Pa = np.zeros((c.shape[0], s))
+    Pb = np.zeros((c.shape[0], s))
+    for j in range(1, s + 1):
+        odd = j % 2 == 1
+        k = (j + 1) // 2 if odd else j // 2
+        shape = np.sin(8 * k * np.pi * c[:, 0]) * np.sin(8 * (k + 1) * np.pi * c[:, 1])
+        region = inside if odd else ~inside
+        qa, qb = (pa, pb) if odd else (pa2, pb2)
+        Pa[:, j - 1] = np.where(region, (SIG_A_IN if odd else SIG_A_OUT) * k ** (-qa) * shape, 0.0)
+        Pb[:, j - 1] = np.where(region, (SIG_B_IN if odd else SIG_B_OUT) * k ** (-qb) * shape, 0.0)
+    return a0, Pa, b0, Pb
+
+
+def problem2_coefficients(n: int, y: np.ndarray, decay=2.0):
+    """(a_t, b_t) = (a0 + sum_j y_j a_j, b0 + sum_j y_j b_j) at the centroids (s = len(y))."""
+    y = np.asarray(y, dtype=np.float64)
+    a0, Pa, b0, Pb = problem2_terms(n, y.size, decay)
+    return a0 + Pa @ y, b0 + Pb @ y
+
+
 def psi_pairs(s: int, family: int = 0):
     """Frequency pairs (k1, k2) of the first s terms of a coefficient family.
 
@@ -150,8 +211,10 @@ def _element_entries(n: int, with_boundary: bool):
     return ent
 
 
-def assemble(n: int, a_t: np.ndarray | None = None, with_boundary: bool = False):
-    """Stiffness A = sum_T a_T K_T and mass M = sum_T M_T over the elements (Sec. 2.3).
+def assemble(n: int, a_t: np.ndarray | None = None, with_boundary: bool = False, b_t: np.ndarray | None = None):
+    """Stiffness A = sum_T a_T K_T and mass M = sum_T M_T over the elements (Sec. 2.3); with
+    ``b_t`` also the reaction matrix B = sum_T b_T M_T of the term b u (the coefficient b
+    constant on each triangle, equal to its centroid value), returned third.
 
     Returns sparse CSR matrices over the interior unknowns, or over all (n+1)^2
     nodes when ``with_boundary`` is set (used by exactness tests).
@@ -167,7 +230,13 @@ def assemble(n: int, a_t: np.ndarray | None = None, with_boundary: bool = False)
     M = sp.coo_matrix((mv, (rows, cols)), shape=(size, size)).tocsr()
     A.sum_duplicates()
     M.sum_duplicates()
-    return A, M
+    if b_t is None:
+        return A, M
+    b_t = np.asarray(b_t, dtype=np.float64).ravel()
+    assert b_t.size == nt
+    Bm = sp.coo_matrix((b_t[tt] * mv, (rows, cols)), shape=(size, size)).tocsr()
+    Bm.sum_duplicates()
+    return A, M, Bm
 
 
 _MASS_CACHE: dict = {}
@@ -182,3 +251,24 @@ def mass(n: int):
 
 def stiffness(n: int, a_t: np.ndarray):
     return assemble(n, a_t)[0]
+
+
+def operator(n: int, y: np.ndarray, a0: float = 1.0, decay=2.0, family: int = 0):
+    """The y-dependent matrix of the eigenproblem on mesh 1/n: the stiffness A(y), plus the
+    reaction matrix B(y) for the second test problem (family 2)."""
+    if family == 2:
+        a_t, b_t = problem2_coefficients(n, y, decay)
+        A, _, Bm = assemble(n, a_t, b_t=b_t)
+        return (A + Bm).tocsr()
+    return stiffness(n, coefficient(n, y, a0, decay, family))
+
+
+def integral(n: int, u: np.ndarray) -> float:
+    """The integral over D of the P1 function with interior nodal values u (zero on the boundary):
+    the sum over the triangles of the area times the mean of the three vertex values (exact for a
+    linear function on a triangle)."""
+    coords, tris, interior = mesh(n)
+    full = np.zeros(coords.shape[0])
+    full[interior >= 0] = u[interior[interior >= 0]]
+    area = 0.5 / (n * n)
+    return float(area * full[tris].mean(axis=1).sum())

@@ -26,36 +26,51 @@ import numpy as np
 from . import lattice, twogrid
 
 
-def sample_level(level, prev, y, a0: float = 1.0, decay: float = 2.0, family: int = 0):
-    """(lambda_H, lambda^l, lambda^{l-1}, difference) for one parameter vector y (len >= s_l).
+QOIS = ("eigenvalue", "functional")
+
+
+def _update(n_fine, y, lam_H, u_H, n_coarse, a0, decay, family, qoi):
+    """The quantity of interest of the two-grid update on mesh n_fine: lambda^h, or G(u^h) of its
+    eigenfunction approximation (Algorithm 1 steps 2-4; G as in ``twogrid.functional``)."""
+    if qoi == "eigenvalue":
+        return twogrid.twogrid_update(n_fine, y, lam_H, u_H, n_coarse, a0, decay, family=family)
+    _, w = twogrid.twogrid_update(n_fine, y, lam_H, u_H, n_coarse, a0, decay, return_vector=True, family=family)
+    return twogrid.functional(n_fine, w)
+
+
+def sample_level(level, prev, y, a0: float = 1.0, decay=2.0, family: int = 0, qoi: str = "eigenvalue"):
+    """(lambda_H, Q^l, Q^{l-1}, difference) for one parameter vector y (len >= s_l), where Q is the
+    eigenvalue (qoi "eigenvalue") or G(u) of the eigenfunction (qoi "functional"; Sec. 4.3: the same
+    estimator for a linear functional of u).
 
     ``level`` and ``prev`` carry n_fine, n_coarse, s, S (``prev`` is None on level 0).
     """
+    assert qoi in QOIS
     lam_H, u_H = twogrid.coarse_pair(level.n_coarse, y[: level.S], a0, decay, family)
+    q_H = lam_H if qoi == "eigenvalue" else twogrid.functional(level.n_coarse, u_H)
     if level.n_fine == level.n_coarse and level.s == level.S:
-        lam_l = lam_H
+        q_l = q_H
     else:
-        lam_l = twogrid.twogrid_update(level.n_fine, y[: level.s], lam_H, u_H, level.n_coarse, a0, decay,
-                                       family=family)
+        q_l = _update(level.n_fine, y[: level.s], lam_H, u_H, level.n_coarse, a0, decay, family, qoi)
     if prev is None:
-        return lam_H, lam_l, 0.0, lam_l
+        return lam_H, q_l, 0.0, q_l
     if prev.n_fine == level.n_coarse and prev.s == level.S:
-        lam_p = lam_H
+        q_p = q_H
     else:
-        lam_p = twogrid.twogrid_update(prev.n_fine, y[: prev.s], lam_H, u_H, level.n_coarse, a0, decay,
-                                       family=family)
-    return lam_H, lam_l, lam_p, lam_l - lam_p
+        q_p = _update(prev.n_fine, y[: prev.s], lam_H, u_H, level.n_coarse, a0, decay, family, qoi)
+    return lam_H, q_l, q_p, q_l - q_p
 
 
-def level_samples(level, prev, z, delta, ks, a0: float = 1.0, decay: float = 2.0, family: int = 0) -> np.ndarray:
-    """Per-sample results [R, len(ks), 4] = (lambda_H, lambda^l, lambda^{l-1}, diff) at lattice
-    indices ks for every shift row of ``delta`` [R, s_l]."""
+def level_samples(level, prev, z, delta, ks, a0: float = 1.0, decay=2.0, family: int = 0,
+                  qoi: str = "eigenvalue") -> np.ndarray:
+    """Per-sample results [R, len(ks), 4] = (lambda_H, Q^l, Q^{l-1}, diff) at lattice indices ks
+    for every shift row of ``delta`` [R, s_l] (Q as in ``sample_level``)."""
     delta = np.atleast_2d(delta)
     out = np.zeros((delta.shape[0], len(ks), 4))
     for r in range(delta.shape[0]):
         Y = lattice.points(z, level.N, delta[r], ks)
         for i in range(len(ks)):
-            out[r, i] = sample_level(level, prev, Y[i], a0, decay, family)
+            out[r, i] = sample_level(level, prev, Y[i], a0, decay, family, qoi)
     return out
 
 
@@ -93,9 +108,9 @@ def estimate(level_shift_means):
 # level l-1 computed there: steps 6-8 and 12-14 of Algorithm 2 are skipped and only the fine
 # two-grid update (h_l, s_l) remains per level.
 
-def shared_samples(levels, z, m_max: int, delta_row, ks, a0: float = 1.0, decay: float = 2.0,
-                   family: int = 0) -> np.ndarray:
-    """Per-sample results [L+1, len(ks), 4] = (lambda_H, lambda^l, lambda^{l-1}, diff) of the reuse
+def shared_samples(levels, z, m_max: int, delta_row, ks, a0: float = 1.0, decay=2.0,
+                   family: int = 0, qoi: str = "eigenvalue") -> np.ndarray:
+    """Per-sample results [L+1, len(ks), 4] = (lambda_H, Q^l, Q^{l-1}, diff) of the reuse
     scheme for one shift row (length >= s_L) at embedded-rule indices ks; entries of levels whose
     N_l <= k are NaN.  Level 0 must be direct (n_coarse = n_fine, S = s); levels l >= 1 must have
     n_coarse = n_fine of level 0 and S = s_0."""
@@ -109,15 +124,16 @@ def shared_samples(levels, z, m_max: int, delta_row, ks, a0: float = 1.0, decay:
     for i, k in enumerate(ks):
         y = Y[i]
         lam0, u0 = twogrid.coarse_pair(lv0.n_fine, y[: lv0.s], a0, decay, family)
-        out[0, i] = (lam0, lam0, 0.0, lam0)
-        prev = lam0
+        q0 = lam0 if qoi == "eigenvalue" else twogrid.functional(lv0.n_fine, u0)
+        out[0, i] = (lam0, q0, 0.0, q0)
+        prev = q0
         for l in range(1, len(levels)):
             lv = levels[l]
             if k >= lv.N:
                 break
-            lam = twogrid.twogrid_update(lv.n_fine, y[: lv.s], lam0, u0, lv0.n_fine, a0, decay, family=family)
-            out[l, i] = (lam0, lam, prev, lam - prev)
-            prev = lam
+            q = _update(lv.n_fine, y[: lv.s], lam0, u0, lv0.n_fine, a0, decay, family, qoi)
+            out[l, i] = (lam0, q, prev, q - prev)
+            prev = q
     return out
 
 

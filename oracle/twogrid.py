@@ -91,19 +91,15 @@ def interpolate(u_coarse: np.ndarray, n_coarse: int, n_fine: int) -> np.ndarray:
     return interpolation_matrix(n_coarse, n_fine) @ u_coarse
 
 
-def coarse_pair(n_coarse: int, y_coarse: np.ndarray, a0: float = 1.0, decay: float = 2.0, family: int = 0):
+def coarse_pair(n_coarse: int, y_coarse: np.ndarray, a0: float = 1.0, decay=2.0, family: int = 0):
     """Step 1 of Algorithm 1: the smallest eigenpair on the coarse mesh with S terms."""
-    a = fem.coefficient(n_coarse, y_coarse, a0, decay, family)
-    A = fem.stiffness(n_coarse, a)
-    M = fem.mass(n_coarse)
-    return smallest_eigpair(A, M)
+    return smallest_eigpair(fem.operator(n_coarse, y_coarse, a0, decay, family), fem.mass(n_coarse))
 
 
 def twogrid_update(n_fine: int, y_fine: np.ndarray, lam_H: float, u_H: np.ndarray, n_coarse: int,
-                   a0: float = 1.0, decay: float = 2.0, return_vector: bool = False, family: int = 0):
+                   a0: float = 1.0, decay=2.0, return_vector: bool = False, family: int = 0):
     """Steps 2-4 of Algorithm 1 for a given coarse pair: one shifted solve and a Rayleigh quotient."""
-    a = fem.coefficient(n_fine, y_fine, a0, decay, family)
-    A = fem.stiffness(n_fine, a)
+    A = fem.operator(n_fine, y_fine, a0, decay, family)
     M = fem.mass(n_fine)
     if n_fine == n_coarse:
         Pu = u_H.copy()
@@ -123,7 +119,7 @@ def twogrid_update(n_fine: int, y_fine: np.ndarray, lam_H: float, u_H: np.ndarra
 
 
 def twogrid(n_fine: int, s: int, n_coarse: int, S: int, y: np.ndarray, a0: float = 1.0,
-            decay: float = 2.0, family: int = 0) -> float:
+            decay=2.0, family: int = 0) -> float:
     """Algorithm 1 for one parameter vector y (len(y) >= s >= S).  Degenerate H = h, S = s:
     the coarse eigenvalue itself."""
     lam_H, u_H = coarse_pair(n_coarse, y[:S], a0, decay, family)
@@ -132,7 +128,14 @@ def twogrid(n_fine: int, s: int, n_coarse: int, S: int, y: np.ndarray, a0: float
     return twogrid_update(n_fine, y[:s], lam_H, u_H, n_coarse, a0, decay, family=family)
 
 
-def fine_eigenvalue(n: int, y: np.ndarray, a0: float = 1.0, decay: float = 2.0, family: int = 0) -> float:
+def fine_eigenvalue(n: int, y: np.ndarray, a0: float = 1.0, decay=2.0, family: int = 0) -> float:
     """lambda_{h,s}(y): the smallest FE eigenvalue on mesh 1/n with s = len(y) terms."""
-    a = fem.coefficient(n, y, a0, decay, family)
-    return smallest_eigpair(fem.stiffness(n, a), fem.mass(n))[0]
+    return smallest_eigpair(fem.operator(n, y, a0, decay, family), fem.mass(n))[0]
+
+
+def functional(n: int, u: np.ndarray) -> float:
+    """G(u) for the linear functional G(v) = integral of v over D, with u scaled to ||u||_{L2} = 1
+    and the sign that makes the integral positive (Sec. 1: the eigenfunction is made unique by its
+    normalisation and a consistent sign, and each approximation u_l likewise):
+    |integral of u| / sqrt(u^T M u)."""
+    return abs(fem.integral(n, u)) / float(np.sqrt(u @ (fem.mass(n) @ u)))
