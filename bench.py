@@ -178,7 +178,10 @@ def setup_context(binding, wl, stream_ptr, prec, rank=0, world=1):
     """A context on the workload; with several ranks, this rank's share of the workload's shifts.
     The reuse workload (shared shifts) uses one embedded lattice and the library's reuse scheme."""
     ctx = binding.Context(0, stream_ptr)
-    ctx.mq_set_coefficient(wl.a0, max(lv.s for lv in wl.levels), wl.family, wl.decay)
+    if wl.family == 2:
+        ctx.mq_set_islands(max(lv.s for lv in wl.levels), *wl.decays)
+    else:
+        ctx.mq_set_coefficient(wl.a0, max(lv.s for lv in wl.levels), wl.family, wl.decay)
     ctx.mq_set_levels(wl.levels)
     shared = wl.extra.get("shared", False)
     if shared:
@@ -378,7 +381,7 @@ def oracle_level_rates(wl, zs, ds, levels, budget, pool, cores):
         pv = wl.levels[l - 1] if l > 0 else None
         for p in range(procs[l]):
             ks = [(p * 7919 + i * 104729) % lv.N for i in range(100000)]
-            jobs.append((lv, pv, zs[l], ds[l], ks, (wl.a0, wl.decay, wl.family), budget))
+            jobs.append((lv, pv, zs[l], ds[l], ks, (wl.a0, wl.coef_decay, wl.family), budget))
             owner.append(l)
     res = pool.map(_oracle_worker, jobs, chunksize=1)
     per = {}

@@ -8,6 +8,11 @@
  * split by its south-west to north-east diagonal (Sec. 2.3), with a evaluated at triangle
  * centroids and the exact consistent mass matrix.
  *
+ * The second test problem of Sec. 5 adds a reaction term: -div(a grad u) + b u = lambda u with
+ * b(x, y) = b0 + sum_j y_j b_j(x) (mq_set_islands).  Instead of the eigenvalue the quantity of
+ * interest can be the linear functional G(u) = integral of u over D of the L2-normalised
+ * eigenfunction with positive integral (mq_set_qoi; Sec. 1 and Sec. 4.3: the same estimator).
+ *
  * The library evaluates, for a batch of randomly shifted rank-1 lattice points (Sec. 2.5,
  * eq. rqmc, eq. t_kl), the two-grid-truncation eigenvalue approximations of Algorithm 1 and the
  * level differences lambda^l - lambda^{l-1} of Algorithm 2, and forms the shift-averaged MLQMC
@@ -48,6 +53,12 @@ typedef enum {
                       its matrix-multiply barriers); the outputs of that call are not valid */
   MQ_ESTATE = 6    /* call out of order (e.g. evaluate before levels, lattice or shifts are set) */
 } mq_status;
+
+/* Quantity of interest of the level samples (mq_set_qoi). */
+typedef enum {
+  MQ_QOI_EIGENVALUE = 0, /* the smallest eigenvalue (default) */
+  MQ_QOI_FUNCTIONAL = 1  /* G(u) = |integral of u over D| / ||u||_L2 of the eigenfunction approximation */
+} mq_qoi;
 
 typedef enum {
   MQ_PREC_FP64 = 0,  /* every step in FP64 */
@@ -92,10 +103,36 @@ mq_status mq_destroy(mq_ctx* ctx);
  * eq. coeff_s), psi_j(x) = j^-decay sin(pi k1_j x1) sin(pi k2_j x2).  family 0: (k1, k2) the
  * j-th pair with k1, k2 >= 1 ordered by k1^2 + k2^2, ties by smaller k1; family 1: (j, j+1), the
  * first test problem of Sec. 5 (decay p~ = 4/3, 2 or 3 there; a0 = pi / sqrt(2) keeps a > 0 for
- * p~ = 4/3).  Other families give MQ_EINVAL.  s_max bounds the
- * truncation of every level.  a0 > 0.  Requires a >= a_min > 0 at all centroids (checked per
- * evaluation: a non-positive value gives MQ_EINVAL). */
+ * p~ = 4/3).  family 2: the second test problem of Sec. 5 with all four decays equal to `decay`
+ * (see mq_set_islands; a0 is then unused but must still be positive).  Other families give
+ * MQ_EINVAL.  s_max bounds the truncation of every level.  a0 > 0.  Requires a >= a_min > 0 at all
+ * centroids (checked per evaluation: a sample with a non-positive value is flagged and the call
+ * returns MQ_ENOCONV). */
 mq_status mq_set_coefficient(mq_ctx* ctx, double a0, int32_t s_max, int32_t family, double decay);
+
+/* The second test problem of Sec. 5 (coefficient family 2): four islands
+ *     D_f = [1/8,3/8]^2 u [5/8,7/8]^2 u [1/8,3/8]x[5/8,7/8] u [5/8,7/8]x[1/8,3/8],
+ * the operator -div(a grad u) + b u with
+ *     a = a_0 + sum_j y_j a_j,  a_0 = 0.01 on D_f, 0.011 off D_f,
+ *     b = b_0 + sum_j y_j b_j,  b_0 = 2 on D_f, 0.3 off D_f,
+ *     odd j, k = (j+1)/2:  a_j = 0.01 w_k(p_a),   b_j = 2 w_k(p_b)     on D_f, 0 off D_f,
+ *     even j, k = j/2:     a_j = 0.011 w_k(p_a'), b_j = 0.3 w_k(p_b')  off D_f, 0 on D_f,
+ *     w_k(q; x) = k^-q sin(8 k pi x1) sin(8 (k+1) pi x2).
+ * A zeroth term is multiplied by pi / sqrt(2) on the region whose decay is below 2 (p_a for a_0 on
+ * D_f, p_a' off D_f, p_b and p_b' for b_0).  A triangle belongs to D_f when its centroid does (the
+ * meshes 1/8 and finer resolve the islands exactly).  The reaction enters every operator as the
+ * P1 matrix B = sum_T b_T M_T (b constant per triangle, its centroid value).  Requires a > 0 and
+ * b >= 0 at all centroids (checked per evaluation like a).  The fine solves of this family run in
+ * the per-sample kernel: levels configured for the streaming tier give MQ_EINVAL when evaluated. */
+mq_status mq_set_islands(mq_ctx* ctx, int32_t s_max, double p_a, double p_a_prime, double p_b, double p_b_prime);
+
+/* Quantity of interest (mq_qoi).  MQ_QOI_FUNCTIONAL: the per-sample values and every estimate
+ * refer to G(u) = |integral of u| / ||u||_L2 (Sec. 1: each eigenfunction approximation is
+ * normalised and given the sign of the eigenfunction, whose integral is positive): G(u_H) of the
+ * coarse eigenvector on direct levels, G(w) of the two-grid solution w of Algorithm 1 otherwise.
+ * Per-sample records then hold (lambda_H, G^l, G^{l-1}, G^l - G^{l-1}).  Changing the quantity
+ * resets the estimator sums and switches the reuse scheme off. */
+mq_status mq_set_qoi(mq_ctx* ctx, int32_t qoi);
 
 /* Levels l = 0..L (copied).  Resets the estimator sums, lattices and shifts. */
 mq_status mq_set_levels(mq_ctx* ctx, int32_t L_plus_1, const mq_level* levels);
@@ -127,7 +164,7 @@ mq_status mq_set_shifts(mq_ctx* ctx, int32_t level, const double* delta);
  * exceed N_{l-1}.  With shared shifts the levels are not independent: mq_estimate takes the
  * standard error from the per-shift totals sum_l Q^(r)_l (eq. sample_var applied to them)
  * instead of adding the level variances (level_var still reports eq. sample_var per level).
- * on = 1: validate, allocate the store (R N_0 (n_0+1)^2 + R sum_l N_l doubles; kept for the next
+ * on = 1: validate, allocate the store (R N_0 ((n_0+1)^2 + 1) + R sum_l N_l doubles; kept for the next
  * mq_set_reuse(1)) and mark every point empty; on = 0: free the store.  A later mq_set_lattice* or
  * mq_set_shifts switches the scheme off (call mq_set_reuse(1) again after them); mq_set_levels
  * also frees the store.
@@ -150,9 +187,10 @@ mq_status mq_set_precision(mq_ctx* ctx, mq_precision prec, double tol_linear);
 mq_status mq_set_solver_options(mq_ctx* ctx, double tol_inner, int32_t max_inner, int32_t max_outer);
 
 /* Coarse eigensolver options (values <= 0 keep the defaults): tol_eig is the target of the
- * relative eigen-residual ||A_H x - theta M_H x|| / (theta ||M_H x||) of LOBPCG (default 1e-8),
- * max_eig the iteration cap (200).  The Rayleigh quotient theta = lambda_H is accurate to about
- * the square of tol_eig. */
+ * relative eigen-residual ||A_H x - theta M_H x|| / (theta ||M_H x||) of LOBPCG (default 1e-8,
+ * 1e-11 for MQ_QOI_FUNCTIONAL), max_eig the iteration cap (200).  The Rayleigh quotient
+ * theta = lambda_H is accurate to about the square of tol_eig, the eigenvector (and so G(u_H)) to
+ * about tol_eig. */
 mq_status mq_set_eig_options(mq_ctx* ctx, double tol_eig, int32_t max_eig);
 
 /* Damped Jacobi steps before and after each coarse-grid correction of the multigrid V-cycle that
@@ -379,12 +417,20 @@ mq_status mq_lattice_points_device(mq_ctx* ctx, int32_t level, uint32_t k0, uint
 
 /* Coefficients at the centroids of mesh 1/n (eq. coeff_s): d_a[b][2n^2] = a0 + sum_{j<s}
  * d_Y[b*ldy + j] psi_{j+1}(c_t), for b < B, with the context's precision mode
- * (FP64: FP64 GEMM; MIXED: tensor-core split GEMM accurate to FP64 rounding of the terms). */
+ * (FP64: FP64 GEMM; MIXED: tensor-core split GEMM accurate to FP64 rounding of the terms).
+ * Family 2: the piecewise a_0 in place of a0. */
 mq_status mq_coefficients_device(mq_ctx* ctx, int32_t n, int32_t s, const double* d_Y,
                                  int32_t B, int32_t ldy, double* d_a);
 
+/* The reaction coefficient of family 2 at the centroids of mesh 1/n, as mq_coefficients_device:
+ * d_b[b][2n^2] = b_0(c_t) + sum_{j<s} d_Y[b*ldy + j] b_{j+1}(c_t).  MQ_ESTATE for other families. */
+mq_status mq_reaction_coefficients_device(mq_ctx* ctx, int32_t n, int32_t s, const double* d_Y,
+                                          int32_t B, int32_t ldy, double* d_b);
+
 /* Operator apply on mesh 1/n for B coefficient fields d_a[b][2n^2] (FP64):
- * which = 0: y = A x, 1: y = M x, 2: y = (A - sigma M) x.  d_x, d_y: [B][(n-1)^2]. */
+ * which = 0: y = A x, 1: y = M x, 2: y = (A - sigma M) x; with d_a holding reaction coefficients b,
+ * which = 3: y = B x, the reaction matrix in the edge-weight form the inner solves use, and 4: the
+ * same from the centroid values (the form of the FP64 residual).  d_x, d_y: [B][(n-1)^2]. */
 mq_status mq_apply_operator_device(mq_ctx* ctx, int32_t n, int32_t B, const double* d_a,
                                    int32_t which, double sigma, const double* d_x, double* d_y);
 

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(HERE, "lib", "libmlqmc_evp.so")
 
 MQ_OK, MQ_EINVAL, MQ_ENOMEM, MQ_ECUDA, MQ_ENOCONV, MQ_ETIMEOUT, MQ_ESTATE = range(7)
 MQ_PREC_FP64, MQ_PREC_MIXED = 0, 1
+MQ_QOI_EIGENVALUE, MQ_QOI_FUNCTIONAL = 0, 1
 STATUS_NAMES = {0: "MQ_OK", 1: "MQ_EINVAL", 2: "MQ_ENOMEM", 3: "MQ_ECUDA", 4: "MQ_ENOCONV", 5: "MQ_ETIMEOUT",
                 6: "MQ_ESTATE"}
 
@@ -31,7 +32,7 @@ EXPORTS = [
     "mq_apply_operator_device", "mq_twogrid_samples_noalloc", "mq_set_lattice_embedded", "mq_set_reuse",
     "mq_cbc_embedded_lattice", "mq_get_sums", "mq_estimate_sums", "mq_run_adaptive", "mq_set_level_config",
     "mq_autotune_level", "mq_graph_capture", "mq_graph_launch", "mq_get_graph_info", "mq_set_kernel_probe",
-    "mq_get_kernel_probe", "mq_measure_fp64_peak",
+    "mq_get_kernel_probe", "mq_measure_fp64_peak", "mq_set_islands", "mq_set_qoi", "mq_reaction_coefficients_device",
 ]
 
 
@@ -128,6 +129,9 @@ def load(path: str = LIB_PATH):
         "mq_cbc_lattice": ([u32, i32, f64, C.POINTER(u32)], C.c_int),
         "mq_lattice_points_device": ([P, i32, u32, u32, P], C.c_int),
         "mq_coefficients_device": ([P, i32, i32, P, i32, i32, P], C.c_int),
+        "mq_reaction_coefficients_device": ([P, i32, i32, P, i32, i32, P], C.c_int),
+        "mq_set_islands": ([P, i32, f64, f64, f64, f64], C.c_int),
+        "mq_set_qoi": ([P, i32], C.c_int),
         "mq_apply_operator_device": ([P, i32, i32, P, i32, f64, P, P], C.c_int),
         "mq_twogrid_samples_noalloc": ([i32, i32, i32, i32, i32, P, P, P, f64, P, P, P, P], C.c_int),
     }
@@ -192,6 +196,13 @@ class Context:
     # --- configuration ---------------------------------------------------------------------
     def mq_set_coefficient(self, a0=1.0, s_max=16, family=0, decay=2.0):
         self._check(self.lib.mq_set_coefficient(self.h, float(a0), int(s_max), int(family), float(decay)))
+
+    def mq_set_islands(self, s_max, p_a=2.0, p_a_prime=2.0, p_b=2.0, p_b_prime=2.0):
+        self._check(self.lib.mq_set_islands(self.h, int(s_max), float(p_a), float(p_a_prime), float(p_b),
+                                            float(p_b_prime)))
+
+    def mq_set_qoi(self, qoi=MQ_QOI_EIGENVALUE):
+        self._check(self.lib.mq_set_qoi(self.h, int(qoi)))
 
     def mq_set_levels(self, levels):
         arr = (mq_level * len(levels))()
@@ -362,6 +373,10 @@ class Context:
     def mq_coefficients_device(self, n, s, d_Y, B, ldy, d_a):
         self._check(self.lib.mq_coefficients_device(self.h, int(n), int(s), _tptr(d_Y), int(B), int(ldy),
                                                     _tptr(d_a)))
+
+    def mq_reaction_coefficients_device(self, n, s, d_Y, B, ldy, d_b):
+        self._check(self.lib.mq_reaction_coefficients_device(self.h, int(n), int(s), _tptr(d_Y), int(B), int(ldy),
+                                                             _tptr(d_b)))
 
     def mq_apply_operator_device(self, n, B, d_a, which, sigma, d_x, d_y):
         self._check(self.lib.mq_apply_operator_device(self.h, int(n), int(B), _tptr(d_a), int(which), float(sigma),

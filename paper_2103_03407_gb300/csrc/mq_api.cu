@@ -43,10 +43,14 @@ struct mq_ctx {
 
   bool coef_set = false;
   double a0 = 1.0, decay = 2.0;
+  double decays[4] = {2.0, 2.0, 2.0, 2.0};  // family 2: p_a, p_a', p_b, p_b'
   int s_max = 0, family = 0;
   int* d_k1 = nullptr;
   int* d_k2 = nullptr;
-  double* d_cj = nullptr;
+  double* d_cj[2] = {nullptr, nullptr};  // term factors of a (and, family 2, of b)
+  int* d_region = nullptr;               // family 2: per term 1 (on D_f) or 2 (off D_f)
+  int psi_exp[2] = {0, 0};               // tensor-core slices of a table hold 2^psi_exp psi
+  int qoi = MQ_QOI_EIGENVALUE;
 
   std::vector<mq_level> levels;
   std::vector<std::vector<uint32_t>> z;
@@ -64,7 +68,8 @@ struct mq_ctx {
   // level's two-grid values, per shift and point, and which points hold values
   bool reuse = false;
   DevBuf ru0;                            // [R][N_0][(n_0+1)^2] padded level-0 eigenvectors
-  std::vector<DevBuf> rlam;              // per level: [R][N_l] lambda^l (level 0: lambda_{h_0,s_0})
+  DevBuf rlamH;                          // [R][N_0] their eigenvalues (the coarse shifts of levels >= 1)
+  std::vector<DevBuf> rlam;              // per level: [R][N_l] the quantity of interest Q^l (lambda^l or G)
   std::vector<std::vector<uint8_t>> rfilled;  // per level: point k has values
 
   // graph schedule (mq_graph_capture / mq_graph_launch): the captured evaluation, its body-capture
@@ -93,10 +98,13 @@ struct mq_ctx {
   int opt_max_eig = 0;
   int opt_nu = 0;  // Jacobi sweeps per side of the V-cycle (0: default)
 
-  std::map<int, std::pair<int, double*>> psi;  // mesh n -> (rows, table [rows][2n^2])
-  std::map<int, std::pair<int, void*>> psi_sl;  // mesh n -> (K pad, BF16 slices [6][nT pad][K pad])
+  // per coefficient (0: a, 1: the reaction b of family 2)
+  std::map<int, std::pair<int, double*>> psi[2];  // mesh n -> (rows, table [rows][2n^2])
+  std::map<int, std::pair<int, void*>> psi_sl[2];  // mesh n -> (K pad, BF16 slices [7][nT pad][K pad])
+  std::map<int, double*> base[2];                  // family 2: mesh n -> zeroth term a_0 (b_0) per triangle
 
   DevBuf Y, af, ac, ap, out, stat, outer, scratch, sums_d, flags_d, uout, misc, upad, arena, ysl, tc_err;
+  DevBuf bf, bc, bp;  // reaction coefficients of the fine, coarse and previous meshes (family 2)
   int stream_min = 0;  // fine meshes 1/n with n >= stream_min use the streaming tier (0: default)
   mq_stats stats{};
   size_t last_B = 0;  // samples of the last pass (their per-sample counters are still on the device)
@@ -173,6 +181,8 @@ void invalidate_reuse(mq_ctx* c) {
 void free_reuse(mq_ctx* c) {
   if (c->ru0.p) cudaFree(c->ru0.p);
   c->ru0 = DevBuf{};
+  if (c->rlamH.p) cudaFree(c->rlamH.p);
+  c->rlamH = DevBuf{};
   for (DevBuf& b : c->rlam)
     if (b.p) cudaFree(b.p);
   c->rlam.clear();
@@ -210,16 +220,31 @@ void psi_pairs(int s, int family, std::vector<int>& k1, std::vector<int>& k2) {
   }
 }
 
-mq_status ensure_psi(mq_ctx* c, int n, int rows, const double** out) {
-  auto it = c->psi.find(n);
-  if (it != c->psi.end() && it->second.first >= rows) {
+// the second test problem of Sec. 5: four islands, two coefficients with piecewise zeroth terms
+constexpr double kSigA[2] = {0.01, 0.011}, kSigB[2] = {2.0, 0.3};  // on D_f, off D_f
+
+void release_tables(mq_ctx* c) {
+  for (int w = 0; w < 2; ++w) {
+    for (auto& kv : c->psi[w]) cudaFree(kv.second.second);
+    c->psi[w].clear();
+    for (auto& kv : c->psi_sl[w]) cudaFree(kv.second.second);
+    c->psi_sl[w].clear();
+    for (auto& kv : c->base[w]) cudaFree(kv.second);
+    c->base[w].clear();
+  }
+}
+
+mq_status ensure_psi(mq_ctx* c, int n, int rows, const double** out, int which = 0) {
+  auto& tab = c->psi[which];
+  auto it = tab.find(n);
+  if (it != tab.end() && it->second.first >= rows) {
     *out = it->second.second;
     return MQ_OK;
   }
-  if (it != c->psi.end()) {
+  if (it != tab.end()) {
     graph_release(c);
     cudaFree(it->second.second);
-    c->psi.erase(it);
+    tab.erase(it);
   }
   const size_t bytes = (size_t)std::max(rows, 1) * 2 * n * n * sizeof(double);
   double* d = nullptr;
@@ -227,23 +252,47 @@ mq_status ensure_psi(mq_ctx* c, int n, int rows, const double** out) {
     cudaGetLastError();
     return fail(c, MQ_ENOMEM, "psi table for n=%d, s=%d (%zu bytes)", n, rows, bytes);
   }
-  MQ_LAUNCH(c, mq::launch_psi_table(n, rows, c->d_k1, c->d_k2, c->d_cj, d, c->stream));
-  c->psi[n] = {rows, d};
+  MQ_LAUNCH(c, mq::launch_psi_table(n, rows, c->d_k1, c->d_k2, c->d_cj[which], d, c->stream, c->d_region));
+  tab[n] = {rows, d};
+  *out = d;
+  return MQ_OK;
+}
+
+// family 2: the zeroth term (a_0 for which = 0, b_0 for 1) on the triangles of mesh n, scaled by
+// pi / sqrt(2) on a region whose terms decay with a power below 2
+mq_status ensure_base(mq_ctx* c, int n, int which, const double** out) {
+  auto it = c->base[which].find(n);
+  if (it != c->base[which].end()) {
+    *out = it->second;
+    return MQ_OK;
+  }
+  double* d = nullptr;
+  const size_t bytes = (size_t)2 * n * n * sizeof(double);
+  if (cudaMalloc(&d, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, MQ_ENOMEM, "zeroth-term field for n=%d (%zu bytes)", n, bytes);
+  }
+  const double* sig = which ? kSigB : kSigA;
+  const double p_in = c->decays[2 * which], p_out = c->decays[2 * which + 1];
+  const double sc = 3.14159265358979323846 / std::sqrt(2.0);
+  MQ_LAUNCH(c, mq::launch_island_field(n, sig[0] * (p_in < 2.0 ? sc : 1.0), sig[1] * (p_out < 2.0 ? sc : 1.0), d,
+                                       c->stream));
+  c->base[which][n] = d;
   *out = d;
   return MQ_OK;
 }
 
 // BF16 slices of the Psi table of mesh n for the tensor-core path (cached per mesh)
-mq_status ensure_psi_slices(mq_ctx* c, int n, const void** out, int* kpad) {
-  auto it = c->psi_sl.find(n);
+mq_status ensure_psi_slices(mq_ctx* c, int n, const void** out, int* kpad, int which = 0) {
+  auto it = c->psi_sl[which].find(n);
   const int rows = std::max(c->s_max, 1);
-  if (it != c->psi_sl.end()) {
+  if (it != c->psi_sl[which].end()) {
     *out = it->second.second;
     *kpad = it->second.first;
     return MQ_OK;
   }
   const double* psi = nullptr;
-  mq_status st = ensure_psi(c, n, rows, &psi);
+  mq_status st = ensure_psi(c, n, rows, &psi, which);
   if (st != MQ_OK) return st;
   const int nT = 2 * n * n;
   void* d = nullptr;
@@ -252,33 +301,37 @@ mq_status ensure_psi_slices(mq_ctx* c, int n, const void** out, int* kpad) {
     cudaGetLastError();
     return fail(c, MQ_ENOMEM, "psi slices for n=%d (%zu bytes)", n, bytes);
   }
-  MQ_LAUNCH(c, mq::launch_psi_slices(psi, rows, nT, d, c->stream));
-  c->psi_sl[n] = {mq::tc_pad_k(rows), d};
+  MQ_LAUNCH(c, mq::launch_psi_slices(psi, rows, nT, d, c->stream, c->psi_exp[which]));
+  c->psi_sl[which][n] = {mq::tc_pad_k(rows), d};
   *out = d;
   *kpad = mq::tc_pad_k(rows);
   return MQ_OK;
 }
 
 // a[b][t] = a0 + sum_{j<K} Y[b][j] psi_j(c_t) for B rows of Y (stride ldy) on mesh n: FP64 GEMM in
-// MQ_PREC_FP64, tensor-core split GEMM in MQ_PREC_MIXED
-mq_status coefficients(mq_ctx* c, int n, int K, const double* d_Y, int B, int ldy, double* d_a) {
+// MQ_PREC_FP64, tensor-core split GEMM in MQ_PREC_MIXED.  which = 1: the reaction coefficient b of
+// family 2 (which, like its a, takes a piecewise zeroth term in place of a0).
+mq_status coefficients(mq_ctx* c, int n, int K, const double* d_Y, int B, int ldy, double* d_a, int which = 0) {
   const int nT = 2 * n * n;
+  mq_status st;
+  const double* base = nullptr;
+  if (c->family == 2 && (st = ensure_base(c, n, which, &base)) != MQ_OK) return st;
+  const double a0 = base ? 0.0 : c->a0;
   if (c->prec == MQ_PREC_MIXED && K > 0) {
     const void* ps = nullptr;
     int kps = 0;
-    mq_status st = ensure_psi_slices(c, n, &ps, &kps);
-    if (st != MQ_OK) return st;
+    if ((st = ensure_psi_slices(c, n, &ps, &kps, which)) != MQ_OK) return st;
     const int kpad = mq::tc_pad_k(K);
     if ((st = grow(c, c->ysl, mq::tc_slices_bytes(B, K))) != MQ_OK) return st;
     if ((st = grow(c, c->tc_err, sizeof(int))) != MQ_OK) return st;
     MQ_LAUNCH(c, mq::launch_y_slices(d_Y, B, ldy, K, kpad, c->ysl.p, c->stream));
-    MQ_LAUNCH(c, mq::launch_coef_tc(c->ysl.p, B, kpad, ps, nT, kps, c->a0, d_a, (int*)c->tc_err.p, c->stream));
+    MQ_LAUNCH(c, mq::launch_coef_tc(c->ysl.p, B, kpad, ps, nT, kps, a0, d_a, (int*)c->tc_err.p, c->stream, base,
+                                    c->psi_exp[which]));
     return MQ_OK;
   }
   const double* psi = nullptr;
-  mq_status st = ensure_psi(c, n, std::max(c->s_max, 1), &psi);
-  if (st != MQ_OK) return st;
-  MQ_LAUNCH(c, mq::launch_coef_gemm_f64(d_Y, ldy, B, K, psi, nT, c->a0, d_a, c->stream));
+  if ((st = ensure_psi(c, n, std::max(c->s_max, 1), &psi, which)) != MQ_OK) return st;
+  MQ_LAUNCH(c, mq::launch_coef_gemm_f64(d_Y, ldy, B, K, psi, nT, a0, d_a, c->stream, base));
   return MQ_OK;
 }
 
@@ -355,9 +408,10 @@ LevelGeom geom(const mq_ctx* c, int level) {
   return g;
 }
 
-// whether the fine solve of mesh g.nf runs in the streaming tier
+// whether the fine solve of mesh g.nf runs in the streaming tier (whose kernels carry no reaction
+// term: the second test problem solves in the per-sample kernel)
 bool streams(const mq_ctx* c, const LevelGeom& g) {
-  if (g.direct_f) return false;
+  if (g.direct_f || c->family == 2) return false;
   if (g.tier >= 0) return g.tier == 1;
   return g.nf >= stream_threshold(c);
 }
@@ -371,11 +425,18 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
   const size_t B = (size_t)R * npts;
   mq_status st;
   const bool given = c->reuse && level >= 1;  // coarse pair and lambda^{l-1} come from the store
+  const bool rxn = c->family == 2;            // reaction term b u
+  if (rxn && g.tier == 1) return fail(c, MQ_EINVAL, "the streaming tier carries no reaction term");
   const size_t nTf = (size_t)2 * g.nf * g.nf, nTc = (size_t)2 * g.nc * g.nc, nTp = (size_t)2 * g.np * g.np;
   const size_t Vc = (size_t)(g.nc + 1) * (g.nc + 1);
   if (!given && (st = grow(c, c->ac, B * nTc * sizeof(double))) != MQ_OK) return st;
   if (!g.direct_f && (st = grow(c, c->af, B * nTf * sizeof(double))) != MQ_OK) return st;
   if (!given && g.np && !g.direct_p && (st = grow(c, c->ap, B * nTp * sizeof(double))) != MQ_OK) return st;
+  if (rxn) {
+    if (!given && (st = grow(c, c->bc, B * nTc * sizeof(double))) != MQ_OK) return st;
+    if (!g.direct_f && (st = grow(c, c->bf, B * nTf * sizeof(double))) != MQ_OK) return st;
+    if (!given && g.np && !g.direct_p && (st = grow(c, c->bp, B * nTp * sizeof(double))) != MQ_OK) return st;
+  }
   if ((st = grow(c, c->out, B * 4 * sizeof(double))) != MQ_OK) return st;
   if ((st = grow(c, c->stat, B * 4 * sizeof(int))) != MQ_OK) return st;
   if ((st = grow(c, c->outer, B * 2 * sizeof(int))) != MQ_OK) return st;
@@ -388,16 +449,22 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
   const double* Y = (const double*)c->Y.p;
   if (given) {
     const uint32_t N0 = c->levels[0].N, Np = c->levels[level - 1].N;
-    MQ_LAUNCH(c, mq::launch_reuse_gather(R, npts, kbase, Vc, (const double*)c->ru0.p, (const double*)c->rlam[0].p, N0,
+    MQ_LAUNCH(c, mq::launch_reuse_gather(R, npts, kbase, Vc, (const double*)c->ru0.p, (const double*)c->rlamH.p, N0,
                                          (const double*)c->rlam[level - 1].p, Np, (double*)c->upad.p,
                                          (double*)c->out.p, c->stream, kshift(c)));
     MQ_CUDA(c, cudaMemsetAsync(c->stat.p, 0, B * 4 * sizeof(int), c->stream));
     MQ_CUDA(c, cudaMemsetAsync(c->outer.p, 0, B * 2 * sizeof(int), c->stream));
   } else {
     if ((st = coefficients(c, g.nc, g.S, Y, (int)B, g.s, (double*)c->ac.p)) != MQ_OK) return st;
+    if (rxn && (st = coefficients(c, g.nc, g.S, Y, (int)B, g.s, (double*)c->bc.p, 1)) != MQ_OK) return st;
   }
   if (!g.direct_f && (st = coefficients(c, g.nf, g.s, Y, (int)B, g.s, (double*)c->af.p)) != MQ_OK) return st;
+  if (rxn && !g.direct_f && (st = coefficients(c, g.nf, g.s, Y, (int)B, g.s, (double*)c->bf.p, 1)) != MQ_OK)
+    return st;
   if (!given && g.np && !g.direct_p && (st = coefficients(c, g.np, g.sp, Y, (int)B, g.s, (double*)c->ap.p)) != MQ_OK)
+    return st;
+  if (rxn && !given && g.np && !g.direct_p &&
+      (st = coefficients(c, g.np, g.sp, Y, (int)B, g.s, (double*)c->bp.p, 1)) != MQ_OK)
     return st;
   if (!c->capturing) MQ_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
 
@@ -426,6 +493,11 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
   p.a_f = (const double*)c->af.p;
   p.a_c = (const double*)c->ac.p;
   p.a_p = (const double*)c->ap.p;
+  p.reaction = rxn ? 1 : 0;
+  p.b_f = rxn ? (const double*)c->bf.p : nullptr;
+  p.b_c = rxn ? (const double*)c->bc.p : nullptr;
+  p.b_p = rxn ? (const double*)c->bp.p : nullptr;
+  p.qoi = c->qoi;
   p.out = (double*)c->out.p;
   p.stat = (int*)c->stat.p;
   p.outer = (int*)c->outer.p;
@@ -440,7 +512,9 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
   // twice whatever the targets (the FP32 rounding of the first correction, which is
   // amplified by the near-singular shift, leaves a residual of ~1e-4): inner reductions of 1e-4
   // and a target of 1e-5 leave lambda^h within ~2e-13 (1e-5 inner reductions above mesh 1/128).
-  p.tol_eig = c->opt_tol_eig > 0 ? c->opt_tol_eig : 1e-8;
+  // The functional G(u_H) of a direct level is first order in the eigenvector error, which the
+  // eigen-residual bounds only to ~tol_eig (lambda_H is second order): it takes 1e-11.
+  p.tol_eig = c->opt_tol_eig > 0 ? c->opt_tol_eig : (c->qoi == MQ_QOI_FUNCTIONAL ? 1e-11 : 1e-8);
   p.max_eig_it = c->opt_max_eig > 0 ? c->opt_max_eig : 200;
   p.tol_lin = c->tol_lin > 0 ? c->tol_lin : (mixed ? 1e-5 : 1e-6);
   if (mixed) {
@@ -473,7 +547,7 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
   const int np_k = given ? 0 : g.np;  // the previous-level solve runs here only without the store
   const int in_kernel_n = std::max(p.mode_f != 2 && !g.direct_f ? g.nf : 0, p.mode_p != 2 && !g.direct_p ? np_k : 0);
   const int threads = g.threads > 0 ? g.threads : threads_for(in_kernel_n, g.nc);
-  const size_t slab = mq::sample_slab_bytes(g.nf, g.nc, np_k, mixed, p.mode_f, p.mode_p);
+  const size_t slab = mq::sample_slab_bytes(g.nf, g.nc, np_k, mixed, p.mode_f, p.mode_p, p.reaction);
   const int static_smem = mq::sample_static_smem(mixed);
   const size_t smem_cap = (size_t)std::max(0, c->smem_optin - static_smem - 1024);
   const bool use_smem = slab <= smem_cap;
@@ -517,6 +591,7 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
     s.omega = p.omega;
     s.nu = g.nu > 0 ? g.nu : (c->opt_nu > 0 ? c->opt_nu : 1);
     s.probe = (c->probe_on && !c->capturing) ? &c->probe : nullptr;
+    s.qoi = c->qoi;
     if (p.mode_f == 2) {
       s.n = g.nf;
       s.a = (const double*)c->af.p;
@@ -674,7 +749,7 @@ mq_status eval_level_impl(mq_ctx* c, int level, uint32_t k0, uint32_t k1, double
       const size_t V0 = (size_t)(l0.n_fine + 1) * (l0.n_fine + 1);
       MQ_LAUNCH(c, mq::launch_reuse_scatter(R, pn, k0 + p0, V0, (const double*)c->upad.p, (const double*)c->out.p,
                                             (double*)c->rlam[level].p, lv.N, level == 0 ? (double*)c->ru0.p : nullptr,
-                                            nullptr, l0.N, c->stream, kshift(c)));
+                                            level == 0 ? (double*)c->rlamH.p : nullptr, l0.N, c->stream, kshift(c)));
     }
     if (c->capturing) {
       // graph schedule: sums and flags accumulate on the device; outputs go to device buffers
@@ -812,10 +887,10 @@ mq_status mq_destroy(mq_ctx* c) {
   for (DevBuf* b : {&c->gcount, &c->gsums, &c->gflags, &c->gk0, &c->probe_bytes})
     if (b->p) cudaFree(b->p);
   for (DevBuf* b : {&c->Y, &c->af, &c->ac, &c->ap, &c->out, &c->stat, &c->outer, &c->scratch, &c->sums_d,
-                    &c->flags_d, &c->uout, &c->misc, &c->upad, &c->arena, &c->ysl, &c->tc_err})
+                    &c->flags_d, &c->uout, &c->misc, &c->upad, &c->arena, &c->ysl, &c->tc_err, &c->bf, &c->bc,
+                    &c->bp})
     if (b->p) cudaFree(b->p);
-  for (auto& kv : c->psi) cudaFree(kv.second.second);
-  for (auto& kv : c->psi_sl) cudaFree(kv.second.second);
+  release_tables(c);
   free_reuse(c);
   for (auto p : c->d_z)
     if (p) cudaFree(p);
@@ -823,7 +898,9 @@ mq_status mq_destroy(mq_ctx* c) {
     if (p) cudaFree(p);
   if (c->d_k1) cudaFree(c->d_k1);
   if (c->d_k2) cudaFree(c->d_k2);
-  if (c->d_cj) cudaFree(c->d_cj);
+  for (double* p : c->d_cj)
+    if (p) cudaFree(p);
+  if (c->d_region) cudaFree(c->d_region);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
   if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -833,39 +910,110 @@ mq_status mq_destroy(mq_ctx* c) {
 
 const char* mq_last_error(const mq_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
-mq_status mq_set_coefficient(mq_ctx* c, double a0, int32_t s_max, int32_t family, double decay) {
-  if (!c) return MQ_EINVAL;
+namespace {
+
+// Term tables of a family: wave numbers, factors of a (and b) and region codes, uploaded once.
+mq_status set_terms(mq_ctx* c, double a0, int32_t s_max, int32_t family, double decay, const double* decays4) {
   c->lanes_stale = true;
   graph_release(c);
   if (!(a0 > 0.0) || !std::isfinite(a0)) return fail(c, MQ_EINVAL, "a0 must be positive, got %g", a0);
   if (s_max < 0 || s_max > 65536) return fail(c, MQ_EINVAL, "s_max %d out of range", s_max);
-  if (family != 0 && family != 1) return fail(c, MQ_EINVAL, "unknown coefficient family %d", family);
+  if (family < 0 || family > 2) return fail(c, MQ_EINVAL, "unknown coefficient family %d", family);
   if (!std::isfinite(decay)) return fail(c, MQ_EINVAL, "decay must be finite");
+  if (decays4)
+    for (int i = 0; i < 4; ++i)
+      if (!std::isfinite(decays4[i])) return fail(c, MQ_EINVAL, "decays must be finite");
   MQ_CUDA(c, cudaSetDevice(c->device));
-  std::vector<int> k1, k2;
-  psi_pairs(std::max(s_max, 1), family, k1, k2);
-  std::vector<double> cj(std::max(s_max, 1));
-  for (int j = 0; j < (int)cj.size(); ++j) cj[j] = std::pow((double)(j + 1), -decay);
-  for (auto& kv : c->psi) cudaFree(kv.second.second);
-  c->psi.clear();
-  for (auto& kv : c->psi_sl) cudaFree(kv.second.second);
-  c->psi_sl.clear();
+  const int m = std::max(s_max, 1);
+  std::vector<int> k1, k2, region;
+  std::vector<double> cj[2];
+  cj[0].resize(m);
+  if (family == 2) {
+    // term j = 1, 2, ...: odd j on D_f with k = (j+1)/2, even j off D_f with k = j/2; w_k has wave
+    // numbers 8k and 8(k+1) in the pi-scaled sines
+    cj[1].resize(m);
+    k1.resize(m);
+    k2.resize(m);
+    region.resize(m);
+    for (int j = 1; j <= m; ++j) {
+      const bool odd = j % 2 == 1;
+      const int k = odd ? (j + 1) / 2 : j / 2;
+      const int r = odd ? 0 : 1;
+      k1[j - 1] = 8 * k;
+      k2[j - 1] = 8 * (k + 1);
+      region[j - 1] = odd ? 1 : 2;
+      cj[0][j - 1] = kSigA[r] * std::pow((double)k, -decays4[r]);
+      cj[1][j - 1] = kSigB[r] * std::pow((double)k, -decays4[2 + r]);
+    }
+  } else {
+    psi_pairs(m, family, k1, k2);
+    for (int j = 0; j < m; ++j) cj[0][j] = std::pow((double)(j + 1), -decay);
+  }
+  release_tables(c);
   if (c->d_k1) cudaFree(c->d_k1);
   if (c->d_k2) cudaFree(c->d_k2);
-  if (c->d_cj) cudaFree(c->d_cj);
-  const size_t m = cj.size();
+  for (double*& p : c->d_cj) {
+    if (p) cudaFree(p);
+    p = nullptr;
+  }
+  if (c->d_region) cudaFree(c->d_region);
+  c->d_k1 = c->d_k2 = c->d_region = nullptr;
   MQ_CUDA(c, cudaMalloc(&c->d_k1, m * sizeof(int)));
   MQ_CUDA(c, cudaMalloc(&c->d_k2, m * sizeof(int)));
-  MQ_CUDA(c, cudaMalloc(&c->d_cj, m * sizeof(double)));
   MQ_CUDA(c, cudaMemcpy(c->d_k1, k1.data(), m * sizeof(int), cudaMemcpyHostToDevice));
   MQ_CUDA(c, cudaMemcpy(c->d_k2, k2.data(), m * sizeof(int), cudaMemcpyHostToDevice));
-  MQ_CUDA(c, cudaMemcpy(c->d_cj, cj.data(), m * sizeof(double), cudaMemcpyHostToDevice));
+  for (int w = 0; w < (family == 2 ? 2 : 1); ++w) {
+    MQ_CUDA(c, cudaMalloc(&c->d_cj[w], m * sizeof(double)));
+    MQ_CUDA(c, cudaMemcpy(c->d_cj[w], cj[w].data(), m * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  if (family == 2) {
+    MQ_CUDA(c, cudaMalloc(&c->d_region, m * sizeof(int)));
+    MQ_CUDA(c, cudaMemcpy(c->d_region, region.data(), m * sizeof(int), cudaMemcpyHostToDevice));
+  }
+  // slice scale of each table: the largest e with 2^e max_j |c_j| <= 1 (|sin sin| <= 1), e = 0 for the
+  // families whose factors j^-decay are at most 1
+  for (int w = 0; w < 2; ++w) {
+    double mx = 0.0;
+    for (double v : cj[w]) mx = std::max(mx, std::fabs(v));
+    int e = 0;
+    if (mx > 0.0 && std::isfinite(mx)) {
+      while (std::ldexp(mx, e) > 1.0) --e;
+      while (std::ldexp(mx, e + 1) <= 1.0) ++e;
+    }
+    c->psi_exp[w] = e;
+  }
   c->a0 = a0;
   c->s_max = s_max;
   c->family = family;
   c->decay = decay;
+  for (int i = 0; i < 4; ++i) c->decays[i] = decays4 ? decays4[i] : decay;
   c->coef_set = true;
   return MQ_OK;
+}
+
+}  // namespace
+
+mq_status mq_set_coefficient(mq_ctx* c, double a0, int32_t s_max, int32_t family, double decay) {
+  if (!c) return MQ_EINVAL;
+  const double d4[4] = {decay, decay, decay, decay};
+  return set_terms(c, a0, s_max, family, decay, family == 2 ? d4 : nullptr);
+}
+
+mq_status mq_set_islands(mq_ctx* c, int32_t s_max, double p_a, double p_a_out, double p_b, double p_b_out) {
+  if (!c) return MQ_EINVAL;
+  const double d4[4] = {p_a, p_a_out, p_b, p_b_out};
+  return set_terms(c, 1.0, s_max, 2, p_a, d4);
+}
+
+mq_status mq_set_qoi(mq_ctx* c, int32_t qoi) {
+  if (!c) return MQ_EINVAL;
+  if (qoi != MQ_QOI_EIGENVALUE && qoi != MQ_QOI_FUNCTIONAL) return fail(c, MQ_EINVAL, "unknown quantity %d", qoi);
+  if (qoi == c->qoi) return MQ_OK;
+  c->lanes_stale = true;
+  graph_release(c);
+  invalidate_reuse(c);  // the store holds values of the previous quantity
+  c->qoi = qoi;
+  return mq_reset_sums(c);
 }
 
 mq_status mq_set_levels(mq_ctx* c, int32_t L_plus_1, const mq_level* levels) {
@@ -1011,6 +1159,7 @@ mq_status mq_set_reuse(mq_ctx* c, int32_t on) {
   const size_t V0 = (size_t)(l0.n_fine + 1) * (l0.n_fine + 1);
   mq_status st = grow(c, c->ru0, (size_t)l0.R * l0.N * V0 * sizeof(double));
   if (st != MQ_OK) return st;
+  if ((st = grow(c, c->rlamH, (size_t)l0.R * l0.N * sizeof(double))) != MQ_OK) return st;
   if ((int)c->rlam.size() != L1) {
     for (DevBuf& b : c->rlam)
       if (b.p) cudaFree(b.p);
@@ -1255,8 +1404,12 @@ mq_status mq_eval_levels_device(mq_ctx* c, int32_t nlev, const int32_t* levels, 
       auto chk = [&](mq_status s2) {
         if (s2 != MQ_OK && st == MQ_OK) st = s2;
       };
-      chk(mq_set_coefficient(ch, c->a0, c->s_max, c->family, c->decay));
+      if (c->family == 2)
+        chk(mq_set_islands(ch, c->s_max, c->decays[0], c->decays[1], c->decays[2], c->decays[3]));
+      else
+        chk(mq_set_coefficient(ch, c->a0, c->s_max, c->family, c->decay));
       chk(mq_set_levels(ch, (int32_t)c->levels.size(), c->levels.data()));
+      chk(mq_set_qoi(ch, c->qoi));
       if (c->mbits[l])
         chk(mq_set_lattice_embedded(ch, l, c->z[l].data(), (int32_t)c->z[l].size(), c->mbits[l]));
       else
@@ -1904,13 +2057,29 @@ mq_status mq_coefficients_device(mq_ctx* c, int32_t n, int32_t s, const double* 
   return check_tc_error(c);
 }
 
+mq_status mq_reaction_coefficients_device(mq_ctx* c, int32_t n, int32_t s, const double* d_Y, int32_t B, int32_t ldy,
+                                          double* d_b) {
+  if (!c) return MQ_EINVAL;
+  if (!c->coef_set) return fail(c, MQ_ESTATE, "coefficient not set");
+  if (c->family != 2) return fail(c, MQ_ESTATE, "the coefficient family has no reaction term");
+  if (!pow2(n) || n < 2 || n > 4096 || s < 0 || s > c->s_max || B < 0 || ldy < s || (!d_Y && B * s) || (!d_b && B))
+    return fail(c, MQ_EINVAL, "bad coefficient arguments");
+  MQ_CUDA(c, cudaSetDevice(c->device));
+  mq_status st = reset_tc_error(c);
+  if (st != MQ_OK) return st;
+  st = coefficients(c, n, s, d_Y, B, ldy, d_b, 1);
+  if (st != MQ_OK) return st;
+  MQ_CUDA(c, cudaStreamSynchronize(c->stream));
+  return check_tc_error(c);
+}
+
 mq_status mq_apply_operator_device(mq_ctx* c, int32_t n, int32_t B, const double* d_a, int32_t which, double sigma,
                                    const double* d_x, double* d_y) {
   if (!c) return MQ_EINVAL;
-  if (!pow2(n) || n < 2 || n > 4096 || B < 0 || which < 0 || which > 2 || (B && (!d_a || !d_x || !d_y)))
+  if (!pow2(n) || n < 2 || n > 4096 || B < 0 || which < 0 || which > 4 || (B && (!d_a || !d_x || !d_y)))
     return fail(c, MQ_EINVAL, "bad operator arguments");
   MQ_CUDA(c, cudaSetDevice(c->device));
-  mq_status st = grow(c, c->misc, (size_t)B * 3 * (n + 1) * (n + 1) * sizeof(double));
+  mq_status st = grow(c, c->misc, (size_t)B * 4 * (n + 1) * (n + 1) * sizeof(double));
   if (st != MQ_OK) return st;
   MQ_LAUNCH(c, mq::launch_apply_operator(n, B, d_a, which, sigma, d_x, d_y, (double*)c->misc.p, c->stream));
   MQ_CUDA(c, cudaStreamSynchronize(c->stream));

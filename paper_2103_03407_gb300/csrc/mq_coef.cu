@@ -2,11 +2,14 @@
 //
 //  * lattice_points: y = {k z / N + Delta_r} - 1/2 (Sec. 2.5, eq. rqmc; eq. t_kl), exact integer
 //    arithmetic for k z mod N, one IEEE division and the same wrap as the fractional part.
-//  * psi_table: Psi[j][t] = j^-decay sin(pi k1_j x_t) sin(pi k2_j y_t) at the centroids of the
+//  * psi_table: Psi[j][t] = c_j sin(pi k1_j x_t) sin(pi k2_j y_t) at the centroids of the
 //    2 n^2 triangles (lower triangle of cell (i,j): ((3i+2)/(3n), (3j+1)/(3n)); upper:
-//    ((3i+1)/(3n), (3j+2)/(3n))).
+//    ((3i+1)/(3n), (3j+2)/(3n))), optionally restricted to the islands D_f of the second test
+//    problem of Sec. 5 or to their complement (region code per term).
+//  * island_field: the piecewise-constant zeroth terms a_0, b_0 of that problem.
 //  * coef_gemm_f64: a[b][t] = a0 + sum_{j<s} Y[b][j] Psi[j][t] (eq. coeff, eq. coeff_s) as a
-//    tiled FP64 GEMM (register-blocked 4 x 8 outputs per thread, shared-memory K tiles).
+//    tiled FP64 GEMM (register-blocked 4 x 8 outputs per thread, shared-memory K tiles); with a
+//    base field, base[t] in place of the constant a0.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -38,20 +41,49 @@ __global__ void lattice_kernel(const uint32_t* __restrict__ z, uint32_t N, const
   }
 }
 
+// Whether the centroid num / (3n) (one coordinate) lies in [1/8, 3/8] or [5/8, 7/8], decided in
+// integers: 8 num against 3n, 9n, 15n, 21n.  (A centroid never lies on such a line: 8 num is not a
+// multiple of 3, 3 n m is.)
+__device__ __forceinline__ bool island_band(long num, long n) {
+  const long e = 8 * num;
+  return (e >= 3 * n && e <= 9 * n) || (e >= 15 * n && e <= 21 * n);
+}
+
+// numerators of the centroid of triangle t (plane 0: lower, 1: upper) of cell (i, j) over 3n
+__device__ __forceinline__ void centroid_num(int n, size_t t, long& nx, long& ny) {
+  const size_t nn = (size_t)n * n;
+  const int plane = (int)(t / nn);
+  const size_t cell = t % nn;
+  const int i = (int)(cell % n), jj = (int)(cell / n);
+  nx = 3L * i + (plane == 0 ? 2 : 1);
+  ny = 3L * jj + (plane == 0 ? 1 : 2);
+}
+
 __global__ void psi_kernel(int n, int s, const int* __restrict__ k1, const int* __restrict__ k2,
-                           const double* __restrict__ cj, double* __restrict__ psi) {
+                           const double* __restrict__ cj, const int* __restrict__ region, double* __restrict__ psi) {
   const size_t nn = (size_t)n * n, nT = 2 * nn, tot = (size_t)s * nT;
-  const double inv3n = 1.0 / (3.0 * n);
-  (void)inv3n;
   for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += (size_t)gridDim.x * blockDim.x) {
     const int j = (int)(q / nT);
     const size_t t = q % nT;
-    const int plane = (int)(t / nn);
-    const size_t cell = t % nn;
-    const int i = (int)(cell % n), jj = (int)(cell / n);
-    const double x = (double)(3 * i + (plane == 0 ? 2 : 1)) / (double)(3 * n);
-    const double y = (double)(3 * jj + (plane == 0 ? 1 : 2)) / (double)(3 * n);
-    psi[q] = cj[j] * sinpi((double)k1[j] * x) * sinpi((double)k2[j] * y);
+    long nx, ny;
+    centroid_num(n, t, nx, ny);
+    const double x = (double)nx / (double)(3 * n);
+    const double y = (double)ny / (double)(3 * n);
+    double v = cj[j] * sinpi((double)k1[j] * x) * sinpi((double)k2[j] * y);
+    if (region && region[j]) {
+      const bool in = island_band(nx, n) && island_band(ny, n);
+      if (in != (region[j] == 1)) v = 0.0;
+    }
+    psi[q] = v;
+  }
+}
+
+__global__ void island_kernel(int n, double v_in, double v_out, double* __restrict__ base) {
+  const size_t nT = (size_t)2 * n * n;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < nT; t += (size_t)gridDim.x * blockDim.x) {
+    long nx, ny;
+    centroid_num(n, t, nx, ny);
+    base[t] = (island_band(nx, n) && island_band(ny, n)) ? v_in : v_out;
   }
 }
 
@@ -76,7 +108,7 @@ constexpr int GBM = 64, GBN = 128, GBK = 16;
 // C[b][t] = a0 + sum_j Y[b*ldy + j] Psi[j*nT + t]; 256 threads as 16 x 16, 4 x 8 outputs each.
 __global__ void __launch_bounds__(256) gemm_f64_kernel(const double* __restrict__ Y, int ldy, int B, int s,
                                                        const double* __restrict__ Psi, int nT, double a0,
-                                                       double* __restrict__ C) {
+                                                       double* __restrict__ C, const double* __restrict__ base) {
   __shared__ double As[GBK][GBM + 1];
   __shared__ double Bs[GBK][GBN];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -121,7 +153,7 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const double* __restrict_
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const int t = t0 + tx + 16 * j;
-      if (t < nT) C[(size_t)b * nT + t] = a0 + acc[i][j];
+      if (t < nT) C[(size_t)b * nT + t] = (base ? base[t] : a0) + acc[i][j];
     }
   }
 }
@@ -180,19 +212,25 @@ cudaError_t launch_lattice_points(const uint32_t* d_z, uint32_t N, const double*
 }
 
 cudaError_t launch_psi_table(int n, int s, const int* d_k1, const int* d_k2, const double* d_cj, double* d_psi,
-                             cudaStream_t st) {
+                             cudaStream_t st, const int* d_region) {
   const size_t tot = (size_t)s * 2 * n * n;
   if (tot == 0) return cudaSuccess;
-  psi_kernel<<<grid_for(tot, 256), 256, 0, st>>>(n, s, d_k1, d_k2, d_cj, d_psi);
+  psi_kernel<<<grid_for(tot, 256), 256, 0, st>>>(n, s, d_k1, d_k2, d_cj, d_region, d_psi);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_island_field(int n, double v_in, double v_out, double* d_base, cudaStream_t st) {
+  const size_t tot = (size_t)2 * n * n;
+  island_kernel<<<grid_for(tot, 256), 256, 0, st>>>(n, v_in, v_out, d_base);
   return cudaGetLastError();
 }
 
 cudaError_t launch_coef_gemm_f64(const double* d_Y, int ldy, int B, int s, const double* d_psi, int nT, double a0,
-                                 double* d_a, cudaStream_t st) {
+                                 double* d_a, cudaStream_t st, const double* d_base) {
   if (B == 0 || nT == 0) return cudaSuccess;
   dim3 grid((nT + GBN - 1) / GBN, (B + GBM - 1) / GBM);
   if (grid.y > 65535) return cudaErrorInvalidValue;
-  gemm_f64_kernel<<<grid, 256, 0, st>>>(d_Y, ldy, B, s, d_psi, nT, a0, d_a);
+  gemm_f64_kernel<<<grid, 256, 0, st>>>(d_Y, ldy, B, s, d_psi, nT, a0, d_a, d_base);
   return cudaGetLastError();
 }
 

@@ -11,6 +11,14 @@
 // Vectors live on the padded (n+1) x (n+1) node grid with a zero boundary ring.  Multigrid
 // coarse operators are the Galerkin operators P^T A P, i.e. the coarse P1 stiffness whose
 // triangle coefficients are the means of the four fine triangles they contain.
+//
+// With a reaction term b u (the second test problem of Sec. 5; b constant per triangle) the
+// operator gains the reaction matrix B = sum_T b_T M_T, a seven-point form over the six edges pq
+// at p:  (B x)_p = h^2/12 sum_{edges pq} r_pq (x_p + x_q),  r_pq = (b_T1 + b_T2) / 2 over the two
+// triangles of the edge (b = 1 gives the mass).  The multigrid preconditioner then approximates
+// (A + D_B)^{-1} with D_B the lumped reaction, (D_B)_pp = h^2/6 sum_{T at p} b_T (the row sums of
+// B), on every level from the coarsened b: symmetric positive definite and spectrally equivalent
+// to A + B.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -63,10 +71,12 @@ struct MGDesc {
   T* cell[2];     // ping-pong per-triangle coefficients while building
   T* cinv;        // symmetric inverse of the operator on the 3 x 3-unknown mesh 1/4 (exact coarse solve)
   int Lc;         // level solved exactly: mesh 1/4 when present, else mesh 1/2
+  T* dr[kMaxMG];  // lumped reaction diagonal D_B per level (NULL: no reaction term)
+  T* rcell[2];    // ping-pong per-triangle reaction coefficients while building
 };
 
 template <typename T>
-__host__ __device__ void carve_mg(Carver& c, int n, MGDesc<T>& d) {
+__host__ __device__ void carve_mg(Carver& c, int n, MGDesc<T>& d, bool reaction = false) {
   d.L = ilog2(n);
   for (int l = 0; l < d.L; ++l) {
     const int nl = n >> l;
@@ -78,10 +88,13 @@ __host__ __device__ void carve_mg(Carver& c, int n, MGDesc<T>& d) {
     d.t[l] = c.take<T>(V);
     d.x[l] = l ? c.take<T>(V) : nullptr;
     d.b[l] = l ? c.take<T>(V) : nullptr;
+    d.dr[l] = reaction ? c.take<T>(V) : nullptr;
   }
   const size_t cells = n >= 4 ? (size_t)2 * (n / 2) * (n / 2) : 1;
   d.cell[0] = c.take<T>(cells);
   d.cell[1] = c.take<T>(cells);
+  d.rcell[0] = reaction ? c.take<T>(cells) : nullptr;
+  d.rcell[1] = reaction ? c.take<T>(cells) : nullptr;
   d.cinv = c.take<T>(81);
   d.Lc = d.L >= 2 ? d.L - 2 : d.L - 1;
 }
@@ -107,6 +120,8 @@ __host__ __device__ void carve_mg_split(Carver& w, Carver& v, int n, MGDesc<T>& 
   d.cell[1] = v.take<T>(cells);
   d.cinv = w.take<T>(81);
   d.Lc = d.L >= 2 ? d.L - 2 : d.L - 1;
+  for (int l = 0; l < kMaxMG; ++l) d.dr[l] = nullptr;
+  d.rcell[0] = d.rcell[1] = nullptr;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -238,6 +253,33 @@ __device__ __forceinline__ double stiff_cells(const double* __restrict__ a, int 
   return we * (xp - x[p + 1]) + ww * (xp - x[p - 1]) + wn * (xp - x[p + ld]) + ws * (xp - x[p - ld]);
 }
 
+// reaction seven-point sum without the h^2/12 factor, from the edge weights rx (edge to E), ry (to
+// N) and rd (to NE) of the padded nodes
+template <typename T, typename X>
+__device__ __forceinline__ T react7(const T* __restrict__ rx, const T* __restrict__ ry, const T* __restrict__ rd,
+                                    const X* x, int p, int ld) {
+  const T xp = (T)x[p];
+  return rx[p] * (xp + (T)x[p + 1]) + rx[p - 1] * (xp + (T)x[p - 1]) + ry[p] * (xp + (T)x[p + ld]) +
+         ry[p - ld] * (xp + (T)x[p - ld]) + rd[p] * (xp + (T)x[p + ld + 1]) + rd[p - ld - 1] * (xp + (T)x[p - ld - 1]);
+}
+
+// FP64 reaction sum (without h^2/12) at interior node (i, j) from the centroid values b of the
+// reaction coefficient (lower triangles first, then upper)
+__device__ __forceinline__ double react_cells(const double* __restrict__ b, int n, const double* x, int p, int ld,
+                                              int i, int j) {
+  const double* lo = b;
+  const double* up = b + (size_t)n * n;
+  const int c = j * n + i;
+  const double lij = lo[c], li1j = lo[c - 1], li1j1 = lo[c - n - 1];
+  const double uij = up[c], uij1 = up[c - n], ui1j1 = up[c - n - 1];
+  const double re = 0.5 * (lij + uij1), rw = 0.5 * (li1j + ui1j1);
+  const double rn = 0.5 * (uij + li1j), rs = 0.5 * (uij1 + li1j1);
+  const double rne = 0.5 * (lij + uij), rsw = 0.5 * (li1j1 + ui1j1);
+  const double xp = x[p];
+  return re * (xp + x[p + 1]) + rw * (xp + x[p - 1]) + rn * (xp + x[p + ld]) + rs * (xp + x[p - ld]) +
+         rne * (xp + x[p + ld + 1]) + rsw * (xp + x[p - ld - 1]);
+}
+
 // ---------------------------------------------------------------------------------------------
 // operator setup
 template <typename T, typename S>
@@ -250,6 +292,35 @@ __device__ void weights_from_cells(int n, const S* low, const S* up, T* wx, T* w
     if (i >= 1 && i <= n - 1 && j <= n - 1) b = T(0.5 * ((double)up[j * n + i] + (double)low[j * n + i - 1]));
     wx[q] = a;
     wy[q] = b;
+  });
+}
+
+// the reaction's edge weights: rx, ry as the stiffness weights of b (same two triangles per edge),
+// rd of the hypotenuse (i,j)-(i+1,j+1) = (b_low(i,j) + b_up(i,j)) / 2
+template <typename T, typename S>
+__device__ void reaction_weights(int n, const S* low, const S* up, T* rx, T* ry, T* rd) {
+  weights_from_cells<T, S>(n, low, up, rx, ry);
+  const int ld = n + 1;
+  for_all(gsz(n), [&](size_t q) {
+    const int i = (int)(q % ld), j = (int)(q / ld);
+    rd[q] = (i <= n - 1 && j <= n - 1) ? T(0.5 * ((double)low[j * n + i] + (double)up[j * n + i])) : T(0);
+  });
+}
+
+// lumped reaction diagonal h^2/6 sum_{T at p} b_T at the interior nodes, 0 on the ring
+template <typename T, typename S>
+__device__ void lumped_reaction(int n, const S* low, const S* up, T* dr) {
+  const int ld = n + 1;
+  const double f = 1.0 / (6.0 * (double)n * (double)n);
+  for_all(gsz(n), [&](size_t q) {
+    const int i = (int)(q % ld), j = (int)(q / ld);
+    T v = T(0);
+    if (i >= 1 && i <= n - 1 && j >= 1 && j <= n - 1) {
+      const int c = j * n + i;
+      v = T(f * ((double)low[c] + (double)up[c] + (double)low[c - 1] + (double)up[c - n] + (double)low[c - n - 1] +
+                 (double)up[c - n - 1]));
+    }
+    dr[q] = v;
   });
 }
 
@@ -271,12 +342,14 @@ __device__ void coarsen_cells(int n, const S* low, const S* up, T* out) {
 // 1 / diag(A) at the interior nodes and 0 on the boundary ring (the fused smoothing phase of the
 // V-cycle reads it at the neighbours of every interior node)
 template <typename T>
-__device__ void inverse_diagonal(int n, const T* wx, const T* wy, T* dinv) {
+__device__ void inverse_diagonal(int n, const T* wx, const T* wy, T* dinv, const T* dr = nullptr) {
   const int ld = n + 1;
   for_all(gsz(n), [&](size_t q) {
     const int i = (int)(q % ld), j = (int)(q / ld);
     const int p = (int)q;
-    dinv[q] = (i >= 1 && i <= n - 1 && j >= 1 && j <= n - 1) ? T(1) / (wx[p] + wx[p - 1] + wy[p] + wy[p - ld]) : T(0);
+    dinv[q] = (i >= 1 && i <= n - 1 && j >= 1 && j <= n - 1)
+                  ? T(1) / (wx[p] + wx[p - 1] + wy[p] + wy[p - ld] + (dr ? dr[p] : T(0)))
+                  : T(0);
   });
 }
 
@@ -285,7 +358,7 @@ __device__ void inverse_diagonal(int n, const T* wx, const T* wy, T* dinv) {
 // in registers), written symmetrised.  The V-cycle only needs a symmetric positive definite
 // approximation of A^{-1} on this level; this one is exact to FP32 rounding.
 template <typename T>
-__device__ void coarse_inverse4(const T* wx, const T* wy, T* cinv) {
+__device__ void coarse_inverse4(const T* wx, const T* wy, T* cinv, const T* dr = nullptr) {
   constexpr int ld = 5;
   float L[9][9];
 #pragma unroll
@@ -295,7 +368,7 @@ __device__ void coarse_inverse4(const T* wx, const T* wy, T* cinv) {
 #pragma unroll
   for (int r = 0; r < 9; ++r) {
     const int i = r % 3 + 1, j = r / 3 + 1, p = j * ld + i;
-    L[r][r] = (float)(wx[p] + wx[p - 1] + wy[p] + wy[p - ld]);
+    L[r][r] = (float)(wx[p] + wx[p - 1] + wy[p] + wy[p - ld] + (dr ? dr[p] : T(0)));
     if (i > 1) L[r][r - 1] = -(float)wx[p - 1];
     if (j > 1) L[r][r - 3] = -(float)wy[p - ld];
   }
@@ -344,31 +417,46 @@ __device__ void coarse_inverse4(const T* wx, const T* wy, T* cinv) {
     for (int c = r + 1; c < 9; ++c) cinv[r * 9 + c] = cinv[c * 9 + r];
 }
 
-// Builds every level (weights, inverse diagonals) from the fine centroid coefficients a.
-// Returns true when every coefficient is positive (Assumption A1).
+// Builds every level (weights, inverse diagonals) from the fine centroid coefficients a, and with
+// rb (hierarchy carved with the reaction arrays) the lumped reaction of every level from the
+// centroid values rb of the reaction coefficient.  Returns true when every a is positive
+// (Assumption A1) and every b nonnegative.
 template <typename T, typename S = double>
-__device__ bool build_mg(MGDesc<T>& d, const S* __restrict__ a, int n, double* red) {
+__device__ bool build_mg(MGDesc<T>& d, const S* __restrict__ a, int n, double* red, const S* __restrict__ rb = nullptr) {
   int bad = 0;
+  const bool rx = rb != nullptr && d.dr[0] != nullptr;
   for_all((size_t)2 * n * n, [&](size_t q) { bad |= !(a[q] > S(0)); });
+  if (rx) for_all((size_t)2 * n * n, [&](size_t q) { bad |= !(rb[q] >= S(0)); });
   weights_from_cells<T, S>(n, a, a + (size_t)n * n, d.wx[0], d.wy[0]);
   if (d.L > 1) coarsen_cells<T, S>(n, a, a + (size_t)n * n, d.cell[0]);
+  if (rx) {
+    lumped_reaction<T, S>(n, rb, rb + (size_t)n * n, d.dr[0]);
+    if (d.L > 1) coarsen_cells<T, S>(n, rb, rb + (size_t)n * n, d.rcell[0]);
+  }
   __syncthreads();
   for (int l = 1; l < d.L; ++l) {
     const int nl = d.n[l];
     const T* src = d.cell[(l - 1) & 1];
     weights_from_cells<T, T>(nl, src, src + (size_t)nl * nl, d.wx[l], d.wy[l]);
     if (l + 1 < d.L) coarsen_cells<T, T>(nl, src, src + (size_t)nl * nl, d.cell[l & 1]);
-    inverse_diagonal<T>(d.n[l - 1], d.wx[l - 1], d.wy[l - 1], d.dinv[l - 1]);
+    if (rx) {
+      const T* rs = d.rcell[(l - 1) & 1];
+      lumped_reaction<T, T>(nl, rs, rs + (size_t)nl * nl, d.dr[l]);
+      if (l + 1 < d.L) coarsen_cells<T, T>(nl, rs, rs + (size_t)nl * nl, d.rcell[l & 1]);
+    }
+    inverse_diagonal<T>(d.n[l - 1], d.wx[l - 1], d.wy[l - 1], d.dinv[l - 1], rx ? d.dr[l - 1] : nullptr);
     __syncthreads();
   }
-  inverse_diagonal<T>(d.n[d.L - 1], d.wx[d.L - 1], d.wy[d.L - 1], d.dinv[d.L - 1]);
-  if (d.L >= 2 && threadIdx.x == 0) coarse_inverse4<T>(d.wx[d.L - 2], d.wy[d.L - 2], d.cinv);
+  inverse_diagonal<T>(d.n[d.L - 1], d.wx[d.L - 1], d.wy[d.L - 1], d.dinv[d.L - 1], rx ? d.dr[d.L - 1] : nullptr);
+  if (d.L >= 2 && threadIdx.x == 0)
+    coarse_inverse4<T>(d.wx[d.L - 2], d.wy[d.L - 2], d.cinv, rx ? d.dr[d.L - 2] : nullptr);
   double v[1] = {(double)bad}, o[1];
   block_sum<1, double>(v, o, red);
   return o[0] == 0.0;
 }
 
-// Symmetric V-cycle for A with nu (2 or 1) damped Jacobi steps before and after each coarse-grid
+// Symmetric V-cycle for A (A + D_B when the hierarchy holds a lumped reaction, which build_mg must
+// then have formed) with nu (2 or 1) damped Jacobi steps before and after each coarse-grid
 // correction, Galerkin coarse levels and an exact solve on mesh 1/4 (or 1/2): x0 = B^{-1} b0.
 // Phases per level: [two Jacobi steps from zero, fused] -> [residual restricted with P^T] going
 // down; [prolongation + correction + one Jacobi step, fused] -> [one Jacobi step] going up.
@@ -385,6 +473,7 @@ __device__ __noinline__ T vcycle(const MGDesc<T>& d, const T* b0, T* x0, T omega
     const T* __restrict__ wx = d.wx[l];
     const T* __restrict__ wy = d.wy[l];
     const T* __restrict__ di = d.dinv[l];
+    const T* __restrict__ dg = d.dr[l];  // lumped reaction (NULL: none)
     if (nu == 1) {
       // V(1,1): the one Jacobi step from zero is x1 = omega D^-1 b, pointwise; the restriction
       // forms it on the fly and nothing is stored
@@ -395,7 +484,7 @@ __device__ __noinline__ T vcycle(const MGDesc<T>& d, const T* b0, T* x0, T omega
         auto res = [&](int q) {
           const T xq = x1(q);
           return b[q] - (wx[q] * (xq - x1(q + 1)) + wx[q - 1] * (xq - x1(q - 1)) + wy[q] * (xq - x1(q + ld)) +
-                         wy[q - ld] * (xq - x1(q - ld)));
+                         wy[q - ld] * (xq - x1(q - ld)) + (dg ? dg[q] * xq : T(0)));
         };
         bc[P] = res(p) + T(0.5) * ((res(p + 1) + res(p - 1)) + (res(p + ld) + res(p - ld)) +
                                    (res(p + ld + 1) + res(p - ld - 1)));
@@ -407,7 +496,7 @@ __device__ __noinline__ T vcycle(const MGDesc<T>& d, const T* b0, T* x0, T omega
       auto x1 = [&](int q) { return omega * di[q] * b[q]; };
       const T xp = x1(p);
       const T ax = wx[p] * (xp - x1(p + 1)) + wx[p - 1] * (xp - x1(p - 1)) + wy[p] * (xp - x1(p + ld)) +
-                   wy[p - ld] * (xp - x1(p - ld));
+                   wy[p - ld] * (xp - x1(p - ld)) + (dg ? dg[p] * xp : T(0));
       xa[p] = xp + omega * di[p] * (b[p] - ax);
     });
     __syncthreads();
@@ -415,7 +504,7 @@ __device__ __noinline__ T vcycle(const MGDesc<T>& d, const T* b0, T* x0, T omega
     const T* cx = xa;
     for_interior(n >> 1, [&](int P, int I, int J) {
       const int p = (2 * J) * ld + 2 * I;
-      auto res = [&](int q) { return b[q] - stiff<T, T>(wx, wy, cx, q, ld); };
+      auto res = [&](int q) { return b[q] - (stiff<T, T>(wx, wy, cx, q, ld) + (dg ? dg[q] * cx[q] : T(0))); };
       bc[P] = res(p) + T(0.5) * ((res(p + 1) + res(p - 1)) + (res(p + ld) + res(p - ld)) +
                                  (res(p + ld + 1) + res(p - ld - 1)));
     });
@@ -447,6 +536,7 @@ __device__ __noinline__ T vcycle(const MGDesc<T>& d, const T* b0, T* x0, T omega
     const T* __restrict__ wx = d.wx[l];
     const T* __restrict__ wy = d.wy[l];
     const T* __restrict__ di = d.dinv[l];
+    const T* __restrict__ dg = d.dr[l];
     const T* xc = d.x[l + 1];
     const int ldc = (n >> 1) + 1;
     if (nu == 1) {
@@ -459,7 +549,8 @@ __device__ __noinline__ T vcycle(const MGDesc<T>& d, const T* b0, T* x0, T omega
         };
         const T tp = t(p, i, j);
         const T ax = wx[p] * (tp - t(p + 1, i + 1, j)) + wx[p - 1] * (tp - t(p - 1, i - 1, j)) +
-                     wy[p] * (tp - t(p + ld, i, j + 1)) + wy[p - ld] * (tp - t(p - ld, i, j - 1));
+                     wy[p] * (tp - t(p + ld, i, j + 1)) + wy[p - ld] * (tp - t(p - ld, i, j - 1)) +
+                     (dg ? dg[p] * tp : T(0));
         const T o = tp + omega * di[p] * (b[p] - ax);
         xa[p] = o;
         if (last) dot += dotv[p] * o;
@@ -476,13 +567,14 @@ __device__ __noinline__ T vcycle(const MGDesc<T>& d, const T* b0, T* x0, T omega
       };
       const T tp = t(p, i, j);
       const T ax = wx[p] * (tp - t(p + 1, i + 1, j)) + wx[p - 1] * (tp - t(p - 1, i - 1, j)) +
-                   wy[p] * (tp - t(p + ld, i, j + 1)) + wy[p - ld] * (tp - t(p - ld, i, j - 1));
+                   wy[p] * (tp - t(p + ld, i, j + 1)) + wy[p - ld] * (tp - t(p - ld, i, j - 1)) +
+                   (dg ? dg[p] * tp : T(0));
       tt[p] = tp + omega * di[p] * (b[p] - ax);
     });
     __syncthreads();
     const bool last = (l == 0) && dotv;
     for_interior(n, [&](int p, int, int) {
-      const T o = tt[p] + omega * di[p] * (b[p] - stiff<T, T>(wx, wy, tt, p, ld));
+      const T o = tt[p] + omega * di[p] * (b[p] - (stiff<T, T>(wx, wy, tt, p, ld) + (dg ? dg[p] * tt[p] : T(0))));
       xa[p] = o;
       if (last) dot += dotv[p] * o;
     });
@@ -503,6 +595,7 @@ __device__ void zero_mg(const MGDesc<T>& d) {
   for (int l = 0; l < d.L; ++l) {
     zero_vec(d.t[l], d.n[l]);
     zero_vec(d.dinv[l], d.n[l]);
+    if (d.dr[l]) zero_vec(d.dr[l], d.n[l]);
     if (l) {
       zero_vec(d.x[l], d.n[l]);
       zero_vec(d.b[l], d.n[l]);

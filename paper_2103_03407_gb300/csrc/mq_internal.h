@@ -42,6 +42,12 @@ struct SampleLaunch {
   int prev_given;          // lambda^{l-1} given in out[b][2] (no previous-level solve)
   int mode_f, mode_p;      // fine / previous-fine solve: 0 in the kernel (inner precision T),
                            // 1 in the kernel with an FP64 inner solve, 2 elsewhere (streaming)
+  int reaction;            // the operator has a reaction term b u (b_f, b_c, b_p hold b)
+  const double* b_f;       // [B][2 nf^2] centroid values of the reaction coefficient, like a_f
+  const double* b_c;
+  const double* b_p;
+  int qoi;                 // 0: columns 1-3 of out hold eigenvalues; 1: the functional G(u) of the
+                           // eigenfunction approximations (|integral of u| / ||u||_L2)
 };
 
 // Live timing of the streaming tier's operator sweep (k_minres_q, the largest kernel of the
@@ -78,6 +84,8 @@ struct StreamSolve {
   double omega;
   int nu;                  // Jacobi sweeps before and after each coarse-grid correction (1 or 2)
   KernelProbe* probe;      // NULL, or the live timing of the operator sweep
+  int qoi;                 // 1: lam_out receives G(u^h) = |integral of w| / ||w||_L2 instead of the
+                           // Rayleigh quotient
 };
 // Graph mode of the streaming solve: the refinement and MINRES loops become conditional WHILE nodes
 // of the CUDA graph being captured on the solve's stream (no host reads); their bodies are
@@ -97,10 +105,13 @@ cudaError_t launch_finalize(int B, double* d_out, int has_prev, cudaStream_t st)
 size_t tc_slices_bytes(int rows, int k);
 int tc_pad_rows(int rows);
 int tc_pad_k(int k);
-cudaError_t launch_psi_slices(const double* d_psi, int s_rows, int nT, void* d_out, cudaStream_t st);
+// slices of 2^pexp psi (|2^pexp psi| <= 1 required)
+cudaError_t launch_psi_slices(const double* d_psi, int s_rows, int nT, void* d_out, cudaStream_t st, int pexp = 0);
 cudaError_t launch_y_slices(const double* d_Y, int B, int ldy, int k, int kpad, void* d_out, cudaStream_t st);
+// pexp: the scale exponent the psi slices were built with
 cudaError_t launch_coef_tc(const void* d_yslices, int B, int kpad, const void* d_pslices, int nT, int kpad_psi,
-                           double a0, double* d_a, int* d_err, cudaStream_t st);
+                           double a0, double* d_a, int* d_err, cudaStream_t st, const double* d_base = nullptr,
+                           int pexp = 0);
 
 // Sample flags (stat[b][3])
 enum : int {
@@ -111,7 +122,7 @@ enum : int {
 };
 
 size_t sample_slab_bytes(int nf, int nc, int np, int mixed);
-size_t sample_slab_bytes(int nf, int nc, int np, int mixed, int mode_f, int mode_p);
+size_t sample_slab_bytes(int nf, int nc, int np, int mixed, int mode_f, int mode_p, int reaction = 0);
 cudaError_t launch_sample(const SampleLaunch& p, int mixed, int blocks, int threads, size_t smem,
                           cudaStream_t st);
 int sample_occupancy(int mixed, int threads, size_t smem);
@@ -130,10 +141,15 @@ cudaError_t measure_fp64_peak(int device, double* tflops, double* ms);
 cudaError_t launch_lattice_points(const uint32_t* d_z, uint32_t N, const double* d_delta, int R, int s,
                                   uint32_t k0, int npts, int mbits, double* d_Y, cudaStream_t st,
                                   const uint32_t* d_kshift = nullptr);
+// d_region: NULL (every term on all of D), or per term 1 (only on the islands D_f of the second test
+// problem of Sec. 5) or 2 (only off them)
 cudaError_t launch_psi_table(int n, int s, const int* d_k1, const int* d_k2, const double* d_cj,
-                             double* d_psi, cudaStream_t st);
+                             double* d_psi, cudaStream_t st, const int* d_region = nullptr);
+// base[t] = v_in on the triangles whose centroid lies in D_f, v_out elsewhere
+cudaError_t launch_island_field(int n, double v_in, double v_out, double* d_base, cudaStream_t st);
+// a[b][t] = a0 + sum_j Y[b][j] Psi[j][t], or base[t] + sum_j ... when d_base is not NULL
 cudaError_t launch_coef_gemm_f64(const double* d_Y, int ldy, int B, int s, const double* d_psi, int nT,
-                                 double a0, double* d_a, cudaStream_t st);
+                                 double a0, double* d_a, cudaStream_t st, const double* d_base = nullptr);
 cudaError_t launch_apply_operator(int n, int B, const double* d_a, int which, double sigma,
                                   const double* d_x, double* d_y, double* d_scratch, cudaStream_t st);
 // reuse scheme store: u0 [R][N0][V] padded level-0 eigenvectors, lam [R][N_l] per level.

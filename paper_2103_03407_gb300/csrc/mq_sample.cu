@@ -10,7 +10,13 @@
 //      (A_h - lambda_H M_h) w = b (eq. 2grid_source) by MINRES preconditioned with a symmetric
 //      multigrid V-cycle on A_h, inside FP64 iterative refinement, and returns the Rayleigh
 //      quotient w^T A_h w / w^T M_h w (Algorithm 1 steps 3-4, eq. RQ_update);
-//   3. writes lambda_H, lambda^l, lambda^{l-1} and the difference.
+//   3. writes lambda_H, lambda^l, lambda^{l-1} and the difference (or, for the functional
+//      quantity of interest, lambda_H and G of the two eigenfunction approximations and their
+//      difference, G(u) = |integral of u| / ||u||_L2).
+//
+// With a reaction term (the second test problem of Sec. 5) every operator above is A + B, B the
+// reaction matrix of b (seven-point form, see mq_device.cuh), and the V-cycles precondition with
+// A + D_B (the lumped reaction).
 //
 // Operators are matrix-free.  On the SW-NE triangulation with centroid coefficients the P1
 // stiffness is the weighted five-point edge form
@@ -46,6 +52,7 @@ using namespace dev;
 struct CoarseWS {
   MGDesc<float> mg;
   double *wx, *wy;
+  double *rx, *ry, *rd;  // reaction edge weights (NULL without a reaction term)
   double *x, *Ax, *Mx, *w, *Aw, *Mw, *p, *Ap, *Mp, *uprev;
   float *r32, *w32;
 };
@@ -53,12 +60,16 @@ struct CoarseWS {
 // uprev comes first: it holds the coarse eigenvector through the fine solves (and as the warm
 // start of the next point), while the rest of the coarse workspace is dead during the fine solves
 // and shares its memory with the fine workspace.  *persist receives the bytes of that head.
-__host__ __device__ void carve_coarse(Carver& c, int nc, CoarseWS& ws, size_t* persist = nullptr) {
+__host__ __device__ void carve_coarse(Carver& c, int nc, CoarseWS& ws, size_t* persist = nullptr,
+                                      bool reaction = false) {
   const size_t V = gsz(nc);
   ws.uprev = c.take<double>(V);
   if (persist) *persist = c.used();
   ws.wx = c.take<double>(V);
   ws.wy = c.take<double>(V);
+  ws.rx = reaction ? c.take<double>(V) : nullptr;
+  ws.ry = reaction ? c.take<double>(V) : nullptr;
+  ws.rd = reaction ? c.take<double>(V) : nullptr;
   ws.x = c.take<double>(V);
   ws.Ax = c.take<double>(V);
   ws.Mx = c.take<double>(V);
@@ -70,7 +81,7 @@ __host__ __device__ void carve_coarse(Carver& c, int nc, CoarseWS& ws, size_t* p
   ws.Mp = c.take<double>(V);
   ws.r32 = c.take<float>(V);
   ws.w32 = c.take<float>(V);
-  carve_mg<float>(c, nc, ws.mg);
+  carve_mg<float>(c, nc, ws.mg, reaction);
 }
 
 // Fine shifted-solve workspace: FP64 solution and right-hand side, inner vectors in T.
@@ -79,10 +90,11 @@ struct FineWS {
   MGDesc<T> mg;
   double *x64, *b64;
   T *vo, *v, *z, *zn, *wo, *w, *q, *xi;
+  T *rx, *ry, *rd;  // reaction edge weights in the inner precision (NULL without a reaction term)
 };
 
 template <typename T>
-__host__ __device__ void carve_fine(Carver& c, int n, FineWS<T>& ws) {
+__host__ __device__ void carve_fine(Carver& c, int n, FineWS<T>& ws, bool reaction = false) {
   const size_t V = gsz(n);
   ws.x64 = c.take<double>(V);
   ws.b64 = c.take<double>(V);
@@ -94,15 +106,18 @@ __host__ __device__ void carve_fine(Carver& c, int n, FineWS<T>& ws) {
   ws.w = c.take<T>(V);
   ws.q = c.take<T>(V);
   ws.xi = c.take<T>(V);
-  carve_mg<T>(c, n, ws.mg);
+  ws.rx = reaction ? c.take<T>(V) : nullptr;
+  ws.ry = reaction ? c.take<T>(V) : nullptr;
+  ws.rd = reaction ? c.take<T>(V) : nullptr;
+  carve_mg<T>(c, n, ws.mg, reaction);
 }
 
 template <typename T>
-__host__ __device__ size_t fine_bytes(int n) {
+__host__ __device__ size_t fine_bytes(int n, bool reaction = false) {
   if (n < 2) return 0;
   Carver f(nullptr);
   FineWS<T> fw;
-  carve_fine<T>(f, n, fw);
+  carve_fine<T>(f, n, fw, reaction);
   return (f.used() + 15) & ~(size_t)15;
 }
 
@@ -113,16 +128,16 @@ __host__ __device__ size_t fine_bytes(int n) {
 // exactly as sized here (an unaligned slab start would shift its arrays by up to 15 bytes into
 // the next slab).
 template <typename T>
-__host__ __device__ size_t slab_size(int nf, int nc, int np, int mode_f = 0, int mode_p = 0) {
+__host__ __device__ size_t slab_size(int nf, int nc, int np, int mode_f = 0, int mode_p = 0, bool reaction = false) {
   Carver c(nullptr);
   CoarseWS cw;
   size_t persist = 0;
-  carve_coarse(c, nc, cw, &persist);
+  carve_coarse(c, nc, cw, &persist, reaction);
   persist = (persist + 15) & ~(size_t)15;  // the fine region starts 16-byte aligned
   const size_t coarse = (c.used() + 15) & ~(size_t)15;
   auto need = [&](int n, int mode) -> size_t {
     if (mode == 2) return 0;
-    return mode == 1 ? fine_bytes<double>(n) : fine_bytes<T>(n);
+    return mode == 1 ? fine_bytes<double>(n, reaction) : fine_bytes<T>(n, reaction);
   };
   size_t m = coarse - persist;
   const size_t a = need(nf, mode_f), b = need(np, mode_p);
@@ -241,21 +256,29 @@ struct EigShared {
   int conv;
 };
 
-// LOBPCG for the smallest eigenpair of (A_H, M_H), preconditioned by one FP32 V-cycle on A_H.
-// x holds the start vector.  Returns the iterations used, or -1 when the tolerance was not
-// reached.  On return x is the M-normalised eigenvector with a positive sum and lam its
-// Rayleigh quotient.
+// LOBPCG for the smallest eigenpair of (A_H, M_H), preconditioned by one FP32 V-cycle on A_H
+// (A_H + B_H and A_H + D_B with a reaction term).  x holds the start vector.  Returns the
+// iterations used, or -1 when the tolerance was not reached.  On return x is the M-normalised
+// eigenvector with a positive sum, lam its Rayleigh quotient and g = |integral of x| (= G(x)).
 __device__ __noinline__ int lobpcg(CoarseWS& ws, int n, double tol, int maxit, int nu, float omega, double* red, EigShared* sh,
-                      double& lam) {
+                      double& lam, double& g) {
   const int ld = n + 1;
   const int nact = (n - 1) * n;  // threads for_interior gives work to
   const double hm = 1.0 / (12.0 * n * n);
   const double* __restrict__ wx = ws.wx;
   const double* __restrict__ wy = ws.wy;
+  const double* __restrict__ rx = ws.rx;
+  const double* __restrict__ ry = ws.ry;
+  const double* __restrict__ rd = ws.rd;
+  // the operator A (+ B): stiffness and, with a reaction term, the reaction's seven-point form
+  auto opA = [&](const double* u, int p) {
+    const double au = stiff<double, double>(wx, wy, u, p, ld);
+    return rx ? au + hm * react7<double, double>(rx, ry, rd, u, p, ld) : au;
+  };
   auto applyAM = [&](const double* u, double* Au, double* Mu, double& uAu, double& uMu) {
     double acc[2] = {0.0, 0.0}, o[2];
     for_interior(n, [&](int p, int, int) {
-      const double au = stiff<double, double>(wx, wy, u, p, ld);
+      const double au = opA(u, p);
       const double mu = hm * mass7(u, p, ld);
       Au[p] = au;
       Mu[p] = mu;
@@ -305,7 +328,7 @@ __device__ __noinline__ int lobpcg(CoarseWS& ws, int n, double tol, int maxit, i
       double acc[12];
       for (int i = 0; i < 12; ++i) acc[i] = 0.0;
       for_interior(n, [&](int p, int, int) {
-        const double aw = stiff<double, double>(wx, wy, ws.w, p, ld);
+        const double aw = opA(ws.w, p);
         const double mw = hm * mass7(ws.w, p, ld);
         ws.Aw[p] = aw;
         ws.Mw[p] = mw;
@@ -409,11 +432,15 @@ __device__ __noinline__ int lobpcg(CoarseWS& ws, int n, double tol, int maxit, i
   block_sum<1, double>(sacc, so, red, [&](const double* t) {
     sh->scale = (t[0] < 0 ? -1.0 : 1.0) / sqrt(xM);
     sh->theta = xA / xM;
+    // the integral of a P1 function with zero boundary values is h^2 times the sum of its nodal
+    // values (each interior hat function integrates to h^2)
+    sh->c[0] = fabs(t[0]) / ((double)n * n * sqrt(xM));
   }, nact);
   const double sc = sh->scale;
   for_interior(n, [&](int p, int, int) { ws.x[p] *= sc; });
   __syncthreads();
   lam = sh->theta;
+  g = sh->c[0];
   return conv ? it : -1;
 }
 
@@ -430,6 +457,7 @@ struct MinresShared {
   double rnorm, bnorm;
   double knorm, xnorm;  // ||A - sigma M|| bound and ||x|| for the FP64 residual floor
   double xax, xmx;      // x.Ax and x.Mx of the last FP64 residual pass (the Rayleigh quotient)
+  double xsum;          // sum of the nodal values of x in that pass (h^2 xsum = integral of x)
   int done, breakdown;
 };
 
@@ -444,17 +472,19 @@ __host__ __device__ inline double residual_target(double tol, double bnorm, doub
 
 // ---------------------------------------------------------------------------------------------
 // two-grid update on the fine mesh n: returns the Rayleigh quotient of the solution of
-// (A - sigma M) w = M P u_H.  iters / outer report the inner MINRES iterations and refinement
-// steps; flags receives kFlag* bits.
+// (A - sigma M) w = M P u_H (A + B - sigma M with the reaction coefficient rb), and in gq the
+// functional G(w) = |integral of w| / ||w||_L2.  iters / outer report the inner MINRES iterations
+// and refinement steps; flags receives kFlag* bits.
 template <typename T>
 __device__ __noinline__ double twogrid_fine(FineWS<T>& ws, char* fine_base, int n, const double* __restrict__ a,
-                               const double* uH, int nc, double sigma, const SampleLaunch& P, double* red,
-                               MinresShared<T>* ms, int& iters, int& outer, int& flags) {
+                               const double* __restrict__ rb, const double* uH, int nc, double sigma,
+                               const SampleLaunch& P, double* red, MinresShared<T>* ms, int& iters, int& outer,
+                               int& flags, double& gq) {
   const int ld = n + 1;
   __syncthreads();
   if (threadIdx.x == 0) {
     Carver f(fine_base);
-    carve_fine<T>(f, n, ws);
+    carve_fine<T>(f, n, ws, rb != nullptr);
   }
   __syncthreads();
   const double hm = 1.0 / (12.0 * n * n);
@@ -468,20 +498,39 @@ __device__ __noinline__ double twogrid_fine(FineWS<T>& ws, char* fine_base, int 
   zero_vec(ws.w, n);
   zero_vec(ws.q, n);
   zero_vec(ws.xi, n);
+  if (rb) {
+    zero_vec(ws.rx, n);
+    zero_vec(ws.ry, n);
+    zero_vec(ws.rd, n);
+  }
   zero_mg(ws.mg);
   __syncthreads();
-  if (!build_mg<T>(ws.mg, a, n, red)) flags |= kFlagBadCoef;
+  if (!build_mg<T>(ws.mg, a, n, red, rb)) flags |= kFlagBadCoef;
+  if (rb) reaction_weights<T, double>(n, rb, rb + (size_t)n * n, ws.rx, ws.ry, ws.rd);
   {
-    // ||A - sigma M||_inf <= 8 max a + sigma h^2 (row sums of the edge form and of the mass)
-    double amax = 0.0;
-    for_all((size_t)2 * n * n, [&](size_t q) { amax = fmax(amax, a[q]); });
-    for (int off = 16; off > 0; off >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, off));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = amax;
+    // ||A + B - sigma M||_inf <= 8 max a + (max b + sigma) h^2 (row sums of the edge form, of the
+    // reaction and of the mass)
+    double amax = 0.0, bmax = 0.0;
+    for_all((size_t)2 * n * n, [&](size_t q) {
+      amax = fmax(amax, a[q]);
+      if (rb) bmax = fmax(bmax, rb[q]);
+    });
+    for (int off = 16; off > 0; off >>= 1) {
+      amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+      bmax = fmax(bmax, __shfl_xor_sync(0xffffffffu, bmax, off));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      red[threadIdx.x >> 5] = amax;
+      red[32 + (threadIdx.x >> 5)] = bmax;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-      double m = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
-      ms->knorm = 8.0 * m + sigma / ((double)n * n);
+      double m = 0.0, mb = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        m = fmax(m, red[w]);
+        mb = fmax(mb, red[32 + w]);
+      }
+      ms->knorm = 8.0 * m + (mb + sigma) / ((double)n * n);
       ms->xnorm = 0.0;
       ms->xax = ms->xmx = 0.0;
     }
@@ -493,7 +542,11 @@ __device__ __noinline__ double twogrid_fine(FineWS<T>& ws, char* fine_base, int 
   const double* wx64 = (const double*)ws.mg.wx[0];
   const double* wy64 = (const double*)ws.mg.wy[0];
   auto K64 = [&](const double* x, int p, int i, int j) {
-    return w64 ? stiff<double, double>(wx64, wy64, x, p, ld) : stiff_cells(a, n, x, p, ld, i, j);
+    double k = w64 ? stiff<double, double>(wx64, wy64, x, p, ld) : stiff_cells(a, n, x, p, ld, i, j);
+    if (rb)
+      k += hm * (w64 ? react7<double, double>((const double*)ws.rx, (const double*)ws.ry, (const double*)ws.rd, x, p, ld)
+                     : react_cells(rb, n, x, p, ld, i, j));
+    return k;
   };
   // b = M P u_H  (P: P1 interpolation from the nested coarse mesh); x64 holds P u_H for a moment
   {
@@ -530,9 +583,13 @@ __device__ __noinline__ double twogrid_fine(FineWS<T>& ws, char* fine_base, int 
   outer = 0;
   iters = 0;
   const T sigm = T(sigma * hm);
+  const T hmt = T(hm);
   const T om = T(P.omega);
   const T* twx = ws.mg.wx[0];
   const T* twy = ws.mg.wy[0];
+  const T* trx = ws.rx;
+  const T* try_ = ws.ry;
+  const T* trd = ws.rd;
   for (; outer < P.max_outer; ++outer) {
     if (!(ms->rnorm > residual_target(P.tol_lin, ms->bnorm, ms->knorm, ms->xnorm, 16.0))) break;
     // inner: MINRES on (A - sigma M) xi = r / ||r|| in precision T, preconditioned by the V-cycle;
@@ -589,7 +646,9 @@ __device__ __noinline__ double twogrid_fine(FineWS<T>& ws, char* fine_base, int 
             wo[p] = wnew;
             ws.xi[p] += tcx * wnew;
           }
-          const T kz = (stiff<T, T>(twx, twy, z, p, ld) - sigm * mass7(z, p, ld)) * ig;
+          T kz = stiff<T, T>(twx, twy, z, p, ld) - sigm * mass7(z, p, ld);
+          if (trx) kz += hmt * react7<T, T>(trx, try_, trd, z, p, ld);
+          kz *= ig;
           ws.q[p] = kz;
           acc1[0] += kz * z[p];
         });
@@ -670,8 +729,9 @@ __device__ __noinline__ double twogrid_fine(FineWS<T>& ws, char* fine_base, int 
     const double rn = ms->rnorm;
     for_interior(n, [&](int p, int, int) { ws.x64[p] += rn * (double)ws.xi[p]; });
     __syncthreads();
-    // the same pass forms x.Ax and x.Mx: the last one gives the Rayleigh quotient of the result
-    double acc2[4] = {0.0, 0.0, 0.0, 0.0}, o2[4];
+    // the same pass forms x.Ax, x.Mx and sum(x): the last one gives the Rayleigh quotient and the
+    // functional of the result
+    double acc2[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, o2[5];
     for_interior(n, [&](int p, int i, int j) {
       const double xv = ws.x64[p];
       const double ax = K64(ws.x64, p, i, j);
@@ -682,14 +742,16 @@ __device__ __noinline__ double twogrid_fine(FineWS<T>& ws, char* fine_base, int 
       acc2[1] += xv * xv;
       acc2[2] += xv * ax;
       acc2[3] += xv * mx;
+      acc2[4] += xv;
     });
     int stalled = 0;
     const int first = outer == 0;
-    block_sum<4, double>(acc2, o2, red, [&](const double* t) {
+    block_sum<5, double>(acc2, o2, red, [&](const double* t) {
       const double rnew = sqrt(t[0]);
       ms->xnorm = sqrt(t[1]);
       ms->xax = t[2];
       ms->xmx = t[3];
+      ms->xsum = t[4];
       // no progress: stop refining (not after the first step, whose FP32 rounding noise can
       // leave a residual above ||b|| on fine meshes)
       ms->done = !first && !(rnew < 0.5 * ms->rnorm);
@@ -705,7 +767,8 @@ __device__ __noinline__ double twogrid_fine(FineWS<T>& ws, char* fine_base, int 
   // flagged only well above the target (or the FP64 floor): the refinement may stop a little short
   if (!(ms->rnorm <= residual_target(fmax(1e-5, 10.0 * P.tol_lin), ms->bnorm, ms->knorm, ms->xnorm, 256.0)))
     flags |= kFlagLinNoConv;
-  // Rayleigh quotient in FP64, from the residual pass over the final iterate
+  // Rayleigh quotient and functional in FP64, from the residual pass over the final iterate
+  gq = fabs(ms->xsum) / ((double)n * n * sqrt(ms->xmx));
   return ms->xax / ms->xmx;
 }
 
@@ -721,10 +784,11 @@ __global__ void __launch_bounds__(512) sample_kernel(SampleLaunch P) {
   __shared__ FineWS<double> fws64;
   char* base = P.use_smem ? smem_dyn : P.gscratch + (size_t)blockIdx.x * P.slab_bytes;
   size_t persist_bytes;
+  const bool rxn = P.reaction != 0;
   {
     Carver c(base);
     CoarseWS tmp;
-    carve_coarse(c, P.nc, tmp, &persist_bytes);
+    carve_coarse(c, P.nc, tmp, &persist_bytes, rxn);
     if (threadIdx.x == 0) cws = tmp;
   }
   char* fine_base = base + ((persist_bytes + 15) & ~(size_t)15);  // the fine workspace overlays the coarse one
@@ -747,25 +811,43 @@ __global__ void __launch_bounds__(512) sample_kernel(SampleLaunch P) {
       // ---- coarse eigenpair (Algorithm 1 step 1; Algorithm 2 steps 6-7), or, in the reuse scheme
       // across levels, the level-0 eigenpair of this point given in u_in / out[b][0]
       CoarseWS& cw = cws;
-      double lamH;
+      double lamH, gH = 0.0;
       int eit = 0;
       if (P.u_in) {
         const size_t Vc = gsz(nc);
         for_all(Vc, [&](size_t q) { cw.uprev[q] = P.u_in[b * Vc + q]; });
         lamH = P.out[b * 4 + 0];
         __syncthreads();
+        if (P.qoi && (P.direct_f || (P.np > 0 && P.direct_p && !P.prev_given))) {
+          // G(u_H) of the given (M-normalised) eigenvector: h^2 |sum u| / sqrt(u^T M u)
+          const double hmc = 1.0 / (12.0 * nc * nc);
+          double acc[2] = {0.0, 0.0}, o[2];
+          for_interior(nc, [&](int p, int, int) {
+            acc[0] += cw.uprev[p];
+            acc[1] += cw.uprev[p] * hmc * mass7(cw.uprev, p, nc + 1);
+          });
+          block_sum<2, double>(acc, o, red);
+          gH = fabs(o[0]) / ((double)nc * nc * sqrt(o[1]));
+        }
       } else {
         // the fine solves of the previous point reused this memory: clear the coarse vectors
         // (rings must be zero; interiors are written before use)
         double* vs[11] = {cw.wx, cw.wy, cw.x, cw.Ax, cw.Mx, cw.w, cw.Aw, cw.Mw, cw.p, cw.Ap, cw.Mp};
         for (int i = 0; i < 11; ++i) zero_vec(vs[i], nc);
+        if (rxn) {
+          zero_vec(cw.rx, nc);
+          zero_vec(cw.ry, nc);
+          zero_vec(cw.rd, nc);
+        }
         zero_vec(cw.r32, nc);
         zero_vec(cw.w32, nc);
         zero_mg(cw.mg);
         __syncthreads();
         const double* ac = P.a_c + b * ncT;
-        if (!build_mg<float>(cw.mg, ac, nc, red)) flags |= kFlagBadCoef;
+        const double* bc = rxn ? P.b_c + b * ncT : nullptr;
+        if (!build_mg<float>(cw.mg, ac, nc, red, bc)) flags |= kFlagBadCoef;
         weights_from_cells<double, double>(nc, ac, ac + (size_t)nc * nc, cw.wx, cw.wy);
+        if (rxn) reaction_weights<double, double>(nc, bc, bc + (size_t)nc * nc, cw.rx, cw.ry, cw.rd);
         if (kk == k0) {
           const float inc = 1.0f / (float)nc;
           for_interior(nc, [&](int p, int i, int j) { cw.x[p] = (double)(sinpif(i * inc) * sinpif(j * inc)); });
@@ -773,7 +855,7 @@ __global__ void __launch_bounds__(512) sample_kernel(SampleLaunch P) {
           for_interior(nc, [&](int p, int, int) { cw.x[p] = cw.uprev[p]; });
         }
         __syncthreads();
-        eit = lobpcg(cw, nc, P.tol_eig, P.max_eig_it, P.nu, omega, red, &esh, lamH);
+        eit = lobpcg(cw, nc, P.tol_eig, P.max_eig_it, P.nu, omega, red, &esh, lamH, gH);
         if (eit < 0) flags |= kFlagEigNoConv;
         for_interior(nc, [&](int p, int, int) { cw.uprev[p] = cw.x[p]; });
         if (P.u_out) {
@@ -789,23 +871,33 @@ __global__ void __launch_bounds__(512) sample_kernel(SampleLaunch P) {
       }
       // ---- fine two-grid updates (Algorithm 1 steps 2-4; Algorithm 2 steps 9-14); a solve of
       // mode 2 runs elsewhere and leaves the coarse eigenvalue as a placeholder
-      double lf = lamH, lp = P.np > 0 ? lamH : 0.0;
+      // the quantity of interest of a level whose eigenpair is the coarse one: lambda_H or G(u_H)
+      // (the reuse scheme gives coarse pairs only to levels that solve their own fine problems)
+      const double qH = P.qoi ? gH : lamH;
+      double lf = qH, lp = P.np > 0 ? qH : 0.0;
+      double gf = 0.0, gp = 0.0;
       int itf = 0, itp = 0, of = 0, op = 0;
+      const double* rbf = rxn ? P.b_f + b * nfT : nullptr;
+      const double* rbp = rxn ? P.b_p + b * npT : nullptr;
       if (!P.direct_f) {
         if (P.mode_f == 0)
-          lf = twogrid_fine<T>(fws, fine_base, P.nf, P.a_f + b * nfT, cw.uprev, nc, lamH, P, red, &msh, itf, of, flags);
+          lf = twogrid_fine<T>(fws, fine_base, P.nf, P.a_f + b * nfT, rbf, cw.uprev, nc, lamH, P, red, &msh, itf, of,
+                               flags, gf);
         else if (P.mode_f == 1)
-          lf = twogrid_fine<double>(fws64, fine_base, P.nf, P.a_f + b * nfT, cw.uprev, nc, lamH, P, red, &msh64, itf, of,
-                                    flags);
+          lf = twogrid_fine<double>(fws64, fine_base, P.nf, P.a_f + b * nfT, rbf, cw.uprev, nc, lamH, P, red, &msh64,
+                                    itf, of, flags, gf);
+        if (P.qoi && P.mode_f != 2) lf = gf;
       }
       if (P.prev_given) {
         lp = P.out[b * 4 + 2];  // every thread reads it before thread 0 rewrites the same value below
       } else if (P.np > 0 && !P.direct_p) {
         if (P.mode_p == 0)
-          lp = twogrid_fine<T>(fws, fine_base, P.np, P.a_p + b * npT, cw.uprev, nc, lamH, P, red, &msh, itp, op, flags);
+          lp = twogrid_fine<T>(fws, fine_base, P.np, P.a_p + b * npT, rbp, cw.uprev, nc, lamH, P, red, &msh, itp, op,
+                               flags, gp);
         else if (P.mode_p == 1)
-          lp = twogrid_fine<double>(fws64, fine_base, P.np, P.a_p + b * npT, cw.uprev, nc, lamH, P, red, &msh64, itp, op,
-                                    flags);
+          lp = twogrid_fine<double>(fws64, fine_base, P.np, P.a_p + b * npT, rbp, cw.uprev, nc, lamH, P, red, &msh64,
+                                    itp, op, flags, gp);
+        if (P.qoi && P.mode_p != 2) lp = gp;
       }
       if (threadIdx.x == 0) {
         P.out[b * 4 + 0] = lamH;
@@ -824,18 +916,23 @@ __global__ void __launch_bounds__(512) sample_kernel(SampleLaunch P) {
 }
 
 // Operator application for parity checks of the stencils: one CTA per coefficient field; the
-// scratch holds three padded grids per field.  Uses the same weight builder and stencils as the
-// solver.
+// scratch holds four padded grids per field.  Uses the same weight builders and stencils as the
+// solver.  which: 0 stiffness, 1 mass, 2 stiffness - sigma mass; 3 the reaction matrix of the
+// field (edge-weight form), 4 the same from the centroid values (the FP64 residual's form).
 __global__ void apply_kernel(int n, const double* __restrict__ a, int which, double sigma,
                              const double* __restrict__ x, double* __restrict__ y, double* scratch) {
   const size_t V = gsz(n);
   const size_t b = blockIdx.x;
-  double* wx = scratch + b * 3 * V;
+  double* wx = scratch + b * 4 * V;
   double* wy = wx + V;
   double* xp = wy + V;
+  double* wd = xp + V;
   const size_t nT = (size_t)2 * n * n, nI = (size_t)(n - 1) * (n - 1);
   const double* ab = a + b * nT;
-  weights_from_cells<double, double>(n, ab, ab + (size_t)n * n, wx, wy);
+  if (which == 3)
+    reaction_weights<double, double>(n, ab, ab + (size_t)n * n, wx, wy, wd);
+  else
+    weights_from_cells<double, double>(n, ab, ab + (size_t)n * n, wx, wy);
   for_all(V, [&](size_t q) { xp[q] = 0.0; });
   __syncthreads();
   for_interior(n, [&](int p, int i, int j) { xp[p] = x[b * nI + (size_t)(j - 1) * (n - 1) + (i - 1)]; });
@@ -843,9 +940,17 @@ __global__ void apply_kernel(int n, const double* __restrict__ a, int which, dou
   const int ld = n + 1;
   const double hm = 1.0 / (12.0 * n * n);
   for_interior(n, [&](int p, int i, int j) {
-    const double ax = stiff<double, double>(wx, wy, xp, p, ld);
-    const double mx = hm * mass7(xp, p, ld);
-    y[b * nI + (size_t)(j - 1) * (n - 1) + (i - 1)] = which == 0 ? ax : which == 1 ? mx : ax - sigma * mx;
+    double v;
+    if (which == 3) {
+      v = hm * react7<double, double>(wx, wy, wd, xp, p, ld);
+    } else if (which == 4) {
+      v = hm * react_cells(ab, n, xp, p, ld, i, j);
+    } else {
+      const double ax = stiff<double, double>(wx, wy, xp, p, ld);
+      const double mx = hm * mass7(xp, p, ld);
+      v = which == 0 ? ax : which == 1 ? mx : ax - sigma * mx;
+    }
+    y[b * nI + (size_t)(j - 1) * (n - 1) + (i - 1)] = v;
   });
 }
 
@@ -934,8 +1039,9 @@ size_t sample_slab_bytes(int nf, int nc, int np, int mixed) {
   return mixed ? slab_size<float>(nf, nc, np) : slab_size<double>(nf, nc, np);
 }
 
-size_t sample_slab_bytes(int nf, int nc, int np, int mixed, int mode_f, int mode_p) {
-  return mixed ? slab_size<float>(nf, nc, np, mode_f, mode_p) : slab_size<double>(nf, nc, np, mode_f, mode_p);
+size_t sample_slab_bytes(int nf, int nc, int np, int mixed, int mode_f, int mode_p, int reaction) {
+  return mixed ? slab_size<float>(nf, nc, np, mode_f, mode_p, reaction != 0)
+               : slab_size<double>(nf, nc, np, mode_f, mode_p, reaction != 0);
 }
 
 int sample_occupancy(int mixed, int threads, size_t smem) {

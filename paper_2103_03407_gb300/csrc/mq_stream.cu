@@ -97,6 +97,7 @@ struct SS {  // per-sample solver scalars
   double rnorm, bnorm, lam_h;
   double xnorm;   // ||x64||
   double xax, xmx;  // x.Ax and x.Mx of the last FP64 residual pass (the Rayleigh quotient)
+  double xsum;      // sum of the nodal values of x64 in that pass (h^2 xsum = integral of x)
   float amax;     // largest centroid coefficient (for the bound ||A - sigma M|| <= 8 amax + sigma h^2)
   int act_outer;  // refinement still running
   int act;        // inner MINRES running
@@ -969,7 +970,8 @@ __global__ void k_outer_update(int n, int B, const SS<T>* __restrict__ ss, const
 }
 
 // FP64 residual r = b - (A - sigma M) x64 (FP64 edge weights); v = T(r).
-// Partials r.r, x.x, x.Ax, x.Mx: the last pass of a sample gives its Rayleigh quotient.
+// Partials r.r, x.x, x.Ax, x.Mx, sum x: the last pass of a sample gives its Rayleigh quotient and
+// its functional.
 template <typename T>
 __global__ void k_residual(int n, int B, const int* __restrict__ ran, const double* __restrict__ wx64,
                            const double* __restrict__ wy64,
@@ -985,7 +987,7 @@ __global__ void k_residual(int n, int B, const int* __restrict__ ran, const doub
   const double* __restrict__ WX = wx64 + off;
   const double* __restrict__ WY = wy64 + off;
   const double* __restrict__ X = x64 + off;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   for_tile(n, ch, [&](int p, int, int) {
     const double xv = X[p];
     const double ax = stiff<double, double>(WX, WY, X, p, ld);
@@ -996,26 +998,29 @@ __global__ void k_residual(int n, int B, const int* __restrict__ ran, const doub
     acc[1] += xv * xv;
     acc[2] += xv * ax;
     acc[3] += xv * mx;
+    acc[4] += xv;
   });
-  tile_partials<4, double>(acc, part, (size_t)b * nt + ch);
+  tile_partials<5, double>(acc, part, (size_t)b * nt + ch);
 }
 
 template <typename T>
 __global__ void k_sc_outer_end(int B, int nch, const double* part, const int* ran, SS<T>* ss) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B || !ran[b]) return;
-  double s = 0.0, sx = 0.0, sa = 0.0, sm = 0.0;
+  double s = 0.0, sx = 0.0, sa = 0.0, sm = 0.0, su = 0.0;
   for (int k = 0; k < nch; ++k) {
-    const double* pk = part + ((size_t)b * nch + k) * 4;
+    const double* pk = part + ((size_t)b * nch + k) * 5;
     s += pk[0];
     sx += pk[1];
     sa += pk[2];
     sm += pk[3];
+    su += pk[4];
   }
   SS<T>& S = ss[b];
   S.xnorm = sqrt(sx);
   S.xax = sa;
   S.xmx = sm;
+  S.xsum = su;
   const double rnew = sqrt(s);
   // No progress: stop refining.  Not on the first step: on fine meshes the FP32 rounding of the
   // first inner solution alone leaves an FP64 residual above ||b|| (the operator amplifies its
@@ -1026,15 +1031,16 @@ __global__ void k_sc_outer_end(int B, int nch, const double* part, const int* ra
   S.outer += 1;
 }
 
+// the Rayleigh quotient x.Ax / x.Mx, or with qoi the functional G(x) = h^2 |sum x| / sqrt(x.Mx)
 template <typename T>
 __global__ void k_sc_rq(int B, int n, const double* sigma, int sig_stride, const SS<T>* ss, double tol_lin,
                         double* lam_out,
                         int lam_stride, int* it_out, int it_stride, int* outer_out, int outer_stride, int* flags,
-                        int flag_stride) {
+                        int flag_stride, int qoi) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
   const SS<T>& S = ss[b];
-  lam_out[(size_t)b * lam_stride] = S.xax / S.xmx;
+  lam_out[(size_t)b * lam_stride] = qoi ? fabs(S.xsum) / ((double)n * n * sqrt(S.xmx)) : S.xax / S.xmx;
   it_out[(size_t)b * it_stride] = S.iters;
   outer_out[(size_t)b * outer_stride] = S.outer;
   int f = S.flags;
@@ -1167,7 +1173,7 @@ size_t carve_arena(void* base, int n, int B, Arena<T>& A) {
   A.subw = c.take<char>(Bz * A.subw_bytes + 256);
   A.subw = (char*)(((uintptr_t)A.subw + 255) & ~(uintptr_t)255);
   const int nch = tiles_interior(n) > 1 ? tiles_interior(n) : 1;
-  A.part = c.take<double>(Bz * nch * 4 + Bz);
+  A.part = c.take<double>(Bz * nch * 5 + Bz);
   A.ss = c.take<SS<T>>(Bz);
   A.act = c.take<int>(Bz);
   A.ran = c.take<int>(Bz);
@@ -1510,7 +1516,7 @@ cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st, c
   }
   // ---- Rayleigh quotient (from each sample's last residual pass)
   ++tl_launches, k_sc_rq<T><<<gs, 256, 0, st>>>(B, n, s.lamH, s.lam_stride, A.ss, s.tol_lin, s.lam_out, s.lam_out_stride, s.iters_out,
-                                 s.iters_stride, s.outer_out, s.outer_stride, s.flags, s.flags_stride);
+                                 s.iters_stride, s.outer_out, s.outer_stride, s.flags, s.flags_stride, s.qoi);
   LAUNCH_CHECK();
   return cudaSuccess;
 }

@@ -5,6 +5,8 @@
 // into exact BF16 integer slices (an Ozaki-type splitting):
 //   y   in [-1/2, 1/2):  y   = sum_{p<7} Y_p 2^{-8(p+1)}  + r,  |r| <= 2^-57,  Y_p integers in [-128, 128]
 //   psi in [-1, 1]:      psi = sum_{q<7} P_q 2^{-7-8q}    + r,  |r| <= 2^-64,  P_q integers in [-128, 128]
+// (a table is scaled by 2^e first, e chosen from its largest term factor so that |2^e psi| <= 1
+// with the most bits kept; the result is scaled back by the exact factor 2^-e)
 // Integers of magnitude <= 256 are exact in BF16, products of two are exact in the FP32
 // accumulator, and every accumulated sum stays an integer below 2^24 (K is processed in chunks of
 // at most 128 and the products are grouped by g = p + q, at most 7 per group: 7 * 128 * 2^14 <
@@ -31,6 +33,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 #include <mutex>
 
@@ -173,11 +176,13 @@ struct alignas(1024) TcSmem {
   int err;
 };
 
-// a[b][t] = a0 + sum_j y[b][j] psi[j][t], b < B, t < nT.  Tiles: tm = tile mod ntm (128 samples),
-// tn = tile div ntm (64 triangles); CTA c takes tiles c, c + grid, ...  Kpad: K of the Y slices.
+// a[b][t] = a0 + sum_j y[b][j] psi[j][t], b < B, t < nT (with base: base[t] in place of a0).
+// Tiles: tm = tile mod ntm (128 samples), tn = tile div ntm (64 triangles); CTA c takes tiles c,
+// c + grid, ...  Kpad: K of the Y slices.
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_coef_tc(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmP, int B, int nT, int Kpad,
-              int ntm, int ntiles, double a0, double* __restrict__ out, int* __restrict__ err_flag) {
+              int ntm, int ntiles, double a0, double* __restrict__ out, int* __restrict__ err_flag,
+              const double* __restrict__ base, int pexp) {
   extern __shared__ __align__(1024) char dyn[];
   TcSmem& S = *reinterpret_cast<TcSmem*>(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -228,6 +233,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   for (int ti = 0; ti < my_tiles && ok; ++ti) {
     const int tile = (int)blockIdx.x + ti * (int)gridDim.x;
     const int tm = tile % ntm, tn = tile / ntm;
+    // 2^-39 and 2^-63 of the fold, times the table's exact scale 2^-pexp
+    const double chi = ldexp(1.0, -39 - pexp), clo = ldexp(1.0, -63 - pexp);
     double acc[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) acc[i] = 0.0;
@@ -314,7 +321,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           }
           // value of the chunk = (hi 2^24 + lo) 2^{-15-48}; hi < 2^56 and lo < 2^40 in magnitude
 #pragma unroll
-          for (int i = 0; i < 16; ++i) acc[sh * 16 + i] += fma((double)hi[i], 0x1p-39, (double)lo[i] * 0x1p-63);
+          for (int i = 0; i < 16; ++i) acc[sh * 16 + i] += fma((double)hi[i], chi, (double)lo[i] * clo);
         }
       }
       tc_fence_before();
@@ -326,7 +333,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         double* o = out + (size_t)b * nT;
         const int t0 = tn * kTN + half * 32;
         // nT = 2 n^2 and t0 are even: pairs are 16-byte aligned whenever the output base is
-        if (((uintptr_t)out & 15) == 0) {
+        if (base) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i)
+            if (t0 + i < nT) o[t0 + i] = base[t0 + i] + acc[i];
+        } else if (((uintptr_t)out & 15) == 0) {
 #pragma unroll
           for (int i = 0; i < 32; i += 2)
             if (t0 + i < nT) *reinterpret_cast<double2*>(o + t0 + i) = make_double2(a0 + acc[i], a0 + acc[i + 1]);
@@ -399,11 +410,11 @@ size_t tc_slices_bytes(int rows, int k) {
 int tc_pad_rows(int rows) { return (rows + 127) / 128 * 128; }
 int tc_pad_k(int k) { return (k + 15) / 16 * 16; }
 
-cudaError_t launch_psi_slices(const double* d_psi, int s_rows, int nT, void* d_out, cudaStream_t st) {
-  // psi is [s_rows][nT] (row = term j): the slices are [7][K_pad/8][nT_pad][8]
+cudaError_t launch_psi_slices(const double* d_psi, int s_rows, int nT, void* d_out, cudaStream_t st, int pexp) {
+  // psi is [s_rows][nT] (row = term j): the slices are [7][K_pad/8][nT_pad][8] of 2^pexp psi
   const int rp = tc_pad_rows(nT), kp = tc_pad_k(s_rows);
-  k_slice_rows<<<grid1((size_t)rp * kp), 256, 0, st>>>(d_psi, nT, s_rows, 1, (size_t)nT, 128.0, rp, kp,
-                                                      (__nv_bfloat16*)d_out);
+  k_slice_rows<<<grid1((size_t)rp * kp), 256, 0, st>>>(d_psi, nT, s_rows, 1, (size_t)nT, std::ldexp(128.0, pexp), rp,
+                                                      kp, (__nv_bfloat16*)d_out);
   return cudaGetLastError();
 }
 
@@ -417,7 +428,7 @@ cudaError_t launch_y_slices(const double* d_Y, int B, int ldy, int k, int kpad, 
 // a[B][nT] = a0 + Y psi from slices: y slices [7][kpad/8][Bpad][8] built for K = kpad columns, psi
 // slices [7][kpad_psi/8][nTpad][8] (only the first kpad columns are read)
 cudaError_t launch_coef_tc(const void* d_yslices, int B, int kpad, const void* d_pslices, int nT, int kpad_psi,
-                           double a0, double* d_a, int* d_err, cudaStream_t st) {
+                           double a0, double* d_a, int* d_err, cudaStream_t st, const double* d_base, int pexp) {
   if (B == 0 || nT == 0) return cudaSuccess;
   if (kpad > kpad_psi || kpad % kTK || kpad <= 0) return cudaErrorInvalidValue;
   const int Bp = tc_pad_rows(B), nTp = tc_pad_rows(nT);
@@ -437,7 +448,7 @@ cudaError_t launch_coef_tc(const void* d_yslices, int B, int kpad, const void* d
   const long ntiles = (long)ntm * (nTp / kTN);
   if (ntiles > 0x7fffffffL) return cudaErrorInvalidValue;
   const int grid = (int)(ntiles < sms ? ntiles : sms);
-  k_coef_tc<<<grid, kTcThreads, smem, st>>>(tmY, tmP, B, nT, kpad, ntm, (int)ntiles, a0, d_a, d_err);
+  k_coef_tc<<<grid, kTcThreads, smem, st>>>(tmY, tmP, B, nT, kpad, ntm, (int)ntiles, a0, d_a, d_err, d_base, pexp);
   return cudaGetLastError();
 }
 

@@ -43,7 +43,10 @@ def main():
     build.build()
     wl = WORKLOADS[a.workload]
     ctx = binding.Context(0)
-    ctx.mq_set_coefficient(wl.a0, max(lv.s for lv in wl.levels), wl.family, wl.decay)
+    if wl.family == 2:
+        ctx.mq_set_islands(max(lv.s for lv in wl.levels), *wl.decays)
+    else:
+        ctx.mq_set_coefficient(wl.a0, max(lv.s for lv in wl.levels), wl.family, wl.decay)
     ctx.mq_set_levels(wl.levels)
     ds = shifts(wl.seed, wl.levels)
     for l, lv in enumerate(wl.levels):

@@ -42,13 +42,19 @@ class Workload:
     tol: float  # relative tolerance on each per-sample eigenvalue versus the oracle
     a0: float = 1.0
     decay: float = 2.0
-    family: int = 0  # 0: the workload sine family; 1: the paper's first test problem (Sec. 5)
+    family: int = 0  # 0: the workload sine family; 1, 2: the paper's first and second test problems (Sec. 5)
     notes: str = ""
     extra: dict = field(default_factory=dict)
+    decays: tuple = ()  # family 2: the term decays (p_a, p_a', p_b, p_b'); `decay` then weights the lattice
 
     @property
     def samples(self) -> int:
         return sum(lv.N * lv.R for lv in self.levels)
+
+    @property
+    def coef_decay(self):
+        """The decay argument of the coefficient: the four decays of family 2, else ``decay``."""
+        return self.decays if self.family == 2 else self.decay
 
 
 def _ceil_sqrt(s: int) -> int:
@@ -58,7 +64,7 @@ def _ceil_sqrt(s: int) -> int:
     return r
 
 
-# The five workloads of the build.  Coarse truncation S = ceil(sqrt(s)) (Sec. 4.3);
+# The workloads.  Coarse truncation S = ceil(sqrt(s)) (Sec. 4.3);
 # coarse meshes as read for each workload.
 WORKLOADS = {
     # single level, FP64: h = 1/16 (225 dofs), H = 1/8, s = 16, S = 4, N = 256, R = 8, seed 0
@@ -98,6 +104,15 @@ WORKLOADS = {
         "paper_p1_h8_64",
         [Level(8, 8, 64, 64, 2048, 8)] + [Level(8 << l, 8, 64, _ceil_sqrt(64), 2048 >> l, 8) for l in range(1, 4)],
         seed=5, precision="mixed", tol=1e-10, a0=float(np.pi / np.sqrt(2.0)), decay=4.0 / 3.0, family=1,
+    ),
+    # the paper's second test problem (Sec. 5: four islands, parametric reaction term) with decays
+    # p_a = p_b = 4/3 on the islands and p_a' = p_b' = 2 off them (the left case of the paper's
+    # figure), s = 64 terms, S = 8, H = 1/8, h_l = 2^-(l+3) (level 0 direct; every mesh resolves the
+    # islands), R = 8 shifts, point counts halving level by level; lattice weights j^-(4/3)
+    "paper_p2_h8_64": Workload(
+        "paper_p2_h8_64",
+        [Level(8, 8, 64, 64, 2048, 8)] + [Level(8 << l, 8, 64, _ceil_sqrt(64), 2048 >> l, 8) for l in range(1, 4)],
+        seed=7, precision="mixed", tol=1e-10, decay=4.0 / 3.0, family=2, decays=(4.0 / 3.0, 2.0, 4.0 / 3.0, 2.0),
     ),
     # shared shifts and nested points with reuse (Sec. 4.3, after Algorithm 2): h_l = 1/16 .. 1/128,
     # s_l = 16 .. 128, level 0 direct on (h_0, s_0) = (1/16, 16); every level l >= 1 takes its coarse

@@ -41,6 +41,12 @@ def test_workload_levels_follow_the_readings(name):
             pv = wl.levels[l - 1]
             assert lv.n_fine > pv.n_fine and lv.s >= pv.s
     assert wl.samples == sum(lv.N * lv.R for lv in wl.levels)
+    if wl.family == 2:
+        # the second test problem: four decays, every mesh resolves the islands (width 1/8)
+        assert len(wl.decays) == 4 and wl.coef_decay == wl.decays
+        assert all(lv.n_coarse >= 8 for lv in wl.levels)
+    else:
+        assert wl.coef_decay == wl.decay
 
 
 @pytest.mark.parametrize("name", sorted(WORKLOADS))
