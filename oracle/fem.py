@@ -161,7 +161,9 @@ def coefficient(n: int, y: np.ndarray, a0: float = 1.0, decay: float = 2.0, fami
     """a(c_t, y) = a0 + sum_{j<=s} y_j psi_j(c_t) for every triangle t (eq. coeff, eq. coeff_s).
 
     The truncation dimension is len(y): terms beyond it are zero.  Small meshes use the cached
-    Psi matrix; large ones add the terms one by one (same formula, no s x 2n^2 matrix in memory).
+    Psi matrix; large ones add the terms one by one (same formula, no s x 2n^2 matrix in memory)
+    with compensated (Neumaier) summation, so their rounding error stays near one unit of the
+    result however many terms there are.
     """
     y = np.asarray(y, dtype=np.float64)
     if y.size == 0:
@@ -173,9 +175,14 @@ def coefficient(n: int, y: np.ndarray, a0: float = 1.0, decay: float = 2.0, fami
     # sin(pi k x) only depends on k and on the 2n distinct centroid abscissae (ordinates)
     xs, xi = np.unique(c[:, 0], return_inverse=True)
     ys, yi = np.unique(c[:, 1], return_inverse=True)
+    comp = np.zeros_like(a)
     for j, (k1, k2) in enumerate(psi_pairs(y.size, family), start=1):
-        a += y[j - 1] * j ** (-decay) * np.sin(np.pi * k1 * xs)[xi] * np.sin(np.pi * k2 * ys)[yi]
-    return a
+        term = y[j - 1] * j ** (-decay) * np.sin(np.pi * k1 * xs)[xi] * np.sin(np.pi * k2 * ys)[yi]
+        t = a + term
+        # the low-order part lost by the addition, whichever operand is larger
+        comp += np.where(np.abs(a) >= np.abs(term), (a - t) + term, (term - t) + a)
+        a = t
+    return a + comp
 
 
 _ELEMENT_CACHE: dict = {}

@@ -260,3 +260,19 @@ def test_family1_two_grid_between_fine_and_coarse_eigenvalues():
     # coarse eigenvalue is
     assert lam_tg >= lam_h - 1e-12 * lam_h
     assert abs(lam_tg - lam_h) < 0.1 * abs(lam_H - lam_h)
+
+
+def test_large_coefficient_path_is_correctly_summed():
+    # above 2^25 table entries the coefficient adds its terms one by one with compensated
+    # summation: on sampled triangles it equals math.fsum (the correctly rounded sum) of the terms
+    import math
+
+    n, s = 256, 1024
+    y = random_points(77, 1, s)[0]
+    a = fem.coefficient(n, y)
+    c = fem.centroids(n)
+    pairs = fem.psi_pairs(s)
+    for t in (0, 777, 65535, 2 * n * n - 1):
+        terms = [1.0] + [y[j] * (j + 1) ** -2.0 * np.sin(np.pi * k1 * c[t, 0]) * np.sin(np.pi * k2 * c[t, 1])
+                         for j, (k1, k2) in enumerate(pairs)]
+        assert abs(a[t] - math.fsum(terms)) <= np.finfo(float).eps * abs(a[t])
