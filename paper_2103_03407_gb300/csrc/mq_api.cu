@@ -50,6 +50,15 @@ struct mq_ctx {
   double* d_cj[2] = {nullptr, nullptr};  // term factors of a (and, family 2, of b)
   int* d_region = nullptr;               // family 2: per term 1 (on D_f) or 2 (off D_f)
   int psi_exp[2] = {0, 0};               // tensor-core slices of a table hold 2^psi_exp psi
+  // separable evaluation (family 0): terms grouped by k1, and per truncation K the largest k1 and
+  // the sum of |c_t| of the first K terms
+  bool sep_ok = false;
+  int* d_k1start = nullptr;
+  int* d_tlist = nullptr;
+  int k1max = 0, k2max = 0;
+  std::vector<int> k1prefix;
+  std::vector<double> csum;
+  std::map<int, std::pair<void*, mq::SepTables>> sep_tab;  // mesh n -> tables
   int qoi = MQ_QOI_EIGENVALUE;
 
   std::vector<mq_level> levels;
@@ -105,6 +114,7 @@ struct mq_ctx {
 
   DevBuf Y, af, ac, ap, out, stat, outer, scratch, sums_d, flags_d, uout, misc, upad, arena, ysl, tc_err;
   DevBuf bf, bc, bp;  // reaction coefficients of the fine, coarse and previous meshes (family 2)
+  DevBuf tsl, sepw;   // separable evaluation: stage-1 slices, table scratch
   int stream_min = 0;  // fine meshes 1/n with n >= stream_min use the streaming tier (0: default)
   mq_stats stats{};
   size_t last_B = 0;  // samples of the last pass (their per-sample counters are still on the device)
@@ -232,6 +242,8 @@ void release_tables(mq_ctx* c) {
     for (auto& kv : c->base[w]) cudaFree(kv.second);
     c->base[w].clear();
   }
+  for (auto& kv : c->sep_tab) cudaFree(kv.second.first);
+  c->sep_tab.clear();
 }
 
 mq_status ensure_psi(mq_ctx* c, int n, int rows, const double** out, int which = 0) {
@@ -311,11 +323,58 @@ mq_status ensure_psi_slices(mq_ctx* c, int n, const void** out, int* kpad, int w
 // a[b][t] = a0 + sum_{j<K} Y[b][j] psi_j(c_t) for B rows of Y (stride ldy) on mesh n: FP64 GEMM in
 // MQ_PREC_FP64, tensor-core split GEMM in MQ_PREC_MIXED.  which = 1: the reaction coefficient b of
 // family 2 (which, like its a, takes a piecewise zeroth term in place of a0).
+// The separable evaluation pays off on fine meshes when the terms use few distinct k1: stage 2
+// contracts over the padded k1 count instead of K.
+bool use_separable(const mq_ctx* c, int n, int K) {
+  if (!c->sep_ok || c->prec != MQ_PREC_MIXED || K <= 0 || n < 128) return false;
+  return 4 * mq::tc_pad_k(c->k1prefix[K - 1]) <= K;
+}
+
+mq_status coefficients_separable(mq_ctx* c, int n, int K, const double* d_Y, int B, int ldy, double* d_a) {
+  mq_status st;
+  auto it = c->sep_tab.find(n);
+  if (it == c->sep_tab.end()) {
+    const int kp = mq::tc_pad_k(c->k1max);
+    void* mem = nullptr;
+    const size_t bytes = mq::sep_tables_bytes(n, kp, c->k2max);
+    if (cudaMalloc(&mem, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, MQ_ENOMEM, "separable tables for n=%d (%zu bytes)", n, bytes);
+    }
+    if ((st = grow(c, c->sepw, (size_t)n * kp * sizeof(double))) != MQ_OK) {
+      cudaFree(mem);
+      return st;
+    }
+    mq::SepTables t{};
+    const cudaError_t e = mq::launch_sep_tables(n, c->k1max, kp, c->k2max, (double*)c->sepw.p, mem, &t, c->stream);
+    if (e != cudaSuccess) {
+      cudaFree(mem);
+      return fail(c, MQ_ECUDA, "separable tables: %s", cudaGetErrorString(e));
+    }
+    c->n_launches += 6;
+    it = c->sep_tab.emplace(n, std::make_pair(mem, t)).first;
+  }
+  const int k1pad = mq::tc_pad_k(c->k1prefix[K - 1]);
+  // |T| <= sum_{t<K} |y_t c_t| < csum / 2: the largest ey with 2^ey csum <= 1 keeps 2^ey |T| <= 1/2
+  int ey = 0;
+  const double cs = c->csum[K - 1];
+  while (std::ldexp(cs, ey) > 1.0) --ey;
+  while (std::ldexp(cs, ey + 1) <= 1.0) ++ey;
+  if ((st = grow(c, c->tsl, mq::tc_slices_bytes(B * n, k1pad))) != MQ_OK) return st;
+  if ((st = grow(c, c->tc_err, sizeof(int))) != MQ_OK) return st;
+  const mq::SepTerms terms{c->d_k1start, c->d_tlist, c->d_k2, c->d_cj[0]};
+  MQ_CUDA(c, mq::launch_coef_sep(d_Y, ldy, B, K, k1pad, terms, it->second.second, n, c->a0, ey, c->tsl.p, d_a,
+                                 (int*)c->tc_err.p, c->stream));
+  c->n_launches += 4;  // two stage-1 kernels and two tensor-core launches
+  return MQ_OK;
+}
+
 mq_status coefficients(mq_ctx* c, int n, int K, const double* d_Y, int B, int ldy, double* d_a, int which = 0) {
   const int nT = 2 * n * n;
   mq_status st;
   const double* base = nullptr;
   if (c->family == 2 && (st = ensure_base(c, n, which, &base)) != MQ_OK) return st;
+  if (!base && which == 0 && use_separable(c, n, K)) return coefficients_separable(c, n, K, d_Y, B, ldy, d_a);
   const double a0 = base ? 0.0 : c->a0;
   if (c->prec == MQ_PREC_MIXED && K > 0) {
     const void* ps = nullptr;
@@ -888,7 +947,7 @@ mq_status mq_destroy(mq_ctx* c) {
     if (b->p) cudaFree(b->p);
   for (DevBuf* b : {&c->Y, &c->af, &c->ac, &c->ap, &c->out, &c->stat, &c->outer, &c->scratch, &c->sums_d,
                     &c->flags_d, &c->uout, &c->misc, &c->upad, &c->arena, &c->ysl, &c->tc_err, &c->bf, &c->bc,
-                    &c->bp})
+                    &c->bp, &c->tsl, &c->sepw})
     if (b->p) cudaFree(b->p);
   release_tables(c);
   free_reuse(c);
@@ -901,6 +960,8 @@ mq_status mq_destroy(mq_ctx* c) {
   for (double* p : c->d_cj)
     if (p) cudaFree(p);
   if (c->d_region) cudaFree(c->d_region);
+  if (c->d_k1start) cudaFree(c->d_k1start);
+  if (c->d_tlist) cudaFree(c->d_tlist);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
   if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -981,6 +1042,42 @@ mq_status set_terms(mq_ctx* c, double a0, int32_t s_max, int32_t family, double 
       while (std::ldexp(mx, e + 1) <= 1.0) ++e;
     }
     c->psi_exp[w] = e;
+  }
+  // separable evaluation (family 0): the terms grouped by k1 in increasing t
+  if (c->d_k1start) cudaFree(c->d_k1start);
+  if (c->d_tlist) cudaFree(c->d_tlist);
+  c->d_k1start = c->d_tlist = nullptr;
+  c->sep_ok = false;
+  if (family == 0) {
+    int k1m = 0, k2m = 0;
+    c->k1prefix.assign(m, 0);
+    c->csum.assign(m, 0.0);
+    double cs = 0.0;
+    for (int t = 0; t < m; ++t) {
+      k1m = std::max(k1m, k1[t]);
+      k2m = std::max(k2m, k2[t]);
+      cs += std::fabs(cj[0][t]);
+      c->k1prefix[t] = k1m;
+      c->csum[t] = cs;
+    }
+    const int kp = mq::tc_pad_k(k1m);
+    // start[v] .. start[v + 1] lists the terms of k1 = v (start[kp + 1] = m closes the last list)
+    std::vector<int> start(kp + 2, 0), list;
+    list.reserve(m);
+    for (int v = 1; v <= kp; ++v) {
+      start[v] = (int)list.size();
+      for (int t = 0; t < m; ++t)
+        if (k1[t] == v) list.push_back(t);
+    }
+    start[kp + 1] = (int)list.size();
+    start[0] = 0;
+    MQ_CUDA(c, cudaMalloc(&c->d_k1start, start.size() * sizeof(int)));
+    MQ_CUDA(c, cudaMalloc(&c->d_tlist, std::max<size_t>(list.size(), 1) * sizeof(int)));
+    MQ_CUDA(c, cudaMemcpy(c->d_k1start, start.data(), start.size() * sizeof(int), cudaMemcpyHostToDevice));
+    MQ_CUDA(c, cudaMemcpy(c->d_tlist, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice));
+    c->k1max = k1m;
+    c->k2max = k2m;
+    c->sep_ok = true;
   }
   c->a0 = a0;
   c->s_max = s_max;

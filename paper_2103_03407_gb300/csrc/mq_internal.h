@@ -113,6 +113,32 @@ cudaError_t launch_coef_tc(const void* d_yslices, int B, int kpad, const void* d
                            double a0, double* d_a, int* d_err, cudaStream_t st, const double* d_base = nullptr,
                            int pexp = 0);
 
+// Separable coefficient evaluation for the workload family (mq_tc.cu): the terms grouped by k1
+// (device arrays: tlist[k1start[k1] .. k1start[k1+1]) the terms t of wave number k1 in increasing
+// t; tk2[t] = k2_t; cj[t] = c_t), and per mesh the tables of both triangle planes (sx: BF16 slices
+// of sin(pi k1 x_i), [n][k1pad]; syt: sin(pi k2 y_j), [k2max + 1][n]).
+struct SepTerms {
+  const int* k1start;
+  const int* tlist;
+  const int* tk2;
+  const double* cj;
+};
+struct SepTables {
+  const void* sx[2];
+  const double* syt[2];
+  int k1pad;
+};
+size_t sep_tables_bytes(int n, int k1pad, int k2max);
+// builds the tables of mesh n in d_tables (sep_tables_bytes); d_work: n k1pad doubles of scratch
+cudaError_t launch_sep_tables(int n, int k1max, int k1pad, int k2max, double* d_work, void* d_tables, SepTables* t,
+                              cudaStream_t st);
+// a[b][t] for B rows of Y with the first K terms: k1pad >= the padded largest k1 of those terms,
+// ey the exponent with |2^ey T| <= 1/2 for every stage-1 value T; d_tslices: tc_slices_bytes(B n,
+// k1pad) bytes of scratch
+cudaError_t launch_coef_sep(const double* d_Y, int ldy, int B, int K, int k1pad, const SepTerms& terms,
+                            const SepTables& tab, int n, double a0, int ey, void* d_tslices, double* d_a, int* d_err,
+                            cudaStream_t st);
+
 // Sample flags (stat[b][3])
 enum : int {
   kFlagEigNoConv = 1,

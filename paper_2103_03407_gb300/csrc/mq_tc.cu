@@ -166,6 +166,81 @@ __global__ void k_slice_rows(const double* __restrict__ src, int rows, int k, si
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Separable evaluation (families whose terms are c_t sin(pi k1_t x1) sin(pi k2_t x2) with few
+// distinct k1, like the workload family, where k1 <= ~2 sqrt(s)).  On one plane of triangles
+// (lower or upper: the centroid abscissa x_i depends only on the cell column i, the ordinate y_j
+// only on the cell row j)
+//     a[b][j][i] = a0 + sum_{k1} T[b][j][k1] sin(pi k1 x_i),
+//     T[b][j][k1] = sum_{t < K, k1_t = k1} Y[b][t] c_t sin(pi k2_t y_j),
+// the same sum as eq. coeff_s grouped by k1.  Stage 1 forms T in FP64 on the CUDA cores (B n K
+// fused multiply-adds per plane) and writes its exact BF16 slices; stage 2 is the tensor-core
+// kernel below with rows (b, j), columns i and K = the padded count of k1 values: 2 B n^2 K1
+// products per plane instead of 2 B n^2 K.
+
+// centroid numerators over 3n: abscissa of column i, ordinate of row j, per plane
+__device__ __forceinline__ int cx_num(int i, int plane) { return 3 * i + (plane == 0 ? 2 : 1); }
+__device__ __forceinline__ int cy_num(int j, int plane) { return 3 * j + (plane == 0 ? 1 : 2); }
+
+// syt[k][j] = sin(pi k y_j), k = 0..kmax, j < n (plane `plane`)
+__global__ void k_sep_syt(int n, int plane, int kmax, double* __restrict__ syt) {
+  const size_t tot = (size_t)(kmax + 1) * n;
+  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(q / n), j = (int)(q % n);
+    syt[q] = sinpi((double)k * (double)cy_num(j, plane) / (double)(3 * n));
+  }
+}
+
+// sx[i][e] = sin(pi (e+1) x_i) for e + 1 <= k1max, 0 beyond (kpad columns)
+__global__ void k_sep_sx(int n, int plane, int k1max, int kpad, double* __restrict__ sx) {
+  const size_t tot = (size_t)n * kpad;
+  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(q / kpad), e = (int)(q % kpad);
+    sx[q] = e + 1 <= k1max ? sinpi((double)(e + 1) * (double)cx_num(i, plane) / (double)(3 * n)) : 0.0;
+  }
+}
+
+// Stage 1: T[m = b n + j][k1 - 1] for one plane, written as the 7 BF16 slices of scale * T in the
+// layout of k_slice_rows ([7][kpad/8][rows_pad][8]); one thread per (row, group of 8 k1 values).
+// The terms of each k1 are listed in increasing t: tlist[k1start[k1] .. k1start[k1 + 1]).
+__global__ void k_sep_stage1(const double* __restrict__ Y, int ldy, int B, int n, int plane, int K, int kpad,
+                             const int* __restrict__ k1start, const int* __restrict__ tlist,
+                             const int* __restrict__ tk2, const double* __restrict__ cj, const double* __restrict__ syt,
+                             double scale, int rows_pad, __nv_bfloat16* __restrict__ out) {
+  (void)plane;
+  const size_t tot = (size_t)rows_pad * (kpad / 8);
+  const size_t sstride = (size_t)rows_pad * kpad;
+  const int rows = B * n;
+  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += (size_t)gridDim.x * blockDim.x) {
+    const int m = (int)(q % rows_pad), kg = (int)(q / rows_pad);
+    __align__(16) __nv_bfloat16 sl[kSlices][8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      double v = 0.0;
+      if (m < rows) {
+        const int b = m / n, j = m % n, k1 = kg * 8 + e + 1;
+        const double* yb = Y + (size_t)b * ldy;
+        for (int idx = k1start[k1]; idx < k1start[k1 + 1]; ++idx) {
+          const int t = tlist[idx];
+          if (t >= K) break;
+          v = fma(yb[t] * cj[t], syt[(size_t)tk2[t] * n + j], v);
+        }
+      }
+      v *= scale;
+#pragma unroll
+      for (int p = 0; p < kSlices; ++p) {
+        const double r = rint(v);
+        sl[p][e] = __float2bfloat16_rn((float)r);
+        v = (v - r) * 256.0;
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < kSlices; ++p)
+      *reinterpret_cast<uint4*>(out + (size_t)p * sstride + ((size_t)kg * rows_pad + m) * 8) =
+          *reinterpret_cast<const uint4*>(sl[p]);
+  }
+}
+
 struct alignas(1024) TcSmem {
   __nv_bfloat16 a[kStages][kSlices * kTM * kTK];  // [slice][K half][128 rows][8]
   __nv_bfloat16 b[kStages][kSlices * kTN * kTK];  // [slice][K half][64 rows][8]
@@ -176,13 +251,34 @@ struct alignas(1024) TcSmem {
   int err;
 };
 
+// Output placement: element (row b, column t) goes to out[row_off(b) + t] with row_off(b) = b nT,
+// or, with mdiv > 0, (b / mdiv) m_hi + (b mod mdiv) m_lo (rows that index (sample, mesh row)
+// pairs of a coefficient field).  Rows come in tiles of 128, columns in tiles of 64.
+struct TcOut {
+  double* out;
+  int mdiv;
+  long long m_hi, m_lo;
+  int cols_fast;  // tile order: 0 row tiles fastest (tiles sharing a column tile run together), 1 columns
+};
+
 // a[b][t] = a0 + sum_j y[b][j] psi[j][t], b < B, t < nT (with base: base[t] in place of a0).
-// Tiles: tm = tile mod ntm (128 samples), tn = tile div ntm (64 triangles); CTA c takes tiles c,
-// c + grid, ...  Kpad: K of the Y slices.
+// Tiles: tm = tile mod ntm (128 samples), tn = tile div ntm (64 triangles), or the transposed
+// order; CTA c takes tiles c, c + grid, ...  Kpad: K of the Y slices.
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_coef_tc(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmP, int B, int nT, int Kpad,
-              int ntm, int ntiles, double a0, double* __restrict__ out, int* __restrict__ err_flag,
-              const double* __restrict__ base, int pexp) {
+              int ntm, int ntiles, double a0, TcOut O, int* __restrict__ err_flag, const double* __restrict__ base,
+              int pexp) {
+  double* __restrict__ out = O.out;
+  const int ntn = ntiles / ntm;
+  auto coords = [&](int tile, int& tm, int& tn) {
+    if (O.cols_fast) {
+      tm = tile / ntn;
+      tn = tile % ntn;
+    } else {
+      tm = tile % ntm;
+      tn = tile / ntm;
+    }
+  };
   extern __shared__ __align__(1024) char dyn[];
   TcSmem& S = *reinterpret_cast<TcSmem*>(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -217,7 +313,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   auto issue_load = [&](uint32_t u) {
     const int ti = (int)(u / (uint32_t)T), ks = (int)(u % (uint32_t)T);
     const int tile = (int)blockIdx.x + ti * (int)gridDim.x;
-    const int tm = tile % ntm, tn = tile / ntm;
+    int tm, tn;
+    coords(tile, tm, tn);
     const int st = (int)(u % kStages);
     mbar_arrive_expect(&S.full[st], kABytes + kBBytes);
     tma_load4(S.a[st], &tmY, 0, tm * kTM, 2 * ks, 0, &S.full[st]);
@@ -232,7 +329,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   bool ok = true;
   for (int ti = 0; ti < my_tiles && ok; ++ti) {
     const int tile = (int)blockIdx.x + ti * (int)gridDim.x;
-    const int tm = tile % ntm, tn = tile / ntm;
+    int tm, tn;
+    coords(tile, tm, tn);
     // 2^-39 and 2^-63 of the fold, times the table's exact scale 2^-pexp
     const double chi = ldexp(1.0, -39 - pexp), clo = ldexp(1.0, -63 - pexp);
     double acc[32];
@@ -330,14 +428,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (ok) {
       const int b = tm * kTM + q4 * 32 + lane;
       if (b < B) {
-        double* o = out + (size_t)b * nT;
+        double* o = out + (O.mdiv > 0 ? (size_t)(b / O.mdiv) * (size_t)O.m_hi + (size_t)(b % O.mdiv) * (size_t)O.m_lo
+                                      : (size_t)b * nT);
         const int t0 = tn * kTN + half * 32;
-        // nT = 2 n^2 and t0 are even: pairs are 16-byte aligned whenever the output base is
+        // t0 is even: pairs are 16-byte aligned whenever the row start is
         if (base) {
 #pragma unroll
           for (int i = 0; i < 32; ++i)
             if (t0 + i < nT) o[t0 + i] = base[t0 + i] + acc[i];
-        } else if (((uintptr_t)out & 15) == 0) {
+        } else if (((uintptr_t)o & 15) == 0) {
 #pragma unroll
           for (int i = 0; i < 32; i += 2)
             if (t0 + i < nT) *reinterpret_cast<double2*>(o + t0 + i) = make_double2(a0 + acc[i], a0 + acc[i + 1]);
@@ -427,8 +526,9 @@ cudaError_t launch_y_slices(const double* d_Y, int B, int ldy, int k, int kpad, 
 
 // a[B][nT] = a0 + Y psi from slices: y slices [7][kpad/8][Bpad][8] built for K = kpad columns, psi
 // slices [7][kpad_psi/8][nTpad][8] (only the first kpad columns are read)
-cudaError_t launch_coef_tc(const void* d_yslices, int B, int kpad, const void* d_pslices, int nT, int kpad_psi,
-                           double a0, double* d_a, int* d_err, cudaStream_t st, const double* d_base, int pexp) {
+namespace {
+cudaError_t coef_tc(const void* d_yslices, int B, int kpad, const void* d_pslices, int nT, int kpad_psi, double a0,
+                    const TcOut& O, int* d_err, cudaStream_t st, const double* d_base, int pexp) {
   if (B == 0 || nT == 0) return cudaSuccess;
   if (kpad > kpad_psi || kpad % kTK || kpad <= 0) return cudaErrorInvalidValue;
   const int Bp = tc_pad_rows(B), nTp = tc_pad_rows(nT);
@@ -448,8 +548,62 @@ cudaError_t launch_coef_tc(const void* d_yslices, int B, int kpad, const void* d
   const long ntiles = (long)ntm * (nTp / kTN);
   if (ntiles > 0x7fffffffL) return cudaErrorInvalidValue;
   const int grid = (int)(ntiles < sms ? ntiles : sms);
-  k_coef_tc<<<grid, kTcThreads, smem, st>>>(tmY, tmP, B, nT, kpad, ntm, (int)ntiles, a0, d_a, d_err, d_base, pexp);
+  k_coef_tc<<<grid, kTcThreads, smem, st>>>(tmY, tmP, B, nT, kpad, ntm, (int)ntiles, a0, O, d_err, d_base, pexp);
   return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_coef_tc(const void* d_yslices, int B, int kpad, const void* d_pslices, int nT, int kpad_psi,
+                           double a0, double* d_a, int* d_err, cudaStream_t st, const double* d_base, int pexp) {
+  const TcOut O{d_a, 0, 0, 0, 0};
+  return coef_tc(d_yslices, B, kpad, d_pslices, nT, kpad_psi, a0, O, d_err, st, d_base, pexp);
+}
+
+size_t sep_tables_bytes(int n, int k1pad, int k2max) {
+  return 2 * (tc_slices_bytes(n, k1pad) + (size_t)(k2max + 1) * n * sizeof(double)) + 4 * 256;
+}
+
+cudaError_t launch_sep_tables(int n, int k1max, int k1pad, int k2max, double* d_work, void* d_tables, SepTables* t,
+                              cudaStream_t st) {
+  char* p = (char*)d_tables;
+  auto take = [&](size_t bytes) {
+    p = (char*)(((uintptr_t)p + 255) & ~(uintptr_t)255);
+    char* r = p;
+    p += bytes;
+    return r;
+  };
+  t->k1pad = k1pad;
+  for (int plane = 0; plane < 2; ++plane) {
+    t->sx[plane] = take(tc_slices_bytes(n, k1pad));
+    t->syt[plane] = (double*)take((size_t)(k2max + 1) * n * sizeof(double));
+    k_sep_sx<<<grid1((size_t)n * k1pad), 256, 0, st>>>(n, plane, k1max, k1pad, d_work);
+    const int rp = tc_pad_rows(n);
+    k_slice_rows<<<grid1((size_t)rp * k1pad), 256, 0, st>>>(d_work, n, k1pad, (size_t)k1pad, 1, 128.0, rp, k1pad,
+                                                           (__nv_bfloat16*)t->sx[plane]);
+    k_sep_syt<<<grid1((size_t)(k2max + 1) * n), 256, 0, st>>>(n, plane, k2max, (double*)t->syt[plane]);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coef_sep(const double* d_Y, int ldy, int B, int K, int k1pad, const SepTerms& terms,
+                            const SepTables& tab, int n, double a0, int ey, void* d_tslices, double* d_a, int* d_err,
+                            cudaStream_t st) {
+  if (B == 0) return cudaSuccess;
+  if (k1pad % kTK || k1pad <= 0 || k1pad > tab.k1pad || (long)B * n > 0x7fffffffL - 128) return cudaErrorInvalidValue;
+  const int rows = B * n, rp = tc_pad_rows(rows);
+  for (int plane = 0; plane < 2; ++plane) {
+    k_sep_stage1<<<grid1((size_t)rp * (k1pad / 8)), 256, 0, st>>>(
+        d_Y, ldy, B, n, plane, K, k1pad, terms.k1start, terms.tlist, terms.tk2, terms.cj, tab.syt[plane],
+        std::ldexp(256.0, ey), rp, (__nv_bfloat16*)d_tslices);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // rows (b, j) of this plane land at a[b][plane][j][.]: b 2n^2 + plane n^2 + j n
+    const TcOut O{d_a + (size_t)plane * n * n, n, 2LL * n * n, (long long)n, 1};
+    if ((e = coef_tc(d_tslices, rows, k1pad, tab.sx[plane], n, tab.k1pad, a0, O, d_err, st, nullptr, ey)) !=
+        cudaSuccess)
+      return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace mq

@@ -86,6 +86,32 @@ def test_tensor_core_coefficients_match_oracle(B, n, s, nb, offset):
     assert np.abs(got - ref).max() < 5e-15
 
 
+@pytest.mark.parametrize("n,s,nb,decay", [(128, 128, 3, 2.0), (128, 100, 130, 2.0), (256, 1024, 3, 2.0),
+                                           (256, 1024, 2, 4.0 / 3.0), (512, 300, 1, 2.0)])
+def test_separable_coefficients_match_oracle(B, n, s, nb, decay):
+    # mixed precision on meshes 1/128 and finer: the workload family is evaluated separably (the
+    # terms grouped by k1: an FP64 first stage and a tensor-core second stage over the k1 values);
+    # ragged row counts (130 samples x 128 rows), the decay below 2 takes a smaller slice scale
+    ctx = B.Context(0)
+    ctx.mq_set_coefficient(1.0, s, 0, decay)
+    ctx.mq_set_levels([Level(n, n, s, s, 8, 2)])
+    ctx.mq_set_precision(1)
+    Y = random_points(n + s + nb, nb, s)
+    dY = torch.from_numpy(Y).cuda()
+    da = torch.empty((nb, 2 * n * n), dtype=torch.float64, device="cuda")
+    ctx.mq_coefficients_device(n, s, dY, nb, s, da)
+    got = da.cpu().numpy()
+    for b in range(nb):
+        ref = fem.coefficient(n, Y[b], 1.0, decay)
+        assert np.abs(got[b] - ref).max() < 5e-15, (b, np.abs(got[b] - ref).max())
+    # a truncation shorter than the table's (fewer k1 values) reads a prefix of the term lists
+    k = s // 3
+    ctx.mq_coefficients_device(n, k, dY, nb, s, da)
+    got = da.cpu().numpy()
+    assert np.abs(got[0] - fem.coefficient(n, Y[0][:k], 1.0, decay)).max() < 5e-15
+    ctx.close()
+
+
 @pytest.mark.parametrize("n", [2, 4, 8, 16, 64])
 def test_operator_apply_matches_assembled_matrices(B, n):
     ctx, _, _ = make_ctx(B, [Level(8, 8, 1, 1, 8, 2)])
