@@ -18,6 +18,7 @@
 //   * FP64 iterative refinement around the inner solve and the FP64 Rayleigh quotient.
 // Partial sums of every reduction are written per (sample, tile) and added in fixed order by
 // the scalar kernels: results do not depend on scheduling.  Converged samples are masked out.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -125,10 +126,13 @@ __device__ __forceinline__ void tile_partials(A (&v)[NV], double* part, size_t s
 // ---------------------------------------------------------------------------------------------
 // setup
 // weights and inverse diagonal of mesh n from per-triangle coefficients (lower plane, upper plane)
+// (with hx: BF16 copies of the weights and of om D^-1 for the V(1,1) sweeps of the FP32 path)
 template <typename T, typename S>
 __global__ void k_weights(int n, int B, const S* __restrict__ cells, size_t cstride, T* __restrict__ wx,
                           T* __restrict__ wy, T* __restrict__ dinv, T om, double* __restrict__ wx64,
-                          double* __restrict__ wy64, const int* __restrict__ act, SS<T>* ss) {
+                          double* __restrict__ wy64, const int* __restrict__ act, SS<T>* ss,
+                          __nv_bfloat16* __restrict__ hx = nullptr, __nv_bfloat16* __restrict__ hy = nullptr,
+                          __nv_bfloat16* __restrict__ hd = nullptr) {
   const int nt = tiles_padded(n);
   const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
   if (b >= B || (act && !act[b])) return;
@@ -162,6 +166,11 @@ __global__ void k_weights(int n, int B, const S* __restrict__ cells, size_t cstr
     wx[(size_t)b * V + q] = a;
     wy[(size_t)b * V + q] = c;
     dinv[(size_t)b * V + q] = d;
+    if (hx) {
+      hx[(size_t)b * V + q] = __float2bfloat16_rn((float)a);
+      hy[(size_t)b * V + q] = __float2bfloat16_rn((float)c);
+      hd[(size_t)b * V + q] = __float2bfloat16_rn((float)d);
+    }
     if (wx64) {
       wx64[(size_t)b * V + q] = a64;
       wy64[(size_t)b * V + q] = c64;
@@ -440,9 +449,27 @@ __global__ void k_prolong_smooth(int n, int B, const int* __restrict__ act, cons
 
 // V(1,1) down-sweep: the one Jacobi step from zero, x1 = om D^-1 b, is pointwise; its residual
 // b - A x1 is formed on the fly and restricted with P^T (nothing stored on the fine mesh)
-template <typename T>
-__global__ void k_restrict1(int n, int B, const int* __restrict__ act, const T* __restrict__ wx,
-                            const T* __restrict__ wy, const T* __restrict__ dinv, const T* __restrict__ bb,
+template <typename WT>
+__device__ __forceinline__ float wval(WT v) {
+  return (float)v;
+}
+template <>
+__device__ __forceinline__ float wval<__nv_bfloat16>(__nv_bfloat16 v) {
+  return __bfloat162float(v);
+}
+template <typename T, typename WT>
+__device__ __forceinline__ T wget(const WT* p) {
+  if constexpr (sizeof(WT) == 2)
+    return T(wval(*p));
+  else
+    return T(*p);
+}
+
+// (weights and om D^-1 of type WT: T, or BF16 copies on the FP32 path -- the V-cycle is only the
+// preconditioner, and BF16 keeps it symmetric positive definite and spectrally equivalent)
+template <typename T, typename WT = T>
+__global__ void k_restrict1(int n, int B, const int* __restrict__ act, const WT* __restrict__ wx,
+                            const WT* __restrict__ wy, const WT* __restrict__ dinv, const T* __restrict__ bb,
                             T* __restrict__ bc, int ldo) {
   const int m = n / 2;
   const int nt = tiles_interior(m);
@@ -450,18 +477,18 @@ __global__ void k_restrict1(int n, int B, const int* __restrict__ act, const T* 
   if (b >= B || !act[b]) return;
   const int ld = sld(n);
   const size_t off = (size_t)b * ssz(n);
-  const T* __restrict__ W = wx + off;
-  const T* __restrict__ Y = wy + off;
-  const T* __restrict__ D = dinv + off;
+  const WT* __restrict__ W = wx + off;
+  const WT* __restrict__ Y = wy + off;
+  const WT* __restrict__ D = dinv + off;
   const T* __restrict__ R = bb + off;
   T* __restrict__ C = bc + (size_t)b * (size_t)(m + 1) * ldo;
   for_tile(m, ch, [&](int, int I, int J) {
     const int p = (2 * J) * ld + 2 * I;
-    auto x1 = [&](int q) { return D[q] * R[q]; };
+    auto x1 = [&](int q) { return wget<T>(D + q) * R[q]; };
     auto res = [&](int q) {
       const T xq = x1(q);
-      return R[q] - (W[q] * (xq - x1(q + 1)) + W[q - 1] * (xq - x1(q - 1)) + Y[q] * (xq - x1(q + ld)) +
-                     Y[q - ld] * (xq - x1(q - ld)));
+      return R[q] - (wget<T>(W + q) * (xq - x1(q + 1)) + wget<T>(W + q - 1) * (xq - x1(q - 1)) +
+                     wget<T>(Y + q) * (xq - x1(q + ld)) + wget<T>(Y + q - ld) * (xq - x1(q - ld)));
     };
     C[J * ldo + I] = res(p) + T(0.5) * ((res(p + 1) + res(p - 1)) + (res(p + ld) + res(p - ld)) +
                                         (res(p + ld + 1) + res(p - ld - 1)));
@@ -784,9 +811,19 @@ __global__ void k_minres_v4(int n, int B, const int* __restrict__ act, const SS<
 // neighbours, then out = t + om D^-1 (b - A t); with DOT also the partial <dotv, out>.  The coarse
 // correction P xc (mean of the two coarse values on the coarse edge through each fine node) reads
 // the coarse vector with scalar loads (rows of ldc entries).
-template <bool DOT>
-__global__ void k_prolong_smooth1_4(int n, int B, const int* __restrict__ act, const float* __restrict__ wx,
-                                    const float* __restrict__ wy, const float* __restrict__ dinv,
+// four consecutive weights (16-byte aligned FP32, or 8-byte aligned BF16) as a float4
+__device__ __forceinline__ float4 ldw4(const float* p) { return ld4(p); }
+__device__ __forceinline__ float4 ldw4(const __nv_bfloat16* p) {
+  const uint2 u = *reinterpret_cast<const uint2*>(p);
+  const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162*>(&u.x);
+  const __nv_bfloat162 c = *reinterpret_cast<const __nv_bfloat162*>(&u.y);
+  const float2 fa = __bfloat1622float2(a), fc = __bfloat1622float2(c);
+  return make_float4(fa.x, fa.y, fc.x, fc.y);
+}
+
+template <bool DOT, typename WT = float>
+__global__ void k_prolong_smooth1_4(int n, int B, const int* __restrict__ act, const WT* __restrict__ wx,
+                                    const WT* __restrict__ wy, const WT* __restrict__ dinv,
                                     const float* __restrict__ bb, const float* __restrict__ xc, int ldc,
                                     float* __restrict__ out, const float* __restrict__ dotv, double* part) {
   const int nt = tiles_vec(n);
@@ -804,15 +841,15 @@ __global__ void k_prolong_smooth1_4(int n, int B, const int* __restrict__ act, c
       return 0.5f * (XC[c] + XC[c + (ii & 1) + (jj & 1) * ldc]);
     };
     const bool first = c0 == 0;
-    const float4 dc = ld4(dinv + p), rc = ld4(bb + p);
-    const float4 dn = ld4(dinv + p + ld), rn = ld4(bb + p + ld);
-    const float4 ds = ld4(dinv + p - ld), rs = ld4(bb + p - ld);
-    const float4 wc = ld4(wx + p), yc = ld4(wy + p), ys = ld4(wy + p - ld);
-    const float wwest = first ? 0.0f : wx[p - 1];
+    const float4 dc = ldw4(dinv + p), rc = ld4(bb + p);
+    const float4 dn = ldw4(dinv + p + ld), rn = ld4(bb + p + ld);
+    const float4 ds = ldw4(dinv + p - ld), rs = ld4(bb + p - ld);
+    const float4 wc = ldw4(wx + p), yc = ldw4(wy + p), ys = ldw4(wy + p - ld);
+    const float wwest = first ? 0.0f : wget<float>(wx + p - 1);
     // t along row j at columns c0-1 .. c0+4, and at rows j+1, j-1 under the four nodes
     float tr[kVec + 2], tn[kVec], ts[kVec];
-    tr[0] = first ? 0.0f : dinv[p - 1] * bb[p - 1] + pc(c0 - 1, j);
-    tr[kVec + 1] = dinv[p + kVec] * bb[p + kVec] + pc(c0 + kVec, j);
+    tr[0] = first ? 0.0f : wget<float>(dinv + p - 1) * bb[p - 1] + pc(c0 - 1, j);
+    tr[kVec + 1] = wget<float>(dinv + p + kVec) * bb[p + kVec] + pc(c0 + kVec, j);
 #pragma unroll
     for (int k = 0; k < kVec; ++k) {
       tr[k + 1] = at(dc, k) * at(rc, k) + pc(c0 + k, j);
@@ -1122,6 +1159,8 @@ struct Arena {
   double *x64, *b64;
   double *wx64, *wy64;  // FP64 edge weights of the finest mesh (the residual operator)
   T *wx[kMaxMG], *wy[kMaxMG], *dinv[kMaxMG], *x[kMaxMG], *t[kMaxMG], *b[kMaxMG];
+  // FP32 path: BF16 copies of wx, wy, om D^-1 per streaming level, read by the V(1,1) sweeps
+  __nv_bfloat16 *hx[kMaxMG], *hy[kMaxMG], *hd[kMaxMG];
   T* cells[kMaxMG];  // per-triangle coefficients of streaming level l >= 1 and of the sub mesh
   T *bsub, *xsub;
   char* subw;  // per-sample operator arrays of the sub meshes
@@ -1160,6 +1199,10 @@ size_t carve_arena(void* base, int n, int B, Arena<T>& A) {
     A.t[l] = l < A.Ls ? c.take<T>(Bz * V) : nullptr;
     A.x[l] = l ? c.take<T>(Bz * V) : nullptr;
     A.b[l] = l ? c.take<T>(Bz * V) : nullptr;
+    const bool h = sizeof(T) == sizeof(float) && l < A.Ls;
+    A.hx[l] = h ? c.take<__nv_bfloat16>(Bz * V) : nullptr;
+    A.hy[l] = h ? c.take<__nv_bfloat16>(Bz * V) : nullptr;
+    A.hd[l] = h ? c.take<__nv_bfloat16>(Bz * V) : nullptr;
   }
   for (int l = 1; l <= A.Ls; ++l) {
     const size_t nl = (size_t)(n >> l);
@@ -1204,8 +1247,12 @@ cudaError_t vcycle_stream(Arena<T>& A, const T* b0, T* x0, const int* act, T om,
       const T* b = l ? A.b[l] : b0;
       T* bc = (l + 1 < A.Ls) ? A.b[l + 1] : A.bsub;
       const int ldo = (l + 1 < A.Ls) ? sld(nl / 2) : nl / 2 + 1;
-      ++tl_launches, k_restrict1<T><<<B * tiles_interior(nl / 2), kThreads, 0, st>>>(nl, B, act, A.wx[l], A.wy[l],
-                                                                                   A.dinv[l], b, bc, ldo);
+      if (A.hx[l])
+        ++tl_launches, k_restrict1<T, __nv_bfloat16><<<B * tiles_interior(nl / 2), kThreads, 0, st>>>(
+            nl, B, act, A.hx[l], A.hy[l], A.hd[l], b, bc, ldo);
+      else
+        ++tl_launches, k_restrict1<T><<<B * tiles_interior(nl / 2), kThreads, 0, st>>>(nl, B, act, A.wx[l], A.wy[l],
+                                                                                     A.dinv[l], b, bc, ldo);
       LAUNCH_CHECK();
     }
     const int ns = n >> A.Ls;
@@ -1220,11 +1267,11 @@ cudaError_t vcycle_stream(Arena<T>& A, const T* b0, T* x0, const int* act, T om,
       const int ldc = (l + 1 < A.Ls) ? sld(nl / 2) : nl / 2 + 1;
       if constexpr (sizeof(T) == sizeof(float)) {
         if (l == 0 && dotv)
-          ++tl_launches, k_prolong_smooth1_4<true><<<B * tiles_vec(nl), kThreads, 0, st>>>(
-              nl, B, act, A.wx[l], A.wy[l], A.dinv[l], b, xc, ldc, xa, dotv, part);
+          ++tl_launches, k_prolong_smooth1_4<true, __nv_bfloat16><<<B * tiles_vec(nl), kThreads, 0, st>>>(
+              nl, B, act, A.hx[l], A.hy[l], A.hd[l], b, xc, ldc, xa, dotv, part);
         else
-          ++tl_launches, k_prolong_smooth1_4<false><<<B * tiles_vec(nl), kThreads, 0, st>>>(
-              nl, B, act, A.wx[l], A.wy[l], A.dinv[l], b, xc, ldc, xa, nullptr, nullptr);
+          ++tl_launches, k_prolong_smooth1_4<false, __nv_bfloat16><<<B * tiles_vec(nl), kThreads, 0, st>>>(
+              nl, B, act, A.hx[l], A.hy[l], A.hd[l], b, xc, ldc, xa, nullptr, nullptr);
       } else {
         if (l == 0 && dotv)
           ++tl_launches, k_prolong_smooth1<T, true><<<B * tiles_interior(nl), kThreads, 0, st>>>(
@@ -1362,10 +1409,12 @@ cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st, c
     const int nl = n >> l;
     if (l == 0)
       ++tl_launches, k_weights<T, double><<<B * tiles_padded(nl), kThreads, 0, st>>>(nl, B, s.a, astride, A.wx[0], A.wy[0],
-                                                                     A.dinv[0], om, A.wx64, A.wy64, nullptr, A.ss);
+                                                                     A.dinv[0], om, A.wx64, A.wy64, nullptr, A.ss,
+                                                                     A.hx[0], A.hy[0], A.hd[0]);
     else
       ++tl_launches, k_weights<T, T><<<B * tiles_padded(nl), kThreads, 0, st>>>(nl, B, A.cells[l], (size_t)2 * nl * nl, A.wx[l],
-                                                                A.wy[l], A.dinv[l], om, nullptr, nullptr, nullptr, nullptr);
+                                                                A.wy[l], A.dinv[l], om, nullptr, nullptr, nullptr, nullptr,
+                                                                A.hx[l], A.hy[l], A.hd[l]);
     LAUNCH_CHECK();
     if (l >= A.Ls) continue;
     const int m = nl / 2;

@@ -2,6 +2,7 @@
 
     python -m paper_2103_03407_gb300.profile_level --workload mlqmc4_h16_128 --level 1 --points 64 \
         --precision mixed [--repeat 2]
+    python -m paper_2103_03407_gb300.profile_level --workload mlqmc6_h32_1024 --level 0 ... --level 5 --fraction 32
 
 Prints the device time and iteration statistics of each evaluation as JSON lines.
 
@@ -27,11 +28,15 @@ def main():
     ap.add_argument("--workload", default="mlqmc4_h16_128")
     ap.add_argument("--level", type=int, action="append")
     ap.add_argument("--points", type=int, default=64)
+    ap.add_argument("--fraction", type=int, default=0,
+                    help="evaluate N_l / F points of every level instead of --points (F = 32: one benchmark step)")
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--stream-min", type=int, default=0, help="fine meshes from 1/n on run in the streaming tier")
     ap.add_argument("--threads", type=int, default=0, help="threads per CTA of the per-sample kernel (0: default)")
     ap.add_argument("--nu", type=int, default=0, help="Jacobi steps per side of the V-cycle (0: default)")
+    ap.add_argument("--tol-inner", type=float, default=0.0,
+                    help="relative reduction of each inner solve (0: the library's default)")
     ap.add_argument("--gemm", type=int, nargs=3, metavar=("N", "S", "B"),
                     help="time the coefficient evaluation alone on mesh 1/N with S terms for B samples")
     a = ap.parse_args()
@@ -57,16 +62,18 @@ def main():
         ctx.mq_set_tier(a.stream_min)
     if a.nu:
         ctx.mq_set_smoothing(a.nu)
+    if a.tol_inner:
+        ctx.mq_set_solver_options(a.tol_inner, 0, 0)
     if a.threads:
         for l in range(len(wl.levels)):
             ctx.mq_set_cta_threads(l, a.threads)
     for l in a.level or [len(wl.levels) - 1]:
-        n = min(a.points, wl.levels[l].N)
+        n = max(1, wl.levels[l].N // a.fraction) if a.fraction else min(a.points, wl.levels[l].N)
         for _ in range(a.repeat):
             ctx.mq_eval_level(l, 0, n, per_sample=False)
             st = ctx.mq_get_stats()
             print(json.dumps({"level": l, "points": n, "samples": n * wl.levels[l].R, "stream_min": a.stream_min,
-                              "threads_req": a.threads, "nu": a.nu, **st}))
+                              "threads_req": a.threads, "nu": a.nu, "tol_inner": a.tol_inner, **st}))
     ctx.close()
 
 
