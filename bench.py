@@ -485,16 +485,19 @@ def stream_bytes(wl, level, st, prec, samples):
     return per * samples
 
 
-# ncu DRAM traffic of the per-sample kernel's launch on a level, valid only for the kernel source
-# it was measured on (profiles/sample_kernel_mlqmc4_h16_128_level0.md; one full-size launch)
-SAMPLE_KERNEL_TRAFFIC = {"source_sha256": "ea104697312beb4c1049dd2e4748a39fb69098d045db313210a6548ea7eab8d1",
-                         "level": 0, "precision": "mixed", "bytes_per_launch": 366.075648e6 + 27.624704e6}
+# ncu DRAM traffic of the per-sample kernel's launch on a level (one launch of the benchmark's size:
+# level 1 of the six-level workload, 4,096 samples; summarised under profiles/), valid only for the
+# kernel source it was measured on
+SAMPLE_KERNEL_TRAFFIC = {"source_sha256": "79b7f26fcfff6e0ece6d816e2ffaa1432af5cc4ba599a1a77e8a7e9a2f01b84c",
+                         "level": 1, "precision": "mixed", "bytes_per_launch": 139.522816e6 + 41.857024e6}
 
 
-# ncu DRAM traffic of the operator sweep k_minres_q per algorithmic byte (one launch on the level
-# with mesh 1/256 of the six-level workload, 1,024 samples; profiles/stream_kernels_*.md), valid only
-# for the kernel source it was measured on
-KMINRES_TRAFFIC = {"source_sha256": "", "dram_per_algorithmic": None}
+# ncu DRAM traffic of the operator sweep k_minres_q per algorithmic byte: one launch with the pending
+# MINRES update (10 arrays per node) on mesh 1/1024, 16 samples of the six-level workload's finest
+# level (summarised under profiles/), scaled to a launch by its algorithmic bytes; valid only for
+# the kernel source it was measured on
+KMINRES_TRAFFIC = {"source_sha256": "47e8fcd64bdf97ee76ecf3334ac3eacbba70c44c2530ac33e5a96f3ca4665d66",
+                   "dram_per_algorithmic": (471.806976e6 + 171.258368e6) / (16 * 1023 * 1023 * 40)}
 
 
 def _stream_source_hash():

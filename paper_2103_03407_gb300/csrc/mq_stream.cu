@@ -141,7 +141,10 @@ __global__ void k_weights(int n, int B, const S* __restrict__ cells, size_t cstr
   const size_t V = ssz(n);
   const int ld = sld(n);
   int bad = 0;
-  float amax = 0.0f;
+  // largest coefficient as the bit pattern of a double: positive doubles order as their bit patterns
+  // (the coefficient checks run on the integer units; GB300 has few FP64 units)
+  long long mbits = 0;
+  constexpr long long kInfBits = 0x7ff0000000000000LL;
   for (int k = 0; k < kPer; ++k) {
     const size_t q = (size_t)ch * kTile + threadIdx.x + k * kThreads;
     if (q >= V) break;
@@ -153,15 +156,15 @@ __global__ void k_weights(int n, int B, const S* __restrict__ cells, size_t cstr
     if (i <= n - 1 && j >= 1 && j <= n - 1) a64 = 0.5 * (LO(i, j) + UP(i, j - 1));
     if (i >= 1 && i <= n - 1 && j <= n - 1) c64 = 0.5 * (UP(i, j) + LO(i - 1, j));
     const T a = T(a64), c = T(c64);
-    if (i <= n - 1 && j <= n - 1) {  // every triangle once
-      bad |= !(LO(i, j) > 0.0) | !(UP(i, j) > 0.0);
-      amax = fmaxf(amax, (float)fmax(LO(i, j), UP(i, j)) * 1.0001f);
+    if (i <= n - 1 && j <= n - 1) {  // every triangle once: a > 0 and not NaN
+      const long long bl = __double_as_longlong(LO(i, j)), bu = __double_as_longlong(UP(i, j));
+      bad |= !(bl > 0 && bl <= kInfBits) | !(bu > 0 && bu <= kInfBits);
+      mbits = max(mbits, max(bl, bu));
     }
     if (i >= 1 && i <= n - 1 && j >= 1 && j <= n - 1) {
-      const double l0 = LO(i, j), l1 = LO(i - 1, j), l2 = LO(i - 1, j - 1);
-      const double u0 = UP(i, j), u1 = UP(i, j - 1), u2 = UP(i - 1, j - 1);
-      const T we = T(0.5 * (l0 + u1)), ww = T(0.5 * (l1 + u2)), wn = T(0.5 * (u0 + l1)), ws = T(0.5 * (u1 + l2));
-      d = om / (we + ww + wn + ws);  // the damped Jacobi factor omega D^-1
+      // the east and north edges are this node's own (a, c); west and south are the neighbours'
+      const T ww = T(0.5 * (LO(i - 1, j) + UP(i - 1, j - 1))), ws = T(0.5 * (UP(i, j - 1) + LO(i - 1, j - 1)));
+      d = om / (a + ww + c + ws);  // the damped Jacobi factor omega D^-1
     }
     wx[(size_t)b * V + q] = a;
     wy[(size_t)b * V + q] = c;
@@ -178,6 +181,7 @@ __global__ void k_weights(int n, int B, const S* __restrict__ cells, size_t cstr
   }
   if (ss) {
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&ss[b].flags, kFlagBadCoef);
+    float amax = (mbits > 0 && mbits <= kInfBits) ? (float)__longlong_as_double(mbits) * 1.0001f : 0.0f;
     for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
     if ((threadIdx.x & 31) == 0 && amax > 0.0f) atomicMax((int*)&ss[b].amax, __float_as_int(amax));  // positive floats order as ints
   }
