@@ -107,7 +107,7 @@ mq_status mq_destroy(mq_ctx* ctx);
  * (see mq_set_islands; a0 is then unused but must still be positive).  Other families give
  * MQ_EINVAL.  s_max bounds the truncation of every level.  a0 > 0.  Requires a >= a_min > 0 at all
  * centroids (checked per evaluation: a sample with a non-positive value is flagged and the call
- * returns MQ_ENOCONV). */
+ * returns MQ_EINVAL, its outputs written). */
 mq_status mq_set_coefficient(mq_ctx* ctx, double a0, int32_t s_max, int32_t family, double decay);
 
 /* The second test problem of Sec. 5 (coefficient family 2): four islands

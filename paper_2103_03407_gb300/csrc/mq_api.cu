@@ -737,7 +737,7 @@ mq_status timing(mq_ctx* c, int level) {
 
 mq_status flags_status(mq_ctx* c, int fl) {
   if (fl & mq::kFlagBadCoef)
-    return fail(c, MQ_EINVAL, "coefficient a(x, y) <= 0 at a centroid (Assumption A1 violated)");
+    return fail(c, MQ_EINVAL, "coefficient a(x, y) <= 0 (or reaction b(x, y) < 0) at a centroid");
   if (fl & (mq::kFlagEigNoConv | mq::kFlagLinNoConv | mq::kFlagBreakdown))
     return fail(c, MQ_ENOCONV, "%llu sample(s) hit an iteration cap or broke down (flags 0x%x)",
                 (unsigned long long)c->stats.noconv, fl);
@@ -746,8 +746,10 @@ mq_status flags_status(mq_ctx* c, int fl) {
 
 // points per pass so that the coefficient buffers stay within a memory budget
 int points_per_pass(const mq_ctx* c, const LevelGeom& g, int R, int npts) {
-  size_t per_sample = sizeof(double) * ((size_t)2 * g.nf * g.nf + (size_t)2 * g.nc * g.nc +
-                                        (size_t)2 * g.np * g.np + (size_t)g.s + 8 + (size_t)(g.nc + 1) * (g.nc + 1));
+  // coefficient fields of the three meshes (twice with the reaction coefficient of family 2)
+  const size_t fields = (size_t)2 * g.nf * g.nf + (size_t)2 * g.nc * g.nc + (size_t)2 * g.np * g.np;
+  size_t per_sample = sizeof(double) * ((c->family == 2 ? 2 : 1) * fields + (size_t)g.s + 8 +
+                                        (size_t)(g.nc + 1) * (g.nc + 1));
   if (streams(c, g) && g.nf != g.nc)
     per_sample += mq::stream_arena_bytes(g.nf, 1, c->prec == MQ_PREC_MIXED);
   size_t free_b = 0, total_b = 0;
