@@ -825,6 +825,86 @@ __device__ __forceinline__ float4 ldw4(const __nv_bfloat16* p) {
   return make_float4(fa.x, fa.y, fc.x, fc.y);
 }
 
+// CTAs per sample of the vectorised restriction: (m - 1) coarse rows x m/2 pairs of coarse nodes
+__host__ __device__ inline int tiles_pairs(int m) {
+  const long t = (long)(m - 1) * (m / 2);
+  return (int)((t + kThreads - 1) / kThreads);
+}
+
+// V(1,1) down-sweep, vectorised: the same restriction as k_restrict1 for two coarse nodes (2t, 2t+1)
+// of coarse row J per thread.  The thread loads the fine rows 2J-2 .. 2J+2 at columns 4t-4 ..
+// 4t+7 as aligned four-wide vectors (BF16 weights, FP32 right-hand side), forms x1 = om D^-1 b on
+// the 5 x 7 block it needs, the residual b - A x1 at the 13 fine nodes of the two 7-point
+// restrictions, and writes both coarse values.  Columns left of the row start read as zero (the
+// coarse node 0 is the boundary and is not written).
+template <typename WT>
+__global__ void k_restrict1_4(int n, int B, const int* __restrict__ act, const WT* __restrict__ wx,
+                              const WT* __restrict__ wy, const WT* __restrict__ dinv, const float* __restrict__ bb,
+                              float* __restrict__ bc, int ldo) {
+  const int m = n / 2, pairs = m / 2;
+  const int nt = tiles_pairs(m);
+  const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
+  if (b >= B || !act[b]) return;
+  const int g = ch * kThreads + threadIdx.x;
+  const int J = g / pairs + 1, t = g % pairs;
+  if (J > m - 1) return;
+  const int ld = sld(n);
+  const size_t off = (size_t)b * ssz(n);
+  const int c = 4 * t, jc = 2 * J;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  // x1 and r on rows jc-2 .. jc+2 (index 0..4), columns c-2 .. c+4 (index 0..6)
+  float x1[5][7], rr[5][7];
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    const size_t row = off + (size_t)(jc - 2 + r) * ld;
+    const float4 d0 = c ? ldw4(dinv + row + c - 4) : z4, r0 = c ? ld4(bb + row + c - 4) : z4;
+    const float4 d1 = ldw4(dinv + row + c), r1 = ld4(bb + row + c);
+    const float4 d2 = ldw4(dinv + row + c + 4), r2 = ld4(bb + row + c + 4);
+    const float dv[7] = {d0.z, d0.w, d1.x, d1.y, d1.z, d1.w, d2.x};
+    const float rv[7] = {r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, r2.x};
+    (void)r2;
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+      x1[r][q] = dv[q] * rv[q];
+      rr[r][q] = rv[q];
+    }
+  }
+  // weights: w_x on rows jc-1 .. jc+1 and w_y on rows jc-2 .. jc+1, columns c-2 .. c+3 (index 0..5)
+  float wxv[3][6], wyv[4][6];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const size_t row = off + (size_t)(jc - 1 + r) * ld;
+    const float4 a0 = c ? ldw4(wx + row + c - 4) : z4, a1 = ldw4(wx + row + c);
+    const float v[6] = {a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+    for (int q = 0; q < 6; ++q) wxv[r][q] = v[q];
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const size_t row = off + (size_t)(jc - 2 + r) * ld;
+    const float4 a0 = c ? ldw4(wy + row + c - 4) : z4, a1 = ldw4(wy + row + c);
+    const float v[6] = {a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+    for (int q = 0; q < 6; ++q) wyv[r][q] = v[q];
+  }
+  // residual at fine row jc - 2 + r, column c - 2 + q (r = 1..3, q = 1..5)
+  auto res = [&](int r, int q) {
+    const float xq = x1[r][q];
+    return rr[r][q] - (wxv[r - 1][q] * (xq - x1[r][q + 1]) + wxv[r - 1][q - 1] * (xq - x1[r][q - 1]) +
+                       wyv[r][q] * (xq - x1[r + 1][q]) + wyv[r - 1][q] * (xq - x1[r - 1][q]));
+  };
+  float* __restrict__ C = bc + (size_t)b * (size_t)(m + 1) * ldo + (size_t)J * ldo;
+  // coarse node 2t (fine column c: q = 2) and 2t + 1 (fine column c + 2: q = 4)
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int q = 2 + 2 * h;
+    const int I = 2 * t + h;
+    if (I < 1) continue;
+    C[I] = res(2, q) + 0.5f * ((res(2, q + 1) + res(2, q - 1)) + (res(3, q) + res(1, q)) +
+                               (res(3, q + 1) + res(1, q - 1)));
+  }
+}
+
 template <bool DOT, typename WT = float>
 __global__ void k_prolong_smooth1_4(int n, int B, const int* __restrict__ act, const WT* __restrict__ wx,
                                     const WT* __restrict__ wy, const WT* __restrict__ dinv,
@@ -840,9 +920,33 @@ __global__ void k_prolong_smooth1_4(int n, int B, const int* __restrict__ act, c
   int j, c0;
   if (vec_walk(n, ch, j, c0)) {
     const size_t p = off + (size_t)j * ld + c0;
-    auto pc = [&](int ii, int jj) {  // P xc at fine node (ii, jj)
-      const int c = (jj >> 1) * ldc + (ii >> 1);
-      return 0.5f * (XC[c] + XC[c + (ii & 1) + (jj & 1) * ldc]);
+    // The coarse values under the tile: rows Jb .. Jb + 2 (Jb = (j - 1) / 2), columns c0/2 - 1 ..
+    // c0/2 + 2, loaded once (12 loads for the 14 interpolated nodes).  P xc at fine node (ii, jj) is
+    // the mean of the coarse values at the two ends of the coarse edge through it: row jj/2, column
+    // ii/2 and row jj/2 + (jj mod 2), column ii/2 + (ii mod 2).
+    const int Jb = (j - 1) >> 1, cb = (c0 >> 1) - 1, mh = n >> 1;
+    float X[3][4];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        X[r][q] = (Jb + r <= mh && cb + q >= 0) ? XC[(Jb + r) * ldc + cb + q] : 0.0f;
+    const bool ev = (j & 1) == 0;
+    // the two coarse rows of each fine row j - 1, j, j + 1
+    float Am[4], Bm[4], A0[4], B0[4], Ap[4], Bp[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      Am[q] = X[0][q];
+      Bm[q] = ev ? X[1][q] : X[0][q];
+      A0[q] = ev ? X[1][q] : X[0][q];
+      B0[q] = X[1][q];
+      Ap[q] = X[1][q];
+      Bp[q] = ev ? X[2][q] : X[1][q];
+    }
+    // fine column c0 + k, k = -1 .. 4: coarse column index (relative to cb) and parity
+    auto pcr = [&](const float (&A)[4], const float (&Bv)[4], int k) {
+      const int q = ((k + 4) >> 1) - 1, o = k & 1;
+      return 0.5f * (A[q] + Bv[q + o]);
     };
     const bool first = c0 == 0;
     const float4 dc = ldw4(dinv + p), rc = ld4(bb + p);
@@ -852,13 +956,13 @@ __global__ void k_prolong_smooth1_4(int n, int B, const int* __restrict__ act, c
     const float wwest = first ? 0.0f : wget<float>(wx + p - 1);
     // t along row j at columns c0-1 .. c0+4, and at rows j+1, j-1 under the four nodes
     float tr[kVec + 2], tn[kVec], ts[kVec];
-    tr[0] = first ? 0.0f : wget<float>(dinv + p - 1) * bb[p - 1] + pc(c0 - 1, j);
-    tr[kVec + 1] = wget<float>(dinv + p + kVec) * bb[p + kVec] + pc(c0 + kVec, j);
+    tr[0] = first ? 0.0f : wget<float>(dinv + p - 1) * bb[p - 1] + pcr(A0, B0, -1);
+    tr[kVec + 1] = wget<float>(dinv + p + kVec) * bb[p + kVec] + pcr(A0, B0, kVec);
 #pragma unroll
     for (int k = 0; k < kVec; ++k) {
-      tr[k + 1] = at(dc, k) * at(rc, k) + pc(c0 + k, j);
-      tn[k] = at(dn, k) * at(rn, k) + pc(c0 + k, j + 1);
-      ts[k] = at(ds, k) * at(rs, k) + pc(c0 + k, j - 1);
+      tr[k + 1] = at(dc, k) * at(rc, k) + pcr(A0, B0, k);
+      tn[k] = at(dn, k) * at(rn, k) + pcr(Ap, Bp, k);
+      ts[k] = at(ds, k) * at(rs, k) + pcr(Am, Bm, k);
     }
     float o[kVec];
 #pragma unroll
@@ -1251,6 +1355,14 @@ cudaError_t vcycle_stream(Arena<T>& A, const T* b0, T* x0, const int* act, T om,
       const T* b = l ? A.b[l] : b0;
       T* bc = (l + 1 < A.Ls) ? A.b[l + 1] : A.bsub;
       const int ldo = (l + 1 < A.Ls) ? sld(nl / 2) : nl / 2 + 1;
+      if constexpr (sizeof(T) == sizeof(float)) {
+        if (A.hx[l]) {
+          ++tl_launches, k_restrict1_4<__nv_bfloat16><<<B * tiles_pairs(nl / 2), kThreads, 0, st>>>(
+              nl, B, act, A.hx[l], A.hy[l], A.hd[l], b, bc, ldo);
+          LAUNCH_CHECK();
+          continue;
+        }
+      }
       if (A.hx[l])
         ++tl_launches, k_restrict1<T, __nv_bfloat16><<<B * tiles_interior(nl / 2), kThreads, 0, st>>>(
             nl, B, act, A.hx[l], A.hy[l], A.hd[l], b, bc, ldo);
