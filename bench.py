@@ -53,9 +53,11 @@ def parse():
     ap.add_argument("--baseline-seconds", type=float, default=20.0)
     ap.add_argument("--fraction", type=int, default=0,
                     help="evaluate 1/F of every level's points per step (0: the workload's default)")
-    ap.add_argument("--schedule", default="sequential", choices=["concurrent", "sequential"],
-                    help="levels one after another (clean per-kernel timing for the rooflines), or all "
-                         "at once on their own streams (mq_eval_levels_device)")
+    ap.add_argument("--schedule", default="graph", choices=["graph", "concurrent", "sequential"],
+                    help="graph: every step one replay of one CUDA graph holding all levels' windows (the "
+                         "headline; one process); sequential: levels one after another through the host "
+                         "API; concurrent: all levels at once on their own streams (mq_eval_levels_device). "
+                         "The sequential run always times the per-kernel rooflines")
     return ap.parse_args()
 
 
@@ -496,8 +498,8 @@ SAMPLE_KERNEL_TRAFFIC = {"source_sha256": "79b7f26fcfff6e0ece6d816e2ffaa1432af5c
 # MINRES update (10 arrays per node) on mesh 1/1024, 16 samples of the six-level workload's finest
 # level (summarised under profiles/), scaled to a launch by its algorithmic bytes; valid only for
 # the kernel source it was measured on
-KMINRES_TRAFFIC = {"source_sha256": "47e8fcd64bdf97ee76ecf3334ac3eacbba70c44c2530ac33e5a96f3ca4665d66",
-                   "dram_per_algorithmic": (471.806976e6 + 171.258368e6) / (16 * 1023 * 1023 * 40)}
+KMINRES_TRAFFIC = {"source_sha256": "43cdf27c83b8e549f3e98f6af50118bf28bd9f868c837d36d752401f599cf13b",
+                   "dram_per_algorithmic": (471.805440e6 + 170.703360e6) / (16 * 1023 * 1023 * 40)}
 
 
 def _stream_source_hash():
@@ -611,34 +613,43 @@ def main():
     torch.cuda.synchronize()
     F = step_fraction(wl, args)
     samples = step_samples(wl, F)  # samples per step (every level's window, every shift)
+    use_graph = args.schedule == "graph" and world == 1
     with torch.cuda.stream(stream):
         with sampler:
             ctx, ms, timing, kstats, outs, launches, lsums, probe = time_device(
                 binding, torch, wl, args.precision, args.steps, args.warmup, stream, F, rank=rank, world=world,
-                sequential=args.schedule == "sequential")
+                sequential=args.schedule != "concurrent")
     # one exchange of the per-level shift sums: the estimate over every rank's shifts
     estimate = merged_estimate(binding, [x[0] for x in lsums], [x[1] for x in lsums], world,
                                shared=wl.extra.get("shared", False))
     if world > 1:
         torch.distributed.barrier()
     ms = max_over_ranks(ms, world, "cuda")
-    value = whole_job_rate(samples, world, args.steps, ms)
-    dof_rate = whole_job_rate(fine_dof_solves(wl) / F, world, args.steps, ms)
+    seq_value = whole_job_rate(samples, world, args.steps, ms)
+    graph = None
+    if use_graph or (not args.no_graph and world == 1 and args.schedule == "sequential"):
+        # the graph schedule on the same windows, with its own clock record (the headline when chosen)
+        gsampler = ClockSampler(local)
+        with torch.cuda.stream(stream):
+            with gsampler:
+                graph = time_graph(binding, torch, wl, args.precision, args.steps, args.warmup, stream, F, outs)
+        graph["clocks"] = gsampler.summary()
+    if use_graph:
+        value, ms_step, head_clocks = graph["value"], graph["ms_per_step"], graph["clocks"]
+    else:
+        value, ms_step, head_clocks = seq_value, ms / args.steps, None
+    dof_rate = fine_dof_solves(wl) / F * world / (ms_step / 1e3)
     plain = None
     if not args.no_plain and args.precision == "mixed" and rank == 0:
         # the plain FP64 GPU path on the same steps (same windows) and warm-up
         with torch.cuda.stream(stream):
             ctxp, msp, _, _, outs_p, _, _, _ = time_device(binding, torch, wl, "fp64", args.steps, args.warmup,
-                                                           stream, F, sequential=args.schedule == "sequential")
+                                                           stream, F, sequential=args.schedule != "concurrent")
         ctxp.close()
         plain = {"value": samples * args.steps / (msp / 1e3), "unit": "samples/s", "ms_per_step": msp / args.steps,
                  "steps": args.steps, "warmup": args.warmup,
                  "max_rel_diff_mixed_vs_fp64": max_rel_diff(outs, outs_p),
                  "note": "per-sample results of the last timed step of both paths compared"}
-    graph = None
-    if not args.no_graph and world == 1 and args.schedule == "sequential":
-        with torch.cuda.stream(stream):
-            graph = time_graph(binding, torch, wl, args.precision, args.steps, args.warmup, stream, F, outs)
     e2e = None
     if not args.no_e2e:
         steps_e2e = max(1, args.steps)
@@ -657,7 +668,7 @@ def main():
     win = windows(wl, F, 0)
     # samples per launch: all samples a level evaluated in the timed region over its launches
     per_launch = [wl.levels[l].R * (win[l][1] - win[l][0]) * args.steps / max(1, timing[l][2]) for l in range(nl)]
-    clocks = sampler.summary()
+    clocks = head_clocks or sampler.summary()
     top = int(np.argmax(percta_ms))
     fp64_peak = None
     try:
@@ -674,12 +685,18 @@ def main():
                        if stream_ms[stop] > 0 else None)
     result = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
-        "config": dict(workload_config(wl, args.precision, world, F), schedule=args.schedule),
+        "config": dict(workload_config(wl, args.precision, world, F),
+                       schedule="graph" if use_graph else ("concurrent" if args.schedule == "concurrent" else
+                                                           "sequential")),
         "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "roofline_stream": roofline_stream,
         "roofline_sample_kernel": roofline_sample, "fp64_peak_measured_tflops": fp64_peak,
         "graph_schedule": graph,
+        "sequential_schedule": {"value": seq_value, "unit": "samples/s", "ms_per_step": ms / args.steps,
+                                "clocks": sampler.summary(),
+                                "note": "the same steps level by level through the host API; the per-kernel "
+                                        "rooflines, per-level timings and gpu_launches come from this run"},
         "clocks": clocks,
         "per_level": [{"level": l, "kernel_ms": coef_ms[l] + sample_ms[l], "coef_ms": coef_ms[l],
                        "sample_ms": sample_ms[l], "percta_ms": percta_ms[l], "stream_ms": stream_ms[l],

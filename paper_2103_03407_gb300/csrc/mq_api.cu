@@ -467,10 +467,14 @@ LevelGeom geom(const mq_ctx* c, int level) {
   return g;
 }
 
-// whether the fine solve of mesh g.nf runs in the streaming tier (whose kernels carry no reaction
-// term: the second test problem solves in the per-sample kernel)
+// Jacobi sweeps per side of the streaming tier's V-cycle (V(1,1) unless set)
+int stream_nu(const mq_ctx* c, const LevelGeom& g) { return g.nu > 0 ? g.nu : (c->opt_nu > 0 ? c->opt_nu : 1); }
+
+// whether the fine solve of mesh g.nf runs in the streaming tier (whose kernels carry the reaction
+// term of the second test problem on the FP32 path with V(1,1) smoothing only)
 bool streams(const mq_ctx* c, const LevelGeom& g) {
-  if (g.direct_f || c->family == 2) return false;
+  if (g.direct_f) return false;
+  if (c->family == 2 && !(c->prec == MQ_PREC_MIXED && stream_nu(c, g) == 1)) return false;
   if (g.tier >= 0) return g.tier == 1;
   return g.nf >= stream_threshold(c);
 }
@@ -485,7 +489,8 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
   mq_status st;
   const bool given = c->reuse && level >= 1;  // coarse pair and lambda^{l-1} come from the store
   const bool rxn = c->family == 2;            // reaction term b u
-  if (rxn && g.tier == 1) return fail(c, MQ_EINVAL, "the streaming tier carries no reaction term");
+  if (rxn && g.tier == 1 && !streams(c, g))
+    return fail(c, MQ_EINVAL, "the streaming tier carries the reaction term only in mixed precision with V(1,1)");
   const size_t nTf = (size_t)2 * g.nf * g.nf, nTc = (size_t)2 * g.nc * g.nc, nTp = (size_t)2 * g.np * g.np;
   const size_t Vc = (size_t)(g.nc + 1) * (g.nc + 1);
   if (!given && (st = grow(c, c->ac, B * nTc * sizeof(double))) != MQ_OK) return st;
@@ -630,7 +635,9 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
   if (!c->capturing) MQ_CUDA(c, cudaEventRecord(c->ev[3], c->stream));
   if (ext) {
     const uint64_t launched0 = mq::stream_launches();
-    if ((st = grow(c, c->arena, mq::stream_arena_bytes(g.nf, (int)B, mixed))) != MQ_OK) return st;
+    if ((st = grow(c, c->arena, mq::stream_arena_bytes(std::max(p.mode_f == 2 ? g.nf : 0, p.mode_p == 2 ? g.np : 0),
+                                                       (int)B, mixed, rxn))) != MQ_OK)
+      return st;
     mq::StreamSolve s{};
     mq::StreamGraph sg{{c->gbody[0], c->gbody[1]}, (int*)c->gcount.p};
     s.nc = g.nc;
@@ -648,12 +655,14 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
     s.max_inner = p.max_inner_it;
     s.max_outer = p.max_outer;
     s.omega = p.omega;
-    s.nu = g.nu > 0 ? g.nu : (c->opt_nu > 0 ? c->opt_nu : 1);
+    s.nu = stream_nu(c, g);
     s.probe = (c->probe_on && !c->capturing) ? &c->probe : nullptr;
     s.qoi = c->qoi;
+    s.b = nullptr;
     if (p.mode_f == 2) {
       s.n = g.nf;
       s.a = (const double*)c->af.p;
+      s.b = rxn ? (const double*)c->bf.p : nullptr;
       s.lam_out = (double*)c->out.p + 1;
       s.iters_out = (int*)c->stat.p + 1;
       s.outer_out = (int*)c->outer.p + 0;
@@ -662,6 +671,7 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
     if (p.mode_p == 2 && !given) {
       s.n = g.np;
       s.a = (const double*)c->ap.p;
+      s.b = rxn ? (const double*)c->bp.p : nullptr;
       s.lam_out = (double*)c->out.p + 2;
       s.iters_out = (int*)c->stat.p + 2;
       s.outer_out = (int*)c->outer.p + 1;
@@ -751,7 +761,7 @@ int points_per_pass(const mq_ctx* c, const LevelGeom& g, int R, int npts) {
   size_t per_sample = sizeof(double) * ((c->family == 2 ? 2 : 1) * fields + (size_t)g.s + 8 +
                                         (size_t)(g.nc + 1) * (g.nc + 1));
   if (streams(c, g) && g.nf != g.nc)
-    per_sample += mq::stream_arena_bytes(g.nf, 1, c->prec == MQ_PREC_MIXED);
+    per_sample += mq::stream_arena_bytes(g.nf, 1, c->prec == MQ_PREC_MIXED, c->family == 2);
   size_t free_b = 0, total_b = 0;
   size_t budget = (size_t)24 << 30;
   if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) budget = std::min<size_t>((size_t)(0.4 * free_b), (size_t)64 << 30);
@@ -1396,6 +1406,8 @@ mq_status mq_autotune_level(mq_ctx* c, int32_t level, uint32_t points, const cha
   for (int tier : tiers)
     for (int th : thr)
       for (int nu = 1; nu <= 2 && result == MQ_OK; ++nu) {
+        // the streaming tier takes the reaction term only in mixed precision with V(1,1)
+        if (tier == 1 && c->family == 2 && (c->prec != MQ_PREC_MIXED || nu != 1)) continue;
         if ((result = mq_set_level_config(c, level, tier, th, nu)) != MQ_OK) break;
         double ms = 1e300;
         for (int rep = 0; rep < 2; ++rep) {  // the first run also builds tables and buffers

@@ -102,8 +102,9 @@ __host__ __device__ void carve_mg(Carver& c, int n, MGDesc<T>& d, bool reaction 
 // Same hierarchy with the operator arrays (weights, inverse diagonals) taken from carver w and
 // the vectors (t, x, b) and building buffers taken from carver v.
 template <typename T>
-__host__ __device__ void carve_mg_split(Carver& w, Carver& v, int n, MGDesc<T>& d) {
+__host__ __device__ void carve_mg_split(Carver& w, Carver& v, int n, MGDesc<T>& d, bool reaction = false) {
   d.L = ilog2(n);
+  for (int l = 0; l < kMaxMG; ++l) d.dr[l] = nullptr;
   for (int l = 0; l < d.L; ++l) {
     const int nl = n >> l;
     d.n[l] = nl;
@@ -111,6 +112,7 @@ __host__ __device__ void carve_mg_split(Carver& w, Carver& v, int n, MGDesc<T>& 
     d.wx[l] = w.take<T>(V);
     d.wy[l] = w.take<T>(V);
     d.dinv[l] = w.take<T>(V);
+    d.dr[l] = reaction ? w.take<T>(V) : nullptr;
     d.t[l] = v.take<T>(V);
     d.x[l] = l ? v.take<T>(V) : nullptr;
     d.b[l] = l ? v.take<T>(V) : nullptr;
@@ -118,10 +120,10 @@ __host__ __device__ void carve_mg_split(Carver& w, Carver& v, int n, MGDesc<T>& 
   const size_t cells = n >= 4 ? (size_t)2 * (n / 2) * (n / 2) : 1;
   d.cell[0] = v.take<T>(cells);
   d.cell[1] = v.take<T>(cells);
+  d.rcell[0] = reaction ? v.take<T>(cells) : nullptr;
+  d.rcell[1] = reaction ? v.take<T>(cells) : nullptr;
   d.cinv = w.take<T>(81);
   d.Lc = d.L >= 2 ? d.L - 2 : d.L - 1;
-  for (int l = 0; l < kMaxMG; ++l) d.dr[l] = nullptr;
-  d.rcell[0] = d.rcell[1] = nullptr;
 }
 
 // ---------------------------------------------------------------------------------------------

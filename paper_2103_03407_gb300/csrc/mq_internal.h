@@ -86,6 +86,8 @@ struct StreamSolve {
   KernelProbe* probe;      // NULL, or the live timing of the operator sweep
   int qoi;                 // 1: lam_out receives G(u^h) = |integral of w| / ||w||_L2 instead of the
                            // Rayleigh quotient
+  const double* b;         // NULL, or [B][2 n^2] reaction coefficients: the operator is A + B (FP32 path,
+                           // V(1,1) smoothing only; cudaErrorNotSupported otherwise)
 };
 // Graph mode of the streaming solve: the refinement and MINRES loops become conditional WHILE nodes
 // of the CUDA graph being captured on the solve's stream (no host reads); their bodies are
@@ -94,7 +96,7 @@ struct StreamGraph {
   cudaStream_t body[2];
   int* counters;
 };
-size_t stream_arena_bytes(int n, int B, int mixed);
+size_t stream_arena_bytes(int n, int B, int mixed, int reaction = 0);
 cudaError_t stream_solve(const StreamSolve& s, int mixed, void* arena, cudaStream_t st,
                          const StreamGraph* sg = nullptr);
 // kernels the streaming tier has launched from the calling thread (monotone counter)

@@ -100,6 +100,7 @@ struct SS {  // per-sample solver scalars
   double xax, xmx;  // x.Ax and x.Mx of the last FP64 residual pass (the Rayleigh quotient)
   double xsum;      // sum of the nodal values of x64 in that pass (h^2 xsum = integral of x)
   float amax;     // largest centroid coefficient (for the bound ||A - sigma M|| <= 8 amax + sigma h^2)
+  float bmax;     // largest reaction coefficient (the bound gains bmax h^2)
   int act_outer;  // refinement still running
   int act;        // inner MINRES running
   int pend;       // a w/x update is pending
@@ -127,12 +128,18 @@ __device__ __forceinline__ void tile_partials(A (&v)[NV], double* part, size_t s
 // setup
 // weights and inverse diagonal of mesh n from per-triangle coefficients (lower plane, upper plane)
 // (with hx: BF16 copies of the weights and of om D^-1 for the V(1,1) sweeps of the FP32 path)
+// (with rcells: the reaction term of the second test problem of Sec. 5 -- om D^-1 includes the
+// lumped reaction h^2/6 sum_{T at p} b_T, written in BF16 to hr for the V(1,1) sweeps; with rxo also
+// the reaction's FP32 edge weights for the operator sweep (b averaged over the two triangles of
+// the edges to E, N and NE) and the largest b into ss)
 template <typename T, typename S>
 __global__ void k_weights(int n, int B, const S* __restrict__ cells, size_t cstride, T* __restrict__ wx,
                           T* __restrict__ wy, T* __restrict__ dinv, T om, double* __restrict__ wx64,
                           double* __restrict__ wy64, const int* __restrict__ act, SS<T>* ss,
                           __nv_bfloat16* __restrict__ hx = nullptr, __nv_bfloat16* __restrict__ hy = nullptr,
-                          __nv_bfloat16* __restrict__ hd = nullptr) {
+                          __nv_bfloat16* __restrict__ hd = nullptr, const S* __restrict__ rcells = nullptr,
+                          __nv_bfloat16* __restrict__ hr = nullptr, T* __restrict__ rxo = nullptr,
+                          T* __restrict__ ryo = nullptr, T* __restrict__ rdo = nullptr) {
   const int nt = tiles_padded(n);
   const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
   if (b >= B || (act && !act[b])) return;
@@ -141,6 +148,10 @@ __global__ void k_weights(int n, int B, const S* __restrict__ cells, size_t cstr
   const size_t V = ssz(n);
   const int ld = sld(n);
   int bad = 0;
+  const S* rlo = rcells ? rcells + (size_t)b * cstride : nullptr;
+  const S* rup = rcells ? rlo + (size_t)n * n : nullptr;
+  const double hr6 = 1.0 / (6.0 * (double)n * (double)n);
+  long long rbits = 0;  // largest reaction coefficient (bit pattern)
   // largest coefficient as the bit pattern of a double: positive doubles order as their bit patterns
   // (the coefficient checks run on the integer units; GB300 has few FP64 units)
   long long mbits = 0;
@@ -161,10 +172,28 @@ __global__ void k_weights(int n, int B, const S* __restrict__ cells, size_t cstr
       bad |= !(bl > 0 && bl <= kInfBits) | !(bu > 0 && bu <= kInfBits);
       mbits = max(mbits, max(bl, bu));
     }
+    T dr = T(0);
+    if (rlo) {
+      auto RL = [&](int ii, int jj) { return (double)rlo[jj * n + ii]; };
+      auto RU = [&](int ii, int jj) { return (double)rup[jj * n + ii]; };
+      if (i <= n - 1 && j <= n - 1) {  // b >= 0 and not NaN
+        const long long bl = __double_as_longlong(RL(i, j)), bu = __double_as_longlong(RU(i, j));
+        bad |= !(bl >= 0 && bl <= kInfBits) | !(bu >= 0 && bu <= kInfBits);
+        rbits = max(rbits, max(bl, bu));
+      }
+      if (i >= 1 && i <= n - 1 && j >= 1 && j <= n - 1)
+        dr = T(hr6 * (RL(i, j) + RU(i, j) + RL(i - 1, j) + RU(i, j - 1) + RL(i - 1, j - 1) + RU(i - 1, j - 1)));
+      if (rxo) {
+        rxo[(size_t)b * V + q] = (i <= n - 1 && j >= 1 && j <= n - 1) ? T(0.5 * (RL(i, j) + RU(i, j - 1))) : T(0);
+        ryo[(size_t)b * V + q] = (i >= 1 && i <= n - 1 && j <= n - 1) ? T(0.5 * (RU(i, j) + RL(i - 1, j))) : T(0);
+        rdo[(size_t)b * V + q] = (i <= n - 1 && j <= n - 1) ? T(0.5 * (RL(i, j) + RU(i, j))) : T(0);
+      }
+      if (hr) hr[(size_t)b * V + q] = __float2bfloat16_rn((float)dr);
+    }
     if (i >= 1 && i <= n - 1 && j >= 1 && j <= n - 1) {
       // the east and north edges are this node's own (a, c); west and south are the neighbours'
       const T ww = T(0.5 * (LO(i - 1, j) + UP(i - 1, j - 1))), ws = T(0.5 * (UP(i, j - 1) + LO(i - 1, j - 1)));
-      d = om / (a + ww + c + ws);  // the damped Jacobi factor omega D^-1
+      d = om / (a + ww + c + ws + dr);  // the damped Jacobi factor omega D^-1 (with the lumped reaction)
     }
     wx[(size_t)b * V + q] = a;
     wy[(size_t)b * V + q] = c;
@@ -184,6 +213,11 @@ __global__ void k_weights(int n, int B, const S* __restrict__ cells, size_t cstr
     float amax = (mbits > 0 && mbits <= kInfBits) ? (float)__longlong_as_double(mbits) * 1.0001f : 0.0f;
     for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
     if ((threadIdx.x & 31) == 0 && amax > 0.0f) atomicMax((int*)&ss[b].amax, __float_as_int(amax));  // positive floats order as ints
+    if (rlo) {
+      float bmx = (rbits > 0 && rbits <= kInfBits) ? (float)__longlong_as_double(rbits) * 1.0001f : 0.0f;
+      for (int o = 16; o > 0; o >>= 1) bmx = fmaxf(bmx, __shfl_xor_sync(0xffffffffu, bmx, o));
+      if ((threadIdx.x & 31) == 0 && bmx > 0.0f) atomicMax((int*)&ss[b].bmax, __float_as_int(bmx));
+    }
   }
 }
 
@@ -284,7 +318,7 @@ __host__ __device__ inline double residual_target(double tol, double bnorm, doub
 
 template <typename T>
 __device__ inline double knorm_of(const SS<T>& S, int n, double sigma) {
-  return 8.0 * (double)S.amax + sigma / ((double)n * n);
+  return 8.0 * (double)S.amax + ((double)S.bmax + sigma) / ((double)n * n);
 }
 
 // start of a refinement step: samples above the residual target run an inner solve (target: tol
@@ -584,28 +618,31 @@ __global__ void k_smooth(int n, int B, const int* __restrict__ act, const T* __r
   if (DOT) tile_partials<1, T>(acc, part, (size_t)b * nt + ch);
 }
 
-// per-sample operator arrays of the meshes 1/ns .. 1/2 (sizes from carve_mg_split)
+// per-sample operator arrays of the meshes 1/ns .. 1/2 (sizes from carve_mg_split; with the
+// reaction term also the lumped reaction of every level)
 template <typename T>
-__host__ __device__ size_t sub_weights_bytes(int ns) {
+__host__ __device__ size_t sub_weights_bytes(int ns, bool rxn = false) {
   Carver w(nullptr), v(nullptr);
   MGDesc<T> d;
-  carve_mg_split<T>(w, v, ns, d);
+  carve_mg_split<T>(w, v, ns, d, rxn);
   return (w.used() + 255) & ~(size_t)255;
 }
 template <typename T>
-__host__ __device__ size_t sub_vectors_bytes(int ns) {
+__host__ __device__ size_t sub_vectors_bytes(int ns, bool rxn = false) {
   Carver w(nullptr), v(nullptr);
   MGDesc<T> d;
   v.take<T>(gsz(ns));
   v.take<T>(gsz(ns));
-  carve_mg_split<T>(w, v, ns, d);
+  carve_mg_split<T>(w, v, ns, d, rxn);
   return v.used() + 64;
 }
 
-// builds the operator arrays of meshes 1/ns .. 1/2 of every sample once per solve
+// builds the operator arrays of meshes 1/ns .. 1/2 of every sample once per solve (rcells: the
+// reaction coefficient on the same cells, or NULL)
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_sub_build(int ns, int B, const T* __restrict__ cells,
-                                                        char* __restrict__ subw, size_t wbytes) {
+                                                        char* __restrict__ subw, size_t wbytes,
+                                                        const T* __restrict__ rcells) {
   extern __shared__ __align__(16) char sm[];
   __shared__ double red[kRedSlots];
   __shared__ MGDesc<T> mg;
@@ -615,10 +652,10 @@ __global__ void __launch_bounds__(kThreads) k_sub_build(int ns, int B, const T* 
   MGDesc<T> d;
   v.take<T>(gsz(ns));
   v.take<T>(gsz(ns));
-  carve_mg_split<T>(w, v, ns, d);
+  carve_mg_split<T>(w, v, ns, d, rcells != nullptr);
   if (threadIdx.x == 0) mg = d;
   __syncthreads();
-  build_mg<T, T>(mg, cells + (size_t)b * 2 * ns * ns, ns, red);
+  build_mg<T, T>(mg, cells + (size_t)b * 2 * ns * ns, ns, red, rcells ? rcells + (size_t)b * 2 * ns * ns : nullptr);
 }
 
 // meshes 1/ns .. 1/2 of one sample inside one CTA: x = B^{-1} b (operator arrays read from the
@@ -627,7 +664,8 @@ template <typename T>
 __global__ void __launch_bounds__(kSubThreads) k_subcycle(int ns, int B, const int* __restrict__ act,
                                                        const char* __restrict__ subw, size_t wbytes,
                                                        const T* __restrict__ bin, T* __restrict__ xout, int ldio,
-                                                       int nu, T om, double* part, const T* __restrict__ dotv) {
+                                                       int nu, T om, double* part, const T* __restrict__ dotv,
+                                                       int rxn) {
   // bin / xout: rows of ldio entries (ns + 1 for the sub-cycle's own arrays, sld(ns) when the
   // whole V-cycle of a streamed mesh runs here); the shared-memory copies have rows of ns + 1
   extern __shared__ __align__(16) char sm[];
@@ -640,7 +678,7 @@ __global__ void __launch_bounds__(kSubThreads) k_subcycle(int ns, int B, const i
   MGDesc<T> d;
   T* b0 = v.take<T>(V);
   T* x0 = v.take<T>(V);
-  carve_mg_split<T>(w, v, ns, d);
+  carve_mg_split<T>(w, v, ns, d, rxn != 0);
   if (threadIdx.x == 0) mg = d;
   const T* src = bin + (size_t)b * (size_t)(ns + 1) * ldio;
   for_all(V, [&](size_t q) {
@@ -734,11 +772,15 @@ __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 __device__ __forceinline__ float at(const float4& v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
 
-// K1, vectorised: the pending w/x update, q = (A - sigma M) z * ig and the partial <q, z>
+// K1, vectorised: the pending w/x update, q = (A - sigma M) z * ig and the partial <q, z>; with RX
+// the operator is A + B - sigma M, B the reaction matrix from its edge weights rx, ry, rd (edges to
+// E, N and NE)
+template <bool RX>
 __global__ void k_minres_q4(int n, int B, const int* __restrict__ act, const SS<float>* __restrict__ ss,
                             const float* __restrict__ wx, const float* __restrict__ wy, const float* __restrict__ z,
                             const float* __restrict__ zp, float* __restrict__ wo, const float* __restrict__ w,
-                            float* __restrict__ xi, float* __restrict__ qv, double* part, unsigned long long* work) {
+                            float* __restrict__ xi, float* __restrict__ qv, double* part, unsigned long long* work,
+                            const float* __restrict__ rx, const float* __restrict__ ry, const float* __restrict__ rd) {
   const int nt = tiles_vec(n);
   const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
   if (b >= B || !act[b]) return;
@@ -749,7 +791,7 @@ __global__ void k_minres_q4(int n, int B, const int* __restrict__ act, const SS<
     // interior nodes of the tile: four per thread, minus the boundary column of each row start
     const long per_row = n / kVec;
     const long nodes = kVec * (g1 - g0) - ((g1 + per_row - 1) / per_row - (g0 + per_row - 1) / per_row);
-    atomicAdd(work, (unsigned long long)(nodes * (S.pend ? 10 : 4) * (long)sizeof(float)));
+    atomicAdd(work, (unsigned long long)(nodes * ((S.pend ? 10 : 4) + (RX ? 3 : 0)) * (long)sizeof(float)));
   }
   const int ld = sld(n);
   const size_t off = (size_t)b * ssz(n);
@@ -777,6 +819,18 @@ __global__ void k_minres_q4(int n, int B, const int* __restrict__ act, const SS<
     const bool first = c0 == 0;
     const float zw = first ? 0.0f : z[p - 1], ze = z[p + kVec], zne = z[p + ld + kVec];
     const float zsw = first ? 0.0f : z[p - ld - 1], wwest = first ? 0.0f : wx[p - 1];
+    float4 rxc, ryc, rys, rdc, rds;
+    float rxw = 0.0f, rdsw = 0.0f;
+    if (RX) {
+      rxc = ld4(rx + p);
+      ryc = ld4(ry + p);
+      rys = ld4(ry + p - ld);
+      rdc = ld4(rd + p);
+      rds = ld4(rd + p - ld);
+      rxw = first ? 0.0f : rx[p - 1];
+      rdsw = first ? 0.0f : rd[p - ld - 1];
+    }
+    const float hmf = 1.0f / (12.0f * (float)n * (float)n);
     float q[kVec];
 #pragma unroll
     for (int k = 0; k < kVec; ++k) {
@@ -787,7 +841,13 @@ __global__ void k_minres_q4(int n, int B, const int* __restrict__ act, const SS<
       const float we = at(wc, k), wwv = k > 0 ? at(wc, k - 1) : wwest;
       const float st = we * (xp - xe) + wwv * (xp - xw) + at(yc, k) * (xp - xn) + at(ys, k) * (xp - xs);
       const float ms = 6.0f * xp + (xe + xw) + (xn + xs) + (xne + xsw);
-      const float kz = (st - S.sigm * ms) * S.ig;
+      float kz = st - S.sigm * ms;
+      if (RX) {
+        const float rw = k > 0 ? at(rxc, k - 1) : rxw, rsw = k > 0 ? at(rds, k - 1) : rdsw;
+        kz += hmf * (at(rxc, k) * (xp + xe) + rw * (xp + xw) + at(ryc, k) * (xp + xn) + at(rys, k) * (xp + xs) +
+                     at(rdc, k) * (xp + xne) + rsw * (xp + xsw));
+      }
+      kz *= S.ig;
       q[k] = (first && k == 0) ? 0.0f : kz;
       acc[0] += q[k] * xp;
     }
@@ -837,10 +897,11 @@ __host__ __device__ inline int tiles_pairs(int m) {
 // the 5 x 7 block it needs, the residual b - A x1 at the 13 fine nodes of the two 7-point
 // restrictions, and writes both coarse values.  Columns left of the row start read as zero (the
 // coarse node 0 is the boundary and is not written).
-template <typename WT>
+// (RX: the multigrid operator is A + D_B, D_B the lumped reaction in dr)
+template <typename WT, bool RX = false>
 __global__ void k_restrict1_4(int n, int B, const int* __restrict__ act, const WT* __restrict__ wx,
                               const WT* __restrict__ wy, const WT* __restrict__ dinv, const float* __restrict__ bb,
-                              float* __restrict__ bc, int ldo) {
+                              float* __restrict__ bc, int ldo, const WT* __restrict__ dr = nullptr) {
   const int m = n / 2, pairs = m / 2;
   const int nt = tiles_pairs(m);
   const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
@@ -887,11 +948,27 @@ __global__ void k_restrict1_4(int n, int B, const int* __restrict__ act, const W
 #pragma unroll
     for (int q = 0; q < 6; ++q) wyv[r][q] = v[q];
   }
+  // lumped reaction on rows jc-1 .. jc+1, columns c-2 .. c+3 (index 0..5)
+  float drv[3][6];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) drv[r][q] = 0.0f;
+    if (RX) {
+      const size_t row = off + (size_t)(jc - 1 + r) * ld;
+      const float4 a0 = c ? ldw4(dr + row + c - 4) : z4, a1 = ldw4(dr + row + c);
+      const float v[6] = {a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+      for (int q = 0; q < 6; ++q) drv[r][q] = v[q];
+    }
+  }
   // residual at fine row jc - 2 + r, column c - 2 + q (r = 1..3, q = 1..5)
   auto res = [&](int r, int q) {
     const float xq = x1[r][q];
-    return rr[r][q] - (wxv[r - 1][q] * (xq - x1[r][q + 1]) + wxv[r - 1][q - 1] * (xq - x1[r][q - 1]) +
-                       wyv[r][q] * (xq - x1[r + 1][q]) + wyv[r - 1][q] * (xq - x1[r - 1][q]));
+    float ax = wxv[r - 1][q] * (xq - x1[r][q + 1]) + wxv[r - 1][q - 1] * (xq - x1[r][q - 1]) +
+               wyv[r][q] * (xq - x1[r + 1][q]) + wyv[r - 1][q] * (xq - x1[r - 1][q]);
+    if (RX) ax += drv[r - 1][q] * xq;
+    return rr[r][q] - ax;
   };
   float* __restrict__ C = bc + (size_t)b * (size_t)(m + 1) * ldo + (size_t)J * ldo;
   // coarse node 2t (fine column c: q = 2) and 2t + 1 (fine column c + 2: q = 4)
@@ -905,11 +982,12 @@ __global__ void k_restrict1_4(int n, int B, const int* __restrict__ act, const W
   }
 }
 
-template <bool DOT, typename WT = float>
+template <bool DOT, typename WT = float, bool RX = false>
 __global__ void k_prolong_smooth1_4(int n, int B, const int* __restrict__ act, const WT* __restrict__ wx,
                                     const WT* __restrict__ wy, const WT* __restrict__ dinv,
                                     const float* __restrict__ bb, const float* __restrict__ xc, int ldc,
-                                    float* __restrict__ out, const float* __restrict__ dotv, double* part) {
+                                    float* __restrict__ out, const float* __restrict__ dotv, double* part,
+                                    const WT* __restrict__ dr = nullptr) {
   const int nt = tiles_vec(n);
   const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
   if (b >= B || !act[b]) return;
@@ -964,13 +1042,15 @@ __global__ void k_prolong_smooth1_4(int n, int B, const int* __restrict__ act, c
       tn[k] = at(dn, k) * at(rn, k) + pcr(Ap, Bp, k);
       ts[k] = at(ds, k) * at(rs, k) + pcr(Am, Bm, k);
     }
+    const float4 drc = RX ? ldw4(dr + p) : make_float4(0.f, 0.f, 0.f, 0.f);
     float o[kVec];
 #pragma unroll
     for (int k = 0; k < kVec; ++k) {
       const float tp = tr[k + 1];
       const float wwv = k > 0 ? at(wc, k - 1) : wwest;
-      const float ax = at(wc, k) * (tp - tr[k + 2]) + wwv * (tp - tr[k]) + at(yc, k) * (tp - tn[k]) +
-                       at(ys, k) * (tp - ts[k]);
+      float ax = at(wc, k) * (tp - tr[k + 2]) + wwv * (tp - tr[k]) + at(yc, k) * (tp - tn[k]) +
+                 at(ys, k) * (tp - ts[k]);
+      if (RX) ax += at(drc, k) * tp;
       o[k] = (first && k == 0) ? 0.0f : tp + at(dc, k) * (at(rc, k) - ax);
     }
     st4(out + p, make_float4(o[0], o[1], o[2], o[3]));
@@ -1117,11 +1197,14 @@ __global__ void k_outer_update(int n, int B, const SS<T>* __restrict__ ss, const
 // FP64 residual r = b - (A - sigma M) x64 (FP64 edge weights); v = T(r).
 // Partials r.r, x.x, x.Ax, x.Mx, sum x: the last pass of a sample gives its Rayleigh quotient and
 // its functional.
+// (rcb: the reaction coefficient's centroid values [B][2 n^2], or NULL; its seven-point form is added
+// to the operator, formed on the fly in FP64)
 template <typename T>
 __global__ void k_residual(int n, int B, const int* __restrict__ ran, const double* __restrict__ wx64,
                            const double* __restrict__ wy64,
                            const double* __restrict__ sigma, int sig_stride, const double* __restrict__ x64,
-                           const double* __restrict__ b64, T* __restrict__ v, double* part) {
+                           const double* __restrict__ b64, T* __restrict__ v, double* part,
+                           const double* __restrict__ rcb = nullptr) {
   const int nt = tiles_interior(n);
   const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
   if (b >= B || !ran[b]) return;
@@ -1133,9 +1216,11 @@ __global__ void k_residual(int n, int B, const int* __restrict__ ran, const doub
   const double* __restrict__ WY = wy64 + off;
   const double* __restrict__ X = x64 + off;
   double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  for_tile(n, ch, [&](int p, int, int) {
+  const double* RB = rcb ? rcb + (size_t)b * 2 * n * n : nullptr;
+  for_tile(n, ch, [&](int p, int i, int j) {
     const double xv = X[p];
-    const double ax = stiff<double, double>(WX, WY, X, p, ld);
+    double ax = stiff<double, double>(WX, WY, X, p, ld);
+    if (RB) ax += hm * react_cells(RB, n, X, p, ld, i, j);
     const double mx = hm * mass7(X, p, ld);
     const double r = b64[off + p] - (ax - sg * mx);
     v[off + p] = T(r);
@@ -1232,11 +1317,17 @@ __global__ void k_set_int(int B, int* p, int v) {
 template <typename T>
 int launch_minres_q(int n, int B, const int* act, const SS<T>* ss, const T* wx, const T* wy, const double* lamH,
                     int lam_stride, const T* z, const T* zp, T* wo, const T* w, T* xi, T* q, double* part,
-                    unsigned long long* work, cudaStream_t st) {
+                    unsigned long long* work, cudaStream_t st, const T* rx = nullptr, const T* ry = nullptr,
+                    const T* rd = nullptr) {
   if constexpr (sizeof(T) == sizeof(float)) {
     (void)lamH;
     (void)lam_stride;
-    k_minres_q4<<<B * tiles_vec(n), kThreads, 0, st>>>(n, B, act, ss, wx, wy, z, zp, wo, w, xi, q, part, work);
+    if (rx)
+      k_minres_q4<true><<<B * tiles_vec(n), kThreads, 0, st>>>(n, B, act, ss, wx, wy, z, zp, wo, w, xi, q, part, work,
+                                                              rx, ry, rd);
+    else
+      k_minres_q4<false><<<B * tiles_vec(n), kThreads, 0, st>>>(n, B, act, ss, wx, wy, z, zp, wo, w, xi, q, part, work,
+                                                               nullptr, nullptr, nullptr);
     return tiles_vec(n);
   } else {
     k_minres_q<T><<<B * tiles_interior(n), kThreads, 0, st>>>(n, B, act, ss, wx, wy, lamH, lam_stride, z, zp, wo, w,
@@ -1270,6 +1361,12 @@ struct Arena {
   // FP32 path: BF16 copies of wx, wy, om D^-1 per streaming level, read by the V(1,1) sweeps
   __nv_bfloat16 *hx[kMaxMG], *hy[kMaxMG], *hd[kMaxMG];
   T* cells[kMaxMG];  // per-triangle coefficients of streaming level l >= 1 and of the sub mesh
+  // reaction term (FP32 path): the operator's reaction edge weights on the finest mesh, the lumped
+  // reaction per streaming level (BF16, V(1,1) sweeps) and the coarsened reaction coefficients
+  int rxn;
+  T *rx, *ry, *rd;
+  __nv_bfloat16* hr[kMaxMG];
+  T* rcells[kMaxMG];
   T *bsub, *xsub;
   char* subw;  // per-sample operator arrays of the sub meshes
   size_t subw_bytes;
@@ -1279,10 +1376,11 @@ struct Arena {
 };
 
 template <typename T>
-size_t carve_arena(void* base, int n, int B, Arena<T>& A) {
+size_t carve_arena(void* base, int n, int B, Arena<T>& A, bool rxn = false) {
   Carver c(base);
   A.n = n;
   A.B = B;
+  A.rxn = rxn ? 1 : 0;
   A.V0 = ssz(n);
   const size_t Bz = (size_t)B;
   A.v = c.take<T>(Bz * A.V0);
@@ -1311,16 +1409,25 @@ size_t carve_arena(void* base, int n, int B, Arena<T>& A) {
     A.hx[l] = h ? c.take<__nv_bfloat16>(Bz * V) : nullptr;
     A.hy[l] = h ? c.take<__nv_bfloat16>(Bz * V) : nullptr;
     A.hd[l] = h ? c.take<__nv_bfloat16>(Bz * V) : nullptr;
+    A.hr[l] = (h && rxn) ? c.take<__nv_bfloat16>(Bz * V) : nullptr;
   }
+  A.rx = rxn ? c.take<T>(Bz * A.V0) : nullptr;
+  A.ry = rxn ? c.take<T>(Bz * A.V0) : nullptr;
+  A.rd = rxn ? c.take<T>(Bz * A.V0) : nullptr;
+  for (int l = 0; l < kMaxMG; ++l) A.rcells[l] = nullptr;
   for (int l = 1; l <= A.Ls; ++l) {
     const size_t nl = (size_t)(n >> l);
     A.cells[l] = c.take<T>(Bz * 2 * nl * nl);
+    if (rxn) A.rcells[l] = c.take<T>(Bz * 2 * nl * nl);
   }
   const int ns = n >> A.Ls;  // sub mesh (== n when n <= kSub)
-  if (A.Ls == 0) A.cells[0] = c.take<T>(Bz * 2 * (size_t)ns * ns);
+  if (A.Ls == 0) {
+    A.cells[0] = c.take<T>(Bz * 2 * (size_t)ns * ns);
+    if (rxn) A.rcells[0] = c.take<T>(Bz * 2 * (size_t)ns * ns);
+  }
   A.bsub = A.Ls ? c.take<T>(Bz * gsz(ns)) : nullptr;
   A.xsub = A.Ls ? c.take<T>(Bz * gsz(ns)) : nullptr;
-  A.subw_bytes = sub_weights_bytes<T>(ns);
+  A.subw_bytes = sub_weights_bytes<T>(ns, rxn);
   A.subw = c.take<char>(Bz * A.subw_bytes + 256);
   A.subw = (char*)(((uintptr_t)A.subw + 255) & ~(uintptr_t)255);
   const int nch = tiles_interior(n) > 1 ? tiles_interior(n) : 1;
@@ -1345,7 +1452,7 @@ cudaError_t vcycle_stream(Arena<T>& A, const T* b0, T* x0, const int* act, T om,
   const int n = A.n, B = A.B;
   if (A.Ls == 0) {
     ++tl_launches, k_subcycle<T><<<B, kSubThreads, sub_smem, st>>>(n, B, act, A.subw, A.subw_bytes, b0, x0, sld(n), A.nu,
-                                                                   om, part, dotv);
+                                                                   om, part, dotv, A.rxn);
     LAUNCH_CHECK();
     return cudaSuccess;
   }
@@ -1357,8 +1464,12 @@ cudaError_t vcycle_stream(Arena<T>& A, const T* b0, T* x0, const int* act, T om,
       const int ldo = (l + 1 < A.Ls) ? sld(nl / 2) : nl / 2 + 1;
       if constexpr (sizeof(T) == sizeof(float)) {
         if (A.hx[l]) {
-          ++tl_launches, k_restrict1_4<__nv_bfloat16><<<B * tiles_pairs(nl / 2), kThreads, 0, st>>>(
-              nl, B, act, A.hx[l], A.hy[l], A.hd[l], b, bc, ldo);
+          if (A.hr[l])
+            ++tl_launches, k_restrict1_4<__nv_bfloat16, true><<<B * tiles_pairs(nl / 2), kThreads, 0, st>>>(
+                nl, B, act, A.hx[l], A.hy[l], A.hd[l], b, bc, ldo, A.hr[l]);
+          else
+            ++tl_launches, k_restrict1_4<__nv_bfloat16><<<B * tiles_pairs(nl / 2), kThreads, 0, st>>>(
+                nl, B, act, A.hx[l], A.hy[l], A.hd[l], b, bc, ldo);
           LAUNCH_CHECK();
           continue;
         }
@@ -1373,7 +1484,7 @@ cudaError_t vcycle_stream(Arena<T>& A, const T* b0, T* x0, const int* act, T om,
     }
     const int ns = n >> A.Ls;
     ++tl_launches, k_subcycle<T><<<B, kSubThreads, sub_smem, st>>>(ns, B, act, A.subw, A.subw_bytes, A.bsub, A.xsub,
-                                                                   ns + 1, 1, om, nullptr, nullptr);
+                                                                   ns + 1, 1, om, nullptr, nullptr, A.rxn);
     LAUNCH_CHECK();
     for (int l = A.Ls - 1; l >= 0; --l) {
       const int nl = n >> l;
@@ -1382,12 +1493,20 @@ cudaError_t vcycle_stream(Arena<T>& A, const T* b0, T* x0, const int* act, T om,
       const T* xc = (l + 1 < A.Ls) ? A.x[l + 1] : A.xsub;
       const int ldc = (l + 1 < A.Ls) ? sld(nl / 2) : nl / 2 + 1;
       if constexpr (sizeof(T) == sizeof(float)) {
-        if (l == 0 && dotv)
+        if (A.hr[l]) {
+          if (l == 0 && dotv)
+            ++tl_launches, k_prolong_smooth1_4<true, __nv_bfloat16, true><<<B * tiles_vec(nl), kThreads, 0, st>>>(
+                nl, B, act, A.hx[l], A.hy[l], A.hd[l], b, xc, ldc, xa, dotv, part, A.hr[l]);
+          else
+            ++tl_launches, k_prolong_smooth1_4<false, __nv_bfloat16, true><<<B * tiles_vec(nl), kThreads, 0, st>>>(
+                nl, B, act, A.hx[l], A.hy[l], A.hd[l], b, xc, ldc, xa, nullptr, nullptr, A.hr[l]);
+        } else if (l == 0 && dotv) {
           ++tl_launches, k_prolong_smooth1_4<true, __nv_bfloat16><<<B * tiles_vec(nl), kThreads, 0, st>>>(
               nl, B, act, A.hx[l], A.hy[l], A.hd[l], b, xc, ldc, xa, dotv, part);
-        else
+        } else {
           ++tl_launches, k_prolong_smooth1_4<false, __nv_bfloat16><<<B * tiles_vec(nl), kThreads, 0, st>>>(
               nl, B, act, A.hx[l], A.hy[l], A.hd[l], b, xc, ldc, xa, nullptr, nullptr);
+        }
       } else {
         if (l == 0 && dotv)
           ++tl_launches, k_prolong_smooth1<T, true><<<B * tiles_interior(nl), kThreads, 0, st>>>(
@@ -1415,7 +1534,7 @@ cudaError_t vcycle_stream(Arena<T>& A, const T* b0, T* x0, const int* act, T om,
   }
   const int ns = n >> A.Ls;
   ++tl_launches, k_subcycle<T><<<B, kSubThreads, sub_smem, st>>>(ns, B, act, A.subw, A.subw_bytes, A.bsub, A.xsub, ns + 1,
-                                                                 A.nu, om, nullptr, nullptr);
+                                                                 A.nu, om, nullptr, nullptr, A.rxn);
   LAUNCH_CHECK();
   for (int l = A.Ls - 1; l >= 0; --l) {
     const int nl = n >> l;
@@ -1486,14 +1605,16 @@ cudaError_t close_while(cudaStream_t body) {
 template <typename T>
 cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st, const StreamGraph* sg) {
   Arena<T> A;
-  carve_arena<T>(arena, s.n, s.B, A);
+  // the reaction term runs on the FP32 path with V(1,1) smoothing
+  if (s.b && (sizeof(T) != sizeof(float) || s.nu != 1)) return cudaErrorNotSupported;
+  carve_arena<T>(arena, s.n, s.B, A, s.b != nullptr);
   A.nu = s.nu == 1 ? 1 : 2;
   const int n = s.n, B = s.B;
   const int nt = tiles_interior(n);
   const size_t Bz = (size_t)B;
   const T om = T(s.omega);
   const int ns = n >> A.Ls;
-  const size_t sub_smem = sub_vectors_bytes<T>(ns);
+  const size_t sub_smem = sub_vectors_bytes<T>(ns, A.rxn != 0);
   cudaError_t e = raise_smem_limit((const void*)k_subcycle<T>, (int)sub_smem);
   if (e != cudaSuccess) return e;
   e = raise_smem_limit((const void*)k_sub_build<T>, (int)sub_smem);
@@ -1526,26 +1647,34 @@ cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st, c
     if (l == 0)
       ++tl_launches, k_weights<T, double><<<B * tiles_padded(nl), kThreads, 0, st>>>(nl, B, s.a, astride, A.wx[0], A.wy[0],
                                                                      A.dinv[0], om, A.wx64, A.wy64, nullptr, A.ss,
-                                                                     A.hx[0], A.hy[0], A.hd[0]);
+                                                                     A.hx[0], A.hy[0], A.hd[0], s.b, A.hr[0], A.rx,
+                                                                     A.ry, A.rd);
     else
       ++tl_launches, k_weights<T, T><<<B * tiles_padded(nl), kThreads, 0, st>>>(nl, B, A.cells[l], (size_t)2 * nl * nl, A.wx[l],
                                                                 A.wy[l], A.dinv[l], om, nullptr, nullptr, nullptr, nullptr,
-                                                                A.hx[l], A.hy[l], A.hd[l]);
+                                                                A.hx[l], A.hy[l], A.hd[l], A.rcells[l], A.hr[l]);
     LAUNCH_CHECK();
     if (l >= A.Ls) continue;
     const int m = nl / 2;
     const int ntc = (int)(((size_t)m * m + kTile - 1) / kTile);
-    if (l == 0)
+    if (l == 0) {
       ++tl_launches, k_coarsen<double, T><<<B * ntc, kThreads, 0, st>>>(nl, B, s.a, astride, A.cells[1]);
-    else
+      if (A.rxn) ++tl_launches, k_coarsen<double, T><<<B * ntc, kThreads, 0, st>>>(nl, B, s.b, astride, A.rcells[1]);
+    } else {
       ++tl_launches, k_coarsen<T, T><<<B * ntc, kThreads, 0, st>>>(nl, B, A.cells[l], (size_t)2 * nl * nl, A.cells[l + 1]);
+      if (A.rxn)
+        ++tl_launches, k_coarsen<T, T><<<B * ntc, kThreads, 0, st>>>(nl, B, A.rcells[l], (size_t)2 * nl * nl,
+                                                                     A.rcells[l + 1]);
+    }
     LAUNCH_CHECK();
   }
   if (A.Ls == 0) {
     ++tl_launches, k_convert<double, T><<<grid1(Bz * astride), 256, 0, st>>>(Bz * astride, s.a, A.cells[0]);
+    if (A.rxn) ++tl_launches, k_convert<double, T><<<grid1(Bz * astride), 256, 0, st>>>(Bz * astride, s.b, A.rcells[0]);
     LAUNCH_CHECK();
   }
-  ++tl_launches, k_sub_build<T><<<B, kThreads, sub_smem, st>>>(ns, B, A.cells[A.Ls], A.subw, A.subw_bytes);
+  ++tl_launches, k_sub_build<T><<<B, kThreads, sub_smem, st>>>(ns, B, A.cells[A.Ls], A.subw, A.subw_bytes,
+                                                                A.rcells[A.Ls]);
   LAUNCH_CHECK();
   // ---- right-hand side b = M P u_H
   ++tl_launches, k_interp<T><<<B * nt, kThreads, 0, st>>>(n, s.nc, B, s.uH, A.x64);
@@ -1591,7 +1720,7 @@ cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st, c
     if ((e = open_while(b0, b1, hi)) != cudaSuccess) return e;
     for (int half = 0; half < 2; ++half) {
       const int nq = launch_minres_q<T>(n, B, A.act, A.ss, A.wx[0], A.wy[0], s.lamH, s.lam_stride, z, zn, wo, w, A.xi,
-                                        A.q, A.part, nullptr, b1);
+                                        A.q, A.part, nullptr, b1, A.rx, A.ry, A.rd);
       ++tl_launches;
       LAUNCH_CHECK();
       ++tl_launches, k_sc_retire<T><<<gs, 256, 0, b1>>>(B, A.act, A.ss);
@@ -1614,7 +1743,7 @@ cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st, c
     ++tl_launches, k_minres_finish<T><<<B * nt, kThreads, 0, b0>>>(n, B, A.ran, A.ss, zn, wo, w, A.xi);
     ++tl_launches, k_outer_update<T><<<B * nt, kThreads, 0, b0>>>(n, B, A.ss, A.ran, A.xi, A.x64);
     ++tl_launches, k_residual<T><<<B * nt, kThreads, 0, b0>>>(n, B, A.ran, A.wx64, A.wy64, s.lamH, s.lam_stride, A.x64,
-                                                             A.b64, A.v, A.part);
+                                                             A.b64, A.v, A.part, s.b);
     ++tl_launches, k_sc_outer_end<T><<<gs, 256, 0, b0>>>(B, nt, A.part, A.ran, A.ss);
     ++tl_launches, k_cond_outer<<<1, 1, 0, b0>>>(ho, oc, cnt_o, s.max_outer);
     LAUNCH_CHECK();
@@ -1646,7 +1775,7 @@ cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st, c
         cudaEventRecord(pe->first, st);
       }
       const int nq = launch_minres_q<T>(n, B, A.act, A.ss, A.wx[0], A.wy[0], s.lamH, s.lam_stride, z, zn, wo, w, A.xi,
-                                        A.q, A.part, s.probe ? s.probe->d_bytes : nullptr, st);
+                                        A.q, A.part, s.probe ? s.probe->d_bytes : nullptr, st, A.rx, A.ry, A.rd);
       ++tl_launches;
       LAUNCH_CHECK();
       if (pe) cudaEventRecord(pe->second, st);
@@ -1674,7 +1803,7 @@ cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st, c
     LAUNCH_CHECK();
     ++tl_launches, k_outer_update<T><<<B * nt, kThreads, 0, st>>>(n, B, A.ss, A.ran, A.xi, A.x64);
     ++tl_launches, k_residual<T><<<B * nt, kThreads, 0, st>>>(n, B, A.ran, A.wx64, A.wy64, s.lamH, s.lam_stride, A.x64, A.b64, A.v,
-                                               A.part);
+                                               A.part, s.b);
     ++tl_launches, k_sc_outer_end<T><<<gs, 256, 0, st>>>(B, nt, A.part, A.ran, A.ss);
     LAUNCH_CHECK();
   }
@@ -1701,10 +1830,10 @@ cudaError_t launch_finalize(int B, double* d_out, int has_prev, cudaStream_t st)
   return cudaGetLastError();
 }
 
-size_t stream_arena_bytes(int n, int B, int mixed) {
+size_t stream_arena_bytes(int n, int B, int mixed, int reaction) {
   if (mixed) {
     Arena<float> A;
-    return carve_arena<float>(nullptr, n, B, A) + 256;
+    return carve_arena<float>(nullptr, n, B, A, reaction != 0) + 256;
   }
   Arena<double> A;
   return carve_arena<double>(nullptr, n, B, A) + 256;

@@ -158,8 +158,32 @@ def test_functional_on_both_tiers(B, tier):
     ctx.close()
 
 
-def test_streaming_tier_rejects_the_reaction_term(B):
-    ctx, _, _ = make_ctx(B, LEVELS)
+@pytest.mark.parametrize("qoi", [0, 1])
+def test_problem2_streaming_tier_matches_oracle_and_per_sample_tier(B, qoi):
+    # the reaction term in the streaming tier (mixed precision, V(1,1) with the lumped reaction in the
+    # multigrid): fine meshes 1/64 (streamed levels, several multigrid levels and the sub-cycle) and
+    # 1/32 (the whole V-cycle in the sub-cycle), against the oracle and against the per-sample tier
+    levels = [Level(8, 8, 16, 16, 4, 2), Level(32, 8, 16, 4, 3, 2), Level(64, 8, 16, 4, 3, 2)]
+    ctx_s, zs, ds = make_ctx(B, levels, prec=1, qoi=qoi, tol_linear=1e-10)
+    ctx_p, _, _ = make_ctx(B, levels, prec=1, qoi=qoi, tol_linear=1e-10)
+    for l in (1, 2):
+        ctx_s.mq_set_level_config(l, 1, 0, 0)
+        ctx_p.mq_set_level_config(l, 0, 0, 0)
+    name = "eigenvalue" if qoi == 0 else "functional"
+    for l, lv in enumerate(levels):
+        a, _ = ctx_s.mq_eval_level(l, 0, lv.N)
+        b, _ = ctx_p.mq_eval_level(l, 0, lv.N)
+        ref = _oracle(levels, zs, ds, DECAYS, 2, name, l)
+        e = np.abs(a[..., 1:3] - ref[..., 1:3]) / np.abs(ref[..., 1:2])
+        d = np.abs(a[..., 1:3] - b[..., 1:3]) / np.abs(b[..., 1:2])
+        print(f"problem 2 streaming tier ({name}), level {l}: vs oracle {e.max():.2e}, vs per-sample tier {d.max():.2e}")
+        assert e.max() <= 1e-10 and d.max() <= 1e-10
+    ctx_s.close()
+    ctx_p.close()
+
+
+def test_streaming_tier_rejects_the_reaction_term_in_fp64(B):
+    ctx, _, _ = make_ctx(B, LEVELS, prec=0)
     ctx.mq_set_level_config(2, 1, 0, 0)
     with pytest.raises(B.MQError) as e:
         ctx.mq_eval_level(2, 0, 1)
