@@ -490,8 +490,8 @@ def stream_bytes(wl, level, st, prec, samples):
 # ncu DRAM traffic of the per-sample kernel's launch on a level (one launch of the benchmark's size:
 # level 1 of the six-level workload, 4,096 samples; summarised under profiles/), valid only for the
 # kernel source it was measured on
-SAMPLE_KERNEL_TRAFFIC = {"source_sha256": "79b7f26fcfff6e0ece6d816e2ffaa1432af5cc4ba599a1a77e8a7e9a2f01b84c",
-                         "level": 1, "precision": "mixed", "bytes_per_launch": 139.522816e6 + 41.857024e6}
+SAMPLE_KERNEL_TRAFFIC = {"source_sha256": "7861a6430fbac9e0c146a8aa2dfbd3247634376d533e93997ab395a81abc1a8e",
+                         "level": 1, "precision": "mixed", "bytes_per_launch": 140.174592e6 + 41.903360e6}
 
 
 # ncu DRAM traffic of the operator sweep k_minres_q per algorithmic byte: one launch with the pending
