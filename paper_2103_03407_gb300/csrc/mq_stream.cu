@@ -291,14 +291,39 @@ __global__ void k_rhs(int n, int B, const double* __restrict__ x64, double* __re
   tile_partials<1, double>(acc, part, (size_t)b * nt + ch);
 }
 
+// Sum of sample b's partial slots k = 0..nch-1 (NV values each, part[(b nch + k) NV + i]) by one
+// warp: the lanes stride the slots, then an XOR butterfly.  Every lane returns the same totals
+// (the summation order is fixed, and each butterfly step adds the same two values on both lanes).
+template <int NV>
+__device__ __forceinline__ void warp_sum_slots(const double* __restrict__ part, int b, int nch, double (&s)[NV]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) s[i] = 0.0;
+#pragma unroll 4
+  for (int k = lane; k < nch; k += 32) {
+    const double* pk = part + ((size_t)b * nch + k) * NV;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) s[i] += pk[i];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) s[i] += __shfl_xor_sync(0xffffffffu, s[i], o);
+}
+
+// sample of a warp-per-sample scalar kernel (launched with 32 B threads)
+__device__ __forceinline__ int warp_sample() { return (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); }
+
 template <typename T>
 __global__ void k_sc_start(int B, int n, const double* sigma, int sig_stride, int nch, const double* part,
                            SS<T>* ss) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = warp_sample();
   if (b >= B) return;
+  double t[1];
+  warp_sum_slots<1>(part, b, nch, t);
+  if ((threadIdx.x & 31) != 0) return;
+  const double s = t[0];
   ss[b].sigm = T(sigma[(size_t)b * sig_stride] / (12.0 * n * n));
-  double s = 0.0;
-  for (int k = 0; k < nch; ++k) s += part[(size_t)b * nch + k];
   SS<T>& S = ss[b];
   S.bnorm = S.rnorm = sqrt(s);
   S.rs = T(1.0 / S.rnorm);
@@ -1093,10 +1118,12 @@ __global__ void k_minres_finish(int n, int B, const int* __restrict__ act, const
 
 template <typename T>
 __global__ void k_sc_gamma0(int B, int nch, const double* part, const int* act, SS<T>* ss) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = warp_sample();
   if (b >= B || !act[b]) return;
-  double s = 0.0;
-  for (int k = 0; k < nch; ++k) s += part[(size_t)b * nch + k];
+  double t[1];
+  warp_sum_slots<1>(part, b, nch, t);
+  if ((threadIdx.x & 31) != 0) return;
+  const double s = t[0];
   SS<T>& S = ss[b];
   const T t0 = T(s);
   const int brk = !(t0 > T(0));
@@ -1113,10 +1140,12 @@ __global__ void k_sc_gamma0(int B, int nch, const double* part, const int* act, 
 
 template <typename T>
 __global__ void k_sc_delta(int B, int nch, const double* part, const int* act, SS<T>* ss) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = warp_sample();
   if (b >= B || !act[b]) return;
-  double s = 0.0;
-  for (int k = 0; k < nch; ++k) s += part[(size_t)b * nch + k];
+  double t[1];
+  warp_sum_slots<1>(part, b, nch, t);
+  if ((threadIdx.x & 31) != 0) return;
+  const double s = t[0];
   SS<T>& S = ss[b];
   const T delta = T(s) * S.ig;
   S.c1 = delta * S.ig;
@@ -1132,10 +1161,12 @@ __global__ void k_sc_delta(int B, int nch, const double* part, const int* act, S
 template <typename T>
 __global__ void k_sc_givens(int B, int nch, const double* part, int* act, SS<T>* ss, T tol, int* count,
                             const int* jc = nullptr, int joff = 0, int max_inner = 0) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = warp_sample();
   if (b >= B || !act[b]) return;
-  double s = 0.0;
-  for (int k = 0; k < nch; ++k) s += part[(size_t)b * nch + k];
+  double t[1];
+  warp_sum_slots<1>(part, b, nch, t);
+  if ((threadIdx.x & 31) != 0) return;
+  const double s = t[0];
   SS<T>& S = ss[b];
   T gnew = T(s);
   if (!(gnew >= T(0))) {
@@ -1196,7 +1227,9 @@ __global__ void k_outer_update(int n, int B, const SS<T>* __restrict__ ss, const
 
 // FP64 residual r = b - (A - sigma M) x64 (FP64 edge weights); v = T(r).
 // Partials r.r, x.x, x.Ax, x.Mx, sum x: the last pass of a sample gives its Rayleigh quotient and
-// its functional.
+// its functional.  The two norms only steer the refinement (stopping tests, the scale of the next
+// correction, which the following pass measures again), so each thread sums them in FP32: GB300
+// issues FP64 at 1/64 of the FP32 rate.  The nodal sum is formed only for the functional (with_sum).
 // (rcb: the reaction coefficient's centroid values [B][2 n^2], or NULL; its seven-point form is added
 // to the operator, formed on the fly in FP64)
 template <typename T>
@@ -1204,7 +1237,7 @@ __global__ void k_residual(int n, int B, const int* __restrict__ ran, const doub
                            const double* __restrict__ wy64,
                            const double* __restrict__ sigma, int sig_stride, const double* __restrict__ x64,
                            const double* __restrict__ b64, T* __restrict__ v, double* part,
-                           const double* __restrict__ rcb = nullptr) {
+                           const double* __restrict__ rcb, int with_sum) {
   const int nt = tiles_interior(n);
   const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
   if (b >= B || !ran[b]) return;
@@ -1216,6 +1249,7 @@ __global__ void k_residual(int n, int B, const int* __restrict__ ran, const doub
   const double* __restrict__ WY = wy64 + off;
   const double* __restrict__ X = x64 + off;
   double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  float rr = 0.0f, xx = 0.0f;
   const double* RB = rcb ? rcb + (size_t)b * 2 * n * n : nullptr;
   for_tile(n, ch, [&](int p, int i, int j) {
     const double xv = X[p];
@@ -1223,29 +1257,27 @@ __global__ void k_residual(int n, int B, const int* __restrict__ ran, const doub
     if (RB) ax += hm * react_cells(RB, n, X, p, ld, i, j);
     const double mx = hm * mass7(X, p, ld);
     const double r = b64[off + p] - (ax - sg * mx);
+    const float rf = (float)r, xf = (float)xv;
     v[off + p] = T(r);
-    acc[0] += r * r;
-    acc[1] += xv * xv;
+    rr = fmaf(rf, rf, rr);
+    xx = fmaf(xf, xf, xx);
     acc[2] += xv * ax;
     acc[3] += xv * mx;
-    acc[4] += xv;
+    if (with_sum) acc[4] += xv;
   });
+  acc[0] = (double)rr;
+  acc[1] = (double)xx;
   tile_partials<5, double>(acc, part, (size_t)b * nt + ch);
 }
 
 template <typename T>
 __global__ void k_sc_outer_end(int B, int nch, const double* part, const int* ran, SS<T>* ss) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = warp_sample();
   if (b >= B || !ran[b]) return;
-  double s = 0.0, sx = 0.0, sa = 0.0, sm = 0.0, su = 0.0;
-  for (int k = 0; k < nch; ++k) {
-    const double* pk = part + ((size_t)b * nch + k) * 5;
-    s += pk[0];
-    sx += pk[1];
-    sa += pk[2];
-    sm += pk[3];
-    su += pk[4];
-  }
+  double t[5];
+  warp_sum_slots<5>(part, b, nch, t);
+  if ((threadIdx.x & 31) != 0) return;
+  const double s = t[0], sx = t[1], sa = t[2], sm = t[3], su = t[4];
   SS<T>& S = ss[b];
   S.xnorm = sqrt(sx);
   S.xax = sa;
@@ -1620,6 +1652,7 @@ cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st, c
   e = raise_smem_limit((const void*)k_sub_build<T>, (int)sub_smem);
   if (e != cudaSuccess) return e;
   const int gs = (B + 255) / 256;
+  const int gw = (B + 7) / 8;  // warp-per-sample scalar kernels: 8 samples per 256-thread block
   // ---- clear vectors (boundary rings must be zero), build the operators
   const size_t V0 = A.V0;
   T* const vecs[8] = {A.v, A.vo, A.z, A.zn, A.w, A.wo, A.q, A.xi};
@@ -1682,7 +1715,7 @@ cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st, c
   ++tl_launches, k_rhs<T><<<B * nt, kThreads, 0, st>>>(n, B, A.x64, A.b64, A.v, A.part);
   LAUNCH_CHECK();
   ++tl_launches, k_zero<double><<<grid1(Bz * V0), 256, 0, st>>>(Bz * V0, A.x64);
-  ++tl_launches, k_sc_start<T><<<gs, 256, 0, st>>>(B, n, s.lamH, s.lam_stride, nt, A.part, A.ss);
+  ++tl_launches, k_sc_start<T><<<gw, 256, 0, st>>>(B, n, s.lamH, s.lam_stride, nt, A.part, A.ss);
   LAUNCH_CHECK();
   if (sg) {
     // ---- refinement loop as nested WHILE nodes: no host reads.  The inner loop runs iterations in
@@ -1712,7 +1745,7 @@ cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st, c
     // partial slots per sample of <v, z> (written by the V-cycle's last sweep: the vectorised one for
     // FP32 with V(1,1), the row-mapped one otherwise; one slot when the sub-cycle does it all)
     const int nchd = A.Ls ? ((sizeof(T) == sizeof(float) && A.nu == 1) ? tiles_vec(n) : nt) : 1;
-    ++tl_launches, k_sc_gamma0<T><<<gs, 256, 0, b0>>>(B, nchd, A.part, A.act, A.ss);
+    ++tl_launches, k_sc_gamma0<T><<<gw, 256, 0, b0>>>(B, nchd, A.part, A.act, A.ss);
     LAUNCH_CHECK();
     if ((e = make_handle(b0, &hi)) != cudaSuccess) return e;
     ++tl_launches, k_cond_init<<<1, 1, 0, b0>>>(hi, ic);
@@ -1725,13 +1758,13 @@ cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st, c
       LAUNCH_CHECK();
       ++tl_launches, k_sc_retire<T><<<gs, 256, 0, b1>>>(B, A.act, A.ss);
       { T* tt = wo; wo = w; w = tt; }
-      ++tl_launches, k_sc_delta<T><<<gs, 256, 0, b1>>>(B, nq, A.part, A.act, A.ss);
+      ++tl_launches, k_sc_delta<T><<<gw, 256, 0, b1>>>(B, nq, A.part, A.act, A.ss);
       ++tl_launches, launch_minres_v<T>(n, B, A.act, A.ss, A.q, v, vo, b1);
       LAUNCH_CHECK();
       { T* tt = vo; vo = v; v = tt; }
       if ((e = vcycle_stream<T>(A, v, zn, A.act, om, v, A.part, sub_smem, b1)) != cudaSuccess) return e;
       if ((e = cudaMemsetAsync(cnt_i, 0, sizeof(int), b1)) != cudaSuccess) return e;
-      ++tl_launches, k_sc_givens<T><<<gs, 256, 0, b1>>>(B, nchd, A.part, A.act, A.ss, T(s.tol_inner), cnt_i, ic, half,
+      ++tl_launches, k_sc_givens<T><<<gw, 256, 0, b1>>>(B, nchd, A.part, A.act, A.ss, T(s.tol_inner), cnt_i, ic, half,
                                                        s.max_inner);
       LAUNCH_CHECK();
       { T* tt = z; z = zn; zn = tt; }
@@ -1743,8 +1776,8 @@ cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st, c
     ++tl_launches, k_minres_finish<T><<<B * nt, kThreads, 0, b0>>>(n, B, A.ran, A.ss, zn, wo, w, A.xi);
     ++tl_launches, k_outer_update<T><<<B * nt, kThreads, 0, b0>>>(n, B, A.ss, A.ran, A.xi, A.x64);
     ++tl_launches, k_residual<T><<<B * nt, kThreads, 0, b0>>>(n, B, A.ran, A.wx64, A.wy64, s.lamH, s.lam_stride, A.x64,
-                                                             A.b64, A.v, A.part, s.b);
-    ++tl_launches, k_sc_outer_end<T><<<gs, 256, 0, b0>>>(B, nt, A.part, A.ran, A.ss);
+                                                             A.b64, A.v, A.part, s.b, s.qoi);
+    ++tl_launches, k_sc_outer_end<T><<<gw, 256, 0, b0>>>(B, nt, A.part, A.ran, A.ss);
     ++tl_launches, k_cond_outer<<<1, 1, 0, b0>>>(ho, oc, cnt_o, s.max_outer);
     LAUNCH_CHECK();
     if ((e = close_while(b0)) != cudaSuccess) return e;
@@ -1766,7 +1799,7 @@ cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st, c
     // partial slots per sample of <v, z> (written by the V-cycle's last sweep: the vectorised one for
     // FP32 with V(1,1), the row-mapped one otherwise; one slot when the sub-cycle does it all)
     const int nchd = A.Ls ? ((sizeof(T) == sizeof(float) && A.nu == 1) ? tiles_vec(n) : nt) : 1;
-    ++tl_launches, k_sc_gamma0<T><<<gs, 256, 0, st>>>(B, nchd, A.part, A.act, A.ss);
+    ++tl_launches, k_sc_gamma0<T><<<gw, 256, 0, st>>>(B, nchd, A.part, A.act, A.ss);
     LAUNCH_CHECK();
     for (int j = 0; j < s.max_inner; ++j) {
       std::pair<cudaEvent_t, cudaEvent_t>* pe = nullptr;
@@ -1782,14 +1815,14 @@ cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st, c
       // samples that converged in the previous Givens step have now applied their update
       ++tl_launches, k_sc_retire<T><<<gs, 256, 0, st>>>(B, A.act, A.ss);
       { T* tt = wo; wo = w; w = tt; }
-      ++tl_launches, k_sc_delta<T><<<gs, 256, 0, st>>>(B, nq, A.part, A.act, A.ss);
+      ++tl_launches, k_sc_delta<T><<<gw, 256, 0, st>>>(B, nq, A.part, A.act, A.ss);
       ++tl_launches, launch_minres_v<T>(n, B, A.act, A.ss, A.q, v, vo, st);
       LAUNCH_CHECK();
       { T* tt = vo; vo = v; v = tt; }
       e = vcycle_stream<T>(A, v, zn, A.act, om, v, A.part, sub_smem, st);
       if (e != cudaSuccess) return e;
       cudaMemsetAsync(A.count, 0, sizeof(int), st);
-      ++tl_launches, k_sc_givens<T><<<gs, 256, 0, st>>>(B, nchd, A.part, A.act, A.ss, T(s.tol_inner), A.count);
+      ++tl_launches, k_sc_givens<T><<<gw, 256, 0, st>>>(B, nchd, A.part, A.act, A.ss, T(s.tol_inner), A.count);
       LAUNCH_CHECK();
       { T* tt = z; z = zn; zn = tt; }
       if ((j & 3) == 3 || j + 1 == s.max_inner) {
@@ -1803,8 +1836,8 @@ cudaError_t stream_solve_t(const StreamSolve& s, void* arena, cudaStream_t st, c
     LAUNCH_CHECK();
     ++tl_launches, k_outer_update<T><<<B * nt, kThreads, 0, st>>>(n, B, A.ss, A.ran, A.xi, A.x64);
     ++tl_launches, k_residual<T><<<B * nt, kThreads, 0, st>>>(n, B, A.ran, A.wx64, A.wy64, s.lamH, s.lam_stride, A.x64, A.b64, A.v,
-                                               A.part, s.b);
-    ++tl_launches, k_sc_outer_end<T><<<gs, 256, 0, st>>>(B, nt, A.part, A.ran, A.ss);
+                                               A.part, s.b, s.qoi);
+    ++tl_launches, k_sc_outer_end<T><<<gw, 256, 0, st>>>(B, nt, A.part, A.ran, A.ss);
     LAUNCH_CHECK();
   }
   }
