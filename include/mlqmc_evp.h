@@ -187,10 +187,14 @@ mq_status mq_set_precision(mq_ctx* ctx, mq_precision prec, double tol_linear);
 mq_status mq_set_solver_options(mq_ctx* ctx, double tol_inner, int32_t max_inner, int32_t max_outer);
 
 /* Coarse eigensolver options (values <= 0 keep the defaults): tol_eig is the target of the
- * relative eigen-residual ||A_H x - theta M_H x|| / (theta ||M_H x||) of LOBPCG (default 1e-8,
- * 1e-11 for MQ_QOI_FUNCTIONAL), max_eig the iteration cap (200).  The Rayleigh quotient
- * theta = lambda_H is accurate to about the square of tol_eig, the eigenvector (and so G(u_H)) to
- * about tol_eig. */
+ * relative eigen-residual ||A_H x - theta M_H x|| / (theta ||M_H x||) of LOBPCG, max_eig the
+ * iteration cap (200).  The Rayleigh quotient theta = lambda_H is accurate to about the square of
+ * tol_eig, the eigenvector (and so G(u_H)) to about tol_eig.  Defaults: 1e-6 for level
+ * evaluations of eigenvalues with coefficient families 0 and 1 (lambda_H to ~1e-13; the two-grid
+ * values depend on u_H only through one shifted inverse-iteration step and stay at FP64
+ * rounding); 1e-8 for the islands family of mq_set_islands (its unresolved coarse mesh makes the
+ * two-grid values ~1e4 times more sensitive to u_H) and when mq_eval_point returns the
+ * eigenvector; 1e-11 for MQ_QOI_FUNCTIONAL. */
 mq_status mq_set_eig_options(mq_ctx* ctx, double tol_eig, int32_t max_eig);
 
 /* Damped Jacobi steps before and after each coarse-grid correction of the multigrid V-cycle that

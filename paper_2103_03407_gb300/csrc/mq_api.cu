@@ -567,7 +567,14 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
   p.outer = (int*)c->outer.p;
   p.u_out = want_u ? (double*)c->uout.p : nullptr;
   // Default tolerances.  lambda_H is the Rayleigh quotient of the LOBPCG iterate, accurate to the
-  // square of its relative eigen-residual, so 1e-8 leaves it at the FP64 rounding floor.  The
+  // square of its relative eigen-residual: 1e-6 leaves it within ~5e-14 of the exact coarse
+  // eigenvalue (measured on the six-level workload, levels 0-2 and 5), and the two-grid values,
+  // which depend on u_H only through one shifted inverse-iteration step, moved by less than 3e-15
+  // against 1e-8 -- with 2.6 fewer LOBPCG iterations per sample.  How far lambda^h moves with the
+  // eigenvector error grows with the coarse-fine discrepancy: on the second test problem, whose
+  // coarse mesh does not resolve the islands (lambda_H ~10 % above lambda^h), 1e-6 moved lambda^h
+  // by 1e-10, so that family keeps 1e-8.  When the caller asks for the eigenvector itself
+  // (mq_eval_point), 1e-8 keeps it accurate to ~1e-8.  The
   // Rayleigh quotient lambda^h of the shifted-solve iterate is stationary only at an eigenvector;
   // the two-grid iterate is an O(H^4) perturbation of one, so lambda^h moves to first order in the
   // solve error with a small constant: on the 4-level workload (meshes 1/16..1/128) the largest
@@ -578,7 +585,7 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
   // and a target of 1e-5 leave lambda^h within ~2e-13 (1e-5 inner reductions above mesh 1/128).
   // The functional G(u_H) of a direct level is first order in the eigenvector error, which the
   // eigen-residual bounds only to ~tol_eig (lambda_H is second order): it takes 1e-11.
-  p.tol_eig = c->opt_tol_eig > 0 ? c->opt_tol_eig : (c->qoi == MQ_QOI_FUNCTIONAL ? 1e-11 : 1e-8);
+  p.tol_eig = c->opt_tol_eig > 0 ? c->opt_tol_eig : (c->qoi == MQ_QOI_FUNCTIONAL ? 1e-11 : (want_u || rxn ? 1e-8 : 1e-6));
   p.max_eig_it = c->opt_max_eig > 0 ? c->opt_max_eig : 200;
   p.tol_lin = c->tol_lin > 0 ? c->tol_lin : (mixed ? 1e-5 : 1e-6);
   if (mixed) {

@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 TOL_LAMBDA = 1e-10
-TOL_EIG = 1e-8  # default relative eigen-residual target of the coarse eigensolve
+TOL_EIG = 1e-8  # relative eigen-residual target of the coarse eigensolve when mq_eval_point returns u_H
 
 
 @pytest.fixture(scope="module")
@@ -154,7 +154,7 @@ def test_eval_point_matches_oracle(B, case, prec):
         assert lh == pytest.approx(rh, rel=TOL_LAMBDA)
         assert lp == pytest.approx(rp, rel=TOL_LAMBDA, abs=0 if pv else 1e-300)
         _, uref = twogrid.coarse_pair(lv.n_coarse, y[: lv.S])
-        # the eigenvector is accurate to the eigen-residual target (1e-8 by default) over the
+        # the eigenvector is accurate to the eigen-residual target (1e-8 when it is returned) over the
         # relative spectral gap (about 1.5 for these coefficients); the eigenvalue to its square
         assert np.abs(u - uref).max() < 10 * TOL_EIG * np.abs(uref).max()
 
