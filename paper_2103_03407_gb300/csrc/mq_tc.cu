@@ -13,8 +13,10 @@
 // 2^24), so each group sum
 //   S_g = sum_{p+q=g} sum_{j in chunk} Y_p[b][j] P_q[t][j]
 // is EXACT whatever the accumulation order of the tensor core.  Groups g <= 6 are kept (28 slice
-// products): a = a0 + sum_chunks sum_g 2^{-15-8g} S_g, folded into FP64 registers after every
-// chunk.  Dropped products (g >= 7) and slice remainders are below 2^-56 per term: the result
+// products): a = a0 + sum_chunks sum_g 2^{-15-8g} S_g, the group sums of a chunk combined exactly
+// in 64-bit integers.  A contraction of one chunk (K <= 128: the separable stage, short truncations)
+// is then rounded once to FP64 in integer arithmetic; longer ones add their chunks in FP64
+// registers.  Dropped products (g >= 7) and slice remainders are below 2^-56 per term: the result
 // matches an FP64 GEMM to a few units of FP64 rounding.
 //
 // Kernel (persistent, one CTA of 8 warps per SM): each CTA walks 128-sample x 64-triangle output
@@ -27,7 +29,7 @@
 // stage's "empty" mbarrier and refills the stage used one step earlier, so loads run up to four
 // steps ahead of the tensor cores.  After every 128-wide K chunk the eight warps read the
 // accumulators with tcgen05.ld (warp w: TMEM lanes 32 (w mod 4).., columns 32 (w div 4)..) and fold
-// them exactly into FP64 registers.  Every wait is bounded; a timeout sets an error word, stops the
+// them exactly (integer group sums, one rounding per chunk).  Every wait is bounded; a timeout sets an error word, stops the
 // issuing of new work, drains what is in flight and frees the tensor memory.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -241,6 +243,32 @@ __global__ void k_sep_stage1(const double* __restrict__ Y, int ldy, int B, int n
   }
 }
 
+// (hi 2^24 + lo) 2^e rounded once to the nearest double (ties to even), in integer arithmetic:
+// the exact sum of a chunk's group sums, |hi| < 2^56, |lo| < 2^40.  GB300 issues FP64 at 1/64 of
+// the FP32 rate; the conversions and the fused multiply-add of the FP64 fold cost more issue time
+// than this on the integer units.  The result is finite and normal for every e the tables use.
+__device__ __forceinline__ double exact_fold(long long hi, long long lo, int e) {
+  const __int128 v = ((__int128)hi << 24) + (__int128)lo;
+  if (v == 0) return 0.0;
+  const bool neg = v < 0;
+  unsigned __int128 m = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
+  const unsigned long long mh = (unsigned long long)(m >> 64), ml = (unsigned long long)m;
+  const int lz = mh ? __clzll((long long)mh) : 64 + __clzll((long long)ml);
+  m <<= lz;  // leading one at bit 127
+  const unsigned long long top = (unsigned long long)(m >> 64), rest = (unsigned long long)m;
+  unsigned long long mant = top >> 11;  // 53 bits
+  const unsigned long long rb = top & 0x7FFull;  // the next 11 bits; rest holds the ones below
+  mant += (rb > 0x400ull) || (rb == 0x400ull && (rest != 0ull || (mant & 1ull)));
+  int ex = 127 - lz + e;
+  if (mant >> 53) {
+    mant >>= 1;
+    ++ex;
+  }
+  const unsigned long long bits = ((unsigned long long)neg << 63) | ((unsigned long long)(ex + 1023) << 52) |
+                                  (mant & ((1ull << 52) - 1));
+  return __longlong_as_double((long long)bits);
+}
+
 struct alignas(1024) TcSmem {
   __nv_bfloat16 a[kStages][kSlices * kTM * kTK];  // [slice][K half][128 rows][8]
   __nv_bfloat16 b[kStages][kSlices * kTN * kTK];  // [slice][K half][64 rows][8]
@@ -333,6 +361,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     coords(tile, tm, tn);
     // 2^-39 and 2^-63 of the fold, times the table's exact scale 2^-pexp
     const double chi = ldexp(1.0, -39 - pexp), clo = ldexp(1.0, -63 - pexp);
+    const bool single = T <= kStepsPerChunk;
     double acc[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) acc[i] = 0.0;
@@ -417,9 +446,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               lo[i] = l;
             }
           }
-          // value of the chunk = (hi 2^24 + lo) 2^{-15-48}; hi < 2^56 and lo < 2^40 in magnitude
+          // value of the chunk = (hi 2^24 + lo) 2^{-15-48}; hi < 2^56 and lo < 2^40 in magnitude.  A
+          // contraction of one chunk is rounded once in integer arithmetic; longer ones add the
+          // chunks in FP64
+          if (single) {
 #pragma unroll
-          for (int i = 0; i < 16; ++i) acc[sh * 16 + i] += fma((double)hi[i], chi, (double)lo[i] * clo);
+            for (int i = 0; i < 16; ++i) acc[sh * 16 + i] = exact_fold(hi[i], lo[i], -63 - pexp);
+          } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) acc[sh * 16 + i] += fma((double)hi[i], chi, (double)lo[i] * clo);
+          }
         }
       }
       tc_fence_before();
