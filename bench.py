@@ -498,8 +498,8 @@ SAMPLE_KERNEL_TRAFFIC = {"source_sha256": "7861a6430fbac9e0c146a8aa2dfbd32476343
 # MINRES update (10 arrays per node) on mesh 1/1024, 16 samples of the six-level workload's finest
 # level (summarised under profiles/), scaled to a launch by its algorithmic bytes; valid only for
 # the kernel source it was measured on
-KMINRES_TRAFFIC = {"source_sha256": "9176e2cf1d84afa5cdddef73dc1982ca94e84567e28c3cd9fdb5ec4a9d40518e",
-                   "dram_per_algorithmic": (471.796480e6 + 170.385920e6) / (16 * 1023 * 1023 * 40)}
+KMINRES_TRAFFIC = {"source_sha256": "22f59b77c3bc4dc0a0e79efd7d578bdcdaa1e7ff1ab891b96076f838197586da",
+                   "dram_per_algorithmic": (471.794432e6 + 170.729984e6) / (16 * 1023 * 1023 * 40)}
 
 
 def _stream_source_hash():

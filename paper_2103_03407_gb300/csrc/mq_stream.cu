@@ -126,6 +126,13 @@ __device__ __forceinline__ void tile_partials(A (&v)[NV], double* part, size_t s
 
 // ---------------------------------------------------------------------------------------------
 // setup
+// v / 2 for a sum v of two valid (positive, finite) coefficients, on the integer units: the
+// exponent minus one, exact for every positive normal v (GB300 has few FP64 units).  Coefficients
+// that fail the checks below are flagged; their weights are then meaningless but harmless.
+__device__ __forceinline__ double half_pos(double v) {
+  return __longlong_as_double(__double_as_longlong(v) - (1LL << 52));
+}
+
 // weights and inverse diagonal of mesh n from per-triangle coefficients (lower plane, upper plane)
 // (with hx: BF16 copies of the weights and of om D^-1 for the V(1,1) sweeps of the FP32 path)
 // (with rcells: the reaction term of the second test problem of Sec. 5 -- om D^-1 includes the
@@ -164,8 +171,8 @@ __global__ void k_weights(int n, int B, const S* __restrict__ cells, size_t cstr
     auto UP = [&](int ii, int jj) { return (double)up[jj * n + ii]; };
     T d = T(0);
     double a64 = 0.0, c64 = 0.0;
-    if (i <= n - 1 && j >= 1 && j <= n - 1) a64 = 0.5 * (LO(i, j) + UP(i, j - 1));
-    if (i >= 1 && i <= n - 1 && j <= n - 1) c64 = 0.5 * (UP(i, j) + LO(i - 1, j));
+    if (i <= n - 1 && j >= 1 && j <= n - 1) a64 = half_pos(LO(i, j) + UP(i, j - 1));
+    if (i >= 1 && i <= n - 1 && j <= n - 1) c64 = half_pos(UP(i, j) + LO(i - 1, j));
     const T a = T(a64), c = T(c64);
     if (i <= n - 1 && j <= n - 1) {  // every triangle once: a > 0 and not NaN
       const long long bl = __double_as_longlong(LO(i, j)), bu = __double_as_longlong(UP(i, j));
@@ -192,7 +199,7 @@ __global__ void k_weights(int n, int B, const S* __restrict__ cells, size_t cstr
     }
     if (i >= 1 && i <= n - 1 && j >= 1 && j <= n - 1) {
       // the east and north edges are this node's own (a, c); west and south are the neighbours'
-      const T ww = T(0.5 * (LO(i - 1, j) + UP(i - 1, j - 1))), ws = T(0.5 * (UP(i, j - 1) + LO(i - 1, j - 1)));
+      const T ww = T(half_pos(LO(i - 1, j) + UP(i - 1, j - 1))), ws = T(half_pos(UP(i, j - 1) + LO(i - 1, j - 1)));
       d = om / (a + ww + c + ws + dr);  // the damped Jacobi factor omega D^-1 (with the lumped reaction)
     }
     wx[(size_t)b * V + q] = a;
@@ -251,22 +258,36 @@ __global__ void k_convert(size_t count, const S* __restrict__ in, T* __restrict_
     out[q] = T(in[q]);
 }
 
-// P u_H at the fine nodes (into x64) -- padded arrays, ring zero
+// k 2^-l as a double (0 <= k < 2^l, l <= 30), assembled from its bits on the integer units (the
+// barycentric coordinates of nested P1 interpolation are such dyadic fractions, exactly)
+__device__ __forceinline__ double dyadic(int k, int l) {
+  if (k == 0) return 0.0;
+  const int msb = 31 - __clz(k);
+  const unsigned long long bits = ((unsigned long long)(msb - l + 1023) << 52) |
+                                  (((unsigned long long)k << (52 - msb)) & ((1ull << 52) - 1));
+  return __longlong_as_double((long long)bits);
+}
+
+// P u_H at the fine nodes (into x64) -- padded arrays, ring zero.  In the coarse cell of fine node
+// (i, j), with s = (i mod r) / r and t = (j mod r) / r (r = n / nc): on the lower triangle (s >= t)
+// P u_H = u00 + s (u10 - u00) + t (u11 - u10), on the upper u00 + t (u01 - u00) + s (u11 - u01) --
+// two FP64 differences and two fused multiply-adds per node, the rest on the integer units
 template <typename T>
 __global__ void k_interp(int n, int nc, int B, const double* __restrict__ uH, double* __restrict__ x64) {
   const int nt = tiles_interior(n);
   const int b = blockIdx.x / nt, ch = blockIdx.x % nt;
   if (b >= B) return;
   const int lr = ilog2(n / nc), rm = (1 << lr) - 1, ldc = nc + 1;
-  const double inv = 1.0 / (double)(1 << lr);
   const double* __restrict__ u = uH + (size_t)b * gsz(nc);
   double* x = x64 + (size_t)b * ssz(n);
   for_tile(n, ch, [&](int p, int i, int j) {
-    const int I = i >> lr, J = j >> lr;
-    const double xi_ = (double)(i & rm) * inv, et = (double)(j & rm) * inv;
-    const int c0 = J * ldc + I;
-    x[p] = xi_ >= et ? (1.0 - xi_) * u[c0] + (xi_ - et) * u[c0 + 1] + et * u[c0 + ldc + 1]
-                     : (1.0 - et) * u[c0] + (et - xi_) * u[c0 + ldc] + xi_ * u[c0 + ldc + 1];
+    const int ki = i & rm, kj = j & rm;
+    const int c0 = (j >> lr) * ldc + (i >> lr);
+    const bool lower = ki >= kj;
+    const double u00 = u[c0], u11 = u[c0 + ldc + 1];
+    const double uc = lower ? u[c0 + 1] : u[c0 + ldc];
+    const double s1 = dyadic(lower ? ki : kj, lr), s2 = dyadic(lower ? kj : ki, lr);
+    x[p] = fma(s2, u11 - uc, fma(s1, uc - u00, u00));
   });
 }
 
