@@ -360,12 +360,12 @@ mq_status coefficients_separable(mq_ctx* c, int n, int K, const double* d_Y, int
   const double cs = c->csum[K - 1];
   while (std::ldexp(cs, ey) > 1.0) --ey;
   while (std::ldexp(cs, ey + 1) <= 1.0) ++ey;
-  if ((st = grow(c, c->tsl, mq::tc_slices_bytes(B * n, k1pad))) != MQ_OK) return st;
+  if ((st = grow(c, c->tsl, mq::sep_scratch_bytes(B, n, K, k1pad))) != MQ_OK) return st;
   if ((st = grow(c, c->tc_err, sizeof(int))) != MQ_OK) return st;
   const mq::SepTerms terms{c->d_k1start, c->d_tlist, c->d_k2, c->d_cj[0]};
   MQ_CUDA(c, mq::launch_coef_sep(d_Y, ldy, B, K, k1pad, terms, it->second.second, n, c->a0, ey, c->tsl.p, d_a,
                                  (int*)c->tc_err.p, c->stream));
-  c->n_launches += 4;  // two stage-1 kernels and two tensor-core launches
+  c->n_launches += 5;  // the products Y c, two stage-1 kernels and two tensor-core launches
   return MQ_OK;
 }
 

@@ -135,8 +135,9 @@ size_t sep_tables_bytes(int n, int k1pad, int k2max);
 cudaError_t launch_sep_tables(int n, int k1max, int k1pad, int k2max, double* d_work, void* d_tables, SepTables* t,
                               cudaStream_t st);
 // a[b][t] for B rows of Y with the first K terms: k1pad >= the padded largest k1 of those terms,
-// ey the exponent with |2^ey T| <= 1/2 for every stage-1 value T; d_tslices: tc_slices_bytes(B n,
-// k1pad) bytes of scratch
+// ey the exponent with |2^ey T| <= 1/2 for every stage-1 value T; d_tslices: sep_scratch_bytes(B,
+// n, K, k1pad) bytes of scratch (the stage-1 slices, then the products Y c)
+size_t sep_scratch_bytes(int B, int n, int K, int k1pad);
 cudaError_t launch_coef_sep(const double* d_Y, int ldy, int B, int K, int k1pad, const SepTerms& terms,
                             const SepTables& tab, int n, double a0, int ey, void* d_tslices, double* d_a, int* d_err,
                             cudaStream_t st);

@@ -202,17 +202,32 @@ __global__ void k_sep_sx(int n, int plane, int k1max, int kpad, double* __restri
   }
 }
 
+// yc[b][t] = Y[b][t] c_t for t < K: the products stage 1 sums, formed once per (sample, term)
+// instead of once per (mesh row, term) -- the same roundings, so stage 1 is bit-identical
+__global__ void k_sep_yc(const double* __restrict__ Y, int ldy, int B, int K, const double* __restrict__ cj,
+                         double* __restrict__ yc) {
+  const size_t tot = (size_t)B * K;
+  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(q / K), t = (int)(q % K);
+    yc[q] = Y[(size_t)b * ldy + t] * cj[t];
+  }
+}
+
 // Stage 1: T[m = b n + j][k1 - 1] for one plane, written as the 7 BF16 slices of scale * T in the
 // layout of k_slice_rows ([7][kpad/8][rows_pad][8]); one thread per (row, group of 8 k1 values).
-// The terms of each k1 are listed in increasing t: tlist[k1start[k1] .. k1start[k1 + 1]).
-__global__ void k_sep_stage1(const double* __restrict__ Y, int ldy, int B, int n, int plane, int K, int kpad,
+// The terms of each k1 are listed in increasing t: tlist[k1start[k1] .. k1start[k1 + 1]).  The
+// slices are the balanced base-256 digits of W = scale T 2^48 rounded to an integer (|W| <= 2^55):
+// W = sum_p d_p 2^{8(6-p)}, |d_p| <= 128, formed on the integer units -- the same representation
+// error bound (half a unit of the last digit) as digit-by-digit rounding in FP64.
+__global__ void k_sep_stage1(const double* __restrict__ yc, int B, int n, int plane, int K, int kpad,
                              const int* __restrict__ k1start, const int* __restrict__ tlist,
-                             const int* __restrict__ tk2, const double* __restrict__ cj, const double* __restrict__ syt,
+                             const int* __restrict__ tk2, const double* __restrict__ syt,
                              double scale, int rows_pad, __nv_bfloat16* __restrict__ out) {
   (void)plane;
   const size_t tot = (size_t)rows_pad * (kpad / 8);
   const size_t sstride = (size_t)rows_pad * kpad;
   const int rows = B * n;
+  const double s48 = scale * 281474976710656.0;  // scale 2^48 (a power of two)
   for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += (size_t)gridDim.x * blockDim.x) {
     const int m = (int)(q % rows_pad), kg = (int)(q / rows_pad);
     __align__(16) __nv_bfloat16 sl[kSlices][8];
@@ -221,20 +236,22 @@ __global__ void k_sep_stage1(const double* __restrict__ Y, int ldy, int B, int n
       double v = 0.0;
       if (m < rows) {
         const int b = m / n, j = m % n, k1 = kg * 8 + e + 1;
-        const double* yb = Y + (size_t)b * ldy;
+        const double* yb = yc + (size_t)b * K;
         for (int idx = k1start[k1]; idx < k1start[k1 + 1]; ++idx) {
           const int t = tlist[idx];
           if (t >= K) break;
-          v = fma(yb[t] * cj[t], syt[(size_t)tk2[t] * n + j], v);
+          v = fma(yb[t], syt[(size_t)tk2[t] * n + j], v);
         }
       }
-      v *= scale;
+      long long w = __double2ll_rn(v * s48);
 #pragma unroll
-      for (int p = 0; p < kSlices; ++p) {
-        const double r = rint(v);
-        sl[p][e] = __float2bfloat16_rn((float)r);
-        v = (v - r) * 256.0;
+      for (int p = 0; p < kSlices - 1; ++p) {
+        const int sh = 8 * (kSlices - 1 - p);
+        const long long d = (w + (1LL << (sh - 1))) >> sh;  // nearest, |d| <= 128
+        w -= d << sh;
+        sl[p][e] = __float2bfloat16_rn((float)(int)d);
       }
+      sl[kSlices - 1][e] = __float2bfloat16_rn((float)(int)w);
     }
 #pragma unroll
     for (int p = 0; p < kSlices; ++p)
@@ -621,15 +638,21 @@ cudaError_t launch_sep_tables(int n, int k1max, int k1pad, int k2max, double* d_
   return cudaGetLastError();
 }
 
+size_t sep_scratch_bytes(int B, int n, int K, int k1pad) {
+  return ((tc_slices_bytes(B * n, k1pad) + 255) & ~(size_t)255) + (size_t)B * K * sizeof(double);
+}
+
 cudaError_t launch_coef_sep(const double* d_Y, int ldy, int B, int K, int k1pad, const SepTerms& terms,
                             const SepTables& tab, int n, double a0, int ey, void* d_tslices, double* d_a, int* d_err,
                             cudaStream_t st) {
   if (B == 0) return cudaSuccess;
   if (k1pad % kTK || k1pad <= 0 || k1pad > tab.k1pad || (long)B * n > 0x7fffffffL - 128) return cudaErrorInvalidValue;
   const int rows = B * n, rp = tc_pad_rows(rows);
+  double* yc = (double*)((char*)d_tslices + ((tc_slices_bytes(rows, k1pad) + 255) & ~(size_t)255));
+  k_sep_yc<<<grid1((size_t)B * K), 256, 0, st>>>(d_Y, ldy, B, K, terms.cj, yc);
   for (int plane = 0; plane < 2; ++plane) {
     k_sep_stage1<<<grid1((size_t)rp * (k1pad / 8)), 256, 0, st>>>(
-        d_Y, ldy, B, n, plane, K, k1pad, terms.k1start, terms.tlist, terms.tk2, terms.cj, tab.syt[plane],
+        yc, B, n, plane, K, k1pad, terms.k1start, terms.tlist, terms.tk2, tab.syt[plane],
         std::ldexp(256.0, ey), rp, (__nv_bfloat16*)d_tslices);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
