@@ -189,9 +189,11 @@ mq_status mq_set_solver_options(mq_ctx* ctx, double tol_inner, int32_t max_inner
 /* Coarse eigensolver options (values <= 0 keep the defaults): tol_eig is the target of the
  * relative eigen-residual ||A_H x - theta M_H x|| / (theta ||M_H x||) of LOBPCG, max_eig the
  * iteration cap (200).  The Rayleigh quotient theta = lambda_H is accurate to about the square of
- * tol_eig, the eigenvector (and so G(u_H)) to about tol_eig.  Defaults: 1e-6 for level
- * evaluations of eigenvalues with coefficient families 0 and 1 (lambda_H to ~1e-13; the two-grid
- * values depend on u_H only through one shifted inverse-iteration step and stay at FP64
+ * tol_eig, the eigenvector (and so G(u_H)) to about tol_eig: the relative eigenvalue error is at
+ * most tol_eig^2 kappa(M) theta / (lambda_2 - theta), kappa(M) <= 4 for the P1 mass matrix.
+ * Defaults: 1e-6 for level evaluations of eigenvalues with coefficient families 0 and 1
+ * (lambda_H within ~3e-12 relative at worst, 5e-14 measured on the six-level workload; the
+ * two-grid values depend on u_H only through one shifted inverse-iteration step and stay at FP64
  * rounding); 1e-8 for the islands family of mq_set_islands (its unresolved coarse mesh makes the
  * two-grid values ~1e4 times more sensitive to u_H) and when mq_eval_point returns the
  * eigenvector; 1e-11 for MQ_QOI_FUNCTIONAL. */

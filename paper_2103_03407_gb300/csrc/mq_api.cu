@@ -567,8 +567,9 @@ mq_status run_samples(mq_ctx* c, const LevelGeom& g, int R, int npts, int chunk,
   p.outer = (int*)c->outer.p;
   p.u_out = want_u ? (double*)c->uout.p : nullptr;
   // Default tolerances.  lambda_H is the Rayleigh quotient of the LOBPCG iterate, accurate to the
-  // square of its relative eigen-residual: 1e-6 leaves it within ~5e-14 of the exact coarse
-  // eigenvalue (measured on the six-level workload, levels 0-2 and 5), and the two-grid values,
+  // square of its relative eigen-residual (at most tol^2 kappa(M) theta / (lambda_2 - theta), with
+  // kappa(M) <= 4): 1e-6 leaves it within ~3e-12 of the exact coarse eigenvalue at worst and within
+  // 5e-14 measured on the six-level workload (levels 0-2 and 5), and the two-grid values,
   // which depend on u_H only through one shifted inverse-iteration step, moved by less than 3e-15
   // against 1e-8 -- with 2.6 fewer LOBPCG iterations per sample.  How far lambda^h moves with the
   // eigenvector error grows with the coarse-fine discrepancy: on the second test problem, whose
