@@ -91,3 +91,14 @@ def test_fine_dof_solves_counts_both_meshes_of_a_level():
     wl = WORKLOADS["mlqmc4_h16_128"]
     # 4096*16*15^2 + 2048*16*(31^2+15^2) + 1024*16*(63^2+31^2) + 512*16*(127^2+63^2)
     assert bench.fine_dof_solves(wl) == 65536 * 225 + 32768 * 1186 + 16384 * 4930 + 8192 * 20098
+
+
+def test_bench_traffic_pins_match_the_kernel_sources():
+    # bench.py reports ncu DRAM figures beside two rooflines only while the kernel sources are the
+    # ones the figures were measured on (sha256 of the files); a kernel change without a new
+    # capture would silently turn them into null
+    import bench
+
+    assert bench.KMINRES_TRAFFIC["source_sha256"] == bench._stream_source_hash()
+    assert bench.SAMPLE_KERNEL_TRAFFIC["source_sha256"] == bench._percta_source_hash()
+    assert 0.9 < bench.KMINRES_TRAFFIC["dram_per_algorithmic"] <= 1.05
